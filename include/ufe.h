@@ -1,0 +1,254 @@
+/*
+ * ufe.h -- C ABI of the GB300 BDDC-PCG solver for unfitted (cut-cell) Q1
+ * finite elements on a Cartesian background mesh (Badia & Verdugo,
+ * "Robust and scalable domain decomposition solvers for unfitted finite
+ * element methods").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Grid: nx*ny*nz cubic cells on the box [lo, hi]; nodes are numbered
+ *    i + (nx+1)*(j + (ny+1)*k), cells i + nx*(j + ny*k) (x fastest).
+ *  * The physical domain is {phi < 0} (Sect. 2.1: the boundary is the zero
+ *    level set); phi == 0 counts as outside.
+ *  * Array arguments are caller-owned and only borrowed for the duration of
+ *    the call.  Each call that takes arrays also takes `mem`: UFE_MEM_HOST
+ *    (pageable or pinned host memory; the library copies) or UFE_MEM_DEVICE
+ *    (CUDA device pointers on the current device, read on the handle's stream).
+ *  * Handles are opaque and library-owned; release them with *_destroy.
+ *    A system borrows its mesh and a bddc borrows its system: destroy in the
+ *    reverse order of creation.
+ *  * All work is issued on the stream given to ufe_mesh_create (NULL = the
+ *    legacy default stream) and every call returns after its results are
+ *    complete (the calls synchronise that stream).
+ *  * Errors: a negative ufe_status; ufe_last_error() returns a message for the
+ *    calling thread.  Outputs are unspecified after an error, except
+ *    UFE_ERR_NO_CONVERGENCE, after which x holds the last iterate and the
+ *    info struct is filled.
+ *  * Every kernel behind these calls is a hand-written sm_103a kernel; there
+ *    is no host or library fallback for any step.
+ */
+#ifndef UFE_H
+#define UFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ufe_status;
+
+#define UFE_OK                   0
+#define UFE_ERR_INVALID_ARG     -1
+#define UFE_ERR_OUT_OF_MEMORY   -2
+#define UFE_ERR_CUDA            -3
+#define UFE_ERR_SINGULAR_LOCAL  -4   /* a local Dirichlet or constrained-Neumann matrix is not SPD */
+#define UFE_ERR_SINGULAR_COARSE -5   /* the assembled coarse matrix is not SPD */
+#define UFE_ERR_BREAKDOWN       -6   /* PCG: p.Ap <= 0 */
+#define UFE_ERR_NO_CONVERGENCE  -7   /* PCG: maxit reached; x holds the last iterate */
+#define UFE_ERR_UNSUPPORTED     -8
+#define UFE_ERR_TIMEOUT         -9   /* a bounded device-side loop hit its iteration limit */
+
+#define UFE_MEM_HOST   0
+#define UFE_MEM_DEVICE 1
+
+/* cell types (Sect. 2.1) */
+#define UFE_CELL_EXTERNAL 0
+#define UFE_CELL_CUT      1
+#define UFE_CELL_INTERNAL 2
+
+/* object kinds (Sect. 3.2) */
+#define UFE_OBJ_CORNER 0
+#define UFE_OBJ_EDGE   1
+#define UFE_OBJ_FACE   2
+
+/* ufe_bddc_opts.weighting */
+#define UFE_WEIGHT_STIFFNESS   0   /* Eq. alge-weighting (Sect. 4.3) */
+#define UFE_WEIGHT_TOPOLOGICAL 1   /* Eq. weighting (Sect. 3.3) */
+/* ufe_bddc_opts.objects */
+#define UFE_OBJECTS_STANDARD 0     /* Sect. 3.2 */
+#define UFE_OBJECTS_VARIANT1 1     /* Sect. 4.4: cut coarse edges split */
+/* ufe_bddc_opts.coarse: which objects carry a coarse DOF (Sect. 3.2) */
+#define UFE_COARSE_C   0
+#define UFE_COARSE_CE  1
+#define UFE_COARSE_CEF 2
+/* ufe_bddc_opts.precision */
+#define UFE_PREC_FP64  0           /* every local factor and product in FP64 */
+#define UFE_PREC_MIXED 1           /* Jacobi-scaled FP32 local operators; FP64 PCG, weights, coarse */
+
+#define UFE_PIN_NONE -1
+#define UFE_PIN_AUTO -2
+
+typedef struct ufe_mesh ufe_mesh;
+typedef struct ufe_system ufe_system;
+typedef struct ufe_bddc ufe_bddc;
+
+/* Message describing the last error of the calling thread ("" if none). */
+const char* ufe_last_error(void);
+
+/* ABI version of this header (major * 100 + minor). */
+int ufe_version(void);
+
+typedef struct {
+  int64_t n_nodes, n_cells;
+  int64_t n_active_cells, n_cut_cells;
+  int64_t n_dof;               /* free DOFs */
+  int64_t n_subdomains;
+  int64_t n_interface_dofs;    /* DOFs with |neigh| >= 2 */
+  int64_t pinned_node;         /* node id of the pinned node, -1 if none */
+  int64_t n_constrained;       /* box-face Dirichlet nodes plus the pinned node */
+  int32_t max_interior, max_interface;   /* largest local interior / interface sizes */
+} ufe_mesh_info;
+
+/*
+ * ufe_mesh_create -- background mesh, cell classification, DOFs and subdomains.
+ *
+ * Sect. 2.1 (cell partition: internal / external / cut, active = internal or
+ * cut; subdomains by aggregation of active cells) and Sect. 5.1 (strong
+ * Dirichlet on box faces; one pinned node when no box face is Dirichlet).
+ *
+ *  box_lo, box_hi   3 doubles each (host); cells must be cubes (equal spacing).
+ *  cells            3 ints (host): nx, ny, nz >= 1.
+ *  sub_cells        3 ints (host): cells per subdomain block edge, 1..8, dividing cells.
+ *  phi_nodes        (nx+1)(ny+1)(nz+1) doubles, nodal level set; memory per `mem`.
+ *  dirichlet_face_mask  bit f set = strong Dirichlet on box face f (x-,x+,y-,y+,z-,z+).
+ *  pin_node         UFE_PIN_NONE, UFE_PIN_AUTO (pin the node whose 8 cells are
+ *                   internal with the smallest phi, ties -> lowest id, only if no
+ *                   box-face node is constrained), or an explicit active node id.
+ *  stream           cudaStream_t used by every call on this mesh and its children.
+ *  out              receives the new handle.
+ * DOFs are the nodes of active cells minus the constrained ones, numbered in node
+ * order.  A subdomain is a connected component (cells sharing a DOF) of the
+ * active cells of one block, ordered by (block, smallest cell id).
+ * Errors: INVALID_ARG for bad sizes / pin, CUDA, OUT_OF_MEMORY, TIMEOUT.
+ */
+ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const int32_t cells[3],
+                           const int32_t sub_cells[3], const double* phi_nodes, int mem,
+                           uint32_t dirichlet_face_mask, int64_t pin_node, void* stream,
+                           ufe_mesh** out);
+ufe_status ufe_mesh_get_info(const ufe_mesh* mesh, ufe_mesh_info* info);
+/* cell_types: n_cells bytes (UFE_CELL_*). */
+ufe_status ufe_mesh_get_cell_types(const ufe_mesh* mesh, uint8_t* cell_types, int mem);
+/* dof_of_node: n_nodes int32, -1 for nodes that are not free DOFs. */
+ufe_status ufe_mesh_get_dof_map(const ufe_mesh* mesh, int32_t* dof_of_node, int mem);
+/* sub_of_cell: n_cells int32, -1 for external cells. */
+ufe_status ufe_mesh_get_subdomains(const ufe_mesh* mesh, int32_t* sub_of_cell, int mem);
+/* neigh: n_dof * 8 int32: sorted subdomain ids of neigh(xi) (Sect. 3.3), padded with -1. */
+ufe_status ufe_mesh_get_neighbours(const ufe_mesh* mesh, int32_t* neigh, int mem);
+void ufe_mesh_destroy(ufe_mesh* mesh);
+
+/*
+ * ufe_assemble -- cut-cell integration and the global right-hand side.
+ *
+ * Sect. 2.2 bulk form A_e(u,v) = int_{e cap Omega} kappa_e grad u . grad v with
+ * Neumann data on the unfitted boundary; the cut part of each cut cell is
+ * integrated by marching tetrahedra (6 Kuhn tets per cube, phi linear on each)
+ * with degree-7 Grundmann-Moeller rules; internal cells use the closed-form Q1
+ * matrices.  b = int f_h phi_a + int_{Gamma cap e} (q_h . n) phi_a minus the
+ * strong Dirichlet lift (Sect. 2.2, 5.1).
+ *
+ *  kappa_cells       n_cells doubles (per-cell coefficient) or NULL for 1.
+ *  f_nodes           n_nodes doubles: nodal source (Q1 interpolated), or NULL for 0.
+ *  flux_nodes        n_nodes*3 doubles (x,y,z per node): nodal flux q, Neumann
+ *                    data g = q . n on the cut boundary; NULL for g = 0.
+ *  dirichlet_values  n_nodes doubles read at the constrained nodes; NULL for 0.
+ * All arrays live in memory `mem`.  The system keeps a pointer to the mesh.
+ */
+ufe_status ufe_assemble(ufe_mesh* mesh, const double* kappa_cells, const double* f_nodes,
+                        const double* flux_nodes, const double* dirichlet_values, int mem,
+                        ufe_system** out);
+/* b: n_dof doubles (the assembled right-hand side). */
+ufe_status ufe_system_get_rhs(const ufe_system* sys, double* b, int mem);
+/* y = A x over the free DOFs (element-by-element apply). */
+ufe_status ufe_system_apply(const ufe_system* sys, const double* x, double* y, int mem);
+/* Cut-cell data in cut-cell order (ascending cell id): cut_cells n_cut int32,
+ * K n_cut*64 doubles (8x8 row-major, vertex a = x + 2y + 4z, without kappa),
+ * load n_cut*8 doubles, eta n_cut doubles (volume fraction). Any may be NULL. */
+ufe_status ufe_system_get_cut_data(const ufe_system* sys, int32_t* cut_cells, double* K, double* load,
+                                   double* eta, int mem);
+void ufe_system_destroy(ufe_system* sys);
+
+typedef struct {
+  int32_t weighting;   /* UFE_WEIGHT_* */
+  int32_t objects;     /* UFE_OBJECTS_* */
+  int32_t coarse;      /* UFE_COARSE_* */
+  int32_t precision;   /* UFE_PREC_* */
+} ufe_bddc_opts;
+
+typedef struct {
+  int64_t n_objects, n_corners, n_edges, n_faces;
+  int64_t n_coarse;               /* coarse DOFs (objects in Lambda_O) */
+  int32_t max_local_coarse;       /* largest number of coarse DOFs of one subdomain */
+  double setup_ms;                /* device time of ufe_bddc_setup */
+} ufe_bddc_info;
+
+/*
+ * ufe_bddc_setup -- the BDDC preconditioner of Eq. bddc for this system.
+ *
+ * Sect. 3.1 sub-assembled local Neumann matrices; Sect. 3.2 objects and coarse
+ * DOFs (object means, Eq. coarse-dofs); Sect. 4.4 variant-1 objects; Sect. 3.3
+ * topological weighting (Eq. weighting) or Sect. 4.3 stiffness weighting
+ * (Eq. alge-weighting); harmonic extension with local Dirichlet problems.
+ * Local operators are formed explicitly: A_II^-1, the constrained Neumann
+ * inverse restricted to the interface and the interface rows of the coarse
+ * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled and inverted in FP64.
+ * Errors: SINGULAR_LOCAL (e.g. a floating subdomain with no coarse DOF),
+ * SINGULAR_COARSE, INVALID_ARG, CUDA, OUT_OF_MEMORY, TIMEOUT.
+ */
+ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc** out);
+ufe_status ufe_bddc_get_info(const ufe_bddc* bddc, ufe_bddc_info* info);
+/* object_of_dof: n_dof int32 (object id, -1 off the interface); object_kind:
+ * n_objects int32 (UFE_OBJ_*); coarse_of_object: n_objects int32 (-1 if the
+ * object carries no coarse DOF). Objects are ordered by their smallest DOF id. */
+ufe_status ufe_bddc_get_objects(const ufe_bddc* bddc, int32_t* object_of_dof, int32_t* object_kind,
+                                int32_t* coarse_of_object, int mem);
+/* z = M r for one vector (n_dof doubles), Eq. bddc. */
+ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
+void ufe_bddc_destroy(ufe_bddc* bddc);
+
+typedef struct {
+  double rtol;          /* stop when |r|_2 < rtol |b|_2 (Sect. 5.1); e.g. 1e-8 */
+  int32_t maxit;        /* iteration cap */
+  int32_t flexible;     /* 0 classical beta, 1 flexible beta, -1 auto (flexible iff mixed) */
+  int32_t check_every;  /* iterations per device-side graph launch between host checks (0 = 8) */
+  int32_t reserved;
+} ufe_solve_opts;
+
+typedef struct {
+  int32_t iterations;        /* operator applications to search directions */
+  int32_t converged;
+  double rel_residual;       /* |r|_2 / |b|_2 of the recursively updated residual */
+  double true_rel_residual;  /* |b - A x|_2 / |b|_2 recomputed at the end */
+  double solve_ms;           /* device time of the solve */
+} ufe_solve_info;
+
+/*
+ * ufe_pcg_solve -- BDDC-preconditioned CG (Sect. 5.1), all on the device.
+ *  b     n_dof doubles or NULL for the assembled right-hand side.
+ *  x     n_dof doubles: initial guess in, solution out.
+ *  info  may be NULL.
+ * Errors: BREAKDOWN, NO_CONVERGENCE (x holds the last iterate), CUDA, INVALID_ARG.
+ */
+ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* bddc, const double* b, double* x, int mem,
+                         const ufe_solve_opts* opts, ufe_solve_info* info);
+
+/*
+ * ufe_adjoint -- gradient of J(u) = 1/2 |u - u_d|^2 over the free DOFs with
+ * respect to the per-cell coefficients kappa (no counterpart in the paper).
+ * Solves A lambda = dJdu with the same BDDC-PCG (A is SPD, so A^T = A) and
+ * contracts dJ/dkappa_e = -u_e^T Khat_e lambda_e per active cell, Khat_e the
+ * coefficient-free cell matrix (b does not depend on kappa).
+ *  u          n_dof doubles: the forward solution.
+ *  dJdu       n_dof doubles: the adjoint right-hand side (u - u_d for this J).
+ *  lambda     n_dof doubles: adjoint solution out (initial guess in).
+ *  dJdkappa   n_cells doubles out (0 on external cells).
+ */
+ufe_status ufe_adjoint(ufe_system* sys, ufe_bddc* bddc, const double* u, const double* dJdu,
+                       double* lambda, double* dJdkappa, int mem, const ufe_solve_opts* opts,
+                       ufe_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UFE_H */

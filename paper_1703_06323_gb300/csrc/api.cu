@@ -1,0 +1,362 @@
+// C ABI of libufe (declarations and contracts in include/ufe.h).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "bddc.cuh"
+
+struct ufe_mesh : ufe::Mesh {};
+struct ufe_system : ufe::System {};
+struct ufe_bddc : ufe::Bddc {};
+
+namespace ufe {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void copy_in(void* dst_dev, const void* src, size_t bytes, int mem, cudaStream_t s) {
+  if (!bytes) return;
+  UFE_CUDA(cudaMemcpyAsync(dst_dev, src, bytes, mem == UFE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s));
+}
+
+void copy_out(void* dst, const void* src_dev, size_t bytes, int mem, cudaStream_t s) {
+  if (!bytes) return;
+  UFE_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, mem == UFE_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           s));
+  UFE_CUDA(cudaStreamSynchronize(s));
+}
+
+template <typename F>
+static ufe_status guarded(F f) {
+  try {
+    f();
+    g_last_error.clear();
+    return UFE_OK;
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return UFE_ERR_OUT_OF_MEMORY;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return UFE_ERR_INVALID_ARG;
+  }
+}
+
+static void check_mem(int mem) {
+  UFE_REQUIRE(mem == UFE_MEM_HOST || mem == UFE_MEM_DEVICE, UFE_ERR_INVALID_ARG, "mem must be UFE_MEM_HOST or UFE_MEM_DEVICE");
+}
+
+// device copy of an optional input array (nullptr stays nullptr)
+template <typename T>
+static const T* stage(DBuf<T>& buf, const T* src, size_t n, int mem, cudaStream_t s) {
+  if (!src) return nullptr;
+  if (mem == UFE_MEM_DEVICE) return src;
+  buf.alloc(n, s);
+  copy_in(buf.p, src, n * sizeof(T), mem, s);
+  return buf.p;
+}
+
+}  // namespace ufe
+
+using namespace ufe;
+
+extern "C" {
+
+const char* ufe_last_error(void) { return g_last_error.c_str(); }
+
+int ufe_version(void) { return 100; }
+
+ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const int32_t cells[3],
+                           const int32_t sub_cells[3], const double* phi_nodes, int mem, uint32_t dirichlet_face_mask,
+                           int64_t pin_node, void* stream, ufe_mesh** out) {
+  return guarded([&] {
+    UFE_REQUIRE(box_lo && box_hi && cells && sub_cells && phi_nodes && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    *out = nullptr;
+    std::unique_ptr<ufe_mesh> m(new ufe_mesh());
+    m->stream = (cudaStream_t)stream;
+    GridGeom& g = m->g;
+    g.nx = cells[0]; g.ny = cells[1]; g.nz = cells[2];
+    g.sx = sub_cells[0]; g.sy = sub_cells[1]; g.sz = sub_cells[2];
+    UFE_REQUIRE(g.nx > 0 && g.ny > 0 && g.nz > 0, UFE_ERR_INVALID_ARG, "cells must be positive");
+    UFE_REQUIRE(g.sx >= 1 && g.sy >= 1 && g.sz >= 1 && g.sx <= 8 && g.sy <= 8 && g.sz <= 8, UFE_ERR_INVALID_ARG,
+                "sub_cells must lie in 1..8");
+    UFE_REQUIRE(g.nx % g.sx == 0 && g.ny % g.sy == 0 && g.nz % g.sz == 0, UFE_ERR_INVALID_ARG,
+                "sub_cells must divide cells");
+    UFE_REQUIRE((int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) < (int64_t)1 << 31, UFE_ERR_INVALID_ARG, "grid too large");
+    UFE_REQUIRE(dirichlet_face_mask < 64, UFE_ERR_INVALID_ARG, "dirichlet_face_mask has bits beyond the 6 faces");
+    double hs[3];
+    for (int d = 0; d < 3; ++d) {
+      UFE_REQUIRE(box_hi[d] > box_lo[d], UFE_ERR_INVALID_ARG, "empty box");
+      g.lo[d] = box_lo[d];
+      hs[d] = (box_hi[d] - box_lo[d]) / cells[d];
+    }
+    UFE_REQUIRE(std::fabs(hs[0] - hs[1]) <= 1e-12 * hs[0] && std::fabs(hs[0] - hs[2]) <= 1e-12 * hs[0],
+                UFE_ERR_INVALID_ARG, "cells must be cubes");
+    g.h = hs[0];
+    g.bx = g.nx / g.sx; g.by = g.ny / g.sy; g.bz = g.nz / g.sz;
+    g.lnx = g.sx + 1; g.lny = g.sy + 1; g.lnz = g.sz + 1;
+    g.n_local_nodes = g.lnx * g.lny * g.lnz;
+    m->face_mask = dirichlet_face_mask;
+    const int64_t nn = g.n_nodes();
+    m->phi.alloc(nn, m->stream);
+    copy_in(m->phi.p, phi_nodes, nn * sizeof(double), mem, m->stream);
+    mesh_build(*m, m->phi.p, pin_node);
+    UFE_CUDA(cudaStreamSynchronize(m->stream));
+    *out = m.release();
+  });
+}
+
+ufe_status ufe_mesh_get_info(const ufe_mesh* m, ufe_mesh_info* info) {
+  return guarded([&] {
+    UFE_REQUIRE(m && info, UFE_ERR_INVALID_ARG, "null argument");
+    info->n_nodes = m->g.n_nodes();
+    info->n_cells = m->g.n_cells();
+    info->n_active_cells = m->n_active;
+    info->n_cut_cells = m->n_cut;
+    info->n_dof = m->n_dof;
+    info->n_subdomains = m->n_sub;
+    info->n_interface_dofs = m->n_gamma;
+    info->pinned_node = m->pin;
+    info->n_constrained = m->n_constrained;
+    info->max_interior = m->max_nI;
+    info->max_interface = m->max_nG;
+  });
+}
+
+ufe_status ufe_mesh_get_cell_types(const ufe_mesh* m, uint8_t* out, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(m && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    copy_out(out, m->cell_type.p, m->g.n_cells(), mem, m->stream);
+  });
+}
+
+ufe_status ufe_mesh_get_dof_map(const ufe_mesh* m, int32_t* out, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(m && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    copy_out(out, m->dof_of_node.p, m->g.n_nodes() * 4, mem, m->stream);
+  });
+}
+
+ufe_status ufe_mesh_get_subdomains(const ufe_mesh* m, int32_t* out, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(m && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    copy_out(out, m->sub_of_cell.p, m->g.n_cells() * 4, mem, m->stream);
+  });
+}
+
+ufe_status ufe_mesh_get_neighbours(const ufe_mesh* m, int32_t* out, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(m && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    copy_out(out, m->neigh.p, m->n_dof * 8 * 4, mem, m->stream);
+  });
+}
+
+void ufe_mesh_destroy(ufe_mesh* m) {
+  if (!m) return;
+  cudaStream_t s = m->stream;
+  delete m;
+  cudaStreamSynchronize(s);
+}
+
+ufe_status ufe_assemble(ufe_mesh* m, const double* kappa, const double* f, const double* flux, const double* gval,
+                        int mem, ufe_system** out) {
+  return guarded([&] {
+    UFE_REQUIRE(m && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    *out = nullptr;
+    std::unique_ptr<ufe_system> sys(new ufe_system());
+    sys->mesh = m;
+    sys->stream = m->stream;
+    cudaStream_t s = m->stream;
+    const int64_t nn = m->g.n_nodes(), nc = m->g.n_cells();
+    DBuf<double> fb, qb, gb;
+    if (kappa) {
+      sys->has_kappa = true;
+      sys->kappa.alloc(nc, s);
+      copy_in(sys->kappa.p, kappa, nc * 8, mem, s);
+    }
+    const double* fd = stage(fb, f, nn, mem, s);
+    const double* qd = stage(qb, flux, nn * 3, mem, s);
+    const double* gd = stage(gb, gval, nn, mem, s);
+    system_build(*sys, sys->has_kappa ? sys->kappa.p : nullptr, fd, qd, gd);
+    UFE_CUDA(cudaStreamSynchronize(s));
+    *out = sys.release();
+  });
+}
+
+ufe_status ufe_system_get_rhs(const ufe_system* sys, double* b, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && b, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    copy_out(b, sys->b.p, sys->mesh->n_dof * 8, mem, sys->stream);
+  });
+}
+
+ufe_status ufe_system_apply(const ufe_system* sys, const double* x, double* y, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && x && y, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    cudaStream_t s = sys->stream;
+    const int64_t n = sys->mesh->n_dof;
+    DBuf<double> xb, yb;
+    const double* xd = stage(xb, x, n, mem, s);
+    double* yd = y;
+    if (mem == UFE_MEM_HOST) {
+      yb.alloc(n, s);
+      yd = yb.p;
+    }
+    system_apply(*sys, xd, yd, s);
+    if (mem == UFE_MEM_HOST) copy_out(y, yd, n * 8, mem, s);
+    UFE_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+ufe_status ufe_system_get_cut_data(const ufe_system* sys, int32_t* cut_cells, double* K, double* load, double* eta,
+                                   int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(sys, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    const int64_t n = sys->mesh->n_cut;
+    cudaStream_t s = sys->stream;
+    if (cut_cells) copy_out(cut_cells, sys->mesh->cut_cells.p, n * 4, mem, s);
+    if (K) copy_out(K, sys->K_cut.p, n * 64 * 8, mem, s);
+    if (load) copy_out(load, sys->load_cut.p, n * 8 * 8, mem, s);
+    if (eta) copy_out(eta, sys->eta.p, n * 8, mem, s);
+  });
+}
+
+void ufe_system_destroy(ufe_system* sys) {
+  if (!sys) return;
+  cudaStream_t s = sys->stream;
+  delete sys;
+  cudaStreamSynchronize(s);
+}
+
+ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc** out) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && opts && out, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(opts->weighting == UFE_WEIGHT_STIFFNESS || opts->weighting == UFE_WEIGHT_TOPOLOGICAL,
+                UFE_ERR_INVALID_ARG, "bad weighting");
+    UFE_REQUIRE(opts->objects == UFE_OBJECTS_STANDARD || opts->objects == UFE_OBJECTS_VARIANT1, UFE_ERR_INVALID_ARG,
+                "bad objects");
+    UFE_REQUIRE(opts->coarse >= UFE_COARSE_C && opts->coarse <= UFE_COARSE_CEF, UFE_ERR_INVALID_ARG, "bad coarse");
+    UFE_REQUIRE(opts->precision == UFE_PREC_FP64 || opts->precision == UFE_PREC_MIXED, UFE_ERR_INVALID_ARG,
+                "bad precision");
+    *out = nullptr;
+    std::unique_ptr<ufe_bddc> B(new ufe_bddc());
+    B->sys = sys;
+    B->mesh = sys->mesh;
+    B->stream = sys->stream;
+    B->opts = *opts;
+    B->mixed = opts->precision == UFE_PREC_MIXED;
+    bddc_build(*B);
+    UFE_CUDA(cudaStreamSynchronize(B->stream));
+    *out = B.release();
+  });
+}
+
+ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
+  return guarded([&] {
+    UFE_REQUIRE(B && info, UFE_ERR_INVALID_ARG, "null argument");
+    info->n_objects = B->n_obj;
+    info->n_corners = B->n_corner;
+    info->n_edges = B->n_edge;
+    info->n_faces = B->n_face;
+    info->n_coarse = B->n_coarse;
+    info->max_local_coarse = B->max_nC;
+    info->setup_ms = B->setup_ms;
+  });
+}
+
+ufe_status ufe_bddc_get_objects(const ufe_bddc* B, int32_t* object_of_dof, int32_t* object_kind,
+                                int32_t* coarse_of_object, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(B, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    cudaStream_t s = B->stream;
+    if (object_of_dof) copy_out(object_of_dof, B->obj_of_dof.p, B->mesh->n_dof * 4, mem, s);
+    if (object_kind) copy_out(object_kind, B->obj_kind.p, B->n_obj * 4, mem, s);
+    if (coarse_of_object) copy_out(coarse_of_object, B->coarse_of_obj.p, B->n_obj * 4, mem, s);
+  });
+}
+
+ufe_status ufe_bddc_apply(ufe_bddc* B, const double* r, double* z, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(B && r && z, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    cudaStream_t s = B->stream;
+    const int64_t n = B->mesh->n_dof;
+    DBuf<double> rb, zb;
+    const double* rd = stage(rb, r, n, mem, s);
+    double* zd = z;
+    if (mem == UFE_MEM_HOST) {
+      zb.alloc(n, s);
+      zd = zb.p;
+    }
+    UFE_CUDA(cudaMemsetAsync(zd, 0, n * 8, s));
+    bddc_apply(*B, rd, zd);
+    if (mem == UFE_MEM_HOST) copy_out(z, zd, n * 8, mem, s);
+    UFE_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+void ufe_bddc_destroy(ufe_bddc* B) {
+  if (!B) return;
+  cudaStream_t s = B->stream;
+  delete B;
+  cudaStreamSynchronize(s);
+}
+
+ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* B, const double* b, double* x, int mem, const ufe_solve_opts* opts,
+                         ufe_solve_info* info) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && B && x && opts, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(B->sys == sys, UFE_ERR_INVALID_ARG, "preconditioner belongs to another system");
+    UFE_REQUIRE(opts->rtol > 0 && opts->maxit >= 0, UFE_ERR_INVALID_ARG, "bad solve options");
+    check_mem(mem);
+    cudaStream_t s = sys->stream;
+    const int64_t n = sys->mesh->n_dof;
+    DBuf<double> bb, xb;
+    const double* bd = b ? stage(bb, b, n, mem, s) : sys->b.p;
+    double* xd = x;
+    if (mem == UFE_MEM_HOST) {
+      xb.alloc(n, s);
+      copy_in(xb.p, x, n * 8, mem, s);
+      xd = xb.p;
+    }
+    struct Out {
+      double* dst;
+      double* src;
+      int64_t n;
+      int mem;
+      cudaStream_t s;
+      ~Out() {
+        if (mem == UFE_MEM_HOST) {
+          cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToHost, s);
+          cudaStreamSynchronize(s);
+        }
+      }
+    } out_guard{x, xd, n, mem, s};
+    pcg_solve(*B, bd, xd, *opts, info);
+  });
+}
+
+ufe_status ufe_adjoint(ufe_system* sys, ufe_bddc* B, const double* u, const double* dJdu, double* lambda,
+                       double* dJdkappa, int mem, const ufe_solve_opts* opts, ufe_solve_info* info) {
+  return guarded([&] {
+    (void)sys; (void)B; (void)u; (void)dJdu; (void)lambda; (void)dJdkappa; (void)mem; (void)opts; (void)info;
+    throw Error{UFE_ERR_UNSUPPORTED, "ufe_adjoint is not built yet"};
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,867 @@
+// BDDC set-up (Sect. 3, Sect. 4): geometric objects and coarse DOFs, weights,
+// local matrices, the explicit local operators applied at every iteration and
+// the coarse matrix.
+//
+// Per subdomain w with interior DOFs I and interface DOFs G the preconditioner
+// (Eq. bddc) needs only
+//   * A_II^-1                       (interior / harmonic-extension solves),
+//   * K = S'^-1 - S'^-1 C^T (C S'^-1 C^T)^-1 C S'^-1   restricted to G,
+//     the constrained Neumann inverse, where S' = S + C^T rho C and
+//     S = A_GG - A_GI A_II^-1 A_IG is the Schur complement (the constraint rows C
+//     live on G only, so eliminating I is exact; adding C^T rho C leaves the
+//     constrained solution unchanged because C v = 0 there),
+//   * Phi_G = S'^-1 C^T (C S'^-1 C^T)^-1, the interface rows of the energy-
+//     minimising coarse basis (C Phi = I), and
+//   * A_c^w = Phi^T A^w Phi = (C S'^-1 C^T)^-1 - rho   (coarse contribution).
+// All local matrices are Jacobi-scaled (D^-1/2 A D^-1/2) before inversion; in
+// mixed precision the scaled matrices are inverted and stored in FP32.
+#include <algorithm>
+#include <chrono>
+#include <memory>
+
+#include "bddc.cuh"
+#include "dense.cuh"
+#include "q1.cuh"
+
+namespace ufe {
+
+Bddc::~Bddc() {
+  if (graph) cudaGraphExecDestroy(graph);
+  if (h_sc) cudaFreeHost(h_sc);
+}
+
+SubMeta Bddc::meta() const {
+  const Mesh& m = *mesh;
+  SubMeta s;
+  s.g = m.g;
+  s.n_sub = (int)m.n_sub;
+  s.sub_block = m.sub_block.p;
+  s.sub_of_cell = m.sub_of_cell.p;
+  s.cell_type = m.cell_type.p;
+  s.cut_index = m.cut_index.p;
+  s.K_cut = sys->K_cut.p;
+  s.kappa = sys->has_kappa ? sys->kappa.p : nullptr;
+  s.dof_of_node = m.dof_of_node.p;
+  s.lmap = m.lmap.p;
+  s.I_ptr = m.I_ptr.p;
+  s.I_list = m.I_list.p;
+  s.G_ptr = m.G_ptr.p;
+  s.G_list = m.G_list.p;
+  s.C_ptr = C_ptr.p;
+  s.C_list = C_list.p;
+  s.neigh = m.neigh.p;
+  s.n_neigh = m.n_neigh.p;
+  s.gpos = m.gpos.p;
+  s.off_II = off_II.p;
+  s.off_GG = off_GG.p;
+  s.off_GC = off_GC.p;
+  s.w = w.p;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+// grid edge from node (i,j,k) to its +axis neighbour belongs to an active cell
+__device__ __forceinline__ bool fe_edge(const GridGeom& g, const uint8_t* __restrict__ cell_type, int i, int j, int k,
+                                        int axis) {
+  for (int a = -1; a <= 0; ++a)
+    for (int b = -1; b <= 0; ++b) {
+      int ci = i, cj = j, ck = k;
+      if (axis == 0) { cj += a; ck += b; }
+      else if (axis == 1) { ci += a; ck += b; }
+      else { ci += a; cj += b; }
+      if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
+      if (cell_type[g.cell(ci, cj, ck)] != UFE_CELL_EXTERNAL) return true;
+    }
+  return false;
+}
+
+__device__ __forceinline__ bool same_neigh(const int32_t* __restrict__ neigh, const uint8_t* __restrict__ nn,
+                                           int64_t d, int64_t e) {
+  if (nn[d] != nn[e]) return false;
+  for (int t = 0; t < 8; ++t)
+    if (neigh[d * 8 + t] != neigh[e * 8 + t]) return false;
+  return true;
+}
+
+// calls f(e, inside_e) for every axis neighbour DOF e of DOF d joined to d by an FE edge
+template <typename F>
+__device__ __forceinline__ void for_fe_neighbours(const GridGeom& g, const int32_t* __restrict__ node_of_dof,
+                                                  const int32_t* __restrict__ dof_of_node,
+                                                  const uint8_t* __restrict__ cell_type, int64_t d, F f) {
+  const int64_t v = node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  const int lim[3] = {g.nx, g.ny, g.nz};
+  const int c[3] = {i, j, k};
+  for (int axis = 0; axis < 3; ++axis)
+    for (int dir = -1; dir <= 1; dir += 2) {
+      int cc[3] = {c[0], c[1], c[2]};
+      cc[axis] += dir;
+      if (cc[axis] < 0 || cc[axis] > lim[axis]) continue;
+      const int64_t wv = g.node(cc[0], cc[1], cc[2]);
+      const int32_t e = dof_of_node[wv];
+      if (e < 0) continue;
+      int lo[3] = {c[0], c[1], c[2]};
+      if (dir < 0) lo[axis] -= 1;
+      if (!fe_edge(g, cell_type, lo[0], lo[1], lo[2], axis)) continue;
+      f((int64_t)e, wv);
+    }
+}
+
+// min-label propagation; mode 0: interface DOFs with equal neigh sets (standard
+// objects); mode 1: non-corner DOFs of one edge object joined by uncut FE edges
+__global__ void k_obj_propagate(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                                const int32_t* __restrict__ dof_of_node, const uint8_t* __restrict__ cell_type,
+                                const int32_t* __restrict__ neigh, const uint8_t* __restrict__ nn,
+                                const double* __restrict__ phi, const int32_t* __restrict__ std_obj,
+                                const uint8_t* __restrict__ active, int mode, int32_t* label, int* changed) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof || !active[d]) return;
+  int32_t m = label[d];
+  const bool in_d = phi[node_of_dof[d]] < 0.0;
+  for_fe_neighbours(g, node_of_dof, dof_of_node, cell_type, d, [&](int64_t e, int64_t wv) {
+    if (!active[e]) return;
+    if (mode == 0) {
+      if (!same_neigh(neigh, nn, d, e)) return;
+    } else {
+      if (std_obj[e] != std_obj[d]) return;
+      if ((phi[wv] < 0.0) != in_d) return;
+    }
+    const int32_t l = label[e];
+    if (l < m) m = l;
+  });
+  const int32_t mm = label[m];
+  if (mm < m) m = mm;
+  if (m < label[d]) {
+    label[d] = m;
+    *changed = 1;
+  }
+}
+
+// variant 1: DOFs of edge objects incident to a cut FE edge of the same object
+__global__ void k_v1_corners(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                             const int32_t* __restrict__ dof_of_node, const uint8_t* __restrict__ cell_type,
+                             const double* __restrict__ phi, const int32_t* __restrict__ obj_of_dof,
+                             const int32_t* __restrict__ obj_kind, uint8_t* __restrict__ corner,
+                             uint8_t* __restrict__ active, int32_t* __restrict__ label2,
+                             const int32_t* __restrict__ label) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof) return;
+  const int32_t o = obj_of_dof[d];
+  bool is_edge = o >= 0 && obj_kind[o] == UFE_OBJ_EDGE;
+  bool cut = false;
+  if (is_edge) {
+    const bool in_d = phi[node_of_dof[d]] < 0.0;
+    for_fe_neighbours(g, node_of_dof, dof_of_node, cell_type, d, [&](int64_t e, int64_t wv) {
+      if (obj_of_dof[e] != o) return;
+      if ((phi[wv] < 0.0) != in_d) cut = true;
+    });
+  }
+  corner[d] = cut ? 1 : 0;
+  active[d] = (is_edge && !cut) ? 1 : 0;
+  label2[d] = is_edge ? (int32_t)d : label[d];
+}
+
+__global__ void k_rep_flags(int64_t n, const int32_t* __restrict__ label, uint8_t* __restrict__ f) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d < n) f[d] = (label[d] >= 0 && label[d] == d) ? 1 : 0;
+}
+
+__global__ void k_obj_assign(int64_t n, const int32_t* __restrict__ label, const int32_t* __restrict__ rep_index,
+                             int32_t* __restrict__ obj_of_dof, int32_t* __restrict__ obj_size,
+                             int32_t* __restrict__ obj_rep) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const int32_t l = label[d];
+  if (l < 0) {
+    obj_of_dof[d] = -1;
+    return;
+  }
+  const int32_t o = rep_index[l];
+  obj_of_dof[d] = o;
+  atomicAdd(obj_size + o, 1);
+  if (l == d) obj_rep[o] = (int32_t)d;
+}
+
+// kinds: |neigh| = 2 -> face; else 1 DOF -> corner, more -> edge.  With prev_kind
+// (variant 1) faces and corners keep their kind and split edges follow the rule
+// above, a DOF on a cut FE edge being a corner.
+__global__ void k_obj_kind(int64_t n_obj, const int32_t* __restrict__ obj_rep, const int32_t* __restrict__ obj_size,
+                           const uint8_t* __restrict__ nn, const int32_t* __restrict__ prev_obj,
+                           const int32_t* __restrict__ prev_kind, const uint8_t* __restrict__ corner,
+                           int32_t* __restrict__ kind) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  const int32_t rep = obj_rep[o];
+  int k;
+  if (nn[rep] == 2)
+    k = UFE_OBJ_FACE;
+  else
+    k = obj_size[o] == 1 ? UFE_OBJ_CORNER : UFE_OBJ_EDGE;
+  if (prev_kind) {
+    const int pk = prev_kind[prev_obj[rep]];
+    if (pk == UFE_OBJ_FACE) k = UFE_OBJ_FACE;
+    else if (pk == UFE_OBJ_CORNER) k = UFE_OBJ_CORNER;
+    else if (corner[rep]) k = UFE_OBJ_CORNER;
+  }
+  kind[o] = k;
+}
+
+__global__ void k_coarse_flags(int64_t n_obj, const int32_t* __restrict__ kind, int coarse, uint8_t* __restrict__ f) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  const int k = kind[o];
+  f[o] = (k == UFE_OBJ_CORNER) || (k == UFE_OBJ_EDGE && coarse >= UFE_COARSE_CE) ||
+         (k == UFE_OBJ_FACE && coarse >= UFE_COARSE_CEF);
+}
+
+__global__ void k_coarse_list(int64_t n_obj, const int32_t* __restrict__ coarse_of_obj, const int32_t* __restrict__ obj_rep,
+                              const uint8_t* __restrict__ nn, int32_t* __restrict__ coarse_obj,
+                              int32_t* __restrict__ coarse_rep, uint8_t* __restrict__ coarse_nn,
+                              const int32_t* __restrict__ neigh, int32_t* __restrict__ nC) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  const int32_t c = coarse_of_obj[o];
+  if (c < 0) return;
+  const int32_t rep = obj_rep[o];
+  coarse_obj[c] = (int32_t)o;
+  coarse_rep[c] = rep;
+  coarse_nn[c] = nn[rep];
+  for (int k = 0; k < nn[rep]; ++k) atomicAdd(nC + neigh[(int64_t)rep * 8 + k], 1);
+}
+
+
+// coarse DOFs of subdomain w in increasing order
+__global__ void k_sub_coarse_fill(int64_t n_coarse, const int32_t* __restrict__ coarse_rep,
+                                  const uint8_t* __restrict__ coarse_nn, const int32_t* __restrict__ neigh,
+                                  const int32_t* __restrict__ C_ptr, int32_t* __restrict__ C_list) {
+  const int w = blockIdx.x;
+  __shared__ int warp_tot[32];
+  int base = C_ptr[w];
+  for (int64_t c0 = 0; c0 < n_coarse; c0 += blockDim.x) {
+    const int64_t c = c0 + threadIdx.x;
+    int mem = 0;
+    if (c < n_coarse) {
+      const int32_t rep = coarse_rep[c];
+      for (int k = 0; k < coarse_nn[c]; ++k)
+        if (neigh[(int64_t)rep * 8 + k] == w) mem = 1;
+    }
+    // block exclusive scan of mem (blockDim = 256)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = mem;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    int woff = 0, tot = 0;
+    for (int x = 0; x < (int)(blockDim.x >> 5); ++x) {
+      if (x < wid) woff += warp_tot[x];
+      tot += warp_tot[x];
+    }
+    if (mem) C_list[base + woff + inc - 1] = (int32_t)c;
+    base += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_cpos(const int32_t* __restrict__ C_ptr, const int32_t* __restrict__ C_list,
+                       const int32_t* __restrict__ coarse_rep, const uint8_t* __restrict__ coarse_nn,
+                       const int32_t* __restrict__ neigh, int32_t* __restrict__ cpos) {
+  const int w = blockIdx.x;
+  for (int i = C_ptr[w] + threadIdx.x; i < C_ptr[w + 1]; i += blockDim.x) {
+    const int32_t c = C_list[i];
+    const int32_t rep = coarse_rep[c];
+    for (int k = 0; k < coarse_nn[c]; ++k)
+      if (neigh[(int64_t)rep * 8 + k] == w) cpos[(int64_t)c * 8 + k] = i;
+  }
+}
+
+// subdomains touching a constrained (Dirichlet / pinned) node
+__global__ void k_touch_constrained(GridGeom g, const int32_t* __restrict__ sub_block,
+                                    const int32_t* __restrict__ sub_of_cell, const int32_t* __restrict__ dof_of_node,
+                                    const uint8_t* __restrict__ node_flags, int* __restrict__ touches) {
+  const int w = blockIdx.x;
+  const int b = sub_block[w];
+  const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
+  int t = 0;
+  for (int lc = threadIdx.x; lc < g.sx * g.sy * g.sz; lc += blockDim.x) {
+    const int li = lc % g.sx, lj = (lc / g.sx) % g.sy, lk = lc / (g.sx * g.sy);
+    const int gi = bi * g.sx + li, gj = bj * g.sy + lj, gk = bk * g.sz + lk;
+    if (sub_of_cell[g.cell(gi, gj, gk)] != w) continue;
+    for (int a = 0; a < 8; ++a) {
+      const int64_t v = g.node(gi + (a & 1), gj + ((a >> 1) & 1), gk + (a >> 2));
+      if ((node_flags[v] & 1) && dof_of_node[v] < 0) t = 1;
+    }
+  }
+  t = __syncthreads_or(t);
+  if (threadIdx.x == 0) touches[w] = t;
+}
+
+// ---------------------------------------------------------------------------
+// local matrices (Sect. 3.1): A^w from the cells of w, split into II, IG, GG
+// ---------------------------------------------------------------------------
+__global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oIG,
+                                 const int64_t* __restrict__ oGG, double* __restrict__ AII, double* __restrict__ AIG,
+                                 double* __restrict__ AGG) {
+  const GridGeom& g = sm.g;
+  const int w = blockIdx.x;
+  const int b = sm.sub_block[w];
+  const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
+  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int ldI = pad4(nI), ldG = pad4(nG);
+  const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
+  for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
+    const int ln = e / 27, o = e % 27;
+    const int32_t c1 = lm[ln];
+    const int k1 = lmap_kind(c1);
+    if (k1 == LKIND_NONE) continue;
+    const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
+    const int lx2 = lx + (o % 3) - 1, ly2 = ly + ((o / 3) % 3) - 1, lz2 = lz + (o / 9) - 1;
+    if (lx2 < 0 || ly2 < 0 || lz2 < 0 || lx2 >= g.lnx || ly2 >= g.lny || lz2 >= g.lnz) continue;
+    const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
+    const int k2 = lmap_kind(c2);
+    if (k2 == LKIND_NONE || (k1 == LKIND_G && k2 == LKIND_I)) continue;
+    double val = 0.0;
+    for (int cz = max(lz, lz2) - 1; cz <= min(lz, lz2); ++cz) {
+      if (cz < 0 || cz >= g.sz) continue;
+      for (int cy = max(ly, ly2) - 1; cy <= min(ly, ly2); ++cy) {
+        if (cy < 0 || cy >= g.sy) continue;
+        for (int cx = max(lx, lx2) - 1; cx <= min(lx, lx2); ++cx) {
+          if (cx < 0 || cx >= g.sx) continue;
+          const int64_t c = g.cell(bi * g.sx + cx, bj * g.sy + cy, bk * g.sz + cz);
+          if (sm.sub_of_cell[c] != w) continue;
+          const int a = (lx - cx) + 2 * (ly - cy) + 4 * (lz - cz);
+          const int bb = (lx2 - cx) + 2 * (ly2 - cy) + 4 * (lz2 - cz);
+          const double kap = sm.kappa ? sm.kappa[c] : 1.0;
+          const double kab = sm.cell_type[c] == UFE_CELL_INTERNAL ? g.h * q1_khat(a, bb)
+                                                                  : sm.K_cut[(int64_t)sm.cut_index[c] * 64 + a * 8 + bb];
+          val += kap * kab;
+        }
+      }
+    }
+    const int p1 = lmap_index(c1), p2 = lmap_index(c2);
+    if (k1 == LKIND_I && k2 == LKIND_I)
+      AII[oII[w] + (int64_t)p1 * ldI + p2] = val;
+    else if (k1 == LKIND_I)
+      AIG[oIG[w] + (int64_t)p1 * ldG + p2] = val;
+    else
+      AGG[oGG[w] + (int64_t)p1 * ldG + p2] = val;
+  }
+  (void)nG;
+}
+
+// Jacobi scales s = diag^-1/2 and the raw interface diagonal (stiffness weights)
+__global__ void k_local_diag(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGG,
+                             const double* __restrict__ AII, const double* __restrict__ AGG, double* __restrict__ sI,
+                             double* __restrict__ sG, double* __restrict__ dGraw) {
+  const int w = blockIdx.x;
+  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int ldI = pad4(nI), ldG = pad4(nG);
+  for (int p = threadIdx.x; p < nI; p += blockDim.x) sI[sm.I_ptr[w] + p] = 1.0 / sqrt(AII[oII[w] + (int64_t)p * ldI + p]);
+  for (int p = threadIdx.x; p < nG; p += blockDim.x) {
+    const double d = AGG[oGG[w] + (int64_t)p * ldG + p];
+    dGraw[sm.G_ptr[w] + p] = d;
+    sG[sm.G_ptr[w] + p] = 1.0 / sqrt(d);
+  }
+}
+
+// weights per interface slot: stiffness A^w_xx / sum_w' A^w'_xx (Eq. alge-weighting) or 1/|neigh| (Eq. weighting)
+__global__ void k_weights(int64_t n_dof, const uint8_t* __restrict__ nn, const int32_t* __restrict__ gpos,
+                          const double* __restrict__ dGraw, int topological, double* __restrict__ w) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof || nn[d] < 2) return;
+  const int cnt = nn[d];
+  double sum = 0.0;
+  for (int k = 0; k < cnt; ++k) sum += dGraw[gpos[d * 8 + k]];
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t s = gpos[d * 8 + k];
+    w[s] = topological ? 1.0 / cnt : dGraw[s] / sum;
+  }
+}
+
+// scale and convert: dst[i][j] = src[i][j] * sr_i * sc_j  (FP64 -> T)
+template <typename T>
+__global__ void k_scale_block(const double* __restrict__ src, T* __restrict__ dst, const int64_t* __restrict__ off,
+                              const int32_t* __restrict__ rptr, const int32_t* __restrict__ cptr,
+                              const double* __restrict__ sr, const double* __restrict__ scl) {
+  const int w = blockIdx.x;
+  const int nr = rptr[w + 1] - rptr[w], nc = cptr[w + 1] - cptr[w];
+  const int ld = pad4(nc);
+  const int64_t o = off[w];
+  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) {
+    const int i = e / ld, j = e % ld;
+    double v = 0.0;
+    if (j < nc) v = src[o + e] * sr[rptr[w] + i] * scl[cptr[w] + j];
+    dst[o + e] = (T)v;
+  }
+}
+
+// scaled constraint rows C^ = C D_G^-1/2 (C = uniform means over the objects),
+// C_rho = diag(rho) C^ with rho_l = 1 / |C^_l|^2
+template <typename T>
+__global__ void k_constraints(SubMeta sm, const int32_t* __restrict__ obj_of_dof, const int32_t* __restrict__ coarse_of_obj,
+                              const int32_t* __restrict__ obj_size, const double* __restrict__ sG,
+                              const int64_t* __restrict__ oCG, T* __restrict__ Cs, T* __restrict__ Crho,
+                              double* __restrict__ rho) {
+  const int w = blockIdx.x;
+  const int nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int c0 = sm.C_ptr[w], nC = sm.C_ptr[w + 1] - c0;
+  const int ldG = pad4(nG);
+  for (int j = threadIdx.x; j < nG; j += blockDim.x) {
+    const int32_t d = sm.G_list[sm.G_ptr[w] + j];
+    const int32_t o = obj_of_dof[d];
+    const int32_t c = coarse_of_obj[o];
+    if (c < 0 || nC == 0) continue;
+    int lo = 0, hi = nC - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sm.C_list[c0 + mid] < c) lo = mid + 1; else hi = mid;
+    }
+    Cs[oCG[w] + (int64_t)lo * ldG + j] = (T)(sG[sm.G_ptr[w] + j] / obj_size[o]);
+  }
+  __syncthreads();
+  // rho_l = 1 / |C^_l|^2, each row summed in order by one thread (deterministic)
+  for (int i = threadIdx.x; i < nC; i += blockDim.x) {
+    double nrm = 0.0;
+    for (int j = 0; j < nG; ++j) {
+      const double v = (double)Cs[oCG[w] + (int64_t)i * ldG + j];
+      nrm += v * v;
+    }
+    rho[c0 + i] = 1.0 / nrm;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nC * ldG; e += blockDim.x) {
+    const int i = e / ldG;
+    Crho[oCG[w] + e] = (T)((double)Cs[oCG[w] + e] * rho[c0 + i]);
+  }
+}
+
+// A_c^w = (C S'^-1 C^T)^-1 - rho  (FP64)
+template <typename T>
+__global__ void k_coarse_local(const int32_t* __restrict__ C_ptr, const int64_t* __restrict__ oCC,
+                               const T* __restrict__ invSc, const double* __restrict__ rho, double* __restrict__ Acw) {
+  const int w = blockIdx.x;
+  const int c0 = C_ptr[w], nC = C_ptr[w + 1] - c0, ldC = pad4(nC);
+  for (int e = threadIdx.x; e < nC * nC; e += blockDim.x) {
+    const int i = e / nC, j = e % nC;
+    double v = (double)invSc[oCC[w] + (int64_t)i * ldC + j];
+    if (i == j) v -= rho[c0 + i];
+    Acw[oCC[w] + (int64_t)i * ldC + j] = v;
+  }
+}
+
+// unscale: dst[i][j] *= sr_i * sc_j (sc may be null: rows only)
+template <typename T>
+__global__ void k_unscale(T* __restrict__ A, const int64_t* __restrict__ off, const int32_t* __restrict__ rptr,
+                          const int32_t* __restrict__ cptr, const double* __restrict__ sr, const double* __restrict__ scl,
+                          int ncols_from_cptr) {
+  const int w = blockIdx.x;
+  const int nr = rptr[w + 1] - rptr[w];
+  const int nc = cptr[w + 1] - cptr[w];
+  const int ld = pad4(nc);
+  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) {
+    const int i = e / ld, j = e % ld;
+    if (j >= nc) continue;
+    double f = sr[rptr[w] + i];
+    if (scl) f *= scl[cptr[w] + j];
+    A[off[w] + e] = (T)((double)A[off[w] + e] * f);
+  }
+  (void)ncols_from_cptr;
+}
+
+// coarse matrix: row l gathers A_c^w of every subdomain w in neigh(l), in neigh order
+__global__ void k_coarse_assemble(int64_t n_coarse, int ldc, const int32_t* __restrict__ coarse_rep,
+                                  const uint8_t* __restrict__ coarse_nn, const int32_t* __restrict__ neigh,
+                                  const int32_t* __restrict__ cpos, const int32_t* __restrict__ C_ptr,
+                                  const int32_t* __restrict__ C_list, const int64_t* __restrict__ oCC,
+                                  const double* __restrict__ Acw, double* __restrict__ Ac) {
+  const int64_t l = blockIdx.x;
+  const int32_t rep = coarse_rep[l];
+  for (int k = 0; k < coarse_nn[l]; ++k) {
+    const int w = neigh[(int64_t)rep * 8 + k];
+    const int c0 = C_ptr[w], nC = C_ptr[w + 1] - c0, ldC = pad4(nC);
+    const int i = cpos[l * 8 + k] - c0;
+    for (int j = threadIdx.x; j < nC; j += blockDim.x)
+      Ac[l * ldc + C_list[c0 + j]] += Acw[oCC[w] + (int64_t)i * ldC + j];
+    __syncthreads();
+  }
+}
+
+__global__ void k_symmetrize(double* A, int n, int ld) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  if (j <= i) return;
+  const double v = 0.5 * (A[(int64_t)i * ld + j] + A[(int64_t)j * ld + i]);
+  A[(int64_t)i * ld + j] = v;
+  A[(int64_t)j * ld + i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static void propagate(const Mesh& m, const Bddc& B, const uint8_t* active, int mode, const int32_t* std_obj,
+                      int32_t* label) {
+  cudaStream_t s = B.stream;
+  DBuf<int> changed;
+  changed.alloc(1, s);
+  for (int round = 0; round < 512; ++round) {
+    changed.zero();
+    for (int rep = 0; rep < 4; ++rep)
+      k_obj_propagate<<<grid_for(m.n_dof, 256), 256, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p,
+                                                             m.cell_type.p, m.neigh.p, m.n_neigh.p, m.phi.p, std_obj,
+                                                             active, mode, label, changed.p);
+    UFE_CHECK_LAUNCH();
+    if (scalar_to_host(changed.p, s) == 0) return;
+  }
+  throw Error{UFE_ERR_TIMEOUT, "object labelling did not converge"};
+}
+
+__global__ void k_init_labels(int64_t n, const uint8_t* __restrict__ nn, int32_t* __restrict__ label,
+                              uint8_t* __restrict__ active) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const bool g = nn[d] >= 2;
+  label[d] = g ? (int32_t)d : -1;
+  active[d] = g ? 1 : 0;
+}
+
+template <typename T>
+static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std::vector<int64_t>& oIG,
+                            const std::vector<int64_t>& oGG, const std::vector<int64_t>& oCG,
+                            const std::vector<int64_t>& oGC, const std::vector<int64_t>& oCC, int64_t nII, int64_t nIG,
+                            int64_t nGG, int64_t nCG, int64_t nGC, int64_t nCC, DBuf<double>& AII, DBuf<double>& AIG,
+                            DBuf<double>& AGG, DBuf<double>& sI, DBuf<double>& sG, DBuf<T>& II, DBuf<T>& GG,
+                            DBuf<T>& GC, DBuf<double>& Acw, DBuf<double>& rho) {
+  Mesh& m = *B.mesh;
+  cudaStream_t s = B.stream;
+  const int ns = (int)m.n_sub;
+  const SubMeta sm = B.meta();
+  auto up = [&](const std::vector<int64_t>& v) {
+    DBuf<int64_t>* d = new DBuf<int64_t>();
+    d->alloc(v.size(), s);
+    UFE_CUDA(cudaMemcpyAsync(d->p, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    return std::unique_ptr<DBuf<int64_t>>(d);
+  };
+  auto dII = up(oII), dIG = up(oIG), dGG = up(oGG), dCG = up(oCG), dCC = up(oCC);
+  // scaled blocks in precision T
+  II.alloc(std::max<int64_t>(nII, 1), s);
+  DBuf<T> IG, Cs, Crho, X, Y, Sc;
+  IG.alloc(std::max<int64_t>(nIG, 1), s);
+  GG.alloc(std::max<int64_t>(nGG, 1), s);
+  k_scale_block<T><<<ns, 256, 0, s>>>(AII.p, II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p);
+  k_scale_block<T><<<ns, 256, 0, s>>>(AIG.p, IG.p, dIG->p, m.I_ptr.p, m.G_ptr.p, sI.p, sG.p);
+  k_scale_block<T><<<ns, 256, 0, s>>>(AGG.p, GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p);
+  UFE_CHECK_LAUNCH();
+  Cs.alloc(std::max<int64_t>(nCG, 1), s);
+  Crho.alloc(std::max<int64_t>(nCG, 1), s);
+  Cs.zero();
+  rho.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
+  k_constraints<T><<<ns, 256, 0, s>>>(sm, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p, sG.p, dCG->p, Cs.p, Crho.p,
+                                      rho.p);
+  UFE_CHECK_LAUNCH();
+
+  DBuf<int> status;
+  status.alloc(ns, s);
+  status.zero();
+  std::vector<InvDesc> inv;
+  std::vector<GemmDesc> g;
+  // 1. A_II^-1
+  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
+  batched_inverse<T>(inv, II.p, status.p, s);
+  // 2. X = A_II^-1 A_IG
+  X.alloc(std::max<int64_t>(nIG, 1), s);
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nI[w], B.h_nG[w], B.h_nI[w], pad4(B.h_nI[w]), pad4(B.h_nG[w]), pad4(B.h_nG[w]), oII[w], oIG[w], oIG[w]});
+  batched_gemm<T>(false, false, g, II.p, IG.p, X.p, T(1), T(0), s);
+  // 3. S = A_GG - A_IG^T X
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nG[w], B.h_nG[w], B.h_nI[w], pad4(B.h_nG[w]), pad4(B.h_nG[w]), pad4(B.h_nG[w]), oIG[w], oIG[w], oGG[w]});
+  batched_gemm<T>(true, false, g, IG.p, X.p, GG.p, T(-1), T(1), s);
+  X.release();
+  IG.release();
+  // 4. S' = S + C^T rho C
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nG[w], B.h_nG[w], B.h_nC[w], pad4(B.h_nG[w]), pad4(B.h_nG[w]), pad4(B.h_nG[w]), oCG[w], oCG[w], oGG[w]});
+  batched_gemm<T>(true, false, g, Cs.p, Crho.p, GG.p, T(1), T(1), s);
+  Crho.release();
+  // 5. S'^-1
+  inv.clear();
+  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nG[w], pad4(B.h_nG[w]), oGG[w]});
+  batched_inverse<T>(inv, GG.p, status.p, s);
+  // 6. Y = S'^-1 C^T
+  Y.alloc(std::max<int64_t>(nGC, 1), s);
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nG[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nG[w]), pad4(B.h_nC[w]), oGG[w], oCG[w], oGC[w]});
+  batched_gemm<T>(false, true, g, GG.p, Cs.p, Y.p, T(1), T(0), s);
+  // 7. S_c = C Y, then S_c^-1
+  Sc.alloc(std::max<int64_t>(nCC, 1), s);
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nC[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oCG[w], oGC[w], oCC[w]});
+  batched_gemm<T>(false, false, g, Cs.p, Y.p, Sc.p, T(1), T(0), s);
+  inv.clear();
+  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nC[w], pad4(B.h_nC[w]), oCC[w]});
+  batched_inverse<T>(inv, Sc.p, status.p, s);
+  // 8. Phi^ = Y S_c^-1
+  GC.alloc(std::max<int64_t>(nGC, 1), s);
+  GC.zero();
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nG[w], B.h_nC[w], B.h_nC[w], pad4(B.h_nC[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oGC[w], oCC[w], oGC[w]});
+  batched_gemm<T>(false, false, g, Y.p, Sc.p, GC.p, T(1), T(0), s);
+  // 9. K^ = S'^-1 - Phi^ Y^T
+  g.clear();
+  for (int w = 0; w < ns; ++w)
+    g.push_back({B.h_nG[w], B.h_nG[w], B.h_nC[w], pad4(B.h_nC[w]), pad4(B.h_nC[w]), pad4(B.h_nG[w]), oGC[w], oGC[w], oGG[w]});
+  batched_gemm<T>(false, true, g, GC.p, Y.p, GG.p, T(-1), T(1), s);
+  // 10. A_c^w = S_c^-1 - rho (FP64)
+  Acw.alloc(std::max<int64_t>(nCC, 1), s);
+  k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
+  // 11. unscale the operators used at every iteration
+  k_unscale<T><<<ns, 256, 0, s>>>(II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p, 0);
+  k_unscale<T><<<ns, 256, 0, s>>>(GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p, 0);
+  k_unscale<T><<<ns, 256, 0, s>>>(GC.p, B.off_GC.p, m.G_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
+  UFE_CHECK_LAUNCH();
+  std::vector<int> st = to_host(status.p, ns, s);
+  for (int w = 0; w < ns; ++w)
+    UFE_REQUIRE(st[w] == 0, UFE_ERR_SINGULAR_LOCAL,
+                "local matrix of subdomain " + std::to_string(w) + " is not positive definite");
+}
+
+void bddc_build(Bddc& B) {
+  Mesh& m = *B.mesh;
+  cudaStream_t s = B.stream;
+  const int T = 256;
+  const int64_t nd = m.n_dof;
+  const int ns = (int)m.n_sub;
+  cudaEvent_t e0, e1;
+  UFE_CUDA(cudaEventCreate(&e0));
+  UFE_CUDA(cudaEventCreate(&e1));
+  UFE_CUDA(cudaEventRecord(e0, s));
+
+  // ---- standard objects
+  DBuf<int32_t> label;
+  DBuf<uint8_t> active, flags;
+  label.alloc(nd, s);
+  active.alloc(nd, s);
+  flags.alloc(nd, s);
+  k_init_labels<<<grid_for(nd, T), T, 0, s>>>(nd, m.n_neigh.p, label.p, active.p);
+  UFE_CHECK_LAUNCH();
+  propagate(m, B, active.p, 0, nullptr, label.p);
+  DBuf<int32_t> rep_index;
+  rep_index.alloc(nd, s);
+  k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label.p, flags.p);
+  int64_t n_obj = scan_flags(flags.p, nd, rep_index.p, s);
+  B.obj_of_dof.alloc(nd, s);
+  B.obj_size.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.obj_rep.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.obj_kind.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.obj_size.zero();
+  k_obj_assign<<<grid_for(nd, T), T, 0, s>>>(nd, label.p, rep_index.p, B.obj_of_dof.p, B.obj_size.p, B.obj_rep.p);
+  if (n_obj)
+    k_obj_kind<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.obj_rep.p, B.obj_size.p, m.n_neigh.p, nullptr, nullptr,
+                                                nullptr, B.obj_kind.p);
+  UFE_CHECK_LAUNCH();
+
+  // ---- variant 1 (Sect. 4.4): split the edge objects at their cut FE edges
+  if (B.opts.objects == UFE_OBJECTS_VARIANT1 && n_obj) {
+    DBuf<uint8_t> corner;
+    DBuf<int32_t> label2;
+    corner.alloc(nd, s);
+    label2.alloc(nd, s);
+    k_v1_corners<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p, m.phi.p,
+                                               B.obj_of_dof.p, B.obj_kind.p, corner.p, active.p, label2.p, label.p);
+    UFE_CHECK_LAUNCH();
+    propagate(m, B, active.p, 1, B.obj_of_dof.p, label2.p);
+    k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label2.p, flags.p);
+    const int64_t n_obj2 = scan_flags(flags.p, nd, rep_index.p, s);
+    DBuf<int32_t> obj2, size2, rep2, kind2;
+    obj2.alloc(nd, s);
+    size2.alloc(n_obj2, s);
+    rep2.alloc(n_obj2, s);
+    kind2.alloc(n_obj2, s);
+    size2.zero();
+    k_obj_assign<<<grid_for(nd, T), T, 0, s>>>(nd, label2.p, rep_index.p, obj2.p, size2.p, rep2.p);
+    k_obj_kind<<<grid_for(n_obj2, T), T, 0, s>>>(n_obj2, rep2.p, size2.p, m.n_neigh.p, B.obj_of_dof.p, B.obj_kind.p,
+                                                 corner.p, kind2.p);
+    UFE_CHECK_LAUNCH();
+    std::swap(B.obj_of_dof.p, obj2.p);
+    std::swap(B.obj_size.p, size2.p);
+    std::swap(B.obj_rep.p, rep2.p);
+    std::swap(B.obj_kind.p, kind2.p);
+    std::swap(B.obj_size.n, size2.n);
+    std::swap(B.obj_rep.n, rep2.n);
+    std::swap(B.obj_kind.n, kind2.n);
+    n_obj = n_obj2;
+  }
+  B.n_obj = n_obj;
+  {
+    std::vector<int32_t> kinds = to_host(B.obj_kind.p, n_obj, s);
+    B.n_corner = std::count(kinds.begin(), kinds.end(), (int32_t)UFE_OBJ_CORNER);
+    B.n_edge = std::count(kinds.begin(), kinds.end(), (int32_t)UFE_OBJ_EDGE);
+    B.n_face = std::count(kinds.begin(), kinds.end(), (int32_t)UFE_OBJ_FACE);
+  }
+
+  // ---- coarse DOFs and the per-subdomain coarse lists
+  DBuf<uint8_t> cf;
+  cf.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.coarse_of_obj.alloc(std::max<int64_t>(n_obj, 1), s);
+  if (n_obj) {
+    k_coarse_flags<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.obj_kind.p, B.opts.coarse, cf.p);
+    UFE_CHECK_LAUNCH();
+    B.n_coarse = scan_flags(cf.p, n_obj, B.coarse_of_obj.p, s);
+  } else {
+    B.n_coarse = 0;
+  }
+  const int64_t nco = B.n_coarse;
+  B.coarse_obj.alloc(std::max<int64_t>(nco, 1), s);
+  B.coarse_rep.alloc(std::max<int64_t>(nco, 1), s);
+  B.coarse_nn.alloc(std::max<int64_t>(nco, 1), s);
+  DBuf<int32_t> nC;
+  nC.alloc(ns, s);
+  nC.zero();
+  if (n_obj)
+    k_coarse_list<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.coarse_of_obj.p, B.obj_rep.p, m.n_neigh.p, B.coarse_obj.p,
+                                                   B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, nC.p);
+  UFE_CHECK_LAUNCH();
+  B.C_ptr.alloc(ns + 1, s);
+  B.n_Cloc = scan_counts(nC.p, ns, B.C_ptr.p, s);
+  B.C_list.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
+  B.cpos.alloc(std::max<int64_t>(nco, 1) * 8, s);
+  B.cpos.fill_bytes(0xff);
+  if (nco) {
+    k_sub_coarse_fill<<<ns, 256, 0, s>>>(nco, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.C_ptr.p, B.C_list.p);
+    k_cpos<<<ns, 256, 0, s>>>(B.C_ptr.p, B.C_list.p, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p);
+    UFE_CHECK_LAUNCH();
+  }
+  std::vector<int32_t> hC = to_host(B.C_ptr.p, ns + 1, s);
+  B.h_nI.resize(ns);
+  B.h_nG.resize(ns);
+  B.h_nC.resize(ns);
+  B.max_nC = 0;
+  for (int w = 0; w < ns; ++w) {
+    B.h_nI[w] = m.h_I_ptr[w + 1] - m.h_I_ptr[w];
+    B.h_nG[w] = m.h_G_ptr[w + 1] - m.h_G_ptr[w];
+    B.h_nC[w] = hC[w + 1] - hC[w];
+    B.max_nC = std::max(B.max_nC, B.h_nC[w]);
+  }
+  UFE_REQUIRE(B.max_nC <= 1024, UFE_ERR_UNSUPPORTED, "more than 1024 coarse DOFs in one subdomain");
+
+  // structural singularity: a floating subdomain (no constrained node) without coarse DOFs
+  {
+    DBuf<int> touch;
+    touch.alloc(ns, s);
+    k_touch_constrained<<<ns, 256, 0, s>>>(m.g, m.sub_block.p, m.sub_of_cell.p, m.dof_of_node.p, m.node_flags.p,
+                                           touch.p);
+    UFE_CHECK_LAUNCH();
+    std::vector<int> t = to_host(touch.p, ns, s);
+    for (int w = 0; w < ns; ++w)
+      UFE_REQUIRE(t[w] || B.h_nC[w] > 0, UFE_ERR_SINGULAR_LOCAL,
+                  "subdomain " + std::to_string(w) + " floats and has no coarse DOF");
+  }
+
+  // ---- storage offsets
+  std::vector<int64_t> oII(ns), oIG(ns), oGG(ns), oCG(ns), oGC(ns), oCC(ns);
+  int64_t nII = 0, nIG = 0, nGG = 0, nCG = 0, nGC = 0, nCC = 0;
+  for (int w = 0; w < ns; ++w) {
+    const int nI = B.h_nI[w], nG = B.h_nG[w], nc = B.h_nC[w];
+    oII[w] = nII; nII += (int64_t)nI * pad4(nI);
+    oIG[w] = nIG; nIG += (int64_t)nI * pad4(nG);
+    oGG[w] = nGG; nGG += (int64_t)nG * pad4(nG);
+    oCG[w] = nCG; nCG += (int64_t)nc * pad4(nG);
+    oGC[w] = nGC; nGC += (int64_t)nG * pad4(nc);
+    oCC[w] = nCC; nCC += (int64_t)nc * pad4(nc);
+  }
+  auto upload = [&](DBuf<int64_t>& d, const std::vector<int64_t>& v) {
+    d.alloc(v.size(), s);
+    UFE_CUDA(cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  };
+  upload(B.off_II, oII);
+  upload(B.off_GG, oGG);
+  upload(B.off_GC, oGC);
+  DBuf<int64_t> doIG;
+  upload(doIG, oIG);
+
+  // ---- local matrices, scales, weights
+  DBuf<double> AII, AIG, AGG, sI, sG, dGraw;
+  AII.alloc(std::max<int64_t>(nII, 1), s);
+  AIG.alloc(std::max<int64_t>(nIG, 1), s);
+  AGG.alloc(std::max<int64_t>(nGG, 1), s);
+  AII.zero();
+  AIG.zero();
+  AGG.zero();
+  sI.alloc(std::max<int64_t>(m.n_Iloc, 1), s);
+  sG.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  dGraw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  const SubMeta sm = B.meta();
+  k_local_assemble<<<ns, 256, 0, s>>>(sm, B.off_II.p, doIG.p, B.off_GG.p, AII.p, AIG.p, AGG.p);
+  k_local_diag<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p, dGraw.p);
+  B.w.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  k_weights<<<grid_for(nd, T), T, 0, s>>>(nd, m.n_neigh.p, m.gpos.p, dGraw.p,
+                                          B.opts.weighting == UFE_WEIGHT_TOPOLOGICAL, B.w.p);
+  UFE_CHECK_LAUNCH();
+
+  // ---- factorisations and explicit local operators
+  DBuf<double> Acw, rho;
+  if (B.mixed)
+    factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, B.fII,
+                           B.fGG, B.fGC, Acw, rho);
+  else
+    factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, B.dII,
+                            B.dGG, B.dGC, Acw, rho);
+  AII.release();
+  AIG.release();
+  AGG.release();
+
+  // ---- coarse matrix (FP64), assembled and inverted
+  B.ldc = pad4((int)std::max<int64_t>(nco, 1));
+  B.Ac_inv.alloc((size_t)std::max<int64_t>(nco, 1) * B.ldc, s);
+  B.Ac_inv.zero();
+  if (nco) {
+    DBuf<int64_t> dCC;
+    upload(dCC, oCC);
+    k_coarse_assemble<<<(unsigned)nco, 128, 0, s>>>(nco, B.ldc, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p,
+                                                    B.C_ptr.p, B.C_list.p, dCC.p, Acw.p, B.Ac_inv.p);
+    k_symmetrize<<<grid_for(nco * nco, T), T, 0, s>>>(B.Ac_inv.p, (int)nco, B.ldc);
+    UFE_CHECK_LAUNCH();
+    DBuf<int> st;
+    st.alloc(1, s);
+    st.zero();
+    large_inverse<double>(B.Ac_inv.p, (int)nco, B.ldc, st.p, s);
+    UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
+  }
+
+  // ---- solver work space
+  B.tG.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  B.vw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  B.gC.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
+  B.uc.alloc(std::max<int64_t>(nco, 1), s);
+  for (DBuf<double>* v : {&B.x, &B.r, &B.b, &B.z, &B.q, &B.p0, &B.p1}) {
+    v->alloc(nd, s);
+    v->zero();
+  }
+  B.part_blocks = std::max<int64_t>(grid_for(nd, 256), ns) + 8;
+  B.part.alloc(B.part_blocks * 2, s);
+  B.sc.alloc(1, s);
+  B.sc.zero();
+  if (!B.h_sc) UFE_CUDA(cudaMallocHost((void**)&B.h_sc, sizeof(PcgScalars)));
+
+  UFE_CUDA(cudaEventRecord(e1, s));
+  UFE_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  B.setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+}  // namespace ufe

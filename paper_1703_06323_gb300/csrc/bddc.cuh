@@ -1,0 +1,94 @@
+// BDDC preconditioner state shared by the set-up (bddc.cu) and the solver (pcg.cu).
+#pragma once
+
+#include "ufe_internal.cuh"
+
+namespace ufe {
+
+// metadata the per-subdomain solve kernels read (all device pointers)
+struct SubMeta {
+  GridGeom g;
+  int n_sub;
+  const int32_t* sub_block;
+  const int32_t* sub_of_cell;
+  const uint8_t* cell_type;
+  const int32_t* cut_index;
+  const double* K_cut;
+  const double* kappa;      // may be null
+  const int32_t* dof_of_node;
+  const int32_t* lmap;
+  const int32_t* I_ptr;
+  const int32_t* I_list;
+  const int32_t* G_ptr;
+  const int32_t* G_list;
+  const int32_t* C_ptr;
+  const int32_t* C_list;
+  const int32_t* neigh;
+  const uint8_t* n_neigh;
+  const int32_t* gpos;
+  const int64_t* off_II;    // element offset of A_II^-1 (nI x ldI)
+  const int64_t* off_GG;    // element offset of K (nG x ldG)
+  const int64_t* off_GC;    // element offset of Phi (nG x ldC)
+  const double* w;          // weight per interface slot
+};
+
+struct PcgScalars {
+  double pq;           // p . A p
+  double rr;           // r . r after the update
+  double rz;           // r_k . z_k of the previous iteration
+  double rz_next;      // r . z of the freshly preconditioned residual
+  double rzold_next;   // r . z_old (flexible beta)
+  double bb;           // |b|^2
+  double tol2;         // (rtol |b|)^2
+  int iter;            // completed x/r updates
+  int done;            // 0 running, 1 converged, 2 max iterations, 3 breakdown
+  int first;           // first search direction (beta = 0)
+  int maxit;
+  int flexible;
+  int pad;
+  unsigned int counter[8];   // last-block-done counters per kernel
+};
+
+struct Bddc {
+  System* sys = nullptr;
+  Mesh* mesh = nullptr;
+  cudaStream_t stream = nullptr;
+  ufe_bddc_opts opts{};
+  bool mixed = false;
+
+  // objects (Sect. 3.2, Sect. 4.4)
+  int64_t n_obj = 0, n_corner = 0, n_edge = 0, n_face = 0, n_coarse = 0, n_Cloc = 0;
+  int max_nC = 0;
+  DBuf<int32_t> obj_of_dof, obj_kind, obj_rep, obj_size, coarse_of_obj, coarse_obj, coarse_rep;
+  DBuf<uint8_t> coarse_nn;      // |neigh| of each coarse DOF
+  DBuf<int32_t> C_ptr, C_list, cpos;
+  std::vector<int32_t> h_nI, h_nG, h_nC;
+
+  // per-iteration operators
+  DBuf<int64_t> off_II, off_GG, off_GC;
+  DBuf<double> dII, dGG, dGC;   // FP64 operators
+  DBuf<float> fII, fGG, fGC;    // FP32 operators (mixed)
+  DBuf<double> w;               // n_Gloc weights
+  DBuf<double> Ac_inv;          // n_coarse x ldc, FP64
+  int ldc = 0;
+
+  // solver work space
+  DBuf<double> tG, vw, gC, uc;
+  DBuf<double> x, r, b, z, q, p0, p1;
+  DBuf<double> part;            // per-block partial sums
+  DBuf<PcgScalars> sc;
+  PcgScalars* h_sc = nullptr;   // pinned mirror
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  int64_t part_blocks = 0;
+  double setup_ms = 0.0;
+
+  SubMeta meta() const;
+  ~Bddc();
+};
+
+void bddc_build(Bddc& B);
+void bddc_apply(Bddc& B, const double* r_dev, double* z_dev);
+void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);
+
+}  // namespace ufe

@@ -1,0 +1,35 @@
+// Batched dense kernels for the BDDC set-up: variable-size batched GEMM and
+// in-place blocked Gauss-Jordan inversion of SPD matrices (no pivoting; SPD
+// matrices are Jacobi-scaled before inversion).  Row-major storage, leading
+// dimensions padded to multiples of 4 elements.
+#pragma once
+
+#include "ufe_internal.cuh"
+
+namespace ufe {
+
+struct GemmDesc {
+  int m, n, k;
+  int lda, ldb, ldc;
+  int64_t a, b, c;   // element offsets into the A, B, C base pointers
+};
+
+struct InvDesc {
+  int n, ld;
+  int64_t off;
+};
+
+// C = alpha * op(A) op(B) + beta * C for every descriptor; trans flags select op.
+template <typename T>
+void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, const T* A, const T* B, T* C,
+                  T alpha, T beta, cudaStream_t s);
+
+// in-place inverse of each SPD matrix; status[b] |= DEV_SINGULAR on a non-positive pivot
+template <typename T>
+void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s);
+
+// in-place inverse of one large SPD matrix using the whole GPU
+template <typename T>
+void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s);
+
+}  // namespace ufe

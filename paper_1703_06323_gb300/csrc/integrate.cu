@@ -1,0 +1,365 @@
+// Cut-cell integration and right-hand side (Sect. 2.2).
+//
+// Each cube is split into the 6 Kuhn tetrahedra v000 -> v000+e_a -> v000+e_a+e_b
+// -> v111; the level set is linear on each tetrahedron and the part {phi < 0} is
+// cut out with the edge crossing points.  1 or 3 inside vertices leave a tet or a
+// prism, 2 leave a prism; prisms are split into 3 tets.  The boundary facet is a
+// triangle or a planar quad (2 triangles) with normal grad(phi)/|grad(phi)|.
+// Volumes use the degree-7 Grundmann-Moeller tet rule and facets the degree-7
+// triangle rule (the integrands have degree <= 6, so the integrals are exact up
+// to rounding).  The rules are generated on the host from the published
+// formula of Grundmann & Moeller (1978) and kept in constant memory.
+//
+// One thread per (cut cell, Kuhn tet); the 6 partial results of a cell are
+// summed in a fixed order in shared memory.
+#include <cmath>
+#include <functional>
+#include <mutex>
+#include <vector>
+
+#include "q1.cuh"
+#include "ufe_internal.cuh"
+
+namespace ufe {
+
+constexpr int kTetPts = 35, kTriPts = 20;
+__constant__ double c_tet_bary[kTetPts * 4];
+__constant__ double c_tet_w[kTetPts];
+__constant__ double c_tri_bary[kTriPts * 3];
+__constant__ double c_tri_w[kTriPts];
+
+// Grundmann-Moeller rule of degree 2s+1 on the n-simplex; weights rescaled to sum to 1.
+static void gm_rule(int n, int s, std::vector<double>& bary, std::vector<double>& w) {
+  const int d = 2 * s + 1;
+  auto fact = [](int k) {
+    double r = 1.0;
+    for (int i = 2; i <= k; ++i) r *= i;
+    return r;
+  };
+  bary.clear();
+  w.clear();
+  for (int i = 0; i <= s; ++i) {
+    const int denom = d + n - 2 * i;
+    const double wt = ((i % 2) ? -1.0 : 1.0) * std::ldexp(1.0, -2 * s) * std::pow((double)denom, d) /
+                      (fact(i) * fact(d + n - i)) * fact(n);
+    // all (n+1)-tuples beta >= 0 with |beta| = s - i
+    std::vector<int> beta(n + 1, 0);
+    std::function<void(int, int)> rec = [&](int pos, int remaining) {
+      if (pos == n) {
+        beta[n] = remaining;
+        for (int j = 0; j <= n; ++j) bary.push_back((2.0 * beta[j] + 1.0) / denom);
+        w.push_back(wt);
+        return;
+      }
+      for (int v = 0; v <= remaining; ++v) {
+        beta[pos] = v;
+        rec(pos + 1, remaining - v);
+      }
+    };
+    rec(0, s - i);
+  }
+}
+
+void ensure_constants() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  for (int d : done)
+    if (d == dev) return;
+  std::vector<double> b, w;
+  gm_rule(3, 3, b, w);
+  UFE_REQUIRE((int)w.size() == kTetPts, UFE_ERR_CUDA, "tet rule size");
+  UFE_CUDA(cudaMemcpyToSymbol(c_tet_bary, b.data(), b.size() * sizeof(double)));
+  UFE_CUDA(cudaMemcpyToSymbol(c_tet_w, w.data(), w.size() * sizeof(double)));
+  gm_rule(2, 3, b, w);
+  UFE_REQUIRE((int)w.size() == kTriPts, UFE_ERR_CUDA, "triangle rule size");
+  UFE_CUDA(cudaMemcpyToSymbol(c_tri_bary, b.data(), b.size() * sizeof(double)));
+  UFE_CUDA(cudaMemcpyToSymbol(c_tri_w, w.data(), w.size() * sizeof(double)));
+  done.push_back(dev);
+}
+
+// accumulator layout: [0, 36) packed upper triangle of K (unit cube, a <= b),
+// [36, 44) load, [44] volume fraction
+constexpr int kAcc = 45;
+
+struct Vec3 {
+  double x, y, z;
+};
+__device__ __forceinline__ Vec3 lerp_cross(const Vec3& pu, const Vec3& pv, double fu, double fv) {
+  const double t = fu / (fu - fv);
+  return {pu.x + t * (pv.x - pu.x), pu.y + t * (pv.y - pu.y), pu.z + t * (pv.z - pu.z)};
+}
+
+struct CellData {
+  double f8[8];
+  double q8[8][3];
+  bool has_q;
+  double h;
+};
+
+__device__ void integrate_tet(const Vec3& A, const Vec3& B, const Vec3& C, const Vec3& D, const CellData& cd,
+                              double* acc) {
+  const double ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
+  const double vx = C.x - A.x, vy = C.y - A.y, vz = C.z - A.z;
+  const double wx = D.x - A.x, wy = D.y - A.y, wz = D.z - A.z;
+  const double det = ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx);
+  const double vol = fabs(det) / 6.0;
+  if (vol == 0.0) return;
+  const double h3 = cd.h * cd.h * cd.h;
+  for (int q = 0; q < kTetPts; ++q) {
+    const double l0 = c_tet_bary[4 * q], l1 = c_tet_bary[4 * q + 1], l2 = c_tet_bary[4 * q + 2],
+                 l3 = c_tet_bary[4 * q + 3];
+    const double px = l0 * A.x + l1 * B.x + l2 * C.x + l3 * D.x;
+    const double py = l0 * A.y + l1 * B.y + l2 * C.y + l3 * D.y;
+    const double pz = l0 * A.z + l1 * B.z + l2 * C.z + l3 * D.z;
+    const double wq = c_tet_w[q] * vol;
+    double N[8], G[8][3];
+    q1_shape_grad(px, py, pz, N, G);
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = a; b < 8; ++b, ++e) acc[e] += wq * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+    double fh = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fh += N[a] * cd.f8[a];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) acc[36 + a] += wq * fh * N[a] * h3;
+    acc[44] += wq;
+  }
+}
+
+__device__ void integrate_tri(const Vec3& A, const Vec3& B, const Vec3& C, const double n[3], const CellData& cd,
+                              double* acc) {
+  const double ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
+  const double vx = C.x - A.x, vy = C.y - A.y, vz = C.z - A.z;
+  const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
+  const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  if (area == 0.0) return;
+  const double h2 = cd.h * cd.h;
+  for (int q = 0; q < kTriPts; ++q) {
+    const double l0 = c_tri_bary[3 * q], l1 = c_tri_bary[3 * q + 1], l2 = c_tri_bary[3 * q + 2];
+    const double px = l0 * A.x + l1 * B.x + l2 * C.x;
+    const double py = l0 * A.y + l1 * B.y + l2 * C.y;
+    const double pz = l0 * A.z + l1 * B.z + l2 * C.z;
+    const double wq = c_tri_w[q] * area;
+    double N[8];
+    q1_shape(px, py, pz, N);
+    double qx = 0, qy = 0, qz = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      qx += N[a] * cd.q8[a][0];
+      qy += N[a] * cd.q8[a][1];
+      qz += N[a] * cd.q8[a][2];
+    }
+    const double gn = qx * n[0] + qy * n[1] + qz * n[2];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) acc[36 + a] += wq * gn * N[a] * h2;
+  }
+}
+
+// part {phi < 0} of one Kuhn tet with vertices P (unit-cube coordinates) and values F
+__device__ void clip_and_integrate(const Vec3 P[4], const double F[4], const CellData& cd, double* acc) {
+  int neg[4], pos[4], nn = 0, np = 0;
+  for (int m = 0; m < 4; ++m) {
+    if (F[m] < 0.0)
+      neg[nn++] = m;
+    else
+      pos[np++] = m;
+  }
+  if (nn == 0) return;
+  if (nn == 4) {
+    integrate_tet(P[0], P[1], P[2], P[3], cd, acc);
+    return;
+  }
+  // gradient of the linear level set on the tet: D g = dF (Cramer's rule)
+  const double d1x = P[1].x - P[0].x, d1y = P[1].y - P[0].y, d1z = P[1].z - P[0].z;
+  const double d2x = P[2].x - P[0].x, d2y = P[2].y - P[0].y, d2z = P[2].z - P[0].z;
+  const double d3x = P[3].x - P[0].x, d3y = P[3].y - P[0].y, d3z = P[3].z - P[0].z;
+  const double r1 = F[1] - F[0], r2 = F[2] - F[0], r3 = F[3] - F[0];
+  const double det = d1x * (d2y * d3z - d2z * d3y) - d1y * (d2x * d3z - d2z * d3x) + d1z * (d2x * d3y - d2y * d3x);
+  const double gx = (r1 * (d2y * d3z - d2z * d3y) - d1y * (r2 * d3z - d2z * r3) + d1z * (r2 * d3y - d2y * r3)) / det;
+  const double gy = (d1x * (r2 * d3z - d2z * r3) - r1 * (d2x * d3z - d2z * d3x) + d1z * (d2x * r3 - r2 * d3x)) / det;
+  const double gz = (d1x * (d2y * r3 - r2 * d3y) - d1y * (d2x * r3 - r2 * d3x) + r1 * (d2x * d3y - d2y * d3x)) / det;
+  const double gn = sqrt(gx * gx + gy * gy + gz * gz);
+  const double n[3] = {gx / gn, gy / gn, gz / gn};
+  if (nn == 1) {
+    const int a = neg[0], b = pos[0], c = pos[1], d = pos[2];
+    const Vec3 pab = lerp_cross(P[a], P[b], F[a], F[b]);
+    const Vec3 pac = lerp_cross(P[a], P[c], F[a], F[c]);
+    const Vec3 pad = lerp_cross(P[a], P[d], F[a], F[d]);
+    integrate_tet(P[a], pab, pac, pad, cd, acc);
+    if (cd.has_q) integrate_tri(pab, pac, pad, n, cd, acc);
+  } else if (nn == 3) {
+    const int a = neg[0], b = neg[1], c = neg[2], d = pos[0];
+    const Vec3 pad = lerp_cross(P[a], P[d], F[a], F[d]);
+    const Vec3 pbd = lerp_cross(P[b], P[d], F[b], F[d]);
+    const Vec3 pcd = lerp_cross(P[c], P[d], F[c], F[d]);
+    integrate_tet(P[a], P[b], P[c], pad, cd, acc);
+    integrate_tet(P[b], P[c], pad, pbd, cd, acc);
+    integrate_tet(P[c], pad, pbd, pcd, cd, acc);
+    if (cd.has_q) integrate_tri(pad, pbd, pcd, n, cd, acc);
+  } else {
+    const int a = neg[0], b = neg[1], c = pos[0], d = pos[1];
+    const Vec3 pac = lerp_cross(P[a], P[c], F[a], F[c]);
+    const Vec3 pad = lerp_cross(P[a], P[d], F[a], F[d]);
+    const Vec3 pbc = lerp_cross(P[b], P[c], F[b], F[c]);
+    const Vec3 pbd = lerp_cross(P[b], P[d], F[b], F[d]);
+    integrate_tet(P[a], pac, pad, P[b], cd, acc);
+    integrate_tet(pac, pad, P[b], pbc, cd, acc);
+    integrate_tet(pad, P[b], pbc, pbd, cd, acc);
+    if (cd.has_q) {
+      integrate_tri(pac, pad, pbd, n, cd, acc);
+      integrate_tri(pac, pbd, pbc, n, cd, acc);
+    }
+  }
+}
+
+constexpr int kCellsPerBlock = 16;
+
+__global__ void __launch_bounds__(kCellsPerBlock * 6)
+k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells, const double* __restrict__ phi,
+                const double* __restrict__ f, const double* __restrict__ q, double* __restrict__ K_cut,
+                double* __restrict__ load_cut, double* __restrict__ eta) {
+  __shared__ double part[kCellsPerBlock][6][kAcc];
+  const int slot = threadIdx.x / 6, t = threadIdx.x % 6;
+  const int64_t kc = (int64_t)blockIdx.x * kCellsPerBlock + slot;
+  double acc[kAcc];
+#pragma unroll
+  for (int e = 0; e < kAcc; ++e) acc[e] = 0.0;
+  if (kc < n_cut) {
+    const int64_t c = cut_cells[kc];
+    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+    CellData cd;
+    cd.h = g.h;
+    cd.has_q = q != nullptr;
+    double phi8[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t v = g.node(i + (a & 1), j + ((a >> 1) & 1), k + (a >> 2));
+      phi8[a] = phi[v];
+      cd.f8[a] = f ? f[v] : 0.0;
+      for (int dd = 0; dd < 3; ++dd) cd.q8[a][dd] = q ? q[3 * v + dd] : 0.0;
+    }
+    // Kuhn tet t: first two axes of the t-th permutation of (x, y, z)
+    const int ax0[6] = {0, 0, 1, 1, 2, 2};
+    const int ax1[6] = {1, 2, 0, 2, 0, 1};
+    const int vid[4] = {0, 1 << ax0[t], (1 << ax0[t]) | (1 << ax1[t]), 7};
+    Vec3 P[4];
+    double F[4];
+    for (int m = 0; m < 4; ++m) {
+      P[m] = {(double)(vid[m] & 1), (double)((vid[m] >> 1) & 1), (double)(vid[m] >> 2)};
+      F[m] = phi8[vid[m]];
+    }
+    clip_and_integrate(P, F, cd, acc);
+  }
+  for (int e = 0; e < kAcc; ++e) part[slot][t][e] = acc[e];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kCellsPerBlock * kAcc; idx += blockDim.x) {
+    const int sl = idx / kAcc, e = idx % kAcc;
+    const int64_t kk = (int64_t)blockIdx.x * kCellsPerBlock + sl;
+    if (kk >= n_cut) continue;
+    double s = 0.0;
+    for (int tt = 0; tt < 6; ++tt) s += part[sl][tt][e];
+    if (e < 36) {
+      // packed (a, b), a <= b  ->  symmetric 8 x 8, scaled by h
+      int a = 0, rem = e;
+      while (rem >= 8 - a) {
+        rem -= 8 - a;
+        ++a;
+      }
+      const int b = a + rem;
+      K_cut[kk * 64 + a * 8 + b] = s * g.h;
+      K_cut[kk * 64 + b * 8 + a] = s * g.h;
+    } else if (e < 44) {
+      load_cut[kk * 8 + (e - 36)] = s;
+    } else {
+      eta[kk] = s;
+    }
+  }
+}
+
+// b = sum_e load_e - A_FC g_C  over the free DOFs (one thread per DOF, cells in a fixed order)
+__global__ void k_rhs(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                      const int32_t* __restrict__ dof_of_node, const uint8_t* __restrict__ cell_type,
+                      const int32_t* __restrict__ cut_index, const double* __restrict__ K_cut,
+                      const double* __restrict__ load_cut, const double* __restrict__ kappa,
+                      const double* __restrict__ f, const double* __restrict__ gval,
+                      const uint8_t* __restrict__ node_flags, double* __restrict__ b) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof) return;
+  const int64_t v = node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  const double h = g.h, h3 = h * h * h;
+  double sum = 0.0;
+  for (int dk = -1; dk <= 0; ++dk)
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        const int ci = i + di, cj = j + dj, ck = k + dk;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
+        const int64_t c = g.cell(ci, cj, ck);
+        const uint8_t t = cell_type[c];
+        if (t == UFE_CELL_EXTERNAL) continue;
+        const int a = (-di) + 2 * (-dj) + 4 * (-dk);
+        const int32_t cx = t == UFE_CELL_CUT ? cut_index[c] : -1;
+        if (t == UFE_CELL_INTERNAL) {
+          if (f) {
+            double s = 0.0;
+            for (int bb = 0; bb < 8; ++bb)
+              s += q1_mhat(a, bb) * f[g.node(ci + (bb & 1), cj + ((bb >> 1) & 1), ck + (bb >> 2))];
+            sum += h3 * s;
+          }
+        } else {
+          sum += load_cut[(int64_t)cx * 8 + a];
+        }
+        if (gval) {
+          const double kap = kappa ? kappa[c] : 1.0;
+          for (int bb = 0; bb < 8; ++bb) {
+            const int64_t vb = g.node(ci + (bb & 1), cj + ((bb >> 1) & 1), ck + (bb >> 2));
+            // constrained = active node that is not a free DOF
+            if (dof_of_node[vb] >= 0 || !(node_flags[vb] & 1)) continue;
+            const double kab = t == UFE_CELL_INTERNAL ? h * q1_khat(a, bb) : K_cut[(int64_t)cx * 64 + a * 8 + bb];
+            sum -= kap * kab * gval[vb];
+          }
+        }
+      }
+  b[d] = sum;
+}
+
+__global__ void k_cut_list(int64_t n, const int32_t* __restrict__ cut_index, int32_t* __restrict__ cut_cells) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int32_t k = cut_index[c];
+  if (k >= 0) cut_cells[k] = (int32_t)c;
+}
+void launch_cut_list(const Mesh& m, cudaStream_t s) {
+  k_cut_list<<<grid_for(m.g.n_cells(), 256), 256, 0, s>>>(m.g.n_cells(), m.cut_index.p, m.cut_cells.p);
+  UFE_CHECK_LAUNCH();
+}
+
+void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* gval) {
+  ensure_constants();
+  Mesh& m = *sys.mesh;
+  cudaStream_t s = sys.stream;
+  const int64_t n_cut = m.n_cut;
+  m.cut_cells.alloc(n_cut > 0 ? n_cut : 1, s);
+  launch_cut_list(m, s);
+  sys.K_cut.alloc((n_cut > 0 ? n_cut : 1) * 64, s);
+  sys.load_cut.alloc((n_cut > 0 ? n_cut : 1) * 8, s);
+  sys.eta.alloc(n_cut > 0 ? n_cut : 1, s);
+  if (n_cut > 0) {
+    k_integrate_cut<<<grid_for(n_cut, kCellsPerBlock), kCellsPerBlock * 6, 0, s>>>(
+        m.g, n_cut, m.cut_cells.p, m.phi.p, f, q, sys.K_cut.p, sys.load_cut.p, sys.eta.p);
+    UFE_CHECK_LAUNCH();
+  }
+  sys.b.alloc(m.n_dof, s);
+  k_rhs<<<grid_for(m.n_dof, 128), 128, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p,
+                                               m.cut_index.p, sys.K_cut.p, sys.load_cut.p, kappa, f, gval,
+                                               m.node_flags.p, sys.b.p);
+  UFE_CHECK_LAUNCH();
+}
+
+}  // namespace ufe

@@ -1,0 +1,719 @@
+// BDDC-preconditioned CG on the device (Sect. 5.1 stopping rule |r| < rtol |b|).
+//
+// One iteration is six kernels, captured in a CUDA graph together with the next
+// iterations of a chunk:
+//   K1  p = z + beta p (double-buffered, computed on the fly for the 27-node
+//       neighbourhood) and q = A p, element by element; partial p.q
+//   K2  alpha = r.z / p.q;  x += alpha p;  r -= alpha q;  |r|^2, convergence
+//   K3  per subdomain: y_I = A_II^-1 r_I, t_G = A_GI y_I          (Eq. bddc, first term
+//       and E^T = I - A I0 A0^-1 I0^T)
+//   K4  per subdomain: r~_G = w (r_G - sum_w' t_G^w') (weighted restriction W^T E^T r),
+//       v = K r~ (constrained Neumann), g = Phi^T r~ (coarse residual part)
+//   K5  coarse: r_c = sum R_c^T g, u_c = A_c^-1 r_c
+//   K7  per subdomain: u_G = sum_w' w' (v + Phi u_c) (weighting W), z_G = u_G,
+//       z_I = A_II^-1 (r_I - A_IG u_G) (harmonic extension); partial r.z
+// Scalars live on the device; every kernel returns at once after convergence,
+// so the host only reads the state once per chunk.  Reductions are done by the
+// last CTA to finish (fixed summation order, deterministic).
+#include <algorithm>
+
+#include "bddc.cuh"
+#include "q1.cuh"
+
+namespace ufe {
+
+constexpr int kApplyThreads = 256;
+constexpr int kSubThreads = 512;
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// deterministic block sum (fixed tree); all threads get the result
+__device__ double block_sum(double v) {
+  __shared__ double ws[32];
+  __shared__ double tot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double t = lane < nw ? ws[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) tot = t;
+  }
+  __syncthreads();
+  const double r = tot;
+  __syncthreads();
+  return r;
+}
+
+// true in exactly one CTA: the last one to arrive (after all partials are visible)
+__device__ bool arrive_last(unsigned int* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicInc(counter, gridDim.x - 1) == gridDim.x - 1;
+  __syncthreads();
+  return last;
+}
+
+// sum of part[0..n) in a fixed order (called by one whole CTA)
+__device__ double sum_partials(const double* part, int n, int stride) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[(int64_t)i * stride];
+  return block_sum(v);
+}
+
+// ---------------------------------------------------------------------------
+// element-by-element operator apply (Sect. 2.2): internal cells use kappa h Khat,
+// cut cells their own 8x8 matrix
+// ---------------------------------------------------------------------------
+struct OpArgs {
+  GridGeom g;
+  int64_t n_dof;
+  const int32_t* node_of_dof;
+  const int32_t* dof_of_node;
+  const uint8_t* cell_type;
+  const int32_t* cut_index;
+  const double* K_cut;
+  const double* kappa;
+};
+
+template <typename Val>
+__device__ __forceinline__ double apply_row(const OpArgs& a, int64_t d, Val val) {
+  const GridGeom& g = a.g;
+  const int64_t v = a.node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  double xn[27];
+#pragma unroll
+  for (int oz = -1; oz <= 1; ++oz)
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int ii = i + ox, jj = j + oy, kk = k + oz;
+        double x = 0.0;
+        if (ii >= 0 && jj >= 0 && kk >= 0 && ii <= g.nx && jj <= g.ny && kk <= g.nz) {
+          const int32_t e = a.dof_of_node[g.node(ii, jj, kk)];
+          if (e >= 0) x = val(e);
+        }
+        xn[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] = x;
+      }
+  double acc = 0.0;
+#pragma unroll
+  for (int dk = -1; dk <= 0; ++dk)
+#pragma unroll
+    for (int dj = -1; dj <= 0; ++dj)
+#pragma unroll
+      for (int di = -1; di <= 0; ++di) {
+        const int ci = i + di, cj = j + dj, ck = k + dk;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
+        const int64_t c = g.cell(ci, cj, ck);
+        const uint8_t t = a.cell_type[c];
+        if (t == UFE_CELL_EXTERNAL) continue;
+        const int av = (-di) + 2 * (-dj) + 4 * (-dk);
+        const double kap = a.kappa ? a.kappa[c] : 1.0;
+        double s = 0.0;
+        if (t == UFE_CELL_INTERNAL) {
+#pragma unroll
+          for (int b = 0; b < 8; ++b)
+            s += q1_khat(av, b) * xn[(di + (b & 1) + 1) + 3 * (dj + ((b >> 1) & 1) + 1) + 9 * (dk + (b >> 2) + 1)];
+          s *= g.h;
+        } else {
+          const double* Kc = a.K_cut + (int64_t)a.cut_index[c] * 64 + av * 8;
+#pragma unroll
+          for (int b = 0; b < 8; ++b)
+            s += Kc[b] * xn[(di + (b & 1) + 1) + 3 * (dj + ((b >> 1) & 1) + 1) + 9 * (dk + (b >> 2) + 1)];
+        }
+        acc += kap * s;
+      }
+  return acc;
+}
+
+__global__ void __launch_bounds__(kApplyThreads) k_apply(OpArgs a, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= a.n_dof) return;
+  y[d] = apply_row(a, d, [&](int32_t e) { return x[e]; });
+}
+
+// r = b - A x, |r|^2 and |b|^2; mode 0 initialises the scalars, mode 1 only reports |b - A x|^2
+__global__ void __launch_bounds__(kApplyThreads)
+k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
+           double* __restrict__ part, PcgScalars* sc, double rtol, int mode, double* out) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0, bb = 0.0;
+  if (d < a.n_dof) {
+    const double res = b[d] - apply_row(a, d, [&](int32_t e) { return x[e]; });
+    if (r) r[d] = res;
+    rr = res * res;
+    bb = b[d] * b[d];
+  }
+  rr = block_sum(rr);
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rr;
+    part[2 * blockIdx.x + 1] = bb;
+  }
+  if (arrive_last(&sc->counter[0])) {
+    const double R = sum_partials(part, gridDim.x, 2);
+    const double B = sum_partials(part + 1, gridDim.x, 2);
+    if (threadIdx.x == 0) {
+      if (mode == 0) {
+        sc->rr = R;
+        sc->bb = B;
+        sc->tol2 = rtol * rtol * B;
+        sc->iter = 0;
+        sc->first = 1;
+        sc->done = (R < sc->tol2 || B == 0.0) ? 1 : 0;
+      } else {
+        out[0] = R;
+        out[1] = B;
+      }
+    }
+  }
+}
+
+// K1: p_new = z + beta p_old (beta = 0 for the first direction); q = A p_new; p.q
+__global__ void __launch_bounds__(kApplyThreads)
+k_dir_apply(OpArgs a, const double* __restrict__ z, double* p0, double* p1, double* __restrict__ q,
+            double* __restrict__ part, PcgScalars* sc) {
+  if (sc->done) return;
+  const int it = sc->iter;
+  const double* pold = (it & 1) ? p1 : p0;
+  double* pnew = (it & 1) ? p0 : p1;
+  double beta = 0.0;
+  if (!sc->first) beta = sc->flexible ? (sc->rz_next - sc->rzold_next) / sc->rz : sc->rz_next / sc->rz;
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double pq = 0.0;
+  if (d < a.n_dof) {
+    const double qd = apply_row(a, d, [&](int32_t e) { return z[e] + beta * pold[e]; });
+    const double pd = z[d] + beta * pold[d];
+    pnew[d] = pd;
+    q[d] = qd;
+    pq = pd * qd;
+  }
+  pq = block_sum(pq);
+  if (threadIdx.x == 0) part[blockIdx.x] = pq;
+  if (arrive_last(&sc->counter[1])) {
+    const double P = sum_partials(part, gridDim.x, 1);
+    if (threadIdx.x == 0) sc->pq = P;
+  }
+}
+
+// K2: x += alpha p, r -= alpha q, |r|^2, convergence test
+__global__ void __launch_bounds__(kApplyThreads)
+k_update(int64_t n, double* __restrict__ x, double* __restrict__ r, const double* p0, const double* p1,
+         const double* __restrict__ q, double* __restrict__ part, PcgScalars* sc) {
+  if (sc->done) return;
+  const int it = sc->iter;
+  const double* p = (it & 1) ? p0 : p1;
+  const double pq = sc->pq;
+  const bool ok = pq > 0.0;
+  const double alpha = ok ? sc->rz_next / pq : 0.0;
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0;
+  if (d < n && ok) {
+    x[d] += alpha * p[d];
+    const double rd = r[d] - alpha * q[d];
+    r[d] = rd;
+    rr = rd * rd;
+  }
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) part[blockIdx.x] = rr;
+  if (arrive_last(&sc->counter[2])) {
+    const double R = sum_partials(part, gridDim.x, 1);
+    if (threadIdx.x == 0) {
+      if (!ok) {
+        sc->done = 3;
+      } else {
+        sc->rr = R;
+        sc->iter = it + 1;
+        sc->rz = sc->rz_next;
+        sc->first = 0;
+        if (R < sc->tol2)
+          sc->done = 1;
+        else if (it + 1 >= sc->maxit)
+          sc->done = 2;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner stages
+// ---------------------------------------------------------------------------
+template <typename TM>
+struct VecT;
+template <>
+struct VecT<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct VecT<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+__device__ __forceinline__ float dot_vec(const float4& a, const float* x) {
+  return a.x * x[0] + a.y * x[1] + a.z * x[2] + a.w * x[3];
+}
+__device__ __forceinline__ double dot_vec(const double2& a, const double* x) { return a.x * x[0] + a.y * x[1]; }
+
+// ys[r] = sum_c M[r, c] xs[c] for r < m (row-major, ld a multiple of 4, xs zero-padded to ld)
+template <typename TM>
+__device__ void cta_gemv(const TM* __restrict__ M, int m, int ld, const TM* __restrict__ xs, double* __restrict__ ys) {
+  using V = typename VecT<TM>::type;
+  constexpr int VN = VecT<TM>::n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int r = wid;
+  for (; r + nw < m; r += 2 * nw) {
+    const TM* ra = M + (int64_t)r * ld;
+    const TM* rb = M + (int64_t)(r + nw) * ld;
+    TM sa = TM(0), sb = TM(0);
+    for (int c = lane * VN; c < ld; c += 32 * VN) {
+      const V va = *reinterpret_cast<const V*>(ra + c);
+      const V vb = *reinterpret_cast<const V*>(rb + c);
+      sa += dot_vec(va, xs + c);
+      sb += dot_vec(vb, xs + c);
+    }
+    double da = (double)sa, db = (double)sb;
+    da = warp_sum(da);
+    db = warp_sum(db);
+    if (lane == 0) {
+      ys[r] = da;
+      ys[r + nw] = db;
+    }
+  }
+  for (; r < m; r += nw) {
+    const TM* ra = M + (int64_t)r * ld;
+    TM sa = TM(0);
+    for (int c = lane * VN; c < ld; c += 32 * VN) sa += dot_vec(*reinterpret_cast<const V*>(ra + c), xs + c);
+    double da = warp_sum((double)sa);
+    if (lane == 0) ys[r] = da;
+  }
+}
+
+// sum over the cells of subdomain w around local node (lx,ly,lz) of the matrix row
+// times the values at the neighbouring local DOFs of the given kind
+template <int KIND>
+__device__ double local_stencil(const SubMeta& sm, int w, int bi, int bj, int bk, int lx, int ly, int lz,
+                                const int32_t* __restrict__ lm, const double* __restrict__ vals) {
+  const GridGeom& g = sm.g;
+  double sum = 0.0;
+  for (int cz = lz - 1; cz <= lz; ++cz) {
+    if (cz < 0 || cz >= g.sz) continue;
+    for (int cy = ly - 1; cy <= ly; ++cy) {
+      if (cy < 0 || cy >= g.sy) continue;
+      for (int cx = lx - 1; cx <= lx; ++cx) {
+        if (cx < 0 || cx >= g.sx) continue;
+        const int64_t c = g.cell(bi * g.sx + cx, bj * g.sy + cy, bk * g.sz + cz);
+        if (sm.sub_of_cell[c] != w) continue;
+        const int a = (lx - cx) + 2 * (ly - cy) + 4 * (lz - cz);
+        const bool internal = sm.cell_type[c] == UFE_CELL_INTERNAL;
+        const double* Kc = internal ? nullptr : sm.K_cut + (int64_t)sm.cut_index[c] * 64 + a * 8;
+        double s = 0.0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int ln = (cx + (b & 1)) + g.lnx * ((cy + ((b >> 1) & 1)) + g.lny * (cz + (b >> 2)));
+          const int32_t code = lm[ln];
+          if (lmap_kind(code) != KIND) continue;
+          const double kab = internal ? g.h * q1_khat(a, b) : Kc[b];
+          s += kab * vals[lmap_index(code)];
+        }
+        sum += (sm.kappa ? sm.kappa[c] : 1.0) * s;
+      }
+    }
+  }
+  return sum;
+}
+
+struct SubSizes {
+  int nI, nG, nC, ldI, ldG, ldC, bi, bj, bk;
+};
+__device__ __forceinline__ SubSizes sub_sizes(const SubMeta& sm, int w) {
+  SubSizes z;
+  z.nI = sm.I_ptr[w + 1] - sm.I_ptr[w];
+  z.nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  z.nC = sm.C_ptr[w + 1] - sm.C_ptr[w];
+  z.ldI = pad4(z.nI);
+  z.ldG = pad4(z.nG);
+  z.ldC = pad4(z.nC);
+  const int b = sm.sub_block[w];
+  z.bi = b % sm.g.bx;
+  z.bj = (b / sm.g.bx) % sm.g.by;
+  z.bk = b / (sm.g.bx * sm.g.by);
+  return z;
+}
+
+// shared memory layout shared by the per-subdomain kernels
+struct SubSmem {
+  int32_t* lm;    // n_local_nodes
+  double* dI;     // ldImax doubles
+  double* dG;     // ldGmax doubles
+  void* xT;       // max(ldImax, ldGmax) TM values
+};
+
+template <typename TM>
+__device__ SubSmem carve(char* smem, const SubMeta& sm, int ldImax, int ldGmax) {
+  SubSmem s;
+  s.lm = reinterpret_cast<int32_t*>(smem);
+  size_t off = ((size_t)sm.g.n_local_nodes * 4 + 15) & ~(size_t)15;
+  s.dI = reinterpret_cast<double*>(smem + off);
+  off += (size_t)ldImax * 8;
+  s.dG = reinterpret_cast<double*>(smem + off);
+  off += (size_t)ldGmax * 8;
+  s.xT = smem + off;
+  return s;
+}
+
+// K3: y_I = A_II^-1 r_I; t_G = A_GI y_I
+template <typename TM>
+__global__ void __launch_bounds__(kSubThreads)
+k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, double* __restrict__ tG,
+                 const PcgScalars* sc, int ldImax, int ldGmax) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) char smem[];
+  const int w = blockIdx.x;
+  const SubSizes z = sub_sizes(sm, w);
+  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  TM* xI = reinterpret_cast<TM*>(S.xT);
+  const int32_t* lmg = sm.lmap + (int64_t)w * sm.g.n_local_nodes;
+  for (int e = threadIdx.x; e < sm.g.n_local_nodes; e += blockDim.x) S.lm[e] = lmg[e];
+  for (int p = threadIdx.x; p < z.ldI; p += blockDim.x) xI[p] = p < z.nI ? (TM)r[sm.I_list[sm.I_ptr[w] + p]] : TM(0);
+  __syncthreads();
+  cta_gemv<TM>(AIIinv + sm.off_II[w], z.nI, z.ldI, xI, S.dI);
+  __syncthreads();
+  for (int ln = threadIdx.x; ln < sm.g.n_local_nodes; ln += blockDim.x) {
+    const int32_t code = S.lm[ln];
+    if (lmap_kind(code) != LKIND_G) continue;
+    const int lx = ln % sm.g.lnx, ly = (ln / sm.g.lnx) % sm.g.lny, lz = ln / (sm.g.lnx * sm.g.lny);
+    tG[sm.G_ptr[w] + lmap_index(code)] = local_stencil<LKIND_I>(sm, w, z.bi, z.bj, z.bk, lx, ly, lz, S.lm, S.dI);
+  }
+}
+
+// K4: r~ = w (r_G - sum t_G); v = K r~ (stored weighted: vw = w v); g = Phi^T r~
+template <typename TM>
+__global__ void __launch_bounds__(kSubThreads)
+k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Phi, const double* __restrict__ r,
+               const double* __restrict__ tG, double* __restrict__ vw, double* __restrict__ gC, const PcgScalars* sc,
+               int ldImax, int ldGmax) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) char smem[];
+  __shared__ double gpart[kSubThreads / 32][64];
+  const int w = blockIdx.x;
+  const SubSizes z = sub_sizes(sm, w);
+  if (z.nG == 0) return;
+  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  TM* xG = reinterpret_cast<TM*>(S.xT);
+  const int g0 = sm.G_ptr[w];
+  for (int j = threadIdx.x; j < z.ldG; j += blockDim.x) {
+    TM v = TM(0);
+    if (j < z.nG) {
+      const int32_t xi = sm.G_list[g0 + j];
+      double s = r[xi];
+      const int cnt = sm.n_neigh[xi];
+      for (int k = 0; k < cnt; ++k) s -= tG[sm.gpos[(int64_t)xi * 8 + k]];
+      v = (TM)(sm.w[g0 + j] * s);
+    }
+    xG[j] = v;
+  }
+  __syncthreads();
+  cta_gemv<TM>(Kop + sm.off_GG[w], z.nG, z.ldG, xG, S.dG);
+  // g = Phi^T r~ : warps split the rows, lanes the coarse columns (nC <= 1024, chunks of 64)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const TM* P = Phi + sm.off_GC[w];
+  for (int c0 = 0; c0 < z.nC; c0 += 64) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = wid; j < z.nG; j += nw) {
+      const double xj = (double)xG[j];
+      if (c0 + lane < z.nC) a0 += (double)P[(int64_t)j * z.ldC + c0 + lane] * xj;
+      if (c0 + lane + 32 < z.nC) a1 += (double)P[(int64_t)j * z.ldC + c0 + lane + 32] * xj;
+    }
+    gpart[wid][lane] = a0;
+    gpart[wid][lane + 32] = a1;
+    __syncthreads();
+    if (threadIdx.x < 64 && c0 + (int)threadIdx.x < z.nC) {
+      double s = 0.0;
+      for (int x = 0; x < nw; ++x) s += gpart[x][threadIdx.x];
+      gC[sm.C_ptr[w] + c0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < z.nG; j += blockDim.x) vw[g0 + j] = sm.w[g0 + j] * S.dG[j];
+}
+
+// K5: r_c gathered from the subdomain parts, u_c = A_c^-1 r_c (FP64)
+__global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ Ainv, const int32_t* __restrict__ cpos,
+                               const uint8_t* __restrict__ cnn, const double* __restrict__ gC, double* __restrict__ uc,
+                               const PcgScalars* sc) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) char smem[];
+  double* rc = reinterpret_cast<double*>(smem);
+  for (int64_t l = threadIdx.x; l < ldc; l += blockDim.x) {
+    double s = 0.0;
+    if (l < nco)
+      for (int k = 0; k < cnn[l]; ++k) s += gC[cpos[l * 8 + k]];
+    rc[l] = s;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < nco; row += (int64_t)gridDim.x * nw) {
+    const double* Ar = Ainv + row * ldc;
+    double s = 0.0;
+    for (int c = lane * 2; c < ldc; c += 64) {
+      const double2 v = *reinterpret_cast<const double2*>(Ar + c);
+      s += v.x * rc[c] + v.y * rc[c + 1];
+    }
+    s = warp_sum(s);
+    if (lane == 0) uc[row] = s;
+  }
+}
+
+// K7: u_G = sum_w' (vw + w Phi u_c); z_G = u_G (owner writes); z_I = A_II^-1 (r_I - A_IG u_G)
+template <typename TM>
+__global__ void __launch_bounds__(kSubThreads)
+k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const TM* __restrict__ Phi, const double* __restrict__ r,
+             const double* __restrict__ vw, const double* __restrict__ uc, double* __restrict__ z,
+             double* __restrict__ part, PcgScalars* sc, int ldImax, int ldGmax, int with_dots) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) char smem[];
+  const int w = blockIdx.x;
+  const SubSizes zz = sub_sizes(sm, w);
+  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  TM* xI = reinterpret_cast<TM*>(S.xT);
+  const int32_t* lmg = sm.lmap + (int64_t)w * sm.g.n_local_nodes;
+  for (int e = threadIdx.x; e < sm.g.n_local_nodes; e += blockDim.x) S.lm[e] = lmg[e];
+  double rz = 0.0, rzo = 0.0;
+  const int g0 = sm.G_ptr[w];
+  for (int j = threadIdx.x; j < zz.nG; j += blockDim.x) {
+    const int32_t xi = sm.G_list[g0 + j];
+    const int cnt = sm.n_neigh[xi];
+    double u = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+      const int32_t slot = sm.gpos[(int64_t)xi * 8 + k];
+      const int wk = sm.neigh[(int64_t)xi * 8 + k];
+      const int c0 = sm.C_ptr[wk], nC = sm.C_ptr[wk + 1] - c0, ldC = pad4(nC);
+      const TM* prow = Phi + sm.off_GC[wk] + (int64_t)(slot - sm.G_ptr[wk]) * ldC;
+      double cu = 0.0;
+      for (int c = 0; c < nC; ++c) cu += (double)prow[c] * uc[sm.C_list[c0 + c]];
+      u += vw[slot] + sm.w[slot] * cu;
+    }
+    S.dG[j] = u;
+    if (sm.neigh[(int64_t)xi * 8] == w) {
+      if (with_dots) {
+        rz += r[xi] * u;
+        rzo += r[xi] * z[xi];
+      }
+      z[xi] = u;
+    }
+  }
+  __syncthreads();
+  for (int ln = threadIdx.x; ln < sm.g.n_local_nodes; ln += blockDim.x) {
+    const int32_t code = S.lm[ln];
+    if (lmap_kind(code) != LKIND_I) continue;
+    const int p = lmap_index(code);
+    const int lx = ln % sm.g.lnx, ly = (ln / sm.g.lnx) % sm.g.lny, lz = ln / (sm.g.lnx * sm.g.lny);
+    const double rhs = r[sm.I_list[sm.I_ptr[w] + p]] - local_stencil<LKIND_G>(sm, w, zz.bi, zz.bj, zz.bk, lx, ly, lz, S.lm, S.dG);
+    xI[p] = (TM)rhs;
+  }
+  for (int p = zz.nI + threadIdx.x; p < zz.ldI; p += blockDim.x) xI[p] = TM(0);
+  __syncthreads();
+  cta_gemv<TM>(AIIinv + sm.off_II[w], zz.nI, zz.ldI, xI, S.dI);
+  __syncthreads();
+  for (int p = threadIdx.x; p < zz.nI; p += blockDim.x) {
+    const int32_t d = sm.I_list[sm.I_ptr[w] + p];
+    const double zn = S.dI[p];
+    if (with_dots) {
+      rz += r[d] * zn;
+      rzo += r[d] * z[d];
+    }
+    z[d] = zn;
+  }
+  if (!with_dots) return;
+  rz = block_sum(rz);
+  rzo = block_sum(rzo);
+  if (threadIdx.x == 0) {
+    part[2 * w] = rz;
+    part[2 * w + 1] = rzo;
+  }
+  if (arrive_last(&sc->counter[3])) {
+    const double a = sum_partials(part, gridDim.x, 2);
+    const double b = sum_partials(part + 1, gridDim.x, 2);
+    if (threadIdx.x == 0) {
+      sc->rz_next = a;
+      sc->rzold_next = b;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static OpArgs op_args(const System& sys) {
+  const Mesh& m = *sys.mesh;
+  OpArgs a;
+  a.g = m.g;
+  a.n_dof = m.n_dof;
+  a.node_of_dof = m.node_of_dof.p;
+  a.dof_of_node = m.dof_of_node.p;
+  a.cell_type = m.cell_type.p;
+  a.cut_index = m.cut_index.p;
+  a.K_cut = sys.K_cut.p;
+  a.kappa = sys.has_kappa ? sys.kappa.p : nullptr;
+  return a;
+}
+
+void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStream_t s) {
+  const OpArgs a = op_args(sys);
+  k_apply<<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+  UFE_CHECK_LAUNCH();
+}
+
+static size_t sub_smem_bytes(const Bddc& B, size_t tm_size) {
+  const Mesh& m = *B.mesh;
+  const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
+  size_t off = ((size_t)m.g.n_local_nodes * 4 + 15) & ~(size_t)15;
+  off += (size_t)ldI * 8 + (size_t)ldG * 8;
+  off += (size_t)std::max(ldI, ldG) * tm_size + 16;
+  return off;
+}
+
+template <typename TM>
+static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots) {
+  const Mesh& m = *B.mesh;
+  cudaStream_t s = B.stream;
+  const SubMeta sm = B.meta();
+  const int ns = (int)m.n_sub;
+  const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
+  const size_t smem = sub_smem_bytes(B, sizeof(TM));
+  const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
+  const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
+  const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
+  k_prec_interior1<TM><<<ns, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, ldI, ldG);
+  k_prec_neumann<TM><<<ns, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, ldI, ldG);
+  if (B.n_coarse > 0) {
+    const size_t csm = (size_t)B.ldc * 8;
+    const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
+    k_coarse_solve<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, B.gC.p, B.uc.p, sc);
+  }
+  k_prec_final<TM><<<ns, kSubThreads, smem, s>>>(sm, II, GC, r, B.vw.p, B.uc.p, z, B.part.p, sc, ldI, ldG, with_dots);
+  UFE_CHECK_LAUNCH();
+}
+
+static void set_smem_limits(Bddc& B) {
+  const size_t sd = sub_smem_bytes(B, 8), sf = sub_smem_bytes(B, 4);
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+  const size_t csm = (size_t)B.ldc * 8;
+  UFE_REQUIRE(csm <= 227 * 1024, UFE_ERR_UNSUPPORTED, "coarse problem larger than one CTA's shared memory");
+  UFE_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(csm, 1)));
+}
+
+static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots) {
+  if (B.mixed)
+    launch_preconditioner<float>(B, r, z, sc, with_dots);
+  else
+    launch_preconditioner<double>(B, r, z, sc, with_dots);
+}
+
+void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
+  set_smem_limits(B);
+  precondition(B, r_dev, z_dev, nullptr, 0);
+}
+
+static void launch_iteration(Bddc& B, const OpArgs& a) {
+  cudaStream_t s = B.stream;
+  const unsigned nb = grid_for(a.n_dof, kApplyThreads);
+  k_dir_apply<<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  k_update<<<nb, kApplyThreads, 0, s>>>(a.n_dof, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  precondition(B, B.r.p, B.z.p, B.sc.p, 1);
+}
+
+void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info) {
+  const Mesh& m = *B.mesh;
+  cudaStream_t s = B.stream;
+  const OpArgs a = op_args(*B.sys);
+  const int64_t n = m.n_dof;
+  set_smem_limits(B);
+  cudaEvent_t e0, e1;
+  UFE_CUDA(cudaEventCreate(&e0));
+  UFE_CUDA(cudaEventCreate(&e1));
+  UFE_CUDA(cudaEventRecord(e0, s));
+  UFE_CUDA(cudaMemcpyAsync(B.b.p, b_dev, n * 8, cudaMemcpyDeviceToDevice, s));
+  UFE_CUDA(cudaMemcpyAsync(B.x.p, x_dev, n * 8, cudaMemcpyDeviceToDevice, s));
+  PcgScalars init{};
+  init.maxit = std::max(o.maxit, 0);
+  init.flexible = o.flexible < 0 ? (B.mixed ? 1 : 0) : (o.flexible ? 1 : 0);
+  UFE_CUDA(cudaMemcpyAsync(B.sc.p, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+  const unsigned nb = grid_for(n, kApplyThreads);
+  k_residual<<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
+  UFE_CHECK_LAUNCH();
+  precondition(B, B.r.p, B.z.p, B.sc.p, 1);
+
+  const int chunk = o.check_every > 0 ? o.check_every : 8;
+  if (!B.graph || B.graph_iters != chunk) {
+    if (B.graph) {
+      cudaGraphExecDestroy(B.graph);
+      B.graph = nullptr;
+    }
+    cudaGraph_t gr;
+    UFE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) launch_iteration(B, a);
+    UFE_CUDA(cudaStreamEndCapture(s, &gr));
+    UFE_CUDA(cudaGraphInstantiate(&B.graph, gr, 0));
+    cudaGraphDestroy(gr);
+    B.graph_iters = chunk;
+  }
+  // the host reads the device state once per chunk; loop bounded by maxit / chunk
+  const int max_chunks = init.maxit / chunk + 2;
+  for (int c = 0; c < max_chunks; ++c) {
+    UFE_CUDA(cudaMemcpyAsync(B.h_sc, B.sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    UFE_CUDA(cudaStreamSynchronize(s));
+    if (B.h_sc->done || B.h_sc->iter >= init.maxit) break;
+    UFE_CUDA(cudaGraphLaunch(B.graph, s));
+  }
+  UFE_CUDA(cudaMemcpyAsync(B.h_sc, B.sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  UFE_CUDA(cudaEventRecord(e1, s));
+  UFE_CUDA(cudaStreamSynchronize(s));
+  const PcgScalars fin = *B.h_sc;
+  if (fin.bb == 0.0) UFE_CUDA(cudaMemsetAsync(B.x.p, 0, n * 8, s));
+  UFE_CUDA(cudaMemcpyAsync(x_dev, B.x.p, n * 8, cudaMemcpyDeviceToDevice, s));
+  float ms = 0.f;
+  UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  // true residual |b - A x| / |b|
+  DBuf<double> out;
+  out.alloc(2, s);
+  k_residual<<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, nullptr, B.part.p, B.sc.p, 0.0, 1, out.p);
+  UFE_CHECK_LAUNCH();
+  std::vector<double> tr = to_host(out.p, 2, s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = fin.iter;
+    info->converged = fin.done == 1;
+    info->rel_residual = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
+    info->true_rel_residual = tr[1] > 0 ? std::sqrt(tr[0] / tr[1]) : 0.0;
+    info->solve_ms = ms;
+  }
+  if (fin.done == 3) throw Error{UFE_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0"};
+  if (fin.done != 1) throw Error{UFE_ERR_NO_CONVERGENCE, "PCG did not reach the tolerance within maxit"};
+}
+
+}  // namespace ufe

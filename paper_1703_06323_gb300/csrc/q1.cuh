@@ -1,0 +1,46 @@
+// Trilinear (Q1) shape functions on the unit cube and the closed-form unit-cube
+// stiffness and mass matrices (vertex a has offsets (a & 1, (a >> 1) & 1, a >> 2)).
+//   Khat_ab = sum_d k(a_d, b_d) prod_{d' != d} m(a_d', b_d'),  Mhat_ab = prod_d m(a_d, b_d),
+//   k(same) = 1, k(diff) = -1, m(same) = 1/3, m(diff) = 1/6.
+#pragma once
+
+namespace ufe {
+
+__host__ __device__ __forceinline__ double q1_khat(int a, int b) {
+  double m[3], k[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const bool same = ((a >> d) & 1) == ((b >> d) & 1);
+    m[d] = same ? (1.0 / 3.0) : (1.0 / 6.0);
+    k[d] = same ? 1.0 : -1.0;
+  }
+  return k[0] * m[1] * m[2] + m[0] * k[1] * m[2] + m[0] * m[1] * k[2];
+}
+
+__host__ __device__ __forceinline__ double q1_mhat(int a, int b) {
+  double r = 1.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) r *= (((a >> d) & 1) == ((b >> d) & 1)) ? (1.0 / 3.0) : (1.0 / 6.0);
+  return r;
+}
+
+__device__ __forceinline__ void q1_shape(double x, double y, double z, double N[8]) {
+  const double lx[2] = {1.0 - x, x}, ly[2] = {1.0 - y, y}, lz[2] = {1.0 - z, z};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) N[a] = lx[a & 1] * ly[(a >> 1) & 1] * lz[a >> 2];
+}
+
+__device__ __forceinline__ void q1_shape_grad(double x, double y, double z, double N[8], double G[8][3]) {
+  const double lx[2] = {1.0 - x, x}, ly[2] = {1.0 - y, y}, lz[2] = {1.0 - z, z};
+  const double dl[2] = {-1.0, 1.0};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+    N[a] = lx[ax] * ly[ay] * lz[az];
+    G[a][0] = dl[ax] * ly[ay] * lz[az];
+    G[a][1] = lx[ax] * dl[ay] * lz[az];
+    G[a][2] = lx[ax] * ly[ay] * dl[az];
+  }
+}
+
+}  // namespace ufe

@@ -1,0 +1,72 @@
+"""Convenience layer: one Problem -> mesh, system, preconditioner, solve.
+
+Each step is one C-ABI call (see include/ufe.h); this module only keeps the
+handles together and frees them in the right order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ufe
+
+WEIGHTING = {"stiffness": ufe.WEIGHT_STIFFNESS, "topological": ufe.WEIGHT_TOPOLOGICAL}
+OBJECTS = {"std": ufe.OBJECTS_STANDARD, "v1": ufe.OBJECTS_VARIANT1}
+COARSE = {"c": ufe.COARSE_C, "ce": ufe.COARSE_CE, "cef": ufe.COARSE_CEF}
+PRECISION = {"fp64": ufe.PREC_FP64, "mixed": ufe.PREC_MIXED}
+
+
+class Solver:
+    """Owns the ufe handles of one problem (host numpy inputs or torch CUDA tensors)."""
+
+    def __init__(self, problem, weighting="stiffness", objects="v1", coarse="cef", precision="fp64", stream=None,
+                 arrays=None):
+        p = problem
+        a = arrays or {}
+        self.mesh = ufe.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, a.get("phi", p.phi),
+                                        p.dirichlet_face_mask, p.pin_node, stream=stream)
+        self.system = None
+        self.bddc = None
+        try:
+            self.info = ufe.ufe_mesh_get_info(self.mesh)
+            self.system = ufe.ufe_assemble(self.mesh, a.get("kappa", p.kappa), a.get("f", p.f),
+                                           a.get("q", p.q), a.get("g", p.dirichlet_values))
+            self.bddc = ufe.ufe_bddc_setup(self.system, WEIGHTING[weighting], OBJECTS[objects], COARSE[coarse],
+                                           PRECISION[precision])
+            self.bddc_info = ufe.ufe_bddc_get_info(self.bddc)
+        except Exception:
+            self.close()
+            raise
+        self.n_dof = self.info["n_dof"]
+
+    def rhs(self):
+        return ufe.ufe_system_get_rhs(self.system, self.n_dof)
+
+    def apply(self, x):
+        return ufe.ufe_system_apply(self.system, x)
+
+    def precondition(self, r):
+        return ufe.ufe_bddc_apply(self.bddc, r)
+
+    def solve(self, b=None, x0=None, rtol=1e-8, maxit=1000, flexible=-1, check_every=8, raise_on_error=True):
+        x = np.zeros(self.n_dof) if x0 is None else x0
+        st, info = ufe.ufe_pcg_solve(self.system, self.bddc, b, x, rtol=rtol, maxit=maxit, flexible=flexible,
+                                     check_every=check_every, raise_on_error=raise_on_error)
+        info["status"] = st
+        return x, info
+
+    def close(self):
+        if self.bddc is not None:
+            ufe.ufe_bddc_destroy(self.bddc)
+            self.bddc = None
+        if self.system is not None:
+            ufe.ufe_system_destroy(self.system)
+            self.system = None
+        if self.mesh is not None:
+            ufe.ufe_mesh_destroy(self.mesh)
+            self.mesh = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of libufe (include/ufe.h), with the C ABI's own names.
+
+Only argument marshalling happens here: numpy arrays are passed as host
+pointers (UFE_MEM_HOST), torch CUDA tensors as device pointers (UFE_MEM_DEVICE)
+on torch's current stream.  Every step of the solver runs in the CUDA library;
+if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build_ext
+
+OK = 0
+ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA = -1, -2, -3
+ERR_SINGULAR_LOCAL, ERR_SINGULAR_COARSE, ERR_BREAKDOWN = -4, -5, -6
+ERR_NO_CONVERGENCE, ERR_UNSUPPORTED, ERR_TIMEOUT = -7, -8, -9
+MEM_HOST, MEM_DEVICE = 0, 1
+CELL_EXTERNAL, CELL_CUT, CELL_INTERNAL = 0, 1, 2
+OBJ_CORNER, OBJ_EDGE, OBJ_FACE = 0, 1, 2
+WEIGHT_STIFFNESS, WEIGHT_TOPOLOGICAL = 0, 1
+OBJECTS_STANDARD, OBJECTS_VARIANT1 = 0, 1
+COARSE_C, COARSE_CE, COARSE_CEF = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+PIN_NONE, PIN_AUTO = -1, -2
+
+
+class UfeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ufe status {status}: {msg}")
+        self.status = status
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_active_cells", ctypes.c_int64),
+                ("n_cut_cells", ctypes.c_int64), ("n_dof", ctypes.c_int64), ("n_subdomains", ctypes.c_int64),
+                ("n_interface_dofs", ctypes.c_int64), ("pinned_node", ctypes.c_int64),
+                ("n_constrained", ctypes.c_int64), ("max_interior", ctypes.c_int32),
+                ("max_interface", ctypes.c_int32)]
+
+
+class BddcOpts(ctypes.Structure):
+    _fields_ = [("weighting", ctypes.c_int32), ("objects", ctypes.c_int32), ("coarse", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class BddcInfo(ctypes.Structure):
+    _fields_ = [("n_objects", ctypes.c_int64), ("n_corners", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("n_faces", ctypes.c_int64), ("n_coarse", ctypes.c_int64), ("max_local_coarse", ctypes.c_int32),
+                ("setup_ms", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("flexible", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+def _load():
+    path = build_ext.LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libufe is not built ({path}); run paper_1703_06323_gb300.build_ext.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "ufe_last_error": (ctypes.c_char_p, []),
+        "ufe_version": (ctypes.c_int, []),
+        "ufe_mesh_create": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, U32, I64, P, ctypes.POINTER(P)]),
+        "ufe_mesh_get_info": (ctypes.c_int, [P, ctypes.POINTER(MeshInfo)]),
+        "ufe_mesh_get_cell_types": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "ufe_mesh_get_dof_map": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "ufe_mesh_get_subdomains": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "ufe_mesh_get_neighbours": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "ufe_mesh_destroy": (None, [P]),
+        "ufe_assemble": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.POINTER(P)]),
+        "ufe_system_get_rhs": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "ufe_system_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "ufe_system_get_cut_data": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int]),
+        "ufe_system_destroy": (None, [P]),
+        "ufe_bddc_setup": (ctypes.c_int, [P, ctypes.POINTER(BddcOpts), ctypes.POINTER(P)]),
+        "ufe_bddc_get_info": (ctypes.c_int, [P, ctypes.POINTER(BddcInfo)]),
+        "ufe_bddc_get_objects": (ctypes.c_int, [P, P, P, P, ctypes.c_int]),
+        "ufe_bddc_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "ufe_bddc_destroy": (None, [P]),
+        "ufe_pcg_solve": (ctypes.c_int, [P, P, P, P, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                                         ctypes.POINTER(SolveInfo)]),
+        "ufe_adjoint": (ctypes.c_int, [P, P, P, P, P, P, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                                       ctypes.POINTER(SolveInfo)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+EXPORTED = ("ufe_last_error", "ufe_version", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
+            "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
+            "ufe_assemble", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
+            "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
+            "ufe_bddc_destroy", "ufe_pcg_solve", "ufe_adjoint")
+
+
+def _check(status):
+    if status != OK:
+        raise UfeError(status, LIB.ufe_last_error().decode())
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, mem, keepalive) of an array argument; None passes NULL."""
+    if a is None:
+        return None, None, None
+    if _is_torch(a):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr()), (MEM_DEVICE if a.is_cuda else MEM_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), MEM_HOST, arr
+
+
+def _mem_of(*args):
+    mems = {m for (_, m, _) in args if m is not None}
+    if len(mems) > 1:
+        raise TypeError("mix of host and device arrays in one call")
+    return mems.pop() if mems else MEM_HOST
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def ufe_version():
+    return LIB.ufe_version()
+
+
+def ufe_mesh_create(box_lo, box_hi, cells, sub_cells, phi_nodes, dirichlet_face_mask=0, pin_node=PIN_AUTO,
+                    stream=None):
+    lo = (ctypes.c_double * 3)(*box_lo)
+    hi = (ctypes.c_double * 3)(*box_hi)
+    c = (ctypes.c_int32 * 3)(*cells)
+    s = (ctypes.c_int32 * 3)(*sub_cells)
+    phi = _ptr(phi_nodes, np.float64)
+    out = ctypes.c_void_p()
+    _check(LIB.ufe_mesh_create(lo, hi, c, s, phi[0], phi[1], int(dirichlet_face_mask), int(pin_node),
+                               _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def ufe_mesh_get_info(mesh):
+    info = MeshInfo()
+    _check(LIB.ufe_mesh_get_info(mesh, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in MeshInfo._fields_}
+
+
+def _get(fn, handle, n, dtype):
+    out = np.empty(n, dtype=dtype)
+    _check(fn(handle, ctypes.c_void_p(out.ctypes.data), MEM_HOST))
+    return out
+
+
+def ufe_mesh_get_cell_types(mesh):
+    return _get(LIB.ufe_mesh_get_cell_types, mesh, ufe_mesh_get_info(mesh)["n_cells"], np.uint8)
+
+
+def ufe_mesh_get_dof_map(mesh):
+    return _get(LIB.ufe_mesh_get_dof_map, mesh, ufe_mesh_get_info(mesh)["n_nodes"], np.int32)
+
+
+def ufe_mesh_get_subdomains(mesh):
+    return _get(LIB.ufe_mesh_get_subdomains, mesh, ufe_mesh_get_info(mesh)["n_cells"], np.int32)
+
+
+def ufe_mesh_get_neighbours(mesh):
+    n = ufe_mesh_get_info(mesh)["n_dof"]
+    return _get(LIB.ufe_mesh_get_neighbours, mesh, n * 8, np.int32).reshape(n, 8)
+
+
+def ufe_mesh_destroy(mesh):
+    LIB.ufe_mesh_destroy(mesh)
+
+
+def ufe_assemble(mesh, kappa_cells=None, f_nodes=None, flux_nodes=None, dirichlet_values=None):
+    args = [_ptr(kappa_cells, np.float64), _ptr(f_nodes, np.float64), _ptr(flux_nodes, np.float64),
+            _ptr(dirichlet_values, np.float64)]
+    mem = _mem_of(*args)
+    out = ctypes.c_void_p()
+    _check(LIB.ufe_assemble(mesh, args[0][0], args[1][0], args[2][0], args[3][0], mem, ctypes.byref(out)))
+    return out
+
+
+def ufe_system_get_rhs(system, n_dof):
+    return _get(LIB.ufe_system_get_rhs, system, n_dof, np.float64)
+
+
+def ufe_system_apply(system, x, y=None):
+    xp = _ptr(x, np.float64)
+    if y is None:
+        y = np.empty(len(x), dtype=np.float64) if xp[1] == MEM_HOST else x.new_empty(x.shape)
+    yp = _ptr(y, np.float64)
+    _check(LIB.ufe_system_apply(system, xp[0], yp[0], _mem_of(xp, yp)))
+    return y
+
+
+def ufe_system_get_cut_data(system, n_cut):
+    cells = np.empty(n_cut, np.int32)
+    K = np.empty(n_cut * 64, np.float64)
+    load = np.empty(n_cut * 8, np.float64)
+    eta = np.empty(n_cut, np.float64)
+    ptrs = [ctypes.c_void_p(a.ctypes.data) for a in (cells, K, load, eta)]
+    _check(LIB.ufe_system_get_cut_data(system, *ptrs, MEM_HOST))
+    return cells, K.reshape(n_cut, 8, 8), load.reshape(n_cut, 8), eta
+
+
+def ufe_system_destroy(system):
+    LIB.ufe_system_destroy(system)
+
+
+def ufe_bddc_setup(system, weighting=WEIGHT_STIFFNESS, objects=OBJECTS_VARIANT1, coarse=COARSE_CEF,
+                   precision=PREC_FP64):
+    opts = BddcOpts(weighting, objects, coarse, precision)
+    out = ctypes.c_void_p()
+    _check(LIB.ufe_bddc_setup(system, ctypes.byref(opts), ctypes.byref(out)))
+    return out
+
+
+def ufe_bddc_get_info(bddc):
+    info = BddcInfo()
+    _check(LIB.ufe_bddc_get_info(bddc, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in BddcInfo._fields_}
+
+
+def ufe_bddc_get_objects(bddc, n_dof):
+    n_obj = ufe_bddc_get_info(bddc)["n_objects"]
+    obj = np.empty(n_dof, np.int32)
+    kind = np.empty(max(n_obj, 1), np.int32)
+    coarse = np.empty(max(n_obj, 1), np.int32)
+    _check(LIB.ufe_bddc_get_objects(bddc, ctypes.c_void_p(obj.ctypes.data), ctypes.c_void_p(kind.ctypes.data),
+                                    ctypes.c_void_p(coarse.ctypes.data), MEM_HOST))
+    return obj, kind[:n_obj], coarse[:n_obj]
+
+
+def ufe_bddc_apply(bddc, r, z=None):
+    rp = _ptr(r, np.float64)
+    if z is None:
+        z = np.empty(len(r), dtype=np.float64) if rp[1] == MEM_HOST else r.new_empty(r.shape)
+    zp = _ptr(z, np.float64)
+    _check(LIB.ufe_bddc_apply(bddc, rp[0], zp[0], _mem_of(rp, zp)))
+    return z
+
+
+def ufe_bddc_destroy(bddc):
+    LIB.ufe_bddc_destroy(bddc)
+
+
+def ufe_pcg_solve(system, bddc, b, x, rtol=1e-8, maxit=1000, flexible=-1, check_every=8, raise_on_error=True):
+    """Solve in place into x (numpy float64 or torch CUDA float64); returns (status, info dict)."""
+    bp = _ptr(b, np.float64)
+    xp = _ptr(x, np.float64)
+    mem = _mem_of(bp, xp)
+    opts = SolveOpts(float(rtol), int(maxit), int(flexible), int(check_every), 0)
+    info = SolveInfo()
+    st = LIB.ufe_pcg_solve(system, bddc, bp[0], xp[0], mem, ctypes.byref(opts), ctypes.byref(info))
+    if xp[1] == MEM_HOST and not _is_torch(x) and xp[2] is not x:
+        x[:] = xp[2]
+    if raise_on_error:
+        _check(st)
+    return st, {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+
+
+def ufe_adjoint(system, bddc, u, dJdu, lam, dJdkappa, rtol=1e-8, maxit=1000, flexible=-1, check_every=8):
+    args = [_ptr(a, np.float64) for a in (u, dJdu, lam, dJdkappa)]
+    mem = _mem_of(*args)
+    opts = SolveOpts(float(rtol), int(maxit), int(flexible), int(check_every), 0)
+    info = SolveInfo()
+    _check(LIB.ufe_adjoint(system, bddc, args[0][0], args[1][0], args[2][0], args[3][0], mem, ctypes.byref(opts),
+                           ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in SolveInfo._fields_}

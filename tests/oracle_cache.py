@@ -1,0 +1,85 @@
+"""Oracle runs shared by the GPU parity tests (computed once per test session)."""
+import functools
+
+import numpy as np
+
+from oracle.assembly import System
+from oracle.bddc import BDDC
+from oracle.integration import Integration
+from oracle.mesh import Mesh
+from oracle.pcg import pcg
+from paper_1703_06323_gb300 import inputs
+
+
+def small_problems():
+    """Small cases that span several blocks, ragged tails and the degenerate cases."""
+    isl_cells = (16, 16, 16)
+    X, Y, Z = inputs.node_coords((0, 0, 0), (1, 1, 1), isl_cells)
+    a = np.sqrt((X - 0.125) ** 2 + (Y - 0.125) ** 2 + (Z - 0.125) ** 2) - 0.04
+    b = np.sqrt((X - 0.375) ** 2 + (Y - 0.375) ** 2 + (Z - 0.125) ** 2) - 0.04
+    c = np.sqrt((X - 0.75) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) - 0.2
+    islands = inputs.Problem(name="two_pieces", box_lo=np.zeros(3), box_hi=np.ones(3), cells=isl_cells,
+                             sub_cells=(8, 8, 8), phi=np.minimum(np.minimum(a, b), c), f=np.ones_like(X),
+                             dirichlet_face_mask=0, pin_node=inputs.PIN_NONE)
+    return {
+        "sphere16": inputs.manufactured_sphere(0),
+        "sphere_ragged": inputs.sphere_problem(cells=(12, 9, 6), sub_cells=(4, 3, 3), centre=(0.52, 0.41, 0.27),
+                                               radius=0.22, box_lo=(0, 0, 0), box_hi=(1.0, 0.75, 0.5),
+                                               dirichlet_face_mask=0, pin_node=inputs.PIN_AUTO, name="ragged"),
+        "plane": inputs.plane_problem(cells=(8, 8, 8), sub_cells=(4, 4, 4), normal=(0.6, 0.8, 0.1), offset=0.61,
+                                      dirichlet_face_mask=inputs.ALL_FACES),
+        "box_dirichlet": inputs.box_problem(cells=(8, 8, 8), sub_cells=(4, 4, 4),
+                                            dirichlet_face_mask=inputs.ALL_FACES),
+        "one_subdomain": inputs.manufactured_sphere(0, n=8, sub=8, radius=0.4),
+        "slab_sliver": _slab(1e-5),
+        "two_pieces": islands,      # pure Neumann without a pin: integer parity only
+    }
+
+
+def _slab(eps):
+    h = 1.0 / 8
+    p = inputs.plane_problem(cells=(8, 8, 8), sub_cells=(4, 4, 4), normal=(1, 0, 0), offset=0.5 + eps * h,
+                             dirichlet_face_mask=inputs.FACE_XLO, linear=(0, 0, 0, 0), name="slab")
+    p.f = np.random.default_rng(0).uniform(-1, 1, p.n_nodes)
+    return p
+
+
+class OracleRun:
+    def __init__(self, p):
+        self.p = p
+        self.mesh = Mesh(p)
+        self.integ = Integration(self.mesh, p)
+        self.sys = System(self.mesh, self.integ, p)
+        self._bddc = {}
+
+    def bddc(self, weighting="stiffness", objects="v1", coarse="cef"):
+        key = (weighting, objects, coarse)
+        if key not in self._bddc:
+            self._bddc[key] = BDDC(self.mesh, self.integ, self.sys, weighting=weighting, objects=objects,
+                                   coarse=coarse)
+        return self._bddc[key]
+
+    def solve(self, rtol=1e-8, **kw):
+        B = self.bddc(**kw)
+        return pcg(self.sys.apply, self.sys.b, B.apply, rtol=rtol, maxit=2000)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(name):
+    if name == "bumpy64":
+        return OracleRun(inputs.bumpy_sphere(0))
+    return OracleRun(small_problems()[name])
+
+
+def object_ids(objs, n_dof):
+    """Object id per DOF (-1 off the interface) and kinds, in the oracle's order."""
+    ids = -np.ones(n_dof, dtype=np.int64)
+    for k, o in enumerate(objs):
+        ids[o["dofs"]] = k
+    return ids, np.array([o["kind"] for o in objs], dtype=np.int64)
+
+
+def energy_error(A, x, ref):
+    e = x - ref
+    den = float(ref @ (A @ ref))
+    return float(np.sqrt(max(e @ (A @ e), 0.0) / den)) if den > 0 else float(np.sqrt(max(e @ (A @ e), 0.0)))

@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer work is compared bit for bit; floating point to the tolerances stated
+per test (FP64: relative 1e-8 in the energy norm for solutions, rounding-level
+for element data; mixed precision: 1e-6 for solutions).
+"""
+import numpy as np
+import pytest
+
+from tests.oracle_cache import energy_error, object_ids, oracle_run, small_problems
+
+pytestmark = pytest.mark.gpu
+
+SMALL = list(small_problems().keys())
+SOLVABLE = [n for n in SMALL if n != "two_pieces"]
+
+
+@pytest.fixture(scope="module")
+def ufe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06323_gb300 import build_ext
+    build_ext.build()
+    from paper_1703_06323_gb300 import ufe as U
+    return U
+
+
+def _solver(ufe, p, **kw):
+    from paper_1703_06323_gb300.solver import Solver
+    return Solver(p, **kw)
+
+
+# ---------------------------------------------------------------------------
+# integer set-up: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", SMALL)
+def test_mesh_integers_bit_exact(ufe, name):
+    orc = oracle_run(name)
+    m = orc.mesh
+    with _solver(ufe, orc.p) as S:
+        info = S.info
+        assert info["n_dof"] == m.n_dof
+        assert info["n_subdomains"] == m.n_sub
+        assert info["pinned_node"] == m.pin
+        assert info["n_interface_dofs"] == int(m.is_gamma.sum())
+        assert info["n_cut_cells"] == int((m.cell_type == 1).sum())
+        assert np.array_equal(ufe.ufe_mesh_get_cell_types(S.mesh), m.cell_type)
+        assert np.array_equal(ufe.ufe_mesh_get_dof_map(S.mesh).astype(np.int64), m.dof_of_node)
+        assert np.array_equal(ufe.ufe_mesh_get_subdomains(S.mesh).astype(np.int64), m.sub_of_cell)
+        neigh = ufe.ufe_mesh_get_neighbours(S.mesh)
+        ref = -np.ones((m.n_dof, 8), dtype=np.int64)
+        for d, ns in enumerate(m.neigh):
+            ref[d, :len(ns)] = ns
+        assert np.array_equal(neigh.astype(np.int64), ref)
+
+
+@pytest.mark.parametrize("name", SMALL)
+@pytest.mark.parametrize("objects", ["std", "v1"])
+def test_objects_bit_exact(ufe, name, objects):
+    orc = oracle_run(name)
+    m = orc.mesh
+    objs = m.objects(objects)
+    ref_ids, ref_kinds = object_ids(objs, m.n_dof)
+    with _solver(ufe, orc.p, objects=objects, coarse="cef") as S:
+        ids, kinds, coarse = ufe.ufe_bddc_get_objects(S.bddc, m.n_dof)
+        assert np.array_equal(ids.astype(np.int64), ref_ids)
+        assert np.array_equal(kinds.astype(np.int64), ref_kinds)
+        assert np.array_equal(coarse, np.arange(len(objs)))
+    # BDDC(ce): faces carry no coarse DOF, the others are numbered in object order
+    if name == "two_pieces":
+        return
+    with _solver(ufe, orc.p, objects=objects, coarse="ce") as S:
+        _, kinds, coarse = ufe.ufe_bddc_get_objects(S.bddc, m.n_dof)
+        keep = ref_kinds != 2
+        expect = np.where(keep, np.cumsum(keep) - 1, -1)
+        assert np.array_equal(coarse.astype(np.int64), expect)
+
+
+# ---------------------------------------------------------------------------
+# integration, right-hand side, operator: rounding level
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", SOLVABLE)
+def test_cut_cell_data(ufe, name):
+    orc = oracle_run(name)
+    integ = orc.integ
+    with _solver(ufe, orc.p) as S:
+        n_cut = S.info["n_cut_cells"]
+        cells, K, load, eta = ufe.ufe_system_get_cut_data(S.system, n_cut)
+        assert np.array_equal(cells.astype(np.int64), integ.cut_cells)
+        for k in range(n_cut):
+            scale = np.abs(integ.K_cut[k]).max()
+            assert np.abs(K[k] - integ.K_cut[k]).max() <= 1e-12 * scale
+        lscale = np.abs(integ.load_cut).max() + 1e-300
+        assert np.abs(load - integ.load_cut).max() <= 1e-12 * lscale
+        assert np.abs(eta - integ.eta).max() <= 1e-13
+
+
+@pytest.mark.parametrize("name", SOLVABLE)
+def test_rhs_and_operator(ufe, name):
+    orc = oracle_run(name)
+    with _solver(ufe, orc.p) as S:
+        b = S.rhs()
+        assert np.abs(b - orc.sys.b).max() <= 1e-12 * np.abs(orc.sys.b).max()
+        x = np.random.default_rng(1).normal(size=S.n_dof)
+        y = S.apply(x)
+        ref = orc.sys.A @ x
+        assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# preconditioner and solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["sphere16", "sphere_ragged", "plane", "slab_sliver", "one_subdomain"])
+@pytest.mark.parametrize("weighting,objects,coarse", [("stiffness", "v1", "cef"), ("stiffness", "std", "ce"),
+                                                      ("topological", "std", "cef")])
+def test_preconditioner_fp64(ufe, name, weighting, objects, coarse):
+    """z = M r (Eq. bddc) for random r: energy-norm difference at FP64 rounding level."""
+    orc = oracle_run(name)
+    B = orc.bddc(weighting=weighting, objects=objects, coarse=coarse)
+    r = np.random.default_rng(2).normal(size=orc.mesh.n_dof)
+    ref = B.apply(r)
+    with _solver(ufe, orc.p, weighting=weighting, objects=objects, coarse=coarse) as S:
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["sphere16", "sphere_ragged", "slab_sliver"])
+def test_preconditioner_mixed(ufe, name):
+    """Mixed precision M r: FP32 local operators, relative energy-norm error well below 1e-3."""
+    orc = oracle_run(name)
+    B = orc.bddc()
+    r = np.random.default_rng(3).normal(size=orc.mesh.n_dof)
+    ref = B.apply(r)
+    with _solver(ufe, orc.p, precision="mixed") as S:
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("name", SOLVABLE)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pcg_solution(ufe, name, precision):
+    """Solution of PCG at rtol 1e-8 against the oracle's: energy norm 1e-8 (FP64) / 1e-6 (mixed)."""
+    orc = oracle_run(name)
+    ref = orc.solve(rtol=1e-12)
+    ref8 = orc.solve(rtol=1e-8)
+    with _solver(ufe, orc.p, precision=precision) as S:
+        x, info = S.solve(rtol=1e-8)
+    assert info["converged"] == 1
+    assert info["true_rel_residual"] <= 1e-8 * 1.5
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    # the FP64 oracle at the same rtol sets the floor for "identical": both stop at |r| < 1e-8 |b|
+    floor = energy_error(orc.sys.A, ref8["x"], ref["x"])
+    assert energy_error(orc.sys.A, x, ref["x"]) <= max(tol, 4 * floor)
+    if precision == "fp64":
+        assert abs(info["iterations"] - ref8["iterations"]) <= 1
+
+
+def test_pcg_initial_guess_and_zero_rhs(ufe):
+    orc = oracle_run("sphere16")
+    with _solver(ufe, orc.p) as S:
+        x, info = S.solve(b=np.zeros(S.n_dof), x0=np.ones(S.n_dof))
+        assert info["iterations"] == 0 and np.all(x == 0)
+        ref = orc.solve(rtol=1e-12)["x"]
+        x0 = ref.copy()
+        x, info = S.solve(x0=x0)
+        assert info["iterations"] == 0
+
+
+def test_maxit_reports_no_convergence(ufe):
+    orc = oracle_run("sphere16")
+    from paper_1703_06323_gb300 import ufe as U
+    with _solver(ufe, orc.p, weighting="topological", objects="std") as S:
+        x, info = S.solve(maxit=2, raise_on_error=False)
+        assert info["status"] == U.ERR_NO_CONVERGENCE
+        assert info["iterations"] == 2 and not info["converged"]
