@@ -27,6 +27,7 @@ namespace ufe {
 
 Bddc::~Bddc() {
   if (graph) cudaGraphExecDestroy(graph);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
   if (h_sc) cudaFreeHost(h_sc);
 }
 

@@ -79,6 +79,7 @@ struct Bddc {
   DBuf<PcgScalars> sc;
   PcgScalars* h_sc = nullptr;   // pinned mirror
   cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;   // library-owned stream used only for graph capture
   int graph_iters = 0;
   int64_t part_blocks = 0;
   double setup_ms = 0.0;

@@ -592,9 +592,8 @@ static size_t sub_smem_bytes(const Bddc& B, size_t tm_size) {
 }
 
 template <typename TM>
-static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots) {
+static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
   const Mesh& m = *B.mesh;
-  cudaStream_t s = B.stream;
   const SubMeta sm = B.meta();
   const int ns = (int)m.n_sub;
   const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
@@ -626,24 +625,23 @@ static void set_smem_limits(Bddc& B) {
   UFE_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(csm, 1)));
 }
 
-static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots) {
+static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
   if (B.mixed)
-    launch_preconditioner<float>(B, r, z, sc, with_dots);
+    launch_preconditioner<float>(B, r, z, sc, with_dots, s);
   else
-    launch_preconditioner<double>(B, r, z, sc, with_dots);
+    launch_preconditioner<double>(B, r, z, sc, with_dots, s);
 }
 
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
   set_smem_limits(B);
-  precondition(B, r_dev, z_dev, nullptr, 0);
+  precondition(B, r_dev, z_dev, nullptr, 0, B.stream);
 }
 
-static void launch_iteration(Bddc& B, const OpArgs& a) {
-  cudaStream_t s = B.stream;
+static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
   const unsigned nb = grid_for(a.n_dof, kApplyThreads);
   k_dir_apply<<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   k_update<<<nb, kApplyThreads, 0, s>>>(a.n_dof, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
-  precondition(B, B.r.p, B.z.p, B.sc.p, 1);
+  precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
 }
 
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info) {
@@ -665,7 +663,7 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
   const unsigned nb = grid_for(n, kApplyThreads);
   k_residual<<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
   UFE_CHECK_LAUNCH();
-  precondition(B, B.r.p, B.z.p, B.sc.p, 1);
+  precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
 
   const int chunk = o.check_every > 0 ? o.check_every : 8;
   if (!B.graph || B.graph_iters != chunk) {
@@ -673,10 +671,20 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
       cudaGraphExecDestroy(B.graph);
       B.graph = nullptr;
     }
+    // capture on a library-owned stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's stream
+    if (!B.cap_stream) UFE_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
     cudaGraph_t gr;
-    UFE_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk; ++i) launch_iteration(B, a);
-    UFE_CUDA(cudaStreamEndCapture(s, &gr));
+    UFE_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int i = 0; i < chunk; ++i) launch_iteration(B, a, B.cap_stream);
+    } catch (...) {
+      cudaGraph_t junk;
+      cudaStreamEndCapture(B.cap_stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+      throw;
+    }
+    UFE_CUDA(cudaStreamEndCapture(B.cap_stream, &gr));
     UFE_CUDA(cudaGraphInstantiate(&B.graph, gr, 0));
     cudaGraphDestroy(gr);
     B.graph_iters = chunk;

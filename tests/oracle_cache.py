@@ -32,8 +32,27 @@ def small_problems():
                                             dirichlet_face_mask=inputs.ALL_FACES),
         "one_subdomain": inputs.manufactured_sphere(0, n=8, sub=8, radius=0.4),
         "slab_sliver": _slab(1e-5),
-        "two_pieces": islands,      # pure Neumann without a pin: integer parity only
+        "two_pieces": islands,      # floating islands: integer parity, then SINGULAR_LOCAL
+        "u_shape": _u_shape(),      # block 0 holds two separate subdomains
     }
+
+
+def _box_phi(X, Y, Z, lo, hi):
+    c = [(a + b) / 2 for a, b in zip(lo, hi)]
+    r = [(b - a) / 2 for a, b in zip(lo, hi)]
+    return np.maximum(np.maximum(np.abs(X - c[0]) - r[0], np.abs(Y - c[1]) - r[1]), np.abs(Z - c[2]) - r[2])
+
+
+def _u_shape():
+    """Two bars in one block joined by a cross bar in the next block."""
+    cells = (16, 16, 16)
+    X, Y, Z = inputs.node_coords((0, 0, 0), (1, 1, 1), cells)
+    phi = np.minimum(np.minimum(_box_phi(X, Y, Z, (0.1, 0.1, 0.1), (0.8, 0.2, 0.3)),
+                                _box_phi(X, Y, Z, (0.1, 0.35, 0.1), (0.8, 0.45, 0.3))),
+                     _box_phi(X, Y, Z, (0.6, 0.1, 0.1), (0.8, 0.45, 0.3)))
+    f = np.random.default_rng(5).uniform(-1, 1, X.size)
+    return inputs.Problem(name="u_shape", box_lo=np.zeros(3), box_hi=np.ones(3), cells=cells, sub_cells=(8, 8, 8),
+                          phi=phi, f=f, dirichlet_face_mask=0, pin_node=inputs.PIN_AUTO)
 
 
 def _slab(eps):

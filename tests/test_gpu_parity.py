@@ -13,6 +13,7 @@ pytestmark = pytest.mark.gpu
 
 SMALL = list(small_problems().keys())
 SOLVABLE = [n for n in SMALL if n != "two_pieces"]
+MESH_ONLY = {"two_pieces"}
 
 
 @pytest.fixture(scope="module")
@@ -31,6 +32,21 @@ def _solver(ufe, p, **kw):
     return Solver(p, **kw)
 
 
+def _oracle_bddc_or_none(orc, **kw):
+    """The oracle's preconditioner, or None when the oracle refuses it as singular."""
+    from oracle.bddc import SingularLocal
+    try:
+        return orc.bddc(**kw)
+    except SingularLocal:
+        return None
+
+
+def _expect_singular(ufe, p, **kw):
+    with pytest.raises(ufe.UfeError) as e:
+        _solver(ufe, p, **kw)
+    assert e.value.status == ufe.ERR_SINGULAR_LOCAL
+
+
 # ---------------------------------------------------------------------------
 # integer set-up: bit-exact
 # ---------------------------------------------------------------------------
@@ -38,24 +54,39 @@ def _solver(ufe, p, **kw):
 def test_mesh_integers_bit_exact(ufe, name):
     orc = oracle_run(name)
     m = orc.mesh
-    with _solver(ufe, orc.p) as S:
-        info = S.info
+    p = orc.p
+    mesh = ufe.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, p.phi, p.dirichlet_face_mask, p.pin_node)
+    try:
+        info = ufe.ufe_mesh_get_info(mesh)
         assert info["n_dof"] == m.n_dof
         assert info["n_subdomains"] == m.n_sub
         assert info["pinned_node"] == m.pin
         assert info["n_interface_dofs"] == int(m.is_gamma.sum())
         assert info["n_cut_cells"] == int((m.cell_type == 1).sum())
-        assert np.array_equal(ufe.ufe_mesh_get_cell_types(S.mesh), m.cell_type)
-        assert np.array_equal(ufe.ufe_mesh_get_dof_map(S.mesh).astype(np.int64), m.dof_of_node)
-        assert np.array_equal(ufe.ufe_mesh_get_subdomains(S.mesh).astype(np.int64), m.sub_of_cell)
-        neigh = ufe.ufe_mesh_get_neighbours(S.mesh)
+        assert np.array_equal(ufe.ufe_mesh_get_cell_types(mesh), m.cell_type)
+        assert np.array_equal(ufe.ufe_mesh_get_dof_map(mesh).astype(np.int64), m.dof_of_node)
+        assert np.array_equal(ufe.ufe_mesh_get_subdomains(mesh).astype(np.int64), m.sub_of_cell)
+        neigh = ufe.ufe_mesh_get_neighbours(mesh)
         ref = -np.ones((m.n_dof, 8), dtype=np.int64)
         for d, ns in enumerate(m.neigh):
             ref[d, :len(ns)] = ns
         assert np.array_equal(neigh.astype(np.int64), ref)
+    finally:
+        ufe.ufe_mesh_destroy(mesh)
 
 
-@pytest.mark.parametrize("name", SMALL)
+def test_floating_subdomain_without_coarse_dof_is_singular(ufe):
+    """Islands with no interface and no constrained node: the oracle and the library refuse them."""
+    from oracle.bddc import SingularLocal
+    orc = oracle_run("two_pieces")
+    with pytest.raises(SingularLocal):
+        orc.bddc()
+    with pytest.raises(ufe.UfeError) as e:
+        _solver(ufe, orc.p)
+    assert e.value.status == ufe.ERR_SINGULAR_LOCAL
+
+
+@pytest.mark.parametrize("name", SOLVABLE)
 @pytest.mark.parametrize("objects", ["std", "v1"])
 def test_objects_bit_exact(ufe, name, objects):
     orc = oracle_run(name)
@@ -68,7 +99,10 @@ def test_objects_bit_exact(ufe, name, objects):
         assert np.array_equal(kinds.astype(np.int64), ref_kinds)
         assert np.array_equal(coarse, np.arange(len(objs)))
     # BDDC(ce): faces carry no coarse DOF, the others are numbered in object order
-    if name == "two_pieces":
+    if name == "one_subdomain":
+        return
+    if _oracle_bddc_or_none(orc, objects=objects, coarse="ce") is None:
+        _expect_singular(ufe, orc.p, objects=objects, coarse="ce")
         return
     with _solver(ufe, orc.p, objects=objects, coarse="ce") as S:
         _, kinds, coarse = ufe.ufe_bddc_get_objects(S.bddc, m.n_dof)
@@ -91,9 +125,10 @@ def test_cut_cell_data(ufe, name):
         for k in range(n_cut):
             scale = np.abs(integ.K_cut[k]).max()
             assert np.abs(K[k] - integ.K_cut[k]).max() <= 1e-12 * scale
-        lscale = np.abs(integ.load_cut).max() + 1e-300
-        assert np.abs(load - integ.load_cut).max() <= 1e-12 * lscale
-        assert np.abs(eta - integ.eta).max() <= 1e-13
+        if n_cut:
+            lscale = np.abs(integ.load_cut).max() + 1e-300
+            assert np.abs(load - integ.load_cut).max() <= 1e-12 * lscale
+            assert np.abs(eta - integ.eta).max() <= 1e-13
 
 
 @pytest.mark.parametrize("name", SOLVABLE)
@@ -111,13 +146,16 @@ def test_rhs_and_operator(ufe, name):
 # ---------------------------------------------------------------------------
 # preconditioner and solve
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["sphere16", "sphere_ragged", "plane", "slab_sliver", "one_subdomain"])
+@pytest.mark.parametrize("name", ["sphere16", "sphere_ragged", "plane", "slab_sliver", "one_subdomain", "u_shape"])
 @pytest.mark.parametrize("weighting,objects,coarse", [("stiffness", "v1", "cef"), ("stiffness", "std", "ce"),
                                                       ("topological", "std", "cef")])
 def test_preconditioner_fp64(ufe, name, weighting, objects, coarse):
     """z = M r (Eq. bddc) for random r: energy-norm difference at FP64 rounding level."""
     orc = oracle_run(name)
-    B = orc.bddc(weighting=weighting, objects=objects, coarse=coarse)
+    B = _oracle_bddc_or_none(orc, weighting=weighting, objects=objects, coarse=coarse)
+    if B is None:
+        _expect_singular(ufe, orc.p, weighting=weighting, objects=objects, coarse=coarse)
+        return
     r = np.random.default_rng(2).normal(size=orc.mesh.n_dof)
     ref = B.apply(r)
     with _solver(ufe, orc.p, weighting=weighting, objects=objects, coarse=coarse) as S:
