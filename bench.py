@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""BDDC-PCG time-to-solution on one GB300.
+
+Workload: Poisson on the 64^3-cell bumpy sphere (6 seeded bumps, sub-cell
+shift forcing cut fractions down to ~1e-6), 8^3-cell subdomain blocks, random
+nodal source, Neumann on the cut boundary, stiffness weighting, variant-1
+coarse objects, BDDC(cef), PCG to |r| < 1e-8 |b|.
+
+One step = one complete solve from the device-resident nodal level set and
+source: ufe_mesh_create -> ufe_assemble -> ufe_bddc_setup -> ufe_pcg_solve.
+`value` is the mean time-to-solution per problem in mixed precision; the FP64
+form of the same step is reported beside it.  L2 is flushed between steps.
+
+Under torchrun each rank solves its own seeded replica (no collective on the
+data path): weak scaling, value = max-over-ranks step time / problems per step.
+
+--impl reference times the FP64 CPU oracle (the comparison implementation of
+this project) on the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BDDC-PCG time-to-solution (s) and DOF-iters/s at rtol 1e-8, mixed vs FP64 on 1 GB300"
+RTOL = 1e-8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (the CPU baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_time_to_solution(seed, solves=1):
+    """Time the FP64 oracle on the full workload: every set-up phase once, then
+    `solves` PCG solves.  Returns phase times (s), iterations and DOFs."""
+    from oracle.assembly import System
+    from oracle.bddc import BDDC
+    from oracle.integration import Integration
+    from oracle.mesh import Mesh
+    from oracle.pcg import pcg
+    from paper_1703_06323_gb300 import inputs
+
+    p = inputs.bumpy_sphere(seed)
+    t = {}
+    t0 = time.perf_counter()
+    m = Mesh(p)
+    m.objects("v1")
+    t["mesh"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    integ = Integration(m, p)
+    t["integration"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sysm = System(m, integ, p)
+    t["assembly"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    B = BDDC(m, integ, sysm, weighting="stiffness", objects="v1", coarse="cef")
+    t["bddc_setup"] = time.perf_counter() - t0
+    solve_times, its = [], 0
+    for _ in range(solves):
+        t0 = time.perf_counter()
+        res = pcg(sysm.apply, sysm.b, B.apply, rtol=RTOL, maxit=2000)
+        solve_times.append(time.perf_counter() - t0)
+        its = res["iterations"]
+    return {"phases": t, "solve_times": solve_times, "iterations": its, "n_dof": int(m.n_dof)}
+
+
+def _oracle_worker_entry(seed, solves, out_path):
+    res = oracle_time_to_solution(seed, solves)
+    with open(out_path, "w") as fh:
+        json.dump(res, fh)
+
+
+def spawn_oracle(seed, solves, out_path):
+    """Run the oracle in a spawned single-threaded process (BLAS pinned to 1 thread)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", f"{seed}:{solves}:{out_path}"]
+    return subprocess.Popen(cmd, env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    out = os.path.join("/tmp", f"ufe_oracle_ref_{os.getpid()}.json")
+    solves = args.warmup + args.steps
+    proc = spawn_oracle(args.seed, solves, out)
+    _, err = proc.communicate()
+    if proc.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle failed: {err.decode()[-300:]}"}))
+        return
+    r = json.load(open(out))
+    setup = sum(r["phases"].values())
+    timed = r["solve_times"][args.warmup:]
+    per_step = setup + statistics.mean(timed)
+    sample = ("full workload; set-up phases timed once, then warmup+steps PCG solves; "
+              "value = set-up + mean timed solve")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "bumpy_sphere_64^3_cells_8^3_blocks", "rtol": RTOL, "weighting": "stiffness",
+                   "objects": "v1", "coarse": "cef", "precision": "fp64"},
+        "iterations": r["iterations"], "phases_s": r["phases"],
+        "cpu_baseline": {"value": per_step, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": per_step, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1703_06323_gb300 import build_ext, inputs
+    build_ext.build()
+    from paper_1703_06323_gb300 import ufe as U
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    oracle_proc, oracle_out = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle_out = os.path.join("/tmp", f"ufe_oracle_cpu_{os.getpid()}.json")
+        oracle_proc = spawn_oracle(args.seed, 1, oracle_out)
+
+    p = inputs.bumpy_sphere(args.seed + rank)
+    phi_d = torch.from_numpy(p.phi).to(dev)
+    f_d = torch.from_numpy(p.f).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step(precision, host=False):
+        if host:
+            phi, f = p.phi, p.f
+        else:
+            phi, f = phi_d, f_d
+        mesh = U.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, phi, p.dirichlet_face_mask, p.pin_node,
+                                 stream=stream.cuda_stream)
+        sysh = bddc = None
+        try:
+            n = U.ufe_mesh_get_info(mesh)["n_dof"]
+            sysh = U.ufe_assemble(mesh, None, f, None, None)
+            bddc = U.ufe_bddc_setup(sysh, U.WEIGHT_STIFFNESS, U.OBJECTS_VARIANT1, U.COARSE_CEF,
+                                    U.PREC_MIXED if precision == "mixed" else U.PREC_FP64)
+            x = np.zeros(n) if host else torch.zeros(n, dtype=torch.float64, device=dev)
+            _, info = U.ufe_pcg_solve(sysh, bddc, None, x, rtol=RTOL, maxit=1000)
+            binfo = U.ufe_bddc_get_info(bddc)
+        finally:
+            if bddc is not None:
+                U.ufe_bddc_destroy(bddc)
+            if sysh is not None:
+                U.ufe_system_destroy(sysh)
+            U.ufe_mesh_destroy(mesh)
+        return n, info, binfo, x
+
+    def timed(precision, k, launches=False):
+        times, infos = [], []
+        l0 = U.ufe_kernel_launches()
+        for _ in range(k):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            n, info, binfo, _ = step(precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append((n, info, binfo))
+        nl = U.ufe_kernel_launches() - l0
+        return times, infos, nl
+
+    for _ in range(args.warmup):
+        step("mixed")
+        step("fp64")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t_mixed, i_mixed, launches = timed("mixed", args.steps)
+    clk_stats = clk.stop()
+    t_fp64, i_fp64, _ = timed("fp64", args.fp64_steps)
+    if world > 1:
+        torch.distributed.barrier()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n, info, _, x_host = step("mixed", host=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+
+    mean_mixed = statistics.mean(t_mixed)
+    mean_fp64 = statistics.mean(t_fp64)
+    if world > 1:
+        tt = torch.tensor([mean_mixed, mean_fp64, statistics.mean(e2e_times)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        mean_mixed, mean_fp64, e2e_mean = (float(v) for v in tt)
+    else:
+        e2e_mean = statistics.mean(e2e_times)
+    if rank != 0:
+        return
+
+    n, info, binfo = i_mixed[-1]
+    its = info["iterations"]
+    solve_s = statistics.mean(i[1]["solve_ms"] for i in i_mixed) / 1e3
+    setup_s = statistics.mean(i[2]["setup_ms"] for i in i_mixed) / 1e3
+    n64, info64, binfo64 = i_fp64[-1]
+
+    line = {
+        "metric": METRIC,
+        "value": mean_mixed / world,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": mean_mixed * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "bumpy_sphere_64^3_cells_8^3_blocks", "rtol": RTOL, "precision": "mixed",
+                   "weighting": "stiffness", "objects": "v1", "coarse": "cef", "n_dof": n,
+                   "problems_per_step": world, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iterations": its,
+        "dof_iters_per_s": n * its / (mean_mixed),
+        "solve_dof_iters_per_s": n * its / solve_s if solve_s > 0 else None,
+        "setup_s_device": setup_s,
+        "solve_s_device": solve_s,
+        "n_coarse": binfo["n_coarse"],
+        "fp64": {"value": mean_fp64 / world, "unit": "s", "iterations": info64["iterations"],
+                 "dof_iters_per_s": n64 * info64["iterations"] / mean_fp64,
+                 "true_rel_residual": info64["true_rel_residual"]},
+        "true_rel_residual": info["true_rel_residual"],
+        "gpu_launches": launches,
+        "clocks": clk_stats,
+        "e2e": {"value": e2e_mean / world, "unit": "s",
+                "h2d_bytes_per_step": int(p.phi.nbytes + p.f.nbytes + 8 * n),
+                "d2h_bytes_per_step": int(8 * n)},
+    }
+    if oracle_proc is not None:
+        _, err = oracle_proc.communicate()
+        if oracle_proc.returncode == 0:
+            r = json.load(open(oracle_out))
+            total = sum(r["phases"].values()) + r["solve_times"][0]
+            line["cpu_baseline"] = {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": "one complete time-to-solution of the same workload (seed "
+                                              f"{args.seed}), BLAS pinned to 1 thread",
+                                    "phases_s": r["phases"], "iterations": r["iterations"]}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": f"oracle failed: {err.decode()[-200:]}"}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.oracle_worker:
+        seed, solves, out = args.oracle_worker.split(":", 2)
+        _oracle_worker_entry(int(seed), int(solves), out)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

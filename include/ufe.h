@@ -89,6 +89,11 @@ const char* ufe_last_error(void);
 /* ABI version of this header (major * 100 + minor). */
 int ufe_version(void);
 
+/* Number of library kernels launched by this process so far (every kernel node
+ * of a launched CUDA graph counts once).  Instrumentation only; no paper
+ * counterpart. */
+int64_t ufe_kernel_launches(void);
+
 typedef struct {
   int64_t n_nodes, n_cells;
   int64_t n_active_cells, n_cut_cells;

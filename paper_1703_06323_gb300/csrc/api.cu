@@ -13,6 +13,15 @@ struct ufe_bddc : ufe::Bddc {};
 namespace ufe {
 
 static thread_local std::string g_last_error;
+std::atomic<long long> g_kernel_launches{0};
+thread_local long long* g_capture_counter = nullptr;
+
+void note_launch() {
+  if (g_capture_counter)
+    ++*g_capture_counter;
+  else
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -70,6 +79,8 @@ extern "C" {
 const char* ufe_last_error(void) { return g_last_error.c_str(); }
 
 int ufe_version(void) { return 100; }
+
+int64_t ufe_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
 
 ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const int32_t cells[3],
                            const int32_t sub_cells[3], const double* phi_nodes, int mem, uint32_t dirichlet_face_mask,

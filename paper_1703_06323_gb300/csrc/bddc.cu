@@ -512,11 +512,12 @@ static void propagate(const Mesh& m, const Bddc& B, const uint8_t* active, int m
   changed.alloc(1, s);
   for (int round = 0; round < 512; ++round) {
     changed.zero();
-    for (int rep = 0; rep < 4; ++rep)
+    for (int rep = 0; rep < 4; ++rep) {
       k_obj_propagate<<<grid_for(m.n_dof, 256), 256, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p,
                                                              m.cell_type.p, m.neigh.p, m.n_neigh.p, m.phi.p, std_obj,
                                                              active, mode, label, changed.p);
-    UFE_CHECK_LAUNCH();
+      UFE_CHECK_LAUNCH();
+    }
     if (scalar_to_host(changed.p, s) == 0) return;
   }
   throw Error{UFE_ERR_TIMEOUT, "object labelling did not converge"};
@@ -555,7 +556,9 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   IG.alloc(std::max<int64_t>(nIG, 1), s);
   GG.alloc(std::max<int64_t>(nGG, 1), s);
   k_scale_block<T><<<ns, 256, 0, s>>>(AII.p, II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p);
+  UFE_CHECK_LAUNCH();
   k_scale_block<T><<<ns, 256, 0, s>>>(AIG.p, IG.p, dIG->p, m.I_ptr.p, m.G_ptr.p, sI.p, sG.p);
+  UFE_CHECK_LAUNCH();
   k_scale_block<T><<<ns, 256, 0, s>>>(AGG.p, GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p);
   UFE_CHECK_LAUNCH();
   Cs.alloc(std::max<int64_t>(nCG, 1), s);
@@ -627,9 +630,12 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   // 10. A_c^w = S_c^-1 - rho (FP64)
   Acw.alloc(std::max<int64_t>(nCC, 1), s);
   k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
+  UFE_CHECK_LAUNCH();
   // 11. unscale the operators used at every iteration
   k_unscale<T><<<ns, 256, 0, s>>>(II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p, 0);
+  UFE_CHECK_LAUNCH();
   k_unscale<T><<<ns, 256, 0, s>>>(GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p, 0);
+  UFE_CHECK_LAUNCH();
   k_unscale<T><<<ns, 256, 0, s>>>(GC.p, B.off_GC.p, m.G_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
   UFE_CHECK_LAUNCH();
   std::vector<int> st = to_host(status.p, ns, s);
@@ -661,6 +667,7 @@ void bddc_build(Bddc& B) {
   DBuf<int32_t> rep_index;
   rep_index.alloc(nd, s);
   k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label.p, flags.p);
+  UFE_CHECK_LAUNCH();
   int64_t n_obj = scan_flags(flags.p, nd, rep_index.p, s);
   B.obj_of_dof.alloc(nd, s);
   B.obj_size.alloc(std::max<int64_t>(n_obj, 1), s);
@@ -668,10 +675,12 @@ void bddc_build(Bddc& B) {
   B.obj_kind.alloc(std::max<int64_t>(n_obj, 1), s);
   B.obj_size.zero();
   k_obj_assign<<<grid_for(nd, T), T, 0, s>>>(nd, label.p, rep_index.p, B.obj_of_dof.p, B.obj_size.p, B.obj_rep.p);
-  if (n_obj)
+  UFE_CHECK_LAUNCH();
+  if (n_obj) {
     k_obj_kind<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.obj_rep.p, B.obj_size.p, m.n_neigh.p, nullptr, nullptr,
                                                 nullptr, B.obj_kind.p);
-  UFE_CHECK_LAUNCH();
+    UFE_CHECK_LAUNCH();
+  }
 
   // ---- variant 1 (Sect. 4.4): split the edge objects at their cut FE edges
   if (B.opts.objects == UFE_OBJECTS_VARIANT1 && n_obj) {
@@ -684,6 +693,7 @@ void bddc_build(Bddc& B) {
     UFE_CHECK_LAUNCH();
     propagate(m, B, active.p, 1, B.obj_of_dof.p, label2.p);
     k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label2.p, flags.p);
+    UFE_CHECK_LAUNCH();
     const int64_t n_obj2 = scan_flags(flags.p, nd, rep_index.p, s);
     DBuf<int32_t> obj2, size2, rep2, kind2;
     obj2.alloc(nd, s);
@@ -692,6 +702,7 @@ void bddc_build(Bddc& B) {
     kind2.alloc(n_obj2, s);
     size2.zero();
     k_obj_assign<<<grid_for(nd, T), T, 0, s>>>(nd, label2.p, rep_index.p, obj2.p, size2.p, rep2.p);
+    UFE_CHECK_LAUNCH();
     k_obj_kind<<<grid_for(n_obj2, T), T, 0, s>>>(n_obj2, rep2.p, size2.p, m.n_neigh.p, B.obj_of_dof.p, B.obj_kind.p,
                                                  corner.p, kind2.p);
     UFE_CHECK_LAUNCH();
@@ -730,10 +741,11 @@ void bddc_build(Bddc& B) {
   DBuf<int32_t> nC;
   nC.alloc(ns, s);
   nC.zero();
-  if (n_obj)
+  if (n_obj) {
     k_coarse_list<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.coarse_of_obj.p, B.obj_rep.p, m.n_neigh.p, B.coarse_obj.p,
                                                    B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, nC.p);
-  UFE_CHECK_LAUNCH();
+    UFE_CHECK_LAUNCH();
+  }
   B.C_ptr.alloc(ns + 1, s);
   B.n_Cloc = scan_counts(nC.p, ns, B.C_ptr.p, s);
   B.C_list.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
@@ -741,6 +753,7 @@ void bddc_build(Bddc& B) {
   B.cpos.fill_bytes(0xff);
   if (nco) {
     k_sub_coarse_fill<<<ns, 256, 0, s>>>(nco, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.C_ptr.p, B.C_list.p);
+    UFE_CHECK_LAUNCH();
     k_cpos<<<ns, 256, 0, s>>>(B.C_ptr.p, B.C_list.p, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p);
     UFE_CHECK_LAUNCH();
   }
@@ -805,7 +818,9 @@ void bddc_build(Bddc& B) {
   dGraw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
   const SubMeta sm = B.meta();
   k_local_assemble<<<ns, 256, 0, s>>>(sm, B.off_II.p, doIG.p, B.off_GG.p, AII.p, AIG.p, AGG.p);
+  UFE_CHECK_LAUNCH();
   k_local_diag<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p, dGraw.p);
+  UFE_CHECK_LAUNCH();
   B.w.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
   k_weights<<<grid_for(nd, T), T, 0, s>>>(nd, m.n_neigh.p, m.gpos.p, dGraw.p,
                                           B.opts.weighting == UFE_WEIGHT_TOPOLOGICAL, B.w.p);
@@ -832,6 +847,7 @@ void bddc_build(Bddc& B) {
     upload(dCC, oCC);
     k_coarse_assemble<<<(unsigned)nco, 128, 0, s>>>(nco, B.ldc, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p,
                                                     B.C_ptr.p, B.C_list.p, dCC.p, Acw.p, B.Ac_inv.p);
+    UFE_CHECK_LAUNCH();
     k_symmetrize<<<grid_for(nco * nco, T), T, 0, s>>>(B.Ac_inv.p, (int)nco, B.ldc);
     UFE_CHECK_LAUNCH();
     DBuf<int> st;

@@ -81,6 +81,7 @@ struct Bddc {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;   // library-owned stream used only for graph capture
   int graph_iters = 0;
+  long long graph_kernels = 0;         // kernel nodes in the captured chunk
   int64_t part_blocks = 0;
   double setup_ms = 0.0;
 

@@ -91,15 +91,22 @@ void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, 
   dd.alloc(descs.size(), s);
   UFE_CUDA(cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s));
   dim3 grid(max_tiles, (unsigned)descs.size());
-  if (!transA && !transB)
+  if (!transA && !transB) {
     k_batched_gemm<T, false, false><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-  else if (transA && !transB)
+    UFE_CHECK_LAUNCH();
+  }
+  else if (transA && !transB) {
     k_batched_gemm<T, true, false><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-  else if (!transA && transB)
+    UFE_CHECK_LAUNCH();
+  }
+  else if (!transA && transB) {
     k_batched_gemm<T, false, true><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-  else
+    UFE_CHECK_LAUNCH();
+  }
+  else {
     k_batched_gemm<T, true, true><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-  UFE_CHECK_LAUNCH();
+    UFE_CHECK_LAUNCH();
+  }
   // the descriptor buffer is released stream-ordered after the kernel
 }
 
@@ -318,8 +325,11 @@ void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s) {
   for (int k0 = 0; k0 < n; k0 += kNB) {
     const int kb = std::min(kNB, n - k0);
     k_large_diag<T><<<1, 256, 0, s>>>(A, ld, k0, kb, Dg.p, status);
+    UFE_CHECK_LAUNCH();
     k_large_row_panel<T><<<panel_grid, 256, 0, s>>>(A, ld, n, k0, kb, Dg.p);
+    UFE_CHECK_LAUNCH();
     k_large_update<T><<<upd_grid, kGemmThreads, 0, s>>>(A, ld, n, k0, kb);
+    UFE_CHECK_LAUNCH();
     k_large_col_panel<T><<<panel_grid, 256, 0, s>>>(A, ld, n, k0, kb, Dg.p);
     UFE_CHECK_LAUNCH();
   }

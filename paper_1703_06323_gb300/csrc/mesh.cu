@@ -492,6 +492,7 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
   cnt.alloc(2, s);
   cnt.zero();
   k_count_flag<<<grid_for(nn, T), T, 0, s>>>(nn, m.node_flags.p, 2, cnt.p);
+  UFE_CHECK_LAUNCH();
   k_count_flag<<<grid_for(nc, T), T, 0, s>>>(nc, m.cell_type.p, 0xff, cnt.p + 1);
   UFE_CHECK_LAUNCH();
   std::vector<unsigned long long> hc = to_host(cnt.p, 2, s);
@@ -509,6 +510,7 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
       bidx.alloc(nb, s);
       res.alloc(1, s);
       k_argmin_candidates<<<nb, 256, 0, s>>>(nn, phi_dev, m.node_flags.p, bv.p, bidx.p);
+      UFE_CHECK_LAUNCH();
       k_argmin_final<<<1, 32, 0, s>>>(nb, bv.p, bidx.p, res.p);
       UFE_CHECK_LAUNCH();
       m.pin = scalar_to_host(res.p, s);
@@ -562,6 +564,7 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
   UFE_REQUIRE(m.n_sub > 0, UFE_ERR_INVALID_ARG, "no active cell");
   m.sub_of_cell.alloc(nc, s);
   k_sub_of_cell<<<grid_for(nc, T), T, 0, s>>>(g, comp_rank.p, sub_base.p, m.sub_of_cell.p);
+  UFE_CHECK_LAUNCH();
   m.sub_block.alloc(m.n_sub, s);
   k_sub_block<<<grid_for(nblocks, T), T, 0, s>>>(nblocks, sub_base.p, m.sub_block.p);
   UFE_CHECK_LAUNCH();
@@ -588,6 +591,7 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
   m.G_list.alloc(m.n_Gloc > 0 ? m.n_Gloc : 1, s);
   k_local_fill<<<(unsigned)m.n_sub, 256, 0, s>>>(g, m.sub_block.p, m.dof_of_node.p, m.lmap.p, m.I_ptr.p, m.G_ptr.p,
                                                   m.I_list.p, m.G_list.p);
+  UFE_CHECK_LAUNCH();
   m.gpos.alloc(m.n_dof * 8, s);
   m.gpos.fill_bytes(0xff);
   k_gpos<<<(unsigned)m.n_sub, 256, 0, s>>>(m.G_ptr.p, m.G_list.p, m.neigh.p, m.n_neigh.p, m.gpos.p);

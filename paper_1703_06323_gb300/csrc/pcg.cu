@@ -602,11 +602,14 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
   k_prec_interior1<TM><<<ns, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, ldI, ldG);
+  UFE_CHECK_LAUNCH();
   k_prec_neumann<TM><<<ns, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, ldI, ldG);
+  UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
     const size_t csm = (size_t)B.ldc * 8;
     const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
     k_coarse_solve<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, B.gC.p, B.uc.p, sc);
+    UFE_CHECK_LAUNCH();
   }
   k_prec_final<TM><<<ns, kSubThreads, smem, s>>>(sm, II, GC, r, B.vw.p, B.uc.p, z, B.part.p, sc, ldI, ldG, with_dots);
   UFE_CHECK_LAUNCH();
@@ -640,7 +643,9 @@ void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
 static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
   const unsigned nb = grid_for(a.n_dof, kApplyThreads);
   k_dir_apply<<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  UFE_CHECK_LAUNCH();
   k_update<<<nb, kApplyThreads, 0, s>>>(a.n_dof, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  UFE_CHECK_LAUNCH();
   precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
 }
 
@@ -676,14 +681,19 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
     if (!B.cap_stream) UFE_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
     cudaGraph_t gr;
     UFE_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+    long long captured = 0;
+    g_capture_counter = &captured;
     try {
       for (int i = 0; i < chunk; ++i) launch_iteration(B, a, B.cap_stream);
     } catch (...) {
+      g_capture_counter = nullptr;
       cudaGraph_t junk;
       cudaStreamEndCapture(B.cap_stream, &junk);
       if (junk) cudaGraphDestroy(junk);
       throw;
     }
+    g_capture_counter = nullptr;
+    B.graph_kernels = captured;
     UFE_CUDA(cudaStreamEndCapture(B.cap_stream, &gr));
     UFE_CUDA(cudaGraphInstantiate(&B.graph, gr, 0));
     cudaGraphDestroy(gr);
@@ -696,6 +706,7 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
     UFE_CUDA(cudaStreamSynchronize(s));
     if (B.h_sc->done || B.h_sc->iter >= init.maxit) break;
     UFE_CUDA(cudaGraphLaunch(B.graph, s));
+    g_kernel_launches.fetch_add(B.graph_kernels, std::memory_order_relaxed);
   }
   UFE_CUDA(cudaMemcpyAsync(B.h_sc, B.sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   UFE_CUDA(cudaEventRecord(e1, s));

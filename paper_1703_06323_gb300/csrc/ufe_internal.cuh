@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -28,7 +29,15 @@ struct Error {
       throw ::ufe::Error{UFE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)}; \
   } while (0)
 
-#define UFE_CHECK_LAUNCH() UFE_CUDA(cudaGetLastError())
+// kernel launch accounting: launches issued directly count at once; launches
+// recorded into a graph count once per graph launch (see pcg.cu)
+void note_launch();
+
+#define UFE_CHECK_LAUNCH()         \
+  do {                             \
+    UFE_CUDA(cudaGetLastError());  \
+    ::ufe::note_launch();          \
+  } while (0)
 
 #define UFE_REQUIRE(cond, code, msg)                     \
   do {                                                   \
@@ -186,5 +195,9 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
 
 // constant tables (Q1 reference matrices, quadrature) uploaded once
 void ensure_constants();
+
+// launch accounting state
+extern std::atomic<long long> g_kernel_launches;
+extern thread_local long long* g_capture_counter;   // non-null while a graph is being captured
 
 }  // namespace ufe

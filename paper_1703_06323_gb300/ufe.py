@@ -72,6 +72,7 @@ def _load():
     sig = {
         "ufe_last_error": (ctypes.c_char_p, []),
         "ufe_version": (ctypes.c_int, []),
+        "ufe_kernel_launches": (ctypes.c_int64, []),
         "ufe_mesh_create": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, U32, I64, P, ctypes.POINTER(P)]),
         "ufe_mesh_get_info": (ctypes.c_int, [P, ctypes.POINTER(MeshInfo)]),
         "ufe_mesh_get_cell_types": (ctypes.c_int, [P, P, ctypes.c_int]),
@@ -102,7 +103,7 @@ def _load():
 
 
 LIB = _load()
-EXPORTED = ("ufe_last_error", "ufe_version", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
+EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
             "ufe_assemble", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
@@ -153,6 +154,10 @@ def _stream(stream):
 
 def ufe_version():
     return LIB.ufe_version()
+
+
+def ufe_kernel_launches():
+    return LIB.ufe_kernel_launches()
 
 
 def ufe_mesh_create(box_lo, box_hi, cells, sub_cells, phi_nodes, dirichlet_face_mask=0, pin_node=PIN_AUTO,
