@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -252,7 +253,8 @@ def run_ours(args, rank, world):
 
     for _ in range(args.warmup):
         step("mixed")
-        step("fp64")
+        if args.fp64_steps > 0:
+            step("fp64")
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -260,13 +262,13 @@ def run_ours(args, rank, world):
     clk.start()
     t_mixed, i_mixed, launches = timed("mixed", args.steps)
     clk_stats = clk.stop()
-    t_fp64, i_fp64, _ = timed("fp64", args.fp64_steps)
+    t_fp64, i_fp64, _ = timed("fp64", args.fp64_steps) if args.fp64_steps > 0 else ([float("nan")], [None], 0)
     if world > 1:
         torch.distributed.barrier()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 5))):
+    for _ in range(max(0, min(args.steps, args.e2e_steps))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -281,7 +283,7 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         mean_mixed, mean_fp64, e2e_mean = (float(v) for v in tt)
     else:
-        e2e_mean = statistics.mean(e2e_times)
+        e2e_mean = statistics.mean(e2e_times) if e2e_times else float("nan")
     if rank != 0:
         return
 
@@ -289,7 +291,10 @@ def run_ours(args, rank, world):
     its = info["iterations"]
     solve_s = statistics.mean(i[1]["solve_ms"] for i in i_mixed) / 1e3
     setup_s = statistics.mean(i[2]["setup_ms"] for i in i_mixed) / 1e3
-    n64, info64, binfo64 = i_fp64[-1]
+    if i_fp64[-1] is not None:
+        n64, info64, binfo64 = i_fp64[-1]
+    else:
+        n64, info64 = n, {"iterations": 0, "true_rel_residual": None}
 
     line = {
         "metric": METRIC,
@@ -315,7 +320,7 @@ def run_ours(args, rank, world):
         "solve_s_device": solve_s,
         "n_coarse": binfo["n_coarse"],
         "fp64": {"value": mean_fp64 / world, "unit": "s", "iterations": info64["iterations"],
-                 "dof_iters_per_s": n64 * info64["iterations"] / mean_fp64,
+                 "dof_iters_per_s": n64 * info64["iterations"] / mean_fp64 if mean_fp64 == mean_fp64 else None,
                  "true_rel_residual": info64["true_rel_residual"]},
         "true_rel_residual": info["true_rel_residual"],
         "gpu_launches": launches,

@@ -57,6 +57,10 @@ SubMeta Bddc::meta() const {
   s.off_GG = off_GG.p;
   s.off_GC = off_GC.p;
   s.w = w.p;
+  s.gi_k = gi_k.p;
+  s.gi_v = gi_v.p;
+  s.ig_k = ig_k.p;
+  s.ig_v = ig_v.p;
   return s;
 }
 
@@ -305,9 +309,35 @@ __global__ void k_touch_constrained(GridGeom g, const int32_t* __restrict__ sub_
 // ---------------------------------------------------------------------------
 // local matrices (Sect. 3.1): A^w from the cells of w, split into II, IG, GG
 // ---------------------------------------------------------------------------
-__global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oIG,
-                                 const int64_t* __restrict__ oGG, double* __restrict__ AII, double* __restrict__ AIG,
-                                 double* __restrict__ AGG) {
+// entry A^w(node1, node2) of two local nodes of subdomain w: sum over the cells of w
+// containing both (kappa h Khat for internal cells, the cut-cell matrix otherwise)
+__device__ double local_entry(const SubMeta& sm, int w, int bi, int bj, int bk, int lx, int ly, int lz, int lx2,
+                              int ly2, int lz2) {
+  const GridGeom& g = sm.g;
+  double val = 0.0;
+  for (int cz = max(lz, lz2) - 1; cz <= min(lz, lz2); ++cz) {
+    if (cz < 0 || cz >= g.sz) continue;
+    for (int cy = max(ly, ly2) - 1; cy <= min(ly, ly2); ++cy) {
+      if (cy < 0 || cy >= g.sy) continue;
+      for (int cx = max(lx, lx2) - 1; cx <= min(lx, lx2); ++cx) {
+        if (cx < 0 || cx >= g.sx) continue;
+        const int64_t c = g.cell(bi * g.sx + cx, bj * g.sy + cy, bk * g.sz + cz);
+        if (sm.sub_of_cell[c] != w) continue;
+        const int a = (lx - cx) + 2 * (ly - cy) + 4 * (lz - cz);
+        const int bb = (lx2 - cx) + 2 * (ly2 - cy) + 4 * (lz2 - cz);
+        const double kap = sm.kappa ? sm.kappa[c] : 1.0;
+        const double kab = sm.cell_type[c] == UFE_CELL_INTERNAL ? g.h * q1_khat(a, bb)
+                                                                : sm.K_cut[(int64_t)sm.cut_index[c] * 64 + a * 8 + bb];
+        val += kap * kab;
+      }
+    }
+  }
+  return val;
+}
+
+// dense A_II and A_GG of every subdomain (Sect. 3.1: Neumann matrix over the cells of w)
+__global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGG,
+                                 double* __restrict__ AII, double* __restrict__ AGG) {
   const GridGeom& g = sm.g;
   const int w = blockIdx.x;
   const int b = sm.sub_block[w];
@@ -325,34 +355,154 @@ __global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, co
     if (lx2 < 0 || ly2 < 0 || lz2 < 0 || lx2 >= g.lnx || ly2 >= g.lny || lz2 >= g.lnz) continue;
     const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
     const int k2 = lmap_kind(c2);
-    if (k2 == LKIND_NONE || (k1 == LKIND_G && k2 == LKIND_I)) continue;
-    double val = 0.0;
-    for (int cz = max(lz, lz2) - 1; cz <= min(lz, lz2); ++cz) {
-      if (cz < 0 || cz >= g.sz) continue;
-      for (int cy = max(ly, ly2) - 1; cy <= min(ly, ly2); ++cy) {
-        if (cy < 0 || cy >= g.sy) continue;
-        for (int cx = max(lx, lx2) - 1; cx <= min(lx, lx2); ++cx) {
-          if (cx < 0 || cx >= g.sx) continue;
-          const int64_t c = g.cell(bi * g.sx + cx, bj * g.sy + cy, bk * g.sz + cz);
-          if (sm.sub_of_cell[c] != w) continue;
-          const int a = (lx - cx) + 2 * (ly - cy) + 4 * (lz - cz);
-          const int bb = (lx2 - cx) + 2 * (ly2 - cy) + 4 * (lz2 - cz);
-          const double kap = sm.kappa ? sm.kappa[c] : 1.0;
-          const double kab = sm.cell_type[c] == UFE_CELL_INTERNAL ? g.h * q1_khat(a, bb)
-                                                                  : sm.K_cut[(int64_t)sm.cut_index[c] * 64 + a * 8 + bb];
-          val += kap * kab;
-        }
-      }
-    }
+    if (k2 != k1) continue;
+    const double val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2);
     const int p1 = lmap_index(c1), p2 = lmap_index(c2);
-    if (k1 == LKIND_I && k2 == LKIND_I)
+    if (k1 == LKIND_I)
       AII[oII[w] + (int64_t)p1 * ldI + p2] = val;
-    else if (k1 == LKIND_I)
-      AIG[oIG[w] + (int64_t)p1 * ldG + p2] = val;
     else
       AGG[oGG[w] + (int64_t)p1 * ldG + p2] = val;
   }
   (void)nG;
+}
+
+// A_GI in ELL form: for each interface DOF j of w, the interior DOFs k of w among its
+// 27 neighbours (stencil slot o, -1 when empty) and A^w_jk.  Layout per subdomain is
+// slot-major (entry 27 g0 + o nG + j), so that rows j are read coalesced.
+__global__ void k_gi_ell(SubMeta sm, int32_t* __restrict__ ell_k, double* __restrict__ ell_v) {
+  const GridGeom& g = sm.g;
+  const int w = blockIdx.x;
+  const int b = sm.sub_block[w];
+  const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
+  const int nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
+  for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
+    const int ln = e / 27, o = e % 27;
+    const int32_t c1 = lm[ln];
+    if (lmap_kind(c1) != LKIND_G) continue;
+    const int64_t slot = 27 * (int64_t)sm.G_ptr[w] + (int64_t)o * nG + lmap_index(c1);
+    const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
+    const int lx2 = lx + (o % 3) - 1, ly2 = ly + ((o / 3) % 3) - 1, lz2 = lz + (o / 9) - 1;
+    int32_t k = -1;
+    double val = 0.0;
+    if (lx2 >= 0 && ly2 >= 0 && lz2 >= 0 && lx2 < g.lnx && ly2 < g.lny && lz2 < g.lnz) {
+      const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
+      if (lmap_kind(c2) == LKIND_I) {
+        k = lmap_index(c2);
+        val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2);
+      }
+    }
+    ell_k[slot] = k;
+    ell_v[slot] = val;
+  }
+}
+
+// A_IG in the same form: for each interior DOF p of w, its interface neighbours
+// (entry 27 i0 + o nI + p)
+__global__ void k_ig_ell(SubMeta sm, int32_t* __restrict__ ell_k, double* __restrict__ ell_v) {
+  const GridGeom& g = sm.g;
+  const int w = blockIdx.x;
+  const int b = sm.sub_block[w];
+  const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
+  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w];
+  const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
+  for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
+    const int ln = e / 27, o = e % 27;
+    const int32_t c1 = lm[ln];
+    if (lmap_kind(c1) != LKIND_I) continue;
+    const int64_t slot = 27 * (int64_t)sm.I_ptr[w] + (int64_t)o * nI + lmap_index(c1);
+    const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
+    const int lx2 = lx + (o % 3) - 1, ly2 = ly + ((o / 3) % 3) - 1, lz2 = lz + (o / 9) - 1;
+    int32_t k = -1;
+    double val = 0.0;
+    if (lx2 >= 0 && ly2 >= 0 && lz2 >= 0 && lx2 < g.lnx && ly2 < g.lny && lz2 < g.lnz) {
+      const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
+      if (lmap_kind(c2) == LKIND_G) {
+        k = lmap_index(c2);
+        val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2);
+      }
+    }
+    ell_k[slot] = k;
+    ell_v[slot] = val;
+  }
+}
+
+// scaled A^_GI entries: s_G[j] A_GI[j][k] s_I[k]
+template <typename T>
+__global__ void k_ell_scale(SubMeta sm, const int32_t* __restrict__ ell_k, const double* __restrict__ ell_v,
+                            const double* __restrict__ sI, const double* __restrict__ sG, T* __restrict__ ell_s) {
+  const int w = blockIdx.y;
+  const int nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nG * 27; e += gridDim.x * blockDim.x) {
+    const int64_t slot = (int64_t)sm.G_ptr[w] * 27 + e;
+    const int32_t k = ell_k[slot];
+    ell_s[slot] = k < 0 ? T(0) : (T)(ell_v[slot] * sG[sm.G_ptr[w] + e % nG] * sI[sm.I_ptr[w] + k]);
+  }
+}
+
+// X^T = (A^_II^-1 A^_IG)^T, row j = sum_k A^_GI[j][k] A^_II^-1[k][:]  (A^_II^-1 symmetric)
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_xt(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGI, const int32_t* __restrict__ ell_k,
+     const T* __restrict__ ell_s, const T* __restrict__ IIinv, T* __restrict__ Xt) {
+  __shared__ int32_t sk[8][27];
+  __shared__ T sv[8][27];
+  const int w = blockIdx.y;
+  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int ldI = pad4(nI);
+  const int j0 = blockIdx.x * 8;
+  if (j0 >= nG) return;
+  for (int e = threadIdx.x; e < 8 * 27; e += blockDim.x) {
+    const int jj = e / 27, o = e % 27;
+    const bool ok = j0 + jj < nG;
+    const int64_t slot = 27 * (int64_t)sm.G_ptr[w] + (int64_t)o * nG + j0 + jj;
+    sk[jj][o] = ok ? ell_k[slot] : -1;
+    sv[jj][o] = ok ? ell_s[slot] : T(0);
+  }
+  __syncthreads();
+  const T* Ainv = IIinv + oII[w];
+  for (int jj = 0; jj < 8 && j0 + jj < nG; ++jj) {
+    for (int c = threadIdx.x; c < ldI; c += blockDim.x) {
+      T acc = T(0);
+#pragma unroll
+      for (int o = 0; o < 27; ++o) {
+        const int32_t k = sk[jj][o];
+        if (k >= 0) acc += sv[jj][o] * Ainv[(int64_t)k * ldI + c];
+      }
+      Xt[oGI[w] + (int64_t)(j0 + jj) * ldI + c] = acc;
+    }
+  }
+}
+
+// S^ = A^_GG - A^_GI X^ ; row j of the result is written from column j of the product
+// (S^ is symmetric): S^[j][i] -= sum_k A^_GI[i][k] X^T[j][k]
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_schur(SubMeta sm, const int64_t* __restrict__ oGG, const int64_t* __restrict__ oGI, const int32_t* __restrict__ ell_k,
+        const T* __restrict__ ell_s, const T* __restrict__ Xt, T* __restrict__ GG) {
+  extern __shared__ __align__(16) char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  const int w = blockIdx.y, j = blockIdx.x;
+  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  if (j >= nG) return;
+  const int ldI = pad4(nI), ldG = pad4(nG);
+  for (int c = threadIdx.x; c < nI; c += blockDim.x) xs[c] = Xt[oGI[w] + (int64_t)j * ldI + c];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nG; i += blockDim.x) {
+    const int64_t base = 27 * (int64_t)sm.G_ptr[w] + i;
+    int32_t kk[27];
+    T vv[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      kk[o] = ell_k[base + (int64_t)o * nG];
+      vv[o] = ell_s[base + (int64_t)o * nG];
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int o = 0; o < 27; ++o)
+      if (kk[o] >= 0) acc += vv[o] * xs[kk[o]];
+    GG[oGG[w] + (int64_t)j * ldG + i] -= acc;
+  }
 }
 
 // Jacobi scales s = diag^-1/2 and the raw interface diagonal (stiffness weights)
@@ -384,20 +534,19 @@ __global__ void k_weights(int64_t n_dof, const uint8_t* __restrict__ nn, const i
   }
 }
 
-// scale and convert: dst[i][j] = src[i][j] * sr_i * sc_j  (FP64 -> T)
+// scale and convert: dst[i][j] = src[i][j] * sr_i * sc_j  (FP64 -> T); grid (row chunks, subdomain)
 template <typename T>
 __global__ void k_scale_block(const double* __restrict__ src, T* __restrict__ dst, const int64_t* __restrict__ off,
                               const int32_t* __restrict__ rptr, const int32_t* __restrict__ cptr,
                               const double* __restrict__ sr, const double* __restrict__ scl) {
-  const int w = blockIdx.x;
+  const int w = blockIdx.y;
   const int nr = rptr[w + 1] - rptr[w], nc = cptr[w + 1] - cptr[w];
   const int ld = pad4(nc);
   const int64_t o = off[w];
-  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) {
-    const int i = e / ld, j = e % ld;
-    double v = 0.0;
-    if (j < nc) v = src[o + e] * sr[rptr[w] + i] * scl[cptr[w] + j];
-    dst[o + e] = (T)v;
+  for (int i = blockIdx.x; i < nr; i += gridDim.x) {
+    const double ri = sr[rptr[w] + i];
+    for (int j = threadIdx.x; j < ld; j += blockDim.x)
+      dst[o + (int64_t)i * ld + j] = (T)(j < nc ? src[o + (int64_t)i * ld + j] * ri * scl[cptr[w] + j] : 0.0);
   }
 }
 
@@ -455,23 +604,23 @@ __global__ void k_coarse_local(const int32_t* __restrict__ C_ptr, const int64_t*
   }
 }
 
-// unscale: dst[i][j] *= sr_i * sc_j (sc may be null: rows only)
+// unscale: A[i][j] *= sr_i * sc_j (sc may be null: rows only); grid (row chunks, subdomain)
 template <typename T>
 __global__ void k_unscale(T* __restrict__ A, const int64_t* __restrict__ off, const int32_t* __restrict__ rptr,
                           const int32_t* __restrict__ cptr, const double* __restrict__ sr, const double* __restrict__ scl,
-                          int ncols_from_cptr) {
-  const int w = blockIdx.x;
+                          int unused) {
+  const int w = blockIdx.y;
   const int nr = rptr[w + 1] - rptr[w];
   const int nc = cptr[w + 1] - cptr[w];
   const int ld = pad4(nc);
-  for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) {
-    const int i = e / ld, j = e % ld;
-    if (j >= nc) continue;
-    double f = sr[rptr[w] + i];
-    if (scl) f *= scl[cptr[w] + j];
-    A[off[w] + e] = (T)((double)A[off[w] + e] * f);
+  for (int i = blockIdx.x; i < nr; i += gridDim.x) {
+    const double ri = sr[rptr[w] + i];
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+      T* a = A + off[w] + (int64_t)i * ld + j;
+      *a = (T)((double)*a * ri * (scl ? scl[cptr[w] + j] : 1.0));
+    }
   }
-  (void)ncols_from_cptr;
+  (void)unused;
 }
 
 // coarse matrix: row l gathers A_c^w of every subdomain w in neigh(l), in neigh order
@@ -537,7 +686,8 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
                             const std::vector<int64_t>& oGG, const std::vector<int64_t>& oCG,
                             const std::vector<int64_t>& oGC, const std::vector<int64_t>& oCC, int64_t nII, int64_t nIG,
                             int64_t nGG, int64_t nCG, int64_t nGC, int64_t nCC, DBuf<double>& AII, DBuf<double>& AIG,
-                            DBuf<double>& AGG, DBuf<double>& sI, DBuf<double>& sG, DBuf<T>& II, DBuf<T>& GG,
+                            DBuf<double>& AGG, DBuf<double>& sI, DBuf<double>& sG, DBuf<int32_t>& ell_k,
+                            DBuf<double>& ell_v, DBuf<T>& II, DBuf<T>& GG,
                             DBuf<T>& GC, DBuf<double>& Acw, DBuf<double>& rho) {
   Mesh& m = *B.mesh;
   cudaStream_t s = B.stream;
@@ -552,14 +702,11 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   auto dII = up(oII), dIG = up(oIG), dGG = up(oGG), dCG = up(oCG), dCC = up(oCC);
   // scaled blocks in precision T
   II.alloc(std::max<int64_t>(nII, 1), s);
-  DBuf<T> IG, Cs, Crho, X, Y, Sc;
-  IG.alloc(std::max<int64_t>(nIG, 1), s);
+  DBuf<T> Cs, Crho, X, Y, Sc;
   GG.alloc(std::max<int64_t>(nGG, 1), s);
-  k_scale_block<T><<<ns, 256, 0, s>>>(AII.p, II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p);
+  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AII.p, II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p);
   UFE_CHECK_LAUNCH();
-  k_scale_block<T><<<ns, 256, 0, s>>>(AIG.p, IG.p, dIG->p, m.I_ptr.p, m.G_ptr.p, sI.p, sG.p);
-  UFE_CHECK_LAUNCH();
-  k_scale_block<T><<<ns, 256, 0, s>>>(AGG.p, GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p);
+  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AGG.p, GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p);
   UFE_CHECK_LAUNCH();
   Cs.alloc(std::max<int64_t>(nCG, 1), s);
   Crho.alloc(std::max<int64_t>(nCG, 1), s);
@@ -577,19 +724,23 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   // 1. A_II^-1
   for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
   batched_inverse<T>(inv, II.p, status.p, s);
-  // 2. X = A_II^-1 A_IG
+  // 2. X^T = (A_II^-1 A_IG)^T and 3. S = A_GG - A_GI X, both from the sparse A_GI
   X.alloc(std::max<int64_t>(nIG, 1), s);
-  g.clear();
-  for (int w = 0; w < ns; ++w)
-    g.push_back({B.h_nI[w], B.h_nG[w], B.h_nI[w], pad4(B.h_nI[w]), pad4(B.h_nG[w]), pad4(B.h_nG[w]), oII[w], oIG[w], oIG[w]});
-  batched_gemm<T>(false, false, g, II.p, IG.p, X.p, T(1), T(0), s);
-  // 3. S = A_GG - A_IG^T X
-  g.clear();
-  for (int w = 0; w < ns; ++w)
-    g.push_back({B.h_nG[w], B.h_nG[w], B.h_nI[w], pad4(B.h_nG[w]), pad4(B.h_nG[w]), pad4(B.h_nG[w]), oIG[w], oIG[w], oGG[w]});
-  batched_gemm<T>(true, false, g, IG.p, X.p, GG.p, T(-1), T(1), s);
+  {
+    int nGmax = 1;
+    for (int w = 0; w < ns; ++w) nGmax = std::max(nGmax, B.h_nG[w]);
+    int nImax = 4;
+    for (int w = 0; w < ns; ++w) nImax = std::max(nImax, pad4(B.h_nI[w]));
+    DBuf<T> ell_s;
+    ell_s.alloc(std::max<int64_t>(m.n_Gloc, 1) * 27, s);
+    k_ell_scale<T><<<dim3(8, ns), 256, 0, s>>>(sm, ell_k.p, ell_v.p, sI.p, sG.p, ell_s.p);
+    UFE_CHECK_LAUNCH();
+    k_xt<T><<<dim3((nGmax + 7) / 8, ns), 256, 0, s>>>(sm, dII->p, dIG->p, ell_k.p, ell_s.p, II.p, X.p);
+    UFE_CHECK_LAUNCH();
+    k_schur<T><<<dim3(nGmax, ns), 256, nImax * sizeof(T), s>>>(sm, dGG->p, dIG->p, ell_k.p, ell_s.p, X.p, GG.p);
+    UFE_CHECK_LAUNCH();
+  }
   X.release();
-  IG.release();
   // 4. S' = S + C^T rho C
   g.clear();
   for (int w = 0; w < ns; ++w)
@@ -632,11 +783,11 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
   UFE_CHECK_LAUNCH();
   // 11. unscale the operators used at every iteration
-  k_unscale<T><<<ns, 256, 0, s>>>(II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p, 0);
+  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p, 0);
   UFE_CHECK_LAUNCH();
-  k_unscale<T><<<ns, 256, 0, s>>>(GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p, 0);
+  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p, 0);
   UFE_CHECK_LAUNCH();
-  k_unscale<T><<<ns, 256, 0, s>>>(GC.p, B.off_GC.p, m.G_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
+  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GC.p, B.off_GC.p, m.G_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
   UFE_CHECK_LAUNCH();
   std::vector<int> st = to_host(status.p, ns, s);
   for (int w = 0; w < ns; ++w)
@@ -789,7 +940,7 @@ void bddc_build(Bddc& B) {
   for (int w = 0; w < ns; ++w) {
     const int nI = B.h_nI[w], nG = B.h_nG[w], nc = B.h_nC[w];
     oII[w] = nII; nII += (int64_t)nI * pad4(nI);
-    oIG[w] = nIG; nIG += (int64_t)nI * pad4(nG);
+    oIG[w] = nIG; nIG += (int64_t)nG * pad4(nI);   // X^T (interface rows x interior columns)
     oGG[w] = nGG; nGG += (int64_t)nG * pad4(nG);
     oCG[w] = nCG; nCG += (int64_t)nc * pad4(nG);
     oGC[w] = nGC; nGC += (int64_t)nG * pad4(nc);
@@ -802,22 +953,28 @@ void bddc_build(Bddc& B) {
   upload(B.off_II, oII);
   upload(B.off_GG, oGG);
   upload(B.off_GC, oGC);
-  DBuf<int64_t> doIG;
-  upload(doIG, oIG);
 
   // ---- local matrices, scales, weights
   DBuf<double> AII, AIG, AGG, sI, sG, dGraw;
   AII.alloc(std::max<int64_t>(nII, 1), s);
-  AIG.alloc(std::max<int64_t>(nIG, 1), s);
   AGG.alloc(std::max<int64_t>(nGG, 1), s);
   AII.zero();
-  AIG.zero();
   AGG.zero();
+  DBuf<int32_t>& ell_k = B.gi_k;
+  DBuf<double>& ell_v = B.gi_v;
+  ell_k.alloc(std::max<int64_t>(m.n_Gloc, 1) * 27, s);
+  ell_v.alloc(std::max<int64_t>(m.n_Gloc, 1) * 27, s);
+  B.ig_k.alloc(std::max<int64_t>(m.n_Iloc, 1) * 27, s);
+  B.ig_v.alloc(std::max<int64_t>(m.n_Iloc, 1) * 27, s);
   sI.alloc(std::max<int64_t>(m.n_Iloc, 1), s);
   sG.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
   dGraw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
   const SubMeta sm = B.meta();
-  k_local_assemble<<<ns, 256, 0, s>>>(sm, B.off_II.p, doIG.p, B.off_GG.p, AII.p, AIG.p, AGG.p);
+  k_local_assemble<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
+  UFE_CHECK_LAUNCH();
+  k_gi_ell<<<ns, 256, 0, s>>>(sm, ell_k.p, ell_v.p);
+  UFE_CHECK_LAUNCH();
+  k_ig_ell<<<ns, 256, 0, s>>>(sm, B.ig_k.p, B.ig_v.p);
   UFE_CHECK_LAUNCH();
   k_local_diag<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p, dGraw.p);
   UFE_CHECK_LAUNCH();
@@ -829,11 +986,11 @@ void bddc_build(Bddc& B) {
   // ---- factorisations and explicit local operators
   DBuf<double> Acw, rho;
   if (B.mixed)
-    factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, B.fII,
-                           B.fGG, B.fGC, Acw, rho);
+    factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,
+                           ell_v, B.fII, B.fGG, B.fGC, Acw, rho);
   else
-    factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, B.dII,
-                            B.dGG, B.dGC, Acw, rho);
+    factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,
+                            ell_v, B.dII, B.dGG, B.dGC, Acw, rho);
   AII.release();
   AIG.release();
   AGG.release();
@@ -866,7 +1023,7 @@ void bddc_build(Bddc& B) {
     v->alloc(nd, s);
     v->zero();
   }
-  B.part_blocks = std::max<int64_t>(grid_for(nd, 256), ns) + 8;
+  B.part_blocks = std::max<int64_t>(grid_for(nd, 256), 8 * (int64_t)ns) + 8;
   B.part.alloc(B.part_blocks * 2, s);
   B.sc.alloc(1, s);
   B.sc.zero();

@@ -30,6 +30,10 @@ struct SubMeta {
   const int64_t* off_GG;    // element offset of K (nG x ldG)
   const int64_t* off_GC;    // element offset of Phi (nG x ldC)
   const double* w;          // weight per interface slot
+  const int32_t* gi_k;      // A_GI in ELL form (27 slots, slot-major per subdomain)
+  const double* gi_v;
+  const int32_t* ig_k;      // A_IG in ELL form
+  const double* ig_v;
 };
 
 struct PcgScalars {
@@ -69,6 +73,8 @@ struct Bddc {
   DBuf<double> dII, dGG, dGC;   // FP64 operators
   DBuf<float> fII, fGG, fGC;    // FP32 operators (mixed)
   DBuf<double> w;               // n_Gloc weights
+  DBuf<int32_t> gi_k, ig_k;     // A_GI / A_IG in ELL form (local indices)
+  DBuf<double> gi_v, ig_v;
   DBuf<double> Ac_inv;          // n_coarse x ldc, FP64
   int ldc = 0;
 

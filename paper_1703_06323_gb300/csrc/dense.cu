@@ -3,18 +3,19 @@
 // batched_gemm: one CTA per 64x64 output tile of one problem; 16-deep k slabs
 // staged in shared memory; each of the 256 threads owns a 4x4 register tile.
 //
-// Inversion: blocked Gauss-Jordan in place.  For each diagonal block K (width 32):
-//   A_KK <- A_KK^-1,  A_Kj <- A_KK^-1 A_Kj,  A_ij <- A_ij - A_iK A_Kj,  A_iK <- -A_iK A_KK^-1
+// Inversion: blocked Gauss-Jordan.  For each diagonal block K (width 64):
+//   A_KK <- A_KK^-1,  A_Kj <- A_KK^-1 A_Kj,  A_ij <- A_ij - A_iK A_KK^-1 A_Kj,  A_iK <- -A_iK A_KK^-1
 // (i, j outside K).  After the last block A holds A^-1.  Without pivoting this is
 // stable for SPD matrices, whose pivots are Schur complements and stay positive;
 // a pivot <= 0 (or not finite) flags the matrix as singular.
+#include <algorithm>
 #include <vector>
 
 #include "dense.cuh"
 
 namespace ufe {
 
-constexpr int kTile = 64, kSlab = 16, kGemmThreads = 256, kNB = 32;
+constexpr int kTile = 64, kSlab = 16, kGemmThreads = 256;
 
 template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(kGemmThreads)
@@ -111,228 +112,328 @@ void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, 
 }
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan building blocks (CTA-level); all take the block column k0, kb
+// Batched blocked Gauss-Jordan inversion, one block column (width kGJ) per step,
+// three launches per step over the whole batch:
+//   diag:   D^-1 of the diagonal block (register-blocked, one CTA per matrix);
+//   panel:  the old row panel R_K* = A_K* and Q_K* = D^-1 A_K*;
+//   update: every tile (I <= J) of the next iterate, A_IJ - P_IK Q_KJ, Q_KJ,
+//           -P_IK D^-1 or D^-1, with P_IK = +-R_KI^T, and its mirror tile.
+// Reads of the panels come from R / Q / D^-1, so the update runs in place
+// without races.
 // ---------------------------------------------------------------------------
-
-// invert the kb x kb diagonal block into Dinv (shared memory); returns false if singular
+// Block width: 64 for FP32; 32 for FP64, whose per-SM rate on this chip is low
+// enough that the serial diagonal-block inverse of each step must stay small.
 template <typename T>
-__device__ bool gj_diag(T* A, int ld, int k0, int kb, T (*D)[kNB + 1]) {
+struct GJWidth;
+template <>
+struct GJWidth<float> {
+  static constexpr int value = 64;
+};
+template <>
+struct GJWidth<double> {
+  static constexpr int value = 32;
+};
+constexpr int kGJThreads = 256;
+
+// In-place inverse of the kb x kb leading block of D (NB x NB in shared memory) by
+// Gauss-Jordan without pivoting.  256 threads as 16 x 16; thread (ty, tx) keeps rows
+// ty + 16a and columns tx + 16b (a, b < NB/16) in registers; pivot row and column go
+// through shared memory, two barriers per pivot, the reciprocal is formed once.
+// Rows / columns >= kb are left alone.
+template <typename T, int NB>
+__device__ bool gj_block_inverse(T (*D)[NB + 1], int kb) {
+  constexpr int RA = NB / 16;
+  __shared__ T rowb[NB], colb[NB];
+  __shared__ T s_inv;
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int r = e / kb, c = e % kb;
-    D[r][c] = A[(int64_t)(k0 + r) * ld + k0 + c];
-  }
-  __syncthreads();
-  for (int p = 0; p < kb; ++p) {
-    const T piv = D[p][p];
-    if (!(piv > T(0)) || !isfinite((double)piv)) {
-      if (threadIdx.x == 0) bad = 1;
-    }
-    const T inv = T(1) / piv;
-    __syncthreads();
-    // row p
-    for (int c = threadIdx.x; c < kb; c += blockDim.x)
-      if (c != p) D[p][c] *= inv;
-    __syncthreads();
-    // other rows
-    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-      const int r = e / kb, c = e % kb;
-      if (r == p || c == p) continue;
-      D[r][c] -= D[r][p] * D[p][c];
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < kb; r += blockDim.x)
-      if (r != p) D[r][p] = -D[r][p] * inv;
-    if (threadIdx.x == 0) D[p][p] = inv;
-    __syncthreads();
-  }
-  const bool ok = bad == 0;
-  __syncthreads();
-  return ok;
-}
-
-// A_Kj <- Dinv A_Kj for the columns j in [jb, je) outside K
-template <typename T>
-__device__ void gj_row_panel(T* A, int ld, int n, int k0, int kb, const T (*D)[kNB + 1], int jb, int je, int tid,
-                             int nthreads) {
-  for (int j = jb + tid; j < je; j += nthreads) {
-    if (j >= k0 && j < k0 + kb) continue;
-    T col[kNB];
-#pragma unroll
-    for (int r = 0; r < kNB; ++r) col[r] = r < kb ? A[(int64_t)(k0 + r) * ld + j] : T(0);
-#pragma unroll 4
-    for (int r = 0; r < kb; ++r) {
-      T sacc = T(0);
-#pragma unroll
-      for (int c = 0; c < kNB; ++c) sacc += D[r][c < kb ? c : 0] * (c < kb ? col[c] : T(0));
-      A[(int64_t)(k0 + r) * ld + j] = sacc;
-    }
-  }
-  (void)n;
-}
-
-// A_iK <- -A_iK Dinv for the rows i in [ib, ie) outside K
-template <typename T>
-__device__ void gj_col_panel(T* A, int ld, int k0, int kb, const T (*D)[kNB + 1], int ib, int ie, int tid,
-                             int nthreads) {
-  for (int i = ib + tid; i < ie; i += nthreads) {
-    if (i >= k0 && i < k0 + kb) continue;
-    T row[kNB];
-#pragma unroll
-    for (int c = 0; c < kNB; ++c) row[c] = c < kb ? A[(int64_t)i * ld + k0 + c] : T(0);
-#pragma unroll 4
-    for (int c = 0; c < kb; ++c) {
-      T sacc = T(0);
-#pragma unroll
-      for (int r = 0; r < kNB; ++r) sacc += (r < kb ? row[r] : T(0)) * D[r < kb ? r : 0][c];
-      A[(int64_t)i * ld + k0 + c] = -sacc;
-    }
-  }
-}
-
-// A_ij -= A_iK A_Kj on one 64x64 tile (i0, j0), skipping i or j inside K
-template <typename T>
-__device__ void gj_update_tile(T* A, int ld, int n, int k0, int kb, int i0, int j0, T (*As)[kTile + 1],
-                               T (*Bs)[kTile + 1]) {
-  for (int e = threadIdx.x; e < kNB * kTile; e += blockDim.x) {
-    const int l = e / kTile, r = e % kTile;
-    const int gi = i0 + r, gj = j0 + r;
-    As[l][r] = (l < kb && gi < n) ? A[(int64_t)gi * ld + k0 + l] : T(0);
-    Bs[l][r] = (l < kb && gj < n) ? A[(int64_t)(k0 + l) * ld + gj] : T(0);
-  }
-  __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  T v[RA][RA];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  for (int l = 0; l < kb; ++l) {
-    T av[4], bv[4];
+    for (int b = 0; b < RA; ++b) v[a][b] = D[ty + 16 * a][tx + 16 * b];
+  if (threadIdx.x == 0) bad = 0;
+  for (int p = 0; p < kb; ++p) {
+    const int pa = p >> 4, pr = p & 15;
+    if (ty == pr) {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = As[l][ty + 16 * a];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) bv[b] = Bs[l][tx + 16 * b];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int gi = i0 + ty + 16 * a;
-    if (gi >= n || (gi >= k0 && gi < k0 + kb)) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int gj = j0 + tx + 16 * b;
-      if (gj >= n || (gj >= k0 && gj < k0 + kb)) continue;
-      A[(int64_t)gi * ld + gj] -= acc[a][b];
+      for (int b = 0; b < RA; ++b) rowb[tx + 16 * b] = v[pa][b];
     }
+    if (tx == pr) {
+#pragma unroll
+      for (int a = 0; a < RA; ++a) colb[ty + 16 * a] = v[a][pa];
+    }
+    if (threadIdx.x == (pr << 4) + pr) {
+      const T piv = v[pa][pa];
+      if (!(piv > T(0)) || !isfinite((double)piv)) bad = 1;
+      s_inv = T(1) / piv;
+    }
+    __syncthreads();
+    const T inv = s_inv;
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int r = ty + 16 * a;
+      const T cr = colb[r] * inv;
+#pragma unroll
+      for (int b = 0; b < RA; ++b) {
+        const int c = tx + 16 * b;
+        if (r == p)
+          v[a][b] = (c == p) ? inv : v[a][b] * inv;
+        else if (c == p)
+          v[a][b] = -cr;
+        else
+          v[a][b] -= cr * rowb[c];
+      }
+    }
+    __syncthreads();
   }
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < RA; ++b) D[ty + 16 * a][tx + 16 * b] = v[a][b];
   __syncthreads();
+  return bad == 0;
 }
 
-// one CTA inverts one matrix of the batch
-template <typename T>
-__global__ void __launch_bounds__(kGemmThreads) k_batched_inverse(const InvDesc* __restrict__ descs, T* base, int* status) {
-  const InvDesc d = descs[blockIdx.x];
-  if (d.n <= 0) return;
-  T* A = base + d.off;
-  __shared__ T D[kNB][kNB + 1];
-  __shared__ T As[kNB][kTile + 1];
-  __shared__ T Bs[kNB][kTile + 1];
-  bool ok = true;
-  for (int k0 = 0; k0 < d.n; k0 += kNB) {
-    const int kb = min(kNB, d.n - k0);
-    ok = gj_diag<T>(A, d.ld, k0, kb, D) && ok;
-    gj_row_panel<T>(A, d.ld, d.n, k0, kb, D, 0, d.n, threadIdx.x, blockDim.x);
-    __syncthreads();
-    const int tiles = (d.n + kTile - 1) / kTile;
-    for (int t = 0; t < tiles * tiles; ++t) gj_update_tile<T>(A, d.ld, d.n, k0, kb, (t / tiles) * kTile, (t % tiles) * kTile, As, Bs);
-    gj_col_panel<T>(A, d.ld, k0, kb, D, 0, d.n, threadIdx.x, blockDim.x);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-      const int r = e / kb, c = e % kb;
-      A[(int64_t)(k0 + r) * d.ld + k0 + c] = D[r][c];
-    }
-    __syncthreads();
+// out(NB x NB tile) = sum_l L[i][l] R[l][j], l < kb
+template <typename T, int NB>
+__device__ __forceinline__ void tile_mma(const T (*L)[NB + 1], const T (*R)[NB + 1], int kb, T acc[NB / 16][NB / 16]) {
+  constexpr int RA = NB / 16;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < RA; ++b) acc[a][b] = T(0);
+  for (int l = 0; l < kb; ++l) {
+    T av[RA], bv[RA];
+#pragma unroll
+    for (int a = 0; a < RA; ++a) av[a] = L[ty + 16 * a][l];
+#pragma unroll
+    for (int b = 0; b < RA; ++b) bv[b] = R[l][tx + 16 * b];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int b = 0; b < RA; ++b) acc[a][b] += av[a] * bv[b];
   }
-  if (!ok && threadIdx.x == 0) atomicOr(status + blockIdx.x, DEV_SINGULAR);
+}
+
+struct GJBatch {
+  const InvDesc* d;    // per matrix: n, ld, offset into the matrix base
+  const int64_t* qoff; // per matrix: offset of its row panels R and Q (NB x ld each)
+};
+
+// Symmetric Gauss-Jordan.  With the blocks before K already processed, the iterate
+// is [[X11, X12], [-X12^T, X22]] with X11, X22 symmetric, so every tile below the
+// diagonal is +-(the mirrored tile)^T: -1 exactly when one of its two block indices
+// is processed.  Only tiles with I <= J are computed; each writes its mirror.
+__device__ __forceinline__ int gj_sign(int I, int J, int last_processed) {
+  return ((I <= last_processed) != (J <= last_processed)) ? -1 : 1;
+}
+
+// first diagonal block: D^-1, one CTA per matrix
+template <typename T, int NB>
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_diag(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ Dg, int* status) {
+  const int b = blockIdx.x;
+  const InvDesc d = bt.d[b];
+  const int k0 = step * NB;
+  if (k0 >= d.n) return;
+  const int kb = min(NB, d.n - k0);
+  __shared__ T D[NB][NB + 1];
+  const T* A = base + d.off;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    D[r][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : T(r == c ? 1 : 0);
+  }
+  __syncthreads();
+  const bool ok = gj_block_inverse<T, NB>(D, kb);
+  T* Db = Dg + (int64_t)b * NB * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Db[e] = D[e / NB][e % NB];
+  if (!ok && threadIdx.x == 0) atomicOr(status + b, DEV_SINGULAR);
+}
+
+// old row panel R_Kt = A_Kt and Q_Kt = D^-1 A_Kt, 16 columns per CTA
+template <typename T, int NB>
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_panel(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ R, T* __restrict__ Q,
+           const T* __restrict__ Dg) {
+  const int b = blockIdx.y;
+  const InvDesc d = bt.d[b];
+  const int k0 = step * NB;
+  const int c0 = blockIdx.x * 16;
+  if (k0 >= d.n || c0 >= d.n || (c0 >= k0 && c0 < k0 + NB)) return;
+  const int kb = min(NB, d.n - k0), cb = min(16, d.n - c0);
+  __shared__ T Ds[NB][NB + 1];
+  __shared__ T W[NB][17];
+  const T* A = base + d.off;
+  const T* Db = Dg + (int64_t)b * NB * NB;
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Ds[e / NB][e % NB] = Db[e];
+  T* Rb = R + bt.qoff[b];
+  T* Qb = Q + bt.qoff[b];
+  for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
+    const int r = e / 16, c = e % 16;
+    T v = T(0);
+    if (r < kb && c < cb) {
+      v = A[(int64_t)(k0 + r) * d.ld + c0 + c];
+      Rb[(int64_t)r * d.ld + c0 + c] = v;
+    }
+    W[r][c] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
+    const int r = e / 16, c = e % 16;
+    if (r >= kb || c >= cb) continue;
+    T acc = T(0);
+    for (int l = 0; l < kb; ++l) acc += Ds[r][l] * W[l][c];
+    Qb[(int64_t)r * d.ld + c0 + c] = acc;
+  }
+}
+
+// tiles (I <= J) of the next iterate and their mirrors; CTA 0 takes the next
+// diagonal tile and inverts it for the next step (it starts first)
+template <typename T, int NB>
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R, const T* __restrict__ Q,
+            const T* __restrict__ Dg, T* __restrict__ Dnext, int* status) {
+  constexpr int RA = NB / 16;
+  const int b = blockIdx.y;
+  const InvDesc d = bt.d[b];
+  const int k0 = step * NB;
+  const int nd = step + 1;
+  const int nd_tri = (nd < nblk) ? nd * nblk - nd * (nd - 1) / 2 : -1;   // triangle index of (nd, nd)
+  int t = (int)blockIdx.x;
+  if (nd_tri >= 0) {
+    if (blockIdx.x == 0)
+      t = nd_tri;
+    else if ((int)blockIdx.x <= nd_tri)
+      t = (int)blockIdx.x - 1;
+  }
+  int I = 0;
+  while (t >= nblk - I) {
+    t -= nblk - I;
+    ++I;
+  }
+  const int J = I + t, K = step;
+  if (k0 >= d.n || J * NB >= d.n) return;
+  const int kb = min(NB, d.n - k0);
+  const int i0 = I * NB, j0 = J * NB, ib = min(NB, d.n - i0), jb = min(NB, d.n - j0);
+  T* A = base + d.off;
+  const T* Db = Dg + (int64_t)b * NB * NB;
+  const T* Rb = R + bt.qoff[b];
+  const T* Qb = Q + bt.qoff[b];
+  __shared__ T L[NB][NB + 1];
+  __shared__ T Rt[NB][NB + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[RA][RA];
+  if (I == K && J == K) {
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x)
+      A[(int64_t)(k0 + e / kb) * d.ld + k0 + e % kb] = Db[(e / kb) * NB + e % kb];
+    return;
+  }
+  if (I == K) {
+    // new row panel Q_KJ; mirror (J, K) = -Q_KJ^T
+    for (int e = threadIdx.x; e < kb * jb; e += blockDim.x) {
+      const int r = e / jb, c = e % jb;
+      const T v = Qb[(int64_t)r * d.ld + j0 + c];
+      A[(int64_t)(k0 + r) * d.ld + j0 + c] = v;
+      A[(int64_t)(j0 + c) * d.ld + k0 + r] = -v;
+    }
+    return;
+  }
+  // P_IK = s R_KI^T with s = -1 when I is processed (I < K), else +1
+  const T sP = I < K ? T(-1) : T(1);
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    L[r][c] = (r < ib && c < kb) ? sP * Rb[(int64_t)c * d.ld + i0 + r] : T(0);
+    if (J == K)
+      Rt[r][c] = (r < kb && c < kb) ? Db[r * NB + c] : T(0);
+    else
+      Rt[r][c] = (r < kb && c < jb) ? Qb[(int64_t)r * d.ld + j0 + c] : T(0);
+  }
+  __syncthreads();
+  tile_mma<T, NB>(L, Rt, kb, acc);
+  // tile value: J == K -> -P_IK D^-1, else A_IJ - P_IK Q_KJ;  mirror sign after this step
+  const T sM = (T)gj_sign(I, J, K);
+#pragma unroll
+  for (int a = 0; a < RA; ++a) {
+    const int r = ty + 16 * a;
+#pragma unroll
+    for (int c4 = 0; c4 < RA; ++c4) {
+      const int c = tx + 16 * c4;
+      if (r >= ib || c >= jb) continue;
+      T* ap = A + (int64_t)(i0 + r) * d.ld + j0 + c;
+      const T v = (J == K) ? -acc[a][c4] : (*ap - acc[a][c4]);
+      *ap = v;
+      acc[a][c4] = v;
+      if (I != J) A[(int64_t)(j0 + c) * d.ld + i0 + r] = sM * v;
+    }
+  }
+  if (I == K + 1 && J == K + 1) {
+    // the next diagonal block: invert it now for the next step
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int c4 = 0; c4 < RA; ++c4) {
+        const int r = ty + 16 * a, c = tx + 16 * c4;
+        L[r][c] = (r < ib && c < jb) ? acc[a][c4] : T(r == c ? 1 : 0);
+      }
+    __syncthreads();
+    const bool ok = gj_block_inverse<T, NB>(L, ib);
+    T* Dn = Dnext + (int64_t)b * NB * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Dn[e] = L[e / NB][e % NB];
+    if (!ok && threadIdx.x == 0) atomicOr(status + b, DEV_SINGULAR);
+  }
+}
+
+template <typename T>
+static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s) {
+  constexpr int NB = GJWidth<T>::value;
+  if (descs.empty()) return;
+  int nmax = 0;
+  std::vector<int64_t> qoff(descs.size());
+  int64_t nq = 0;
+  for (size_t b = 0; b < descs.size(); ++b) {
+    nmax = std::max(nmax, descs[b].n);
+    qoff[b] = nq;
+    nq += (int64_t)NB * descs[b].ld;
+  }
+  if (nmax == 0) return;
+  DBuf<InvDesc> dd;
+  DBuf<int64_t> dq;
+  DBuf<T> R, Q, D;
+  dd.alloc(descs.size(), s);
+  dq.alloc(descs.size(), s);
+  R.alloc(std::max<int64_t>(nq, 1), s);
+  Q.alloc(std::max<int64_t>(nq, 1), s);
+  D.alloc(2 * descs.size() * NB * NB, s);
+  T* Dbuf[2] = {D.p, D.p + descs.size() * NB * NB};
+  UFE_CUDA(cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(InvDesc), cudaMemcpyHostToDevice, s));
+  UFE_CUDA(cudaMemcpyAsync(dq.p, qoff.data(), qoff.size() * 8, cudaMemcpyHostToDevice, s));
+  const GJBatch bt{dd.p, dq.p};
+  const int nblk = (nmax + NB - 1) / NB;
+  const unsigned nb = (unsigned)descs.size();
+  const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
+  k_gj_diag<T, NB><<<nb, kGJThreads, 0, s>>>(bt, 0, base, Dbuf[0], status);
+  UFE_CHECK_LAUNCH();
+  for (int step = 0; step < nblk; ++step) {
+    T* Dc = Dbuf[step & 1];
+    T* Dn = Dbuf[(step + 1) & 1];
+    k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s>>>(bt, step, base, R.p, Q.p, Dc);
+    UFE_CHECK_LAUNCH();
+    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, R.p, Q.p, Dc, Dn, status);
+    UFE_CHECK_LAUNCH();
+  }
 }
 
 template <typename T>
 void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s) {
-  if (descs.empty()) return;
-  DBuf<InvDesc> dd;
-  dd.alloc(descs.size(), s);
-  UFE_CUDA(cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(InvDesc), cudaMemcpyHostToDevice, s));
-  k_batched_inverse<T><<<(unsigned)descs.size(), kGemmThreads, 0, s>>>(dd.p, base, status);
-  UFE_CHECK_LAUNCH();
-}
-
-// ---------------------------------------------------------------------------
-// one large matrix: the same four steps, each spread over the grid
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void k_large_diag(T* A, int ld, int k0, int kb, T* Dout, int* status) {
-  __shared__ T D[kNB][kNB + 1];
-  const bool ok = gj_diag<T>(A, ld, k0, kb, D);
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) Dout[e] = D[e / kNB][e % kNB];
-  if (!ok && threadIdx.x == 0) atomicOr(status, DEV_SINGULAR);
-}
-
-template <typename T>
-__device__ void load_D(const T* Dg, T (*D)[kNB + 1]) {
-  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) D[e / kNB][e % kNB] = Dg[e];
-  __syncthreads();
-}
-
-template <typename T>
-__global__ void k_large_row_panel(T* A, int ld, int n, int k0, int kb, const T* Dg) {
-  __shared__ T D[kNB][kNB + 1];
-  load_D<T>(Dg, D);
-  gj_row_panel<T>(A, ld, n, k0, kb, D, 0, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kGemmThreads) k_large_update(T* A, int ld, int n, int k0, int kb) {
-  __shared__ T As[kNB][kTile + 1];
-  __shared__ T Bs[kNB][kTile + 1];
-  const int tiles = (n + kTile - 1) / kTile;
-  for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x)
-    gj_update_tile<T>(A, ld, n, k0, kb, (t / tiles) * kTile, (t % tiles) * kTile, As, Bs);
-}
-
-template <typename T>
-__global__ void k_large_col_panel(T* A, int ld, int n, int k0, int kb, const T* Dg) {
-  __shared__ T D[kNB][kNB + 1];
-  load_D<T>(Dg, D);
-  gj_col_panel<T>(A, ld, k0, kb, D, 0, n, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-  if (blockIdx.x == 0)
-    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x)
-      A[(int64_t)(k0 + e / kb) * ld + k0 + e % kb] = D[e / kb][e % kb];
+  gj_run<T>(descs, base, status, s);
 }
 
 template <typename T>
 void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s) {
-  if (n <= 0) return;
-  DBuf<T> Dg;
-  Dg.alloc(kNB * kNB, s);
-  const int tiles = (n + kTile - 1) / kTile;
-  const unsigned upd_grid = (unsigned)std::min(tiles * tiles, 152 * 8);
-  const unsigned panel_grid = (unsigned)std::max(1, std::min((n + 255) / 256, 152 * 4));
-  for (int k0 = 0; k0 < n; k0 += kNB) {
-    const int kb = std::min(kNB, n - k0);
-    k_large_diag<T><<<1, 256, 0, s>>>(A, ld, k0, kb, Dg.p, status);
-    UFE_CHECK_LAUNCH();
-    k_large_row_panel<T><<<panel_grid, 256, 0, s>>>(A, ld, n, k0, kb, Dg.p);
-    UFE_CHECK_LAUNCH();
-    k_large_update<T><<<upd_grid, kGemmThreads, 0, s>>>(A, ld, n, k0, kb);
-    UFE_CHECK_LAUNCH();
-    k_large_col_panel<T><<<panel_grid, 256, 0, s>>>(A, ld, n, k0, kb, Dg.p);
-    UFE_CHECK_LAUNCH();
-  }
+  gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s);
 }
 
 template void batched_gemm<double>(bool, bool, const std::vector<GemmDesc>&, const double*, const double*, double*,

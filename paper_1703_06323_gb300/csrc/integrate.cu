@@ -10,8 +10,7 @@
 // to rounding).  The rules are generated on the host from the published
 // formula of Grundmann & Moeller (1978) and kept in constant memory.
 //
-// One thread per (cut cell, Kuhn tet); the 6 partial results of a cell are
-// summed in a fixed order in shared memory.
+// One warp per cut cell (see k_integrate_cut).
 #include <cmath>
 #include <functional>
 #include <mutex>
@@ -92,76 +91,29 @@ __device__ __forceinline__ Vec3 lerp_cross(const Vec3& pu, const Vec3& pv, doubl
   return {pu.x + t * (pv.x - pu.x), pu.y + t * (pv.y - pu.y), pu.z + t * (pv.z - pu.z)};
 }
 
-struct CellData {
-  double f8[8];
-  double q8[8][3];
-  bool has_q;
-  double h;
+// Per cut cell, six lanes clip the six Kuhn tets and write the sub-tets and
+// boundary triangles into shared memory; then all 32 lanes of the warp share the
+// (sub-tet, point) and (triangle, point) work items and the 45 partial sums are
+// reduced with warp shuffles.
+constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxSubTets = 18, kMaxTris = 12;
+
+struct CellGeom {
+  double tet[kMaxSubTets][12];   // 4 vertices x (x, y, z), unit-cube coordinates
+  double tri[kMaxTris][12];      // 3 vertices x (x, y, z) + unit normal
+  int n_tet, n_tri;
 };
 
-__device__ void integrate_tet(const Vec3& A, const Vec3& B, const Vec3& C, const Vec3& D, const CellData& cd,
-                              double* acc) {
-  const double ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
-  const double vx = C.x - A.x, vy = C.y - A.y, vz = C.z - A.z;
-  const double wx = D.x - A.x, wy = D.y - A.y, wz = D.z - A.z;
-  const double det = ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx);
-  const double vol = fabs(det) / 6.0;
-  if (vol == 0.0) return;
-  const double h3 = cd.h * cd.h * cd.h;
-  for (int q = 0; q < kTetPts; ++q) {
-    const double l0 = c_tet_bary[4 * q], l1 = c_tet_bary[4 * q + 1], l2 = c_tet_bary[4 * q + 2],
-                 l3 = c_tet_bary[4 * q + 3];
-    const double px = l0 * A.x + l1 * B.x + l2 * C.x + l3 * D.x;
-    const double py = l0 * A.y + l1 * B.y + l2 * C.y + l3 * D.y;
-    const double pz = l0 * A.z + l1 * B.z + l2 * C.z + l3 * D.z;
-    const double wq = c_tet_w[q] * vol;
-    double N[8], G[8][3];
-    q1_shape_grad(px, py, pz, N, G);
-    int e = 0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int b = a; b < 8; ++b, ++e) acc[e] += wq * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
-    double fh = 0.0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) fh += N[a] * cd.f8[a];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) acc[36 + a] += wq * fh * N[a] * h3;
-    acc[44] += wq;
-  }
+__device__ __forceinline__ void put3(double* d, const Vec3& v) {
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
 }
 
-__device__ void integrate_tri(const Vec3& A, const Vec3& B, const Vec3& C, const double n[3], const CellData& cd,
-                              double* acc) {
-  const double ux = B.x - A.x, uy = B.y - A.y, uz = B.z - A.z;
-  const double vx = C.x - A.x, vy = C.y - A.y, vz = C.z - A.z;
-  const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
-  const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
-  if (area == 0.0) return;
-  const double h2 = cd.h * cd.h;
-  for (int q = 0; q < kTriPts; ++q) {
-    const double l0 = c_tri_bary[3 * q], l1 = c_tri_bary[3 * q + 1], l2 = c_tri_bary[3 * q + 2];
-    const double px = l0 * A.x + l1 * B.x + l2 * C.x;
-    const double py = l0 * A.y + l1 * B.y + l2 * C.y;
-    const double pz = l0 * A.z + l1 * B.z + l2 * C.z;
-    const double wq = c_tri_w[q] * area;
-    double N[8];
-    q1_shape(px, py, pz, N);
-    double qx = 0, qy = 0, qz = 0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      qx += N[a] * cd.q8[a][0];
-      qy += N[a] * cd.q8[a][1];
-      qz += N[a] * cd.q8[a][2];
-    }
-    const double gn = qx * n[0] + qy * n[1] + qz * n[2];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) acc[36 + a] += wq * gn * N[a] * h2;
-  }
-}
-
-// part {phi < 0} of one Kuhn tet with vertices P (unit-cube coordinates) and values F
-__device__ void clip_and_integrate(const Vec3 P[4], const double F[4], const CellData& cd, double* acc) {
+// clip one Kuhn tet: writes its sub-tets / triangles into local arrays; returns counts
+__device__ void clip_tet(const Vec3 P[4], const double F[4], double st[3][12], int& nst, double tr[2][12], int& ntr) {
+  nst = 0;
+  ntr = 0;
   int neg[4], pos[4], nn = 0, np = 0;
   for (int m = 0; m < 4; ++m) {
     if (F[m] < 0.0)
@@ -170,11 +122,18 @@ __device__ void clip_and_integrate(const Vec3 P[4], const double F[4], const Cel
       pos[np++] = m;
   }
   if (nn == 0) return;
+  auto tet = [&](const Vec3& A, const Vec3& B, const Vec3& C, const Vec3& D) {
+    put3(st[nst] + 0, A);
+    put3(st[nst] + 3, B);
+    put3(st[nst] + 6, C);
+    put3(st[nst] + 9, D);
+    ++nst;
+  };
   if (nn == 4) {
-    integrate_tet(P[0], P[1], P[2], P[3], cd, acc);
+    tet(P[0], P[1], P[2], P[3]);
     return;
   }
-  // gradient of the linear level set on the tet: D g = dF (Cramer's rule)
+  // gradient of the linear level set on the tet (Cramer's rule); unit normal
   const double d1x = P[1].x - P[0].x, d1y = P[1].y - P[0].y, d1z = P[1].z - P[0].z;
   const double d2x = P[2].x - P[0].x, d2y = P[2].y - P[0].y, d2z = P[2].z - P[0].z;
   const double d3x = P[3].x - P[0].x, d3y = P[3].y - P[0].y, d3z = P[3].z - P[0].z;
@@ -184,100 +143,187 @@ __device__ void clip_and_integrate(const Vec3 P[4], const double F[4], const Cel
   const double gy = (d1x * (r2 * d3z - d2z * r3) - r1 * (d2x * d3z - d2z * d3x) + d1z * (d2x * r3 - r2 * d3x)) / det;
   const double gz = (d1x * (d2y * r3 - r2 * d3y) - d1y * (d2x * r3 - r2 * d3x) + r1 * (d2x * d3y - d2y * d3x)) / det;
   const double gn = sqrt(gx * gx + gy * gy + gz * gz);
-  const double n[3] = {gx / gn, gy / gn, gz / gn};
+  const Vec3 nrm = {gx / gn, gy / gn, gz / gn};
+  auto tri = [&](const Vec3& A, const Vec3& B, const Vec3& C) {
+    put3(tr[ntr] + 0, A);
+    put3(tr[ntr] + 3, B);
+    put3(tr[ntr] + 6, C);
+    put3(tr[ntr] + 9, nrm);
+    ++ntr;
+  };
   if (nn == 1) {
     const int a = neg[0], b = pos[0], c = pos[1], d = pos[2];
     const Vec3 pab = lerp_cross(P[a], P[b], F[a], F[b]);
     const Vec3 pac = lerp_cross(P[a], P[c], F[a], F[c]);
     const Vec3 pad = lerp_cross(P[a], P[d], F[a], F[d]);
-    integrate_tet(P[a], pab, pac, pad, cd, acc);
-    if (cd.has_q) integrate_tri(pab, pac, pad, n, cd, acc);
+    tet(P[a], pab, pac, pad);
+    tri(pab, pac, pad);
   } else if (nn == 3) {
     const int a = neg[0], b = neg[1], c = neg[2], d = pos[0];
     const Vec3 pad = lerp_cross(P[a], P[d], F[a], F[d]);
     const Vec3 pbd = lerp_cross(P[b], P[d], F[b], F[d]);
     const Vec3 pcd = lerp_cross(P[c], P[d], F[c], F[d]);
-    integrate_tet(P[a], P[b], P[c], pad, cd, acc);
-    integrate_tet(P[b], P[c], pad, pbd, cd, acc);
-    integrate_tet(P[c], pad, pbd, pcd, cd, acc);
-    if (cd.has_q) integrate_tri(pad, pbd, pcd, n, cd, acc);
+    tet(P[a], P[b], P[c], pad);
+    tet(P[b], P[c], pad, pbd);
+    tet(P[c], pad, pbd, pcd);
+    tri(pad, pbd, pcd);
   } else {
     const int a = neg[0], b = neg[1], c = pos[0], d = pos[1];
     const Vec3 pac = lerp_cross(P[a], P[c], F[a], F[c]);
     const Vec3 pad = lerp_cross(P[a], P[d], F[a], F[d]);
     const Vec3 pbc = lerp_cross(P[b], P[c], F[b], F[c]);
     const Vec3 pbd = lerp_cross(P[b], P[d], F[b], F[d]);
-    integrate_tet(P[a], pac, pad, P[b], cd, acc);
-    integrate_tet(pac, pad, P[b], pbc, cd, acc);
-    integrate_tet(pad, P[b], pbc, pbd, cd, acc);
-    if (cd.has_q) {
-      integrate_tri(pac, pad, pbd, n, cd, acc);
-      integrate_tri(pac, pbd, pbc, n, cd, acc);
-    }
+    tet(P[a], pac, pad, P[b]);
+    tet(pac, pad, P[b], pbc);
+    tet(pad, P[b], pbc, pbd);
+    tri(pac, pad, pbd);
+    tri(pac, pbd, pbc);
   }
 }
 
-constexpr int kCellsPerBlock = 16;
-
-__global__ void __launch_bounds__(kCellsPerBlock * 6)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
 k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells, const double* __restrict__ phi,
                 const double* __restrict__ f, const double* __restrict__ q, double* __restrict__ K_cut,
                 double* __restrict__ load_cut, double* __restrict__ eta) {
-  __shared__ double part[kCellsPerBlock][6][kAcc];
-  const int slot = threadIdx.x / 6, t = threadIdx.x % 6;
-  const int64_t kc = (int64_t)blockIdx.x * kCellsPerBlock + slot;
+  __shared__ double s_tet[kTetPts * 5];   // 4 barycentric + weight
+  __shared__ double s_tri[kTriPts * 4];
+  __shared__ CellGeom geo[kWarpsPerBlock];
+  __shared__ double s_f[kWarpsPerBlock][8];
+  __shared__ double s_q[kWarpsPerBlock][8][3];
+  for (int e = threadIdx.x; e < kTetPts; e += blockDim.x) {
+    for (int c = 0; c < 4; ++c) s_tet[e * 5 + c] = c_tet_bary[e * 4 + c];
+    s_tet[e * 5 + 4] = c_tet_w[e];
+  }
+  for (int e = threadIdx.x; e < kTriPts; e += blockDim.x) {
+    for (int c = 0; c < 3; ++c) s_tri[e * 4 + c] = c_tri_bary[e * 3 + c];
+    s_tri[e * 4 + 3] = c_tri_w[e];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t kc = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  const bool valid = kc < n_cut;
+  CellGeom& G = geo[warp];
+  int ntet_l = 0, ntri_l = 0;
+  double st[3][12], tr[2][12];
+  if (valid) {
+    const int64_t c = cut_cells[kc];
+    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+    if (lane < 8) {
+      const int64_t v = g.node(i + (lane & 1), j + ((lane >> 1) & 1), k + (lane >> 2));
+      s_f[warp][lane] = f ? f[v] : 0.0;
+      for (int d = 0; d < 3; ++d) s_q[warp][lane][d] = q ? q[3 * v + d] : 0.0;
+    }
+    if (lane < 6) {
+      const int ax0[6] = {0, 0, 1, 1, 2, 2};
+      const int ax1[6] = {1, 2, 0, 2, 0, 1};
+      const int vid[4] = {0, 1 << ax0[lane], (1 << ax0[lane]) | (1 << ax1[lane]), 7};
+      Vec3 P[4];
+      double F[4];
+      for (int m = 0; m < 4; ++m) {
+        P[m] = {(double)(vid[m] & 1), (double)((vid[m] >> 1) & 1), (double)(vid[m] >> 2)};
+        F[m] = phi[g.node(i + (vid[m] & 1), j + ((vid[m] >> 1) & 1), k + (vid[m] >> 2))];
+      }
+      clip_tet(P, F, st, ntet_l, tr, ntri_l);
+    }
+  }
+  // compact the per-tet pieces of lanes 0..5 into the warp's shared geometry
+  int off_t = ntet_l, off_r = ntri_l;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const int a = __shfl_up_sync(0xffffffffu, off_t, o), b = __shfl_up_sync(0xffffffffu, off_r, o);
+    if (lane >= o) {
+      off_t += a;
+      off_r += b;
+    }
+  }
+  const int tot_t = __shfl_sync(0xffffffffu, off_t, 7), tot_r = __shfl_sync(0xffffffffu, off_r, 7);
+  off_t -= ntet_l;
+  off_r -= ntri_l;
+  for (int a = 0; a < ntet_l; ++a)
+    for (int e = 0; e < 12; ++e) G.tet[off_t + a][e] = st[a][e];
+  for (int a = 0; a < ntri_l; ++a)
+    for (int e = 0; e < 12; ++e) G.tri[off_r + a][e] = tr[a][e];
+  if (lane == 0) {
+    G.n_tet = tot_t;
+    G.n_tri = (q != nullptr) ? tot_r : 0;
+  }
+  __syncthreads();
   double acc[kAcc];
 #pragma unroll
   for (int e = 0; e < kAcc; ++e) acc[e] = 0.0;
-  if (kc < n_cut) {
-    const int64_t c = cut_cells[kc];
-    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
-    CellData cd;
-    cd.h = g.h;
-    cd.has_q = q != nullptr;
-    double phi8[8];
+  if (valid) {
+    const double h = g.h, h3 = h * h * h, h2 = h * h;
+    const int n_vol = G.n_tet * kTetPts, n_all = n_vol + G.n_tri * kTriPts;
+    for (int it = lane; it < n_all; it += 32) {
+      if (it < n_vol) {
+        const double* T = G.tet[it / kTetPts];
+        const double* R = s_tet + (it % kTetPts) * 5;
+        const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+        const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+        const double wx = T[9] - T[0], wy = T[10] - T[1], wz = T[11] - T[2];
+        const double vol =
+            fabs(ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx)) / 6.0;
+        const double px = R[0] * T[0] + R[1] * T[3] + R[2] * T[6] + R[3] * T[9];
+        const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7] + R[3] * T[10];
+        const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8] + R[3] * T[11];
+        const double wq = R[4] * vol;
+        double N[8], Gd[8][3];
+        q1_shape_grad(px, py, pz, N, Gd);
+        int e = 0;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int64_t v = g.node(i + (a & 1), j + ((a >> 1) & 1), k + (a >> 2));
-      phi8[a] = phi[v];
-      cd.f8[a] = f ? f[v] : 0.0;
-      for (int dd = 0; dd < 3; ++dd) cd.q8[a][dd] = q ? q[3 * v + dd] : 0.0;
-    }
-    // Kuhn tet t: first two axes of the t-th permutation of (x, y, z)
-    const int ax0[6] = {0, 0, 1, 1, 2, 2};
-    const int ax1[6] = {1, 2, 0, 2, 0, 1};
-    const int vid[4] = {0, 1 << ax0[t], (1 << ax0[t]) | (1 << ax1[t]), 7};
-    Vec3 P[4];
-    double F[4];
-    for (int m = 0; m < 4; ++m) {
-      P[m] = {(double)(vid[m] & 1), (double)((vid[m] >> 1) & 1), (double)(vid[m] >> 2)};
-      F[m] = phi8[vid[m]];
-    }
-    clip_and_integrate(P, F, cd, acc);
-  }
-  for (int e = 0; e < kAcc; ++e) part[slot][t][e] = acc[e];
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < kCellsPerBlock * kAcc; idx += blockDim.x) {
-    const int sl = idx / kAcc, e = idx % kAcc;
-    const int64_t kk = (int64_t)blockIdx.x * kCellsPerBlock + sl;
-    if (kk >= n_cut) continue;
-    double s = 0.0;
-    for (int tt = 0; tt < 6; ++tt) s += part[sl][tt][e];
-    if (e < 36) {
-      // packed (a, b), a <= b  ->  symmetric 8 x 8, scaled by h
-      int a = 0, rem = e;
-      while (rem >= 8 - a) {
-        rem -= 8 - a;
-        ++a;
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = a; b < 8; ++b, ++e)
+            acc[e] += wq * (Gd[a][0] * Gd[b][0] + Gd[a][1] * Gd[b][1] + Gd[a][2] * Gd[b][2]);
+        double fh = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) fh += N[a] * s_f[warp][a];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) acc[36 + a] += wq * fh * N[a] * h3;
+        acc[44] += wq;
+      } else {
+        const int r = it - n_vol;
+        const double* T = G.tri[r / kTriPts];
+        const double* R = s_tri + (r % kTriPts) * 4;
+        const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+        const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+        const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
+        const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+        const double px = R[0] * T[0] + R[1] * T[3] + R[2] * T[6];
+        const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7];
+        const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8];
+        const double wq = R[3] * area;
+        double N[8];
+        q1_shape(px, py, pz, N);
+        double qx = 0, qy = 0, qz = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          qx += N[a] * s_q[warp][a][0];
+          qy += N[a] * s_q[warp][a][1];
+          qz += N[a] * s_q[warp][a][2];
+        }
+        const double gnv = qx * T[9] + qy * T[10] + qz * T[11];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) acc[36 + a] += wq * gnv * N[a] * h2;
       }
-      const int b = a + rem;
-      K_cut[kk * 64 + a * 8 + b] = s * g.h;
-      K_cut[kk * 64 + b * 8 + a] = s * g.h;
-    } else if (e < 44) {
-      load_cut[kk * 8 + (e - 36)] = s;
-    } else {
-      eta[kk] = s;
     }
+  }
+  // warp reduction (fixed tree) and output
+#pragma unroll
+  for (int e = 0; e < kAcc; ++e) {
+    double v = acc[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[e] = v;
+  }
+  if (valid && lane == 0) {
+    int e = 0;
+    for (int a = 0; a < 8; ++a)
+      for (int b = a; b < 8; ++b, ++e) {
+        K_cut[kc * 64 + a * 8 + b] = acc[e] * g.h;
+        K_cut[kc * 64 + b * 8 + a] = acc[e] * g.h;
+      }
+    for (int a = 0; a < 8; ++a) load_cut[kc * 8 + a] = acc[36 + a];
+    eta[kc] = acc[44];
   }
 }
 
@@ -351,7 +397,7 @@ void system_build(System& sys, const double* kappa, const double* f, const doubl
   sys.load_cut.alloc((n_cut > 0 ? n_cut : 1) * 8, s);
   sys.eta.alloc(n_cut > 0 ? n_cut : 1, s);
   if (n_cut > 0) {
-    k_integrate_cut<<<grid_for(n_cut, kCellsPerBlock), kCellsPerBlock * 6, 0, s>>>(
+    k_integrate_cut<<<grid_for(n_cut, kWarpsPerBlock), kWarpsPerBlock * 32, 0, s>>>(
         m.g, n_cut, m.cut_cells.p, m.phi.p, f, q, sys.K_cut.p, sys.load_cut.p, sys.eta.p);
     UFE_CHECK_LAUNCH();
   }

@@ -17,13 +17,18 @@
 // last CTA to finish (fixed summation order, deterministic).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "bddc.cuh"
 #include "q1.cuh"
 
 namespace ufe {
 
+namespace cg = cooperative_groups;
+
 constexpr int kApplyThreads = 256;
-constexpr int kSubThreads = 512;
+constexpr int kSubThreads = 256;
+constexpr int kCL = 4;   // CTAs (one thread-block cluster) per subdomain in the preconditioner stages
 
 // ---------------------------------------------------------------------------
 // reductions
@@ -272,14 +277,16 @@ __device__ __forceinline__ float dot_vec(const float4& a, const float* x) {
 }
 __device__ __forceinline__ double dot_vec(const double2& a, const double* x) { return a.x * x[0] + a.y * x[1]; }
 
-// ys[r] = sum_c M[r, c] xs[c] for r < m (row-major, ld a multiple of 4, xs zero-padded to ld)
+// ys[r] = sum_c M[r, c] xs[c] for r in [r0, r1) (row-major, ld a multiple of 4, xs
+// zero-padded to ld); each warp streams two rows at a time with 16-byte loads
 template <typename TM>
-__device__ void cta_gemv(const TM* __restrict__ M, int m, int ld, const TM* __restrict__ xs, double* __restrict__ ys) {
+__device__ void cta_gemv_rows(const TM* __restrict__ M, int r0, int r1, int ld, const TM* __restrict__ xs,
+                              double* __restrict__ ys) {
   using V = typename VecT<TM>::type;
   constexpr int VN = VecT<TM>::n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int r = wid;
-  for (; r + nw < m; r += 2 * nw) {
+  int r = r0 + wid;
+  for (; r + nw < r1; r += 2 * nw) {
     const TM* ra = M + (int64_t)r * ld;
     const TM* rb = M + (int64_t)(r + nw) * ld;
     TM sa = TM(0), sb = TM(0);
@@ -297,7 +304,7 @@ __device__ void cta_gemv(const TM* __restrict__ M, int m, int ld, const TM* __re
       ys[r + nw] = db;
     }
   }
-  for (; r < m; r += nw) {
+  for (; r < r1; r += nw) {
     const TM* ra = M + (int64_t)r * ld;
     TM sa = TM(0);
     for (int c = lane * VN; c < ld; c += 32 * VN) sa += dot_vec(*reinterpret_cast<const V*>(ra + c), xs + c);
@@ -379,41 +386,73 @@ __device__ SubSmem carve(char* smem, const SubMeta& sm, int ldImax, int ldGmax) 
   return s;
 }
 
+// The per-subdomain stages run as thread-block clusters of kCL CTAs per subdomain:
+// each CTA computes a contiguous slice of the rows of a local GEMV and the slices
+// are exchanged through distributed shared memory.
+__device__ __forceinline__ void row_slice(int n, int rank, int& b, int& e) {
+  b = (n * rank) / kCL;
+  e = (n * (rank + 1)) / kCL;
+}
+
+// copy the slices of `local` that the other CTAs of the cluster computed
+template <typename V>
+__device__ void cluster_gather(cg::cluster_group& cl, V* local, int n) {
+  const int me = (int)cl.block_rank();
+  for (int r = 0; r < kCL; ++r) {
+    if (r == me) continue;
+    int b, e;
+    row_slice(n, r, b, e);
+    const V* remote = cl.map_shared_rank(local, r);
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) local[i] = remote[i];
+  }
+}
+
 // K3: y_I = A_II^-1 r_I; t_G = A_GI y_I
 template <typename TM>
-__global__ void __launch_bounds__(kSubThreads)
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, double* __restrict__ tG,
                  const PcgScalars* sc, int ldImax, int ldGmax) {
   if (sc && sc->done) return;
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x;
+  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
   TM* xI = reinterpret_cast<TM*>(S.xT);
-  const int32_t* lmg = sm.lmap + (int64_t)w * sm.g.n_local_nodes;
-  for (int e = threadIdx.x; e < sm.g.n_local_nodes; e += blockDim.x) S.lm[e] = lmg[e];
   for (int p = threadIdx.x; p < z.ldI; p += blockDim.x) xI[p] = p < z.nI ? (TM)r[sm.I_list[sm.I_ptr[w] + p]] : TM(0);
   __syncthreads();
-  cta_gemv<TM>(AIIinv + sm.off_II[w], z.nI, z.ldI, xI, S.dI);
-  __syncthreads();
-  for (int ln = threadIdx.x; ln < sm.g.n_local_nodes; ln += blockDim.x) {
-    const int32_t code = S.lm[ln];
-    if (lmap_kind(code) != LKIND_G) continue;
-    const int lx = ln % sm.g.lnx, ly = (ln / sm.g.lnx) % sm.g.lny, lz = ln / (sm.g.lnx * sm.g.lny);
-    tG[sm.G_ptr[w] + lmap_index(code)] = local_stencil<LKIND_I>(sm, w, z.bi, z.bj, z.bk, lx, ly, lz, S.lm, S.dI);
+  int r0, r1;
+  row_slice(z.nI, rank, r0, r1);
+  cta_gemv_rows<TM>(AIIinv + sm.off_II[w], r0, r1, z.ldI, xI, S.dI);
+  cl.sync();
+  cluster_gather(cl, S.dI, z.nI);
+  cl.sync();
+  int j0, j1;
+  row_slice(z.nG, rank, j0, j1);
+  const int64_t e0 = 27 * (int64_t)sm.G_ptr[w];
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    double t = 0.0;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const int32_t k = sm.gi_k[e0 + (int64_t)o * z.nG + j];
+      if (k >= 0) t += sm.gi_v[e0 + (int64_t)o * z.nG + j] * S.dI[k];
+    }
+    tG[sm.G_ptr[w] + j] = t;
   }
 }
 
 // K4: r~ = w (r_G - sum t_G); v = K r~ (stored weighted: vw = w v); g = Phi^T r~
 template <typename TM>
-__global__ void __launch_bounds__(kSubThreads)
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Phi, const double* __restrict__ r,
                const double* __restrict__ tG, double* __restrict__ vw, double* __restrict__ gC, const PcgScalars* sc,
                int ldImax, int ldGmax) {
   if (sc && sc->done) return;
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
   __shared__ double gpart[kSubThreads / 32][64];
-  const int w = blockIdx.x;
+  __shared__ double gsum[1024];
+  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0) return;
   SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
@@ -431,13 +470,15 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
     xG[j] = v;
   }
   __syncthreads();
-  cta_gemv<TM>(Kop + sm.off_GG[w], z.nG, z.ldG, xG, S.dG);
-  // g = Phi^T r~ : warps split the rows, lanes the coarse columns (nC <= 1024, chunks of 64)
+  int r0, r1;
+  row_slice(z.nG, rank, r0, r1);
+  cta_gemv_rows<TM>(Kop + sm.off_GG[w], r0, r1, z.ldG, xG, S.dG);
+  // partial g = Phi^T r~ over this CTA's rows: warps split the rows, lanes the columns
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const TM* P = Phi + sm.off_GC[w];
   for (int c0 = 0; c0 < z.nC; c0 += 64) {
     double a0 = 0.0, a1 = 0.0;
-    for (int j = wid; j < z.nG; j += nw) {
+    for (int j = r0 + wid; j < r1; j += nw) {
       const double xj = (double)xG[j];
       if (c0 + lane < z.nC) a0 += (double)P[(int64_t)j * z.ldC + c0 + lane] * xj;
       if (c0 + lane + 32 < z.nC) a1 += (double)P[(int64_t)j * z.ldC + c0 + lane + 32] * xj;
@@ -446,13 +487,22 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
     gpart[wid][lane + 32] = a1;
     __syncthreads();
     if (threadIdx.x < 64 && c0 + (int)threadIdx.x < z.nC) {
-      double s = 0.0;
-      for (int x = 0; x < nw; ++x) s += gpart[x][threadIdx.x];
-      gC[sm.C_ptr[w] + c0 + threadIdx.x] = s;
+      double sacc = 0.0;
+      for (int x = 0; x < nw; ++x) sacc += gpart[x][threadIdx.x];
+      gsum[c0 + threadIdx.x] = sacc;
     }
     __syncthreads();
   }
-  for (int j = threadIdx.x; j < z.nG; j += blockDim.x) vw[g0 + j] = sm.w[g0 + j] * S.dG[j];
+  for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) vw[g0 + j] = sm.w[g0 + j] * S.dG[j];
+  cl.sync();
+  if (rank == 0) {
+    for (int c = threadIdx.x; c < z.nC; c += blockDim.x) {
+      double sacc = 0.0;
+      for (int q = 0; q < kCL; ++q) sacc += cl.map_shared_rank(gsum, q)[c];
+      gC[sm.C_ptr[w] + c] = sacc;
+    }
+  }
+  cl.sync();
 }
 
 // K5: r_c gathered from the subdomain parts, u_c = A_c^-1 r_c (FP64)
@@ -482,58 +532,86 @@ __global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ 
   }
 }
 
-// K7: u_G = sum_w' (vw + w Phi u_c); z_G = u_G (owner writes); z_I = A_II^-1 (r_I - A_IG u_G)
+// K6: coarse prolongation, vw += w Phi u_c^w on the interface rows of w
 template <typename TM>
-__global__ void __launch_bounds__(kSubThreads)
-k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const TM* __restrict__ Phi, const double* __restrict__ r,
-             const double* __restrict__ vw, const double* __restrict__ uc, double* __restrict__ z,
-             double* __restrict__ part, PcgScalars* sc, int ldImax, int ldGmax, int with_dots) {
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
+k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict__ uc, double* __restrict__ vw,
+               const PcgScalars* sc, int ldImax, int ldGmax) {
   if (sc && sc->done) return;
+  cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x;
+  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
+  const SubSizes z = sub_sizes(sm, w);
+  if (z.nG == 0 || z.nC == 0) return;
+  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  TM* xc = reinterpret_cast<TM*>(S.xT);
+  for (int c = threadIdx.x; c < z.ldC; c += blockDim.x) xc[c] = c < z.nC ? (TM)uc[sm.C_list[sm.C_ptr[w] + c]] : TM(0);
+  __syncthreads();
+  int j0, j1;
+  row_slice(z.nG, rank, j0, j1);
+  cta_gemv_rows<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
+  __syncthreads();
+  const int g0 = sm.G_ptr[w];
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vw[g0 + j] += sm.w[g0 + j] * S.dG[j];
+}
+
+// K7: u_G = sum_w' w' (v + Phi u_c) (the weighted local values, W); z_G = u_G (the
+// owner writes); z_I = A_II^-1 (r_I - A_IG u_G) (harmonic extension)
+template <typename TM>
+__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
+k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, const double* __restrict__ vw,
+             double* __restrict__ z, double* __restrict__ part, PcgScalars* sc, int ldImax, int ldGmax,
+             int with_dots) {
+  if (sc && sc->done) return;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) char smem[];
+  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes zz = sub_sizes(sm, w);
   SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
   TM* xI = reinterpret_cast<TM*>(S.xT);
-  const int32_t* lmg = sm.lmap + (int64_t)w * sm.g.n_local_nodes;
-  for (int e = threadIdx.x; e < sm.g.n_local_nodes; e += blockDim.x) S.lm[e] = lmg[e];
   double rz = 0.0, rzo = 0.0;
   const int g0 = sm.G_ptr[w];
+  // the whole interface vector of w (cheap gathers, computed by every CTA)
   for (int j = threadIdx.x; j < zz.nG; j += blockDim.x) {
     const int32_t xi = sm.G_list[g0 + j];
     const int cnt = sm.n_neigh[xi];
     double u = 0.0;
-    for (int k = 0; k < cnt; ++k) {
-      const int32_t slot = sm.gpos[(int64_t)xi * 8 + k];
-      const int wk = sm.neigh[(int64_t)xi * 8 + k];
-      const int c0 = sm.C_ptr[wk], nC = sm.C_ptr[wk + 1] - c0, ldC = pad4(nC);
-      const TM* prow = Phi + sm.off_GC[wk] + (int64_t)(slot - sm.G_ptr[wk]) * ldC;
-      double cu = 0.0;
-      for (int c = 0; c < nC; ++c) cu += (double)prow[c] * uc[sm.C_list[c0 + c]];
-      u += vw[slot] + sm.w[slot] * cu;
-    }
+    for (int k = 0; k < cnt; ++k) u += vw[sm.gpos[(int64_t)xi * 8 + k]];
     S.dG[j] = u;
-    if (sm.neigh[(int64_t)xi * 8] == w) {
-      if (with_dots) {
-        rz += r[xi] * u;
-        rzo += r[xi] * z[xi];
-      }
-      z[xi] = u;
-    }
   }
   __syncthreads();
-  for (int ln = threadIdx.x; ln < sm.g.n_local_nodes; ln += blockDim.x) {
-    const int32_t code = S.lm[ln];
-    if (lmap_kind(code) != LKIND_I) continue;
-    const int p = lmap_index(code);
-    const int lx = ln % sm.g.lnx, ly = (ln / sm.g.lnx) % sm.g.lny, lz = ln / (sm.g.lnx * sm.g.lny);
-    const double rhs = r[sm.I_list[sm.I_ptr[w] + p]] - local_stencil<LKIND_G>(sm, w, zz.bi, zz.bj, zz.bk, lx, ly, lz, S.lm, S.dG);
-    xI[p] = (TM)rhs;
+  int j0, j1;
+  row_slice(zz.nG, rank, j0, j1);
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const int32_t xi = sm.G_list[g0 + j];
+    if (sm.neigh[(int64_t)xi * 8] != w) continue;
+    const double u = S.dG[j];
+    if (with_dots) {
+      rz += r[xi] * u;
+      rzo += r[xi] * z[xi];
+    }
+    z[xi] = u;
+  }
+  // interior right-hand side r_I - A_IG u_G for this CTA's rows, then exchanged
+  int p0, p1;
+  row_slice(zz.nI, rank, p0, p1);
+  const int64_t e0 = 27 * (int64_t)sm.I_ptr[w];
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    double t = 0.0;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const int32_t k = sm.ig_k[e0 + (int64_t)o * zz.nI + p];
+      if (k >= 0) t += sm.ig_v[e0 + (int64_t)o * zz.nI + p] * S.dG[k];
+    }
+    xI[p] = (TM)(r[sm.I_list[sm.I_ptr[w] + p]] - t);
   }
   for (int p = zz.nI + threadIdx.x; p < zz.ldI; p += blockDim.x) xI[p] = TM(0);
+  cl.sync();
+  cluster_gather(cl, xI, zz.nI);
+  cl.sync();
+  cta_gemv_rows<TM>(AIIinv + sm.off_II[w], p0, p1, zz.ldI, xI, S.dI);
   __syncthreads();
-  cta_gemv<TM>(AIIinv + sm.off_II[w], zz.nI, zz.ldI, xI, S.dI);
-  __syncthreads();
-  for (int p = threadIdx.x; p < zz.nI; p += blockDim.x) {
+  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const int32_t d = sm.I_list[sm.I_ptr[w] + p];
     const double zn = S.dI[p];
     if (with_dots) {
@@ -546,8 +624,8 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const TM* __restrict__ P
   rz = block_sum(rz);
   rzo = block_sum(rzo);
   if (threadIdx.x == 0) {
-    part[2 * w] = rz;
-    part[2 * w + 1] = rzo;
+    part[2 * blockIdx.x] = rz;
+    part[2 * blockIdx.x + 1] = rzo;
   }
   if (arrive_last(&sc->counter[3])) {
     const double a = sum_partials(part, gridDim.x, 2);
@@ -601,9 +679,9 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
   const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
-  k_prec_interior1<TM><<<ns, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, ldI, ldG);
+  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, ldI, ldG);
   UFE_CHECK_LAUNCH();
-  k_prec_neumann<TM><<<ns, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, ldI, ldG);
+  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, ldI, ldG);
   UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
     const size_t csm = (size_t)B.ldc * 8;
@@ -611,7 +689,11 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
     k_coarse_solve<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, B.gC.p, B.uc.p, sc);
     UFE_CHECK_LAUNCH();
   }
-  k_prec_final<TM><<<ns, kSubThreads, smem, s>>>(sm, II, GC, r, B.vw.p, B.uc.p, z, B.part.p, sc, ldI, ldG, with_dots);
+  if (B.n_coarse > 0) {
+    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, ldI, ldG);
+    UFE_CHECK_LAUNCH();
+  }
+  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, ldI, ldG, with_dots);
   UFE_CHECK_LAUNCH();
 }
 
@@ -620,6 +702,8 @@ static void set_smem_limits(Bddc& B) {
   UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_prolong<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_prolong<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
