@@ -365,8 +365,32 @@ ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* B, const double* b, double* 
 ufe_status ufe_adjoint(ufe_system* sys, ufe_bddc* B, const double* u, const double* dJdu, double* lambda,
                        double* dJdkappa, int mem, const ufe_solve_opts* opts, ufe_solve_info* info) {
   return guarded([&] {
-    (void)sys; (void)B; (void)u; (void)dJdu; (void)lambda; (void)dJdkappa; (void)mem; (void)opts; (void)info;
-    throw Error{UFE_ERR_UNSUPPORTED, "ufe_adjoint is not built yet"};
+    UFE_REQUIRE(sys && B && u && dJdu && lambda && dJdkappa && opts, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(B->sys == sys, UFE_ERR_INVALID_ARG, "preconditioner belongs to another system");
+    UFE_REQUIRE(opts->rtol > 0 && opts->maxit >= 0, UFE_ERR_INVALID_ARG, "bad solve options");
+    check_mem(mem);
+    cudaStream_t s = sys->stream;
+    const int64_t n = sys->mesh->n_dof, nc = sys->mesh->g.n_cells();
+    DBuf<double> ub, jb, lb, gb;
+    const double* ud = stage(ub, u, n, mem, s);
+    const double* jd = stage(jb, dJdu, n, mem, s);
+    double* ld = lambda;
+    double* gd = dJdkappa;
+    if (mem == UFE_MEM_HOST) {
+      lb.alloc(n, s);
+      copy_in(lb.p, lambda, n * 8, mem, s);
+      ld = lb.p;
+      gb.alloc(nc, s);
+      gd = gb.p;
+    }
+    // A is symmetric positive definite, so the adjoint solve reuses the same BDDC-PCG
+    pcg_solve(*B, jd, ld, *opts, info);
+    kappa_gradient(*sys, ud, ld, gd, s);
+    if (mem == UFE_MEM_HOST) {
+      copy_out(lambda, ld, n * 8, mem, s);
+      copy_out(dJdkappa, gd, nc * 8, mem, s);
+    }
+    UFE_CUDA(cudaStreamSynchronize(s));
   });
 }
 

@@ -401,6 +401,11 @@ void system_build(System& sys, const double* kappa, const double* f, const doubl
         m.g, n_cut, m.cut_cells.p, m.phi.p, f, q, sys.K_cut.p, sys.load_cut.p, sys.eta.p);
     UFE_CHECK_LAUNCH();
   }
+  sys.gnode.alloc(m.g.n_nodes(), s);
+  if (gval)
+    UFE_CUDA(cudaMemcpyAsync(sys.gnode.p, gval, m.g.n_nodes() * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    sys.gnode.zero();
   sys.b.alloc(m.n_dof, s);
   k_rhs<<<grid_for(m.n_dof, 128), 128, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p,
                                                m.cut_index.p, sys.K_cut.p, sys.load_cut.p, kappa, f, gval,

@@ -654,6 +654,46 @@ static OpArgs op_args(const System& sys) {
   return a;
 }
 
+// adjoint contraction (no counterpart in the paper): with A = sum_e kappa_e Khat_e and
+// b independent of kappa, dJ/dkappa_e = -ubar_e^T Khat_e lambda_e, where ubar holds the
+// free values u and the Dirichlet values at constrained nodes and lambda vanishes there
+__global__ void k_kappa_gradient(OpArgs a, const double* __restrict__ u, const double* __restrict__ lam,
+                                 const double* __restrict__ gnode, double* __restrict__ out) {
+  const GridGeom& g = a.g;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n_cells()) return;
+  const uint8_t t = a.cell_type[c];
+  if (t == UFE_CELL_EXTERNAL) {
+    out[c] = 0.0;
+    return;
+  }
+  const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+  double ue[8], le[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const int64_t node = g.node(i + (v & 1), j + ((v >> 1) & 1), k + (v >> 2));
+    const int32_t d = a.dof_of_node[node];
+    ue[v] = d >= 0 ? u[d] : gnode[node];
+    le[v] = d >= 0 ? lam[d] : 0.0;
+  }
+  const double* Kc = t == UFE_CELL_CUT ? a.K_cut + (int64_t)a.cut_index[c] * 64 : nullptr;
+  double sacc = 0.0;
+#pragma unroll
+  for (int va = 0; va < 8; ++va) {
+    double row = 0.0;
+#pragma unroll
+    for (int vb = 0; vb < 8; ++vb) row += (Kc ? Kc[va * 8 + vb] : g.h * q1_khat(va, vb)) * le[vb];
+    sacc += ue[va] * row;
+  }
+  out[c] = -sacc;
+}
+
+void kappa_gradient(const System& sys, const double* u_dev, const double* lambda_dev, double* out_dev, cudaStream_t s) {
+  const OpArgs a = op_args(sys);
+  k_kappa_gradient<<<grid_for(a.g.n_cells(), 256), 256, 0, s>>>(a, u_dev, lambda_dev, sys.gnode.p, out_dev);
+  UFE_CHECK_LAUNCH();
+}
+
 void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStream_t s) {
   const OpArgs a = op_args(sys);
   k_apply<<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);

@@ -177,6 +177,7 @@ struct System {
   DBuf<double> load_cut;    // n_cut * 8
   DBuf<double> eta;         // n_cut
   DBuf<double> b;           // n_dof
+  DBuf<double> gnode;       // n_nodes: Dirichlet values read at constrained nodes (zeros if none given)
 };
 
 struct Bddc;   // defined in bddc.cu
@@ -192,6 +193,8 @@ int64_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets_out, cuda
 void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node);
 void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* g);
 void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStream_t s);
+// dJ/dkappa_e = -ubar_e^T Khat_e lambda_e per cell (ubar: u with the Dirichlet values)
+void kappa_gradient(const System& sys, const double* u_dev, const double* lambda_dev, double* out_dev, cudaStream_t s);
 
 // constant tables (Q1 reference matrices, quadrature) uploaded once
 void ensure_constants();
