@@ -35,6 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "BDDC-PCG time-to-solution (s) and DOF-iters/s at rtol 1e-8, mixed vs FP64 on 1 GB300"
 RTOL = 1e-8
 
+# ALU peaks from unit counts and clocks (no measured FP32/FP64 SIMT peak is available):
+# FP64 1.25 TFLOP/s nominal for GB300; FP32 SIMT 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
+PEAK_FP64_TFLOPS = 1.25
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/ summary named
+# in the design doc); None once the kernel has changed since the counters were taken.
+TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": None, "gj_update_f32": None}
+
 
 def parse_args():
     ap = argparse.ArgumentParser()
@@ -260,7 +268,12 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
+    U.ufe_timing_reset()
+    U.ufe_timing_enable(True)
     t_mixed, i_mixed, launches = timed("mixed", args.steps)
+    U.ufe_timing_enable(False)
+    kt = {k: U.ufe_timing_get(k) for k in ("gj_update_f64", "gj_update_f32", "integrate_cut")}
+    U.ufe_timing_reset()
     clk_stats = clk.stop()
     t_fp64, i_fp64, _ = timed("fp64", args.fp64_steps) if args.fp64_steps > 0 else ([float("nan")], [None], 0)
     if world > 1:
@@ -296,6 +309,21 @@ def run_ours(args, rank, world):
     else:
         n64, info64 = n, {"iterations": 0, "true_rel_residual": None}
 
+    # roofline of the dominant instrumented kernel (the Gauss-Jordan update steps are
+    # ALU bound: symmetric inversion of an n x n matrix takes n^3 flops)
+    flops = {"gj_update_f64": binfo["inverse_flops_coarse"], "gj_update_f32": binfo["inverse_flops_local"]}
+    peaks = {"gj_update_f64": PEAK_FP64_TFLOPS, "gj_update_f32": PEAK_FP32_TFLOPS}
+    dom = max(flops, key=lambda k: kt[k][0])
+    ms_tot, n_launch = kt[dom]
+    per_launch_flops = flops[dom] * args.steps / max(n_launch, 1)
+    avg_s = ms_tot / 1e3 / max(n_launch, 1)
+    achieved = per_launch_flops / avg_s / 1e12 if avg_s > 0 else None
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peaks[dom], "unit": "TFLOP/s",
+                "frac": achieved / peaks[dom] if achieved else None, "traffic": TRAFFIC_BYTES_PER_LAUNCH[dom],
+                "peak_source": "derived from unit counts and clocks (FP64: 1.25 TFLOP/s nominal)",
+                "launches": n_launch, "avg_launch_us": avg_s * 1e6,
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()}}
+
     line = {
         "metric": METRIC,
         "value": mean_mixed / world,
@@ -324,6 +352,7 @@ def run_ours(args, rank, world):
                  "true_rel_residual": info64["true_rel_residual"]},
         "true_rel_residual": info["true_rel_residual"],
         "gpu_launches": launches,
+        "roofline": roofline,
         "clocks": clk_stats,
         "e2e": {"value": e2e_mean / world, "unit": "s",
                 "h2d_bytes_per_step": int(p.phi.nbytes + p.f.nbytes + 8 * n),

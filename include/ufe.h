@@ -94,6 +94,19 @@ int ufe_version(void);
  * counterpart. */
 int64_t ufe_kernel_launches(void);
 
+/* Kernel timing (instrumentation only; no paper counterpart).  While enabled, the
+ * library brackets every launch of the named set-up kernels with CUDA events on
+ * the stream it launches them on:
+ *   "gj_update_f64"  FP64 Gauss-Jordan update step (coarse matrix; local matrices in FP64 mode)
+ *   "gj_update_f32"  FP32 Gauss-Jordan update step (local matrices in mixed precision)
+ *   "integrate_cut"  marching-tetrahedra cut-cell integration
+ * ufe_timing_get sums the elapsed device time (ms) and the launch count of one
+ * name since the last reset (it synchronises on the recorded events).
+ * Unknown names return UFE_ERR_INVALID_ARG. */
+void ufe_timing_enable(int on);
+void ufe_timing_reset(void);
+ufe_status ufe_timing_get(const char* kernel, double* total_ms, int64_t* launches);
+
 typedef struct {
   int64_t n_nodes, n_cells;
   int64_t n_active_cells, n_cut_cells;
@@ -185,6 +198,8 @@ typedef struct {
   int64_t n_coarse;               /* coarse DOFs (objects in Lambda_O) */
   int32_t max_local_coarse;       /* largest number of coarse DOFs of one subdomain */
   double setup_ms;                /* device time of ufe_bddc_setup */
+  double inverse_flops_local;     /* sum of n^3 over the inverted local matrices (A_II, S', S_c) */
+  double inverse_flops_coarse;    /* n_coarse^3 (symmetric Gauss-Jordan, algorithmic count) */
 } ufe_bddc_info;
 
 /*

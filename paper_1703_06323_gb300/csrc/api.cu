@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 
 #include "bddc.cuh"
@@ -15,6 +16,33 @@ namespace ufe {
 static thread_local std::string g_last_error;
 std::atomic<long long> g_kernel_launches{0};
 thread_local long long* g_capture_counter = nullptr;
+
+// ---- kernel timing -------------------------------------------------------------
+namespace {
+std::mutex g_tmu;
+bool g_timing = false;
+struct TRec {
+  std::string name;
+  cudaEvent_t e0, e1;
+};
+std::vector<TRec> g_trecs;
+}  // namespace
+
+void TimedLaunch::begin(const char* nm, cudaStream_t s) {
+  if (!g_timing) return;
+  name = nm;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+}
+
+void TimedLaunch::end(cudaStream_t s) {
+  if (!e0) return;
+  cudaEventRecord(e1, s);
+  std::lock_guard<std::mutex> lock(g_tmu);
+  g_trecs.push_back({name, e0, e1});
+  e0 = e1 = nullptr;
+}
 
 void note_launch() {
   if (g_capture_counter)
@@ -81,6 +109,40 @@ const char* ufe_last_error(void) { return g_last_error.c_str(); }
 int ufe_version(void) { return 100; }
 
 int64_t ufe_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
+
+void ufe_timing_enable(int on) { g_timing = on != 0; }
+
+void ufe_timing_reset(void) {
+  std::lock_guard<std::mutex> lock(g_tmu);
+  for (auto& r : g_trecs) {
+    cudaEventSynchronize(r.e1);
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  g_trecs.clear();
+}
+
+ufe_status ufe_timing_get(const char* kernel, double* total_ms, int64_t* launches) {
+  return guarded([&] {
+    UFE_REQUIRE(kernel && total_ms && launches, UFE_ERR_INVALID_ARG, "null argument");
+    const std::string k(kernel);
+    UFE_REQUIRE(k == "gj_update_f64" || k == "gj_update_f32" || k == "integrate_cut", UFE_ERR_INVALID_ARG,
+                "unknown timed kernel");
+    std::lock_guard<std::mutex> lock(g_tmu);
+    double tot = 0.0;
+    int64_t n = 0;
+    for (auto& r : g_trecs) {
+      if (r.name != k) continue;
+      UFE_CUDA(cudaEventSynchronize(r.e1));
+      float ms = 0.f;
+      UFE_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+      tot += ms;
+      ++n;
+    }
+    *total_ms = tot;
+    *launches = n;
+  });
+}
 
 ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const int32_t cells[3],
                            const int32_t sub_cells[3], const double* phi_nodes, int mem, uint32_t dirichlet_face_mask,
@@ -286,6 +348,8 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->n_coarse = B->n_coarse;
     info->max_local_coarse = B->max_nC;
     info->setup_ms = B->setup_ms;
+    info->inverse_flops_local = B->inv_flops_local;
+    info->inverse_flops_coarse = B->inv_flops_coarse;
   });
 }
 

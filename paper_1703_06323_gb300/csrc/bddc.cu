@@ -17,6 +17,7 @@
 // mixed precision the scaled matrices are inverted and stored in FP32.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <memory>
 
 #include "bddc.cuh"
@@ -920,6 +921,10 @@ void bddc_build(Bddc& B) {
     B.max_nC = std::max(B.max_nC, B.h_nC[w]);
   }
   UFE_REQUIRE(B.max_nC <= 1024, UFE_ERR_UNSUPPORTED, "more than 1024 coarse DOFs in one subdomain");
+  B.inv_flops_local = 0.0;
+  for (int w = 0; w < ns; ++w)
+    B.inv_flops_local += std::pow((double)B.h_nI[w], 3) + std::pow((double)B.h_nG[w], 3) + std::pow((double)B.h_nC[w], 3);
+  B.inv_flops_coarse = std::pow((double)B.n_coarse, 3);
 
   // structural singularity: a floating subdomain (no constrained node) without coarse DOFs
   {

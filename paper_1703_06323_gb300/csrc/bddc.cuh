@@ -90,6 +90,7 @@ struct Bddc {
   long long graph_kernels = 0;         // kernel nodes in the captured chunk
   int64_t part_blocks = 0;
   double setup_ms = 0.0;
+  double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
 
   SubMeta meta() const;
   ~Bddc();

@@ -421,8 +421,11 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
     T* Dn = Dbuf[(step + 1) & 1];
     k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s>>>(bt, step, base, R.p, Q.p, Dc);
     UFE_CHECK_LAUNCH();
+    TimedLaunch tl;
+    tl.begin(sizeof(T) == 8 ? "gj_update_f64" : "gj_update_f32", s);
     k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, R.p, Q.p, Dc, Dn, status);
     UFE_CHECK_LAUNCH();
+    tl.end(s);
   }
 }
 

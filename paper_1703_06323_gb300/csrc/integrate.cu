@@ -397,9 +397,12 @@ void system_build(System& sys, const double* kappa, const double* f, const doubl
   sys.load_cut.alloc((n_cut > 0 ? n_cut : 1) * 8, s);
   sys.eta.alloc(n_cut > 0 ? n_cut : 1, s);
   if (n_cut > 0) {
+    TimedLaunch tl;
+    tl.begin("integrate_cut", s);
     k_integrate_cut<<<grid_for(n_cut, kWarpsPerBlock), kWarpsPerBlock * 32, 0, s>>>(
         m.g, n_cut, m.cut_cells.p, m.phi.p, f, q, sys.K_cut.p, sys.load_cut.p, sys.eta.p);
     UFE_CHECK_LAUNCH();
+    tl.end(s);
   }
   sys.gnode.alloc(m.g.n_nodes(), s);
   if (gval)

@@ -199,6 +199,14 @@ void kappa_gradient(const System& sys, const double* u_dev, const double* lambda
 // constant tables (Q1 reference matrices, quadrature) uploaded once
 void ensure_constants();
 
+// optional event timing of named kernels (see ufe_timing_enable)
+struct TimedLaunch {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void begin(const char* name, cudaStream_t s);
+  void end(cudaStream_t s);
+  const char* name = nullptr;
+};
+
 // launch accounting state
 extern std::atomic<long long> g_kernel_launches;
 extern thread_local long long* g_capture_counter;   // non-null while a graph is being captured

@@ -50,7 +50,8 @@ class BddcOpts(ctypes.Structure):
 class BddcInfo(ctypes.Structure):
     _fields_ = [("n_objects", ctypes.c_int64), ("n_corners", ctypes.c_int64), ("n_edges", ctypes.c_int64),
                 ("n_faces", ctypes.c_int64), ("n_coarse", ctypes.c_int64), ("max_local_coarse", ctypes.c_int32),
-                ("setup_ms", ctypes.c_double)]
+                ("setup_ms", ctypes.c_double), ("inverse_flops_local", ctypes.c_double),
+                ("inverse_flops_coarse", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -73,6 +74,10 @@ def _load():
         "ufe_last_error": (ctypes.c_char_p, []),
         "ufe_version": (ctypes.c_int, []),
         "ufe_kernel_launches": (ctypes.c_int64, []),
+        "ufe_timing_enable": (None, [ctypes.c_int]),
+        "ufe_timing_reset": (None, []),
+        "ufe_timing_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64)]),
         "ufe_mesh_create": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, U32, I64, P, ctypes.POINTER(P)]),
         "ufe_mesh_get_info": (ctypes.c_int, [P, ctypes.POINTER(MeshInfo)]),
         "ufe_mesh_get_cell_types": (ctypes.c_int, [P, P, ctypes.c_int]),
@@ -103,7 +108,8 @@ def _load():
 
 
 LIB = _load()
-EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
+EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_enable", "ufe_timing_reset",
+            "ufe_timing_get", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
             "ufe_assemble", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
@@ -158,6 +164,21 @@ def ufe_version():
 
 def ufe_kernel_launches():
     return LIB.ufe_kernel_launches()
+
+
+def ufe_timing_enable(on=True):
+    LIB.ufe_timing_enable(1 if on else 0)
+
+
+def ufe_timing_reset():
+    LIB.ufe_timing_reset()
+
+
+def ufe_timing_get(kernel):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(LIB.ufe_timing_get(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def ufe_mesh_create(box_lo, box_hi, cells, sub_cells, phi_nodes, dirichlet_face_mask=0, pin_node=PIN_AUTO,
