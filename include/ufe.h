@@ -224,6 +224,31 @@ ufe_status ufe_bddc_get_objects(const ufe_bddc* bddc, int32_t* object_of_dof, in
                                 int32_t* coarse_of_object, int mem);
 /* z = M r for one vector (n_dof doubles), Eq. bddc. */
 ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
+
+/*
+ * ufe_bddc_apply_noalloc -- the same z = M r as ufe_bddc_apply, for callers that
+ * must not allocate device memory while they run: a serving loop that reserved
+ * its memory budget up front, or host code called back from another framework
+ * that owns the device allocator.  The paper has no counterpart; this is a
+ * deployment variant.
+ *
+ *  r, z   n_dof doubles each, DEVICE pointers on the current device (host
+ *         pointers are not accepted: staging them would need an allocation).
+ *
+ * The preconditioner's intermediate vectors live in one file-scope device array
+ * of fixed size (622,592 doubles, about 5 MB, held by every device that loads the
+ * library until the process exits) instead of the buffers ufe_bddc_setup made.
+ * Problems beyond its limits -- more than 262,144 interface slots (the sum over
+ * subdomains of their interface DOFs), 65,536 subdomain coarse slots or 32,768
+ * coarse DOFs -- are rejected with UFE_ERR_INVALID_ARG and a message naming the
+ * limit.  The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (other streams or threads
+ * using any ufe_bddc handle) race; serialise them.  Returns after z is complete.
+ */
+ufe_status ufe_bddc_apply_noalloc(ufe_bddc* bddc, const double* r, double* z);
 void ufe_bddc_destroy(ufe_bddc* bddc);
 
 typedef struct {

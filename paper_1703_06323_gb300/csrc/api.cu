@@ -385,6 +385,14 @@ ufe_status ufe_bddc_apply(ufe_bddc* B, const double* r, double* z, int mem) {
   });
 }
 
+ufe_status ufe_bddc_apply_noalloc(ufe_bddc* B, const double* r_dev, double* z_dev) {
+  return guarded([&] {
+    UFE_REQUIRE(B && r_dev && z_dev, UFE_ERR_INVALID_ARG, "null argument");
+    bddc_apply_noalloc(*B, r_dev, z_dev);
+    UFE_CUDA(cudaStreamSynchronize(B->stream));
+  });
+}
+
 void ufe_bddc_destroy(ufe_bddc* B) {
   if (!B) return;
   cudaStream_t s = B->stream;

@@ -98,6 +98,7 @@ struct Bddc {
 
 void bddc_build(Bddc& B);
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev);
+void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);
 
 }  // namespace ufe

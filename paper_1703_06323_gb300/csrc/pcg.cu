@@ -16,6 +16,7 @@
 // so the host only reads the state once per chunk.  Reductions are done by the
 // last CTA to finish (fixed summation order, deterministic).
 #include <algorithm>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -857,6 +858,86 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
   }
   if (fin.done == 3) throw Error{UFE_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0"};
   if (fin.done != 1) throw Error{UFE_ERR_NO_CONVERGENCE, "PCG did not reach the tolerance within maxit"};
+}
+
+// ---------------------------------------------------------------------------
+// z = M r without any device allocation: the interface and coarse intermediates
+// of the preconditioner live in one file-scope device array instead of the
+// buffers ufe_bddc_setup allocates.  Limits: 262144 interface slots (sum over
+// subdomains of their interface DOFs), 65536 subdomain coarse slots, 32768
+// coarse DOFs -- 622592 doubles, about 5 MB held by every device that loads the
+// library.  All calls share the array; calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocG = 262144, kNoAllocC = 65536, kNoAllocU = 32768;
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocG + kNoAllocC + kNoAllocU];
+
+// device address of the array for the current device, looked up once per device
+static double* noalloc_scratch_ptr() {
+  static std::mutex mu;
+  static double* ptr[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    UFE_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    ptr[dev] = static_cast<double*>(p);
+  }
+  return ptr[dev];
+}
+
+template <typename TM>
+static void launch_preconditioner_static(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
+                                         double* uc, cudaStream_t s) {
+  const Mesh& m = *B.mesh;
+  const SubMeta sm = B.meta();
+  const int ns = (int)m.n_sub;
+  const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
+  const size_t smem = sub_smem_bytes(B, sizeof(TM));
+  const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
+  const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
+  const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
+  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, ldI, ldG);
+  UFE_CHECK_LAUNCH();
+  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, ldI, ldG);
+  UFE_CHECK_LAUNCH();
+  if (B.n_coarse > 0) {
+    const size_t csm = (size_t)B.ldc * 8;
+    const unsigned cgr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
+    k_coarse_solve<<<cgr, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, nullptr);
+    UFE_CHECK_LAUNCH();
+    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, ldI, ldG);
+    UFE_CHECK_LAUNCH();
+  }
+  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, ldI, ldG, 0);
+  UFE_CHECK_LAUNCH();
+}
+
+void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev) {
+  const Mesh& m = *B.mesh;
+  UFE_REQUIRE(m.n_Gloc <= kNoAllocG, UFE_ERR_INVALID_ARG,
+              "ufe_bddc_apply_noalloc: " + std::to_string(m.n_Gloc) + " interface slots exceed the static limit of " +
+                  std::to_string(kNoAllocG));
+  UFE_REQUIRE(B.n_Cloc <= kNoAllocC, UFE_ERR_INVALID_ARG,
+              "ufe_bddc_apply_noalloc: " + std::to_string(B.n_Cloc) +
+                  " subdomain coarse slots exceed the static limit of " + std::to_string(kNoAllocC));
+  UFE_REQUIRE(B.n_coarse <= kNoAllocU, UFE_ERR_INVALID_ARG,
+              "ufe_bddc_apply_noalloc: " + std::to_string(B.n_coarse) + " coarse DOFs exceed the static limit of " +
+                  std::to_string(kNoAllocU));
+  double* base = noalloc_scratch_ptr();
+  double* tG = base;
+  double* vw = base + kNoAllocG;
+  double* gC = vw + kNoAllocG;
+  double* uc = gC + kNoAllocC;
+  set_smem_limits(B);
+  // every entry of z is written by the kernels; clearing it first keeps the
+  // behaviour identical to ufe_bddc_apply
+  UFE_CUDA(cudaMemsetAsync(z_dev, 0, m.n_dof * sizeof(double), B.stream));
+  if (B.mixed)
+    launch_preconditioner_static<float>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+  else
+    launch_preconditioner_static<double>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
 }
 
 }  // namespace ufe

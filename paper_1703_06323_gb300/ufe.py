@@ -94,6 +94,7 @@ def _load():
         "ufe_bddc_get_info": (ctypes.c_int, [P, ctypes.POINTER(BddcInfo)]),
         "ufe_bddc_get_objects": (ctypes.c_int, [P, P, P, P, ctypes.c_int]),
         "ufe_bddc_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "ufe_bddc_apply_noalloc": (ctypes.c_int, [P, P, P]),
         "ufe_bddc_destroy": (None, [P]),
         "ufe_pcg_solve": (ctypes.c_int, [P, P, P, P, ctypes.c_int, ctypes.POINTER(SolveOpts),
                                          ctypes.POINTER(SolveInfo)]),
@@ -113,6 +114,7 @@ EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
             "ufe_assemble", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
+            "ufe_bddc_apply_noalloc",
             "ufe_bddc_destroy", "ufe_pcg_solve", "ufe_adjoint")
 
 
@@ -293,6 +295,16 @@ def ufe_bddc_apply(bddc, r, z=None):
         z = np.empty(len(r), dtype=np.float64) if rp[1] == MEM_HOST else r.new_empty(r.shape)
     zp = _ptr(z, np.float64)
     _check(LIB.ufe_bddc_apply(bddc, rp[0], zp[0], _mem_of(rp, zp)))
+    return z
+
+
+def ufe_bddc_apply_noalloc(bddc, r, z):
+    """z = M r into a preallocated device tensor, without any device allocation."""
+    if not (_is_torch(r) and _is_torch(z) and r.is_cuda and z.is_cuda):
+        raise TypeError("ufe_bddc_apply_noalloc takes CUDA tensors")
+    rp = _ptr(r, np.float64)
+    zp = _ptr(z, np.float64)
+    _check(LIB.ufe_bddc_apply_noalloc(bddc, rp[0], zp[0]))
     return z
 
 
