@@ -1,0 +1,81 @@
+"""Parity at the benchmark's own workload and launch configuration: the 64^3
+bumpy sphere (51,081 DOFs, 172 subdomains, cut fractions down to 2e-10), set up
+and solved exactly as bench.py does (device inputs, stiffness weighting,
+variant-1 objects, BDDC(cef), rtol 1e-8), against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from tests.oracle_cache import energy_error, object_ids, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06323_gb300 import build_ext
+    build_ext.build()
+    from paper_1703_06323_gb300 import ufe
+    return torch, ufe, oracle_run("bumpy64")
+
+
+def _device_solver(torch, orc, precision):
+    from paper_1703_06323_gb300.solver import Solver
+    dev = torch.device("cuda", 0)
+    p = orc.p
+    arrays = {"phi": torch.from_numpy(p.phi).to(dev), "f": torch.from_numpy(p.f).to(dev), "q": None, "g": None}
+    return Solver(p, precision=precision, arrays=arrays)
+
+
+def test_integer_setup_bit_exact(env):
+    torch, ufe, orc = env
+    m = orc.mesh
+    with _device_solver(torch, orc, "mixed") as S:
+        assert S.info["n_dof"] == m.n_dof == 51081
+        assert np.array_equal(ufe.ufe_mesh_get_cell_types(S.mesh), m.cell_type)
+        assert np.array_equal(ufe.ufe_mesh_get_dof_map(S.mesh).astype(np.int64), m.dof_of_node)
+        assert np.array_equal(ufe.ufe_mesh_get_subdomains(S.mesh).astype(np.int64), m.sub_of_cell)
+        neigh = ufe.ufe_mesh_get_neighbours(S.mesh).astype(np.int64)
+        for d in range(0, m.n_dof, 97):
+            ns = m.neigh[d]
+            assert tuple(neigh[d, :len(ns)]) == ns and np.all(neigh[d, len(ns):] == -1)
+        ids, kinds, coarse = ufe.ufe_bddc_get_objects(S.bddc, m.n_dof)
+        ref_ids, ref_kinds = object_ids(m.objects("v1"), m.n_dof)
+        assert np.array_equal(ids.astype(np.int64), ref_ids)
+        assert np.array_equal(kinds.astype(np.int64), ref_kinds)
+        assert S.bddc_info["n_coarse"] == len(m.objects("v1"))
+
+
+def test_cut_cells_and_rhs(env):
+    torch, ufe, orc = env
+    integ = orc.integ
+    with _device_solver(torch, orc, "mixed") as S:
+        n_cut = S.info["n_cut_cells"]
+        cells, K, load, eta = ufe.ufe_system_get_cut_data(S.system, n_cut)
+        assert np.array_equal(cells.astype(np.int64), integ.cut_cells)
+        scale = np.abs(integ.K_cut).reshape(n_cut, -1).max(axis=1)
+        assert np.all(np.abs(K - integ.K_cut).reshape(n_cut, -1).max(axis=1) <= 1e-12 * scale)
+        assert np.abs(eta - integ.eta).max() <= 1e-13
+        b = S.rhs()
+        assert np.abs(b - orc.sys.b).max() <= 1e-12 * np.abs(orc.sys.b).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solution(env, precision):
+    torch, ufe, orc = env
+    ref = orc.solve(rtol=1e-12)
+    ref8 = orc.solve(rtol=1e-8)
+    with _device_solver(torch, orc, precision) as S:
+        dev = torch.device("cuda", 0)
+        x = torch.zeros(S.n_dof, dtype=torch.float64, device=dev)
+        _, info = S.solve(x0=x, rtol=1e-8)
+        xh = x.cpu().numpy()
+    assert info["converged"] == 1 and info["true_rel_residual"] <= 1.5e-8
+    floor = energy_error(orc.sys.A, ref8["x"], ref["x"])
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    assert energy_error(orc.sys.A, xh, ref["x"]) <= max(tol, 4 * floor)
+    if precision == "fp64":
+        assert abs(info["iterations"] - ref8["iterations"]) <= 1
