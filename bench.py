@@ -273,6 +273,9 @@ def run_ours(args, rank, world):
     t_mixed, i_mixed, launches = timed("mixed", args.steps)
     U.ufe_timing_enable(False)
     kt = {k: U.ufe_timing_get(k) for k in ("gj_update_f64", "gj_update_f32", "integrate_cut")}
+    phases = {k: U.ufe_timing_get(k)[0] / args.steps for k in
+              ("phase_mesh", "phase_assemble", "phase_objects", "phase_local", "phase_factor", "phase_coarse",
+               "phase_solve")}
     U.ufe_timing_reset()
     clk_stats = clk.stop()
     t_fp64, i_fp64, _ = timed("fp64", args.fp64_steps) if args.fp64_steps > 0 else ([float("nan")], [None], 0)
@@ -352,6 +355,7 @@ def run_ours(args, rank, world):
                  "true_rel_residual": info64["true_rel_residual"]},
         "true_rel_residual": info["true_rel_residual"],
         "gpu_launches": launches,
+        "phase_ms": phases,
         "roofline": roofline,
         "clocks": clk_stats,
         "e2e": {"value": e2e_mean / world, "unit": "s",

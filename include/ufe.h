@@ -100,6 +100,9 @@ int64_t ufe_kernel_launches(void);
  *   "gj_update_f64"  FP64 Gauss-Jordan update step (coarse matrix; local matrices in FP64 mode)
  *   "gj_update_f32"  FP32 Gauss-Jordan update step (local matrices in mixed precision)
  *   "integrate_cut"  marching-tetrahedra cut-cell integration
+ * and the phases "phase_mesh", "phase_assemble", "phase_objects", "phase_local",
+ * "phase_factor", "phase_coarse", "phase_solve" (events around the host code of
+ * each phase, so they include its synchronisations and host work).
  * ufe_timing_get sums the elapsed device time (ms) and the launch count of one
  * name since the last reset (it synchronises on the recorded events).
  * Unknown names return UFE_ERR_INVALID_ARG. */

@@ -126,8 +126,11 @@ ufe_status ufe_timing_get(const char* kernel, double* total_ms, int64_t* launche
   return guarded([&] {
     UFE_REQUIRE(kernel && total_ms && launches, UFE_ERR_INVALID_ARG, "null argument");
     const std::string k(kernel);
-    UFE_REQUIRE(k == "gj_update_f64" || k == "gj_update_f32" || k == "integrate_cut", UFE_ERR_INVALID_ARG,
-                "unknown timed kernel");
+    static const char* known[] = {"gj_update_f64", "gj_update_f32", "integrate_cut", "phase_mesh", "phase_assemble",
+                                  "phase_objects", "phase_local", "phase_factor", "phase_coarse", "phase_solve"};
+    bool ok = false;
+    for (const char* kn : known) ok = ok || k == kn;
+    UFE_REQUIRE(ok, UFE_ERR_INVALID_ARG, "unknown timed kernel or phase");
     std::lock_guard<std::mutex> lock(g_tmu);
     double tot = 0.0;
     int64_t n = 0;
@@ -179,7 +182,10 @@ ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const
     const int64_t nn = g.n_nodes();
     m->phi.alloc(nn, m->stream);
     copy_in(m->phi.p, phi_nodes, nn * sizeof(double), mem, m->stream);
+    TimedLaunch tl;
+    tl.begin("phase_mesh", m->stream);
     mesh_build(*m, m->phi.p, pin_node);
+    tl.end(m->stream);
     UFE_CUDA(cudaStreamSynchronize(m->stream));
     *out = m.release();
   });
@@ -261,7 +267,10 @@ ufe_status ufe_assemble(ufe_mesh* m, const double* kappa, const double* f, const
     const double* fd = stage(fb, f, nn, mem, s);
     const double* qd = stage(qb, flux, nn * 3, mem, s);
     const double* gd = stage(gb, gval, nn, mem, s);
+    TimedLaunch tl;
+    tl.begin("phase_assemble", s);
     system_build(*sys, sys->has_kappa ? sys->kappa.p : nullptr, fd, qd, gd);
+    tl.end(s);
     UFE_CUDA(cudaStreamSynchronize(s));
     *out = sys.release();
   });
@@ -430,7 +439,10 @@ ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* B, const double* b, double* 
         }
       }
     } out_guard{x, xd, n, mem, s};
+    TimedLaunch tl;
+    tl.begin("phase_solve", s);
     pcg_solve(*B, bd, xd, *opts, info);
+    tl.end(s);
   });
 }
 

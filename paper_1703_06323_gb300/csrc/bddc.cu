@@ -807,6 +807,8 @@ void bddc_build(Bddc& B) {
   UFE_CUDA(cudaEventCreate(&e1));
   UFE_CUDA(cudaEventRecord(e0, s));
 
+  TimedLaunch ph_obj;
+  ph_obj.begin("phase_objects", s);
   // ---- standard objects
   DBuf<int32_t> label;
   DBuf<uint8_t> active, flags;
@@ -939,6 +941,9 @@ void bddc_build(Bddc& B) {
                   "subdomain " + std::to_string(w) + " floats and has no coarse DOF");
   }
 
+  ph_obj.end(s);
+  TimedLaunch ph_loc;
+  ph_loc.begin("phase_local", s);
   // ---- storage offsets
   std::vector<int64_t> oII(ns), oIG(ns), oGG(ns), oCG(ns), oGC(ns), oCC(ns);
   int64_t nII = 0, nIG = 0, nGG = 0, nCG = 0, nGC = 0, nCC = 0;
@@ -988,6 +993,9 @@ void bddc_build(Bddc& B) {
                                           B.opts.weighting == UFE_WEIGHT_TOPOLOGICAL, B.w.p);
   UFE_CHECK_LAUNCH();
 
+  ph_loc.end(s);
+  TimedLaunch ph_fac;
+  ph_fac.begin("phase_factor", s);
   // ---- factorisations and explicit local operators
   DBuf<double> Acw, rho;
   if (B.mixed)
@@ -1000,6 +1008,9 @@ void bddc_build(Bddc& B) {
   AIG.release();
   AGG.release();
 
+  ph_fac.end(s);
+  TimedLaunch ph_co;
+  ph_co.begin("phase_coarse", s);
   // ---- coarse matrix (FP64), assembled and inverted
   B.ldc = pad4((int)std::max<int64_t>(nco, 1));
   B.Ac_inv.alloc((size_t)std::max<int64_t>(nco, 1) * B.ldc, s);
@@ -1019,6 +1030,7 @@ void bddc_build(Bddc& B) {
     UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
   }
 
+  ph_co.end(s);
   // ---- solver work space
   B.tG.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
   B.vw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);

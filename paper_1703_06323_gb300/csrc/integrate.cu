@@ -5,9 +5,10 @@
 // cut out with the edge crossing points.  1 or 3 inside vertices leave a tet or a
 // prism, 2 leave a prism; prisms are split into 3 tets.  The boundary facet is a
 // triangle or a planar quad (2 triangles) with normal grad(phi)/|grad(phi)|.
-// Volumes use the degree-7 Grundmann-Moeller tet rule and facets the degree-7
-// triangle rule (the integrands have degree <= 6, so the integrals are exact up
-// to rounding).  The rules are generated on the host from the published
+// The stiffness integrand grad N_a . grad N_b has degree <= 4 and uses the degree-5
+// Grundmann-Moeller tet rule (15 points); the source load f_h N_a has degree <= 6
+// and uses the degree-7 rule (35 points); facets use the degree-7 triangle rule.
+// Every integral is therefore exact up to rounding.  The rules are generated on the host from the published
 // formula of Grundmann & Moeller (1978) and kept in constant memory.
 //
 // One warp per cut cell (see k_integrate_cut).
@@ -21,9 +22,11 @@
 
 namespace ufe {
 
-constexpr int kTetPts = 35, kTriPts = 20;
+constexpr int kTetPts = 35, kTriPts = 20, kTet5Pts = 15;
 __constant__ double c_tet_bary[kTetPts * 4];
 __constant__ double c_tet_w[kTetPts];
+__constant__ double c_tet5_bary[kTet5Pts * 4];
+__constant__ double c_tet5_w[kTet5Pts];
 __constant__ double c_tri_bary[kTriPts * 3];
 __constant__ double c_tri_w[kTriPts];
 
@@ -72,6 +75,10 @@ void ensure_constants() {
   UFE_REQUIRE((int)w.size() == kTetPts, UFE_ERR_CUDA, "tet rule size");
   UFE_CUDA(cudaMemcpyToSymbol(c_tet_bary, b.data(), b.size() * sizeof(double)));
   UFE_CUDA(cudaMemcpyToSymbol(c_tet_w, w.data(), w.size() * sizeof(double)));
+  gm_rule(3, 2, b, w);
+  UFE_REQUIRE((int)w.size() == kTet5Pts, UFE_ERR_CUDA, "tet degree-5 rule size");
+  UFE_CUDA(cudaMemcpyToSymbol(c_tet5_bary, b.data(), b.size() * sizeof(double)));
+  UFE_CUDA(cudaMemcpyToSymbol(c_tet5_w, w.data(), w.size() * sizeof(double)));
   gm_rule(2, 3, b, w);
   UFE_REQUIRE((int)w.size() == kTriPts, UFE_ERR_CUDA, "triangle rule size");
   UFE_CUDA(cudaMemcpyToSymbol(c_tri_bary, b.data(), b.size() * sizeof(double)));
@@ -186,6 +193,7 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
                 const double* __restrict__ f, const double* __restrict__ q, double* __restrict__ K_cut,
                 double* __restrict__ load_cut, double* __restrict__ eta) {
   __shared__ double s_tet[kTetPts * 5];   // 4 barycentric + weight
+  __shared__ double s_tet5[kTet5Pts * 5];
   __shared__ double s_tri[kTriPts * 4];
   __shared__ CellGeom geo[kWarpsPerBlock];
   __shared__ double s_f[kWarpsPerBlock][8];
@@ -193,6 +201,10 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
   for (int e = threadIdx.x; e < kTetPts; e += blockDim.x) {
     for (int c = 0; c < 4; ++c) s_tet[e * 5 + c] = c_tet_bary[e * 4 + c];
     s_tet[e * 5 + 4] = c_tet_w[e];
+  }
+  for (int e = threadIdx.x; e < kTet5Pts; e += blockDim.x) {
+    for (int c = 0; c < 4; ++c) s_tet5[e * 5 + c] = c_tet5_bary[e * 4 + c];
+    s_tet5[e * 5 + 4] = c_tet5_w[e];
   }
   for (int e = threadIdx.x; e < kTriPts; e += blockDim.x) {
     for (int c = 0; c < 3; ++c) s_tri[e * 4 + c] = c_tri_bary[e * 3 + c];
@@ -252,11 +264,17 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
   for (int e = 0; e < kAcc; ++e) acc[e] = 0.0;
   if (valid) {
     const double h = g.h, h3 = h * h * h, h2 = h * h;
-    const int n_vol = G.n_tet * kTetPts, n_all = n_vol + G.n_tri * kTriPts;
+    // work items: stiffness + volume (15-point rule), source load (35-point rule), facets
+    const int n_k = G.n_tet * kTet5Pts;
+    const int n_l = (f != nullptr) ? G.n_tet * kTetPts : 0;
+    const int n_all = n_k + n_l + G.n_tri * kTriPts;
     for (int it = lane; it < n_all; it += 32) {
-      if (it < n_vol) {
-        const double* T = G.tet[it / kTetPts];
-        const double* R = s_tet + (it % kTetPts) * 5;
+      if (it < n_k || it < n_k + n_l) {
+        const bool stiff = it < n_k;
+        const int e = stiff ? it : it - n_k;
+        const int np = stiff ? kTet5Pts : kTetPts;
+        const double* T = G.tet[e / np];
+        const double* R = (stiff ? s_tet5 : s_tet) + (e % np) * 5;
         const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
         const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
         const double wx = T[9] - T[0], wy = T[10] - T[1], wz = T[11] - T[2];
@@ -266,22 +284,27 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
         const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7] + R[3] * T[10];
         const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8] + R[3] * T[11];
         const double wq = R[4] * vol;
-        double N[8], Gd[8][3];
-        q1_shape_grad(px, py, pz, N, Gd);
-        int e = 0;
+        if (stiff) {
+          double N[8], Gd[8][3];
+          q1_shape_grad(px, py, pz, N, Gd);
+          int k = 0;
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+          for (int a = 0; a < 8; ++a)
 #pragma unroll
-          for (int b = a; b < 8; ++b, ++e)
-            acc[e] += wq * (Gd[a][0] * Gd[b][0] + Gd[a][1] * Gd[b][1] + Gd[a][2] * Gd[b][2]);
-        double fh = 0.0;
+            for (int b = a; b < 8; ++b, ++k)
+              acc[k] += wq * (Gd[a][0] * Gd[b][0] + Gd[a][1] * Gd[b][1] + Gd[a][2] * Gd[b][2]);
+          acc[44] += wq;
+        } else {
+          double N[8];
+          q1_shape(px, py, pz, N);
+          double fh = 0.0;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) fh += N[a] * s_f[warp][a];
+          for (int a = 0; a < 8; ++a) fh += N[a] * s_f[warp][a];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) acc[36 + a] += wq * fh * N[a] * h3;
-        acc[44] += wq;
+          for (int a = 0; a < 8; ++a) acc[36 + a] += wq * fh * N[a] * h3;
+        }
       } else {
-        const int r = it - n_vol;
+        const int r = it - n_k - n_l;
         const double* T = G.tri[r / kTriPts];
         const double* R = s_tri + (r % kTriPts) * 4;
         const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
