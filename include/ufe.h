@@ -100,6 +100,14 @@ int64_t ufe_kernel_launches(void);
  *   "gj_update_f64"  FP64 Gauss-Jordan update step (coarse matrix; local matrices in FP64 mode)
  *   "gj_update_f32"  FP32 Gauss-Jordan update step (local matrices in mixed precision)
  *   "integrate_cut"  marching-tetrahedra cut-cell integration
+ * the per-iteration kernels when they run outside a CUDA graph (ufe_system_apply,
+ * ufe_bddc_apply and the first preconditioner application of ufe_pcg_solve):
+ *   "apply"          operator apply y = A x
+ *   "prec_interior"  y_I = A_II^-1 r_I, t_G = A_GI y_I
+ *   "prec_neumann"   weighted restriction, constrained Neumann solve, coarse residual parts
+ *   "coarse_solve"   u_c = A_c^-1 r_c
+ *   "prec_prolong"   coarse prolongation Phi u_c
+ *   "prec_final"     weighted average and harmonic extension
  * and the phases "phase_mesh", "phase_assemble", "phase_objects", "phase_local",
  * "phase_factor", "phase_coarse", "phase_solve" (events around the host code of
  * each phase, so they include its synchronisations and host work).

@@ -29,7 +29,7 @@ std::vector<TRec> g_trecs;
 }  // namespace
 
 void TimedLaunch::begin(const char* nm, cudaStream_t s) {
-  if (!g_timing) return;
+  if (!g_timing || g_capture_counter) return;   // never inside a graph capture
   name = nm;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -126,8 +126,10 @@ ufe_status ufe_timing_get(const char* kernel, double* total_ms, int64_t* launche
   return guarded([&] {
     UFE_REQUIRE(kernel && total_ms && launches, UFE_ERR_INVALID_ARG, "null argument");
     const std::string k(kernel);
-    static const char* known[] = {"gj_update_f64", "gj_update_f32", "integrate_cut", "phase_mesh", "phase_assemble",
-                                  "phase_objects", "phase_local", "phase_factor", "phase_coarse", "phase_solve"};
+    static const char* known[] = {"gj_update_f64", "gj_update_f32", "integrate_cut", "phase_mesh",
+                                  "phase_assemble", "phase_objects", "phase_local", "phase_factor",
+                                  "phase_coarse", "phase_solve", "apply", "prec_interior",
+                                  "prec_neumann", "coarse_solve", "prec_prolong", "prec_final"};
     bool ok = false;
     for (const char* kn : known) ok = ok || k == kn;
     UFE_REQUIRE(ok, UFE_ERR_INVALID_ARG, "unknown timed kernel or phase");

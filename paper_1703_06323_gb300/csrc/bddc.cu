@@ -62,6 +62,7 @@ SubMeta Bddc::meta() const {
   s.gi_v = gi_v.p;
   s.ig_k = ig_k.p;
   s.ig_v = ig_v.p;
+  s.status = status.p;
   return s;
 }
 
@@ -806,6 +807,8 @@ void bddc_build(Bddc& B) {
   UFE_CUDA(cudaEventCreate(&e0));
   UFE_CUDA(cudaEventCreate(&e1));
   UFE_CUDA(cudaEventRecord(e0, s));
+  B.status.alloc(1, s);
+  B.status.zero();
 
   TimedLaunch ph_obj;
   ph_obj.begin("phase_objects", s);

@@ -34,6 +34,7 @@ struct SubMeta {
   const double* gi_v;
   const int32_t* ig_k;      // A_IG in ELL form
   const double* ig_v;
+  int* status;              // DEV_* flags raised by bounded device waits
 };
 
 struct PcgScalars {
@@ -83,6 +84,7 @@ struct Bddc {
   DBuf<double> x, r, b, z, q, p0, p1;
   DBuf<double> part;            // per-block partial sums
   DBuf<PcgScalars> sc;
+  DBuf<int> status;             // DEV_* flags of the per-iteration kernels
   PcgScalars* h_sc = nullptr;   // pinned mirror
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;   // library-owned stream used only for graph capture

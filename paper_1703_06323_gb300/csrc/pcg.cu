@@ -314,39 +314,11 @@ __device__ void cta_gemv_rows(const TM* __restrict__ M, int r0, int r1, int ld, 
   }
 }
 
-// sum over the cells of subdomain w around local node (lx,ly,lz) of the matrix row
-// times the values at the neighbouring local DOFs of the given kind
-template <int KIND>
-__device__ double local_stencil(const SubMeta& sm, int w, int bi, int bj, int bk, int lx, int ly, int lz,
-                                const int32_t* __restrict__ lm, const double* __restrict__ vals) {
-  const GridGeom& g = sm.g;
-  double sum = 0.0;
-  for (int cz = lz - 1; cz <= lz; ++cz) {
-    if (cz < 0 || cz >= g.sz) continue;
-    for (int cy = ly - 1; cy <= ly; ++cy) {
-      if (cy < 0 || cy >= g.sy) continue;
-      for (int cx = lx - 1; cx <= lx; ++cx) {
-        if (cx < 0 || cx >= g.sx) continue;
-        const int64_t c = g.cell(bi * g.sx + cx, bj * g.sy + cy, bk * g.sz + cz);
-        if (sm.sub_of_cell[c] != w) continue;
-        const int a = (lx - cx) + 2 * (ly - cy) + 4 * (lz - cz);
-        const bool internal = sm.cell_type[c] == UFE_CELL_INTERNAL;
-        const double* Kc = internal ? nullptr : sm.K_cut + (int64_t)sm.cut_index[c] * 64 + a * 8;
-        double s = 0.0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int ln = (cx + (b & 1)) + g.lnx * ((cy + ((b >> 1) & 1)) + g.lny * (cz + (b >> 2)));
-          const int32_t code = lm[ln];
-          if (lmap_kind(code) != KIND) continue;
-          const double kab = internal ? g.h * q1_khat(a, b) : Kc[b];
-          s += kab * vals[lmap_index(code)];
-        }
-        sum += (sm.kappa ? sm.kappa[c] : 1.0) * s;
-      }
-    }
-  }
-  return sum;
-}
+// launch parameters shared by the per-subdomain kernels
+struct SubLaunch {
+  int ldImax, ldGmax;   // largest padded interior / interface sizes
+  int n_stages;         // row-stream stages per CTA (1..kMaxStages)
+};
 
 struct SubSizes {
   int nI, nG, nC, ldI, ldG, ldC, bi, bj, bk;
@@ -368,23 +340,163 @@ __device__ __forceinline__ SubSizes sub_sizes(const SubMeta& sm, int w) {
 
 // shared memory layout shared by the per-subdomain kernels
 struct SubSmem {
-  int32_t* lm;    // n_local_nodes
   double* dI;     // ldImax doubles
   double* dG;     // ldGmax doubles
   void* xT;       // max(ldImax, ldGmax) TM values
+  void* stage;    // row-stream stages (128-byte aligned)
 };
 
-template <typename TM>
-__device__ SubSmem carve(char* smem, const SubMeta& sm, int ldImax, int ldGmax) {
+__device__ __forceinline__ SubSmem carve(char* smem, int ldImax, int ldGmax, size_t tm_size) {
   SubSmem s;
-  s.lm = reinterpret_cast<int32_t*>(smem);
-  size_t off = ((size_t)sm.g.n_local_nodes * 4 + 15) & ~(size_t)15;
+  size_t off = 0;
   s.dI = reinterpret_cast<double*>(smem + off);
   off += (size_t)ldImax * 8;
   s.dG = reinterpret_cast<double*>(smem + off);
   off += (size_t)ldGmax * 8;
   s.xT = smem + off;
+  off += (size_t)(ldImax > ldGmax ? ldImax : ldGmax) * tm_size;
+  off = (off + 127) & ~(size_t)127;
+  s.stage = smem + off;
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// row streaming: the rows of a CTA's slice of a dense local operator are moved
+// from HBM into a ring of shared-memory stages by bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), kStreamRows rows per stage,
+// so that a whole stage per CTA is in flight while the previous one is consumed.
+// One warp per row of a stage; each lane reads 16 bytes at a time from shared
+// memory.  Every wait is bounded by a wall-clock limit; on expiry the CTA records
+// DEV_TIMEOUT, drains its copies (again bounded) and leaves its results undefined.
+// ---------------------------------------------------------------------------
+constexpr int kStreamRows = kSubThreads / 32;
+constexpr int kMaxStages = 4;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // one second
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity; false after the limit
+__device__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+template <typename TM>
+struct RowStream {
+  const TM* M;      // first row of the slice
+  TM* buf;          // n_stages * kStreamRows * ld values
+  uint64_t* full;   // one barrier per stage
+  int rows, ld, n_stages, n_steps;
+
+  __device__ void issue(int step) const {
+    const int row0 = step * kStreamRows;
+    const int nr = min(kStreamRows, rows - row0);
+    const int slot = step % n_stages;
+    const unsigned bytes = (unsigned)(nr * ld * (int)sizeof(TM));
+    mbar_arrive_tx(&full[slot], bytes);
+    bulk_load(buf + (size_t)slot * kStreamRows * ld, M + (size_t)row0 * ld, bytes, &full[slot]);
+  }
+  // thread 0: initialise the barriers and put the first stages in flight; the
+  // other threads may wait on them only after a later __syncthreads
+  __device__ void begin(const TM* M_, int r0, int r1, int ld_, void* stage, uint64_t* bars, int n_stages_) {
+    M = M_ + (size_t)r0 * ld_;
+    buf = reinterpret_cast<TM*>(stage);
+    full = bars;
+    rows = r1 - r0;
+    ld = ld_;
+    n_stages = n_stages_;
+    n_steps = (rows + kStreamRows - 1) / kStreamRows;
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < n_stages; ++i) mbar_init(&full[i], 1);
+      mbar_fence_init();
+      for (int i = 0; i < min(n_stages, n_steps); ++i) issue(i);
+    }
+  }
+  // ys[r0 + i] = sum_c M[r0 + i, c] xs[c] (xs zero-padded to ld, in shared memory)
+  __device__ void gemv(const TM* __restrict__ xs, double* __restrict__ ys, int* status) const {
+    using V = typename VecT<TM>::type;
+    constexpr int VN = VecT<TM>::n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int step = 0; step < n_steps; ++step) {
+      const int slot = step % n_stages;
+      const bool ok = mbar_wait(&full[slot], (unsigned)((step / n_stages) & 1));
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicOr(status, DEV_TIMEOUT);
+          for (int s2 = step; s2 < min(step + n_stages, n_steps); ++s2)
+            mbar_wait(&full[s2 % n_stages], (unsigned)((s2 / n_stages) & 1));
+        }
+        __syncthreads();
+        return;
+      }
+      const int i = step * kStreamRows + wid;
+      if (i < rows) {
+        const TM* row = buf + ((size_t)slot * kStreamRows + wid) * ld;
+        TM acc = TM(0);
+        for (int c = lane * VN; c < ld; c += 32 * VN) acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
+        const double d = warp_sum((double)acc);
+        if (lane == 0) ys[i] = d;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && step + n_stages < n_steps) issue(step + n_stages);
+    }
+  }
+};
+
+// ys[r] = sum_c M[r, c] xs[c] for short rows (ld <= 32 * VN): groups of G lanes per row
+template <typename TM>
+__device__ void cta_gemv_short(const TM* __restrict__ M, int r0, int r1, int ld, const TM* __restrict__ xs,
+                               double* __restrict__ ys) {
+  using V = typename VecT<TM>::type;
+  constexpr int VN = VecT<TM>::n;
+  int G = 1;
+  while (G * VN < ld && G < 32) G <<= 1;
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  const int per_warp = 32 / G;
+  const int gid = (threadIdx.x >> 5) * per_warp + lane / G, ng = (blockDim.x >> 5) * per_warp;
+  for (int rb = r0; rb < r1; rb += ng) {
+    const int r = rb + gid;
+    TM acc = TM(0);
+    if (r < r1) {
+      const TM* row = M + (int64_t)r * ld;
+      for (int c = sub * VN; c < ld; c += G * VN) acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
+    }
+    double d = (double)acc;
+    for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (r < r1 && sub == 0) ys[r] = d;
+  }
 }
 
 // The per-subdomain stages run as thread-block clusters of kCL CTAs per subdomain:
@@ -412,19 +524,22 @@ __device__ void cluster_gather(cg::cluster_group& cl, V* local, int n) {
 template <typename TM>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, double* __restrict__ tG,
-                 const PcgScalars* sc, int ldImax, int ldGmax) {
+                 const PcgScalars* sc, SubLaunch L) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
   const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
-  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
+  __shared__ uint64_t full[kMaxStages];
+  int r0, r1;
+  row_slice(z.nI, rank, r0, r1);
+  RowStream<TM> rs;
+  rs.begin(AIIinv + sm.off_II[w], r0, r1, z.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
   for (int p = threadIdx.x; p < z.ldI; p += blockDim.x) xI[p] = p < z.nI ? (TM)r[sm.I_list[sm.I_ptr[w] + p]] : TM(0);
   __syncthreads();
-  int r0, r1;
-  row_slice(z.nI, rank, r0, r1);
-  cta_gemv_rows<TM>(AIIinv + sm.off_II[w], r0, r1, z.ldI, xI, S.dI);
+  rs.gemv(xI, S.dI + r0, sm.status);
   cl.sync();
   cluster_gather(cl, S.dI, z.nI);
   cl.sync();
@@ -447,7 +562,7 @@ template <typename TM>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Phi, const double* __restrict__ r,
                const double* __restrict__ tG, double* __restrict__ vw, double* __restrict__ gC, const PcgScalars* sc,
-               int ldImax, int ldGmax) {
+               SubLaunch L) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
@@ -456,7 +571,12 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0) return;
-  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
+  __shared__ uint64_t full[kMaxStages];
+  int r0, r1;
+  row_slice(z.nG, rank, r0, r1);
+  RowStream<TM> rs;
+  rs.begin(Kop + sm.off_GG[w], r0, r1, z.ldG, S.stage, full, L.n_stages);
   TM* xG = reinterpret_cast<TM*>(S.xT);
   const int g0 = sm.G_ptr[w];
   for (int j = threadIdx.x; j < z.ldG; j += blockDim.x) {
@@ -471,10 +591,8 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
     xG[j] = v;
   }
   __syncthreads();
-  int r0, r1;
-  row_slice(z.nG, rank, r0, r1);
-  cta_gemv_rows<TM>(Kop + sm.off_GG[w], r0, r1, z.ldG, xG, S.dG);
-  // partial g = Phi^T r~ over this CTA's rows: warps split the rows, lanes the columns
+  // partial g = Phi^T r~ over this CTA's rows (while the first rows of K are in
+  // flight): warps split the rows, lanes the columns
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const TM* P = Phi + sm.off_GC[w];
   for (int c0 = 0; c0 < z.nC; c0 += 64) {
@@ -494,6 +612,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
     }
     __syncthreads();
   }
+  rs.gemv(xG, S.dG + r0, sm.status);
   for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) vw[g0 + j] = sm.w[g0 + j] * S.dG[j];
   cl.sync();
   if (rank == 0) {
@@ -520,13 +639,24 @@ __global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ 
     rc[l] = s;
   }
   __syncthreads();
+  // one warp per row; eight independent 16-byte loads per lane in flight
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int U = 8;
   for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < nco; row += (int64_t)gridDim.x * nw) {
     const double* Ar = Ainv + row * ldc;
     double s = 0.0;
-    for (int c = lane * 2; c < ldc; c += 64) {
-      const double2 v = *reinterpret_cast<const double2*>(Ar + c);
-      s += v.x * rc[c] + v.y * rc[c + 1];
+    for (int c0 = lane * 2; c0 < ldc; c0 += 64 * U) {
+      double2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + 64 * u;
+        v[u] = c < ldc ? *reinterpret_cast<const double2*>(Ar + c) : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + 64 * u;
+        if (c < ldc) s += v[u].x * rc[c] + v[u].y * rc[c + 1];
+      }
     }
     s = warp_sum(s);
     if (lane == 0) uc[row] = s;
@@ -537,20 +667,23 @@ __global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ 
 template <typename TM>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict__ uc, double* __restrict__ vw,
-               const PcgScalars* sc, int ldImax, int ldGmax) {
+               const PcgScalars* sc, SubLaunch L) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
   const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0 || z.nC == 0) return;
-  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   TM* xc = reinterpret_cast<TM*>(S.xT);
   for (int c = threadIdx.x; c < z.ldC; c += blockDim.x) xc[c] = c < z.nC ? (TM)uc[sm.C_list[sm.C_ptr[w] + c]] : TM(0);
   __syncthreads();
   int j0, j1;
   row_slice(z.nG, rank, j0, j1);
-  cta_gemv_rows<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
+  if (z.ldC <= 32 * VecT<TM>::n)
+    cta_gemv_short<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
+  else
+    cta_gemv_rows<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
   __syncthreads();
   const int g0 = sm.G_ptr[w];
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vw[g0 + j] += sm.w[g0 + j] * S.dG[j];
@@ -561,14 +694,18 @@ k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict_
 template <typename TM>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, const double* __restrict__ vw,
-             double* __restrict__ z, double* __restrict__ part, PcgScalars* sc, int ldImax, int ldGmax,
-             int with_dots) {
+             double* __restrict__ z, double* __restrict__ part, PcgScalars* sc, SubLaunch L, int with_dots) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
   const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
   const SubSizes zz = sub_sizes(sm, w);
-  SubSmem S = carve<TM>(smem, sm, ldImax, ldGmax);
+  SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
+  __shared__ uint64_t full[kMaxStages];
+  int p0, p1;
+  row_slice(zz.nI, rank, p0, p1);
+  RowStream<TM> rs;
+  rs.begin(AIIinv + sm.off_II[w], p0, p1, zz.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
   double rz = 0.0, rzo = 0.0;
   const int g0 = sm.G_ptr[w];
@@ -594,8 +731,6 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
     z[xi] = u;
   }
   // interior right-hand side r_I - A_IG u_G for this CTA's rows, then exchanged
-  int p0, p1;
-  row_slice(zz.nI, rank, p0, p1);
   const int64_t e0 = 27 * (int64_t)sm.I_ptr[w];
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     double t = 0.0;
@@ -610,8 +745,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   cl.sync();
   cluster_gather(cl, xI, zz.nI);
   cl.sync();
-  cta_gemv_rows<TM>(AIIinv + sm.off_II[w], p0, p1, zz.ldI, xI, S.dI);
-  __syncthreads();
+  rs.gemv(xI, S.dI + p0, sm.status);
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const int32_t d = sm.I_list[sm.I_ptr[w] + p];
     const double zn = S.dI[p];
@@ -697,17 +831,29 @@ void kappa_gradient(const System& sys, const double* u_dev, const double* lambda
 
 void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStream_t s) {
   const OpArgs a = op_args(sys);
+  TimedLaunch t;
+  t.begin("apply", s);
   k_apply<<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
   UFE_CHECK_LAUNCH();
+  t.end(s);
 }
 
-static size_t sub_smem_bytes(const Bddc& B, size_t tm_size) {
+// shared-memory size and stage count of the per-subdomain kernels: the row-stream
+// ring gets about 26 KB, so that five CTAs fit on an SM next to each other
+constexpr size_t kStageBudget = 26 * 1024;
+
+static SubLaunch sub_launch(const Bddc& B, size_t tm_size, size_t* smem) {
   const Mesh& m = *B.mesh;
-  const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
-  size_t off = ((size_t)m.g.n_local_nodes * 4 + 15) & ~(size_t)15;
-  off += (size_t)ldI * 8 + (size_t)ldG * 8;
-  off += (size_t)std::max(ldI, ldG) * tm_size + 16;
-  return off;
+  SubLaunch L;
+  L.ldImax = pad4(std::max(m.max_nI, 1));
+  L.ldGmax = pad4(std::max(m.max_nG, 1));
+  const size_t ldmax = (size_t)std::max(L.ldImax, L.ldGmax);
+  const size_t stage = (size_t)kStreamRows * ldmax * tm_size;
+  L.n_stages = (int)std::max<size_t>(1, std::min<size_t>(kMaxStages, kStageBudget / stage));
+  size_t off = (size_t)L.ldImax * 8 + (size_t)L.ldGmax * 8 + ldmax * tm_size;
+  off = (off + 127) & ~(size_t)127;
+  *smem = off + (size_t)L.n_stages * stage;
+  return L;
 }
 
 template <typename TM>
@@ -715,31 +861,42 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   const Mesh& m = *B.mesh;
   const SubMeta sm = B.meta();
   const int ns = (int)m.n_sub;
-  const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
-  const size_t smem = sub_smem_bytes(B, sizeof(TM));
+  size_t smem = 0;
+  const SubLaunch L = sub_launch(B, sizeof(TM), &smem);
   const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
   const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
-  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, ldI, ldG);
+  TimedLaunch t3, t4, t5, t6, t7;   // per-stage event timing (outside graph capture, when enabled)
+  t3.begin("prec_interior", s);
+  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, L);
   UFE_CHECK_LAUNCH();
-  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, ldI, ldG);
+  t3.end(s);
+  t4.begin("prec_neumann", s);
+  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, L);
   UFE_CHECK_LAUNCH();
+  t4.end(s);
   if (B.n_coarse > 0) {
     const size_t csm = (size_t)B.ldc * 8;
     const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
+    t5.begin("coarse_solve", s);
     k_coarse_solve<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, B.gC.p, B.uc.p, sc);
     UFE_CHECK_LAUNCH();
-  }
-  if (B.n_coarse > 0) {
-    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, ldI, ldG);
+    t5.end(s);
+    t6.begin("prec_prolong", s);
+    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
     UFE_CHECK_LAUNCH();
+    t6.end(s);
   }
-  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, ldI, ldG, with_dots);
+  t7.begin("prec_final", s);
+  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, L, with_dots);
   UFE_CHECK_LAUNCH();
+  t7.end(s);
 }
 
 static void set_smem_limits(Bddc& B) {
-  const size_t sd = sub_smem_bytes(B, 8), sf = sub_smem_bytes(B, 4);
+  size_t sd = 0, sf = 0;
+  sub_launch(B, 8, &sd);
+  sub_launch(B, 4, &sf);
   UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
   UFE_CUDA(cudaFuncSetAttribute(k_prec_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
@@ -753,6 +910,14 @@ static void set_smem_limits(Bddc& B) {
   UFE_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(csm, 1)));
 }
 
+// raise the flags the per-iteration kernels left behind (after the stream has synchronised)
+static void check_device_status(Bddc& B) {
+  int st = 0;
+  UFE_CUDA(cudaMemcpyAsync(&st, B.status.p, sizeof(int), cudaMemcpyDeviceToHost, B.stream));
+  UFE_CUDA(cudaStreamSynchronize(B.stream));
+  if (st & DEV_TIMEOUT) throw Error{UFE_ERR_TIMEOUT, "a bulk copy of a local operator did not complete in time"};
+}
+
 static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
   if (B.mixed)
     launch_preconditioner<float>(B, r, z, sc, with_dots, s);
@@ -763,6 +928,7 @@ static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, in
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
   set_smem_limits(B);
   precondition(B, r_dev, z_dev, nullptr, 0, B.stream);
+  check_device_status(B);
 }
 
 static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
@@ -849,6 +1015,7 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
   std::vector<double> tr = to_host(out.p, 2, s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  check_device_status(B);
   if (info) {
     info->iterations = fin.iter;
     info->converged = fin.done == 1;
@@ -893,24 +1060,24 @@ static void launch_preconditioner_static(Bddc& B, const double* r, double* z, do
   const Mesh& m = *B.mesh;
   const SubMeta sm = B.meta();
   const int ns = (int)m.n_sub;
-  const int ldI = pad4(std::max(m.max_nI, 1)), ldG = pad4(std::max(m.max_nG, 1));
-  const size_t smem = sub_smem_bytes(B, sizeof(TM));
+  size_t smem = 0;
+  const SubLaunch L = sub_launch(B, sizeof(TM), &smem);
   const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
   const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
-  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, ldI, ldG);
+  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, L);
   UFE_CHECK_LAUNCH();
-  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, ldI, ldG);
+  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
   UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
     const size_t csm = (size_t)B.ldc * 8;
     const unsigned cgr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
     k_coarse_solve<<<cgr, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, nullptr);
     UFE_CHECK_LAUNCH();
-    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, ldI, ldG);
+    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
     UFE_CHECK_LAUNCH();
   }
-  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, ldI, ldG, 0);
+  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, L, 0);
   UFE_CHECK_LAUNCH();
 }
 
@@ -938,6 +1105,7 @@ void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev) {
     launch_preconditioner_static<float>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
   else
     launch_preconditioner_static<double>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+  check_device_status(B);
 }
 
 }  // namespace ufe
