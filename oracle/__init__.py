@@ -27,7 +27,12 @@ Modules and what they follow:
   * ``pcg``         -- (flexible) preconditioned CG with the relative residual
                        stopping rule of Sect. 5.1;
   * ``adjoint``     -- gradient of J = 1/2 |u - u_d|^2 w.r.t. per-cell
-                       coefficients via the adjoint solve (no counterpart in the paper).
+                       coefficients via the adjoint solve (no counterpart in the paper);
+  * ``elasticity``  -- the vector-valued (Q1^3, isotropic linear elasticity)
+                       variant of the same unfitted discretisation: 24x24 element
+                       matrices, loads, assembly (no counterpart in the paper; the
+                       BDDC of ``bddc`` takes 3 DOFs per node and rigid-mode
+                       coarse rows for it).
 
 Parity status per function is stated in each module header.
 """

@@ -34,11 +34,45 @@ class SingularLocal(Exception):
     pass
 
 
+def object_rows(obj, grid, mesh, ncomp):
+    """Coarse DOFs of one object as rows over its (node DOF, component) pairs.
+
+    Poisson (ncomp = 1): the uniform nodal mean (Eq. coarse-dofs, reading R10).
+    Elasticity (ncomp = 3, reading R20): the mean of each component, and for
+    objects of several nodes the mean rotation moments (1/n) sum (y x u)_k, y the
+    node position relative to the object's centroid in grid units; row k is
+    dropped when every node has the same coordinates k+1 and k+2 (an object on a
+    grid line along axis k, for which the row vanishes), so corners carry 3 rows,
+    edges 5 and faces 6.  Returns a list of dicts {(node_dof, comp): weight}."""
+    nodes = [int(d) for d in obj["dofs"]]
+    n = len(nodes)
+    rows = []
+    for c in range(ncomp):
+        rows.append({(d, c): 1.0 / n for d in nodes})
+    if ncomp == 1 or n == 1:
+        return rows
+    ijk = np.array([grid.node_ijk(int(mesh.node_of_dof[d])) for d in nodes], dtype=np.float64)
+    y = ijk - ijk.mean(axis=0)
+    for k in range(3):
+        k1, k2 = (k + 1) % 3, (k + 2) % 3
+        if np.all(ijk[:, k1] == ijk[0, k1]) and np.all(ijk[:, k2] == ijk[0, k2]):
+            continue
+        row = {}
+        for t, d in enumerate(nodes):
+            # (y x u)_k = y_k1 u_k2 - y_k2 u_k1
+            row[(d, k2)] = row.get((d, k2), 0.0) + y[t, k1] / n
+            row[(d, k1)] = row.get((d, k1), 0.0) - y[t, k2] / n
+        rows.append(row)
+    return rows
+
+
 class BDDC:
     def __init__(self, mesh, integ, system, weighting="stiffness", objects="v1", coarse="cef",
                  all_interface_corners=False):
         self.mesh = mesh
         self.system = system
+        nc3 = getattr(system, "ncomp", 1)
+        self.ncomp = nc3
         g = mesh.grid
         if all_interface_corners:
             # enlarged coarse space of Sect. 4.2: every interface DOF is a corner
@@ -47,11 +81,19 @@ class BDDC:
         else:
             objs = coarse_objects(mesh.objects(objects), coarse)
         self.objs = objs
-        self.n_coarse = len(objs)
+        # coarse DOFs: the rows of every object, numbered object by object
+        self.coarse_rows = []
+        self.coarse_obj = []
+        for k, o in enumerate(objs):
+            for row in object_rows(o, g, mesh, nc3):
+                self.coarse_rows.append(row)
+                self.coarse_obj.append(k)
+        self.n_coarse = len(self.coarse_rows)
         self.local = []
         constrained_nodes = set(np.flatnonzero(mesh.constrained).tolist())
         for w in range(mesh.n_sub):
-            dofs = mesh.sub_dofs[w]
+            ndofs = mesh.sub_dofs[w]
+            dofs = (nc3 * ndofs[:, None] + np.arange(nc3)[None, :]).ravel()
             pos = {int(d): i for i, d in enumerate(dofs)}
             n = dofs.size
             A = np.zeros((n, n))
@@ -59,26 +101,28 @@ class BDDC:
             for c in mesh.sub_cells[w]:
                 nodes = g.cell_nodes(c)
                 Ke = integ.stiffness(c)
-                li = [pos.get(int(mesh.dof_of_node[v]), -1) if mesh.dof_of_node[v] >= 0 else -1
-                      for v in nodes]
-                for a in range(8):
-                    if nodes[a] in constrained_nodes:
+                li = []
+                for v in nodes:
+                    if v in constrained_nodes:
                         touches_constraint = True
+                    d = mesh.dof_of_node[v]
+                    for cc in range(nc3):
+                        li.append(pos.get(int(nc3 * d + cc), -1) if d >= 0 else -1)
+                for a in range(8 * nc3):
                     if li[a] < 0:
                         continue
-                    for b in range(8):
+                    for b in range(8 * nc3):
                         if li[b] >= 0:
                             A[li[a], li[b]] += Ke[a, b]
-            gam = np.array([mesh.is_gamma[d] for d in dofs], dtype=bool)
+            gam = np.repeat(np.array([mesh.is_gamma[d] for d in ndofs], dtype=bool), nc3)
             I = np.flatnonzero(~gam)
             G = np.flatnonzero(gam)
-            # coarse objects of this subdomain, in global coarse order
-            cids = [k for k, o in enumerate(objs) if w in o["neigh"]]
+            # coarse DOFs of this subdomain, in global coarse order
+            cids = [k for k, ob in enumerate(self.coarse_obj) if w in objs[ob]["neigh"]]
             C = np.zeros((len(cids), n))
             for r, k in enumerate(cids):
-                o = objs[k]
-                for d in o["dofs"]:
-                    C[r, pos[int(d)]] = 1.0 / len(o["dofs"])
+                for (d, cc), val in self.coarse_rows[k].items():
+                    C[r, pos[nc3 * d + cc]] = val
             if not touches_constraint and len(cids) == 0:
                 raise SingularLocal(f"subdomain {w} floats and has no coarse DOF")
             nc = len(cids)
@@ -103,7 +147,7 @@ class BDDC:
         self.ac_chol = sla.cho_factor(Ac) if self.n_coarse else None
         # weights per (subdomain, local DOF)
         self.weighting = weighting
-        n_dof = mesh.n_dof
+        n_dof = system.n
         if weighting == "stiffness":
             denom = np.zeros(n_dof)
             for L in self.local:
@@ -112,7 +156,7 @@ class BDDC:
                 L["w"] = L["diag"] / denom[L["dofs"]]
         elif weighting == "topological":
             for L in self.local:
-                L["w"] = np.array([1.0 / len(mesh.neigh[d]) for d in L["dofs"]])
+                L["w"] = np.array([1.0 / len(mesh.neigh[d // nc3]) for d in L["dofs"]])
         else:
             raise ValueError(weighting)
 
@@ -132,7 +176,7 @@ class BDDC:
 
     def weight(self, u_loc):
         """W: sub-assembled -> global, weighted sum of the local values."""
-        v = np.zeros(self.mesh.n_dof)
+        v = np.zeros(self.system.n)
         for L, u in zip(self.local, u_loc):
             v[L["dofs"]] += L["w"] * u
         return v
@@ -167,13 +211,13 @@ class BDDC:
 
     # -- diagnostics ------------------------------------------------------------
     def weight_sums(self):
-        tot = np.zeros(self.mesh.n_dof)
+        tot = np.zeros(self.system.n)
         for L in self.local:
             tot[L["dofs"]] += L["w"]
         return tot
 
     def dense_preconditioner(self):
-        n = self.mesh.n_dof
+        n = self.system.n
         M = np.zeros((n, n))
         for j in range(n):
             e = np.zeros(n)

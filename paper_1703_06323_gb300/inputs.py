@@ -6,6 +6,11 @@ per-cell coefficients, and the random draws behind them.  None of the solver's
 arithmetic (classification, integration, assembly, BDDC, PCG) lives here, so
 both the CUDA path and the FP64 oracle can consume the same arrays.
 
+Elasticity problems (ncomp = 3) carry nodal body forces f of shape (n_nodes, 3),
+an optional nodal stress field q of shape (n_nodes, 9) (row-major sigma_ij; the
+boundary traction is sigma n), Dirichlet values of shape (n_nodes, 3) and the
+material (E, nu) in ``lame``.
+
 Array conventions (shared with the C ABI):
   * nodes of an ``nx x ny x nz`` cell grid are numbered ``i + (nx+1)*(j + (ny+1)*k)``
     (x fastest); cells are numbered ``i + nx*(j + ny*k)``;
@@ -51,6 +56,8 @@ class Problem:
     kappa: Optional[np.ndarray] = None      # per-cell diffusion coefficient (None = 1)
     u_exact: Optional[np.ndarray] = None    # nodal exact solution when manufactured
     meta: dict = dataclasses.field(default_factory=dict)
+    ncomp: int = 1                          # 1 Poisson; 3 linear elasticity
+    lame: Optional[tuple] = None            # elasticity: (E, nu); kappa then scales E per cell
 
     @property
     def n_nodes(self) -> int:
@@ -282,3 +289,73 @@ def batched_spheres(count=256, seed=0, sizes=(24, 32, 48, 64), sub=8):
         p.dirichlet_values = np.zeros(p.n_nodes)
         out.append(p)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Linear elasticity (vector Q1, 3 DOFs per node)
+# ---------------------------------------------------------------------------
+
+def _sphere_union_phi(X, Y, Z, centres, radii):
+    phi = np.full(X.shape, np.inf)
+    for c, r in zip(centres, radii):
+        phi = np.minimum(phi, np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) - r)
+    return phi
+
+
+def elastic_patch(cells=(8, 8, 8), sub_cells=(4, 4, 4), normal=(1.0, 0.2, 0.1), offset=0.56,
+                  grad=((0.02, 0.01, -0.03), (0.015, -0.01, 0.02), (-0.025, 0.03, 0.01)),
+                  shift=(0.1, -0.2, 0.05), E=1.0, nu=0.3, name="elastic_patch"):
+    """Plane-cut box with the linear displacement u = shift + grad x.
+
+    The uniform stress sigma = lambda tr(eps) I + 2 mu eps of u is prescribed as
+    the traction sigma n on the unfitted plane; the box faces the domain reaches
+    (all but x = 1) carry u as a strong Dirichlet condition; no body force."""
+    X, Y, Z = node_coords((0, 0, 0), (1, 1, 1), cells)
+    n = np.asarray(normal, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    phi = n[0] * X + n[1] * Y + n[2] * Z - offset
+    B = np.asarray(grad, dtype=np.float64)
+    P = np.stack([X, Y, Z], axis=1)
+    u = np.asarray(shift, dtype=np.float64)[None, :] + P @ B.T
+    eps = 0.5 * (B + B.T)
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    sigma = lam * np.trace(eps) * np.eye(3) + 2 * mu * eps
+    mask = FACE_XLO | FACE_YLO | FACE_YHI | FACE_ZLO | FACE_ZHI
+    return Problem(name=name, box_lo=np.zeros(3), box_hi=np.ones(3), cells=tuple(cells),
+                   sub_cells=tuple(sub_cells), phi=phi, f=np.zeros((X.size, 3)),
+                   q=np.tile(sigma.ravel(), (X.size, 1)), dirichlet_face_mask=mask, pin_node=PIN_NONE,
+                   dirichlet_values=u.copy(), u_exact=u, ncomp=3, lame=(E, nu),
+                   meta={"normal": n.tolist(), "offset": offset})
+
+
+def elastic_spheres(seed=0, n=96, sub=8, count=8, r_range=(0.1, 0.2), E=1.0, nu=0.3):
+    """Union of seeded spheres clamped on the box face x = 0 (body force (0,0,-1)).
+
+    The spheres form a chain: the first one crosses x = 0, each next one is
+    centred at a seeded direction from the previous centre, at a seeded fraction
+    U(0.5, 0.9) of the sum of the two radii, and kept inside [r, 1 - r] in y, z and
+    [.., 1 - r] in x; the union is therefore connected and touches x = 0.  Cut
+    boundary traction-free; other box faces natural."""
+    rng = np.random.default_rng(seed)
+    radii = rng.uniform(r_range[0], r_range[1], count)
+    centres = np.zeros((count, 3))
+    centres[0] = [rng.uniform(0.3, 0.7) * radii[0], rng.uniform(0.3, 0.7), rng.uniform(0.3, 0.7)]
+    for i in range(1, count):
+        for _ in range(1000):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            c = centres[i - 1] + d * rng.uniform(0.5, 0.9) * (radii[i - 1] + radii[i])
+            lo = np.array([0.0, radii[i], radii[i]])
+            hi = 1.0 - radii[i]
+            if np.all(c >= lo) and np.all(c <= hi):
+                break
+        centres[i] = np.clip(c, [0.0, radii[i], radii[i]], 1.0 - radii[i])
+    X, Y, Z = node_coords((0, 0, 0), (1, 1, 1), (n, n, n))
+    phi = _sphere_union_phi(X, Y, Z, centres, radii)
+    f = np.zeros((X.size, 3))
+    f[:, 2] = -1.0
+    return Problem(name=f"elastic_spheres{n}_seed{seed}", box_lo=np.zeros(3), box_hi=np.ones(3),
+                   cells=(n, n, n), sub_cells=(sub, sub, sub), phi=phi, f=f, q=None,
+                   dirichlet_face_mask=FACE_XLO, pin_node=PIN_NONE,
+                   dirichlet_values=np.zeros((X.size, 3)), ncomp=3, lame=(E, nu),
+                   meta={"seed": seed, "centres": centres.tolist(), "radii": radii.tolist()})
