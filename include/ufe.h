@@ -186,13 +186,39 @@ void ufe_mesh_destroy(ufe_mesh* mesh);
 ufe_status ufe_assemble(ufe_mesh* mesh, const double* kappa_cells, const double* f_nodes,
                         const double* flux_nodes, const double* dirichlet_values, int mem,
                         ufe_system** out);
-/* b: n_dof doubles (the assembled right-hand side). */
+/*
+ * ufe_assemble_elastic -- the vector-valued (Q1^3) variant: isotropic linear
+ * elasticity on the same unfitted mesh (no counterpart in the paper, which treats
+ * the Poisson problem; same bulk-form integration, natural boundary condition on
+ * the unfitted boundary).
+ *   a_e(u,v) = int_{e cap Omega} s_e (lambda div u div v + 2 mu eps(u) : eps(v)),
+ *   lambda = E nu / ((1+nu)(1-2nu)), mu = E / (2(1+nu)).
+ * The system has 3 DOFs per free node d, numbered 3 d + c (component c = x, y, z);
+ * element DOF 3 a + c of vertex a.  The Dirichlet box faces of the mesh clamp all
+ * three components; use ufe_mesh_create with pin_node = -1 (no pinned node).
+ *
+ *  E, nu             material (E > 0, -1 < nu < 1/2).
+ *  E_scale_cells     n_cells doubles s_e scaling the element matrix, or NULL for 1.
+ *  f_nodes           n_nodes*3 doubles: nodal body force (Q1 interpolated).
+ *  stress_nodes      n_nodes*9 doubles: nodal stress sigma (row-major), the boundary
+ *                    traction is sigma n on the cut boundary; NULL for traction-free.
+ *  dirichlet_values  n_nodes*3 doubles read at the constrained nodes; NULL for 0.
+ * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY.
+ */
+ufe_status ufe_assemble_elastic(ufe_mesh* mesh, double E, double nu, const double* E_scale_cells,
+                                const double* f_nodes, const double* stress_nodes,
+                                const double* dirichlet_values, int mem, ufe_system** out);
+/* ncomp: 1 (Poisson) or 3 (elasticity); n = ncomp * n_dof, the length of every
+ * solution / right-hand-side vector of this system. */
+ufe_status ufe_system_get_info(const ufe_system* sys, int32_t* ncomp, int64_t* n);
+/* b: n doubles (the assembled right-hand side, n from ufe_system_get_info). */
 ufe_status ufe_system_get_rhs(const ufe_system* sys, double* b, int mem);
-/* y = A x over the free DOFs (element-by-element apply). */
+/* y = A x over the free DOFs (element-by-element apply); x, y of length n. */
 ufe_status ufe_system_apply(const ufe_system* sys, const double* x, double* y, int mem);
 /* Cut-cell data in cut-cell order (ascending cell id): cut_cells n_cut int32,
- * K n_cut*64 doubles (8x8 row-major, vertex a = x + 2y + 4z, without kappa),
- * load n_cut*8 doubles, eta n_cut doubles (volume fraction). Any may be NULL. */
+ * K n_cut*ne*ne doubles (ne x ne row-major with ne = 8 ncomp, element DOF
+ * ncomp a + c, vertex a = x + 2y + 4z, without kappa / E_scale), load n_cut*ne
+ * doubles, eta n_cut doubles (volume fraction). Any may be NULL. */
 ufe_status ufe_system_get_cut_data(const ufe_system* sys, int32_t* cut_cells, double* K, double* load,
                                    double* eta, int mem);
 void ufe_system_destroy(ufe_system* sys);
@@ -228,12 +254,18 @@ typedef struct {
  */
 ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc** out);
 ufe_status ufe_bddc_get_info(const ufe_bddc* bddc, ufe_bddc_info* info);
-/* object_of_dof: n_dof int32 (object id, -1 off the interface); object_kind:
- * n_objects int32 (UFE_OBJ_*); coarse_of_object: n_objects int32 (-1 if the
- * object carries no coarse DOF). Objects are ordered by their smallest DOF id. */
+/* object_of_dof: n_dof int32 (object id, -1 off the interface; objects are sets of
+ * free nodes); object_kind: n_objects int32 (UFE_OBJ_*); coarse_of_object:
+ * n_objects int32, the first coarse DOF of the object (-1 if the object carries
+ * none). Objects are ordered by their smallest DOF id.  Poisson: one coarse DOF
+ * per object, its nodal mean (Eq. coarse-dofs).  Elasticity: consecutive coarse
+ * DOFs per object -- the mean of each component, then the mean rotation moments
+ * (1/n) sum (y x u)_k about each axis k (y the node's grid position relative to
+ * the object's centroid) except about the axis of an object lying on one grid
+ * line; corners carry 3, edges 5, faces 6. */
 ufe_status ufe_bddc_get_objects(const ufe_bddc* bddc, int32_t* object_of_dof, int32_t* object_kind,
                                 int32_t* coarse_of_object, int mem);
-/* z = M r for one vector (n_dof doubles), Eq. bddc. */
+/* z = M r for one vector (n = ncomp n_dof doubles), Eq. bddc. */
 ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
 
 /*
@@ -243,14 +275,14 @@ ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
  * that owns the device allocator.  The paper has no counterpart; this is a
  * deployment variant.
  *
- *  r, z   n_dof doubles each, DEVICE pointers on the current device (host
+ *  r, z   n doubles each (n = ncomp n_dof), DEVICE pointers on the current device (host
  *         pointers are not accepted: staging them would need an allocation).
  *
  * The preconditioner's intermediate vectors live in one file-scope device array
  * of fixed size (622,592 doubles, about 5 MB, held by every device that loads the
  * library until the process exits) instead of the buffers ufe_bddc_setup made.
  * Problems beyond its limits -- more than 262,144 interface slots (the sum over
- * subdomains of their interface DOFs), 65,536 subdomain coarse slots or 32,768
+ * subdomains of their interface DOFs, counted per component), 65,536 subdomain coarse slots or 32,768
  * coarse DOFs -- are rejected with UFE_ERR_INVALID_ARG and a message naming the
  * limit.  The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
  * library routine.  The first call on a device looks up the array's device
@@ -280,8 +312,8 @@ typedef struct {
 
 /*
  * ufe_pcg_solve -- BDDC-preconditioned CG (Sect. 5.1), all on the device.
- *  b     n_dof doubles or NULL for the assembled right-hand side.
- *  x     n_dof doubles: initial guess in, solution out.
+ *  b     n doubles (n = ncomp n_dof) or NULL for the assembled right-hand side.
+ *  x     n doubles: initial guess in, solution out.
  *  info  may be NULL.
  * Errors: BREAKDOWN, NO_CONVERGENCE (x holds the last iterate), CUDA, INVALID_ARG.
  */
@@ -298,6 +330,7 @@ ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* bddc, const double* b, doubl
  *  dJdu       n_dof doubles: the adjoint right-hand side (u - u_d for this J).
  *  lambda     n_dof doubles: adjoint solution out (initial guess in).
  *  dJdkappa   n_cells doubles out (0 on external cells).
+ * Poisson systems only (UFE_ERR_UNSUPPORTED for an elasticity system).
  */
 ufe_status ufe_adjoint(ufe_system* sys, ufe_bddc* bddc, const double* u, const double* dJdu,
                        double* lambda, double* dJdkappa, int mem, const ufe_solve_opts* opts,

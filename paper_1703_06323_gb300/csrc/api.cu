@@ -278,11 +278,52 @@ ufe_status ufe_assemble(ufe_mesh* m, const double* kappa, const double* f, const
   });
 }
 
+ufe_status ufe_assemble_elastic(ufe_mesh* m, double E, double nu, const double* E_scale, const double* f,
+                                const double* stress, const double* gval, int mem, ufe_system** out) {
+  return guarded([&] {
+    UFE_REQUIRE(m && out, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(E > 0.0 && nu > -1.0 && nu < 0.5, UFE_ERR_INVALID_ARG, "need E > 0 and -1 < nu < 1/2");
+    check_mem(mem);
+    *out = nullptr;
+    std::unique_ptr<ufe_system> sys(new ufe_system());
+    sys->mesh = m;
+    sys->stream = m->stream;
+    sys->ncomp = 3;
+    sys->lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    sys->mu = E / (2.0 * (1.0 + nu));
+    cudaStream_t s = m->stream;
+    const int64_t nn = m->g.n_nodes(), nc = m->g.n_cells();
+    DBuf<double> fb, sb, gb;
+    if (E_scale) {
+      sys->has_kappa = true;
+      sys->kappa.alloc(nc, s);
+      copy_in(sys->kappa.p, E_scale, nc * 8, mem, s);
+    }
+    const double* fd = stage(fb, f, nn * 3, mem, s);
+    const double* sd = stage(sb, stress, nn * 9, mem, s);
+    const double* gd = stage(gb, gval, nn * 3, mem, s);
+    TimedLaunch tl;
+    tl.begin("phase_assemble", s);
+    system_build_elastic(*sys, sys->has_kappa ? sys->kappa.p : nullptr, fd, sd, gd);
+    tl.end(s);
+    UFE_CUDA(cudaStreamSynchronize(s));
+    *out = sys.release();
+  });
+}
+
+ufe_status ufe_system_get_info(const ufe_system* sys, int32_t* ncomp, int64_t* n) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && ncomp && n, UFE_ERR_INVALID_ARG, "null argument");
+    *ncomp = sys->ncomp;
+    *n = sys->n_vec();
+  });
+}
+
 ufe_status ufe_system_get_rhs(const ufe_system* sys, double* b, int mem) {
   return guarded([&] {
     UFE_REQUIRE(sys && b, UFE_ERR_INVALID_ARG, "null argument");
     check_mem(mem);
-    copy_out(b, sys->b.p, sys->mesh->n_dof * 8, mem, sys->stream);
+    copy_out(b, sys->b.p, sys->n_vec() * 8, mem, sys->stream);
   });
 }
 
@@ -291,7 +332,7 @@ ufe_status ufe_system_apply(const ufe_system* sys, const double* x, double* y, i
     UFE_REQUIRE(sys && x && y, UFE_ERR_INVALID_ARG, "null argument");
     check_mem(mem);
     cudaStream_t s = sys->stream;
-    const int64_t n = sys->mesh->n_dof;
+    const int64_t n = sys->n_vec();
     DBuf<double> xb, yb;
     const double* xd = stage(xb, x, n, mem, s);
     double* yd = y;
@@ -311,10 +352,11 @@ ufe_status ufe_system_get_cut_data(const ufe_system* sys, int32_t* cut_cells, do
     UFE_REQUIRE(sys, UFE_ERR_INVALID_ARG, "null argument");
     check_mem(mem);
     const int64_t n = sys->mesh->n_cut;
+    const int64_t ne = 8 * sys->ncomp;
     cudaStream_t s = sys->stream;
     if (cut_cells) copy_out(cut_cells, sys->mesh->cut_cells.p, n * 4, mem, s);
-    if (K) copy_out(K, sys->K_cut.p, n * 64 * 8, mem, s);
-    if (load) copy_out(load, sys->load_cut.p, n * 8 * 8, mem, s);
+    if (K) copy_out(K, sys->K_cut.p, n * ne * ne * 8, mem, s);
+    if (load) copy_out(load, sys->load_cut.p, n * ne * 8, mem, s);
     if (eta) copy_out(eta, sys->eta.p, n * 8, mem, s);
   });
 }
@@ -381,7 +423,7 @@ ufe_status ufe_bddc_apply(ufe_bddc* B, const double* r, double* z, int mem) {
     UFE_REQUIRE(B && r && z, UFE_ERR_INVALID_ARG, "null argument");
     check_mem(mem);
     cudaStream_t s = B->stream;
-    const int64_t n = B->mesh->n_dof;
+    const int64_t n = B->sys->n_vec();
     DBuf<double> rb, zb;
     const double* rd = stage(rb, r, n, mem, s);
     double* zd = z;
@@ -419,7 +461,7 @@ ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* B, const double* b, double* 
     UFE_REQUIRE(opts->rtol > 0 && opts->maxit >= 0, UFE_ERR_INVALID_ARG, "bad solve options");
     check_mem(mem);
     cudaStream_t s = sys->stream;
-    const int64_t n = sys->mesh->n_dof;
+    const int64_t n = sys->n_vec();
     DBuf<double> bb, xb;
     const double* bd = b ? stage(bb, b, n, mem, s) : sys->b.p;
     double* xd = x;
@@ -454,6 +496,7 @@ ufe_status ufe_adjoint(ufe_system* sys, ufe_bddc* B, const double* u, const doub
     UFE_REQUIRE(sys && B && u && dJdu && lambda && dJdkappa && opts, UFE_ERR_INVALID_ARG, "null argument");
     UFE_REQUIRE(B->sys == sys, UFE_ERR_INVALID_ARG, "preconditioner belongs to another system");
     UFE_REQUIRE(opts->rtol > 0 && opts->maxit >= 0, UFE_ERR_INVALID_ARG, "bad solve options");
+    UFE_REQUIRE(sys->ncomp == 1, UFE_ERR_UNSUPPORTED, "the coefficient gradient is defined for the Poisson problem");
     check_mem(mem);
     cudaStream_t s = sys->stream;
     const int64_t n = sys->mesh->n_dof, nc = sys->mesh->g.n_cells();

@@ -37,6 +37,10 @@ SubMeta Bddc::meta() const {
   SubMeta s;
   s.g = m.g;
   s.n_sub = (int)m.n_sub;
+  s.ncomp = ncomp;
+  s.vI_ptr = vI_ptr.p;
+  s.vG_ptr = vG_ptr.p;
+  s.Kref = sys->Kref.p;
   s.sub_block = m.sub_block.p;
   s.sub_of_cell = m.sub_of_cell.p;
   s.cell_type = m.cell_type.p;
@@ -216,29 +220,23 @@ __global__ void k_obj_kind(int64_t n_obj, const int32_t* __restrict__ obj_rep, c
   kind[o] = k;
 }
 
-__global__ void k_coarse_flags(int64_t n_obj, const int32_t* __restrict__ kind, int coarse, uint8_t* __restrict__ f) {
-  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n_obj) return;
-  const int k = kind[o];
-  f[o] = (k == UFE_OBJ_CORNER) || (k == UFE_OBJ_EDGE && coarse >= UFE_COARSE_CE) ||
-         (k == UFE_OBJ_FACE && coarse >= UFE_COARSE_CEF);
-}
-
 __global__ void k_coarse_list(int64_t n_obj, const int32_t* __restrict__ coarse_of_obj, const int32_t* __restrict__ obj_rep,
-                              const uint8_t* __restrict__ nn, int32_t* __restrict__ coarse_obj,
-                              int32_t* __restrict__ coarse_rep, uint8_t* __restrict__ coarse_nn,
-                              const int32_t* __restrict__ neigh, int32_t* __restrict__ nC) {
+                              const int32_t* __restrict__ nrows, const uint8_t* __restrict__ nn,
+                              int32_t* __restrict__ coarse_obj, int32_t* __restrict__ coarse_rep,
+                              uint8_t* __restrict__ coarse_nn, const int32_t* __restrict__ neigh,
+                              int32_t* __restrict__ nC) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n_obj) return;
   const int32_t c = coarse_of_obj[o];
   if (c < 0) return;
   const int32_t rep = obj_rep[o];
-  coarse_obj[c] = (int32_t)o;
-  coarse_rep[c] = rep;
-  coarse_nn[c] = nn[rep];
-  for (int k = 0; k < nn[rep]; ++k) atomicAdd(nC + neigh[(int64_t)rep * 8 + k], 1);
+  for (int t = 0; t < nrows[o]; ++t) {
+    coarse_obj[c + t] = (int32_t)o;
+    coarse_rep[c + t] = rep;
+    coarse_nn[c + t] = nn[rep];
+  }
+  for (int k = 0; k < nn[rep]; ++k) atomicAdd(nC + neigh[(int64_t)rep * 8 + k], nrows[o]);
 }
-
 
 // coarse DOFs of subdomain w in increasing order
 __global__ void k_sub_coarse_fill(int64_t n_coarse, const int32_t* __restrict__ coarse_rep,
@@ -311,11 +309,13 @@ __global__ void k_touch_constrained(GridGeom g, const int32_t* __restrict__ sub_
 // ---------------------------------------------------------------------------
 // local matrices (Sect. 3.1): A^w from the cells of w, split into II, IG, GG
 // ---------------------------------------------------------------------------
-// entry A^w(node1, node2) of two local nodes of subdomain w: sum over the cells of w
-// containing both (kappa h Khat for internal cells, the cut-cell matrix otherwise)
+// entry A^w((node1, c1), (node2, c2)) of two local nodes of subdomain w: sum over the
+// cells of w containing both (kappa h Khat for internal cells, the cut-cell matrix
+// otherwise; element DOF ncomp a + c)
 __device__ double local_entry(const SubMeta& sm, int w, int bi, int bj, int bk, int lx, int ly, int lz, int lx2,
-                              int ly2, int lz2) {
+                              int ly2, int lz2, int c1, int c2) {
   const GridGeom& g = sm.g;
+  const int nc = sm.ncomp, ne = 8 * nc;
   double val = 0.0;
   for (int cz = max(lz, lz2) - 1; cz <= min(lz, lz2); ++cz) {
     if (cz < 0 || cz >= g.sz) continue;
@@ -327,9 +327,13 @@ __device__ double local_entry(const SubMeta& sm, int w, int bi, int bj, int bk, 
         if (sm.sub_of_cell[c] != w) continue;
         const int a = (lx - cx) + 2 * (ly - cy) + 4 * (lz - cz);
         const int bb = (lx2 - cx) + 2 * (ly2 - cy) + 4 * (lz2 - cz);
+        const int ra = nc * a + c1, rb = nc * bb + c2;
         const double kap = sm.kappa ? sm.kappa[c] : 1.0;
-        const double kab = sm.cell_type[c] == UFE_CELL_INTERNAL ? g.h * q1_khat(a, bb)
-                                                                : sm.K_cut[(int64_t)sm.cut_index[c] * 64 + a * 8 + bb];
+        double kab;
+        if (sm.cell_type[c] == UFE_CELL_INTERNAL)
+          kab = nc == 1 ? g.h * q1_khat(a, bb) : sm.Kref[ra * 24 + rb];
+        else
+          kab = sm.K_cut[(int64_t)sm.cut_index[c] * ne * ne + ra * ne + rb];
         val += kap * kab;
       }
     }
@@ -337,14 +341,16 @@ __device__ double local_entry(const SubMeta& sm, int w, int bi, int bj, int bk, 
   return val;
 }
 
-// dense A_II and A_GG of every subdomain (Sect. 3.1: Neumann matrix over the cells of w)
+// dense A_II and A_GG of every subdomain (Sect. 3.1: Neumann matrix over the cells of w);
+// local vector index NC p + c
+template <int NC>
 __global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGG,
                                  double* __restrict__ AII, double* __restrict__ AGG) {
   const GridGeom& g = sm.g;
   const int w = blockIdx.x;
   const int b = sm.sub_block[w];
   const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
-  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int ldI = pad4(nI), ldG = pad4(nG);
   const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
   for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
@@ -358,106 +364,85 @@ __global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, co
     const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
     const int k2 = lmap_kind(c2);
     if (k2 != k1) continue;
-    const double val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2);
     const int p1 = lmap_index(c1), p2 = lmap_index(c2);
-    if (k1 == LKIND_I)
-      AII[oII[w] + (int64_t)p1 * ldI + p2] = val;
-    else
-      AGG[oGG[w] + (int64_t)p1 * ldG + p2] = val;
+    for (int a1 = 0; a1 < NC; ++a1)
+      for (int a2 = 0; a2 < NC; ++a2) {
+        const double val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2, a1, a2);
+        const int64_t r = NC * p1 + a1, q = NC * p2 + a2;
+        if (k1 == LKIND_I)
+          AII[oII[w] + r * ldI + q] = val;
+        else
+          AGG[oGG[w] + r * ldG + q] = val;
+      }
   }
-  (void)nG;
 }
 
-// A_GI in ELL form: for each interface DOF j of w, the interior DOFs k of w among its
-// 27 neighbours (stencil slot o, -1 when empty) and A^w_jk.  Layout per subdomain is
-// slot-major (entry 27 g0 + o nG + j), so that rows j are read coalesced.
-__global__ void k_gi_ell(SubMeta sm, int32_t* __restrict__ ell_k, double* __restrict__ ell_v) {
+// Off-diagonal blocks in ELL form.  A_GI: for each interface vector DOF j of w, the
+// interior vector DOFs k among the 27 neighbouring nodes (slot o NC + c2, -1 when
+// empty) and A^w_jk; layout per subdomain slot-major (entry KS g0 + slot nG + j, KS =
+// 27 NC, g0 = vG_ptr[w]) so that rows are read coalesced.  A_IG likewise over the
+// interior rows (entry KS i0 + slot nI + p).
+template <int NC>
+__global__ void k_off_ell(SubMeta sm, int rows_kind, int32_t* __restrict__ ell_k, double* __restrict__ ell_v) {
   const GridGeom& g = sm.g;
   const int w = blockIdx.x;
   const int b = sm.sub_block[w];
   const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
-  const int nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int col_kind = rows_kind == LKIND_G ? LKIND_I : LKIND_G;
+  const int32_t* vptr = rows_kind == LKIND_G ? sm.vG_ptr : sm.vI_ptr;
+  const int nR = vptr[w + 1] - vptr[w];
+  const int64_t base = 27 * NC * (int64_t)vptr[w];
   const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
   for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
     const int ln = e / 27, o = e % 27;
     const int32_t c1 = lm[ln];
-    if (lmap_kind(c1) != LKIND_G) continue;
-    const int64_t slot = 27 * (int64_t)sm.G_ptr[w] + (int64_t)o * nG + lmap_index(c1);
+    if (lmap_kind(c1) != rows_kind) continue;
     const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
     const int lx2 = lx + (o % 3) - 1, ly2 = ly + ((o / 3) % 3) - 1, lz2 = lz + (o / 9) - 1;
-    int32_t k = -1;
-    double val = 0.0;
+    int p2 = -1;
     if (lx2 >= 0 && ly2 >= 0 && lz2 >= 0 && lx2 < g.lnx && ly2 < g.lny && lz2 < g.lnz) {
       const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
-      if (lmap_kind(c2) == LKIND_I) {
-        k = lmap_index(c2);
-        val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2);
-      }
+      if (lmap_kind(c2) == col_kind) p2 = lmap_index(c2);
     }
-    ell_k[slot] = k;
-    ell_v[slot] = val;
+    for (int a1 = 0; a1 < NC; ++a1)
+      for (int a2 = 0; a2 < NC; ++a2) {
+        const int64_t slot = base + (int64_t)(o * NC + a2) * nR + NC * lmap_index(c1) + a1;
+        ell_k[slot] = p2 >= 0 ? NC * p2 + a2 : -1;
+        ell_v[slot] = p2 >= 0 ? local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2, a1, a2) : 0.0;
+      }
   }
 }
 
-// A_IG in the same form: for each interior DOF p of w, its interface neighbours
-// (entry 27 i0 + o nI + p)
-__global__ void k_ig_ell(SubMeta sm, int32_t* __restrict__ ell_k, double* __restrict__ ell_v) {
-  const GridGeom& g = sm.g;
-  const int w = blockIdx.x;
-  const int b = sm.sub_block[w];
-  const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
-  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w];
-  const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
-  for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
-    const int ln = e / 27, o = e % 27;
-    const int32_t c1 = lm[ln];
-    if (lmap_kind(c1) != LKIND_I) continue;
-    const int64_t slot = 27 * (int64_t)sm.I_ptr[w] + (int64_t)o * nI + lmap_index(c1);
-    const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
-    const int lx2 = lx + (o % 3) - 1, ly2 = ly + ((o / 3) % 3) - 1, lz2 = lz + (o / 9) - 1;
-    int32_t k = -1;
-    double val = 0.0;
-    if (lx2 >= 0 && ly2 >= 0 && lz2 >= 0 && lx2 < g.lnx && ly2 < g.lny && lz2 < g.lnz) {
-      const int32_t c2 = lm[lx2 + g.lnx * (ly2 + g.lny * lz2)];
-      if (lmap_kind(c2) == LKIND_G) {
-        k = lmap_index(c2);
-        val = local_entry(sm, w, bi, bj, bk, lx, ly, lz, lx2, ly2, lz2);
-      }
-    }
-    ell_k[slot] = k;
-    ell_v[slot] = val;
-  }
-}
-
-// scaled A^_GI entries: s_G[j] A_GI[j][k] s_I[k]
+// scaled A^_GI entries: s_G[j] A_GI[j][k] s_I[k]  (KS = 27 NC slots per row)
 template <typename T>
-__global__ void k_ell_scale(SubMeta sm, const int32_t* __restrict__ ell_k, const double* __restrict__ ell_v,
+__global__ void k_ell_scale(SubMeta sm, int KS, const int32_t* __restrict__ ell_k, const double* __restrict__ ell_v,
                             const double* __restrict__ sI, const double* __restrict__ sG, T* __restrict__ ell_s) {
   const int w = blockIdx.y;
-  const int nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nG * 27; e += gridDim.x * blockDim.x) {
-    const int64_t slot = (int64_t)sm.G_ptr[w] * 27 + e;
+  const int nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nG * KS; e += gridDim.x * blockDim.x) {
+    const int64_t slot = (int64_t)sm.vG_ptr[w] * KS + e;
     const int32_t k = ell_k[slot];
-    ell_s[slot] = k < 0 ? T(0) : (T)(ell_v[slot] * sG[sm.G_ptr[w] + e % nG] * sI[sm.I_ptr[w] + k]);
+    ell_s[slot] = k < 0 ? T(0) : (T)(ell_v[slot] * sG[sm.vG_ptr[w] + e % nG] * sI[sm.vI_ptr[w] + k]);
   }
 }
 
 // X^T = (A^_II^-1 A^_IG)^T, row j = sum_k A^_GI[j][k] A^_II^-1[k][:]  (A^_II^-1 symmetric)
+constexpr int kMaxKS = 81;
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_xt(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGI, const int32_t* __restrict__ ell_k,
-     const T* __restrict__ ell_s, const T* __restrict__ IIinv, T* __restrict__ Xt) {
-  __shared__ int32_t sk[8][27];
-  __shared__ T sv[8][27];
+k_xt(SubMeta sm, int KS, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGI,
+     const int32_t* __restrict__ ell_k, const T* __restrict__ ell_s, const T* __restrict__ IIinv, T* __restrict__ Xt) {
+  __shared__ int32_t sk[8][kMaxKS];
+  __shared__ T sv[8][kMaxKS];
   const int w = blockIdx.y;
-  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int ldI = pad4(nI);
   const int j0 = blockIdx.x * 8;
   if (j0 >= nG) return;
-  for (int e = threadIdx.x; e < 8 * 27; e += blockDim.x) {
-    const int jj = e / 27, o = e % 27;
+  for (int e = threadIdx.x; e < 8 * KS; e += blockDim.x) {
+    const int jj = e / KS, o = e % KS;
     const bool ok = j0 + jj < nG;
-    const int64_t slot = 27 * (int64_t)sm.G_ptr[w] + (int64_t)o * nG + j0 + jj;
+    const int64_t slot = KS * (int64_t)sm.vG_ptr[w] + (int64_t)o * nG + j0 + jj;
     sk[jj][o] = ok ? ell_k[slot] : -1;
     sv[jj][o] = ok ? ell_s[slot] : T(0);
   }
@@ -466,8 +451,7 @@ k_xt(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oG
   for (int jj = 0; jj < 8 && j0 + jj < nG; ++jj) {
     for (int c = threadIdx.x; c < ldI; c += blockDim.x) {
       T acc = T(0);
-#pragma unroll
-      for (int o = 0; o < 27; ++o) {
+      for (int o = 0; o < KS; ++o) {
         const int32_t k = sk[jj][o];
         if (k >= 0) acc += sv[jj][o] * Ainv[(int64_t)k * ldI + c];
       }
@@ -480,29 +464,31 @@ k_xt(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oG
 // (S^ is symmetric): S^[j][i] -= sum_k A^_GI[i][k] X^T[j][k]
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_schur(SubMeta sm, const int64_t* __restrict__ oGG, const int64_t* __restrict__ oGI, const int32_t* __restrict__ ell_k,
-        const T* __restrict__ ell_s, const T* __restrict__ Xt, T* __restrict__ GG) {
+k_schur(SubMeta sm, int KS, const int64_t* __restrict__ oGG, const int64_t* __restrict__ oGI,
+        const int32_t* __restrict__ ell_k, const T* __restrict__ ell_s, const T* __restrict__ Xt, T* __restrict__ GG) {
   extern __shared__ __align__(16) char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
   const int w = blockIdx.y, j = blockIdx.x;
-  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   if (j >= nG) return;
   const int ldI = pad4(nI), ldG = pad4(nG);
   for (int c = threadIdx.x; c < nI; c += blockDim.x) xs[c] = Xt[oGI[w] + (int64_t)j * ldI + c];
   __syncthreads();
   for (int i = threadIdx.x; i < nG; i += blockDim.x) {
-    const int64_t base = 27 * (int64_t)sm.G_ptr[w] + i;
-    int32_t kk[27];
-    T vv[27];
-#pragma unroll
-    for (int o = 0; o < 27; ++o) {
-      kk[o] = ell_k[base + (int64_t)o * nG];
-      vv[o] = ell_s[base + (int64_t)o * nG];
-    }
+    const int64_t base = KS * (int64_t)sm.vG_ptr[w] + i;
     T acc = T(0);
+    for (int o0 = 0; o0 < KS; o0 += 27) {
+      int32_t kk[27];
+      T vv[27];
 #pragma unroll
-    for (int o = 0; o < 27; ++o)
-      if (kk[o] >= 0) acc += vv[o] * xs[kk[o]];
+      for (int o = 0; o < 27; ++o) {
+        kk[o] = ell_k[base + (int64_t)(o0 + o) * nG];
+        vv[o] = ell_s[base + (int64_t)(o0 + o) * nG];
+      }
+#pragma unroll
+      for (int o = 0; o < 27; ++o)
+        if (kk[o] >= 0) acc += vv[o] * xs[kk[o]];
+    }
     GG[oGG[w] + (int64_t)j * ldG + i] -= acc;
   }
 }
@@ -512,27 +498,30 @@ __global__ void k_local_diag(SubMeta sm, const int64_t* __restrict__ oII, const 
                              const double* __restrict__ AII, const double* __restrict__ AGG, double* __restrict__ sI,
                              double* __restrict__ sG, double* __restrict__ dGraw) {
   const int w = blockIdx.x;
-  const int nI = sm.I_ptr[w + 1] - sm.I_ptr[w], nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int ldI = pad4(nI), ldG = pad4(nG);
-  for (int p = threadIdx.x; p < nI; p += blockDim.x) sI[sm.I_ptr[w] + p] = 1.0 / sqrt(AII[oII[w] + (int64_t)p * ldI + p]);
+  for (int p = threadIdx.x; p < nI; p += blockDim.x) sI[sm.vI_ptr[w] + p] = 1.0 / sqrt(AII[oII[w] + (int64_t)p * ldI + p]);
   for (int p = threadIdx.x; p < nG; p += blockDim.x) {
     const double d = AGG[oGG[w] + (int64_t)p * ldG + p];
-    dGraw[sm.G_ptr[w] + p] = d;
-    sG[sm.G_ptr[w] + p] = 1.0 / sqrt(d);
+    dGraw[sm.vG_ptr[w] + p] = d;
+    sG[sm.vG_ptr[w] + p] = 1.0 / sqrt(d);
   }
 }
 
-// weights per interface slot: stiffness A^w_xx / sum_w' A^w'_xx (Eq. alge-weighting) or 1/|neigh| (Eq. weighting)
-__global__ void k_weights(int64_t n_dof, const uint8_t* __restrict__ nn, const int32_t* __restrict__ gpos,
+// weights per interface vector slot: stiffness A^w_xx / sum_w' A^w'_xx (Eq. alge-weighting,
+// per component) or 1/|neigh| (Eq. weighting)
+__global__ void k_weights(int64_t n_dof, int nc, const uint8_t* __restrict__ nn, const int32_t* __restrict__ gpos,
                           const double* __restrict__ dGraw, int topological, double* __restrict__ w) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n_dof || nn[d] < 2) return;
   const int cnt = nn[d];
-  double sum = 0.0;
-  for (int k = 0; k < cnt; ++k) sum += dGraw[gpos[d * 8 + k]];
-  for (int k = 0; k < cnt; ++k) {
-    const int32_t s = gpos[d * 8 + k];
-    w[s] = topological ? 1.0 / cnt : dGraw[s] / sum;
+  for (int c = 0; c < nc; ++c) {
+    double sum = 0.0;
+    for (int k = 0; k < cnt; ++k) sum += dGraw[(int64_t)nc * gpos[d * 8 + k] + c];
+    for (int k = 0; k < cnt; ++k) {
+      const int64_t s = (int64_t)nc * gpos[d * 8 + k] + c;
+      w[s] = topological ? 1.0 / cnt : dGraw[s] / sum;
+    }
   }
 }
 
@@ -552,18 +541,26 @@ __global__ void k_scale_block(const double* __restrict__ src, T* __restrict__ ds
   }
 }
 
-// scaled constraint rows C^ = C D_G^-1/2 (C = uniform means over the objects),
-// C_rho = diag(rho) C^ with rho_l = 1 / |C^_l|^2
-template <typename T>
-__global__ void k_constraints(SubMeta sm, const int32_t* __restrict__ obj_of_dof, const int32_t* __restrict__ coarse_of_obj,
-                              const int32_t* __restrict__ obj_size, const double* __restrict__ sG,
+// scaled constraint rows C^ = C D_G^-1/2, C_rho = diag(rho) C^ with rho_l = 1 / |C^_l|^2.
+// The rows of an object (consecutive coarse ids from coarse_of_obj[o]): Poisson, the
+// uniform nodal mean (Eq. coarse-dofs); elasticity, the mean of each component and
+// the kept rotation moments (1/n) sum (y x u)_k with y the node's grid position
+// relative to the object's centroid (bit k of obj_rot).
+template <typename T, int NC>
+__global__ void k_constraints(SubMeta sm, const int32_t* __restrict__ node_of_dof,
+                              const int32_t* __restrict__ obj_of_dof, const int32_t* __restrict__ coarse_of_obj,
+                              const int32_t* __restrict__ obj_size, const int32_t* __restrict__ obj_rot,
+                              const long long* __restrict__ obj_sum, const double* __restrict__ sG,
                               const int64_t* __restrict__ oCG, T* __restrict__ Cs, T* __restrict__ Crho,
                               double* __restrict__ rho) {
   const int w = blockIdx.x;
-  const int nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int nGn = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  const int nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int c0 = sm.C_ptr[w], nC = sm.C_ptr[w + 1] - c0;
   const int ldG = pad4(nG);
-  for (int j = threadIdx.x; j < nG; j += blockDim.x) {
+  const int g0 = sm.vG_ptr[w];
+  T* Cw = Cs + oCG[w];
+  for (int j = threadIdx.x; j < nGn; j += blockDim.x) {
     const int32_t d = sm.G_list[sm.G_ptr[w] + j];
     const int32_t o = obj_of_dof[d];
     const int32_t c = coarse_of_obj[o];
@@ -573,14 +570,31 @@ __global__ void k_constraints(SubMeta sm, const int32_t* __restrict__ obj_of_dof
       const int mid = (lo + hi) >> 1;
       if (sm.C_list[c0 + mid] < c) lo = mid + 1; else hi = mid;
     }
-    Cs[oCG[w] + (int64_t)lo * ldG + j] = (T)(sG[sm.G_ptr[w] + j] / obj_size[o]);
+    const double inv_n = 1.0 / obj_size[o];
+    for (int a = 0; a < NC; ++a) Cw[(int64_t)(lo + a) * ldG + NC * j + a] = (T)(sG[g0 + NC * j + a] * inv_n);
+    if (NC == 3 && obj_rot[o]) {
+      const int64_t v = node_of_dof[d];
+      const GridGeom& g = sm.g;
+      const int64_t ijk[3] = {v % (g.nx + 1), (v / (g.nx + 1)) % (g.ny + 1), v / ((int64_t)(g.nx + 1) * (g.ny + 1))};
+      double y[3];
+      for (int k = 0; k < 3; ++k) y[k] = (double)ijk[k] - (double)obj_sum[3 * (int64_t)o + k] * inv_n;
+      int t = 0;
+      for (int k = 0; k < 3; ++k) {
+        if (!((obj_rot[o] >> k) & 1)) continue;
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        T* row = Cw + (int64_t)(lo + 3 + t) * ldG + NC * j;
+        row[k2] = (T)(y[k1] * inv_n * sG[g0 + NC * j + k2]);
+        row[k1] = (T)(-y[k2] * inv_n * sG[g0 + NC * j + k1]);
+        ++t;
+      }
+    }
   }
   __syncthreads();
   // rho_l = 1 / |C^_l|^2, each row summed in order by one thread (deterministic)
   for (int i = threadIdx.x; i < nC; i += blockDim.x) {
     double nrm = 0.0;
     for (int j = 0; j < nG; ++j) {
-      const double v = (double)Cs[oCG[w] + (int64_t)i * ldG + j];
+      const double v = (double)Cw[(int64_t)i * ldG + j];
       nrm += v * v;
     }
     rho[c0 + i] = 1.0 / nrm;
@@ -588,8 +602,61 @@ __global__ void k_constraints(SubMeta sm, const int32_t* __restrict__ obj_of_dof
   __syncthreads();
   for (int e = threadIdx.x; e < nC * ldG; e += blockDim.x) {
     const int i = e / ldG;
-    Crho[oCG[w] + e] = (T)((double)Cs[oCG[w] + e] * rho[c0 + i]);
+    Crho[oCG[w] + e] = (T)((double)Cw[e] * rho[c0 + i]);
   }
+}
+
+// object geometry for the elastic rows: sums and bounds of the node grid coordinates
+__global__ void k_obj_geom(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                           const int32_t* __restrict__ obj_of_dof, long long* __restrict__ sum,
+                           int32_t* __restrict__ lo, int32_t* __restrict__ hi) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof) return;
+  const int32_t o = obj_of_dof[d];
+  if (o < 0) return;
+  const int64_t v = node_of_dof[d];
+  const int c[3] = {(int)(v % (g.nx + 1)), (int)((v / (g.nx + 1)) % (g.ny + 1)),
+                    (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)))};
+  for (int k = 0; k < 3; ++k) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(sum + 3 * (int64_t)o + k), (unsigned long long)c[k]);
+    atomicMin(lo + 3 * (int64_t)o + k, c[k]);
+    atomicMax(hi + 3 * (int64_t)o + k, c[k]);
+  }
+}
+
+// coarse rows of every object: 1 (Poisson); 3 component means plus a rotation row
+// about each axis k unless all nodes share coordinates k+1 and k+2 (elasticity);
+// counts[o] = rows of the kept (coarse) objects, 0 otherwise
+__global__ void k_obj_rows(int64_t n_obj, int nc, const int32_t* __restrict__ kind, int coarse,
+                           const int32_t* __restrict__ size, const int32_t* __restrict__ lo,
+                           const int32_t* __restrict__ hi, int32_t* __restrict__ nrows, int32_t* __restrict__ rot,
+                           int32_t* __restrict__ counts) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_obj) return;
+  int r = 1, bits = 0;
+  if (nc == 3) {
+    r = 3;
+    if (size[o] > 1)
+      for (int k = 0; k < 3; ++k) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        if (lo[3 * o + k1] != hi[3 * o + k1] || lo[3 * o + k2] != hi[3 * o + k2]) {
+          bits |= 1 << k;
+          ++r;
+        }
+      }
+  }
+  nrows[o] = r;
+  rot[o] = bits;
+  const int k = kind[o];
+  const bool keep = (k == UFE_OBJ_CORNER) || (k == UFE_OBJ_EDGE && coarse >= UFE_COARSE_CE) ||
+                    (k == UFE_OBJ_FACE && coarse >= UFE_COARSE_CEF);
+  counts[o] = keep ? r : 0;
+}
+
+__global__ void k_coarse_first(int64_t n_obj, const int32_t* __restrict__ counts, const int32_t* __restrict__ offs,
+                               int32_t* __restrict__ coarse_of_obj) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < n_obj) coarse_of_obj[o] = counts[o] > 0 ? offs[o] : -1;
 }
 
 // A_c^w = (C S'^-1 C^T)^-1 - rho  (FP64)
@@ -653,6 +720,11 @@ __global__ void k_symmetrize(double* A, int n, int ld) {
   A[(int64_t)j * ld + i] = v;
 }
 
+__global__ void k_scale_ptr(int64_t n, int nc, const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = nc * in[i];
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -706,16 +778,20 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   II.alloc(std::max<int64_t>(nII, 1), s);
   DBuf<T> Cs, Crho, X, Y, Sc;
   GG.alloc(std::max<int64_t>(nGG, 1), s);
-  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AII.p, II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p);
+  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AII.p, II.p, dII->p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p);
   UFE_CHECK_LAUNCH();
-  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AGG.p, GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p);
+  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AGG.p, GG.p, dGG->p, B.vG_ptr.p, B.vG_ptr.p, sG.p, sG.p);
   UFE_CHECK_LAUNCH();
   Cs.alloc(std::max<int64_t>(nCG, 1), s);
   Crho.alloc(std::max<int64_t>(nCG, 1), s);
   Cs.zero();
   rho.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
-  k_constraints<T><<<ns, 256, 0, s>>>(sm, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p, sG.p, dCG->p, Cs.p, Crho.p,
-                                      rho.p);
+  if (B.ncomp == 3)
+    k_constraints<T, 3><<<ns, 256, 0, s>>>(sm, m.node_of_dof.p, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p,
+                                           B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p);
+  else
+    k_constraints<T, 1><<<ns, 256, 0, s>>>(sm, m.node_of_dof.p, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p,
+                                           B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p);
   UFE_CHECK_LAUNCH();
 
   DBuf<int> status;
@@ -733,13 +809,14 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
     for (int w = 0; w < ns; ++w) nGmax = std::max(nGmax, B.h_nG[w]);
     int nImax = 4;
     for (int w = 0; w < ns; ++w) nImax = std::max(nImax, pad4(B.h_nI[w]));
+    const int KS = 27 * B.ncomp;
     DBuf<T> ell_s;
-    ell_s.alloc(std::max<int64_t>(m.n_Gloc, 1) * 27, s);
-    k_ell_scale<T><<<dim3(8, ns), 256, 0, s>>>(sm, ell_k.p, ell_v.p, sI.p, sG.p, ell_s.p);
+    ell_s.alloc(std::max<int64_t>(B.n_vGloc, 1) * KS, s);
+    k_ell_scale<T><<<dim3(8, ns), 256, 0, s>>>(sm, KS, ell_k.p, ell_v.p, sI.p, sG.p, ell_s.p);
     UFE_CHECK_LAUNCH();
-    k_xt<T><<<dim3((nGmax + 7) / 8, ns), 256, 0, s>>>(sm, dII->p, dIG->p, ell_k.p, ell_s.p, II.p, X.p);
+    k_xt<T><<<dim3((nGmax + 7) / 8, ns), 256, 0, s>>>(sm, KS, dII->p, dIG->p, ell_k.p, ell_s.p, II.p, X.p);
     UFE_CHECK_LAUNCH();
-    k_schur<T><<<dim3(nGmax, ns), 256, nImax * sizeof(T), s>>>(sm, dGG->p, dIG->p, ell_k.p, ell_s.p, X.p, GG.p);
+    k_schur<T><<<dim3(nGmax, ns), 256, nImax * sizeof(T), s>>>(sm, KS, dGG->p, dIG->p, ell_k.p, ell_s.p, X.p, GG.p);
     UFE_CHECK_LAUNCH();
   }
   X.release();
@@ -785,11 +862,11 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
   UFE_CHECK_LAUNCH();
   // 11. unscale the operators used at every iteration
-  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(II.p, dII->p, m.I_ptr.p, m.I_ptr.p, sI.p, sI.p, 0);
+  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(II.p, dII->p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p, 0);
   UFE_CHECK_LAUNCH();
-  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GG.p, dGG->p, m.G_ptr.p, m.G_ptr.p, sG.p, sG.p, 0);
+  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GG.p, dGG->p, B.vG_ptr.p, B.vG_ptr.p, sG.p, sG.p, 0);
   UFE_CHECK_LAUNCH();
-  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GC.p, B.off_GC.p, m.G_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
+  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GC.p, B.off_GC.p, B.vG_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
   UFE_CHECK_LAUNCH();
   std::vector<int> st = to_host(status.p, ns, s);
   for (int w = 0; w < ns; ++w)
@@ -809,6 +886,18 @@ void bddc_build(Bddc& B) {
   UFE_CUDA(cudaEventRecord(e0, s));
   B.status.alloc(1, s);
   B.status.zero();
+  B.ncomp = B.sys->ncomp;
+  const int NC = B.ncomp;
+  B.vI_ptr.alloc(ns + 1, s);
+  B.vG_ptr.alloc(ns + 1, s);
+  k_scale_ptr<<<grid_for(ns + 1, T), T, 0, s>>>(ns + 1, NC, m.I_ptr.p, B.vI_ptr.p);
+  UFE_CHECK_LAUNCH();
+  k_scale_ptr<<<grid_for(ns + 1, T), T, 0, s>>>(ns + 1, NC, m.G_ptr.p, B.vG_ptr.p);
+  UFE_CHECK_LAUNCH();
+  B.n_vIloc = NC * m.n_Iloc;
+  B.n_vGloc = NC * m.n_Gloc;
+  B.max_nIv = NC * m.max_nI;
+  B.max_nGv = NC * m.max_nG;
 
   TimedLaunch ph_obj;
   ph_obj.begin("phase_objects", s);
@@ -880,14 +969,29 @@ void bddc_build(Bddc& B) {
     B.n_face = std::count(kinds.begin(), kinds.end(), (int32_t)UFE_OBJ_FACE);
   }
 
-  // ---- coarse DOFs and the per-subdomain coarse lists
-  DBuf<uint8_t> cf;
-  cf.alloc(std::max<int64_t>(n_obj, 1), s);
+  // ---- coarse DOFs (rows per object) and the per-subdomain coarse lists
   B.coarse_of_obj.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.obj_nrows.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.obj_rot.alloc(std::max<int64_t>(n_obj, 1), s);
+  B.obj_sum.alloc(std::max<int64_t>(n_obj, 1) * 3, s);
+  B.obj_lo.alloc(std::max<int64_t>(n_obj, 1) * 3, s);
+  B.obj_hi.alloc(std::max<int64_t>(n_obj, 1) * 3, s);
+  B.obj_sum.zero();
+  B.obj_lo.fill_bytes(0x7f);
+  B.obj_hi.zero();
   if (n_obj) {
-    k_coarse_flags<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.obj_kind.p, B.opts.coarse, cf.p);
+    k_obj_geom<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, B.obj_of_dof.p, B.obj_sum.p, B.obj_lo.p,
+                                             B.obj_hi.p);
     UFE_CHECK_LAUNCH();
-    B.n_coarse = scan_flags(cf.p, n_obj, B.coarse_of_obj.p, s);
+    DBuf<int32_t> counts, offs;
+    counts.alloc(n_obj, s);
+    offs.alloc(n_obj + 1, s);
+    k_obj_rows<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, NC, B.obj_kind.p, B.opts.coarse, B.obj_size.p, B.obj_lo.p,
+                                                B.obj_hi.p, B.obj_nrows.p, B.obj_rot.p, counts.p);
+    UFE_CHECK_LAUNCH();
+    B.n_coarse = scan_counts(counts.p, n_obj, offs.p, s);
+    k_coarse_first<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, counts.p, offs.p, B.coarse_of_obj.p);
+    UFE_CHECK_LAUNCH();
   } else {
     B.n_coarse = 0;
   }
@@ -899,8 +1003,8 @@ void bddc_build(Bddc& B) {
   nC.alloc(ns, s);
   nC.zero();
   if (n_obj) {
-    k_coarse_list<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.coarse_of_obj.p, B.obj_rep.p, m.n_neigh.p, B.coarse_obj.p,
-                                                   B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, nC.p);
+    k_coarse_list<<<grid_for(n_obj, T), T, 0, s>>>(n_obj, B.coarse_of_obj.p, B.obj_rep.p, B.obj_nrows.p, m.n_neigh.p,
+                                                   B.coarse_obj.p, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, nC.p);
     UFE_CHECK_LAUNCH();
   }
   B.C_ptr.alloc(ns + 1, s);
@@ -920,8 +1024,8 @@ void bddc_build(Bddc& B) {
   B.h_nC.resize(ns);
   B.max_nC = 0;
   for (int w = 0; w < ns; ++w) {
-    B.h_nI[w] = m.h_I_ptr[w + 1] - m.h_I_ptr[w];
-    B.h_nG[w] = m.h_G_ptr[w + 1] - m.h_G_ptr[w];
+    B.h_nI[w] = NC * (m.h_I_ptr[w + 1] - m.h_I_ptr[w]);
+    B.h_nG[w] = NC * (m.h_G_ptr[w + 1] - m.h_G_ptr[w]);
     B.h_nC[w] = hC[w + 1] - hC[w];
     B.max_nC = std::max(B.max_nC, B.h_nC[w]);
   }
@@ -975,24 +1079,34 @@ void bddc_build(Bddc& B) {
   AGG.zero();
   DBuf<int32_t>& ell_k = B.gi_k;
   DBuf<double>& ell_v = B.gi_v;
-  ell_k.alloc(std::max<int64_t>(m.n_Gloc, 1) * 27, s);
-  ell_v.alloc(std::max<int64_t>(m.n_Gloc, 1) * 27, s);
-  B.ig_k.alloc(std::max<int64_t>(m.n_Iloc, 1) * 27, s);
-  B.ig_v.alloc(std::max<int64_t>(m.n_Iloc, 1) * 27, s);
-  sI.alloc(std::max<int64_t>(m.n_Iloc, 1), s);
-  sG.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
-  dGraw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  const int KS = 27 * NC;
+  ell_k.alloc(std::max<int64_t>(B.n_vGloc, 1) * KS, s);
+  ell_v.alloc(std::max<int64_t>(B.n_vGloc, 1) * KS, s);
+  B.ig_k.alloc(std::max<int64_t>(B.n_vIloc, 1) * KS, s);
+  B.ig_v.alloc(std::max<int64_t>(B.n_vIloc, 1) * KS, s);
+  sI.alloc(std::max<int64_t>(B.n_vIloc, 1), s);
+  sG.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
+  dGraw.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
   const SubMeta sm = B.meta();
-  k_local_assemble<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
-  UFE_CHECK_LAUNCH();
-  k_gi_ell<<<ns, 256, 0, s>>>(sm, ell_k.p, ell_v.p);
-  UFE_CHECK_LAUNCH();
-  k_ig_ell<<<ns, 256, 0, s>>>(sm, B.ig_k.p, B.ig_v.p);
-  UFE_CHECK_LAUNCH();
+  if (NC == 3) {
+    k_local_assemble<3><<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
+    UFE_CHECK_LAUNCH();
+    k_off_ell<3><<<ns, 256, 0, s>>>(sm, LKIND_G, ell_k.p, ell_v.p);
+    UFE_CHECK_LAUNCH();
+    k_off_ell<3><<<ns, 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
+    UFE_CHECK_LAUNCH();
+  } else {
+    k_local_assemble<1><<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
+    UFE_CHECK_LAUNCH();
+    k_off_ell<1><<<ns, 256, 0, s>>>(sm, LKIND_G, ell_k.p, ell_v.p);
+    UFE_CHECK_LAUNCH();
+    k_off_ell<1><<<ns, 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
+    UFE_CHECK_LAUNCH();
+  }
   k_local_diag<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p, dGraw.p);
   UFE_CHECK_LAUNCH();
-  B.w.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
-  k_weights<<<grid_for(nd, T), T, 0, s>>>(nd, m.n_neigh.p, m.gpos.p, dGraw.p,
+  B.w.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
+  k_weights<<<grid_for(nd, T), T, 0, s>>>(nd, NC, m.n_neigh.p, m.gpos.p, dGraw.p,
                                           B.opts.weighting == UFE_WEIGHT_TOPOLOGICAL, B.w.p);
   UFE_CHECK_LAUNCH();
 
@@ -1035,15 +1149,15 @@ void bddc_build(Bddc& B) {
 
   ph_co.end(s);
   // ---- solver work space
-  B.tG.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
-  B.vw.alloc(std::max<int64_t>(m.n_Gloc, 1), s);
+  B.tG.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
+  B.vw.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
   B.gC.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
   B.uc.alloc(std::max<int64_t>(nco, 1), s);
   for (DBuf<double>* v : {&B.x, &B.r, &B.b, &B.z, &B.q, &B.p0, &B.p1}) {
-    v->alloc(nd, s);
+    v->alloc(NC * nd, s);
     v->zero();
   }
-  B.part_blocks = std::max<int64_t>(grid_for(nd, 256), 8 * (int64_t)ns) + 8;
+  B.part_blocks = std::max<int64_t>(grid_for(NC * nd, 256), 8 * (int64_t)ns) + 8;
   B.part.alloc(B.part_blocks * 2, s);
   B.sc.alloc(1, s);
   B.sc.zero();

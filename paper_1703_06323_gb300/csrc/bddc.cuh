@@ -6,9 +6,17 @@
 namespace ufe {
 
 // metadata the per-subdomain solve kernels read (all device pointers)
+// Index spaces: a node-level list (I_list, G_list: free-node DOF ids) holds ncomp
+// vector DOFs per entry; vector DOF ncomp d + c of node DOF d, local vector index
+// ncomp p + c of local node p, and vector CSR pointers vI_ptr = ncomp I_ptr,
+// vG_ptr = ncomp G_ptr.  Poisson has ncomp = 1 and both spaces coincide.
 struct SubMeta {
   GridGeom g;
   int n_sub;
+  int ncomp;
+  const int32_t* vI_ptr;    // vector CSR pointers of the interior / interface DOFs
+  const int32_t* vG_ptr;
+  const double* Kref;       // elasticity: h Khat_el
   const int32_t* sub_block;
   const int32_t* sub_of_cell;
   const uint8_t* cell_type;
@@ -62,9 +70,19 @@ struct Bddc {
   bool mixed = false;
 
   // objects (Sect. 3.2, Sect. 4.4)
+  int ncomp = 1;
   int64_t n_obj = 0, n_corner = 0, n_edge = 0, n_face = 0, n_coarse = 0, n_Cloc = 0;
   int max_nC = 0;
+  int max_nIv = 0, max_nGv = 0;         // largest vector interior / interface sizes
+  int64_t n_vIloc = 0, n_vGloc = 0;     // vector local slots
+  DBuf<int32_t> vI_ptr, vG_ptr;
+  DBuf<int32_t> obj_nrows;              // coarse rows (coarse DOFs) per object
+  DBuf<int32_t> obj_rot;                // elasticity: bit k = rotation row about axis k kept
+  DBuf<long long> obj_sum;              // sum of the node grid coordinates of each object (3 per object)
+  DBuf<int32_t> obj_lo, obj_hi;         // coordinate bounds of each object (3 per object)
   DBuf<int32_t> obj_of_dof, obj_kind, obj_rep, obj_size, coarse_of_obj, coarse_obj, coarse_rep;
+  // coarse_of_obj: first coarse row of an object (-1 if not a coarse object);
+  // coarse_obj / coarse_rep / coarse_nn are per coarse row
   DBuf<uint8_t> coarse_nn;      // |neigh| of each coarse DOF
   DBuf<int32_t> C_ptr, C_list, cpos;
   std::vector<int32_t> h_nI, h_nG, h_nC;

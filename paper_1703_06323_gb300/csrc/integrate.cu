@@ -439,4 +439,338 @@ void system_build(System& sys, const double* kappa, const double* f, const doubl
   UFE_CHECK_LAUNCH();
 }
 
+// ---------------------------------------------------------------------------
+// linear elasticity (vector Q1, 3 DOFs per node): 24 x 24 cut-cell matrices
+// ---------------------------------------------------------------------------
+// The element matrix is assembled from the gradient Gram matrix of the cut part
+//   Gm[p][q] = int d_i N_a d_j N_b    (p = 3a + i, q = 3b + j; symmetric, 300 entries)
+// as K[3a+i][3b+j] = lam Gm[3a+i][3b+j] + mu Gm[3a+j][3b+i] + delta_ij mu sum_d Gm[3a+d][3b+d].
+// One warp per cut cell.  Each lane owns about ten entries of Gm and walks the
+// quadrature points 32 at a time: first every lane evaluates the 24 gradients of
+// one point into shared memory, then every lane accumulates its entries over the
+// 32 points (fixed order, no cross-lane reduction of Gm).  Loads (body force with
+// the 35-point rule, boundary traction sigma_h n with the facet rule) use per-lane
+// partial sums reduced with shuffles, as in the Poisson kernel.
+constexpr int kElWarps = 4;
+constexpr int kGram = 300;
+constexpr int kGramPerLane = (kGram + 31) / 32;
+
+__device__ __forceinline__ int gram_index(int p, int q) {
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+  return p * 24 - (p * (p - 1)) / 2 + (q - p);
+}
+
+__global__ void __launch_bounds__(kElWarps * 32)
+k_integrate_cut_el(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells, const double* __restrict__ phi,
+                   const double* __restrict__ f, const double* __restrict__ sig, double lam, double mu,
+                   double* __restrict__ K_cut, double* __restrict__ load_cut, double* __restrict__ eta) {
+  __shared__ double s_tet[kTetPts * 5];
+  __shared__ double s_tet5[kTet5Pts * 5];
+  __shared__ double s_tri[kTriPts * 4];
+  __shared__ uint8_t s_gp[kGram], s_gq[kGram];
+  __shared__ CellGeom geo[kElWarps];
+  __shared__ double s_f[kElWarps][8][3];
+  __shared__ double s_s[kElWarps][8][9];
+  __shared__ double s_pt[kElWarps][32 * 25];   // a chunk of points: 24 gradients + weight; later Gm
+  for (int e = threadIdx.x; e < kTetPts; e += blockDim.x) {
+    for (int c = 0; c < 4; ++c) s_tet[e * 5 + c] = c_tet_bary[e * 4 + c];
+    s_tet[e * 5 + 4] = c_tet_w[e];
+  }
+  for (int e = threadIdx.x; e < kTet5Pts; e += blockDim.x) {
+    for (int c = 0; c < 4; ++c) s_tet5[e * 5 + c] = c_tet5_bary[e * 4 + c];
+    s_tet5[e * 5 + 4] = c_tet5_w[e];
+  }
+  for (int e = threadIdx.x; e < kTriPts; e += blockDim.x) {
+    for (int c = 0; c < 3; ++c) s_tri[e * 4 + c] = c_tri_bary[e * 3 + c];
+    s_tri[e * 4 + 3] = c_tri_w[e];
+  }
+  if (threadIdx.x < 24) {
+    const int p = threadIdx.x;
+    for (int q = p; q < 24; ++q) {
+      const int e = gram_index(p, q);
+      s_gp[e] = (uint8_t)p;
+      s_gq[e] = (uint8_t)q;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t kc = (int64_t)blockIdx.x * kElWarps + warp;
+  const bool valid = kc < n_cut;
+  CellGeom& G = geo[warp];
+  int ntet_l = 0, ntri_l = 0;
+  double st[3][12], tr[2][12];
+  if (valid) {
+    const int64_t c = cut_cells[kc];
+    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+    if (lane < 8) {
+      const int64_t v = g.node(i + (lane & 1), j + ((lane >> 1) & 1), k + (lane >> 2));
+      for (int d = 0; d < 3; ++d) s_f[warp][lane][d] = f ? f[3 * v + d] : 0.0;
+      for (int d = 0; d < 9; ++d) s_s[warp][lane][d] = sig ? sig[9 * v + d] : 0.0;
+    }
+    if (lane < 6) {
+      const int ax0[6] = {0, 0, 1, 1, 2, 2};
+      const int ax1[6] = {1, 2, 0, 2, 0, 1};
+      const int vid[4] = {0, 1 << ax0[lane], (1 << ax0[lane]) | (1 << ax1[lane]), 7};
+      Vec3 P[4];
+      double F[4];
+      for (int m = 0; m < 4; ++m) {
+        P[m] = {(double)(vid[m] & 1), (double)((vid[m] >> 1) & 1), (double)(vid[m] >> 2)};
+        F[m] = phi[g.node(i + (vid[m] & 1), j + ((vid[m] >> 1) & 1), k + (vid[m] >> 2))];
+      }
+      clip_tet(P, F, st, ntet_l, tr, ntri_l);
+    }
+  }
+  int off_t = ntet_l, off_r = ntri_l;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const int a = __shfl_up_sync(0xffffffffu, off_t, o), b = __shfl_up_sync(0xffffffffu, off_r, o);
+    if (lane >= o) {
+      off_t += a;
+      off_r += b;
+    }
+  }
+  const int tot_t = __shfl_sync(0xffffffffu, off_t, 7), tot_r = __shfl_sync(0xffffffffu, off_r, 7);
+  off_t -= ntet_l;
+  off_r -= ntri_l;
+  for (int a = 0; a < ntet_l; ++a)
+    for (int e = 0; e < 12; ++e) G.tet[off_t + a][e] = st[a][e];
+  for (int a = 0; a < ntri_l; ++a)
+    for (int e = 0; e < 12; ++e) G.tri[off_r + a][e] = tr[a][e];
+  if (lane == 0) {
+    G.n_tet = tot_t;
+    G.n_tri = (sig != nullptr) ? tot_r : 0;
+  }
+  __syncthreads();
+  double gacc[kGramPerLane], lacc[24], vol = 0.0;
+#pragma unroll
+  for (int t = 0; t < kGramPerLane; ++t) gacc[t] = 0.0;
+#pragma unroll
+  for (int e = 0; e < 24; ++e) lacc[e] = 0.0;
+  double* pts = s_pt[warp];
+  if (valid) {
+    const double h = g.h, h3 = h * h * h, h2 = h * h;
+    // stiffness: degree-5 rule, 32 points per round
+    const int n_k = G.n_tet * kTet5Pts;
+    for (int base = 0; base < n_k; base += 32) {
+      const int it = base + lane;
+      if (it < n_k) {
+        const double* T = G.tet[it / kTet5Pts];
+        const double* R = s_tet5 + (it % kTet5Pts) * 5;
+        const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+        const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+        const double wx = T[9] - T[0], wy = T[10] - T[1], wz = T[11] - T[2];
+        const double tv =
+            fabs(ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx)) / 6.0;
+        const double px = R[0] * T[0] + R[1] * T[3] + R[2] * T[6] + R[3] * T[9];
+        const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7] + R[3] * T[10];
+        const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8] + R[3] * T[11];
+        const double wq = R[4] * tv;
+        double N[8], Gd[8][3];
+        q1_shape_grad(px, py, pz, N, Gd);
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) pts[lane * 25 + 3 * a + d] = Gd[a][d];
+        pts[lane * 25 + 24] = wq;
+        vol += wq;
+      }
+      __syncwarp();
+      const int np = min(32, n_k - base);
+#pragma unroll
+      for (int t = 0; t < kGramPerLane; ++t) {
+        const int e = lane + 32 * t;
+        if (e < kGram) {
+          const int p = s_gp[e], q = s_gq[e];
+          double a = 0.0;
+          for (int k = 0; k < np; ++k) a += pts[k * 25 + 24] * pts[k * 25 + p] * pts[k * 25 + q];
+          gacc[t] += a;
+        }
+      }
+      __syncwarp();
+    }
+    // loads: body force (35-point rule) and boundary traction (facet rule)
+    const int n_l = G.n_tet * kTetPts;
+    const int n_all = n_l + G.n_tri * kTriPts;
+    for (int it = lane; it < n_all; it += 32) {
+      if (it < n_l) {
+        const double* T = G.tet[it / kTetPts];
+        const double* R = s_tet + (it % kTetPts) * 5;
+        const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+        const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+        const double wx = T[9] - T[0], wy = T[10] - T[1], wz = T[11] - T[2];
+        const double tv =
+            fabs(ux * (vy * wz - vz * wy) - uy * (vx * wz - vz * wx) + uz * (vx * wy - vy * wx)) / 6.0;
+        const double px = R[0] * T[0] + R[1] * T[3] + R[2] * T[6] + R[3] * T[9];
+        const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7] + R[3] * T[10];
+        const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8] + R[3] * T[11];
+        const double wq = R[4] * tv;
+        double N[8];
+        q1_shape(px, py, pz, N);
+        double fh[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) fh[c] += N[a] * s_f[warp][a][c];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) lacc[3 * a + c] += wq * N[a] * fh[c] * h3;
+      } else {
+        const int r = it - n_l;
+        const double* T = G.tri[r / kTriPts];
+        const double* R = s_tri + (r % kTriPts) * 4;
+        const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+        const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+        const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
+        const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+        const double px = R[0] * T[0] + R[1] * T[3] + R[2] * T[6];
+        const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7];
+        const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8];
+        const double wq = R[3] * area;
+        double N[8];
+        q1_shape(px, py, pz, N);
+        double sh[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) sh[e] = 0.0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int e = 0; e < 9; ++e) sh[e] += N[a] * s_s[warp][a][e];
+        double tq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tq[c] = sh[3 * c] * T[9] + sh[3 * c + 1] * T[10] + sh[3 * c + 2] * T[11];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) lacc[3 * a + c] += wq * N[a] * tq[c] * h2;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 24; ++e) {
+    double v = lacc[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    lacc[e] = v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vol += __shfl_xor_sync(0xffffffffu, vol, o);
+  // Gm into shared memory (reusing the point buffer), then the element matrix
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < kGramPerLane; ++t) {
+    const int e = lane + 32 * t;
+    if (e < kGram) pts[e] = gacc[t];
+  }
+  __syncwarp();
+  if (valid) {
+    for (int e = lane; e < 576; e += 32) {
+      const int p = e / 24, q = e % 24;
+      const int a = p / 3, i = p % 3, b = q / 3, j = q % 3;
+      double v = lam * pts[gram_index(p, q)] + mu * pts[gram_index(3 * a + j, 3 * b + i)];
+      if (i == j)
+        v += mu * (pts[gram_index(3 * a, 3 * b)] + pts[gram_index(3 * a + 1, 3 * b + 1)] +
+                   pts[gram_index(3 * a + 2, 3 * b + 2)]);
+      K_cut[kc * 576 + e] = v * g.h;
+    }
+    if (lane == 0) {
+      for (int e = 0; e < 24; ++e) load_cut[kc * 24 + e] = lacc[e];
+      eta[kc] = vol;
+    }
+  }
+}
+
+// elasticity right-hand side: b = sum_e load_e - A_FC g_C, three components per free node
+__global__ void k_rhs_el(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                         const int32_t* __restrict__ dof_of_node, const uint8_t* __restrict__ cell_type,
+                         const int32_t* __restrict__ cut_index, const double* __restrict__ Kref,
+                         const double* __restrict__ K_cut, const double* __restrict__ load_cut,
+                         const double* __restrict__ kappa, const double* __restrict__ f,
+                         const double* __restrict__ gval, const uint8_t* __restrict__ node_flags,
+                         double* __restrict__ b) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof) return;
+  const int64_t v = node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  const double h = g.h, h3 = h * h * h;
+  double sum[3] = {0.0, 0.0, 0.0};
+  for (int dk = -1; dk <= 0; ++dk)
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        const int ci = i + di, cj = j + dj, ck = k + dk;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
+        const int64_t c = g.cell(ci, cj, ck);
+        const uint8_t t = cell_type[c];
+        if (t == UFE_CELL_EXTERNAL) continue;
+        const int a = (-di) + 2 * (-dj) + 4 * (-dk);
+        const int32_t cx = t == UFE_CELL_CUT ? cut_index[c] : -1;
+        for (int comp = 0; comp < 3; ++comp) {
+          if (t == UFE_CELL_INTERNAL) {
+            if (f) {
+              double s = 0.0;
+              for (int bb = 0; bb < 8; ++bb)
+                s += q1_mhat(a, bb) * f[3 * g.node(ci + (bb & 1), cj + ((bb >> 1) & 1), ck + (bb >> 2)) + comp];
+              sum[comp] += h3 * s;
+            }
+          } else {
+            sum[comp] += load_cut[(int64_t)cx * 24 + 3 * a + comp];
+          }
+        }
+        if (gval) {
+          const double kap = kappa ? kappa[c] : 1.0;
+          const double* Ke = t == UFE_CELL_INTERNAL ? Kref : K_cut + (int64_t)cx * 576;
+          for (int bb = 0; bb < 8; ++bb) {
+            const int64_t vb = g.node(ci + (bb & 1), cj + ((bb >> 1) & 1), ck + (bb >> 2));
+            if (dof_of_node[vb] >= 0 || !(node_flags[vb] & 1)) continue;
+            for (int comp = 0; comp < 3; ++comp)
+              for (int jc = 0; jc < 3; ++jc)
+                sum[comp] -= kap * Ke[(3 * a + comp) * 24 + 3 * bb + jc] * gval[3 * vb + jc];
+          }
+        }
+      }
+  for (int comp = 0; comp < 3; ++comp) b[3 * d + comp] = sum[comp];
+}
+
+void system_build_elastic(System& sys, const double* kappa, const double* f, const double* sig, const double* gval) {
+  ensure_constants();
+  Mesh& m = *sys.mesh;
+  cudaStream_t s = sys.stream;
+  const int64_t n_cut = m.n_cut;
+  m.cut_cells.alloc(n_cut > 0 ? n_cut : 1, s);
+  launch_cut_list(m, s);
+  {
+    std::vector<double> K(576);
+    elastic_khat(sys.lam, sys.mu, K.data());
+    for (double& x : K) x *= m.g.h;
+    sys.Kref.alloc(576, s);
+    UFE_CUDA(cudaMemcpyAsync(sys.Kref.p, K.data(), 576 * 8, cudaMemcpyHostToDevice, s));
+    UFE_CUDA(cudaStreamSynchronize(s));
+  }
+  sys.K_cut.alloc((n_cut > 0 ? n_cut : 1) * 576, s);
+  sys.load_cut.alloc((n_cut > 0 ? n_cut : 1) * 24, s);
+  sys.eta.alloc(n_cut > 0 ? n_cut : 1, s);
+  if (n_cut > 0) {
+    TimedLaunch tl;
+    tl.begin("integrate_cut", s);
+    k_integrate_cut_el<<<grid_for(n_cut, kElWarps), kElWarps * 32, 0, s>>>(
+        m.g, n_cut, m.cut_cells.p, m.phi.p, f, sig, sys.lam, sys.mu, sys.K_cut.p, sys.load_cut.p, sys.eta.p);
+    UFE_CHECK_LAUNCH();
+    tl.end(s);
+  }
+  sys.gnode.alloc(3 * m.g.n_nodes(), s);
+  if (gval)
+    UFE_CUDA(cudaMemcpyAsync(sys.gnode.p, gval, 3 * m.g.n_nodes() * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    sys.gnode.zero();
+  sys.b.alloc(3 * m.n_dof, s);
+  k_rhs_el<<<grid_for(m.n_dof, 128), 128, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p,
+                                                   m.cut_index.p, sys.Kref.p, sys.K_cut.p, sys.load_cut.p, kappa, f,
+                                                   gval, m.node_flags.p, sys.b.p);
+  UFE_CHECK_LAUNCH();
+}
+
 }  // namespace ufe

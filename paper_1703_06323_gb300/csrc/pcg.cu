@@ -87,17 +87,18 @@ __device__ double sum_partials(const double* part, int n, int stride) {
 // ---------------------------------------------------------------------------
 struct OpArgs {
   GridGeom g;
-  int64_t n_dof;
+  int64_t n_dof;            // free nodes
   const int32_t* node_of_dof;
   const int32_t* dof_of_node;
   const uint8_t* cell_type;
   const int32_t* cut_index;
-  const double* K_cut;
+  const double* K_cut;      // n_cut x (8 ncomp)^2
   const double* kappa;
+  const double* Kref;       // elasticity: h Khat_el
 };
 
 template <typename Val>
-__device__ __forceinline__ double apply_row(const OpArgs& a, int64_t d, Val val) {
+__device__ __forceinline__ double apply_row(const OpArgs& a, int64_t d, Val val) {  // Poisson
   const GridGeom& g = a.g;
   const int64_t v = a.node_of_dof[d];
   const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
@@ -148,23 +149,81 @@ __device__ __forceinline__ double apply_row(const OpArgs& a, int64_t d, Val val)
   return acc;
 }
 
+// elasticity: the three rows of free node d, y_c = sum over the cells around d of
+// kappa_e K_e[3 a + c][3 b + j] x_{3 e_b + j}  (val(3 e + j) returns the input entry)
+template <typename Val>
+__device__ __forceinline__ void apply_node_el(const OpArgs& a, int64_t d, Val val, double y[3]) {
+  const GridGeom& g = a.g;
+  const int64_t v = a.node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  y[0] = y[1] = y[2] = 0.0;
+  for (int dk = -1; dk <= 0; ++dk)
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        const int ci = i + di, cj = j + dj, ck = k + dk;
+        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
+        const int64_t c = g.cell(ci, cj, ck);
+        const uint8_t t = a.cell_type[c];
+        if (t == UFE_CELL_EXTERNAL) continue;
+        const int av = (-di) + 2 * (-dj) + 4 * (-dk);
+        const double kap = a.kappa ? a.kappa[c] : 1.0;
+        const double* Ke = (t == UFE_CELL_INTERNAL ? a.Kref : a.K_cut + (int64_t)a.cut_index[c] * 576) + 3 * av * 24;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int32_t e = a.dof_of_node[g.node(ci + (b & 1), cj + ((b >> 1) & 1), ck + (b >> 2))];
+          if (e < 0) continue;
+#pragma unroll
+          for (int jc = 0; jc < 3; ++jc) {
+            const double x = val(3 * (int64_t)e + jc);
+            s0 += Ke[3 * b + jc] * x;
+            s1 += Ke[24 + 3 * b + jc] * x;
+            s2 += Ke[48 + 3 * b + jc] * x;
+          }
+        }
+        y[0] += kap * s0;
+        y[1] += kap * s1;
+        y[2] += kap * s2;
+      }
+}
+
+// the NC rows of free node d
+template <int NC, typename Val>
+__device__ __forceinline__ void apply_node(const OpArgs& a, int64_t d, Val val, double y[NC]) {
+  if constexpr (NC == 1)
+    y[0] = apply_row(a, d, val);
+  else
+    apply_node_el(a, d, val, y);
+}
+
+template <int NC>
 __global__ void __launch_bounds__(kApplyThreads) k_apply(OpArgs a, const double* __restrict__ x, double* __restrict__ y) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= a.n_dof) return;
-  y[d] = apply_row(a, d, [&](int32_t e) { return x[e]; });
+  double yy[NC];
+  apply_node<NC>(a, d, [&](int64_t e) { return x[e]; }, yy);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) y[NC * d + c] = yy[c];
 }
 
 // r = b - A x, |r|^2 and |b|^2; mode 0 initialises the scalars, mode 1 only reports |b - A x|^2
+template <int NC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
            double* __restrict__ part, PcgScalars* sc, double rtol, int mode, double* out) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double rr = 0.0, bb = 0.0;
   if (d < a.n_dof) {
-    const double res = b[d] - apply_row(a, d, [&](int32_t e) { return x[e]; });
-    if (r) r[d] = res;
-    rr = res * res;
-    bb = b[d] * b[d];
+    double ax[NC];
+    apply_node<NC>(a, d, [&](int64_t e) { return x[e]; }, ax);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double res = b[NC * d + c] - ax[c];
+      if (r) r[NC * d + c] = res;
+      rr += res * res;
+      bb += b[NC * d + c] * b[NC * d + c];
+    }
   }
   rr = block_sum(rr);
   bb = block_sum(bb);
@@ -192,6 +251,7 @@ k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x,
 }
 
 // K1: p_new = z + beta p_old (beta = 0 for the first direction); q = A p_new; p.q
+template <int NC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_dir_apply(OpArgs a, const double* __restrict__ z, double* p0, double* p1, double* __restrict__ q,
             double* __restrict__ part, PcgScalars* sc) {
@@ -204,11 +264,16 @@ k_dir_apply(OpArgs a, const double* __restrict__ z, double* p0, double* p1, doub
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double pq = 0.0;
   if (d < a.n_dof) {
-    const double qd = apply_row(a, d, [&](int32_t e) { return z[e] + beta * pold[e]; });
-    const double pd = z[d] + beta * pold[d];
-    pnew[d] = pd;
-    q[d] = qd;
-    pq = pd * qd;
+    double qd[NC];
+    apply_node<NC>(a, d, [&](int64_t e) { return z[e] + beta * pold[e]; }, qd);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int64_t e = NC * d + c;
+      const double pd = z[e] + beta * pold[e];
+      pnew[e] = pd;
+      q[e] = qd[c];
+      pq += pd * qd[c];
+    }
   }
   pq = block_sum(pq);
   if (threadIdx.x == 0) part[blockIdx.x] = pq;
@@ -325,8 +390,8 @@ struct SubSizes {
 };
 __device__ __forceinline__ SubSizes sub_sizes(const SubMeta& sm, int w) {
   SubSizes z;
-  z.nI = sm.I_ptr[w + 1] - sm.I_ptr[w];
-  z.nG = sm.G_ptr[w + 1] - sm.G_ptr[w];
+  z.nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w];
+  z.nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   z.nC = sm.C_ptr[w + 1] - sm.C_ptr[w];
   z.ldI = pad4(z.nI);
   z.ldG = pad4(z.nG);
@@ -336,6 +401,12 @@ __device__ __forceinline__ SubSizes sub_sizes(const SubMeta& sm, int w) {
   z.bj = (b / sm.g.bx) % sm.g.by;
   z.bk = b / (sm.g.bx * sm.g.by);
   return z;
+}
+
+// global vector DOF of local interior vector index p of subdomain w
+template <int NC>
+__device__ __forceinline__ int64_t vdof_I(const SubMeta& sm, int w, int p) {
+  return (int64_t)NC * sm.I_list[sm.I_ptr[w] + p / NC] + p % NC;
 }
 
 // shared memory layout shared by the per-subdomain kernels
@@ -521,7 +592,7 @@ __device__ void cluster_gather(cg::cluster_group& cl, V* local, int n) {
 }
 
 // K3: y_I = A_II^-1 r_I; t_G = A_GI y_I
-template <typename TM>
+template <typename TM, int NC>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, double* __restrict__ tG,
                  const PcgScalars* sc, SubLaunch L) {
@@ -537,7 +608,7 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   RowStream<TM> rs;
   rs.begin(AIIinv + sm.off_II[w], r0, r1, z.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
-  for (int p = threadIdx.x; p < z.ldI; p += blockDim.x) xI[p] = p < z.nI ? (TM)r[sm.I_list[sm.I_ptr[w] + p]] : TM(0);
+  for (int p = threadIdx.x; p < z.ldI; p += blockDim.x) xI[p] = p < z.nI ? (TM)r[vdof_I<NC>(sm, w, p)] : TM(0);
   __syncthreads();
   rs.gemv(xI, S.dI + r0, sm.status);
   cl.sync();
@@ -545,20 +616,21 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   cl.sync();
   int j0, j1;
   row_slice(z.nG, rank, j0, j1);
-  const int64_t e0 = 27 * (int64_t)sm.G_ptr[w];
+  constexpr int KS = 27 * NC;
+  const int64_t e0 = KS * (int64_t)sm.vG_ptr[w];
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     double t = 0.0;
-#pragma unroll
-    for (int o = 0; o < 27; ++o) {
+#pragma unroll 27
+    for (int o = 0; o < KS; ++o) {
       const int32_t k = sm.gi_k[e0 + (int64_t)o * z.nG + j];
       if (k >= 0) t += sm.gi_v[e0 + (int64_t)o * z.nG + j] * S.dI[k];
     }
-    tG[sm.G_ptr[w] + j] = t;
+    tG[sm.vG_ptr[w] + j] = t;
   }
 }
 
 // K4: r~ = w (r_G - sum t_G); v = K r~ (stored weighted: vw = w v); g = Phi^T r~
-template <typename TM>
+template <typename TM, int NC>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Phi, const double* __restrict__ r,
                const double* __restrict__ tG, double* __restrict__ vw, double* __restrict__ gC, const PcgScalars* sc,
@@ -578,14 +650,15 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   RowStream<TM> rs;
   rs.begin(Kop + sm.off_GG[w], r0, r1, z.ldG, S.stage, full, L.n_stages);
   TM* xG = reinterpret_cast<TM*>(S.xT);
-  const int g0 = sm.G_ptr[w];
+  const int g0 = sm.vG_ptr[w];
   for (int j = threadIdx.x; j < z.ldG; j += blockDim.x) {
     TM v = TM(0);
     if (j < z.nG) {
-      const int32_t xi = sm.G_list[g0 + j];
-      double s = r[xi];
+      const int32_t xi = sm.G_list[sm.G_ptr[w] + j / NC];
+      const int c = j % NC;
+      double s = r[(int64_t)NC * xi + c];
       const int cnt = sm.n_neigh[xi];
-      for (int k = 0; k < cnt; ++k) s -= tG[sm.gpos[(int64_t)xi * 8 + k]];
+      for (int k = 0; k < cnt; ++k) s -= tG[(int64_t)NC * sm.gpos[(int64_t)xi * 8 + k] + c];
       v = (TM)(sm.w[g0 + j] * s);
     }
     xG[j] = v;
@@ -664,7 +737,7 @@ __global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ 
 }
 
 // K6: coarse prolongation, vw += w Phi u_c^w on the interface rows of w
-template <typename TM>
+template <typename TM, int NC>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict__ uc, double* __restrict__ vw,
                const PcgScalars* sc, SubLaunch L) {
@@ -685,13 +758,13 @@ k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict_
   else
     cta_gemv_rows<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
   __syncthreads();
-  const int g0 = sm.G_ptr[w];
+  const int g0 = sm.vG_ptr[w];
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vw[g0 + j] += sm.w[g0 + j] * S.dG[j];
 }
 
 // K7: u_G = sum_w' w' (v + Phi u_c) (the weighted local values, W); z_G = u_G (the
 // owner writes); z_I = A_II^-1 (r_I - A_IG u_G) (harmonic extension)
-template <typename TM>
+template <typename TM, int NC>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, const double* __restrict__ vw,
              double* __restrict__ z, double* __restrict__ part, PcgScalars* sc, SubLaunch L, int with_dots) {
@@ -708,38 +781,41 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   rs.begin(AIIinv + sm.off_II[w], p0, p1, zz.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
   double rz = 0.0, rzo = 0.0;
-  const int g0 = sm.G_ptr[w];
+  const int gn0 = sm.G_ptr[w];
   // the whole interface vector of w (cheap gathers, computed by every CTA)
   for (int j = threadIdx.x; j < zz.nG; j += blockDim.x) {
-    const int32_t xi = sm.G_list[g0 + j];
+    const int32_t xi = sm.G_list[gn0 + j / NC];
+    const int c = j % NC;
     const int cnt = sm.n_neigh[xi];
     double u = 0.0;
-    for (int k = 0; k < cnt; ++k) u += vw[sm.gpos[(int64_t)xi * 8 + k]];
+    for (int k = 0; k < cnt; ++k) u += vw[(int64_t)NC * sm.gpos[(int64_t)xi * 8 + k] + c];
     S.dG[j] = u;
   }
   __syncthreads();
   int j0, j1;
   row_slice(zz.nG, rank, j0, j1);
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    const int32_t xi = sm.G_list[g0 + j];
+    const int32_t xi = sm.G_list[gn0 + j / NC];
     if (sm.neigh[(int64_t)xi * 8] != w) continue;
+    const int64_t e = (int64_t)NC * xi + j % NC;
     const double u = S.dG[j];
     if (with_dots) {
-      rz += r[xi] * u;
-      rzo += r[xi] * z[xi];
+      rz += r[e] * u;
+      rzo += r[e] * z[e];
     }
-    z[xi] = u;
+    z[e] = u;
   }
   // interior right-hand side r_I - A_IG u_G for this CTA's rows, then exchanged
-  const int64_t e0 = 27 * (int64_t)sm.I_ptr[w];
+  constexpr int KS = 27 * NC;
+  const int64_t e0 = KS * (int64_t)sm.vI_ptr[w];
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     double t = 0.0;
-#pragma unroll
-    for (int o = 0; o < 27; ++o) {
+#pragma unroll 27
+    for (int o = 0; o < KS; ++o) {
       const int32_t k = sm.ig_k[e0 + (int64_t)o * zz.nI + p];
       if (k >= 0) t += sm.ig_v[e0 + (int64_t)o * zz.nI + p] * S.dG[k];
     }
-    xI[p] = (TM)(r[sm.I_list[sm.I_ptr[w] + p]] - t);
+    xI[p] = (TM)(r[vdof_I<NC>(sm, w, p)] - t);
   }
   for (int p = zz.nI + threadIdx.x; p < zz.ldI; p += blockDim.x) xI[p] = TM(0);
   cl.sync();
@@ -747,7 +823,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   cl.sync();
   rs.gemv(xI, S.dI + p0, sm.status);
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const int32_t d = sm.I_list[sm.I_ptr[w] + p];
+    const int64_t d = vdof_I<NC>(sm, w, p);
     const double zn = S.dI[p];
     if (with_dots) {
       rz += r[d] * zn;
@@ -786,6 +862,7 @@ static OpArgs op_args(const System& sys) {
   a.cut_index = m.cut_index.p;
   a.K_cut = sys.K_cut.p;
   a.kappa = sys.has_kappa ? sys.kappa.p : nullptr;
+  a.Kref = sys.Kref.p;
   return a;
 }
 
@@ -833,7 +910,10 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
   const OpArgs a = op_args(sys);
   TimedLaunch t;
   t.begin("apply", s);
-  k_apply<<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+  if (sys.ncomp == 3)
+    k_apply<3><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+  else
+    k_apply<1><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
   UFE_CHECK_LAUNCH();
   t.end(s);
 }
@@ -843,10 +923,9 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
 constexpr size_t kStageBudget = 26 * 1024;
 
 static SubLaunch sub_launch(const Bddc& B, size_t tm_size, size_t* smem) {
-  const Mesh& m = *B.mesh;
   SubLaunch L;
-  L.ldImax = pad4(std::max(m.max_nI, 1));
-  L.ldGmax = pad4(std::max(m.max_nG, 1));
+  L.ldImax = pad4(std::max(B.max_nIv, 1));
+  L.ldGmax = pad4(std::max(B.max_nGv, 1));
   const size_t ldmax = (size_t)std::max(L.ldImax, L.ldGmax);
   const size_t stage = (size_t)kStreamRows * ldmax * tm_size;
   L.n_stages = (int)std::max<size_t>(1, std::min<size_t>(kMaxStages, kStageBudget / stage));
@@ -856,7 +935,7 @@ static SubLaunch sub_launch(const Bddc& B, size_t tm_size, size_t* smem) {
   return L;
 }
 
-template <typename TM>
+template <typename TM, int NC>
 static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
   const Mesh& m = *B.mesh;
   const SubMeta sm = B.meta();
@@ -868,11 +947,11 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
   TimedLaunch t3, t4, t5, t6, t7;   // per-stage event timing (outside graph capture, when enabled)
   t3.begin("prec_interior", s);
-  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, L);
+  k_prec_interior1<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, L);
   UFE_CHECK_LAUNCH();
   t3.end(s);
   t4.begin("prec_neumann", s);
-  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, L);
+  k_prec_neumann<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, L);
   UFE_CHECK_LAUNCH();
   t4.end(s);
   if (B.n_coarse > 0) {
@@ -883,28 +962,36 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
     UFE_CHECK_LAUNCH();
     t5.end(s);
     t6.begin("prec_prolong", s);
-    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
+    k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
     UFE_CHECK_LAUNCH();
     t6.end(s);
   }
   t7.begin("prec_final", s);
-  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, L, with_dots);
+  k_prec_final<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, L, with_dots);
   UFE_CHECK_LAUNCH();
   t7.end(s);
+}
+
+template <typename TM, int NC>
+static void set_smem_limits_for(size_t bytes) {
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_final<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  UFE_CUDA(cudaFuncSetAttribute(k_prec_prolong<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
 static void set_smem_limits(Bddc& B) {
   size_t sd = 0, sf = 0;
   sub_launch(B, 8, &sd);
   sub_launch(B, 4, &sf);
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_prolong<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_prolong<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+  UFE_REQUIRE(sd <= 227 * 1024, UFE_ERR_UNSUPPORTED, "local interface / interior sizes exceed one CTA's shared memory");
+  if (B.ncomp == 3) {
+    set_smem_limits_for<double, 3>(sd);
+    set_smem_limits_for<float, 3>(sf);
+  } else {
+    set_smem_limits_for<double, 1>(sd);
+    set_smem_limits_for<float, 1>(sf);
+  }
   const size_t csm = (size_t)B.ldc * 8;
   UFE_REQUIRE(csm <= 227 * 1024, UFE_ERR_UNSUPPORTED, "coarse problem larger than one CTA's shared memory");
   UFE_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(csm, 1)));
@@ -919,10 +1006,17 @@ static void check_device_status(Bddc& B) {
 }
 
 static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
-  if (B.mixed)
-    launch_preconditioner<float>(B, r, z, sc, with_dots, s);
-  else
-    launch_preconditioner<double>(B, r, z, sc, with_dots, s);
+  if (B.ncomp == 3) {
+    if (B.mixed)
+      launch_preconditioner<float, 3>(B, r, z, sc, with_dots, s);
+    else
+      launch_preconditioner<double, 3>(B, r, z, sc, with_dots, s);
+  } else {
+    if (B.mixed)
+      launch_preconditioner<float, 1>(B, r, z, sc, with_dots, s);
+    else
+      launch_preconditioner<double, 1>(B, r, z, sc, with_dots, s);
+  }
 }
 
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
@@ -933,9 +1027,14 @@ void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
 
 static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
   const unsigned nb = grid_for(a.n_dof, kApplyThreads);
-  k_dir_apply<<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  const int64_t nv = (int64_t)B.ncomp * a.n_dof;
+  if (B.ncomp == 3)
+    k_dir_apply<3><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  else
+    k_dir_apply<1><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   UFE_CHECK_LAUNCH();
-  k_update<<<nb, kApplyThreads, 0, s>>>(a.n_dof, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+  k_update<<<grid_for(nv, kApplyThreads), kApplyThreads, 0, s>>>(nv, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p,
+                                                                 B.sc.p);
   UFE_CHECK_LAUNCH();
   precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
 }
@@ -944,7 +1043,7 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
   const Mesh& m = *B.mesh;
   cudaStream_t s = B.stream;
   const OpArgs a = op_args(*B.sys);
-  const int64_t n = m.n_dof;
+  const int64_t n = (int64_t)B.ncomp * m.n_dof;   // vector length
   set_smem_limits(B);
   cudaEvent_t e0, e1;
   UFE_CUDA(cudaEventCreate(&e0));
@@ -956,8 +1055,11 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
   init.maxit = std::max(o.maxit, 0);
   init.flexible = o.flexible < 0 ? (B.mixed ? 1 : 0) : (o.flexible ? 1 : 0);
   UFE_CUDA(cudaMemcpyAsync(B.sc.p, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-  const unsigned nb = grid_for(n, kApplyThreads);
-  k_residual<<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
+  const unsigned nb = grid_for(m.n_dof, kApplyThreads);
+  if (B.ncomp == 3)
+    k_residual<3><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
+  else
+    k_residual<1><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
   UFE_CHECK_LAUNCH();
   precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
 
@@ -1010,7 +1112,10 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
   // true residual |b - A x| / |b|
   DBuf<double> out;
   out.alloc(2, s);
-  k_residual<<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, nullptr, B.part.p, B.sc.p, 0.0, 1, out.p);
+  if (B.ncomp == 3)
+    k_residual<3><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, nullptr, B.part.p, B.sc.p, 0.0, 1, out.p);
+  else
+    k_residual<1><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, nullptr, B.part.p, B.sc.p, 0.0, 1, out.p);
   UFE_CHECK_LAUNCH();
   std::vector<double> tr = to_host(out.p, 2, s);
   cudaEventDestroy(e0);
@@ -1054,7 +1159,7 @@ static double* noalloc_scratch_ptr() {
   return ptr[dev];
 }
 
-template <typename TM>
+template <typename TM, int NC>
 static void launch_preconditioner_static(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
                                          double* uc, cudaStream_t s) {
   const Mesh& m = *B.mesh;
@@ -1065,26 +1170,26 @@ static void launch_preconditioner_static(Bddc& B, const double* r, double* z, do
   const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
   const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
-  k_prec_interior1<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, L);
+  k_prec_interior1<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, L);
   UFE_CHECK_LAUNCH();
-  k_prec_neumann<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
+  k_prec_neumann<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
   UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
     const size_t csm = (size_t)B.ldc * 8;
     const unsigned cgr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
     k_coarse_solve<<<cgr, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, nullptr);
     UFE_CHECK_LAUNCH();
-    k_prec_prolong<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
+    k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
     UFE_CHECK_LAUNCH();
   }
-  k_prec_final<TM><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, L, 0);
+  k_prec_final<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, L, 0);
   UFE_CHECK_LAUNCH();
 }
 
 void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev) {
   const Mesh& m = *B.mesh;
-  UFE_REQUIRE(m.n_Gloc <= kNoAllocG, UFE_ERR_INVALID_ARG,
-              "ufe_bddc_apply_noalloc: " + std::to_string(m.n_Gloc) + " interface slots exceed the static limit of " +
+  UFE_REQUIRE(B.n_vGloc <= kNoAllocG, UFE_ERR_INVALID_ARG,
+              "ufe_bddc_apply_noalloc: " + std::to_string(B.n_vGloc) + " interface slots exceed the static limit of " +
                   std::to_string(kNoAllocG));
   UFE_REQUIRE(B.n_Cloc <= kNoAllocC, UFE_ERR_INVALID_ARG,
               "ufe_bddc_apply_noalloc: " + std::to_string(B.n_Cloc) +
@@ -1100,11 +1205,18 @@ void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev) {
   set_smem_limits(B);
   // every entry of z is written by the kernels; clearing it first keeps the
   // behaviour identical to ufe_bddc_apply
-  UFE_CUDA(cudaMemsetAsync(z_dev, 0, m.n_dof * sizeof(double), B.stream));
-  if (B.mixed)
-    launch_preconditioner_static<float>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
-  else
-    launch_preconditioner_static<double>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+  UFE_CUDA(cudaMemsetAsync(z_dev, 0, (size_t)B.ncomp * m.n_dof * sizeof(double), B.stream));
+  if (B.ncomp == 3) {
+    if (B.mixed)
+      launch_preconditioner_static<float, 3>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+    else
+      launch_preconditioner_static<double, 3>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+  } else {
+    if (B.mixed)
+      launch_preconditioner_static<float, 1>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+    else
+      launch_preconditioner_static<double, 1>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
+  }
   check_device_status(B);
 }
 

@@ -44,3 +44,45 @@ __device__ __forceinline__ void q1_shape_grad(double x, double y, double z, doub
 }
 
 }  // namespace ufe
+
+namespace ufe {
+
+// int over the unit cube of d_i N_a d_j N_b: a product of 1-D integrals of the
+// linear shape functions n_0 = 1 - x, n_1 = x (slopes s_0 = -1, s_1 = +1):
+//   int n_a' n_b' = s_a s_b,  int n_a' n_b = s_a / 2,  int n_a n_b = 1/3 (same) or 1/6
+__host__ __device__ inline double q1_grad_grad(int a, int b, int i, int j) {
+  double v = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const int ab = (a >> d) & 1, bb = (b >> d) & 1;
+    const double sa = ab ? 1.0 : -1.0, sb = bb ? 1.0 : -1.0;
+    const bool da = d == i, db = d == j;
+    if (da && db)
+      v *= sa * sb;
+    else if (da)
+      v *= 0.5 * sa;
+    else if (db)
+      v *= 0.5 * sb;
+    else
+      v *= ab == bb ? (1.0 / 3.0) : (1.0 / 6.0);
+  }
+  return v;
+}
+
+// unit-cube isotropic elasticity matrix (24 x 24, DOF 3 a + i):
+//   K[3a+i][3b+j] = lambda G(a,i;b,j) + mu G(a,j;b,i) + delta_ij mu sum_d G(a,d;b,d),
+//   G(a,i;b,j) = int d_i N_a d_j N_b
+inline void elastic_khat(double lam, double mu, double* K) {
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) {
+      double lap = 0.0;
+      for (int d = 0; d < 3; ++d) lap += q1_grad_grad(a, b, d, d);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double v = lam * q1_grad_grad(a, b, i, j) + mu * q1_grad_grad(a, b, j, i);
+          if (i == j) v += mu * lap;
+          K[(3 * a + i) * 24 + 3 * b + j] = v;
+        }
+    }
+}
+
+}  // namespace ufe

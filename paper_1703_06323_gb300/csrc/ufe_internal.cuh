@@ -168,16 +168,22 @@ enum : int { LKIND_NONE = 0, LKIND_I = 1, LKIND_G = 2 };
 __host__ __device__ inline int lmap_kind(int32_t code) { return (code >> 24) & 0xff; }
 __host__ __device__ inline int lmap_index(int32_t code) { return code & 0xffffff; }
 
+// Poisson (ncomp = 1) or linear elasticity (ncomp = 3, DOF 3 d + c of free node d).
+// Element matrices have ne = 8 ncomp rows (element DOF ncomp a + c of vertex a).
 struct System {
   Mesh* mesh = nullptr;
   cudaStream_t stream = nullptr;
+  int ncomp = 1;
+  double lam = 0.0, mu = 0.0;   // elasticity: Lame parameters
   bool has_kappa = false;
-  DBuf<double> kappa;       // n_cells (only if has_kappa)
-  DBuf<double> K_cut;       // n_cut * 64
-  DBuf<double> load_cut;    // n_cut * 8
+  DBuf<double> kappa;       // n_cells (only if has_kappa): scales the element matrix
+  DBuf<double> Kref;        // elasticity: h Khat_el (24 x 24)
+  DBuf<double> K_cut;       // n_cut * ne^2
+  DBuf<double> load_cut;    // n_cut * ne
   DBuf<double> eta;         // n_cut
-  DBuf<double> b;           // n_dof
-  DBuf<double> gnode;       // n_nodes: Dirichlet values read at constrained nodes (zeros if none given)
+  DBuf<double> b;           // ncomp * n_dof
+  DBuf<double> gnode;       // ncomp * n_nodes: Dirichlet values read at constrained nodes (zeros if none given)
+  int64_t n_vec() const { return (int64_t)ncomp * mesh->n_dof; }
 };
 
 struct Bddc;   // defined in bddc.cu
@@ -192,6 +198,8 @@ int64_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets_out, cuda
 
 void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node);
 void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* g);
+// elasticity: f 3 values per node, sigma 9 per node (may be null), g 3 per node (may be null)
+void system_build_elastic(System& sys, const double* kappa, const double* f, const double* sigma, const double* g);
 void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStream_t s);
 // dJ/dkappa_e = -ubar_e^T Khat_e lambda_e per cell (ubar: u with the Dirichlet values)
 void kappa_gradient(const System& sys, const double* u_dev, const double* lambda_dev, double* out_dev, cudaStream_t s);

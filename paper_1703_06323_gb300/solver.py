@@ -28,15 +28,22 @@ class Solver:
         self.bddc = None
         try:
             self.info = ufe.ufe_mesh_get_info(self.mesh)
-            self.system = ufe.ufe_assemble(self.mesh, a.get("kappa", p.kappa), a.get("f", p.f),
-                                           a.get("q", p.q), a.get("g", p.dirichlet_values))
+            if getattr(p, "ncomp", 1) == 3:
+                E, nu = p.lame
+                self.system = ufe.ufe_assemble_elastic(self.mesh, E, nu, a.get("kappa", p.kappa), a.get("f", p.f),
+                                                       a.get("q", p.q), a.get("g", p.dirichlet_values))
+            else:
+                self.system = ufe.ufe_assemble(self.mesh, a.get("kappa", p.kappa), a.get("f", p.f),
+                                               a.get("q", p.q), a.get("g", p.dirichlet_values))
             self.bddc = ufe.ufe_bddc_setup(self.system, WEIGHTING[weighting], OBJECTS[objects], COARSE[coarse],
                                            PRECISION[precision])
             self.bddc_info = ufe.ufe_bddc_get_info(self.bddc)
         except Exception:
             self.close()
             raise
-        self.n_dof = self.info["n_dof"]
+        # length of solution vectors: ncomp * free nodes (3 per node for elasticity)
+        self.ncomp = ufe.ufe_system_get_info(self.system)["ncomp"]
+        self.n_dof = ufe.ufe_system_get_info(self.system)["n"]
 
     def rhs(self):
         return ufe.ufe_system_get_rhs(self.system, self.n_dof)

@@ -86,6 +86,9 @@ def _load():
         "ufe_mesh_get_neighbours": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ufe_mesh_destroy": (None, [P]),
         "ufe_assemble": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.POINTER(P)]),
+        "ufe_assemble_elastic": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, P, P, P, P, ctypes.c_int,
+                                                ctypes.POINTER(P)]),
+        "ufe_system_get_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
         "ufe_system_get_rhs": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ufe_system_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
         "ufe_system_get_cut_data": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int]),
@@ -112,7 +115,7 @@ LIB = _load()
 EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_enable", "ufe_timing_reset",
             "ufe_timing_get", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
-            "ufe_assemble", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
+            "ufe_assemble", "ufe_assemble_elastic", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
             "ufe_bddc_apply_noalloc",
             "ufe_bddc_destroy", "ufe_pcg_solve", "ufe_adjoint")
@@ -238,8 +241,29 @@ def ufe_assemble(mesh, kappa_cells=None, f_nodes=None, flux_nodes=None, dirichle
     return out
 
 
-def ufe_system_get_rhs(system, n_dof):
-    return _get(LIB.ufe_system_get_rhs, system, n_dof, np.float64)
+def ufe_assemble_elastic(mesh, E, nu, E_scale_cells=None, f_nodes=None, stress_nodes=None, dirichlet_values=None):
+    """Q1^3 linear elasticity: f (n_nodes, 3), stress (n_nodes, 9) or None, Dirichlet values (n_nodes, 3)."""
+    def flat(a):
+        return None if a is None else (a.reshape(-1) if _is_torch(a) else np.asarray(a).reshape(-1))
+    args = [_ptr(flat(E_scale_cells), np.float64), _ptr(flat(f_nodes), np.float64),
+            _ptr(flat(stress_nodes), np.float64), _ptr(flat(dirichlet_values), np.float64)]
+    mem = _mem_of(*args)
+    out = ctypes.c_void_p()
+    _check(LIB.ufe_assemble_elastic(mesh, float(E), float(nu), args[0][0], args[1][0], args[2][0], args[3][0], mem,
+                                    ctypes.byref(out)))
+    return out
+
+
+def ufe_system_get_info(system):
+    nc = ctypes.c_int32()
+    n = ctypes.c_int64()
+    _check(LIB.ufe_system_get_info(system, ctypes.byref(nc), ctypes.byref(n)))
+    return {"ncomp": nc.value, "n": n.value}
+
+
+def ufe_system_get_rhs(system, n):
+    """The assembled right-hand side (n = ncomp * n_dof doubles)."""
+    return _get(LIB.ufe_system_get_rhs, system, n, np.float64)
 
 
 def ufe_system_apply(system, x, y=None):
@@ -252,13 +276,14 @@ def ufe_system_apply(system, x, y=None):
 
 
 def ufe_system_get_cut_data(system, n_cut):
+    ne = 8 * ufe_system_get_info(system)["ncomp"]
     cells = np.empty(n_cut, np.int32)
-    K = np.empty(n_cut * 64, np.float64)
-    load = np.empty(n_cut * 8, np.float64)
+    K = np.empty(n_cut * ne * ne, np.float64)
+    load = np.empty(n_cut * ne, np.float64)
     eta = np.empty(n_cut, np.float64)
     ptrs = [ctypes.c_void_p(a.ctypes.data) for a in (cells, K, load, eta)]
     _check(LIB.ufe_system_get_cut_data(system, *ptrs, MEM_HOST))
-    return cells, K.reshape(n_cut, 8, 8), load.reshape(n_cut, 8), eta
+    return cells, K.reshape(n_cut, ne, ne), load.reshape(n_cut, ne), eta
 
 
 def ufe_system_destroy(system):

@@ -3,6 +3,7 @@ import functools
 
 import numpy as np
 
+from oracle import elasticity as EL
 from oracle.assembly import System
 from oracle.bddc import BDDC
 from oracle.integration import Integration
@@ -83,10 +84,45 @@ class OracleRun:
         return pcg(self.sys.apply, self.sys.b, B.apply, rtol=rtol, maxit=2000)
 
 
+def _elastic_sphere(cells, sub, centre, radius, box_hi=(1.0, 1.0, 1.0), name="el_sphere"):
+    """A sphere crossing the clamped face x = 0 with body force (0, 0, -1)."""
+    X, Y, Z = inputs.node_coords((0, 0, 0), box_hi, cells)
+    c = np.asarray(centre)
+    phi = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) - radius
+    f = np.zeros((X.size, 3))
+    f[:, 2] = -1.0
+    return inputs.Problem(name=name, box_lo=np.zeros(3), box_hi=np.asarray(box_hi, float), cells=cells,
+                          sub_cells=sub, phi=phi, f=f, q=None, dirichlet_face_mask=inputs.FACE_XLO,
+                          pin_node=inputs.PIN_NONE, dirichlet_values=np.zeros((X.size, 3)), ncomp=3,
+                          lame=(1.0, 0.3))
+
+
+def elastic_problems():
+    """Small elasticity cases: several blocks, a ragged block grid, the patch test, a sphere union."""
+    return {
+        "el_sphere8": _elastic_sphere((8, 8, 8), (4, 4, 4), (0.2, 0.5, 0.5), 0.42),
+        "el_ragged": _elastic_sphere((12, 9, 6), (4, 3, 3), (0.25, 0.4, 0.24), 0.3, box_hi=(1.0, 0.75, 0.5),
+                                     name="el_ragged"),
+        "el_patch": inputs.elastic_patch(),
+        "el_spheres16": inputs.elastic_spheres(seed=0, n=16, sub=8),
+    }
+
+
+class ElasticOracleRun(OracleRun):
+    def __init__(self, p):
+        self.p = p
+        self.mesh = Mesh(p)
+        self.integ = EL.ElasticIntegration(self.mesh, p)
+        self.sys = EL.ElasticSystem(self.mesh, self.integ, p)
+        self._bddc = {}
+
+
 @functools.lru_cache(maxsize=None)
 def oracle_run(name):
     if name == "bumpy64":
         return OracleRun(inputs.bumpy_sphere(0))
+    if name.startswith("el_"):
+        return ElasticOracleRun(elastic_problems()[name])
     return OracleRun(small_problems()[name])
 
 

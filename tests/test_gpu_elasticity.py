@@ -1,0 +1,149 @@
+"""GPU parity of the linear-elasticity path (Q1^3, 3 DOFs per node) against the
+FP64 oracle, through the C ABI.
+
+Integer work (objects, coarse-DOF counts and numbering) bit for bit; element
+data, right-hand side and operator to rounding; preconditioner and solutions in
+the energy norm (FP64 1e-8 / mixed 1e-6 for solutions).
+"""
+import numpy as np
+import pytest
+
+from tests.oracle_cache import elastic_problems, energy_error, object_ids, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+NAMES = list(elastic_problems().keys())
+
+
+@pytest.fixture(scope="module")
+def ufe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06323_gb300 import build_ext
+    build_ext.build()
+    from paper_1703_06323_gb300 import ufe as U
+    return U
+
+
+def _solver(p, **kw):
+    from paper_1703_06323_gb300.solver import Solver
+    return Solver(p, **kw)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_elastic_cut_cells_rhs_and_operator(ufe, name):
+    orc = oracle_run(name)
+    m, integ = orc.mesh, orc.integ
+    with _solver(orc.p) as S:
+        assert S.ncomp == 3 and S.n_dof == 3 * m.n_dof
+        n_cut = S.info["n_cut_cells"]
+        assert n_cut == integ.cut_cells.size
+        cells, K, load, eta = ufe.ufe_system_get_cut_data(S.system, n_cut)
+        assert np.array_equal(cells, integ.cut_cells)
+        if n_cut:
+            assert np.abs(K - integ.K_cut).max() <= 1e-12 * np.abs(integ.K_cut).max()
+            lscale = max(np.abs(integ.load_cut).max(), 1e-300)
+            assert np.abs(load - integ.load_cut).max() <= 1e-12 * lscale
+            assert np.abs(eta - integ.eta).max() <= 1e-13
+        b = S.rhs()
+        assert np.abs(b - orc.sys.b).max() <= 1e-12 * np.abs(orc.sys.b).max()
+        x = np.random.default_rng(1).normal(size=S.n_dof)
+        y = S.apply(x)
+        ref = orc.sys.A @ x
+        assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("objects,coarse", [("v1", "cef"), ("std", "ce")])
+def test_elastic_objects_and_coarse_rows_bit_exact(ufe, name, objects, coarse):
+    orc = oracle_run(name)
+    m = orc.mesh
+    B = orc.bddc(objects=objects, coarse=coarse)
+    objs = m.objects(objects)
+    ref_ids, ref_kinds = object_ids(objs, m.n_dof)
+    with _solver(orc.p, objects=objects, coarse=coarse) as S:
+        ids, kinds, first = ufe.ufe_bddc_get_objects(S.bddc, m.n_dof)
+        assert np.array_equal(ids, ref_ids)
+        assert np.array_equal(kinds, ref_kinds)
+        assert S.bddc_info["n_coarse"] == B.n_coarse
+        # first coarse row of each kept object, in the oracle's object-by-object order
+        kept = {id(o): k for k, o in enumerate(B.objs)}
+        ref_first = -np.ones(len(objs), dtype=np.int64)
+        for i, o in enumerate(objs):
+            if id(o) in kept:
+                ref_first[i] = B.coarse_obj.index(kept[id(o)])
+        assert np.array_equal(first, ref_first)
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("weighting", ["stiffness", "topological"])
+def test_elastic_preconditioner_fp64(ufe, name, weighting):
+    """z = M r in FP64.  The explicit local operators pass through the inverse of
+    S_c = C S'^-1 C^T (unpivoted Gauss-Jordan), whose condition number reaches
+    1e5 .. 1e9 on these cut meshes once the rotation rows are present (the oracle
+    solves the saddle-point systems with pivoted LU instead): 1e-6 in the energy
+    norm.  The solution tests below hold the path to 1e-8."""
+    orc = oracle_run(name)
+    B = orc.bddc(weighting=weighting)
+    r = np.random.default_rng(2).normal(size=orc.sys.n)
+    ref = B.apply(r)
+    with _solver(orc.p, weighting=weighting) as S:
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_elastic_preconditioner_mixed(ufe, name):
+    """Mixed precision M r: FP32 local operators; the FP32 rounding of S'^-1 is
+    amplified by cond(S_c) (1e5 .. 1e9 here), so M r is an approximation of a few
+    1e-3 in the energy norm (1e-2 bound); flexible PCG absorbs it and the mixed
+    solutions still meet 1e-6 (test_elastic_pcg_solution)."""
+    orc = oracle_run(name)
+    B = orc.bddc()
+    r = np.random.default_rng(3).normal(size=orc.sys.n)
+    ref = B.apply(r)
+    with _solver(orc.p, precision="mixed") as S:
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-2
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_elastic_pcg_solution(ufe, name, precision):
+    orc = oracle_run(name)
+    ref = orc.solve(rtol=1e-12)
+    ref8 = orc.solve(rtol=1e-8)
+    with _solver(orc.p, precision=precision) as S:
+        x, info = S.solve(rtol=1e-8)
+    assert info["converged"] == 1
+    assert info["true_rel_residual"] <= 1e-8 * 1.5
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    floor = energy_error(orc.sys.A, ref8["x"], ref["x"])
+    assert energy_error(orc.sys.A, x, ref["x"]) <= max(tol, 4 * floor)
+    if precision == "fp64":
+        assert abs(info["iterations"] - ref8["iterations"]) <= 1
+
+
+def test_elastic_patch_test_on_the_gpu(ufe):
+    """The linear displacement with its traction on the cut plane is the discrete solution."""
+    orc = oracle_run("el_patch")
+    m = orc.mesh
+    ue = orc.p.u_exact[m.node_of_dof].ravel()
+    with _solver(orc.p) as S:
+        x, info = S.solve(rtol=1e-12)
+    assert info["converged"] == 1
+    assert energy_error(orc.sys.A, x, ue) <= 1e-9
+
+
+def test_adjoint_rejects_elasticity(ufe):
+    import torch
+    orc = oracle_run("el_sphere8")
+    with _solver(orc.p) as S:
+        n = S.n_dof
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        lam = torch.zeros_like(u)
+        g = torch.zeros(orc.mesh.grid.n_cells, dtype=torch.float64, device="cuda")
+        with pytest.raises(ufe.UfeError) as e:
+            ufe.ufe_adjoint(S.system, S.bddc, u, u, lam, g, rtol=1e-8, maxit=10)
+        assert e.value.status == ufe.ERR_UNSUPPORTED
