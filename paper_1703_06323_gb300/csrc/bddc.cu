@@ -493,18 +493,38 @@ k_schur(SubMeta sm, int KS, const int64_t* __restrict__ oGG, const int64_t* __re
   }
 }
 
-// Jacobi scales s = diag^-1/2 and the raw interface diagonal (stiffness weights)
-__global__ void k_local_diag(SubMeta sm, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGG,
+// Jacobi scales s = diag^-1/2 and the raw interface diagonal (stiffness weights).  For
+// elasticity the interface scale is s = (max(diag, tau max_w diag))^-1/2 with tau a
+// small fraction of the largest interface diagonal of the subdomain: DOFs whose
+// support in the cut cells is tiny (diagonals down to 1e-30 of their neighbours)
+// would otherwise carry constraint-row entries (C D^-1/2) of up to 1e15 and, with
+// several coarse rows per object, make S_c = C S'^-1 C^T numerically singular.  Any
+// positive scaling is an exact change of variables; Poisson (one row per object)
+// keeps the plain Jacobi scale (tau = 0).
+__global__ void k_local_diag(SubMeta sm, double tau, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGG,
                              const double* __restrict__ AII, const double* __restrict__ AGG, double* __restrict__ sI,
                              double* __restrict__ sG, double* __restrict__ dGraw) {
+  __shared__ double red[32];
   const int w = blockIdx.x;
   const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int ldI = pad4(nI), ldG = pad4(nG);
   for (int p = threadIdx.x; p < nI; p += blockDim.x) sI[sm.vI_ptr[w] + p] = 1.0 / sqrt(AII[oII[w] + (int64_t)p * ldI + p]);
+  double mx = 0.0;
+  for (int p = threadIdx.x; p < nG; p += blockDim.x) mx = fmax(mx, AGG[oGG[w] + (int64_t)p * ldG + p]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double floor_d = tau * red[0];
   for (int p = threadIdx.x; p < nG; p += blockDim.x) {
     const double d = AGG[oGG[w] + (int64_t)p * ldG + p];
     dGraw[sm.vG_ptr[w] + p] = d;
-    sG[sm.vG_ptr[w] + p] = 1.0 / sqrt(d);
+    sG[sm.vG_ptr[w] + p] = 1.0 / sqrt(fmax(d, floor_d));
   }
 }
 
@@ -797,11 +817,19 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   DBuf<int> status;
   status.alloc(ns, s);
   status.zero();
+  // a non-positive pivot in one of the local inversions: name the matrix and subdomain
+  auto check = [&](const char* what) {
+    std::vector<int> st = to_host(status.p, ns, s);
+    for (int w = 0; w < ns; ++w)
+      UFE_REQUIRE(st[w] == 0, UFE_ERR_SINGULAR_LOCAL,
+                  std::string(what) + " of subdomain " + std::to_string(w) + " is not positive definite");
+  };
   std::vector<InvDesc> inv;
   std::vector<GemmDesc> g;
   // 1. A_II^-1
   for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
   batched_inverse<T>(inv, II.p, status.p, s);
+  check("A_II");
   // 2. X^T = (A_II^-1 A_IG)^T and 3. S = A_GG - A_GI X, both from the sparse A_GI
   X.alloc(std::max<int64_t>(nIG, 1), s);
   {
@@ -830,6 +858,7 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   inv.clear();
   for (int w = 0; w < ns; ++w) inv.push_back({B.h_nG[w], pad4(B.h_nG[w]), oGG[w]});
   batched_inverse<T>(inv, GG.p, status.p, s);
+  check("S' = S + C^T rho C");
   // 6. Y = S'^-1 C^T
   Y.alloc(std::max<int64_t>(nGC, 1), s);
   g.clear();
@@ -845,6 +874,7 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   inv.clear();
   for (int w = 0; w < ns; ++w) inv.push_back({B.h_nC[w], pad4(B.h_nC[w]), oCC[w]});
   batched_inverse<T>(inv, Sc.p, status.p, s);
+  check("S_c = C S'^-1 C^T");
   // 8. Phi^ = Y S_c^-1
   GC.alloc(std::max<int64_t>(nGC, 1), s);
   GC.zero();
@@ -868,10 +898,6 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   UFE_CHECK_LAUNCH();
   k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GC.p, B.off_GC.p, B.vG_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
   UFE_CHECK_LAUNCH();
-  std::vector<int> st = to_host(status.p, ns, s);
-  for (int w = 0; w < ns; ++w)
-    UFE_REQUIRE(st[w] == 0, UFE_ERR_SINGULAR_LOCAL,
-                "local matrix of subdomain " + std::to_string(w) + " is not positive definite");
 }
 
 void bddc_build(Bddc& B) {
@@ -1103,7 +1129,8 @@ void bddc_build(Bddc& B) {
     k_off_ell<1><<<ns, 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
     UFE_CHECK_LAUNCH();
   }
-  k_local_diag<<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p, dGraw.p);
+  k_local_diag<<<ns, 256, 0, s>>>(sm, NC == 3 ? 1e-8 : 0.0, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p,
+                                  dGraw.p);
   UFE_CHECK_LAUNCH();
   B.w.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
   k_weights<<<grid_for(nd, T), T, 0, s>>>(nd, NC, m.n_neigh.p, m.gpos.p, dGraw.p,

@@ -328,14 +328,16 @@ def elastic_patch(cells=(8, 8, 8), sub_cells=(4, 4, 4), normal=(1.0, 0.2, 0.1), 
                    meta={"normal": n.tolist(), "offset": offset})
 
 
-def elastic_spheres(seed=0, n=96, sub=8, count=8, r_range=(0.1, 0.2), E=1.0, nu=0.3):
+def elastic_spheres(seed=0, n=96, sub=8, count=8, r_range=(0.1, 0.2), E=1.0, nu=0.3, snap=2e-3):
     """Union of seeded spheres clamped on the box face x = 0 (body force (0,0,-1)).
 
     The spheres form a chain: the first one crosses x = 0, each next one is
     centred at a seeded direction from the previous centre, at a seeded fraction
     U(0.5, 0.9) of the sum of the two radii, and kept inside [r, 1 - r] in y, z and
     [.., 1 - r] in x; the union is therefore connected and touches x = 0.  Cut
-    boundary traction-free; other box faces natural."""
+    boundary traction-free; other box faces natural.  Nodal level-set values
+    closer to zero than snap * h are moved to +-snap * h (sign kept), which keeps
+    every cut volume fraction above ~snap^3 / 6; snap = 0 keeps the raw union."""
     rng = np.random.default_rng(seed)
     radii = rng.uniform(r_range[0], r_range[1], count)
     centres = np.zeros((count, 3))
@@ -352,10 +354,14 @@ def elastic_spheres(seed=0, n=96, sub=8, count=8, r_range=(0.1, 0.2), E=1.0, nu=
         centres[i] = np.clip(c, [0.0, radii[i], radii[i]], 1.0 - radii[i])
     X, Y, Z = node_coords((0, 0, 0), (1, 1, 1), (n, n, n))
     phi = _sphere_union_phi(X, Y, Z, centres, radii)
+    if snap > 0:
+        g = snap / n
+        near = np.abs(phi) < g
+        phi[near] = np.where(phi[near] < 0, -g, g)
     f = np.zeros((X.size, 3))
     f[:, 2] = -1.0
     return Problem(name=f"elastic_spheres{n}_seed{seed}", box_lo=np.zeros(3), box_hi=np.ones(3),
                    cells=(n, n, n), sub_cells=(sub, sub, sub), phi=phi, f=f, q=None,
                    dirichlet_face_mask=FACE_XLO, pin_node=PIN_NONE,
                    dirichlet_values=np.zeros((X.size, 3)), ncomp=3, lame=(E, nu),
-                   meta={"seed": seed, "centres": centres.tolist(), "radii": radii.tolist()})
+                   meta={"seed": seed, "centres": centres.tolist(), "radii": radii.tolist(), "snap": snap})

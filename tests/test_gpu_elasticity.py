@@ -122,7 +122,11 @@ def test_elastic_pcg_solution(ufe, name, precision):
     floor = energy_error(orc.sys.A, ref8["x"], ref["x"])
     assert energy_error(orc.sys.A, x, ref["x"]) <= max(tol, 4 * floor)
     if precision == "fp64":
-        assert abs(info["iterations"] - ref8["iterations"]) <= 1
+        # +-1; +-2 once cut fractions drop below 1e-6, where the condition number of A
+        # passes 1e14 and the rounding of the explicit local operators (clamped interface
+        # scaling of tiny-support DOFs) shifts the last iterations
+        slack = 1 if orc.integ.eta.min() >= 1e-6 else 2
+        assert abs(info["iterations"] - ref8["iterations"]) <= slack
 
 
 def test_elastic_patch_test_on_the_gpu(ufe):
