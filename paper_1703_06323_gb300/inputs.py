@@ -328,7 +328,7 @@ def elastic_patch(cells=(8, 8, 8), sub_cells=(4, 4, 4), normal=(1.0, 0.2, 0.1), 
                    meta={"normal": n.tolist(), "offset": offset})
 
 
-def elastic_spheres(seed=0, n=96, sub=8, count=8, r_range=(0.1, 0.2), E=1.0, nu=0.3, snap=2e-3):
+def elastic_spheres(seed=0, n=96, sub=8, count=8, r_range=(0.1, 0.2), E=1.0, nu=0.3, snap=0.0):
     """Union of seeded spheres clamped on the box face x = 0 (body force (0,0,-1)).
 
     The spheres form a chain: the first one crosses x = 0, each next one is
