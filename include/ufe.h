@@ -298,7 +298,7 @@ typedef struct {
   double rtol;          /* stop when |r|_2 < rtol |b|_2 (Sect. 5.1); e.g. 1e-8 */
   int32_t maxit;        /* iteration cap */
   int32_t flexible;     /* 0 classical beta, 1 flexible beta, -1 auto (flexible iff mixed) */
-  int32_t check_every;  /* iterations per device-side graph launch between host checks (0 = 8) */
+  int32_t check_every;  /* unused: the iterations run in a device-side loop (kept for layout) */
   int32_t reserved;
 } ufe_solve_opts;
 
@@ -312,6 +312,10 @@ typedef struct {
 
 /*
  * ufe_pcg_solve -- BDDC-preconditioned CG (Sect. 5.1), all on the device.
+ * The solve runs as one CUDA graph built at the first call and reused: initial
+ * residual and preconditioner, a conditional while node around one iteration whose
+ * last kernel decides from the device-side state whether to run again (bounded by
+ * maxit + 1 passes), and the true residual; the host waits once.
  *  b     n doubles (n = ncomp n_dof) or NULL for the assembled right-hand side.
  *  x     n doubles: initial guess in, solution out.
  *  info  may be NULL.
@@ -319,6 +323,23 @@ typedef struct {
  */
 ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* bddc, const double* b, double* x, int mem,
                          const ufe_solve_opts* opts, ufe_solve_info* info);
+
+/*
+ * ufe_pcg_solve_batched -- n independent solves at once (many problems of uneven
+ * size, e.g. a serving queue; no counterpart in the paper).  Each problem's solve
+ * graph (as in ufe_pcg_solve) is launched on one of 16 library-owned streams after
+ * that problem's own stream, so the GPU runs the problems side by side; later work
+ * on each problem's stream waits for its solve.  Returns when all are done.
+ *  systems, bddcs  n handles; bddcs[i] set up on systems[i]; no handle twice.
+ *  b               NULL, or n pointers (each NULL for the assembled right-hand side).
+ *  x               n pointers: initial guesses in, solutions out (length ncomp n_dof each).
+ *  infos           n entries or NULL.
+ * Every problem is solved and reported; the return value is the first non-OK
+ * status among them (BREAKDOWN, NO_CONVERGENCE), or an argument / CUDA error.
+ */
+ufe_status ufe_pcg_solve_batched(int32_t n, ufe_system* const* systems, ufe_bddc* const* bddcs,
+                                 const double* const* b, double* const* x, int mem,
+                                 const ufe_solve_opts* opts, ufe_solve_info* infos);
 
 /*
  * ufe_adjoint -- gradient of J(u) = 1/2 |u - u_d|^2 over the free DOFs with

@@ -490,6 +490,48 @@ ufe_status ufe_pcg_solve(ufe_system* sys, ufe_bddc* B, const double* b, double* 
   });
 }
 
+ufe_status ufe_pcg_solve_batched(int32_t n, ufe_system* const* systems, ufe_bddc* const* bddcs, const double* const* b,
+                                 double* const* x, int mem, const ufe_solve_opts* opts, ufe_solve_info* infos) {
+  ufe_status result = UFE_OK;
+  const ufe_status st = guarded([&] {
+    UFE_REQUIRE(n >= 0, UFE_ERR_INVALID_ARG, "negative problem count");
+    if (n == 0) return;
+    UFE_REQUIRE(systems && bddcs && x && opts, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(opts->rtol > 0 && opts->maxit >= 0, UFE_ERR_INVALID_ARG, "bad solve options");
+    check_mem(mem);
+    std::vector<Bddc*> Bs(n);
+    for (int i = 0; i < n; ++i) {
+      UFE_REQUIRE(systems[i] && bddcs[i] && x[i], UFE_ERR_INVALID_ARG, "null problem " + std::to_string(i));
+      UFE_REQUIRE(bddcs[i]->sys == systems[i], UFE_ERR_INVALID_ARG,
+                  "preconditioner " + std::to_string(i) + " belongs to another system");
+      for (int j = 0; j < i; ++j)
+        UFE_REQUIRE(bddcs[j] != bddcs[i], UFE_ERR_INVALID_ARG, "a preconditioner appears twice in the batch");
+      Bs[i] = bddcs[i];
+    }
+    std::vector<DBuf<double>> bb(n), xb(n);
+    std::vector<const double*> bd(n);
+    std::vector<double*> xd(n);
+    for (int i = 0; i < n; ++i) {
+      cudaStream_t s = systems[i]->stream;
+      const int64_t len = systems[i]->n_vec();
+      bd[i] = (b && b[i]) ? stage(bb[i], b[i], len, mem, s) : systems[i]->b.p;
+      xd[i] = x[i];
+      if (mem == UFE_MEM_HOST) {
+        xb[i].alloc(len, s);
+        copy_in(xb[i].p, x[i], len * 8, mem, s);
+        xd[i] = xb[i].p;
+      }
+    }
+    result = pcg_solve_batched(n, Bs.data(), bd.data(), xd.data(), *opts, infos);
+    if (mem == UFE_MEM_HOST)
+      for (int i = 0; i < n; ++i) copy_out(x[i], xd[i], systems[i]->n_vec() * 8, mem, systems[i]->stream);
+  });
+  if (st != UFE_OK) return st;
+  if (result == UFE_ERR_BREAKDOWN) set_error("PCG breakdown (p.Ap <= 0) in at least one problem of the batch");
+  if (result == UFE_ERR_NO_CONVERGENCE) set_error("at least one problem of the batch did not reach the tolerance");
+  return result;
+}
+
 ufe_status ufe_adjoint(ufe_system* sys, ufe_bddc* B, const double* u, const double* dJdu, double* lambda,
                        double* dJdkappa, int mem, const ufe_solve_opts* opts, ufe_solve_info* info) {
   return guarded([&] {

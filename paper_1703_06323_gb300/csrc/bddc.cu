@@ -27,8 +27,9 @@
 namespace ufe {
 
 Bddc::~Bddc() {
-  if (graph) cudaGraphExecDestroy(graph);
+  if (solve_exec) cudaGraphExecDestroy(solve_exec);
   if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (cap_stream2) cudaStreamDestroy(cap_stream2);
   if (h_sc) cudaFreeHost(h_sc);
 }
 
@@ -1188,6 +1189,8 @@ void bddc_build(Bddc& B) {
   B.part.alloc(B.part_blocks * 2, s);
   B.sc.alloc(1, s);
   B.sc.zero();
+  B.tres.alloc(2, s);
+  B.tres.zero();
   if (!B.h_sc) UFE_CUDA(cudaMallocHost((void**)&B.h_sc, sizeof(PcgScalars)));
 
   UFE_CUDA(cudaEventRecord(e1, s));

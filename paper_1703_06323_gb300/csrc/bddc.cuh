@@ -46,6 +46,7 @@ struct SubMeta {
 };
 
 struct PcgScalars {
+  double rtol;         // relative residual target (set by the host before a solve)
   double pq;           // p . A p
   double rr;           // r . r after the update
   double rz;           // r_k . z_k of the previous iteration
@@ -58,7 +59,7 @@ struct PcgScalars {
   int first;           // first search direction (beta = 0)
   int maxit;
   int flexible;
-  int pad;
+  unsigned passes;     // passes of the device-side loop (bounds it at maxit + 1)
   unsigned int counter[8];   // last-block-done counters per kernel
 };
 
@@ -104,10 +105,13 @@ struct Bddc {
   DBuf<PcgScalars> sc;
   DBuf<int> status;             // DEV_* flags of the per-iteration kernels
   PcgScalars* h_sc = nullptr;   // pinned mirror
-  cudaGraphExec_t graph = nullptr;
-  cudaStream_t cap_stream = nullptr;   // library-owned stream used only for graph capture
-  int graph_iters = 0;
-  long long graph_kernels = 0;         // kernel nodes in the captured chunk
+  // the whole solve as one instantiated graph: initial residual and preconditioner,
+  // a conditional while node whose body is one PCG iteration, the true residual
+  cudaGraphExec_t solve_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;    // library-owned streams used only for graph capture
+  cudaStream_t cap_stream2 = nullptr;
+  long long k_init = 0, k_body = 0, k_final = 0;   // kernel nodes per part of the graph
+  DBuf<double> tres;                    // |b - A x|^2, |b|^2 after the solve
   int64_t part_blocks = 0;
   double setup_ms = 0.0;
   double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
@@ -120,5 +124,7 @@ void bddc_build(Bddc& B);
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev);
 void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);
+ufe_status pcg_solve_batched(int n, Bddc* const* Bs, const double* const* b_dev, double* const* x_dev,
+                             const ufe_solve_opts& o, ufe_solve_info* infos);
 
 }  // namespace ufe

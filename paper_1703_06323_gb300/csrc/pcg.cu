@@ -1,7 +1,11 @@
 // BDDC-preconditioned CG on the device (Sect. 5.1 stopping rule |r| < rtol |b|).
 //
-// One iteration is six kernels, captured in a CUDA graph together with the next
-// iterations of a chunk:
+// A solve is one instantiated CUDA graph: the initial residual and preconditioner,
+// then a conditional while node whose body is one iteration (the body's last kernel
+// decides whether to run again, from the device-side convergence state), then the
+// true residual.  The host launches it once and reads the result once; nothing
+// returns to the host between iterations.  One iteration is six kernels (seven
+// with the coarse prolongation):
 //   K1  p = z + beta p (double-buffered, computed on the fly for the 27-node
 //       neighbourhood) and q = A p, element by element; partial p.q
 //   K2  alpha = r.z / p.q;  x += alpha p;  r -= alpha q;  |r|^2, convergence
@@ -12,9 +16,8 @@
 //   K5  coarse: r_c = sum R_c^T g, u_c = A_c^-1 r_c
 //   K7  per subdomain: u_G = sum_w' w' (v + Phi u_c) (weighting W), z_G = u_G,
 //       z_I = A_II^-1 (r_I - A_IG u_G) (harmonic extension); partial r.z
-// Scalars live on the device; every kernel returns at once after convergence,
-// so the host only reads the state once per chunk.  Reductions are done by the
-// last CTA to finish (fixed summation order, deterministic).
+// Scalars live on the device.  Reductions are done by the last CTA to finish
+// (fixed summation order, deterministic).
 #include <algorithm>
 #include <mutex>
 
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(OpArgs a, const double*
 template <int NC>
 __global__ void __launch_bounds__(kApplyThreads)
 k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
-           double* __restrict__ part, PcgScalars* sc, double rtol, int mode, double* out) {
+           double* __restrict__ part, PcgScalars* sc, int mode, double* out) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double rr = 0.0, bb = 0.0;
   if (d < a.n_dof) {
@@ -238,7 +241,7 @@ k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x,
       if (mode == 0) {
         sc->rr = R;
         sc->bb = B;
-        sc->tol2 = rtol * rtol * B;
+        sc->tol2 = sc->rtol * sc->rtol * B;
         sc->iter = 0;
         sc->first = 1;
         sc->done = (R < sc->tol2 || B == 0.0) ? 1 : 0;
@@ -320,6 +323,16 @@ k_update(int64_t n, double* __restrict__ x, double* __restrict__ r, const double
       }
     }
   }
+}
+
+// the condition of the device-side loop: run another iteration while the solve is
+// running; every pass is counted and the loop stops after maxit + 1 passes whatever
+// the state says, so it always ends
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, PcgScalars* sc) {
+  const unsigned pass = sc->passes;
+  sc->passes = pass + 1;
+  const bool more = sc->done == 0 && sc->iter < sc->maxit && pass < (unsigned)sc->maxit + 1u;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -972,29 +985,54 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   t7.end(s);
 }
 
-template <typename TM, int NC>
-static void set_smem_limits_for(size_t bytes) {
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_interior1<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_neumann<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_final<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  UFE_CUDA(cudaFuncSetAttribute(k_prec_prolong<TM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+// raise a kernel's dynamic shared-memory limit to what the device allows next to its
+// static shared memory
+template <typename K>
+static void raise_smem_limit(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  UFE_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  UFE_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes));
 }
 
+template <typename TM, int NC>
+static void set_smem_limits_for(int optin) {
+  raise_smem_limit(k_prec_interior1<TM, NC>, optin);
+  raise_smem_limit(k_prec_neumann<TM, NC>, optin);
+  raise_smem_limit(k_prec_final<TM, NC>, optin);
+  raise_smem_limit(k_prec_prolong<TM, NC>, optin);
+}
+
+// The per-subdomain kernels take their dynamic shared memory from the problem; the
+// opt-in limit is raised once per device to the largest a CTA may use (the limit
+// does not change what a launch requests, so problems of different sizes can share
+// it); each problem checks that its own request fits (with 16 KB left for the
+// kernels' static shared memory).
+constexpr int kMaxDynSmem = 211 * 1024;
 static void set_smem_limits(Bddc& B) {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
   size_t sd = 0, sf = 0;
   sub_launch(B, 8, &sd);
   sub_launch(B, 4, &sf);
-  UFE_REQUIRE(sd <= 227 * 1024, UFE_ERR_UNSUPPORTED, "local interface / interior sizes exceed one CTA's shared memory");
-  if (B.ncomp == 3) {
-    set_smem_limits_for<double, 3>(sd);
-    set_smem_limits_for<float, 3>(sf);
-  } else {
-    set_smem_limits_for<double, 1>(sd);
-    set_smem_limits_for<float, 1>(sf);
-  }
-  const size_t csm = (size_t)B.ldc * 8;
-  UFE_REQUIRE(csm <= 227 * 1024, UFE_ERR_UNSUPPORTED, "coarse problem larger than one CTA's shared memory");
-  UFE_CUDA(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(csm, 1)));
+  UFE_REQUIRE(std::max(sd, sf) <= (size_t)kMaxDynSmem, UFE_ERR_UNSUPPORTED,
+              "local interface / interior sizes exceed one CTA's shared memory");
+  UFE_REQUIRE((size_t)B.ldc * 8 <= (size_t)kMaxDynSmem, UFE_ERR_UNSUPPORTED,
+              "coarse problem larger than one CTA's shared memory");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  int optin = 0;
+  UFE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  UFE_REQUIRE(optin >= kMaxDynSmem + 16 * 1024, UFE_ERR_UNSUPPORTED, "device offers too little shared memory per block");
+  set_smem_limits_for<double, 1>(optin);
+  set_smem_limits_for<float, 1>(optin);
+  set_smem_limits_for<double, 3>(optin);
+  set_smem_limits_for<float, 3>(optin);
+  raise_smem_limit(k_coarse_solve, optin);
+  done[dev] = true;
 }
 
 // raise the flags the per-iteration kernels left behind (after the stream has synchronised)
@@ -1039,88 +1077,112 @@ static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
   precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
 }
 
-void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info) {
-  const Mesh& m = *B.mesh;
-  cudaStream_t s = B.stream;
+static void launch_residual(Bddc& B, const OpArgs& a, int mode, double* r, double* out, cudaStream_t s) {
+  const unsigned nb = grid_for(a.n_dof, kApplyThreads);
+  if (B.ncomp == 3)
+    k_residual<3><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, r, B.part.p, B.sc.p, mode, out);
+  else
+    k_residual<1><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, r, B.part.p, B.sc.p, mode, out);
+  UFE_CHECK_LAUNCH();
+}
+
+// Records the whole solve of B into one graph (once per preconditioner): initial
+// residual and preconditioner, a conditional while node around one iteration, the
+// true residual.  The graph reads and writes only B's own buffers, so it is reused
+// by every later solve.
+static void build_solve_graph(Bddc& B) {
+  if (B.solve_exec) return;
   const OpArgs a = op_args(*B.sys);
-  const int64_t n = (int64_t)B.ncomp * m.n_dof;   // vector length
-  set_smem_limits(B);
-  cudaEvent_t e0, e1;
-  UFE_CUDA(cudaEventCreate(&e0));
-  UFE_CUDA(cudaEventCreate(&e1));
-  UFE_CUDA(cudaEventRecord(e0, s));
+  // capture on library-owned streams (the caller's may be the legacy default stream,
+  // which cannot be captured); the graph is launched on the caller's stream
+  if (!B.cap_stream) UFE_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+  if (!B.cap_stream2) UFE_CUDA(cudaStreamCreateWithFlags(&B.cap_stream2, cudaStreamNonBlocking));
+  cudaStream_t cs = B.cap_stream;
+  long long captured = 0;
+  bool body_open = false;
+  UFE_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  g_capture_counter = &captured;
+  try {
+    launch_residual(B, a, 0, B.r.p, nullptr, cs);
+    precondition(B, B.r.p, B.z.p, B.sc.p, 1, cs);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    UFE_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphConditionalHandle h;
+    UFE_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
+    k_loop_cond<<<1, 1, 0, cs>>>(h, B.sc.p);
+    UFE_CHECK_LAUNCH();
+    B.k_init = captured;
+    captured = 0;
+    UFE_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    UFE_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, nd, &cp));
+    UFE_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    UFE_CUDA(cudaStreamBeginCaptureToGraph(B.cap_stream2, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    body_open = true;
+    launch_iteration(B, a, B.cap_stream2);
+    k_loop_cond<<<1, 1, 0, B.cap_stream2>>>(h, B.sc.p);
+    UFE_CHECK_LAUNCH();
+    cudaGraph_t body_out = nullptr;
+    body_open = false;
+    UFE_CUDA(cudaStreamEndCapture(B.cap_stream2, &body_out));
+    B.k_body = captured;
+    captured = 0;
+    launch_residual(B, a, 1, nullptr, B.tres.p, cs);
+    B.k_final = captured;
+  } catch (...) {
+    g_capture_counter = nullptr;
+    cudaGraph_t junk = nullptr;
+    if (body_open) cudaStreamEndCapture(B.cap_stream2, &junk);
+    junk = nullptr;
+    cudaStreamEndCapture(cs, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    throw;
+  }
+  g_capture_counter = nullptr;
+  cudaGraph_t gr = nullptr;
+  UFE_CUDA(cudaStreamEndCapture(cs, &gr));
+  const cudaError_t e = cudaGraphInstantiate(&B.solve_exec, gr, 0);
+  cudaGraphDestroy(gr);
+  UFE_CUDA(e);
+}
+
+// stage the inputs and launch the solve graph on stream s
+static void solve_launch(Bddc& B, const double* b_dev, const double* x_dev, const ufe_solve_opts& o, cudaStream_t s) {
+  const int64_t n = (int64_t)B.ncomp * B.mesh->n_dof;
   UFE_CUDA(cudaMemcpyAsync(B.b.p, b_dev, n * 8, cudaMemcpyDeviceToDevice, s));
   UFE_CUDA(cudaMemcpyAsync(B.x.p, x_dev, n * 8, cudaMemcpyDeviceToDevice, s));
   PcgScalars init{};
+  init.rtol = o.rtol;
   init.maxit = std::max(o.maxit, 0);
   init.flexible = o.flexible < 0 ? (B.mixed ? 1 : 0) : (o.flexible ? 1 : 0);
   UFE_CUDA(cudaMemcpyAsync(B.sc.p, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-  const unsigned nb = grid_for(m.n_dof, kApplyThreads);
-  if (B.ncomp == 3)
-    k_residual<3><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
-  else
-    k_residual<1><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, B.r.p, B.part.p, B.sc.p, o.rtol, 0, nullptr);
-  UFE_CHECK_LAUNCH();
-  precondition(B, B.r.p, B.z.p, B.sc.p, 1, s);
+  UFE_CUDA(cudaGraphLaunch(B.solve_exec, s));
+}
 
-  const int chunk = o.check_every > 0 ? o.check_every : 8;
-  if (!B.graph || B.graph_iters != chunk) {
-    if (B.graph) {
-      cudaGraphExecDestroy(B.graph);
-      B.graph = nullptr;
-    }
-    // capture on a library-owned stream (the caller's may be the legacy default
-    // stream, which cannot be captured); the graph is launched on the caller's stream
-    if (!B.cap_stream) UFE_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
-    cudaGraph_t gr;
-    UFE_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
-    long long captured = 0;
-    g_capture_counter = &captured;
-    try {
-      for (int i = 0; i < chunk; ++i) launch_iteration(B, a, B.cap_stream);
-    } catch (...) {
-      g_capture_counter = nullptr;
-      cudaGraph_t junk;
-      cudaStreamEndCapture(B.cap_stream, &junk);
-      if (junk) cudaGraphDestroy(junk);
-      throw;
-    }
-    g_capture_counter = nullptr;
-    B.graph_kernels = captured;
-    UFE_CUDA(cudaStreamEndCapture(B.cap_stream, &gr));
-    UFE_CUDA(cudaGraphInstantiate(&B.graph, gr, 0));
-    cudaGraphDestroy(gr);
-    B.graph_iters = chunk;
-  }
-  // the host reads the device state once per chunk; loop bounded by maxit / chunk
-  const int max_chunks = init.maxit / chunk + 2;
-  for (int c = 0; c < max_chunks; ++c) {
-    UFE_CUDA(cudaMemcpyAsync(B.h_sc, B.sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-    UFE_CUDA(cudaStreamSynchronize(s));
-    if (B.h_sc->done || B.h_sc->iter >= init.maxit) break;
-    UFE_CUDA(cudaGraphLaunch(B.graph, s));
-    g_kernel_launches.fetch_add(B.graph_kernels, std::memory_order_relaxed);
-  }
+// read the state, copy x out (stream s must have the solve queued); returns the status
+static ufe_status solve_finish(Bddc& B, double* x_dev, cudaStream_t s, ufe_solve_info* info, float ms) {
+  const int64_t n = (int64_t)B.ncomp * B.mesh->n_dof;
   UFE_CUDA(cudaMemcpyAsync(B.h_sc, B.sc.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-  UFE_CUDA(cudaEventRecord(e1, s));
+  double tr[2] = {0.0, 0.0};
+  UFE_CUDA(cudaMemcpyAsync(tr, B.tres.p, sizeof(tr), cudaMemcpyDeviceToHost, s));
+  UFE_CUDA(cudaMemcpyAsync(x_dev, B.x.p, n * 8, cudaMemcpyDeviceToDevice, s));
   UFE_CUDA(cudaStreamSynchronize(s));
   const PcgScalars fin = *B.h_sc;
-  if (fin.bb == 0.0) UFE_CUDA(cudaMemsetAsync(B.x.p, 0, n * 8, s));
-  UFE_CUDA(cudaMemcpyAsync(x_dev, B.x.p, n * 8, cudaMemcpyDeviceToDevice, s));
-  float ms = 0.f;
-  UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  // true residual |b - A x| / |b|
-  DBuf<double> out;
-  out.alloc(2, s);
-  if (B.ncomp == 3)
-    k_residual<3><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, nullptr, B.part.p, B.sc.p, 0.0, 1, out.p);
-  else
-    k_residual<1><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, nullptr, B.part.p, B.sc.p, 0.0, 1, out.p);
-  UFE_CHECK_LAUNCH();
-  std::vector<double> tr = to_host(out.p, 2, s);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  check_device_status(B);
+  if (fin.bb == 0.0) {
+    UFE_CUDA(cudaMemsetAsync(x_dev, 0, n * 8, s));
+    UFE_CUDA(cudaStreamSynchronize(s));
+  }
+  const long long body_runs = fin.passes > 0 ? (long long)fin.passes - 1 : 0;
+  g_kernel_launches.fetch_add(B.k_init + body_runs * B.k_body + B.k_final, std::memory_order_relaxed);
   if (info) {
     info->iterations = fin.iter;
     info->converged = fin.done == 1;
@@ -1128,8 +1190,82 @@ void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts
     info->true_rel_residual = tr[1] > 0 ? std::sqrt(tr[0] / tr[1]) : 0.0;
     info->solve_ms = ms;
   }
-  if (fin.done == 3) throw Error{UFE_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0"};
-  if (fin.done != 1) throw Error{UFE_ERR_NO_CONVERGENCE, "PCG did not reach the tolerance within maxit"};
+  if (fin.done == 3) return UFE_ERR_BREAKDOWN;
+  if (fin.done != 1) return UFE_ERR_NO_CONVERGENCE;
+  return UFE_OK;
+}
+
+void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info) {
+  cudaStream_t s = B.stream;
+  set_smem_limits(B);
+  build_solve_graph(B);
+  cudaEvent_t e0, e1;
+  UFE_CUDA(cudaEventCreate(&e0));
+  UFE_CUDA(cudaEventCreate(&e1));
+  UFE_CUDA(cudaEventRecord(e0, s));
+  solve_launch(B, b_dev, x_dev, o, s);
+  UFE_CUDA(cudaEventRecord(e1, s));
+  UFE_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const ufe_status st = solve_finish(B, x_dev, s, info, ms);
+  check_device_status(B);
+  if (st == UFE_ERR_BREAKDOWN) throw Error{UFE_ERR_BREAKDOWN, "PCG breakdown: p.Ap <= 0"};
+  if (st == UFE_ERR_NO_CONVERGENCE) throw Error{UFE_ERR_NO_CONVERGENCE, "PCG did not reach the tolerance within maxit"};
+}
+
+// Many independent solves at once: every problem's solve graph is launched on one of
+// a few library-owned streams, so the GPU runs the problems side by side; each
+// stream first waits for its problems' own streams.  Returns the first non-OK status
+// (all problems are solved and reported regardless).
+constexpr int kBatchStreams = 16;
+ufe_status pcg_solve_batched(int n, Bddc* const* Bs, const double* const* b_dev, double* const* x_dev,
+                             const ufe_solve_opts& o, ufe_solve_info* infos) {
+  static std::mutex mu;
+  static cudaStream_t pool[128][kBatchStreams] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int k = 0; k < kBatchStreams; ++k)
+      if (!pool[dev][k]) UFE_CUDA(cudaStreamCreateWithFlags(&pool[dev][k], cudaStreamNonBlocking));
+  }
+  for (int i = 0; i < n; ++i) {
+    set_smem_limits(*Bs[i]);
+    build_solve_graph(*Bs[i]);
+  }
+  std::vector<cudaEvent_t> ev(2 * (size_t)n, nullptr);
+  struct Cleanup {
+    std::vector<cudaEvent_t>& ev;
+    ~Cleanup() {
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } cleanup{ev};
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t si = pool[dev][i % kBatchStreams];
+    cudaEvent_t ready;
+    UFE_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    ev[2 * i] = ready;
+    UFE_CUDA(cudaEventRecord(ready, Bs[i]->stream));
+    UFE_CUDA(cudaStreamWaitEvent(si, ready, 0));
+    solve_launch(*Bs[i], b_dev[i], x_dev[i], o, si);
+    cudaEvent_t done;
+    UFE_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    ev[2 * i + 1] = done;
+    UFE_CUDA(cudaEventRecord(done, si));
+    UFE_CUDA(cudaStreamWaitEvent(Bs[i]->stream, done, 0));   // later work on the problem's stream follows
+  }
+  ufe_status first = UFE_OK;
+  for (int i = 0; i < n; ++i) {
+    const ufe_status st = solve_finish(*Bs[i], x_dev[i], pool[dev][i % kBatchStreams], infos ? infos + i : nullptr, 0.f);
+    check_device_status(*Bs[i]);
+    if (first == UFE_OK && st != UFE_OK) first = st;
+  }
+  return first;
 }
 
 // ---------------------------------------------------------------------------

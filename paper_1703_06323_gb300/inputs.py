@@ -280,7 +280,7 @@ def batched_spheres(count=256, seed=0, sizes=(24, 32, 48, 64), sub=8):
     for i in range(count):
         n = int(sizes[rng.integers(len(sizes))])
         r = float(rng.uniform(0.25, 0.45))
-        delta = 0.5 - r - 2.0 / n
+        delta = max(0.5 - r - 2.0 / n, 0.0)    # the sphere stays 2h inside the box where it can
         c = 0.5 + rng.uniform(-delta, delta, 3)
         p = sphere_problem(cells=(n, n, n), sub_cells=(sub, sub, sub), centre=c, radius=r,
                            dirichlet_face_mask=0, pin_node=PIN_AUTO, name=f"batch{i}_n{n}")

@@ -101,6 +101,8 @@ def _load():
         "ufe_bddc_destroy": (None, [P]),
         "ufe_pcg_solve": (ctypes.c_int, [P, P, P, P, ctypes.c_int, ctypes.POINTER(SolveOpts),
                                          ctypes.POINTER(SolveInfo)]),
+        "ufe_pcg_solve_batched": (ctypes.c_int, [ctypes.c_int32, P, P, P, P, ctypes.c_int,
+                                                 ctypes.POINTER(SolveOpts), P]),
         "ufe_adjoint": (ctypes.c_int, [P, P, P, P, P, P, ctypes.c_int, ctypes.POINTER(SolveOpts),
                                        ctypes.POINTER(SolveInfo)]),
     }
@@ -118,7 +120,7 @@ EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_
             "ufe_assemble", "ufe_assemble_elastic", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
             "ufe_bddc_apply_noalloc",
-            "ufe_bddc_destroy", "ufe_pcg_solve", "ufe_adjoint")
+            "ufe_bddc_destroy", "ufe_pcg_solve", "ufe_pcg_solve_batched", "ufe_adjoint")
 
 
 def _check(status):
@@ -350,6 +352,31 @@ def ufe_pcg_solve(system, bddc, b, x, rtol=1e-8, maxit=1000, flexible=-1, check_
     if raise_on_error:
         _check(st)
     return st, {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+
+
+def ufe_pcg_solve_batched(systems, bddcs, bs, xs, rtol=1e-8, maxit=1000, flexible=-1, raise_on_error=True):
+    """Solve every (system, bddc) pair at once into xs[i] (numpy or torch CUDA float64;
+    bs None or a list with None for the assembled right-hand side); returns (status, infos)."""
+    n = len(systems)
+    if not (len(bddcs) == n and len(xs) == n and (bs is None or len(bs) == n)):
+        raise ValueError("systems, bddcs, xs (and bs) must have the same length")
+    xp = [_ptr(x, np.float64) for x in xs]
+    bp = [_ptr(b, np.float64) for b in bs] if bs is not None else [(None, None, None)] * n
+    mem = _mem_of(*xp, *bp)
+    Parr = ctypes.c_void_p * max(n, 1)
+    sys_a = Parr(*[ctypes.cast(h, ctypes.c_void_p) for h in systems])
+    bd_a = Parr(*[ctypes.cast(h, ctypes.c_void_p) for h in bddcs])
+    b_a = Parr(*[p[0] for p in bp])
+    x_a = Parr(*[p[0] for p in xp])
+    infos = (SolveInfo * max(n, 1))()
+    opts = SolveOpts(float(rtol), int(maxit), int(flexible), 0, 0)
+    st = LIB.ufe_pcg_solve_batched(n, sys_a, bd_a, b_a, x_a, mem, ctypes.byref(opts), infos)
+    for x, p in zip(xs, xp):
+        if p[1] == MEM_HOST and not _is_torch(x) and p[2] is not x:
+            x[:] = p[2]
+    if raise_on_error:
+        _check(st)
+    return st, [{k: getattr(infos[i], k) for k, _ in SolveInfo._fields_} for i in range(n)]
 
 
 def ufe_adjoint(system, bddc, u, dJdu, lam, dJdkappa, rtol=1e-8, maxit=1000, flexible=-1, check_every=8):
