@@ -47,7 +47,7 @@ TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": None, "gj_update_f32": None}
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
@@ -192,6 +192,69 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def per_iteration_roofline(U, p, phi_d, f_d, stream, flush, reps=20):
+    """HBM roofline of the per-iteration kernels (mixed precision): CUDA-event timing of
+    each kernel over `reps` preconditioner + operator applications, L2 flushed before
+    each application; algorithmic bytes = the operator storage each kernel must read
+    (BDDC info) plus 8 bytes per local vector entry it gathers or writes."""
+    import torch
+    peak, src = hbm_peak_gbs()
+    mesh = U.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, phi_d, p.dirichlet_face_mask, p.pin_node,
+                             stream=stream.cuda_stream)
+    sysh = bddc = None
+    try:
+        minfo = U.ufe_mesh_get_info(mesh)
+        n = minfo["n_dof"]
+        sysh = U.ufe_assemble(mesh, None, f_d, None, None)
+        bddc = U.ufe_bddc_setup(sysh, U.WEIGHT_STIFFNESS, U.OBJECTS_VARIANT1, U.COARSE_CEF, U.PREC_MIXED)
+        bi = U.ufe_bddc_get_info(bddc)
+        g = torch.Generator(device="cpu").manual_seed(1)
+        r = torch.randn(n, dtype=torch.float64, generator=g).to(phi_d.device)
+        for _ in range(3):
+            U.ufe_bddc_apply(bddc, r)
+            U.ufe_system_apply(sysh, r)
+        U.ufe_timing_reset()
+        U.ufe_timing_enable(True)
+        for _ in range(reps):
+            flush.fill_(1.0)
+            U.ufe_bddc_apply(bddc, r)
+            U.ufe_system_apply(sysh, r)
+        U.ufe_timing_enable(False)
+        ni, ng, nc = bi["interior_slots"], bi["interface_slots"], bi["n_coarse"]
+        gi, ig = 12 * 27 * ng, 12 * 27 * ni
+        bytes_ = {
+            "prec_interior": bi["bytes_interior_inverse"] + gi + 8 * ni + 8 * ng,
+            "prec_neumann": bi["bytes_neumann"] + bi["bytes_coarse_basis"] + 24 * ng,
+            "coarse_solve": bi["bytes_coarse_inverse"] + 16 * nc,
+            "prec_prolong": bi["bytes_coarse_basis"] + 16 * ng,
+            "prec_final": bi["bytes_interior_inverse"] + ig + 16 * ng + 16 * ni,
+            "apply": 16 * n + 4 * minfo["n_nodes"] + minfo["n_cells"] + 512 * minfo["n_cut_cells"],
+        }
+        out = {"peak_gbs": peak, "peak_source": src, "l2": "flushed before each application", "reps": reps}
+        for k, b in bytes_.items():
+            ms, cnt = U.ufe_timing_get(k)
+            us = 1e3 * ms / max(cnt, 1)
+            gbs = b / (us * 1e-6) / 1e9 if us > 0 else None
+            out[k] = {"us": us, "bytes": int(b), "gbs": gbs, "frac": gbs / peak if gbs else None}
+        U.ufe_timing_reset()
+        return out
+    finally:
+        if bddc is not None:
+            U.ufe_bddc_destroy(bddc)
+        if sysh is not None:
+            U.ufe_system_destroy(sysh)
+        U.ufe_mesh_destroy(mesh)
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -292,6 +355,8 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
 
+    per_iter = per_iteration_roofline(U, p, phi_d, f_d, stream, flush) if rank == 0 else None
+
     mean_mixed = statistics.mean(t_mixed)
     mean_fp64 = statistics.mean(t_fp64)
     if world > 1:
@@ -357,6 +422,7 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "phase_ms": phases,
         "roofline": roofline,
+        "per_iteration_roofline": per_iter,
         "clocks": clk_stats,
         "e2e": {"value": e2e_mean / world, "unit": "s",
                 "h2d_bytes_per_step": int(p.phi.nbytes + p.f.nbytes + 8 * n),

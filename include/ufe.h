@@ -237,6 +237,11 @@ typedef struct {
   double setup_ms;                /* device time of ufe_bddc_setup */
   double inverse_flops_local;     /* sum of n^3 over the inverted local matrices (A_II, S', S_c) */
   double inverse_flops_coarse;    /* n_coarse^3 (symmetric Gauss-Jordan, algorithmic count) */
+  /* storage read by the per-iteration kernels (bytes): A_II^-1, the constrained
+   * Neumann operator K, the coarse basis Phi (FP32 in mixed precision), the A_GI and
+   * A_IG stencils (index + value per slot), the FP64 coarse inverse */
+  double bytes_interior_inverse, bytes_neumann, bytes_coarse_basis, bytes_offdiag, bytes_coarse_inverse;
+  int64_t interior_slots, interface_slots;   /* sum over subdomains of local interior / interface DOFs */
 } ufe_bddc_info;
 
 /*

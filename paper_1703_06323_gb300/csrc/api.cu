@@ -403,6 +403,13 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->setup_ms = B->setup_ms;
     info->inverse_flops_local = B->inv_flops_local;
     info->inverse_flops_coarse = B->inv_flops_coarse;
+    info->bytes_interior_inverse = B->bytes_II;
+    info->bytes_neumann = B->bytes_GG;
+    info->bytes_coarse_basis = B->bytes_GC;
+    info->bytes_offdiag = B->bytes_off;
+    info->bytes_coarse_inverse = B->bytes_Ac;
+    info->interior_slots = B->n_vIloc;
+    info->interface_slots = B->n_vGloc;
   });
 }
 

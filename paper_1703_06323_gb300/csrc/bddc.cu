@@ -1097,6 +1097,14 @@ void bddc_build(Bddc& B) {
   upload(B.off_II, oII);
   upload(B.off_GG, oGG);
   upload(B.off_GC, oGC);
+  {
+    const double tm = B.mixed ? 4.0 : 8.0;
+    B.bytes_II = tm * nII;
+    B.bytes_GG = tm * nGG;
+    B.bytes_GC = tm * nGC;
+    B.bytes_off = 12.0 * 27 * NC * (double)(B.n_vGloc + B.n_vIloc);
+    B.bytes_Ac = 8.0 * (double)nco * pad4((int)std::max<int64_t>(nco, 1));
+  }
 
   // ---- local matrices, scales, weights
   DBuf<double> AII, AIG, AGG, sI, sG, dGraw;

@@ -115,6 +115,7 @@ struct Bddc {
   int64_t part_blocks = 0;
   double setup_ms = 0.0;
   double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
+  double bytes_II = 0.0, bytes_GG = 0.0, bytes_GC = 0.0, bytes_off = 0.0, bytes_Ac = 0.0;
 
   SubMeta meta() const;
   ~Bddc();

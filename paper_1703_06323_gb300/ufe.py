@@ -51,7 +51,10 @@ class BddcInfo(ctypes.Structure):
     _fields_ = [("n_objects", ctypes.c_int64), ("n_corners", ctypes.c_int64), ("n_edges", ctypes.c_int64),
                 ("n_faces", ctypes.c_int64), ("n_coarse", ctypes.c_int64), ("max_local_coarse", ctypes.c_int32),
                 ("setup_ms", ctypes.c_double), ("inverse_flops_local", ctypes.c_double),
-                ("inverse_flops_coarse", ctypes.c_double)]
+                ("inverse_flops_coarse", ctypes.c_double), ("bytes_interior_inverse", ctypes.c_double),
+                ("bytes_neumann", ctypes.c_double), ("bytes_coarse_basis", ctypes.c_double),
+                ("bytes_offdiag", ctypes.c_double), ("bytes_coarse_inverse", ctypes.c_double),
+                ("interior_slots", ctypes.c_int64), ("interface_slots", ctypes.c_int64)]
 
 
 class SolveOpts(ctypes.Structure):
