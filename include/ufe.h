@@ -242,6 +242,8 @@ typedef struct {
    * A_IG stencils (index + value per slot), the FP64 coarse inverse */
   double bytes_interior_inverse, bytes_neumann, bytes_coarse_basis, bytes_offdiag, bytes_coarse_inverse;
   int64_t interior_slots, interface_slots;   /* sum over subdomains of local interior / interface DOFs */
+  int32_t fp64_refactor;   /* mixed precision only: 1 when a scaled local matrix lost positivity in FP32
+                              and the local operators were factored in FP64 (then stored in FP32) */
 } ufe_bddc_info;
 
 /*

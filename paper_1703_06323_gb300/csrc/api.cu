@@ -410,6 +410,7 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->bytes_coarse_inverse = B->bytes_Ac;
     info->interior_slots = B->n_vIloc;
     info->interface_slots = B->n_vGloc;
+    info->fp64_refactor = B->fp64_refactor;
   });
 }
 

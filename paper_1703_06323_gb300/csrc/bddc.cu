@@ -741,6 +741,11 @@ __global__ void k_symmetrize(double* A, int n, int ld) {
   A[(int64_t)j * ld + i] = v;
 }
 
+__global__ void k_to_float(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
 __global__ void k_scale_ptr(int64_t n, int nc, const int32_t* __restrict__ in, int32_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = nc * in[i];
@@ -1151,10 +1156,26 @@ void bddc_build(Bddc& B) {
   ph_fac.begin("phase_factor", s);
   // ---- factorisations and explicit local operators
   DBuf<double> Acw, rho;
-  if (B.mixed)
-    factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,
-                           ell_v, B.fII, B.fGG, B.fGC, Acw, rho);
-  else
+  if (B.mixed) {
+    try {
+      factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
+                             ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho);
+    } catch (const Error& e) {
+      if (e.code != UFE_ERR_SINGULAR_LOCAL) throw;
+      // a scaled local matrix lost positivity in FP32 (tiny cut fractions make it too
+      // ill-conditioned): factor this problem in FP64 and keep the operators the
+      // iterations read in FP32
+      DBuf<double> tII, tGG, tGC;
+      factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
+                              ell_k, ell_v, tII, tGG, tGC, Acw, rho);
+      for (auto pr : {std::make_pair(&tII, &B.fII), std::make_pair(&tGG, &B.fGG), std::make_pair(&tGC, &B.fGC)}) {
+        pr.second->alloc(pr.first->n, s);
+        k_to_float<<<grid_for((int64_t)pr.first->n, T), T, 0, s>>>((int64_t)pr.first->n, pr.first->p, pr.second->p);
+        UFE_CHECK_LAUNCH();
+      }
+      B.fp64_refactor = 1;
+    }
+  } else
     factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,
                             ell_v, B.dII, B.dGG, B.dGC, Acw, rho);
   AII.release();

@@ -54,7 +54,8 @@ class BddcInfo(ctypes.Structure):
                 ("inverse_flops_coarse", ctypes.c_double), ("bytes_interior_inverse", ctypes.c_double),
                 ("bytes_neumann", ctypes.c_double), ("bytes_coarse_basis", ctypes.c_double),
                 ("bytes_offdiag", ctypes.c_double), ("bytes_coarse_inverse", ctypes.c_double),
-                ("interior_slots", ctypes.c_int64), ("interface_slots", ctypes.c_int64)]
+                ("interior_slots", ctypes.c_int64), ("interface_slots", ctypes.c_int64),
+                ("fp64_refactor", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
