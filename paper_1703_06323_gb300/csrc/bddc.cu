@@ -68,6 +68,8 @@ SubMeta Bddc::meta() const {
   s.ig_k = ig_k.p;
   s.ig_v = ig_v.p;
   s.status = status.p;
+  s.sI = sI.p;
+  s.sG = sG.p;
   return s;
 }
 
@@ -694,25 +696,6 @@ __global__ void k_coarse_local(const int32_t* __restrict__ C_ptr, const int64_t*
   }
 }
 
-// unscale: A[i][j] *= sr_i * sc_j (sc may be null: rows only); grid (row chunks, subdomain)
-template <typename T>
-__global__ void k_unscale(T* __restrict__ A, const int64_t* __restrict__ off, const int32_t* __restrict__ rptr,
-                          const int32_t* __restrict__ cptr, const double* __restrict__ sr, const double* __restrict__ scl,
-                          int unused) {
-  const int w = blockIdx.y;
-  const int nr = rptr[w + 1] - rptr[w];
-  const int nc = cptr[w + 1] - cptr[w];
-  const int ld = pad4(nc);
-  for (int i = blockIdx.x; i < nr; i += gridDim.x) {
-    const double ri = sr[rptr[w] + i];
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-      T* a = A + off[w] + (int64_t)i * ld + j;
-      *a = (T)((double)*a * ri * (scl ? scl[cptr[w] + j] : 1.0));
-    }
-  }
-  (void)unused;
-}
-
 // coarse matrix: row l gathers A_c^w of every subdomain w in neigh(l), in neigh order
 __global__ void k_coarse_assemble(int64_t n_coarse, int ldc, const int32_t* __restrict__ coarse_rep,
                                   const uint8_t* __restrict__ coarse_nn, const int32_t* __restrict__ neigh,
@@ -897,13 +880,10 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   Acw.alloc(std::max<int64_t>(nCC, 1), s);
   k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
   UFE_CHECK_LAUNCH();
-  // 11. unscale the operators used at every iteration
-  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(II.p, dII->p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p, 0);
-  UFE_CHECK_LAUNCH();
-  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GG.p, dGG->p, B.vG_ptr.p, B.vG_ptr.p, sG.p, sG.p, 0);
-  UFE_CHECK_LAUNCH();
-  k_unscale<T><<<dim3(64, ns), 128, 0, s>>>(GC.p, B.off_GC.p, B.vG_ptr.p, B.C_ptr.p, sG.p, nullptr, 0);
-  UFE_CHECK_LAUNCH();
+  // 11. the operators stay in the scaled variables: the iterations apply
+  //     A_II^-1 = S_I Ahat_II^-1 S_I, K = S_G Khat S_G and Phi = S_G Phihat with the FP64
+  //     scale vectors, so the stored entries are O(1) whatever the cut fractions (the
+  //     unscaled entries of a DOF with a 1e-40 diagonal would overflow FP32)
 }
 
 void bddc_build(Bddc& B) {
@@ -1112,7 +1092,9 @@ void bddc_build(Bddc& B) {
   }
 
   // ---- local matrices, scales, weights
-  DBuf<double> AII, AIG, AGG, sI, sG, dGraw;
+  DBuf<double> AII, AIG, AGG, dGraw;
+  DBuf<double>& sI = B.sI;
+  DBuf<double>& sG = B.sG;
   AII.alloc(std::max<int64_t>(nII, 1), s);
   AGG.alloc(std::max<int64_t>(nGG, 1), s);
   AII.zero();

@@ -43,6 +43,8 @@ struct SubMeta {
   const int32_t* ig_k;      // A_IG in ELL form
   const double* ig_v;
   int* status;              // DEV_* flags raised by bounded device waits
+  const double* sI;         // scale of each local interior / interface vector slot: the stored
+  const double* sG;         // operators are those of the scaled problem (D^-1/2 A D^-1/2)
 };
 
 struct PcgScalars {
@@ -93,6 +95,7 @@ struct Bddc {
   DBuf<double> dII, dGG, dGC;   // FP64 operators
   DBuf<float> fII, fGG, fGC;    // FP32 operators (mixed)
   DBuf<double> w;               // n_Gloc weights
+  DBuf<double> sI, sG;          // Jacobi scales of the local slots (operators stored scaled)
   DBuf<int32_t> gi_k, ig_k;     // A_GI / A_IG in ELL form (local indices)
   DBuf<double> gi_v, ig_v;
   DBuf<double> Ac_inv;          // n_coarse x ldc, FP64

@@ -621,12 +621,17 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   RowStream<TM> rs;
   rs.begin(AIIinv + sm.off_II[w], r0, r1, z.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
-  for (int p = threadIdx.x; p < z.ldI; p += blockDim.x) xI[p] = p < z.nI ? (TM)r[vdof_I<NC>(sm, w, p)] : TM(0);
+  const int i0 = sm.vI_ptr[w];
+  for (int p = threadIdx.x; p < z.ldI; p += blockDim.x)
+    xI[p] = p < z.nI ? (TM)(sm.sI[i0 + p] * r[vdof_I<NC>(sm, w, p)]) : TM(0);
   __syncthreads();
   rs.gemv(xI, S.dI + r0, sm.status);
   cl.sync();
   cluster_gather(cl, S.dI, z.nI);
   cl.sync();
+  // y_I = S_I (Ahat_II^-1 (S_I r_I)), on every CTA's full copy
+  for (int p = threadIdx.x; p < z.nI; p += blockDim.x) S.dI[p] *= sm.sI[i0 + p];
+  __syncthreads();
   int j0, j1;
   row_slice(z.nG, rank, j0, j1);
   constexpr int KS = 27 * NC;
@@ -672,7 +677,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
       double s = r[(int64_t)NC * xi + c];
       const int cnt = sm.n_neigh[xi];
       for (int k = 0; k < cnt; ++k) s -= tG[(int64_t)NC * sm.gpos[(int64_t)xi * 8 + k] + c];
-      v = (TM)(sm.w[g0 + j] * s);
+      v = (TM)(sm.sG[g0 + j] * sm.w[g0 + j] * s);
     }
     xG[j] = v;
   }
@@ -699,7 +704,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
     __syncthreads();
   }
   rs.gemv(xG, S.dG + r0, sm.status);
-  for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) vw[g0 + j] = sm.w[g0 + j] * S.dG[j];
+  for (int j = r0 + threadIdx.x; j < r1; j += blockDim.x) vw[g0 + j] = sm.w[g0 + j] * sm.sG[g0 + j] * S.dG[j];
   cl.sync();
   if (rank == 0) {
     for (int c = threadIdx.x; c < z.nC; c += blockDim.x) {
@@ -772,7 +777,7 @@ k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict_
     cta_gemv_rows<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
   __syncthreads();
   const int g0 = sm.vG_ptr[w];
-  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vw[g0 + j] += sm.w[g0 + j] * S.dG[j];
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) vw[g0 + j] += sm.w[g0 + j] * sm.sG[g0 + j] * S.dG[j];
 }
 
 // K7: u_G = sum_w' w' (v + Phi u_c) (the weighted local values, W); z_G = u_G (the
@@ -828,7 +833,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
       const int32_t k = sm.ig_k[e0 + (int64_t)o * zz.nI + p];
       if (k >= 0) t += sm.ig_v[e0 + (int64_t)o * zz.nI + p] * S.dG[k];
     }
-    xI[p] = (TM)(r[vdof_I<NC>(sm, w, p)] - t);
+    xI[p] = (TM)(sm.sI[sm.vI_ptr[w] + p] * (r[vdof_I<NC>(sm, w, p)] - t));
   }
   for (int p = zz.nI + threadIdx.x; p < zz.ldI; p += blockDim.x) xI[p] = TM(0);
   cl.sync();
@@ -837,7 +842,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   rs.gemv(xI, S.dI + p0, sm.status);
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const int64_t d = vdof_I<NC>(sm, w, p);
-    const double zn = S.dI[p];
+    const double zn = sm.sI[sm.vI_ptr[w] + p] * S.dI[p];
     if (with_dots) {
       rz += r[d] * zn;
       rzo += r[d] * z[d];
