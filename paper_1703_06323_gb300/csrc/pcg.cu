@@ -1165,11 +1165,13 @@ static void solve_launch(Bddc& B, const double* b_dev, const double* x_dev, cons
   const int64_t n = (int64_t)B.ncomp * B.mesh->n_dof;
   UFE_CUDA(cudaMemcpyAsync(B.b.p, b_dev, n * 8, cudaMemcpyDeviceToDevice, s));
   UFE_CUDA(cudaMemcpyAsync(B.x.p, x_dev, n * 8, cudaMemcpyDeviceToDevice, s));
+  // initial scalars through the pinned mirror, so the copy does not synchronise the host
   PcgScalars init{};
   init.rtol = o.rtol;
   init.maxit = std::max(o.maxit, 0);
   init.flexible = o.flexible < 0 ? (B.mixed ? 1 : 0) : (o.flexible ? 1 : 0);
-  UFE_CUDA(cudaMemcpyAsync(B.sc.p, &init, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+  *B.h_sc = init;
+  UFE_CUDA(cudaMemcpyAsync(B.sc.p, B.h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
   UFE_CUDA(cudaGraphLaunch(B.solve_exec, s));
 }
 
@@ -1262,8 +1264,11 @@ ufe_status pcg_solve_batched(int n, Bddc* const* Bs, const double* const* b_dev,
     UFE_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     ev[2 * i + 1] = done;
     UFE_CUDA(cudaEventRecord(done, si));
-    UFE_CUDA(cudaStreamWaitEvent(Bs[i]->stream, done, 0));   // later work on the problem's stream follows
   }
+  // later work on each problem's stream follows its solve; added only after every
+  // launch, since problems often share one stream and an earlier wait there would
+  // chain the next problem's start to this one's end
+  for (int i = 0; i < n; ++i) UFE_CUDA(cudaStreamWaitEvent(Bs[i]->stream, ev[2 * i + 1], 0));
   ufe_status first = UFE_OK;
   for (int i = 0; i < n; ++i) {
     const ufe_status st = solve_finish(*Bs[i], x_dev[i], pool[dev][i % kBatchStreams], infos ? infos + i : nullptr, 0.f);
