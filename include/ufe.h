@@ -242,8 +242,9 @@ typedef struct {
    * A_IG stencils (index + value per slot), the FP64 coarse inverse */
   double bytes_interior_inverse, bytes_neumann, bytes_coarse_basis, bytes_offdiag, bytes_coarse_inverse;
   int64_t interior_slots, interface_slots;   /* sum over subdomains of local interior / interface DOFs */
-  int32_t fp64_refactor;   /* mixed precision only: 1 when a scaled local matrix lost positivity in FP32
-                              and the local operators were factored in FP64 (then stored in FP32) */
+  int32_t fp64_refactor;   /* mixed precision requested: 1 when a Jacobi-scaled local matrix had an FP32
+                              pivot below 1e-3 (or not positive), so this problem keeps FP64 local
+                              operators (factored and applied in FP64, classical PCG) */
 } ufe_bddc_info;
 
 /*

@@ -724,11 +724,6 @@ __global__ void k_symmetrize(double* A, int n, int ld) {
   A[(int64_t)j * ld + i] = v;
 }
 
-__global__ void k_to_float(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (float)in[i];
-}
-
 __global__ void k_scale_ptr(int64_t n, int nc, const int32_t* __restrict__ in, int32_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = nc * in[i];
@@ -806,18 +801,22 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   DBuf<int> status;
   status.alloc(ns, s);
   status.zero();
-  // a non-positive pivot in one of the local inversions: name the matrix and subdomain
+  // a non-positive pivot in one of the local inversions (in FP32 also a pivot of a
+  // Jacobi-scaled matrix below 1e-3: the operators of such a subdomain are too
+  // ill-conditioned to be stored and applied in FP32): name the matrix and subdomain
   auto check = [&](const char* what) {
     std::vector<int> st = to_host(status.p, ns, s);
     for (int w = 0; w < ns; ++w)
       UFE_REQUIRE(st[w] == 0, UFE_ERR_SINGULAR_LOCAL,
-                  std::string(what) + " of subdomain " + std::to_string(w) + " is not positive definite");
+                  std::string(what) + " of subdomain " + std::to_string(w) +
+                      ((st[w] & DEV_SINGULAR) ? " is not positive definite" : " is too ill-conditioned"));
   };
+  const T floor = sizeof(T) == 4 ? T(1e-3) : T(0);
   std::vector<InvDesc> inv;
   std::vector<GemmDesc> g;
   // 1. A_II^-1
   for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
-  batched_inverse<T>(inv, II.p, status.p, s);
+  batched_inverse<T>(inv, II.p, status.p, s, floor);
   check("A_II");
   // 2. X^T = (A_II^-1 A_IG)^T and 3. S = A_GG - A_GI X, both from the sparse A_GI
   X.alloc(std::max<int64_t>(nIG, 1), s);
@@ -846,7 +845,7 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   // 5. S'^-1
   inv.clear();
   for (int w = 0; w < ns; ++w) inv.push_back({B.h_nG[w], pad4(B.h_nG[w]), oGG[w]});
-  batched_inverse<T>(inv, GG.p, status.p, s);
+  batched_inverse<T>(inv, GG.p, status.p, s, floor);
   check("S' = S + C^T rho C");
   // 6. Y = S'^-1 C^T
   Y.alloc(std::max<int64_t>(nGC, 1), s);
@@ -1144,18 +1143,18 @@ void bddc_build(Bddc& B) {
                              ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho);
     } catch (const Error& e) {
       if (e.code != UFE_ERR_SINGULAR_LOCAL) throw;
-      // a scaled local matrix lost positivity in FP32 (tiny cut fractions make it too
-      // ill-conditioned): factor this problem in FP64 and keep the operators the
-      // iterations read in FP32
-      DBuf<double> tII, tGG, tGC;
-      factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
-                              ell_k, ell_v, tII, tGG, tGC, Acw, rho);
-      for (auto pr : {std::make_pair(&tII, &B.fII), std::make_pair(&tGG, &B.fGG), std::make_pair(&tGC, &B.fGC)}) {
-        pr.second->alloc(pr.first->n, s);
-        k_to_float<<<grid_for((int64_t)pr.first->n, T), T, 0, s>>>((int64_t)pr.first->n, pr.first->p, pr.second->p);
-        UFE_CHECK_LAUNCH();
-      }
+      // a scaled local matrix is too ill-conditioned for FP32 (tiny cut fractions):
+      // this problem keeps FP64 local operators (factored and applied in FP64)
+      B.fII.release();
+      B.fGG.release();
+      B.fGC.release();
+      B.mixed = false;
       B.fp64_refactor = 1;
+      B.bytes_II *= 2.0;
+      B.bytes_GG *= 2.0;
+      B.bytes_GC *= 2.0;
+      factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
+                              ell_k, ell_v, B.dII, B.dGG, B.dGC, Acw, rho);
     }
   } else
     factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,

@@ -119,7 +119,7 @@ struct Bddc {
   double setup_ms = 0.0;
   double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
   double bytes_II = 0.0, bytes_GG = 0.0, bytes_GC = 0.0, bytes_off = 0.0, bytes_Ac = 0.0;
-  int fp64_refactor = 0;                // mixed precision: local operators factored in FP64 (FP32 failed)
+  int fp64_refactor = 0;                // mixed precision requested, FP64 local operators kept (FP32 too ill-conditioned)
 
   SubMeta meta() const;
   ~Bddc();

@@ -139,9 +139,12 @@ constexpr int kGJThreads = 256;
 // Gauss-Jordan without pivoting.  256 threads as 16 x 16; thread (ty, tx) keeps rows
 // ty + 16a and columns tx + 16b (a, b < NB/16) in registers; pivot row and column go
 // through shared memory, two barriers per pivot, the reciprocal is formed once.
-// Rows / columns >= kb are left alone.
+// Rows / columns >= kb are left alone.  Returns DEV_* flags: DEV_SINGULAR for a
+// non-positive or non-finite pivot, DEV_ILLCOND for a pivot below `floor` (used on
+// Jacobi-scaled matrices, whose pivots are at most 1: a tiny pivot means the
+// inverse has lost most of the working precision).
 template <typename T, int NB>
-__device__ bool gj_block_inverse(T (*D)[NB + 1], int kb) {
+__device__ int gj_block_inverse(T (*D)[NB + 1], int kb, T floor) {
   constexpr int RA = NB / 16;
   __shared__ T rowb[NB], colb[NB];
   __shared__ T s_inv;
@@ -165,7 +168,10 @@ __device__ bool gj_block_inverse(T (*D)[NB + 1], int kb) {
     }
     if (threadIdx.x == (pr << 4) + pr) {
       const T piv = v[pa][pa];
-      if (!(piv > T(0)) || !isfinite((double)piv)) bad = 1;
+      if (!(piv > T(0)) || !isfinite((double)piv))
+        bad |= DEV_SINGULAR;
+      else if (piv < floor)
+        bad |= DEV_ILLCOND;
       s_inv = T(1) / piv;
     }
     __syncthreads();
@@ -192,7 +198,7 @@ __device__ bool gj_block_inverse(T (*D)[NB + 1], int kb) {
 #pragma unroll
     for (int b = 0; b < RA; ++b) D[ty + 16 * a][tx + 16 * b] = v[a][b];
   __syncthreads();
-  return bad == 0;
+  return bad;
 }
 
 // out(NB x NB tile) = sum_l L[i][l] R[l][j], l < kb
@@ -233,7 +239,7 @@ __device__ __forceinline__ int gj_sign(int I, int J, int last_processed) {
 // first diagonal block: D^-1, one CTA per matrix
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_diag(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ Dg, int* status) {
+k_gj_diag(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ Dg, int* status, T floor) {
   const int b = blockIdx.x;
   const InvDesc d = bt.d[b];
   const int k0 = step * NB;
@@ -246,10 +252,10 @@ k_gj_diag(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ Dg, 
     D[r][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : T(r == c ? 1 : 0);
   }
   __syncthreads();
-  const bool ok = gj_block_inverse<T, NB>(D, kb);
+  const int flags = gj_block_inverse<T, NB>(D, kb, floor);
   T* Db = Dg + (int64_t)b * NB * NB;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Db[e] = D[e / NB][e % NB];
-  if (!ok && threadIdx.x == 0) atomicOr(status + b, DEV_SINGULAR);
+  if (flags && threadIdx.x == 0) atomicOr(status + b, flags);
 }
 
 // old row panel R_Kt = A_Kt and Q_Kt = D^-1 A_Kt, 16 columns per CTA
@@ -294,7 +300,7 @@ k_gj_panel(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ R, 
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
 k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R, const T* __restrict__ Q,
-            const T* __restrict__ Dg, T* __restrict__ Dnext, int* status) {
+            const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
   constexpr int RA = NB / 16;
   const int b = blockIdx.y;
   const InvDesc d = bt.d[b];
@@ -379,15 +385,15 @@ k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __res
         L[r][c] = (r < ib && c < jb) ? acc[a][c4] : T(r == c ? 1 : 0);
       }
     __syncthreads();
-    const bool ok = gj_block_inverse<T, NB>(L, ib);
+    const int flags = gj_block_inverse<T, NB>(L, ib, floor);
     T* Dn = Dnext + (int64_t)b * NB * NB;
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Dn[e] = L[e / NB][e % NB];
-    if (!ok && threadIdx.x == 0) atomicOr(status + b, DEV_SINGULAR);
+    if (flags && threadIdx.x == 0) atomicOr(status + b, flags);
   }
 }
 
 template <typename T>
-static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s) {
+static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T floor) {
   constexpr int NB = GJWidth<T>::value;
   if (descs.empty()) return;
   int nmax = 0;
@@ -414,7 +420,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const int nblk = (nmax + NB - 1) / NB;
   const unsigned nb = (unsigned)descs.size();
   const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
-  k_gj_diag<T, NB><<<nb, kGJThreads, 0, s>>>(bt, 0, base, Dbuf[0], status);
+  k_gj_diag<T, NB><<<nb, kGJThreads, 0, s>>>(bt, 0, base, Dbuf[0], status, floor);
   UFE_CHECK_LAUNCH();
   for (int step = 0; step < nblk; ++step) {
     T* Dc = Dbuf[step & 1];
@@ -423,28 +429,28 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
     UFE_CHECK_LAUNCH();
     TimedLaunch tl;
     tl.begin(sizeof(T) == 8 ? "gj_update_f64" : "gj_update_f32", s);
-    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, R.p, Q.p, Dc, Dn, status);
+    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, R.p, Q.p, Dc, Dn, status, floor);
     UFE_CHECK_LAUNCH();
     tl.end(s);
   }
 }
 
 template <typename T>
-void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s) {
-  gj_run<T>(descs, base, status, s);
+void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T pivot_floor) {
+  gj_run<T>(descs, base, status, s, pivot_floor);
 }
 
 template <typename T>
 void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s) {
-  gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s);
+  gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s, T(0));
 }
 
 template void batched_gemm<double>(bool, bool, const std::vector<GemmDesc>&, const double*, const double*, double*,
                                    double, double, cudaStream_t);
 template void batched_gemm<float>(bool, bool, const std::vector<GemmDesc>&, const float*, const float*, float*, float,
                                   float, cudaStream_t);
-template void batched_inverse<double>(const std::vector<InvDesc>&, double*, int*, cudaStream_t);
-template void batched_inverse<float>(const std::vector<InvDesc>&, float*, int*, cudaStream_t);
+template void batched_inverse<double>(const std::vector<InvDesc>&, double*, int*, cudaStream_t, double);
+template void batched_inverse<float>(const std::vector<InvDesc>&, float*, int*, cudaStream_t, float);
 template void large_inverse<double>(double*, int, int, int*, cudaStream_t);
 
 }  // namespace ufe

@@ -24,9 +24,10 @@ template <typename T>
 void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, const T* A, const T* B, T* C,
                   T alpha, T beta, cudaStream_t s);
 
-// in-place inverse of each SPD matrix; status[b] |= DEV_SINGULAR on a non-positive pivot
+// in-place inverse of each SPD matrix; status[b] |= DEV_SINGULAR on a non-positive
+// pivot, |= DEV_ILLCOND on a pivot below pivot_floor (0: no test)
 template <typename T>
-void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s);
+void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T pivot_floor = T(0));
 
 // in-place inverse of one large SPD matrix using the whole GPU
 template <typename T>

@@ -49,6 +49,7 @@ enum DevStatus : int {
   DEV_OK = 0,
   DEV_SINGULAR = 1,
   DEV_TIMEOUT = 2,
+  DEV_ILLCOND = 4,   // a pivot of a Jacobi-scaled matrix fell below the precision's floor
 };
 
 // ---------------------------------------------------------------------------
