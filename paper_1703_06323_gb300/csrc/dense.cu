@@ -201,6 +201,75 @@ __device__ int gj_block_inverse(T (*D)[NB + 1], int kb, T floor) {
   return bad;
 }
 
+struct GJBatch {
+  const InvDesc* d;    // per matrix: n, ld, offset into the matrix base
+  const int64_t* qoff; // per matrix: offset of its row panels R and Q (NB x ld each)
+};
+
+// In-place inverse of the kb x kb leading block of one matrix by a single warp (FP32):
+// lane l keeps rows l + 32 i (i < NB/32) in registers, the pivot row is broadcast
+// column by column with shuffles, so the elimination needs no block-wide barrier
+// (the 256-thread version above spends two barriers per pivot).  Same flags as
+// gj_block_inverse.  The block is read from and written to global memory
+// (row-major, leading dimension ld); rows / columns >= kb are not touched.
+template <int NB>
+__global__ void __launch_bounds__(32)
+k_gj_diag_warp(GJBatch bt, int step, float* __restrict__ base, float* __restrict__ Dg, int* status, float floor) {
+  constexpr int R = NB / 32;
+  const int b = blockIdx.x;
+  const InvDesc d = bt.d[b];
+  const int k0 = step * NB;
+  if (k0 >= d.n) return;
+  const int kb = min(NB, d.n - k0);
+  const int lane = threadIdx.x;
+  const float* A = base + d.off;
+  float v[R][NB];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int r = lane + 32 * i;
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      v[i][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : (r == c ? 1.f : 0.f);
+  }
+  int flags = 0;
+#pragma unroll
+  for (int p = 0; p < NB; ++p) {
+    if (p < kb) {
+      const int o = p % 32, s = p / 32;
+      const float piv = __shfl_sync(0xffffffffu, v[s][p], o);
+      if (!(piv > 0.f) || !isfinite(piv))
+        flags |= DEV_SINGULAR;
+      else if (piv < floor)
+        flags |= DEV_ILLCOND;
+      const float inv = 1.f / piv;
+      float cr[R];
+      bool isp[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        isp[i] = lane + 32 * i == p;
+        cr[i] = v[i][p] * inv;
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        const float rc = __shfl_sync(0xffffffffu, v[s][c], o);
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (c == p)
+            v[i][c] = isp[i] ? inv : -cr[i];
+          else
+            v[i][c] = isp[i] ? v[i][c] * inv : v[i][c] - cr[i] * rc;
+        }
+      }
+    }
+  }
+  float* Db = Dg + (int64_t)b * NB * NB;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Db[(lane + 32 * i) * NB + c] = v[i][c];
+  if (flags) atomicOr(status + b, flags);
+}
+
 // out(NB x NB tile) = sum_l L[i][l] R[l][j], l < kb
 template <typename T, int NB>
 __device__ __forceinline__ void tile_mma(const T (*L)[NB + 1], const T (*R)[NB + 1], int kb, T acc[NB / 16][NB / 16]) {
@@ -222,11 +291,6 @@ __device__ __forceinline__ void tile_mma(const T (*L)[NB + 1], const T (*R)[NB +
       for (int b = 0; b < RA; ++b) acc[a][b] += av[a] * bv[b];
   }
 }
-
-struct GJBatch {
-  const InvDesc* d;    // per matrix: n, ld, offset into the matrix base
-  const int64_t* qoff; // per matrix: offset of its row panels R and Q (NB x ld each)
-};
 
 // Symmetric Gauss-Jordan.  With the blocks before K already processed, the iterate
 // is [[X11, X12], [-X12^T, X22]] with X11, X22 symmetric, so every tile below the
@@ -374,8 +438,9 @@ k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __res
       if (I != J) A[(int64_t)(j0 + c) * d.ld + i0 + r] = sM * v;
     }
   }
-  if (I == K + 1 && J == K + 1) {
-    // the next diagonal block: invert it now for the next step
+  if (sizeof(T) == 8 && I == K + 1 && J == K + 1) {
+    // FP64: the next diagonal block is inverted now by this CTA, for the next step
+    // (FP32 uses the separate warp kernel after the update)
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < RA; ++a)
@@ -420,7 +485,10 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const int nblk = (nmax + NB - 1) / NB;
   const unsigned nb = (unsigned)descs.size();
   const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
-  k_gj_diag<T, NB><<<nb, kGJThreads, 0, s>>>(bt, 0, base, Dbuf[0], status, floor);
+  if constexpr (sizeof(T) == 4)
+    k_gj_diag_warp<NB><<<nb, 32, 0, s>>>(bt, 0, base, Dbuf[0], status, floor);
+  else
+    k_gj_diag<T, NB><<<nb, kGJThreads, 0, s>>>(bt, 0, base, Dbuf[0], status, floor);
   UFE_CHECK_LAUNCH();
   for (int step = 0; step < nblk; ++step) {
     T* Dc = Dbuf[step & 1];
@@ -432,6 +500,12 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
     k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, R.p, Q.p, Dc, Dn, status, floor);
     UFE_CHECK_LAUNCH();
     tl.end(s);
+    if constexpr (sizeof(T) == 4) {
+      if (step + 1 < nblk) {
+        k_gj_diag_warp<NB><<<nb, 32, 0, s>>>(bt, step + 1, base, Dn, status, floor);
+        UFE_CHECK_LAUNCH();
+      }
+    }
   }
 }
 
