@@ -9,6 +9,7 @@
 // stable for SPD matrices, whose pivots are Schur complements and stay positive;
 // a pivot <= 0 (or not finite) flags the matrix as singular.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "dense.cuh"
@@ -135,83 +136,19 @@ struct GJWidth<double> {
 };
 constexpr int kGJThreads = 256;
 
-// In-place inverse of the kb x kb leading block of D (NB x NB in shared memory) by
-// Gauss-Jordan without pivoting.  256 threads as 16 x 16; thread (ty, tx) keeps rows
-// ty + 16a and columns tx + 16b (a, b < NB/16) in registers; pivot row and column go
-// through shared memory, two barriers per pivot, the reciprocal is formed once.
-// Rows / columns >= kb are left alone.  Returns DEV_* flags: DEV_SINGULAR for a
-// non-positive or non-finite pivot, DEV_ILLCOND for a pivot below `floor` (used on
-// Jacobi-scaled matrices, whose pivots are at most 1: a tiny pivot means the
-// inverse has lost most of the working precision).
-template <typename T, int NB>
-__device__ int gj_block_inverse(T (*D)[NB + 1], int kb, T floor) {
-  constexpr int RA = NB / 16;
-  __shared__ T rowb[NB], colb[NB];
-  __shared__ T s_inv;
-  __shared__ int bad;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T v[RA][RA];
-#pragma unroll
-  for (int a = 0; a < RA; ++a)
-#pragma unroll
-    for (int b = 0; b < RA; ++b) v[a][b] = D[ty + 16 * a][tx + 16 * b];
-  if (threadIdx.x == 0) bad = 0;
-  for (int p = 0; p < kb; ++p) {
-    const int pa = p >> 4, pr = p & 15;
-    if (ty == pr) {
-#pragma unroll
-      for (int b = 0; b < RA; ++b) rowb[tx + 16 * b] = v[pa][b];
-    }
-    if (tx == pr) {
-#pragma unroll
-      for (int a = 0; a < RA; ++a) colb[ty + 16 * a] = v[a][pa];
-    }
-    if (threadIdx.x == (pr << 4) + pr) {
-      const T piv = v[pa][pa];
-      if (!(piv > T(0)) || !isfinite((double)piv))
-        bad |= DEV_SINGULAR;
-      else if (piv < floor)
-        bad |= DEV_ILLCOND;
-      s_inv = T(1) / piv;
-    }
-    __syncthreads();
-    const T inv = s_inv;
-#pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      const int r = ty + 16 * a;
-      const T cr = colb[r] * inv;
-#pragma unroll
-      for (int b = 0; b < RA; ++b) {
-        const int c = tx + 16 * b;
-        if (r == p)
-          v[a][b] = (c == p) ? inv : v[a][b] * inv;
-        else if (c == p)
-          v[a][b] = -cr;
-        else
-          v[a][b] -= cr * rowb[c];
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < RA; ++a)
-#pragma unroll
-    for (int b = 0; b < RA; ++b) D[ty + 16 * a][tx + 16 * b] = v[a][b];
-  __syncthreads();
-  return bad;
-}
-
 struct GJBatch {
   const InvDesc* d;    // per matrix: n, ld, offset into the matrix base
   const int64_t* qoff; // per matrix: offset of its row panels R and Q (NB x ld each)
 };
 
-// In-place inverse of the kb x kb leading block of one matrix by a single warp (FP32):
-// lane l keeps rows l + 32 i (i < NB/32) in registers, the pivot row is broadcast
-// column by column with shuffles, so the elimination needs no block-wide barrier
-// (the 256-thread version above spends two barriers per pivot).  Same flags as
-// gj_block_inverse.  The block is read from and written to global memory
-// (row-major, leading dimension ld); rows / columns >= kb are not touched.
+// Inverse of the kb x kb diagonal block of step `step` of one matrix by a single warp
+// (FP32), by Gauss-Jordan without pivoting (SPD, Jacobi-scaled): lane l keeps rows
+// l + 32 i (i < NB/32) in registers and the pivot row is broadcast column by column
+// with shuffles, so the elimination needs no block-wide barrier.  Flags:
+// DEV_SINGULAR for a non-positive or non-finite pivot, DEV_ILLCOND for a pivot below
+// `floor` (Jacobi-scaled matrices have pivots of at most 1).  The block is read from
+// the matrix (row-major, leading dimension ld), padded with the identity beyond kb,
+// and its inverse written to Dg (NB x NB).
 template <int NB>
 __global__ void __launch_bounds__(32)
 k_gj_diag_warp(GJBatch bt, int step, float* __restrict__ base, float* __restrict__ Dg, int* status, float floor) {
@@ -270,6 +207,73 @@ k_gj_diag_warp(GJBatch bt, int step, float* __restrict__ base, float* __restrict
   if (flags) atomicOr(status + b, flags);
 }
 
+// In-place inverse of the kb x kb (kb <= 32) leading block of one matrix in FP64 by
+// four warps, one per SM sub-partition so that all four FP64 pipes work: warp w keeps
+// rows 8w .. 8w+7, lane l column l.  Per pivot the owner warp scales the pivot row
+// (sc_c = a_pc / a_pp, sc_p = 1 / a_pp) into a double-buffered shared row, one
+// barrier, then every thread updates its 8 entries: a_rc -= a_rp sc_c (r != p, c != p),
+// a_rp = -a_rp sc_p, a_pc = sc_c; a_rp comes from lane p of the same warp by shuffle.
+// Flags as in the FP32 kernel.
+__global__ void __launch_bounds__(128)
+k_gj_diag_f64(GJBatch bt, int step, const double* __restrict__ base, double* __restrict__ Dg, int* status,
+              double floor) {
+  constexpr int NB = 32;
+  const int b = blockIdx.x;
+  const InvDesc d = bt.d[b];
+  const int k0 = step * NB;
+  if (k0 >= d.n) return;
+  const int kb = min(NB, d.n - k0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double row[2][NB];
+  __shared__ int s_flags;
+  if (threadIdx.x == 0) s_flags = 0;
+  const double* A = base + d.off;
+  double v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = 8 * warp + i;
+    v[i] = (r < kb && lane < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + lane] : (r == lane ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int p = 0; p < kb; ++p) {
+    const int o = p >> 3, sl = p & 7;
+    double* sc = row[p & 1];
+    if (warp == o) {
+      double vp = 0.0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i == sl) vp = v[i];
+      const double piv = __shfl_sync(0xffffffffu, vp, p);
+      if (lane == 0) {
+        if (!(piv > 0.0) || !isfinite(piv))
+          s_flags |= DEV_SINGULAR;
+        else if (piv < floor)
+          s_flags |= DEV_ILLCOND;
+      }
+      const double inv = 1.0 / piv;
+      sc[lane] = lane == p ? inv : vp * inv;
+    }
+    __syncthreads();
+    const double scl = sc[lane], scp = sc[p];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = 8 * warp + i;
+      const double a = __shfl_sync(0xffffffffu, v[i], p);
+      if (r == p)
+        v[i] = scl;
+      else if (lane == p)
+        v[i] = -a * scp;
+      else
+        v[i] -= a * scl;
+    }
+  }
+  double* Db = Dg + (int64_t)b * NB * NB;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) Db[(8 * warp + i) * NB + lane] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0 && s_flags) atomicOr(status + b, s_flags);
+}
+
 // out(NB x NB tile) = sum_l L[i][l] R[l][j], l < kb
 template <typename T, int NB>
 __device__ __forceinline__ void tile_mma(const T (*L)[NB + 1], const T (*R)[NB + 1], int kb, T acc[NB / 16][NB / 16]) {
@@ -300,27 +304,6 @@ __device__ __forceinline__ int gj_sign(int I, int J, int last_processed) {
   return ((I <= last_processed) != (J <= last_processed)) ? -1 : 1;
 }
 
-// first diagonal block: D^-1, one CTA per matrix
-template <typename T, int NB>
-__global__ void __launch_bounds__(kGJThreads)
-k_gj_diag(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ Dg, int* status, T floor) {
-  const int b = blockIdx.x;
-  const InvDesc d = bt.d[b];
-  const int k0 = step * NB;
-  if (k0 >= d.n) return;
-  const int kb = min(NB, d.n - k0);
-  __shared__ T D[NB][NB + 1];
-  const T* A = base + d.off;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    D[r][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : T(r == c ? 1 : 0);
-  }
-  __syncthreads();
-  const int flags = gj_block_inverse<T, NB>(D, kb, floor);
-  T* Db = Dg + (int64_t)b * NB * NB;
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Db[e] = D[e / NB][e % NB];
-  if (flags && threadIdx.x == 0) atomicOr(status + b, flags);
-}
 
 // old row panel R_Kt = A_Kt and Q_Kt = D^-1 A_Kt, 16 columns per CTA
 template <typename T, int NB>
@@ -359,31 +342,37 @@ k_gj_panel(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ R, 
   }
 }
 
-// tiles (I <= J) of the next iterate and their mirrors; CTA 0 takes the next
-// diagonal tile and inverts it for the next step (it starts first)
+// Tiles (I <= J) of the next iterate and their mirrors.  Look-ahead split:
+// mode 0 takes the tiles of block row / column K+1 (the next pivot's panel, one CTA
+// per block J, tile (min(K+1,J), max(K+1,J))), mode 1 all the others; the two run
+// on different streams, so the next diagonal inverse and panel overlap the bulk of
+// this step.
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R, const T* __restrict__ Q,
-            const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
+k_gj_update(GJBatch bt, int step, int nblk, int mode, T* __restrict__ base, const T* __restrict__ R,
+            const T* __restrict__ Q, const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
   constexpr int RA = NB / 16;
   const int b = blockIdx.y;
   const InvDesc d = bt.d[b];
   const int k0 = step * NB;
   const int nd = step + 1;
-  const int nd_tri = (nd < nblk) ? nd * nblk - nd * (nd - 1) / 2 : -1;   // triangle index of (nd, nd)
-  int t = (int)blockIdx.x;
-  if (nd_tri >= 0) {
-    if (blockIdx.x == 0)
-      t = nd_tri;
-    else if ((int)blockIdx.x <= nd_tri)
-      t = (int)blockIdx.x - 1;
+  int I, J;
+  if (mode == 0) {
+    if (nd >= nblk) return;
+    const int t = (int)blockIdx.x;
+    I = min(nd, t);
+    J = max(nd, t);
+  } else {
+    int t = (int)blockIdx.x;
+    I = 0;
+    while (t >= nblk - I) {
+      t -= nblk - I;
+      ++I;
+    }
+    J = I + t;
+    if (I == nd || J == nd) return;
   }
-  int I = 0;
-  while (t >= nblk - I) {
-    t -= nblk - I;
-    ++I;
-  }
-  const int J = I + t, K = step;
+  const int K = step;
   if (k0 >= d.n || J * NB >= d.n) return;
   const int kb = min(NB, d.n - k0);
   const int i0 = I * NB, j0 = J * NB, ib = min(NB, d.n - i0), jb = min(NB, d.n - j0);
@@ -438,24 +427,45 @@ k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __res
       if (I != J) A[(int64_t)(j0 + c) * d.ld + i0 + r] = sM * v;
     }
   }
-  if (sizeof(T) == 8 && I == K + 1 && J == K + 1) {
-    // FP64: the next diagonal block is inverted now by this CTA, for the next step
-    // (FP32 uses the separate warp kernel after the update)
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < RA; ++a)
-#pragma unroll
-      for (int c4 = 0; c4 < RA; ++c4) {
-        const int r = ty + 16 * a, c = tx + 16 * c4;
-        L[r][c] = (r < ib && c < jb) ? acc[a][c4] : T(r == c ? 1 : 0);
-      }
-    __syncthreads();
-    const int flags = gj_block_inverse<T, NB>(L, ib, floor);
-    T* Dn = Dnext + (int64_t)b * NB * NB;
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Dn[e] = L[e / NB][e % NB];
-    if (flags && threadIdx.x == 0) atomicOr(status + b, flags);
-  }
+
 }
+
+// inverse of the diagonal block of step `step` of every matrix into Dg
+template <typename T, int NB>
+static void launch_diag_inverse(const GJBatch& bt, int step, T* base, T* Dg, int* status, T floor, unsigned nb,
+                                cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    k_gj_diag_warp<NB><<<nb, 32, 0, s>>>(bt, step, base, Dg, status, floor);
+  } else {
+    static_assert(NB == 32, "the FP64 diagonal kernel takes 32 x 32 blocks");
+    k_gj_diag_f64<<<nb, 128, 0, s>>>(bt, step, base, Dg, status, floor);
+  }
+  UFE_CHECK_LAUNCH();
+}
+
+// library-owned side stream of the current device (look-ahead of the Gauss-Jordan steps)
+static cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t st[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!st[dev]) UFE_CUDA(cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking));
+  return st[dev];
+}
+
+struct GJEvents {
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  GJEvents() {
+    for (auto& x : e) UFE_CUDA(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+  }
+  ~GJEvents() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  cudaEvent_t operator[](int i) const { return e[i]; }
+};
 
 template <typename T>
 static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T floor) {
@@ -475,8 +485,11 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   DBuf<T> R, Q, D;
   dd.alloc(descs.size(), s);
   dq.alloc(descs.size(), s);
-  R.alloc(std::max<int64_t>(nq, 1), s);
-  Q.alloc(std::max<int64_t>(nq, 1), s);
+  R.alloc(2 * std::max<int64_t>(nq, 1), s);   // panels of two consecutive steps (look-ahead)
+  Q.alloc(2 * std::max<int64_t>(nq, 1), s);
+  nq = std::max<int64_t>(nq, 1);
+  cudaStream_t s2 = side_stream();
+  GJEvents ev;
   D.alloc(2 * descs.size() * NB * NB, s);
   T* Dbuf[2] = {D.p, D.p + descs.size() * NB * NB};
   UFE_CUDA(cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(InvDesc), cudaMemcpyHostToDevice, s));
@@ -485,27 +498,37 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const int nblk = (nmax + NB - 1) / NB;
   const unsigned nb = (unsigned)descs.size();
   const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
-  if constexpr (sizeof(T) == 4)
-    k_gj_diag_warp<NB><<<nb, 32, 0, s>>>(bt, 0, base, Dbuf[0], status, floor);
-  else
-    k_gj_diag<T, NB><<<nb, kGJThreads, 0, s>>>(bt, 0, base, Dbuf[0], status, floor);
-  UFE_CHECK_LAUNCH();
+  launch_diag_inverse<T, NB>(bt, 0, base, Dbuf[0], status, floor, nb, s);
   for (int step = 0; step < nblk; ++step) {
     T* Dc = Dbuf[step & 1];
     T* Dn = Dbuf[(step + 1) & 1];
-    k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s>>>(bt, step, base, R.p, Q.p, Dc);
-    UFE_CHECK_LAUNCH();
+    T* Rc = R.p + (step & 1) * nq;
+    T* Qc = Q.p + (step & 1) * nq;
+    if (step == 0) {
+      k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s>>>(bt, 0, base, Rc, Qc, Dc);
+      UFE_CHECK_LAUNCH();
+    }
+    // look-ahead: block row / column K+1, the next diagonal inverse and the next
+    // panel on the side stream while the main stream updates the other tiles
+    UFE_CUDA(cudaEventRecord(ev[0], s));
+    UFE_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
+    if (step + 1 < nblk) {
+      T* Rn = R.p + ((step + 1) & 1) * nq;
+      T* Qn = Q.p + ((step + 1) & 1) * nq;
+      k_gj_update<T, NB><<<dim3(nblk, nb), kGJThreads, 0, s2>>>(bt, step, nblk, 0, base, Rc, Qc, Dc, Dn, status,
+                                                                floor);
+      UFE_CHECK_LAUNCH();
+      launch_diag_inverse<T, NB>(bt, step + 1, base, Dn, status, floor, nb, s2);
+      k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s2>>>(bt, step + 1, base, Rn, Qn, Dn);
+      UFE_CHECK_LAUNCH();
+    }
     TimedLaunch tl;
     tl.begin(sizeof(T) == 8 ? "gj_update_f64" : "gj_update_f32", s);
-    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, R.p, Q.p, Dc, Dn, status, floor);
+    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, 1, base, Rc, Qc, Dc, Dn, status, floor);
     UFE_CHECK_LAUNCH();
     tl.end(s);
-    if constexpr (sizeof(T) == 4) {
-      if (step + 1 < nblk) {
-        k_gj_diag_warp<NB><<<nb, 32, 0, s>>>(bt, step + 1, base, Dn, status, floor);
-        UFE_CHECK_LAUNCH();
-      }
-    }
+    UFE_CUDA(cudaEventRecord(ev[1], s2));
+    UFE_CUDA(cudaStreamWaitEvent(s, ev[1], 0));
   }
 }
 
