@@ -141,70 +141,95 @@ struct GJBatch {
   const int64_t* qoff; // per matrix: offset of its row panels R and Q (NB x ld each)
 };
 
-// Inverse of the kb x kb diagonal block of step `step` of one matrix by a single warp
-// (FP32), by Gauss-Jordan without pivoting (SPD, Jacobi-scaled): lane l keeps rows
-// l + 32 i (i < NB/32) in registers and the pivot row is broadcast column by column
-// with shuffles, so the elimination needs no block-wide barrier.  Flags:
+// Inverse of the kb x kb diagonal block of step `step` of one matrix (FP32, NB = 64)
+// by Gauss-Jordan without pivoting (SPD, Jacobi-scaled), four warps, one per SM
+// sub-partition: warp w keeps rows 16w .. 16w+15, lane l columns l and l + 32.  Per
+// pivot the owner warp writes the pivot row twice into double-buffered shared rows,
+// as is (column p set to 1) and scaled (a_pc / a_pp, column p 1 / a_pp), one barrier,
+// then every thread forms its row factors l_r = a_rp / a_pp (a_rp by shuffle from the
+// lane holding column p) and updates its 32 entries with one FMA each:
+// a_rc -= l_r a_pc, column p from 0 (giving -l_r), row p takes the scaled row.  Flags:
 // DEV_SINGULAR for a non-positive or non-finite pivot, DEV_ILLCOND for a pivot below
 // `floor` (Jacobi-scaled matrices have pivots of at most 1).  The block is read from
-// the matrix (row-major, leading dimension ld), padded with the identity beyond kb,
-// and its inverse written to Dg (NB x NB).
-template <int NB>
-__global__ void __launch_bounds__(32)
-k_gj_diag_warp(GJBatch bt, int step, float* __restrict__ base, float* __restrict__ Dg, int* status, float floor) {
-  constexpr int R = NB / 32;
+// the matrix (row-major, leading dimension ld), padded with the identity beyond kb;
+// the inverse goes to Dg (NB x NB).
+__global__ void __launch_bounds__(128)
+k_gj_diag_f32(GJBatch bt, int step, const float* __restrict__ base, float* __restrict__ Dg, int* status,
+              float floor) {
+  constexpr int NB = 64, RW = 16;
   const int b = blockIdx.x;
   const InvDesc d = bt.d[b];
   const int k0 = step * NB;
   if (k0 >= d.n) return;
   const int kb = min(NB, d.n - k0);
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float prow[2][NB], srow[2][NB];
+  __shared__ int s_flags;
+  if (threadIdx.x == 0) s_flags = 0;
   const float* A = base + d.off;
-  float v[R][NB];
+  float v[RW][2];
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int r = lane + 32 * i;
+  for (int i = 0; i < RW; ++i) {
+    const int r = RW * warp + i;
 #pragma unroll
-    for (int c = 0; c < NB; ++c)
-      v[i][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : (r == c ? 1.f : 0.f);
+    for (int j = 0; j < 2; ++j) {
+      const int c = lane + 32 * j;
+      v[i][j] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : (r == c ? 1.f : 0.f);
+    }
   }
-  int flags = 0;
+  __syncthreads();
+  for (int p = 0; p < kb; ++p) {
+    const int o = p / RW, sl = p % RW, pl = p & 31, pj = p >> 5;
+    float* pr = prow[p & 1];
+    float* sc = srow[p & 1];
+    if (warp == o) {
+      float vp0 = 0.f, vp1 = 0.f;
 #pragma unroll
-  for (int p = 0; p < NB; ++p) {
-    if (p < kb) {
-      const int o = p % 32, s = p / 32;
-      const float piv = __shfl_sync(0xffffffffu, v[s][p], o);
-      if (!(piv > 0.f) || !isfinite(piv))
-        flags |= DEV_SINGULAR;
-      else if (piv < floor)
-        flags |= DEV_ILLCOND;
-      const float inv = 1.f / piv;
-      float cr[R];
-      bool isp[R];
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        isp[i] = lane + 32 * i == p;
-        cr[i] = v[i][p] * inv;
-      }
-#pragma unroll
-      for (int c = 0; c < NB; ++c) {
-        const float rc = __shfl_sync(0xffffffffu, v[s][c], o);
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          if (c == p)
-            v[i][c] = isp[i] ? inv : -cr[i];
-          else
-            v[i][c] = isp[i] ? v[i][c] * inv : v[i][c] - cr[i] * rc;
+      for (int i = 0; i < RW; ++i)
+        if (i == sl) {
+          vp0 = v[i][0];
+          vp1 = v[i][1];
         }
+      const float piv = __shfl_sync(0xffffffffu, pj ? vp1 : vp0, pl);
+      if (lane == 0) {
+        if (!(piv > 0.f) || !isfinite(piv))
+          s_flags |= DEV_SINGULAR;
+        else if (piv < floor)
+          s_flags |= DEV_ILLCOND;
+      }
+      const float inv = 1.f / piv;
+      sc[lane] = lane == p ? inv : vp0 * inv;
+      sc[lane + 32] = lane + 32 == p ? inv : vp1 * inv;
+      pr[lane] = lane == p ? 1.f : vp0;
+      pr[lane + 32] = lane + 32 == p ? 1.f : vp1;
+    }
+    __syncthreads();
+    const float inv = sc[p];
+    float scl[2], m[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      scl[j] = sc[lane + 32 * j];
+      m[j] = pr[lane + 32 * j];
+    }
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+      const int r = RW * warp + i;
+      const float l = __shfl_sync(0xffffffffu, pj ? v[i][1] : v[i][0], pl) * inv;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float base_v = (lane + 32 * j == p) ? 0.f : v[i][j];
+        const float nv = fmaf(-l, m[j], base_v);
+        v[i][j] = r == p ? scl[j] : nv;
       }
     }
   }
   float* Db = Dg + (int64_t)b * NB * NB;
 #pragma unroll
-  for (int i = 0; i < R; ++i)
+  for (int i = 0; i < RW; ++i)
 #pragma unroll
-    for (int c = 0; c < NB; ++c) Db[(lane + 32 * i) * NB + c] = v[i][c];
-  if (flags) atomicOr(status + b, flags);
+    for (int j = 0; j < 2; ++j) Db[(RW * warp + i) * NB + lane + 32 * j] = v[i][j];
+  __syncthreads();
+  if (threadIdx.x == 0 && s_flags) atomicOr(status + b, s_flags);
 }
 
 // In-place inverse of the kb x kb (kb <= 32) leading block of one matrix in FP64 by
@@ -254,17 +279,16 @@ k_gj_diag_f64(GJBatch bt, int step, const double* __restrict__ base, double* __r
       sc[lane] = lane == p ? inv : vp * inv;
     }
     __syncthreads();
-    const double scl = sc[lane], scp = sc[p];
+    // one FMA per entry: column p starts from 0 and takes sc_p
+    const double scl = sc[lane];
+    const double m = lane == p ? sc[p] : scl;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = 8 * warp + i;
       const double a = __shfl_sync(0xffffffffu, v[i], p);
-      if (r == p)
-        v[i] = scl;
-      else if (lane == p)
-        v[i] = -a * scp;
-      else
-        v[i] -= a * scl;
+      const double base = lane == p ? 0.0 : v[i];
+      const double nv = fma(-a, m, base);
+      v[i] = r == p ? scl : nv;
     }
   }
   double* Db = Dg + (int64_t)b * NB * NB;
@@ -305,17 +329,19 @@ __device__ __forceinline__ int gj_sign(int I, int J, int last_processed) {
 }
 
 
-// old row panel R_Kt = A_Kt and Q_Kt = D^-1 A_Kt, 16 columns per CTA
+// old row panel R_Kt = A_Kt and Q_Kt = D^-1 A_Kt: each CTA loads D^-1 once and walks
+// `cols` columns in chunks of 16 (64 for large batches, 16 when few matrices need
+// the CTAs)
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_panel(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ R, T* __restrict__ Q,
+k_gj_panel(GJBatch bt, int step, int cols, const T* __restrict__ base, T* __restrict__ R, T* __restrict__ Q,
            const T* __restrict__ Dg) {
   const int b = blockIdx.y;
   const InvDesc d = bt.d[b];
   const int k0 = step * NB;
-  const int c0 = blockIdx.x * 16;
-  if (k0 >= d.n || c0 >= d.n || (c0 >= k0 && c0 < k0 + NB)) return;
-  const int kb = min(NB, d.n - k0), cb = min(16, d.n - c0);
+  const int cbase = blockIdx.x * cols;
+  if (k0 >= d.n || cbase >= d.n) return;
+  const int kb = min(NB, d.n - k0);
   __shared__ T Ds[NB][NB + 1];
   __shared__ T W[NB][17];
   const T* A = base + d.off;
@@ -323,22 +349,27 @@ k_gj_panel(GJBatch bt, int step, const T* __restrict__ base, T* __restrict__ R, 
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Ds[e / NB][e % NB] = Db[e];
   T* Rb = R + bt.qoff[b];
   T* Qb = Q + bt.qoff[b];
-  for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
-    const int r = e / 16, c = e % 16;
-    T v = T(0);
-    if (r < kb && c < cb) {
-      v = A[(int64_t)(k0 + r) * d.ld + c0 + c];
-      Rb[(int64_t)r * d.ld + c0 + c] = v;
+  for (int c0 = cbase; c0 < min(cbase + cols, d.n); c0 += 16) {
+    if (c0 >= k0 && c0 < k0 + NB) continue;   // the diagonal block (uniform across the CTA)
+    const int cb = min(16, d.n - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
+      const int r = e / 16, c = e % 16;
+      T v = T(0);
+      if (r < kb && c < cb) {
+        v = A[(int64_t)(k0 + r) * d.ld + c0 + c];
+        Rb[(int64_t)r * d.ld + c0 + c] = v;
+      }
+      W[r][c] = v;
     }
-    W[r][c] = v;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
-    const int r = e / 16, c = e % 16;
-    if (r >= kb || c >= cb) continue;
-    T acc = T(0);
-    for (int l = 0; l < kb; ++l) acc += Ds[r][l] * W[l][c];
-    Qb[(int64_t)r * d.ld + c0 + c] = acc;
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
+      const int r = e / 16, c = e % 16;
+      if (r >= kb || c >= cb) continue;
+      T acc = T(0);
+      for (int l = 0; l < kb; ++l) acc += Ds[r][l] * W[l][c];
+      Qb[(int64_t)r * d.ld + c0 + c] = acc;
+    }
   }
 }
 
@@ -434,13 +465,17 @@ k_gj_update(GJBatch bt, int step, int nblk, int mode, T* __restrict__ base, cons
 template <typename T, int NB>
 static void launch_diag_inverse(const GJBatch& bt, int step, T* base, T* Dg, int* status, T floor, unsigned nb,
                                 cudaStream_t s) {
+  TimedLaunch tl;
+  tl.begin(sizeof(T) == 8 ? "gj_diag_f64" : "gj_diag_f32", s);
   if constexpr (sizeof(T) == 4) {
-    k_gj_diag_warp<NB><<<nb, 32, 0, s>>>(bt, step, base, Dg, status, floor);
+    static_assert(NB == 64, "the FP32 diagonal kernel takes 64 x 64 blocks");
+    k_gj_diag_f32<<<nb, 128, 0, s>>>(bt, step, base, Dg, status, floor);
   } else {
     static_assert(NB == 32, "the FP64 diagonal kernel takes 32 x 32 blocks");
     k_gj_diag_f64<<<nb, 128, 0, s>>>(bt, step, base, Dg, status, floor);
   }
   UFE_CHECK_LAUNCH();
+  tl.end(s);
 }
 
 // library-owned side stream of the current device (look-ahead of the Gauss-Jordan steps)
@@ -498,6 +533,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const int nblk = (nmax + NB - 1) / NB;
   const unsigned nb = (unsigned)descs.size();
   const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
+  const int pcols = descs.size() >= 16 ? 64 : 16;
   launch_diag_inverse<T, NB>(bt, 0, base, Dbuf[0], status, floor, nb, s);
   for (int step = 0; step < nblk; ++step) {
     T* Dc = Dbuf[step & 1];
@@ -505,7 +541,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
     T* Rc = R.p + (step & 1) * nq;
     T* Qc = Q.p + (step & 1) * nq;
     if (step == 0) {
-      k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s>>>(bt, 0, base, Rc, Qc, Dc);
+      k_gj_panel<T, NB><<<dim3((nmax + pcols - 1) / pcols, nb), kGJThreads, 0, s>>>(bt, 0, pcols, base, Rc, Qc, Dc);
       UFE_CHECK_LAUNCH();
     }
     // look-ahead: block row / column K+1, the next diagonal inverse and the next
@@ -519,8 +555,11 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
                                                                 floor);
       UFE_CHECK_LAUNCH();
       launch_diag_inverse<T, NB>(bt, step + 1, base, Dn, status, floor, nb, s2);
-      k_gj_panel<T, NB><<<dim3((nmax + 15) / 16, nb), kGJThreads, 0, s2>>>(bt, step + 1, base, Rn, Qn, Dn);
+      TimedLaunch tp;
+      tp.begin(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s2);
+      k_gj_panel<T, NB><<<dim3((nmax + pcols - 1) / pcols, nb), kGJThreads, 0, s2>>>(bt, step + 1, pcols, base, Rn, Qn, Dn);
       UFE_CHECK_LAUNCH();
+      tp.end(s2);
     }
     TimedLaunch tl;
     tl.begin(sizeof(T) == 8 ? "gj_update_f64" : "gj_update_f32", s);
