@@ -74,7 +74,7 @@ typedef int ufe_status;
 #define UFE_COARSE_CEF 2
 /* ufe_bddc_opts.precision */
 #define UFE_PREC_FP64  0           /* every local factor and product in FP64 */
-#define UFE_PREC_MIXED 1           /* Jacobi-scaled FP32 local operators and coarse inverse; FP64 PCG, weights */
+#define UFE_PREC_MIXED 1           /* Jacobi-scaled FP32 local operators; FP64 PCG, weights, coarse */
 
 #define UFE_PIN_NONE -1
 #define UFE_PIN_AUTO -2
@@ -97,8 +97,8 @@ int64_t ufe_kernel_launches(void);
 /* Kernel timing (instrumentation only; no paper counterpart).  While enabled, the
  * library brackets every launch of the named set-up kernels with CUDA events on
  * the stream it launches them on:
- *   "gj_update_f64"  FP64 Gauss-Jordan update step (coarse and local matrices in FP64 mode)
- *   "gj_update_f32"  FP32 Gauss-Jordan update step (local and coarse matrices in mixed precision)
+ *   "gj_update_f64"  FP64 Gauss-Jordan update step (coarse matrix; local matrices in FP64 mode)
+ *   "gj_update_f32"  FP32 Gauss-Jordan update step (local matrices in mixed precision)
  *   "gj_diag_f64", "gj_diag_f32", "gj_panel_f64", "gj_panel_f32"  the diagonal-block
  *                    inverse and the row panel of each Gauss-Jordan step
  *   "integrate_cut"  marching-tetrahedra cut-cell integration
@@ -241,16 +241,12 @@ typedef struct {
   double inverse_flops_coarse;    /* n_coarse^3 (symmetric Gauss-Jordan, algorithmic count) */
   /* storage read by the per-iteration kernels (bytes): A_II^-1, the constrained
    * Neumann operator K, the coarse basis Phi (FP32 in mixed precision), the A_GI and
-   * A_IG stencils (index + value per slot), the coarse inverse (FP32 with its FP64
-   * scale vector in mixed precision, else FP64) */
+   * A_IG stencils (index + value per slot), the FP64 coarse inverse */
   double bytes_interior_inverse, bytes_neumann, bytes_coarse_basis, bytes_offdiag, bytes_coarse_inverse;
   int64_t interior_slots, interface_slots;   /* sum over subdomains of local interior / interface DOFs */
   int32_t fp64_refactor;   /* mixed precision requested: 1 when a Jacobi-scaled local matrix had an FP32
                               pivot below 1e-3 (or not positive), so this problem keeps FP64 local
                               operators (factored and applied in FP64, classical PCG) */
-  int32_t fp64_coarse;     /* mixed precision requested: 1 when the Jacobi-scaled coarse matrix had an
-                              FP32 pivot below 1e-3 (or the local operators fell back to FP64), so the
-                              coarse inverse is kept in FP64 */
 } ufe_bddc_info;
 
 /*
@@ -262,9 +258,7 @@ typedef struct {
  * (Eq. alge-weighting); harmonic extension with local Dirichlet problems.
  * Local operators are formed explicitly: A_II^-1, the constrained Neumann
  * inverse restricted to the interface and the interface rows of the coarse
- * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled in FP64 and inverted by
- * Gauss-Jordan: in FP64, or in mixed precision in FP32 after Jacobi scaling
- * (S A_c S, S = diag(A_c)^-1/2) when every scaled pivot is at least 1e-3.
+ * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled and inverted in FP64.
  * Errors: SINGULAR_LOCAL (e.g. a floating subdomain with no coarse DOF),
  * SINGULAR_COARSE, INVALID_ARG, CUDA, OUT_OF_MEMORY, TIMEOUT.
  */

@@ -412,7 +412,6 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->interior_slots = B->n_vIloc;
     info->interface_slots = B->n_vGloc;
     info->fp64_refactor = B->fp64_refactor;
-    info->fp64_coarse = B->fp64_coarse;
   });
 }
 

@@ -724,24 +724,6 @@ __global__ void k_symmetrize(double* A, int n, int ld) {
   A[(int64_t)j * ld + i] = v;
 }
 
-// Jacobi scale of the coarse matrix, s_i = a_ii^-1/2 (0 for a non-positive diagonal,
-// which the FP32 inversion then reports as a zero pivot)
-__global__ void k_coarse_scale(int n, int ld, const double* __restrict__ A, double* __restrict__ sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double d = A[(int64_t)i * ld + i];
-  sc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
-}
-
-// FP32 copy of the Jacobi-scaled coarse matrix, s_i a_ij s_j (padding columns 0)
-__global__ void k_coarse_to_f32(int n, int ld, const double* __restrict__ A, const double* __restrict__ sc,
-                                float* __restrict__ F) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n * ld) return;
-  const int i = (int)(e / ld), j = (int)(e % ld);
-  F[e] = j < n ? (float)(sc[i] * A[e] * sc[j]) : 0.f;
-}
-
 __global__ void k_scale_ptr(int64_t n, int nc, const int32_t* __restrict__ in, int32_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = nc * in[i];
@@ -1168,7 +1150,6 @@ void bddc_build(Bddc& B) {
       B.fGC.release();
       B.mixed = false;
       B.fp64_refactor = 1;
-      B.fp64_coarse = 1;
       B.bytes_II *= 2.0;
       B.bytes_GG *= 2.0;
       B.bytes_GC *= 2.0;
@@ -1200,32 +1181,8 @@ void bddc_build(Bddc& B) {
     DBuf<int> st;
     st.alloc(1, s);
     st.zero();
-    if (B.mixed) {
-      // mixed precision: FP32 Gauss-Jordan on the Jacobi-scaled A_c under the same
-      // pivot floor as the local operators; the coarse solve applies S (S A_c S)^-1 S
-      B.sc_c.alloc(nco, s);
-      B.fAc_inv.alloc((size_t)nco * B.ldc, s);
-      k_coarse_scale<<<grid_for(nco, T), T, 0, s>>>((int)nco, B.ldc, B.Ac_inv.p, B.sc_c.p);
-      UFE_CHECK_LAUNCH();
-      k_coarse_to_f32<<<grid_for(nco * B.ldc, T), T, 0, s>>>((int)nco, B.ldc, B.Ac_inv.p, B.sc_c.p, B.fAc_inv.p);
-      UFE_CHECK_LAUNCH();
-      large_inverse<float>(B.fAc_inv.p, (int)nco, B.ldc, st.p, s, 1e-3f);
-      if (scalar_to_host(st.p, s) == 0) {
-        B.coarse_f32 = true;
-        B.Ac_inv.release();
-        B.bytes_Ac = 0.5 * B.bytes_Ac + 8.0 * (double)nco;
-      } else {
-        // a scaled pivot below the floor (or a non-positive one): FP64 coarse inverse
-        B.fAc_inv.release();
-        B.sc_c.release();
-        B.fp64_coarse = 1;
-        st.zero();
-      }
-    }
-    if (!B.coarse_f32) {
-      large_inverse<double>(B.Ac_inv.p, (int)nco, B.ldc, st.p, s);
-      UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
-    }
+    large_inverse<double>(B.Ac_inv.p, (int)nco, B.ldc, st.p, s);
+    UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
   }
 
   ph_co.end(s);

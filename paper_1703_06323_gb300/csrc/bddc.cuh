@@ -98,10 +98,7 @@ struct Bddc {
   DBuf<double> sI, sG;          // Jacobi scales of the local slots (operators stored scaled)
   DBuf<int32_t> gi_k, ig_k;     // A_GI / A_IG in ELL form (local indices)
   DBuf<double> gi_v, ig_v;
-  DBuf<double> Ac_inv;          // n_coarse x ldc, FP64 (released when the FP32 inverse is kept)
-  DBuf<float> fAc_inv;          // n_coarse x ldc, FP32 inverse of the Jacobi-scaled A_c (mixed)
-  DBuf<double> sc_c;            // n_coarse Jacobi scale of A_c (with fAc_inv)
-  bool coarse_f32 = false;      // the coarse solve applies S fAc_inv S
+  DBuf<double> Ac_inv;          // n_coarse x ldc, FP64
   int ldc = 0;
 
   // solver work space
@@ -123,7 +120,6 @@ struct Bddc {
   double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
   double bytes_II = 0.0, bytes_GG = 0.0, bytes_GC = 0.0, bytes_off = 0.0, bytes_Ac = 0.0;
   int fp64_refactor = 0;                // mixed precision requested, FP64 local operators kept (FP32 too ill-conditioned)
-  int fp64_coarse = 0;                  // mixed precision requested, FP64 coarse inverse kept
 
   SubMeta meta() const;
   ~Bddc();

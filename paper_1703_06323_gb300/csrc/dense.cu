@@ -577,8 +577,8 @@ void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cu
 }
 
 template <typename T>
-void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s, T pivot_floor) {
-  gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s, pivot_floor);
+void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s) {
+  gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s, T(0));
 }
 
 template void batched_gemm<double>(bool, bool, const std::vector<GemmDesc>&, const double*, const double*, double*,
@@ -587,7 +587,6 @@ template void batched_gemm<float>(bool, bool, const std::vector<GemmDesc>&, cons
                                   float, cudaStream_t);
 template void batched_inverse<double>(const std::vector<InvDesc>&, double*, int*, cudaStream_t, double);
 template void batched_inverse<float>(const std::vector<InvDesc>&, float*, int*, cudaStream_t, float);
-template void large_inverse<double>(double*, int, int, int*, cudaStream_t, double);
-template void large_inverse<float>(float*, int, int, int*, cudaStream_t, float);
+template void large_inverse<double>(double*, int, int, int*, cudaStream_t);
 
 }  // namespace ufe

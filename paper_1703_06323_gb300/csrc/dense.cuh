@@ -31,6 +31,6 @@ void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cu
 
 // in-place inverse of one large SPD matrix using the whole GPU
 template <typename T>
-void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s, T pivot_floor = T(0));
+void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s);
 
 }  // namespace ufe

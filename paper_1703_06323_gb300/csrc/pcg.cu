@@ -716,69 +716,42 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   cl.sync();
 }
 
-// K5: r_c gathered from the subdomain parts, u_c = A_c^-1 r_c: FP64 inverse, or (TA =
-// float, mixed precision) u_c = S X S r_c with X the FP32 inverse of the Jacobi-scaled
-// S A_c S; rows accumulate in FP64 either way
-template <typename TA>
-__global__ void k_coarse_solve(int64_t nco, int ldc, const TA* __restrict__ Ainv, const double* __restrict__ scl,
-                               const int32_t* __restrict__ cpos, const uint8_t* __restrict__ cnn,
-                               const double* __restrict__ gC, double* __restrict__ uc, const PcgScalars* sc) {
+// K5: r_c gathered from the subdomain parts, u_c = A_c^-1 r_c (FP64)
+__global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ Ainv, const int32_t* __restrict__ cpos,
+                               const uint8_t* __restrict__ cnn, const double* __restrict__ gC, double* __restrict__ uc,
+                               const PcgScalars* sc) {
   if (sc && sc->done) return;
   extern __shared__ __align__(16) char smem[];
   double* rc = reinterpret_cast<double*>(smem);
   for (int64_t l = threadIdx.x; l < ldc; l += blockDim.x) {
     double s = 0.0;
-    if (l < nco) {
+    if (l < nco)
       for (int k = 0; k < cnn[l]; ++k) s += gC[cpos[l * 8 + k]];
-      if (scl) s *= scl[l];
-    }
     rc[l] = s;
   }
   __syncthreads();
   // one warp per row; eight independent 16-byte loads per lane in flight
-  using V = typename VecT<TA>::type;
-  constexpr int VN = VecT<TA>::n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   constexpr int U = 8;
   for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < nco; row += (int64_t)gridDim.x * nw) {
-    const TA* Ar = Ainv + row * ldc;
+    const double* Ar = Ainv + row * ldc;
     double s = 0.0;
-    for (int c0 = lane * VN; c0 < ldc; c0 += 32 * VN * U) {
-      V v[U];
+    for (int c0 = lane * 2; c0 < ldc; c0 += 64 * U) {
+      double2 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int c = c0 + 32 * VN * u;
-        if (c < ldc)
-          v[u] = *reinterpret_cast<const V*>(Ar + c);
-        else
-          v[u] = V{};
+        const int c = c0 + 64 * u;
+        v[u] = c < ldc ? *reinterpret_cast<const double2*>(Ar + c) : make_double2(0.0, 0.0);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int c = c0 + 32 * VN * u;
-        if (c < ldc) {
-          const TA* e = reinterpret_cast<const TA*>(&v[u]);
-#pragma unroll
-          for (int q = 0; q < VN; ++q) s += (double)e[q] * rc[c + q];
-        }
+        const int c = c0 + 64 * u;
+        if (c < ldc) s += v[u].x * rc[c] + v[u].y * rc[c + 1];
       }
     }
     s = warp_sum(s);
-    if (lane == 0) uc[row] = scl ? scl[row] * s : s;
+    if (lane == 0) uc[row] = s;
   }
-}
-
-// u_c = A_c^-1 r_c in the precision the coarse inverse was kept in
-static void launch_coarse_solve(const Bddc& B, const double* gC, double* uc, const PcgScalars* sc, cudaStream_t s) {
-  const size_t csm = (size_t)B.ldc * 8;
-  const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
-  if (B.coarse_f32)
-    k_coarse_solve<float><<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.fAc_inv.p, B.sc_c.p, B.cpos.p, B.coarse_nn.p, gC,
-                                               uc, sc);
-  else
-    k_coarse_solve<double><<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, nullptr, B.cpos.p, B.coarse_nn.p, gC,
-                                                uc, sc);
-  UFE_CHECK_LAUNCH();
 }
 
 // K6: coarse prolongation, vw += w Phi u_c^w on the interface rows of w
@@ -1000,8 +973,11 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   UFE_CHECK_LAUNCH();
   t4.end(s);
   if (B.n_coarse > 0) {
+    const size_t csm = (size_t)B.ldc * 8;
+    const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
     t5.begin("coarse_solve", s);
-    launch_coarse_solve(B, B.gC.p, B.uc.p, sc, s);
+    k_coarse_solve<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, B.gC.p, B.uc.p, sc);
+    UFE_CHECK_LAUNCH();
     t5.end(s);
     t6.begin("prec_prolong", s);
     k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
@@ -1060,8 +1036,7 @@ static void set_smem_limits(Bddc& B) {
   set_smem_limits_for<float, 1>(optin);
   set_smem_limits_for<double, 3>(optin);
   set_smem_limits_for<float, 3>(optin);
-  raise_smem_limit(k_coarse_solve<double>, optin);
-  raise_smem_limit(k_coarse_solve<float>, optin);
+  raise_smem_limit(k_coarse_solve, optin);
   done[dev] = true;
 }
 
@@ -1346,7 +1321,10 @@ static void launch_preconditioner_static(Bddc& B, const double* r, double* z, do
   k_prec_neumann<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
   UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
-    launch_coarse_solve(B, gC, uc, nullptr, s);
+    const size_t csm = (size_t)B.ldc * 8;
+    const unsigned cgr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
+    k_coarse_solve<<<cgr, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, nullptr);
+    UFE_CHECK_LAUNCH();
     k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
     UFE_CHECK_LAUNCH();
   }

@@ -55,7 +55,7 @@ class BddcInfo(ctypes.Structure):
                 ("bytes_neumann", ctypes.c_double), ("bytes_coarse_basis", ctypes.c_double),
                 ("bytes_offdiag", ctypes.c_double), ("bytes_coarse_inverse", ctypes.c_double),
                 ("interior_slots", ctypes.c_int64), ("interface_slots", ctypes.c_int64),
-                ("fp64_refactor", ctypes.c_int32), ("fp64_coarse", ctypes.c_int32)]
+                ("fp64_refactor", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):

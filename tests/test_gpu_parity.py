@@ -175,24 +175,6 @@ def test_preconditioner_mixed(ufe, name):
     assert energy_error(orc.sys.A, z, ref) <= 1e-3
 
 
-@pytest.mark.parametrize("name", ["sphere16", "sphere_ragged"])
-def test_mixed_precision_choice(ufe, name):
-    """Mixed precision keeps FP32 local operators and an FP32 coarse inverse when every
-    Jacobi-scaled pivot clears 1e-3 (these meshes); FP64 mode reports neither fallback.
-    The coarse inverse is then half the FP64 bytes plus its FP64 scale vector."""
-    orc = oracle_run(name)
-    with _solver(ufe, orc.p, precision="mixed") as S:
-        bi = S.bddc_info
-        assert bi["fp64_refactor"] == 0 and bi["fp64_coarse"] == 0
-        nc = bi["n_coarse"]
-        ldc = (nc + 3) // 4 * 4
-        assert bi["bytes_coarse_inverse"] == 4.0 * nc * ldc + 8.0 * nc
-    with _solver(ufe, orc.p, precision="fp64") as S:
-        bi = S.bddc_info
-        assert bi["fp64_refactor"] == 0 and bi["fp64_coarse"] == 0
-        assert bi["bytes_coarse_inverse"] == 8.0 * nc * ldc
-
-
 @pytest.mark.parametrize("name", SOLVABLE)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_pcg_solution(ufe, name, precision):
