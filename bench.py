@@ -336,8 +336,8 @@ def run_ours(args, rank, world):
     t_mixed, i_mixed, launches = timed("mixed", args.steps)
     U.ufe_timing_enable(False)
     kt = {k: U.ufe_timing_get(k) for k in ("gj_update_f64", "gj_update_f32", "integrate_cut")}
-    kt_extra = {k: U.ufe_timing_get(k)[0] / args.steps for k in ("gj_diag_f64", "gj_diag_f32", "gj_panel_f64",
-                                                                   "gj_panel_f32")}
+    kt_extra = {k: U.ufe_timing_get(k)[0] / args.steps for k in ("gj_lookahead_f64", "gj_lookahead_f32",
+                                                                   "gj_panel_f64", "gj_panel_f32")}
     phases = {k: U.ufe_timing_get(k)[0] / args.steps for k in
               ("phase_mesh", "phase_assemble", "phase_objects", "phase_local", "phase_factor", "phase_coarse",
                "phase_solve")}

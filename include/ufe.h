@@ -99,8 +99,10 @@ int64_t ufe_kernel_launches(void);
  * the stream it launches them on:
  *   "gj_update_f64"  FP64 Gauss-Jordan update step (coarse matrix; local matrices in FP64 mode)
  *   "gj_update_f32"  FP32 Gauss-Jordan update step (local matrices in mixed precision)
- *   "gj_diag_f64", "gj_diag_f32", "gj_panel_f64", "gj_panel_f32"  the diagonal-block
- *                    inverse and the row panel of each Gauss-Jordan step
+ *   "gj_lookahead_f64", "gj_lookahead_f32"  block row / column K+1 of each step with the
+ *                    next diagonal-block inverse
+ *   "gj_panel_f64", "gj_panel_f32"  the row panel of each Gauss-Jordan step
+ *   "gj_diag_f64", "gj_diag_f32"  the first diagonal-block inverse
  *   "integrate_cut"  marching-tetrahedra cut-cell integration
  * the per-iteration kernels when they run outside a CUDA graph (ufe_system_apply,
  * ufe_bddc_apply and the first preconditioner application of ufe_pcg_solve):

@@ -130,7 +130,8 @@ ufe_status ufe_timing_get(const char* kernel, double* total_ms, int64_t* launche
                                   "phase_assemble", "phase_objects", "phase_local", "phase_factor",
                                   "phase_coarse", "phase_solve", "apply", "prec_interior",
                                   "prec_neumann", "coarse_solve", "prec_prolong", "prec_final",
-                                  "gj_diag_f64", "gj_diag_f32", "gj_panel_f64", "gj_panel_f32"};
+                                  "gj_diag_f64", "gj_diag_f32", "gj_panel_f64", "gj_panel_f32",
+                                  "gj_lookahead_f64", "gj_lookahead_f32"};
     bool ok = false;
     for (const char* kn : known) ok = ok || k == kn;
     UFE_REQUIRE(ok, UFE_ERR_INVALID_ARG, "unknown timed kernel or phase");

@@ -113,13 +113,17 @@ void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, 
 }
 
 // ---------------------------------------------------------------------------
-// Batched blocked Gauss-Jordan inversion, one block column (width kGJ) per step,
+// Batched blocked Gauss-Jordan inversion, one block column (width NB) per step,
 // three launches per step over the whole batch:
-//   diag:   D^-1 of the diagonal block (register-blocked, one CTA per matrix);
-//   panel:  the old row panel R_K* = A_K* and Q_K* = D^-1 A_K*;
-//   update: every tile (I <= J) of the next iterate, A_IJ - P_IK Q_KJ, Q_KJ,
-//           -P_IK D^-1 or D^-1, with P_IK = +-R_KI^T, and its mirror tile.
-// Reads of the panels come from R / Q / D^-1, so the update runs in place
+//   panel:     the old row panel R_K* = A_K* and Q_K* = D^-1 A_K*;
+//   update:    every tile (I <= J) of the next iterate, A_IJ - P_IK Q_KJ, Q_KJ,
+//              -P_IK D^-1 or D^-1, with P_IK = +-R_KI^T, and its mirror tile, except
+//              block row / column K+1;
+//   lookahead: block row / column K+1 of the same update, with the diagonal tile
+//              (K+1, K+1) kept in shared memory and inverted there (D^-1 of the next
+//              step; register-blocked Gauss-Jordan, one CTA per matrix).
+// lookahead and the next panel run on a side stream while update runs on the
+// caller's.  Reads of the panels come from R / Q / D^-1, so the update runs in place
 // without races.
 // ---------------------------------------------------------------------------
 // Block width: 64 for FP32; 32 for FP64, whose per-SM rate on this chip is low
@@ -141,159 +145,115 @@ struct GJBatch {
   const int64_t* qoff; // per matrix: offset of its row panels R and Q (NB x ld each)
 };
 
-// Inverse of the kb x kb diagonal block of step `step` of one matrix (FP32, NB = 64)
-// by Gauss-Jordan without pivoting (SPD, Jacobi-scaled), four warps, one per SM
-// sub-partition: warp w keeps rows 16w .. 16w+15, lane l columns l and l + 32.  Per
-// pivot the owner warp writes the pivot row twice into double-buffered shared rows,
-// as is (column p set to 1) and scaled (a_pc / a_pp, column p 1 / a_pp), one barrier,
-// then every thread forms its row factors l_r = a_rp / a_pp (a_rp by shuffle from the
-// lane holding column p) and updates its 32 entries with one FMA each:
-// a_rc -= l_r a_pc, column p from 0 (giving -l_r), row p takes the scaled row.  Flags:
+// Inverse of one kb x kb diagonal block by Gauss-Jordan without pivoting (SPD,
+// Jacobi-scaled), spread over NW warps (one or two per SM sub-partition): warp w keeps
+// rows RW w .. RW w + RW - 1 (RW = NB / NW), lane l the columns l + 32 j.  Per pivot the
+// owner warp writes the pivot row twice into double-buffered shared rows, as is
+// (column p set to 1) and scaled (a_pc / a_pp, column p 1 / a_pp), one barrier, then
+// every thread forms its row factors l_r = a_rp / a_pp (a_rp by shuffle from the lane
+// holding column p) and updates each entry with one FMA: a_rc -= l_r a_pc, column p
+// from 0 (giving -l_r), row p takes the scaled row.  FP64, whose pipe is the bound on
+// this chip, skips the row factor: a_rc -= a_rp (a_pc / a_pp) (column p: -a_rp / a_pp),
+// one FMA per entry and no multiply per row.  `src(r, c)` gives the block's
+// entries (r, c < kb); beyond kb it is padded with the identity.  Flags in *s_flags:
 // DEV_SINGULAR for a non-positive or non-finite pivot, DEV_ILLCOND for a pivot below
-// `floor` (Jacobi-scaled matrices have pivots of at most 1).  The block is read from
-// the matrix (row-major, leading dimension ld), padded with the identity beyond kb;
-// the inverse goes to Dg (NB x NB).
-__global__ void __launch_bounds__(128)
-k_gj_diag_f32(GJBatch bt, int step, const float* __restrict__ base, float* __restrict__ Dg, int* status,
-              float floor) {
-  constexpr int NB = 64, RW = 16;
-  const int b = blockIdx.x;
-  const InvDesc d = bt.d[b];
-  const int k0 = step * NB;
-  if (k0 >= d.n) return;
-  const int kb = min(NB, d.n - k0);
+// `floor` (Jacobi-scaled matrices have pivots of at most 1).  The inverse goes to Db
+// (NB x NB).  Every thread of the first NW warps must call it.
+template <typename T, int NB, int NW, typename Src>
+__device__ __forceinline__ void gj_diag_body(Src src, int kb, T floor, T* __restrict__ Db, int* s_flags,
+                                             T (*prow)[NB], T (*srow)[NB]) {
+  constexpr int RW = NB / NW, CJ = NB / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ float prow[2][NB], srow[2][NB];
-  __shared__ int s_flags;
-  if (threadIdx.x == 0) s_flags = 0;
-  const float* A = base + d.off;
-  float v[RW][2];
+  T v[RW][CJ];
 #pragma unroll
   for (int i = 0; i < RW; ++i) {
     const int r = RW * warp + i;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < CJ; ++j) {
       const int c = lane + 32 * j;
-      v[i][j] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + c] : (r == c ? 1.f : 0.f);
+      v[i][j] = (r < kb && c < kb) ? src(r, c) : (r == c ? T(1) : T(0));
     }
   }
-  __syncthreads();
   for (int p = 0; p < kb; ++p) {
     const int o = p / RW, sl = p % RW, pl = p & 31, pj = p >> 5;
-    float* pr = prow[p & 1];
-    float* sc = srow[p & 1];
+    T* pr = prow[p & 1];
+    T* sc = srow[p & 1];
     if (warp == o) {
-      float vp0 = 0.f, vp1 = 0.f;
+      T vp[CJ];
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) vp[j] = T(0);
 #pragma unroll
       for (int i = 0; i < RW; ++i)
         if (i == sl) {
-          vp0 = v[i][0];
-          vp1 = v[i][1];
+#pragma unroll
+          for (int j = 0; j < CJ; ++j) vp[j] = v[i][j];
         }
-      const float piv = __shfl_sync(0xffffffffu, pj ? vp1 : vp0, pl);
+      T pv = vp[0];
+#pragma unroll
+      for (int j = 1; j < CJ; ++j)
+        if (pj == j) pv = vp[j];
+      const T piv = __shfl_sync(0xffffffffu, pv, pl);
       if (lane == 0) {
-        if (!(piv > 0.f) || !isfinite(piv))
-          s_flags |= DEV_SINGULAR;
+        if (!(piv > T(0)) || !isfinite(piv))
+          *s_flags |= DEV_SINGULAR;
         else if (piv < floor)
-          s_flags |= DEV_ILLCOND;
+          *s_flags |= DEV_ILLCOND;
       }
-      const float inv = 1.f / piv;
-      sc[lane] = lane == p ? inv : vp0 * inv;
-      sc[lane + 32] = lane + 32 == p ? inv : vp1 * inv;
-      pr[lane] = lane == p ? 1.f : vp0;
-      pr[lane + 32] = lane + 32 == p ? 1.f : vp1;
+      const T inv = T(1) / piv;
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) {
+        const int c = lane + 32 * j;
+        sc[c] = c == p ? inv : vp[j] * inv;
+        pr[c] = c == p ? T(1) : vp[j];
+      }
     }
     __syncthreads();
-    const float inv = sc[p];
-    float scl[2], m[2];
+    constexpr bool kRowFactor = sizeof(T) == 4;
+    const T inv = sc[p];
+    T scl[CJ], m[CJ];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < CJ; ++j) {
       scl[j] = sc[lane + 32 * j];
-      m[j] = pr[lane + 32 * j];
+      m[j] = kRowFactor ? pr[lane + 32 * j] : scl[j];
     }
 #pragma unroll
     for (int i = 0; i < RW; ++i) {
       const int r = RW * warp + i;
-      const float l = __shfl_sync(0xffffffffu, pj ? v[i][1] : v[i][0], pl) * inv;
+      T a = v[i][0];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const float base_v = (lane + 32 * j == p) ? 0.f : v[i][j];
-        const float nv = fmaf(-l, m[j], base_v);
+      for (int j = 1; j < CJ; ++j)
+        if (pj == j) a = v[i][j];
+      const T l = kRowFactor ? __shfl_sync(0xffffffffu, a, pl) * inv : __shfl_sync(0xffffffffu, a, pl);
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) {
+        const T base_v = (lane + 32 * j == p) ? T(0) : v[i][j];
+        const T nv = fma(-l, m[j], base_v);
         v[i][j] = r == p ? scl[j] : nv;
       }
     }
   }
-  float* Db = Dg + (int64_t)b * NB * NB;
 #pragma unroll
   for (int i = 0; i < RW; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) Db[(RW * warp + i) * NB + lane + 32 * j] = v[i][j];
-  __syncthreads();
-  if (threadIdx.x == 0 && s_flags) atomicOr(status + b, s_flags);
+    for (int j = 0; j < CJ; ++j) Db[(RW * warp + i) * NB + lane + 32 * j] = v[i][j];
 }
 
-// In-place inverse of the kb x kb (kb <= 32) leading block of one matrix in FP64 by
-// four warps, one per SM sub-partition so that all four FP64 pipes work: warp w keeps
-// rows 8w .. 8w+7, lane l column l.  Per pivot the owner warp scales the pivot row
-// (sc_c = a_pc / a_pp, sc_p = 1 / a_pp) into a double-buffered shared row, one
-// barrier, then every thread updates its 8 entries: a_rc -= a_rp sc_c (r != p, c != p),
-// a_rp = -a_rp sc_p, a_pc = sc_c; a_rp comes from lane p of the same warp by shuffle.
-// Flags as in the FP32 kernel.
-__global__ void __launch_bounds__(128)
-k_gj_diag_f64(GJBatch bt, int step, const double* __restrict__ base, double* __restrict__ Dg, int* status,
-              double floor) {
-  constexpr int NB = 32;
+// D^-1 of the first diagonal block of every matrix (step 0), read from the matrix
+// (row-major, leading dimension ld); later steps fuse it into k_gj_lookahead
+template <typename T, int NB>
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_diag0(GJBatch bt, const T* __restrict__ base, T* __restrict__ Dg, int* status, T floor) {
   const int b = blockIdx.x;
   const InvDesc d = bt.d[b];
-  const int k0 = step * NB;
-  if (k0 >= d.n) return;
-  const int kb = min(NB, d.n - k0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ double row[2][NB];
+  if (d.n <= 0) return;
+  const int kb = min(NB, d.n);
+  __shared__ T prow[2][NB], srow[2][NB];
   __shared__ int s_flags;
   if (threadIdx.x == 0) s_flags = 0;
-  const double* A = base + d.off;
-  double v[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int r = 8 * warp + i;
-    v[i] = (r < kb && lane < kb) ? A[(int64_t)(k0 + r) * d.ld + k0 + lane] : (r == lane ? 1.0 : 0.0);
-  }
   __syncthreads();
-  for (int p = 0; p < kb; ++p) {
-    const int o = p >> 3, sl = p & 7;
-    double* sc = row[p & 1];
-    if (warp == o) {
-      double vp = 0.0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (i == sl) vp = v[i];
-      const double piv = __shfl_sync(0xffffffffu, vp, p);
-      if (lane == 0) {
-        if (!(piv > 0.0) || !isfinite(piv))
-          s_flags |= DEV_SINGULAR;
-        else if (piv < floor)
-          s_flags |= DEV_ILLCOND;
-      }
-      const double inv = 1.0 / piv;
-      sc[lane] = lane == p ? inv : vp * inv;
-    }
-    __syncthreads();
-    // one FMA per entry: column p starts from 0 and takes sc_p
-    const double scl = sc[lane];
-    const double m = lane == p ? sc[p] : scl;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = 8 * warp + i;
-      const double a = __shfl_sync(0xffffffffu, v[i], p);
-      const double base = lane == p ? 0.0 : v[i];
-      const double nv = fma(-a, m, base);
-      v[i] = r == p ? scl : nv;
-    }
-  }
-  double* Db = Dg + (int64_t)b * NB * NB;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) Db[(8 * warp + i) * NB + lane] = v[i];
+  const T* A = base + d.off;
+  gj_diag_body<T, NB, kGJThreads / 32>([&](int r, int c) { return A[(int64_t)r * d.ld + c]; }, kb, floor,
+                                       Dg + (int64_t)b * NB * NB, &s_flags, prow, srow);
   __syncthreads();
   if (threadIdx.x == 0 && s_flags) atomicOr(status + b, s_flags);
 }
@@ -373,48 +333,20 @@ k_gj_panel(GJBatch bt, int step, int cols, const T* __restrict__ base, T* __rest
   }
 }
 
-// Tiles (I <= J) of the next iterate and their mirrors.  Look-ahead split:
-// mode 0 takes the tiles of block row / column K+1 (the next pivot's panel, one CTA
-// per block J, tile (min(K+1,J), max(K+1,J))), mode 1 all the others; the two run
-// on different streams, so the next diagonal inverse and panel overlap the bulk of
-// this step.
+// One tile (I <= J) of the iterate after step K and its mirror: D^-1 (I = J = K),
+// the new row panel Q_KJ (I = K), -P_IK D^-1 (J = K) or A_IJ - P_IK Q_KJ.  With `keep`
+// (the diagonal tile of step K+1, which only that step's inverse reads) the new values
+// go to keep[r][c] instead of the matrix; keep may alias L.
 template <typename T, int NB>
-__global__ void __launch_bounds__(kGJThreads)
-k_gj_update(GJBatch bt, int step, int nblk, int mode, T* __restrict__ base, const T* __restrict__ R,
-            const T* __restrict__ Q, const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
+__device__ __forceinline__ void gj_tile(const InvDesc& d, int K, int I, int J, T* __restrict__ A,
+                                        const T* __restrict__ Db, const T* __restrict__ Rb,
+                                        const T* __restrict__ Qb, T (*L)[NB + 1], T (*Rt)[NB + 1],
+                                        T (*keep)[NB + 1]) {
   constexpr int RA = NB / 16;
-  const int b = blockIdx.y;
-  const InvDesc d = bt.d[b];
-  const int k0 = step * NB;
-  const int nd = step + 1;
-  int I, J;
-  if (mode == 0) {
-    if (nd >= nblk) return;
-    const int t = (int)blockIdx.x;
-    I = min(nd, t);
-    J = max(nd, t);
-  } else {
-    int t = (int)blockIdx.x;
-    I = 0;
-    while (t >= nblk - I) {
-      t -= nblk - I;
-      ++I;
-    }
-    J = I + t;
-    if (I == nd || J == nd) return;
-  }
-  const int K = step;
-  if (k0 >= d.n || J * NB >= d.n) return;
+  const int k0 = K * NB;
   const int kb = min(NB, d.n - k0);
   const int i0 = I * NB, j0 = J * NB, ib = min(NB, d.n - i0), jb = min(NB, d.n - j0);
-  T* A = base + d.off;
-  const T* Db = Dg + (int64_t)b * NB * NB;
-  const T* Rb = R + bt.qoff[b];
-  const T* Qb = Q + bt.qoff[b];
-  __shared__ T L[NB][NB + 1];
-  __shared__ T Rt[NB][NB + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[RA][RA];
   if (I == K && J == K) {
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x)
       A[(int64_t)(k0 + e / kb) * d.ld + k0 + e % kb] = Db[(e / kb) * NB + e % kb];
@@ -441,7 +373,9 @@ k_gj_update(GJBatch bt, int step, int nblk, int mode, T* __restrict__ base, cons
       Rt[r][c] = (r < kb && c < jb) ? Qb[(int64_t)r * d.ld + j0 + c] : T(0);
   }
   __syncthreads();
+  T acc[RA][RA];
   tile_mma<T, NB>(L, Rt, kb, acc);
+  if (keep) __syncthreads();   // keep may alias L (uniform branch)
   // tile value: J == K -> -P_IK D^-1, else A_IJ - P_IK Q_KJ;  mirror sign after this step
   const T sM = (T)gj_sign(I, J, K);
 #pragma unroll
@@ -453,29 +387,66 @@ k_gj_update(GJBatch bt, int step, int nblk, int mode, T* __restrict__ base, cons
       if (r >= ib || c >= jb) continue;
       T* ap = A + (int64_t)(i0 + r) * d.ld + j0 + c;
       const T v = (J == K) ? -acc[a][c4] : (*ap - acc[a][c4]);
-      *ap = v;
-      acc[a][c4] = v;
-      if (I != J) A[(int64_t)(j0 + c) * d.ld + i0 + r] = sM * v;
+      if (keep) {
+        keep[r][c] = v;
+      } else {
+        *ap = v;
+        if (I != J) A[(int64_t)(j0 + c) * d.ld + i0 + r] = sM * v;
+      }
     }
   }
-
 }
 
-// inverse of the diagonal block of step `step` of every matrix into Dg
+// Tiles of step K other than block row / column K+1 (one CTA per tile I <= J).
 template <typename T, int NB>
-static void launch_diag_inverse(const GJBatch& bt, int step, T* base, T* Dg, int* status, T floor, unsigned nb,
-                                cudaStream_t s) {
-  TimedLaunch tl;
-  tl.begin(sizeof(T) == 8 ? "gj_diag_f64" : "gj_diag_f32", s);
-  if constexpr (sizeof(T) == 4) {
-    static_assert(NB == 64, "the FP32 diagonal kernel takes 64 x 64 blocks");
-    k_gj_diag_f32<<<nb, 128, 0, s>>>(bt, step, base, Dg, status, floor);
-  } else {
-    static_assert(NB == 32, "the FP64 diagonal kernel takes 32 x 32 blocks");
-    k_gj_diag_f64<<<nb, 128, 0, s>>>(bt, step, base, Dg, status, floor);
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R, const T* __restrict__ Q,
+            const T* __restrict__ Dg) {
+  const int b = blockIdx.y;
+  const InvDesc d = bt.d[b];
+  const int nd = step + 1;
+  int t = (int)blockIdx.x, I = 0;
+  while (t >= nblk - I) {
+    t -= nblk - I;
+    ++I;
   }
-  UFE_CHECK_LAUNCH();
-  tl.end(s);
+  const int J = I + t;
+  if (I == nd || J == nd) return;
+  if (step * NB >= d.n || J * NB >= d.n) return;
+  __shared__ T L[NB][NB + 1];
+  __shared__ T Rt[NB][NB + 1];
+  gj_tile<T, NB>(d, step, I, J, base + d.off, Dg + (int64_t)b * NB * NB, R + bt.qoff[b], Q + bt.qoff[b], L, Rt,
+                 nullptr);
+}
+
+// Look-ahead launch of step K: the tiles of block row / column K+1 (CTA t takes tile
+// (min(K+1, t), max(K+1, t))); CTA t = K+1 keeps the updated diagonal tile in shared
+// memory and inverts it into Dnext, the next step's D^-1.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kGJThreads)
+k_gj_lookahead(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R,
+               const T* __restrict__ Q, const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
+  const int b = blockIdx.y;
+  const InvDesc d = bt.d[b];
+  const int nd = step + 1;
+  if (nd >= nblk) return;
+  const int t = (int)blockIdx.x;
+  const int I = min(nd, t), J = max(nd, t);
+  if (step * NB >= d.n || J * NB >= d.n) return;
+  __shared__ T L[NB][NB + 1];
+  __shared__ T Rt[NB][NB + 1];
+  __shared__ T prow[2][NB], srow[2][NB];
+  __shared__ int s_flags;
+  const bool diag = t == nd;
+  gj_tile<T, NB>(d, step, I, J, base + d.off, Dg + (int64_t)b * NB * NB, R + bt.qoff[b], Q + bt.qoff[b], L, Rt,
+                 diag ? L : nullptr);
+  if (!diag) return;
+  if (threadIdx.x == 0) s_flags = 0;
+  __syncthreads();
+  gj_diag_body<T, NB, kGJThreads / 32>([&](int r, int c) { return L[r][c]; }, min(NB, d.n - nd * NB), floor,
+                                       Dnext + (int64_t)b * NB * NB, &s_flags, prow, srow);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_flags) atomicOr(status + b, s_flags);
 }
 
 // library-owned side stream of the current device (look-ahead of the Gauss-Jordan steps)
@@ -534,7 +505,13 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const unsigned nb = (unsigned)descs.size();
   const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
   const int pcols = descs.size() >= 16 ? 64 : 16;
-  launch_diag_inverse<T, NB>(bt, 0, base, Dbuf[0], status, floor, nb, s);
+  {
+    TimedLaunch tl;
+    tl.begin(sizeof(T) == 8 ? "gj_diag_f64" : "gj_diag_f32", s);
+    k_gj_diag0<T, NB><<<nb, kGJThreads, 0, s>>>(bt, base, Dbuf[0], status, floor);
+    UFE_CHECK_LAUNCH();
+    tl.end(s);
+  }
   for (int step = 0; step < nblk; ++step) {
     T* Dc = Dbuf[step & 1];
     T* Dn = Dbuf[(step + 1) & 1];
@@ -544,17 +521,19 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
       k_gj_panel<T, NB><<<dim3((nmax + pcols - 1) / pcols, nb), kGJThreads, 0, s>>>(bt, 0, pcols, base, Rc, Qc, Dc);
       UFE_CHECK_LAUNCH();
     }
-    // look-ahead: block row / column K+1, the next diagonal inverse and the next
-    // panel on the side stream while the main stream updates the other tiles
+    // look-ahead: block row / column K+1 with the next diagonal inverse, then the next
+    // panel, on the side stream while the main stream updates the other tiles
     UFE_CUDA(cudaEventRecord(ev[0], s));
     UFE_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
     if (step + 1 < nblk) {
       T* Rn = R.p + ((step + 1) & 1) * nq;
       T* Qn = Q.p + ((step + 1) & 1) * nq;
-      k_gj_update<T, NB><<<dim3(nblk, nb), kGJThreads, 0, s2>>>(bt, step, nblk, 0, base, Rc, Qc, Dc, Dn, status,
-                                                                floor);
+      TimedLaunch ta;
+      ta.begin(sizeof(T) == 8 ? "gj_lookahead_f64" : "gj_lookahead_f32", s2);
+      k_gj_lookahead<T, NB><<<dim3(nblk, nb), kGJThreads, 0, s2>>>(bt, step, nblk, base, Rc, Qc, Dc, Dn, status,
+                                                                   floor);
       UFE_CHECK_LAUNCH();
-      launch_diag_inverse<T, NB>(bt, step + 1, base, Dn, status, floor, nb, s2);
+      ta.end(s2);
       TimedLaunch tp;
       tp.begin(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s2);
       k_gj_panel<T, NB><<<dim3((nmax + pcols - 1) / pcols, nb), kGJThreads, 0, s2>>>(bt, step + 1, pcols, base, Rn, Qn, Dn);
@@ -563,7 +542,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
     }
     TimedLaunch tl;
     tl.begin(sizeof(T) == 8 ? "gj_update_f64" : "gj_update_f32", s);
-    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, 1, base, Rc, Qc, Dc, Dn, status, floor);
+    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, Rc, Qc, Dc);
     UFE_CHECK_LAUNCH();
     tl.end(s);
     UFE_CUDA(cudaEventRecord(ev[1], s2));
