@@ -76,6 +76,12 @@ typedef int ufe_status;
 #define UFE_PREC_FP64  0           /* every local factor and product in FP64 */
 #define UFE_PREC_MIXED 1           /* Jacobi-scaled FP32 local operators; FP64 PCG, weights, coarse */
 
+/* ufe_bddc_opts.coarse_solver: how u_c = A_c^-1 r_c is computed (no paper counterpart;
+ * both are exact FP64 solves of the same coarse problem) */
+#define UFE_COARSE_SOLVER_AUTO  0  /* dense inverse up to 2048 coarse DOFs, else cyclic reduction */
+#define UFE_COARSE_SOLVER_DENSE 1  /* explicit FP64 inverse of A_c (n_coarse up to ~28,000: r_c in one CTA's shared memory) */
+#define UFE_COARSE_SOLVER_CR    2  /* FP64 block cyclic reduction over the z layers of subdomain blocks */
+
 #define UFE_PIN_NONE -1
 #define UFE_PIN_AUTO -2
 
@@ -232,6 +238,7 @@ typedef struct {
   int32_t objects;     /* UFE_OBJECTS_* */
   int32_t coarse;      /* UFE_COARSE_* */
   int32_t precision;   /* UFE_PREC_* */
+  int32_t coarse_solver;   /* UFE_COARSE_SOLVER_* (both solve the coarse problem exactly in FP64) */
 } ufe_bddc_opts;
 
 typedef struct {
@@ -240,15 +247,22 @@ typedef struct {
   int32_t max_local_coarse;       /* largest number of coarse DOFs of one subdomain */
   double setup_ms;                /* device time of ufe_bddc_setup */
   double inverse_flops_local;     /* sum of n^3 over the inverted local matrices (A_II, S', S_c) */
-  double inverse_flops_coarse;    /* n_coarse^3 (symmetric Gauss-Jordan, algorithmic count) */
+  double inverse_flops_coarse;    /* sum of n^3 over the inverted coarse matrices (n_coarse^3 for the
+                                     dense solver, the layer blocks for cyclic reduction) */
   /* storage read by the per-iteration kernels (bytes): A_II^-1, the constrained
    * Neumann operator K, the coarse basis Phi (FP32 in mixed precision), the A_GI and
-   * A_IG stencils (index + value per slot), the FP64 coarse inverse */
+   * A_IG stencils (index + value per slot), the FP64 coarse solver's matrices */
   double bytes_interior_inverse, bytes_neumann, bytes_coarse_basis, bytes_offdiag, bytes_coarse_inverse;
   int64_t interior_slots, interface_slots;   /* sum over subdomains of local interior / interface DOFs */
   int32_t fp64_refactor;   /* mixed precision requested: 1 when a Jacobi-scaled local matrix had an FP32
-                              pivot below 1e-3 (or not positive), so this problem keeps FP64 local
+                              pivot below 1e-3 (or not positive), or the FP32 coarse basis missed
+                              C Phi = I by more than 1e-2, so this problem keeps FP64 local
                               operators (factored and applied in FP64, classical PCG) */
+  int32_t coarse_solver;   /* the coarse solver used: UFE_COARSE_SOLVER_DENSE or _CR */
+  double cphi_error;       /* mixed precision requested: max over subdomains of max |C Phi - I| of the
+                              FP32 coarse basis (Sect. 3.2 defines Phi by C Phi = I); above 1e-2
+                              the problem keeps FP64 local operators (fp64_refactor = 1) */
+  int32_t coarse_layers, coarse_levels;   /* cyclic reduction: non-empty z layers, reduction levels */
 } ufe_bddc_info;
 
 /*
@@ -260,7 +274,9 @@ typedef struct {
  * (Eq. alge-weighting); harmonic extension with local Dirichlet problems.
  * Local operators are formed explicitly: A_II^-1, the constrained Neumann
  * inverse restricted to the interface and the interface rows of the coarse
- * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled and inverted in FP64.
+ * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled in FP64 and solved
+ * exactly in FP64: explicit inverse, or block cyclic reduction over the z layers of
+ * subdomain blocks, in which order A_c is block tridiagonal (opts.coarse_solver).
  * Errors: SINGULAR_LOCAL (e.g. a floating subdomain with no coarse DOF),
  * SINGULAR_COARSE, INVALID_ARG, CUDA, OUT_OF_MEMORY, TIMEOUT.
  */
@@ -291,7 +307,7 @@ ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
  *         pointers are not accepted: staging them would need an allocation).
  *
  * The preconditioner's intermediate vectors live in one file-scope device array
- * of fixed size (622,592 doubles, about 5 MB, held by every device that loads the
+ * of fixed size (688,128 doubles, about 5.5 MB, held by every device that loads the
  * library until the process exits) instead of the buffers ufe_bddc_setup made.
  * Problems beyond its limits -- more than 262,144 interface slots (the sum over
  * subdomains of their interface DOFs, counted per component), 65,536 subdomain coarse slots or 32,768

@@ -378,6 +378,8 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     UFE_REQUIRE(opts->objects == UFE_OBJECTS_STANDARD || opts->objects == UFE_OBJECTS_VARIANT1, UFE_ERR_INVALID_ARG,
                 "bad objects");
     UFE_REQUIRE(opts->coarse >= UFE_COARSE_C && opts->coarse <= UFE_COARSE_CEF, UFE_ERR_INVALID_ARG, "bad coarse");
+    UFE_REQUIRE(opts->coarse_solver >= UFE_COARSE_SOLVER_AUTO && opts->coarse_solver <= UFE_COARSE_SOLVER_CR,
+                UFE_ERR_INVALID_ARG, "bad coarse solver");
     UFE_REQUIRE(opts->precision == UFE_PREC_FP64 || opts->precision == UFE_PREC_MIXED, UFE_ERR_INVALID_ARG,
                 "bad precision");
     *out = nullptr;
@@ -387,6 +389,7 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     B->stream = sys->stream;
     B->opts = *opts;
     B->mixed = opts->precision == UFE_PREC_MIXED;
+    B->coarse_solver = opts->coarse_solver;
     bddc_build(*B);
     UFE_CUDA(cudaStreamSynchronize(B->stream));
     *out = B.release();
@@ -413,6 +416,10 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->interior_slots = B->n_vIloc;
     info->interface_slots = B->n_vGloc;
     info->fp64_refactor = B->fp64_refactor;
+    info->coarse_solver = B->coarse_dense ? UFE_COARSE_SOLVER_DENSE : UFE_COARSE_SOLVER_CR;
+    info->coarse_layers = B->cr.nlayers;
+    info->cphi_error = B->cphi_error;
+    info->coarse_levels = B->cr.nlevels;
   });
 }
 

@@ -696,6 +696,32 @@ __global__ void k_coarse_local(const int32_t* __restrict__ C_ptr, const int64_t*
   }
 }
 
+// accuracy of the coarse basis of each subdomain: E = C Phi (computed from the stored
+// operators) must be the identity (Sect. 3.2: Phi^w is defined by C Phi = I); err[w] =
+// max |E - I|, and a subdomain above tol is flagged DEV_ILLCOND
+template <typename T>
+__global__ void k_cphi_error(const int32_t* __restrict__ C_ptr, const int64_t* __restrict__ oCC,
+                             const T* __restrict__ E, double tol, double* __restrict__ err, int* status) {
+  const int w = blockIdx.x;
+  const int nC = C_ptr[w + 1] - C_ptr[w], ldC = pad4(nC);
+  double m = 0.0;
+  for (int e = threadIdx.x; e < nC * nC; e += blockDim.x) {
+    const int i = e / nC, j = e % nC;
+    const double v = (double)E[oCC[w] + (int64_t)i * ldC + j] - (i == j ? 1.0 : 0.0);
+    m = fmax(m, isfinite(v) ? fabs(v) : INFINITY);
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
+    m = fmax(m, red[0]);
+    err[w] = m;
+    if (!(m <= tol)) atomicOr(status + w, DEV_ILLCOND);
+  }
+}
+
 // coarse matrix: row l gathers A_c^w of every subdomain w in neigh(l), in neigh order
 __global__ void k_coarse_assemble(int64_t n_coarse, int ldc, const int32_t* __restrict__ coarse_rep,
                                   const uint8_t* __restrict__ coarse_nn, const int32_t* __restrict__ neigh,
@@ -879,6 +905,23 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   Acw.alloc(std::max<int64_t>(nCC, 1), s);
   k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
   UFE_CHECK_LAUNCH();
+  if (sizeof(T) == 4) {
+    // FP32 operators: the coarse basis must still satisfy C Phi = I to 1e-2, else this
+    // problem keeps FP64 local operators (S_c = C S'^-1 C^T can be too ill-conditioned
+    // for FP32, e.g. the rotation rows of small elasticity objects)
+    g.clear();
+    for (int w = 0; w < ns; ++w)
+      g.push_back({B.h_nC[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oCG[w], oGC[w], oCC[w]});
+    batched_gemm<T>(false, false, g, Cs.p, GC.p, Sc.p, T(1), T(0), s);
+    DBuf<double> err;
+    err.alloc(ns, s);
+    k_cphi_error<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, 1e-2, err.p, status.p);
+    UFE_CHECK_LAUNCH();
+    const std::vector<double> he = to_host(err.p, ns, s);
+    B.cphi_error = 0.0;
+    for (double v : he) B.cphi_error = std::max(B.cphi_error, v);
+    check("the coarse basis (C Phi = I)");
+  }
   // 11. the operators stay in the scaled variables: the iterations apply
   //     A_II^-1 = S_I Ahat_II^-1 S_I, K = S_G Khat S_G and Phi = S_G Phihat with the FP64
   //     scale vectors, so the stored entries are O(1) whatever the cut fractions (the
@@ -1044,7 +1087,6 @@ void bddc_build(Bddc& B) {
   B.inv_flops_local = 0.0;
   for (int w = 0; w < ns; ++w)
     B.inv_flops_local += std::pow((double)B.h_nI[w], 3) + std::pow((double)B.h_nG[w], 3) + std::pow((double)B.h_nC[w], 3);
-  B.inv_flops_coarse = std::pow((double)B.n_coarse, 3);
 
   // structural singularity: a floating subdomain (no constrained node) without coarse DOFs
   {
@@ -1087,7 +1129,6 @@ void bddc_build(Bddc& B) {
     B.bytes_GG = tm * nGG;
     B.bytes_GC = tm * nGC;
     B.bytes_off = 12.0 * 27 * NC * (double)(B.n_vGloc + B.n_vIloc);
-    B.bytes_Ac = 8.0 * (double)nco * pad4((int)std::max<int64_t>(nco, 1));
   }
 
   // ---- local matrices, scales, weights
@@ -1166,24 +1207,27 @@ void bddc_build(Bddc& B) {
   ph_fac.end(s);
   TimedLaunch ph_co;
   ph_co.begin("phase_coarse", s);
-  // ---- coarse matrix (FP64), assembled and inverted
-  B.ldc = pad4((int)std::max<int64_t>(nco, 1));
-  B.Ac_inv.alloc((size_t)std::max<int64_t>(nco, 1) * B.ldc, s);
-  B.Ac_inv.zero();
+  // ---- coarse matrix (FP64), assembled densely, then inverted (small problems) or
+  // factored by block cyclic reduction over the z layers of subdomain blocks (coarse.cu)
   if (nco) {
+    const int ldc = pad4((int)nco);
+    DBuf<double> Ac;
+    Ac.alloc((size_t)nco * ldc, s);
+    Ac.zero();
     DBuf<int64_t> dCC;
     upload(dCC, oCC);
-    k_coarse_assemble<<<(unsigned)nco, 128, 0, s>>>(nco, B.ldc, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p,
-                                                    B.C_ptr.p, B.C_list.p, dCC.p, Acw.p, B.Ac_inv.p);
+    k_coarse_assemble<<<(unsigned)nco, 128, 0, s>>>(nco, ldc, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p,
+                                                    B.C_ptr.p, B.C_list.p, dCC.p, Acw.p, Ac.p);
     UFE_CHECK_LAUNCH();
-    k_symmetrize<<<grid_for(nco * nco, T), T, 0, s>>>(B.Ac_inv.p, (int)nco, B.ldc);
+    k_symmetrize<<<grid_for(nco * nco, T), T, 0, s>>>(Ac.p, (int)nco, ldc);
     UFE_CHECK_LAUNCH();
-    DBuf<int> st;
-    st.alloc(1, s);
-    st.zero();
-    large_inverse<double>(B.Ac_inv.p, (int)nco, B.ldc, st.p, s);
-    UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
+    coarse_setup(B, Ac, ldc, s);
+  } else {
+    DBuf<double> none;
+    coarse_setup(B, none, 4, s);
   }
+  B.bytes_Ac = B.cr.bytes;
+  B.inv_flops_coarse = B.cr.inv_flops;
 
   ph_co.end(s);
   // ---- solver work space

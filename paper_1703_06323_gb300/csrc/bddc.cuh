@@ -65,6 +65,37 @@ struct PcgScalars {
   unsigned int counter[8];   // last-block-done counters per kernel
 };
 
+// coarse solver (coarse.cu): block cyclic reduction of the block-tridiagonal coarse
+// matrix over the z layers of subdomain blocks; every solve step is a list of tasks
+//   V[y + i] = (base >= 0 ? V[base + i] : 0) + sum_t sign_t (M_t V[x_t + .])_i
+struct CoarseTerm {
+  int64_t off;   // matrix offset in the store (row-major, leading dimension ld)
+  int ld, cols;
+  int64_t x;     // input offset in the work vector
+  double sign;
+};
+struct CoarseTask {
+  int64_t y, base;   // output / base offsets in the work vector (base -1: none)
+  int64_t row0;      // first row of the task within its launch
+  int n, term0, nterm;
+};
+struct CoarseStep {
+  int task0, ntask;
+  int64_t rows;
+};
+struct CoarseCR {
+  int64_t n = 0;               // coarse DOFs
+  int nlayers = 0, nlevels = 0;
+  DBuf<int32_t> perm;          // CR position -> coarse DOF
+  DBuf<double> store;          // X, T1, T2, W1, W2 and coupling blocks
+  DBuf<CoarseTask> tasks;
+  DBuf<CoarseTerm> terms;
+  std::vector<CoarseStep> steps;
+  DBuf<double> work;           // r (CR order) then u, 2 n
+  double bytes = 0.0;          // matrix bytes one solve reads
+  double inv_flops = 0.0;      // sum of n_j^3 over the inverted layer blocks
+};
+
 struct Bddc {
   System* sys = nullptr;
   Mesh* mesh = nullptr;
@@ -98,8 +129,11 @@ struct Bddc {
   DBuf<double> sI, sG;          // Jacobi scales of the local slots (operators stored scaled)
   DBuf<int32_t> gi_k, ig_k;     // A_GI / A_IG in ELL form (local indices)
   DBuf<double> gi_v, ig_v;
-  DBuf<double> Ac_inv;          // n_coarse x ldc, FP64
+  int coarse_solver = 0;        // requested UFE_COARSE_SOLVER_*
+  bool coarse_dense = true;     // resolved: explicit inverse (else cyclic reduction)
+  DBuf<double> Ac_inv;          // dense: n_coarse x ldc, FP64
   int ldc = 0;
+  CoarseCR cr;                  // cyclic reduction over the z layers of subdomain blocks
 
   // solver work space
   DBuf<double> tG, vw, gC, uc;
@@ -120,12 +154,18 @@ struct Bddc {
   double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
   double bytes_II = 0.0, bytes_GG = 0.0, bytes_GC = 0.0, bytes_off = 0.0, bytes_Ac = 0.0;
   int fp64_refactor = 0;                // mixed precision requested, FP64 local operators kept (FP32 too ill-conditioned)
+  double cphi_error = 0.0;              // mixed: max |C Phi - I| of the FP32 operators
 
   SubMeta meta() const;
   ~Bddc();
 };
 
 void bddc_build(Bddc& B);
+// coarse solver: set-up from the assembled dense A_c (n_coarse x ldc, symmetric; the
+// dense solver takes ownership of the buffer), and u_c = A_c^-1 r_c with r_c gathered
+// from the subdomain parts gC (work: 2 n_coarse doubles)
+void coarse_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s);
+void coarse_solve(const Bddc& B, const double* gC, double* uc, double* work, const PcgScalars* sc, cudaStream_t s);
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev);
 void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);

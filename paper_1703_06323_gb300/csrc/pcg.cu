@@ -716,44 +716,6 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   cl.sync();
 }
 
-// K5: r_c gathered from the subdomain parts, u_c = A_c^-1 r_c (FP64)
-__global__ void k_coarse_solve(int64_t nco, int ldc, const double* __restrict__ Ainv, const int32_t* __restrict__ cpos,
-                               const uint8_t* __restrict__ cnn, const double* __restrict__ gC, double* __restrict__ uc,
-                               const PcgScalars* sc) {
-  if (sc && sc->done) return;
-  extern __shared__ __align__(16) char smem[];
-  double* rc = reinterpret_cast<double*>(smem);
-  for (int64_t l = threadIdx.x; l < ldc; l += blockDim.x) {
-    double s = 0.0;
-    if (l < nco)
-      for (int k = 0; k < cnn[l]; ++k) s += gC[cpos[l * 8 + k]];
-    rc[l] = s;
-  }
-  __syncthreads();
-  // one warp per row; eight independent 16-byte loads per lane in flight
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  constexpr int U = 8;
-  for (int64_t row = (int64_t)blockIdx.x * nw + wid; row < nco; row += (int64_t)gridDim.x * nw) {
-    const double* Ar = Ainv + row * ldc;
-    double s = 0.0;
-    for (int c0 = lane * 2; c0 < ldc; c0 += 64 * U) {
-      double2 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = c0 + 64 * u;
-        v[u] = c < ldc ? *reinterpret_cast<const double2*>(Ar + c) : make_double2(0.0, 0.0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = c0 + 64 * u;
-        if (c < ldc) s += v[u].x * rc[c] + v[u].y * rc[c + 1];
-      }
-    }
-    s = warp_sum(s);
-    if (lane == 0) uc[row] = s;
-  }
-}
-
 // K6: coarse prolongation, vw += w Phi u_c^w on the interface rows of w
 template <typename TM, int NC>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
@@ -973,11 +935,8 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   UFE_CHECK_LAUNCH();
   t4.end(s);
   if (B.n_coarse > 0) {
-    const size_t csm = (size_t)B.ldc * 8;
-    const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
     t5.begin("coarse_solve", s);
-    k_coarse_solve<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, B.gC.p, B.uc.p, sc);
-    UFE_CHECK_LAUNCH();
+    coarse_solve(B, B.gC.p, B.uc.p, B.cr.work.p, sc, s);
     t5.end(s);
     t6.begin("prec_prolong", s);
     k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
@@ -1025,8 +984,6 @@ static void set_smem_limits(Bddc& B) {
   sub_launch(B, 4, &sf);
   UFE_REQUIRE(std::max(sd, sf) <= (size_t)kMaxDynSmem, UFE_ERR_UNSUPPORTED,
               "local interface / interior sizes exceed one CTA's shared memory");
-  UFE_REQUIRE((size_t)B.ldc * 8 <= (size_t)kMaxDynSmem, UFE_ERR_UNSUPPORTED,
-              "coarse problem larger than one CTA's shared memory");
   std::lock_guard<std::mutex> lock(mu);
   if (done[dev]) return;
   int optin = 0;
@@ -1036,7 +993,6 @@ static void set_smem_limits(Bddc& B) {
   set_smem_limits_for<float, 1>(optin);
   set_smem_limits_for<double, 3>(optin);
   set_smem_limits_for<float, 3>(optin);
-  raise_smem_limit(k_coarse_solve, optin);
   done[dev] = true;
 }
 
@@ -1283,11 +1239,12 @@ ufe_status pcg_solve_batched(int n, Bddc* const* Bs, const double* const* b_dev,
 // of the preconditioner live in one file-scope device array instead of the
 // buffers ufe_bddc_setup allocates.  Limits: 262144 interface slots (sum over
 // subdomains of their interface DOFs), 65536 subdomain coarse slots, 32768
-// coarse DOFs -- 622592 doubles, about 5 MB held by every device that loads the
+// coarse DOFs -- 688128 doubles, about 5.5 MB held by every device that loads the
 // library.  All calls share the array; calls that overlap on the GPU race.
 // ---------------------------------------------------------------------------
 constexpr int64_t kNoAllocG = 262144, kNoAllocC = 65536, kNoAllocU = 32768;
-static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocG + kNoAllocC + kNoAllocU];
+// interface vectors, subdomain coarse parts, u_c and the coarse solver's work vector (2 n_c)
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocG + kNoAllocC + 3 * kNoAllocU];
 
 // device address of the array for the current device, looked up once per device
 static double* noalloc_scratch_ptr() {
@@ -1321,10 +1278,7 @@ static void launch_preconditioner_static(Bddc& B, const double* r, double* z, do
   k_prec_neumann<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
   UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
-    const size_t csm = (size_t)B.ldc * 8;
-    const unsigned cgr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
-    k_coarse_solve<<<cgr, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, nullptr);
-    UFE_CHECK_LAUNCH();
+    coarse_solve(B, gC, uc, uc + kNoAllocU, nullptr, s);
     k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
     UFE_CHECK_LAUNCH();
   }

@@ -35,7 +35,19 @@ def small_problems():
         "slab_sliver": _slab(1e-5),
         "two_pieces": islands,      # floating islands: integer parity, then SINGULAR_LOCAL
         "u_shape": _u_shape(),      # block 0 holds two separate subdomains
+        "tower": _tower(),          # 8 z layers of blocks: multi-level coarse cyclic reduction
     }
+
+
+def _tower():
+    """A wavy cylinder along z through 8 layers of 4^3-cell blocks (pure Neumann, pinned)."""
+    cells = (8, 8, 32)
+    X, Y, Z = inputs.node_coords((0, 0, 0), (1, 1, 4), cells)
+    r = 0.33 + 0.06 * np.sin(2 * np.pi * Z / 1.3)
+    phi = np.sqrt((X - 0.5) ** 2 + (Y - 0.47) ** 2) - r
+    f = np.random.default_rng(7).uniform(-1, 1, X.size)
+    return inputs.Problem(name="tower", box_lo=np.zeros(3), box_hi=np.array([1.0, 1.0, 4.0]), cells=cells,
+                          sub_cells=(4, 4, 4), phi=phi, f=f, dirichlet_face_mask=0, pin_node=inputs.PIN_AUTO)
 
 
 def _box_phi(X, Y, Z, lo, hi):
@@ -105,7 +117,22 @@ def elastic_problems():
                                      name="el_ragged"),
         "el_patch": inputs.elastic_patch(),
         "el_spheres16": inputs.elastic_spheres(seed=0, n=16, sub=8),
+        "el_wall": _elastic_wall(),
     }
+
+
+def _elastic_wall():
+    """A slab below a wavy surface y = 0.55 + 0.2 sin(pi z), clamped on x = 0, through 4
+    z layers of blocks (multi-level coarse cyclic reduction with rotation rows)."""
+    cells = (8, 8, 16)
+    X, Y, Z = inputs.node_coords((0, 0, 0), (1, 1, 2), cells)
+    phi = Y - (0.55 + 0.2 * np.sin(np.pi * Z))
+    f = np.zeros((X.size, 3))
+    f[:, 2] = -1.0
+    return inputs.Problem(name="el_wall", box_lo=np.zeros(3), box_hi=np.array([1.0, 1.0, 2.0]), cells=cells,
+                          sub_cells=(4, 4, 4), phi=phi, f=f, q=None, dirichlet_face_mask=inputs.FACE_XLO,
+                          pin_node=inputs.PIN_NONE, dirichlet_values=np.zeros((X.size, 3)), ncomp=3,
+                          lame=(1.0, 0.3))
 
 
 class ElasticOracleRun(OracleRun):

@@ -175,6 +175,34 @@ def test_preconditioner_mixed(ufe, name):
     assert energy_error(orc.sys.A, z, ref) <= 1e-3
 
 
+@pytest.mark.parametrize("name", ["tower", "sphere_ragged", "plane"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_coarse_cyclic_reduction(ufe, name, precision):
+    """The block cyclic reduction coarse solver (forced here; the default takes it above
+    2048 coarse DOFs) solves the same coarse problem as the dense inverse: M r agrees
+    with the dense-solver preconditioner to rounding, with the oracle as in the
+    preconditioner tests, and PCG takes the same number of iterations."""
+    orc = oracle_run(name)
+    r = np.random.default_rng(4).normal(size=orc.mesh.n_dof)
+    ref = orc.bddc().apply(r)
+    out = {}
+    for cs in ("cr", "dense"):
+        with _solver(ufe, orc.p, precision=precision, coarse_solver=cs) as S:
+            bi = S.bddc_info
+            assert bi["coarse_solver"] == (ufe.COARSE_SOLVER_CR if cs == "cr" else ufe.COARSE_SOLVER_DENSE)
+            z = S.precondition(r)
+            x, info = S.solve(rtol=1e-8)
+            out[cs] = (z, x, info, bi)
+    zc, xc, ic, bc = out["cr"]
+    zd, xd, idn, _ = out["dense"]
+    nl = {"tower": 8, "sphere_ragged": 2, "plane": 2}[name]
+    assert bc["coarse_layers"] == nl and bc["coarse_levels"] == int(np.ceil(np.log2(nl)))
+    assert energy_error(orc.sys.A, zc, zd) <= (1e-11 if precision == "fp64" else 1e-6)
+    assert energy_error(orc.sys.A, zc, ref) <= (1e-9 if precision == "fp64" else 1e-3)
+    assert ic["converged"] == 1 and ic["true_rel_residual"] <= 1.5e-8
+    assert abs(ic["iterations"] - idn["iterations"]) <= (0 if precision == "fp64" else 1)
+
+
 @pytest.mark.parametrize("name", SOLVABLE)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_pcg_solution(ufe, name, precision):
