@@ -225,6 +225,19 @@ ufe_status ufe_system_get_info(const ufe_system* sys, int32_t* ncomp, int64_t* n
 ufe_status ufe_system_get_rhs(const ufe_system* sys, double* b, int mem);
 /* y = A x over the free DOFs (element-by-element apply); x, y of length n. */
 ufe_status ufe_system_apply(const ufe_system* sys, const double* x, double* y, int mem);
+/*
+ * ufe_system_set_kappa -- replace the per-cell coefficient of a Poisson system
+ * (A = sum_e kappa_e K_e) and rebuild its right-hand side (the Dirichlet lifting
+ * depends on kappa).  No paper counterpart: an inverse-problem step (finite
+ * differences, line searches) that keeps the set-up.  A preconditioner built on this
+ * system stays valid and keeps the coefficient it was built with: ufe_pcg_solve still
+ * converges to the solution of the updated system (BDDC of the old coefficient as
+ * the preconditioner).
+ *  kappa_cells  n_cells doubles (> 0 on active cells); the system must have been
+ *               assembled with a coefficient (INVALID_ARG otherwise).
+ * Errors: INVALID_ARG, UNSUPPORTED (elasticity), CUDA.
+ */
+ufe_status ufe_system_set_kappa(ufe_system* sys, const double* kappa_cells, int mem);
 /* Cut-cell data in cut-cell order (ascending cell id): cut_cells n_cut int32,
  * K n_cut*ne*ne doubles (ne x ne row-major with ne = 8 ncomp, element DOF
  * ncomp a + c, vertex a = x + 2y + 4z, without kappa / E_scale), load n_cut*ne

@@ -280,6 +280,22 @@ ufe_status ufe_assemble(ufe_mesh* m, const double* kappa, const double* f, const
   });
 }
 
+ufe_status ufe_system_set_kappa(ufe_system* sys, const double* kappa, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && kappa, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(sys->ncomp == 1, UFE_ERR_UNSUPPORTED, "ufe_system_set_kappa: Poisson systems only");
+    check_mem(mem);
+    cudaStream_t s = sys->stream;
+    // the coefficient buffer must exist already: solves captured in CUDA graphs hold its address
+    UFE_REQUIRE(sys->has_kappa, UFE_ERR_INVALID_ARG,
+                "ufe_system_set_kappa: the system was assembled without a per-cell coefficient");
+    const int64_t nc = sys->mesh->g.n_cells();
+    copy_in(sys->kappa.p, kappa, nc * 8, mem, s);
+    system_rebuild_rhs(*sys);
+    UFE_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 ufe_status ufe_assemble_elastic(ufe_mesh* m, double E, double nu, const double* E_scale, const double* f,
                                 const double* stress, const double* gval, int mem, ufe_system** out) {
   return guarded([&] {

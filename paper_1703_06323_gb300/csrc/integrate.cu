@@ -432,10 +432,24 @@ void system_build(System& sys, const double* kappa, const double* f, const doubl
     UFE_CUDA(cudaMemcpyAsync(sys.gnode.p, gval, m.g.n_nodes() * 8, cudaMemcpyDeviceToDevice, s));
   else
     sys.gnode.zero();
+  sys.fnode.alloc(m.g.n_nodes(), s);
+  if (f)
+    UFE_CUDA(cudaMemcpyAsync(sys.fnode.p, f, m.g.n_nodes() * 8, cudaMemcpyDeviceToDevice, s));
+  else
+    sys.fnode.zero();
   sys.b.alloc(m.n_dof, s);
   k_rhs<<<grid_for(m.n_dof, 128), 128, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p,
                                                m.cut_index.p, sys.K_cut.p, sys.load_cut.p, kappa, f, gval,
                                                m.node_flags.p, sys.b.p);
+  UFE_CHECK_LAUNCH();
+}
+
+void system_rebuild_rhs(System& sys) {
+  Mesh& m = *sys.mesh;
+  k_rhs<<<grid_for(m.n_dof, 128), 128, 0, sys.stream>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p,
+                                                        m.cell_type.p, m.cut_index.p, sys.K_cut.p, sys.load_cut.p,
+                                                        sys.has_kappa ? sys.kappa.p : nullptr, sys.fnode.p,
+                                                        sys.gnode.p, m.node_flags.p, sys.b.p);
   UFE_CHECK_LAUNCH();
 }
 

@@ -184,6 +184,7 @@ struct System {
   DBuf<double> eta;         // n_cut
   DBuf<double> b;           // ncomp * n_dof
   DBuf<double> gnode;       // ncomp * n_nodes: Dirichlet values read at constrained nodes (zeros if none given)
+  DBuf<double> fnode;       // Poisson: nodal source (zeros if none given), kept to rebuild b after a kappa update
   int64_t n_vec() const { return (int64_t)ncomp * mesh->n_dof; }
 };
 
@@ -199,6 +200,8 @@ int64_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets_out, cuda
 
 void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node);
 void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* g);
+// Poisson: b rebuilt from the kept source, cut loads and Dirichlet values after sys.kappa changed
+void system_rebuild_rhs(System& sys);
 // elasticity: f 3 values per node, sigma 9 per node (may be null), g 3 per node (may be null)
 void system_build_elastic(System& sys, const double* kappa, const double* f, const double* sigma, const double* g);
 void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStream_t s);

@@ -252,12 +252,16 @@ def random_field_kappa(cells, seed=0, sigma=1.0, ell=0.1, n_features=1024):
     w = rng.normal(scale=1.0 / ell, size=(n_features, 3))
     b = rng.uniform(0.0, 2.0 * np.pi, n_features)
     a = rng.normal(size=n_features)
-    X, Y, Z = cell_centres((0, 0, 0), (1, 1, 1), cells)
-    P = np.stack([X, Y, Z], axis=1)
-    g = np.zeros(P.shape[0])
-    for s in range(0, n_features, 128):
-        g += np.cos(P @ w[s:s + 128].T + b[s:s + 128]) @ a[s:s + 128]
-    g *= sigma * np.sqrt(2.0 / n_features)
+    # cell centres form a tensor grid, so cos(w.x + b) = Re(e^{ib} e^{i w_x x} e^{i w_y y} e^{i w_z z})
+    # and the feature sum is a product of three 1-D factors contracted over the features
+    nx, ny, nz = cells
+    cx, cy, cz = ((np.arange(n) + 0.5) / n for n in (nx, ny, nz))
+    Ex, Ey, Ez = (np.exp(1j * np.outer(w[:, d], c)) for d, c in enumerate((cx, cy, cz)))
+    T = (a * np.exp(1j * b))[:, None] * Ez                     # features x nz
+    g = np.empty((nz, ny, nx))
+    for k in range(nz):
+        g[k] = ((Ey * T[:, k:k + 1]).T @ Ex).real               # (ny x M) (M x nx)
+    g = g.ravel() * (sigma * np.sqrt(2.0 / n_features))
     return np.exp(g)
 
 

@@ -97,6 +97,7 @@ def _load():
         "ufe_system_get_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
         "ufe_system_get_rhs": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ufe_system_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "ufe_system_set_kappa": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ufe_system_get_cut_data": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int]),
         "ufe_system_destroy": (None, [P]),
         "ufe_bddc_setup": (ctypes.c_int, [P, ctypes.POINTER(BddcOpts), ctypes.POINTER(P)]),
@@ -123,7 +124,8 @@ LIB = _load()
 EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_enable", "ufe_timing_reset",
             "ufe_timing_get", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
-            "ufe_assemble", "ufe_assemble_elastic", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_get_cut_data",
+            "ufe_assemble", "ufe_assemble_elastic", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_set_kappa",
+            "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
             "ufe_bddc_apply_noalloc",
             "ufe_bddc_destroy", "ufe_pcg_solve", "ufe_pcg_solve_batched", "ufe_adjoint")
@@ -281,6 +283,11 @@ def ufe_system_apply(system, x, y=None):
     yp = _ptr(y, np.float64)
     _check(LIB.ufe_system_apply(system, xp[0], yp[0], _mem_of(xp, yp)))
     return y
+
+
+def ufe_system_set_kappa(system, kappa):
+    kp = _ptr(kappa, np.float64)
+    _check(LIB.ufe_system_set_kappa(system, kp[0], kp[1]))
 
 
 def ufe_system_get_cut_data(system, n_cut):
