@@ -5,10 +5,12 @@
 // cut out with the edge crossing points.  1 or 3 inside vertices leave a tet or a
 // prism, 2 leave a prism; prisms are split into 3 tets.  The boundary facet is a
 // triangle or a planar quad (2 triangles) with normal grad(phi)/|grad(phi)|.
-// The stiffness integrand grad N_a . grad N_b has degree <= 4 and uses the degree-5
-// Grundmann-Moeller tet rule (15 points); the source load f_h N_a has degree <= 6
-// and uses the degree-7 rule (35 points); facets use the degree-7 triangle rule.
-// Every integral is therefore exact up to rounding.  The rules are generated on the host from the published
+// Poisson: every volume integrand (grad N_a . grad N_b, degree <= 4, and f_h N_a,
+// degree <= 6) is a combination of the 27 separable moments
+// int q_i(x) q_j(y) q_k(z), q in {(1-t)^2, t(1-t), t^2}, accumulated with the degree-7
+// Grundmann-Moeller tet rule (35 points); elasticity uses the degree-5 rule (15 points)
+// for its degree-4 gradient products; facets use the degree-7 triangle rule.  Every
+// integral is therefore exact up to rounding.  The rules are generated on the host from the published
 // formula of Grundmann & Moeller (1978) and kept in constant memory.
 //
 // One warp per cut cell (see k_integrate_cut).
@@ -86,9 +88,6 @@ void ensure_constants() {
   done.push_back(dev);
 }
 
-// accumulator layout: [0, 36) packed upper triangle of K (unit cube, a <= b),
-// [36, 44) load, [44] volume fraction
-constexpr int kAcc = 45;
 
 struct Vec3 {
   double x, y, z;
@@ -193,7 +192,6 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
                 const double* __restrict__ f, const double* __restrict__ q, double* __restrict__ K_cut,
                 double* __restrict__ load_cut, double* __restrict__ eta) {
   __shared__ double s_tet[kTetPts * 5];   // 4 barycentric + weight
-  __shared__ double s_tet5[kTet5Pts * 5];
   __shared__ double s_tri[kTriPts * 4];
   __shared__ CellGeom geo[kWarpsPerBlock];
   __shared__ double s_f[kWarpsPerBlock][8];
@@ -201,10 +199,6 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
   for (int e = threadIdx.x; e < kTetPts; e += blockDim.x) {
     for (int c = 0; c < 4; ++c) s_tet[e * 5 + c] = c_tet_bary[e * 4 + c];
     s_tet[e * 5 + 4] = c_tet_w[e];
-  }
-  for (int e = threadIdx.x; e < kTet5Pts; e += blockDim.x) {
-    for (int c = 0; c < 4; ++c) s_tet5[e * 5 + c] = c_tet5_bary[e * 4 + c];
-    s_tet5[e * 5 + 4] = c_tet5_w[e];
   }
   for (int e = threadIdx.x; e < kTriPts; e += blockDim.x) {
     for (int c = 0; c < 3; ++c) s_tri[e * 4 + c] = c_tri_bary[e * 3 + c];
@@ -259,22 +253,23 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
     G.n_tri = (q != nullptr) ? tot_r : 0;
   }
   __syncthreads();
-  double acc[kAcc];
+  // Every integrand is a polynomial in the separable basis q_i(x) q_j(y) q_k(z),
+  // q_0 = (1-t)^2, q_1 = t (1-t), q_2 = t^2 (unit-cube coordinates), so the lanes
+  // accumulate the 27 moments M_ijk = int q_i(x) q_j(y) q_k(z) over the sub-tets
+  // (degree 6: the 35-point rule is exact) and, with a flux, the 8 facet loads;
+  // K, the source load and the volume fraction follow from the moments at the end.
+  constexpr int kMom = 27, kVals = kMom + 8;
+  double acc[kVals];
 #pragma unroll
-  for (int e = 0; e < kAcc; ++e) acc[e] = 0.0;
+  for (int e = 0; e < kVals; ++e) acc[e] = 0.0;
+  const double h = g.h, h3 = h * h * h, h2 = h * h;
   if (valid) {
-    const double h = g.h, h3 = h * h * h, h2 = h * h;
-    // work items: stiffness + volume (15-point rule), source load (35-point rule), facets
-    const int n_k = G.n_tet * kTet5Pts;
-    const int n_l = (f != nullptr) ? G.n_tet * kTetPts : 0;
-    const int n_all = n_k + n_l + G.n_tri * kTriPts;
+    const int n_v = G.n_tet * kTetPts;
+    const int n_all = n_v + G.n_tri * kTriPts;
     for (int it = lane; it < n_all; it += 32) {
-      if (it < n_k || it < n_k + n_l) {
-        const bool stiff = it < n_k;
-        const int e = stiff ? it : it - n_k;
-        const int np = stiff ? kTet5Pts : kTetPts;
-        const double* T = G.tet[e / np];
-        const double* R = (stiff ? s_tet5 : s_tet) + (e % np) * 5;
+      if (it < n_v) {
+        const double* T = G.tet[it / kTetPts];
+        const double* R = s_tet + (it % kTetPts) * 5;
         const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
         const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
         const double wx = T[9] - T[0], wy = T[10] - T[1], wz = T[11] - T[2];
@@ -284,27 +279,20 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
         const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7] + R[3] * T[10];
         const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8] + R[3] * T[11];
         const double wq = R[4] * vol;
-        if (stiff) {
-          double N[8], Gd[8][3];
-          q1_shape_grad(px, py, pz, N, Gd);
-          int k = 0;
+        const double mx = 1.0 - px, my = 1.0 - py, mz = 1.0 - pz;
+        const double qx[3] = {mx * mx, px * mx, px * px};
+        const double qy[3] = {my * my, py * my, py * py};
+        const double qz[3] = {wq * mz * mz, wq * pz * mz, wq * pz * pz};
 #pragma unroll
-          for (int a = 0; a < 8; ++a)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int b = a; b < 8; ++b, ++k)
-              acc[k] += wq * (Gd[a][0] * Gd[b][0] + Gd[a][1] * Gd[b][1] + Gd[a][2] * Gd[b][2]);
-          acc[44] += wq;
-        } else {
-          double N[8];
-          q1_shape(px, py, pz, N);
-          double fh = 0.0;
+          for (int j = 0; j < 3; ++j) {
+            const double xy = qx[i] * qy[j];
 #pragma unroll
-          for (int a = 0; a < 8; ++a) fh += N[a] * s_f[warp][a];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) acc[36 + a] += wq * fh * N[a] * h3;
-        }
+            for (int k = 0; k < 3; ++k) acc[9 * i + 3 * j + k] = fma(xy, qz[k], acc[9 * i + 3 * j + k]);
+          }
       } else {
-        const int r = it - n_k - n_l;
+        const int r = it - n_v;
         const double* T = G.tri[r / kTriPts];
         const double* R = s_tri + (r % kTriPts) * 4;
         const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
@@ -317,36 +305,78 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
         const double wq = R[3] * area;
         double N[8];
         q1_shape(px, py, pz, N);
-        double qx = 0, qy = 0, qz = 0;
+        double qxv = 0, qyv = 0, qzv = 0;
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-          qx += N[a] * s_q[warp][a][0];
-          qy += N[a] * s_q[warp][a][1];
-          qz += N[a] * s_q[warp][a][2];
+          qxv += N[a] * s_q[warp][a][0];
+          qyv += N[a] * s_q[warp][a][1];
+          qzv += N[a] * s_q[warp][a][2];
         }
-        const double gnv = qx * T[9] + qy * T[10] + qz * T[11];
+        const double gnv = qxv * T[9] + qyv * T[10] + qzv * T[11];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) acc[36 + a] += wq * gnv * N[a] * h2;
+        for (int a = 0; a < 8; ++a) acc[kMom + a] += wq * gnv * N[a] * h2;
       }
     }
   }
-  // warp reduction (fixed tree) and output
+  // moments: reduce-scatter over the warp (fixed butterfly), after the five levels
+  // lane l holds the warp total of moment l (27 .. 31 are zero padding)
+  double v[32];
 #pragma unroll
-  for (int e = 0; e < kAcc; ++e) {
-    double v = acc[e];
+  for (int e = 0; e < 32; ++e) v[e] = e < kMom ? acc[e] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    acc[e] = v;
+  for (int o = 16, w = 16; o > 0; o >>= 1, w >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const double send = up ? v[i] : v[i + w];
+      const double keep = up ? v[i + w] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
   }
-  if (valid && lane == 0) {
-    int e = 0;
-    for (int a = 0; a < 8; ++a)
-      for (int b = a; b < 8; ++b, ++e) {
-        K_cut[kc * 64 + a * 8 + b] = acc[e] * g.h;
-        K_cut[kc * 64 + b * 8 + a] = acc[e] * g.h;
+  // facet loads (with a flux only): plain butterfly sums, every lane gets all eight
+  double fl = 0.0;
+  if (q != nullptr) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      double t = acc[kMom + a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == a) fl = t;
+    }
+  }
+  __shared__ double s_val[kWarpsPerBlock][32];
+  s_val[warp][lane] = v[0];
+  __syncwarp();
+  if (valid) {
+    const double* M = s_val[warp];
+    // K_ab = h sum_d s(a_d) s(b_d) int prod_{d' != d} l_a l_b, with l_a l_b = q_{a + b}
+    // and int q_j(y) q_k(z) = sum_i c_i M_ijk, c = (1, 2, 1) (q_0 + 2 q_1 + q_2 = 1)
+    for (int e = lane; e < 64; e += 32) {
+      const int a = e >> 3, bb = e & 7;
+      const int sx = (a & 1) + (bb & 1), sy = ((a >> 1) & 1) + ((bb >> 1) & 1), sz = (a >> 2) + (bb >> 2);
+      const double fx = sx == 1 ? -1.0 : 1.0, fy = sy == 1 ? -1.0 : 1.0, fz = sz == 1 ? -1.0 : 1.0;
+      const double Sx = M[0 + 3 * sy + sz] + 2.0 * M[9 + 3 * sy + sz] + M[18 + 3 * sy + sz];
+      const double Sy = M[9 * sx + 0 + sz] + 2.0 * M[9 * sx + 3 + sz] + M[9 * sx + 6 + sz];
+      const double Sz = M[9 * sx + 3 * sy + 0] + 2.0 * M[9 * sx + 3 * sy + 1] + M[9 * sx + 3 * sy + 2];
+      K_cut[kc * 64 + e] = h * (fx * Sx + fy * Sy + fz * Sz);
+    }
+    if (lane < 8) {
+      // source load: h^3 sum_b f_b int N_a N_b, N_a N_b = q_{a_x + b_x} q_{a_y + b_y} q_{a_z + b_z}
+      const int a = lane;
+      double l = 0.0;
+      for (int bb = 0; bb < 8; ++bb) {
+        const int i = (a & 1) + (bb & 1), j = ((a >> 1) & 1) + ((bb >> 1) & 1), k = (a >> 2) + (bb >> 2);
+        l = fma(s_f[warp][bb], M[9 * i + 3 * j + k], l);
       }
-    for (int a = 0; a < 8; ++a) load_cut[kc * 8 + a] = acc[36 + a];
-    eta[kc] = acc[44];
+      load_cut[kc * 8 + a] = h3 * l + fl;
+    } else if (lane == 8) {
+      const double c[3] = {1.0, 2.0, 1.0};
+      double vol = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          for (int k = 0; k < 3; ++k) vol = fma(c[i] * c[j] * c[k], M[9 * i + 3 * j + k], vol);
+      eta[kc] = vol;
+    }
   }
 }
 
