@@ -84,6 +84,29 @@ __global__ void k_coarse_gather_block(const double* __restrict__ Ac, int ldc, co
   dst[(int64_t)i * ldd + j] = Ac[(int64_t)perm[r0 + i] * ldc + perm[c0 + j]];
 }
 
+// dst = src^T for a list of blocks (one CTA row of 32 x 32 tiles per block)
+struct TransDesc {
+  int rows, cols;      // of src
+  int lds, ldd;
+  int64_t src, dst;
+};
+__global__ void k_coarse_transpose(const TransDesc* __restrict__ td, double* __restrict__ S) {
+  const TransDesc d = td[blockIdx.y];
+  const int tc = (d.cols + 31) / 32, tr = (d.rows + 31) / 32;
+  if ((int)blockIdx.x >= tr * tc) return;
+  const int r0 = (blockIdx.x / tc) * 32, c0 = (blockIdx.x % tc) * 32;
+  __shared__ double t[32][33];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int i = e / 32, j = e % 32;
+    t[i][j] = (r0 + i < d.rows && c0 + j < d.cols) ? S[d.src + (int64_t)(r0 + i) * d.lds + c0 + j] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int i = e / 32, j = e % 32;   // dst row c0 + i, column r0 + j
+    if (c0 + i < d.cols && r0 + j < d.rows) S[d.dst + (int64_t)(c0 + i) * d.ldd + r0 + j] = t[j][i];
+  }
+}
+
 // r (CR order) gathered from the subdomain parts: r[p] = sum_k gC[cpos[l * 8 + k]], l = perm[p]
 __global__ void k_coarse_gather(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restrict__ cpos,
                                 const uint8_t* __restrict__ cnn, const double* __restrict__ gC, double* __restrict__ r,
@@ -253,17 +276,19 @@ void coarse_setup(Bddc& B, DBuf<double>& Acb, int ldc, cudaStream_t s) {
   k_coarse_layer<<<grid_for(n, 256), 256, 0, s>>>(n, m.g, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, m.sub_block.p,
                                                  dl.p);
   UFE_CHECK_LAUNCH();
+  std::vector<int32_t> layer(n);
   {
     DBuf<double> bad;
     bad.alloc(1, s);
     bad.zero();
     k_coarse_band_check<<<grid_for(n * n, 256), 256, 0, s>>>(n, ldc, Ac, dl.p, bad.p);
     UFE_CHECK_LAUNCH();
-    UFE_REQUIRE(scalar_to_host(bad.p, s) == 0.0, UFE_ERR_UNSUPPORTED, "coarse matrix couples non-adjacent layers");
+    double hbad = 0.0;
+    UFE_CUDA(cudaMemcpyAsync(layer.data(), dl.p, n * 4, cudaMemcpyDeviceToHost, s));
+    UFE_CUDA(cudaMemcpyAsync(&hbad, bad.p, 8, cudaMemcpyDeviceToHost, s));
+    UFE_CUDA(cudaStreamSynchronize(s));
+    UFE_REQUIRE(hbad == 0.0, UFE_ERR_UNSUPPORTED, "coarse matrix couples non-adjacent layers");
   }
-  std::vector<int32_t> layer(n);
-  UFE_CUDA(cudaMemcpyAsync(layer.data(), dl.p, n * 4, cudaMemcpyDeviceToHost, s));
-  UFE_CUDA(cudaStreamSynchronize(s));
   std::vector<int32_t> perm(n);
   for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return layer[a] < layer[b]; });
@@ -345,20 +370,19 @@ void coarse_setup(Bddc& B, DBuf<double>& Acb, int ldc, cudaStream_t s) {
     }
   }
 
+  // every layer is inverted once: one status slot per layer, read after the last inversion
   DBuf<int> st;
   st.alloc(std::max(nl, 1), s);
+  st.zero();
+  int n_inv = 0;
   auto invert = [&](const std::vector<int>& ids) {
     std::vector<InvDesc> d;
     for (int id : ids) {
       d.push_back({L[id].n, L[id].ld, L[id].D});
       C.inv_flops += std::pow((double)L[id].n, 3);
     }
-    st.zero();
-    batched_inverse<double>(d, S, st.p, s);
-    std::vector<int> hs(ids.size());
-    UFE_CUDA(cudaMemcpyAsync(hs.data(), st.p, hs.size() * 4, cudaMemcpyDeviceToHost, s));
-    UFE_CUDA(cudaStreamSynchronize(s));
-    for (int v : hs) UFE_REQUIRE(v == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
+    batched_inverse<double>(d, S, st.p + n_inv, s);
+    n_inv += (int)ids.size();
   };
   // coupling of layer b to its current left neighbour: F[b] (storage may move to Fn)
   std::vector<int64_t> Fcur(nl, -1);
@@ -371,35 +395,35 @@ void coarse_setup(Bddc& B, DBuf<double>& Acb, int ldc, cudaStream_t s) {
     std::vector<int> ids;
     for (auto& e : lev) ids.push_back(e.j);
     invert(ids);
-    std::vector<GemmDesc> t1, w1, t2, w2, da, db, fn;
+    std::vector<GemmDesc> t1, t2, da, dbf;
+    std::vector<TransDesc> tw;
     for (auto& e : lev) {
       const Layer &J = L[e.j], &A = L[e.a];
-      // T1 = X_j F_j (n_j x n_a);  W1 = F_j^T X_j (n_a x n_j)
+      // T1 = X_j F_j (n_j x n_a);  W1 = T1^T (X_j symmetric);  D_a -= F_j^T T1
       t1.push_back({J.n, A.n, J.n, J.ld, Fld[e.j], A.ld, J.D, Fcur[e.j], e.T1});
-      w1.push_back({A.n, J.n, J.n, Fld[e.j], J.ld, J.ld, Fcur[e.j], J.D, e.W1});
-      // D_a -= W1 F_j
-      da.push_back({A.n, A.n, J.n, J.ld, Fld[e.j], A.ld, e.W1, Fcur[e.j], A.D});
+      tw.push_back({J.n, A.n, A.ld, J.ld, e.T1, e.W1});
+      da.push_back({A.n, A.n, J.n, Fld[e.j], A.ld, A.ld, Fcur[e.j], e.T1, A.D});
       if (e.b >= 0) {
         const Layer& Bl = L[e.b];
-        // T2 = X_j F_b^T (n_j x n_b);  W2 = F_b X_j (n_b x n_j)
+        // T2 = X_j F_b^T (n_j x n_b);  W2 = T2^T;  D_b -= F_b T2;  F'_b = -F_b T1 (into zeros)
         t2.push_back({J.n, Bl.n, J.n, J.ld, Fld[e.b], Bl.ld, J.D, Fcur[e.b], e.T2});
-        w2.push_back({Bl.n, J.n, J.n, Fld[e.b], J.ld, J.ld, Fcur[e.b], J.D, e.W2});
-        // D_b -= W2 F_b^T;  F'_b = -F_b T1
-        db.push_back({Bl.n, Bl.n, J.n, J.ld, Fld[e.b], Bl.ld, e.W2, Fcur[e.b], Bl.D});
-        fn.push_back({Bl.n, A.n, J.n, Fld[e.b], A.ld, A.ld, Fcur[e.b], e.T1, e.Fn});
+        tw.push_back({J.n, Bl.n, Bl.ld, J.ld, e.T2, e.W2});
+        dbf.push_back({Bl.n, Bl.n, J.n, Fld[e.b], Bl.ld, Bl.ld, Fcur[e.b], e.T2, Bl.D});
+        dbf.push_back({Bl.n, A.n, J.n, Fld[e.b], A.ld, A.ld, Fcur[e.b], e.T1, e.Fn});
       }
     }
     batched_gemm<double>(false, false, t1, S, S, S, 1.0, 0.0, s);
-    batched_gemm<double>(true, false, w1, S, S, S, 1.0, 0.0, s);
-    if (!t2.empty()) {
-      batched_gemm<double>(false, true, t2, S, S, S, 1.0, 0.0, s);
-      batched_gemm<double>(false, false, w2, S, S, S, 1.0, 0.0, s);
+    if (!t2.empty()) batched_gemm<double>(false, true, t2, S, S, S, 1.0, 0.0, s);
+    {
+      DBuf<TransDesc> dtw;
+      upload_vec(dtw, tw, s);
+      int mt = 0;
+      for (const TransDesc& d : tw) mt = std::max(mt, ((d.rows + 31) / 32) * ((d.cols + 31) / 32));
+      k_coarse_transpose<<<dim3(mt, (unsigned)tw.size()), 256, 0, s>>>(dtw.p, S);
+      UFE_CHECK_LAUNCH();
     }
-    batched_gemm<double>(false, false, da, S, S, S, -1.0, 1.0, s);
-    if (!db.empty()) {
-      batched_gemm<double>(false, true, db, S, S, S, -1.0, 1.0, s);
-      batched_gemm<double>(false, false, fn, S, S, S, -1.0, 0.0, s);
-    }
+    batched_gemm<double>(true, false, da, S, S, S, -1.0, 1.0, s);
+    if (!dbf.empty()) batched_gemm<double>(false, false, dbf, S, S, S, -1.0, 1.0, s);
     for (auto& e : lev)
       if (e.b >= 0) {
         Fcur[e.b] = e.Fn;
@@ -417,6 +441,10 @@ void coarse_setup(Bddc& B, DBuf<double>& Acb, int ldc, cudaStream_t s) {
     }
     topl = cur[0];
     invert({topl});
+    std::vector<int> hs(n_inv);
+    UFE_CUDA(cudaMemcpyAsync(hs.data(), st.p, n_inv * 4, cudaMemcpyDeviceToHost, s));
+    UFE_CUDA(cudaStreamSynchronize(s));
+    for (int v : hs) UFE_REQUIRE(v == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
   }
 
   // the solve: forward levels, top, backward levels (reverse)

@@ -18,28 +18,31 @@ namespace ufe {
 
 constexpr int kTile = 64, kSlab = 16, kGemmThreads = 256;
 
-template <typename T, bool TA, bool TB>
+// C tile of TS x TS per CTA (TS = 64: 4 x 4 outputs per thread; TS = 16: one output
+// per thread, for batches too small to fill the GPU with 64 x 64 tiles)
+template <typename T, bool TA, bool TB, int TS>
 __global__ void __launch_bounds__(kGemmThreads)
 k_batched_gemm(const GemmDesc* __restrict__ descs, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C,
                T alpha, T beta) {
+  constexpr int RB = TS / 16;
   const GemmDesc d = descs[blockIdx.y];
-  const int tiles_n = (d.n + kTile - 1) / kTile;
-  const int tiles_m = (d.m + kTile - 1) / kTile;
+  const int tiles_n = (d.n + TS - 1) / TS;
+  const int tiles_m = (d.m + TS - 1) / TS;
   if ((int)blockIdx.x >= tiles_m * tiles_n) return;
-  const int i0 = (blockIdx.x / tiles_n) * kTile, j0 = (blockIdx.x % tiles_n) * kTile;
-  __shared__ T As[kSlab][kTile + 1];
-  __shared__ T Bs[kSlab][kTile + 1];
+  const int i0 = (blockIdx.x / tiles_n) * TS, j0 = (blockIdx.x % tiles_n) * TS;
+  __shared__ T As[kSlab][TS + 1];
+  __shared__ T Bs[kSlab][TS + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  T acc[RB][RB];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RB; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < RB; ++b) acc[a][b] = T(0);
   const T* Ab = A + d.a;
   const T* Bb = B + d.b;
   for (int l0 = 0; l0 < d.k; l0 += kSlab) {
-    for (int e = threadIdx.x; e < kSlab * kTile; e += kGemmThreads) {
-      const int l = e / kTile, r = e % kTile;
+    for (int e = threadIdx.x; e < kSlab * TS; e += kGemmThreads) {
+      const int l = e / TS, r = e % TS;
       const int gi = i0 + r, gl = l0 + l;
       T av = T(0);
       if (gi < d.m && gl < d.k) av = TA ? Ab[(int64_t)gl * d.lda + gi] : Ab[(int64_t)gi * d.lda + gl];
@@ -52,25 +55,25 @@ k_batched_gemm(const GemmDesc* __restrict__ descs, const T* __restrict__ A, cons
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < kSlab; ++l) {
-      T av[4], bv[4];
+      T av[RB], bv[RB];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[l][ty + 16 * a];
+      for (int a = 0; a < RB; ++a) av[a] = As[l][ty + 16 * a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[l][tx + 16 * b];
+      for (int b = 0; b < RB; ++b) bv[b] = Bs[l][tx + 16 * b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < RB; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+        for (int b = 0; b < RB; ++b) acc[a][b] += av[a] * bv[b];
     }
     __syncthreads();
   }
   T* Cb = C + d.c;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < RB; ++a) {
     const int gi = i0 + ty + 16 * a;
     if (gi >= d.m) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < RB; ++b) {
       const int gj = j0 + tx + 16 * b;
       if (gj >= d.n) continue;
       T* cp = Cb + (int64_t)gi * d.ldc + gj;
@@ -83,32 +86,39 @@ template <typename T>
 void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, const T* A, const T* B, T* C,
                   T alpha, T beta, cudaStream_t s) {
   if (descs.empty()) return;
-  int max_tiles = 0;
-  for (const auto& d : descs) {
-    const int t = ((d.m + kTile - 1) / kTile) * ((d.n + kTile - 1) / kTile);
-    if (t > max_tiles) max_tiles = t;
-  }
-  if (max_tiles == 0) return;
+  auto tiles = [&](int ts, int64_t* total) {
+    int mx = 0;
+    *total = 0;
+    for (const auto& d : descs) {
+      const int t = ((d.m + ts - 1) / ts) * ((d.n + ts - 1) / ts);
+      mx = std::max(mx, t);
+      *total += t;
+    }
+    return mx;
+  };
+  int64_t total64 = 0, total16 = 0;
+  const int max64 = tiles(kTile, &total64);
+  if (max64 == 0) return;
+  // batches that give fewer 64 x 64 tiles than two per SM (the coarse layers) take
+  // 16 x 16 tiles: FP64 runs a few FMA per clock per SM, so work must spread out
+  const bool small = total64 < 2 * 152;
+  const int max16 = tiles(16, &total16);
   DBuf<GemmDesc> dd;
   dd.alloc(descs.size(), s);
   UFE_CUDA(cudaMemcpyAsync(dd.p, descs.data(), descs.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, s));
-  dim3 grid(max_tiles, (unsigned)descs.size());
-  if (!transA && !transB) {
-    k_batched_gemm<T, false, false><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
+  const dim3 grid(small ? max16 : max64, (unsigned)descs.size());
+  auto go = [&](auto kernel) {
+    kernel<<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
     UFE_CHECK_LAUNCH();
-  }
-  else if (transA && !transB) {
-    k_batched_gemm<T, true, false><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-    UFE_CHECK_LAUNCH();
-  }
-  else if (!transA && transB) {
-    k_batched_gemm<T, false, true><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-    UFE_CHECK_LAUNCH();
-  }
-  else {
-    k_batched_gemm<T, true, true><<<grid, kGemmThreads, 0, s>>>(dd.p, A, B, C, alpha, beta);
-    UFE_CHECK_LAUNCH();
-  }
+  };
+  if (!transA && !transB)
+    small ? go(k_batched_gemm<T, false, false, 16>) : go(k_batched_gemm<T, false, false, kTile>);
+  else if (transA && !transB)
+    small ? go(k_batched_gemm<T, true, false, 16>) : go(k_batched_gemm<T, true, false, kTile>);
+  else if (!transA && transB)
+    small ? go(k_batched_gemm<T, false, true, 16>) : go(k_batched_gemm<T, false, true, kTile>);
+  else
+    small ? go(k_batched_gemm<T, true, true, 16>) : go(k_batched_gemm<T, true, true, kTile>);
   // the descriptor buffer is released stream-ordered after the kernel
 }
 
@@ -258,25 +268,27 @@ k_gj_diag0(GJBatch bt, const T* __restrict__ base, T* __restrict__ Dg, int* stat
   if (threadIdx.x == 0 && s_flags) atomicOr(status + b, s_flags);
 }
 
-// out(NB x NB tile) = sum_l L[i][l] R[l][j], l < kb
-template <typename T, int NB>
-__device__ __forceinline__ void tile_mma(const T (*L)[NB + 1], const T (*R)[NB + 1], int kb, T acc[NB / 16][NB / 16]) {
-  constexpr int RA = NB / 16;
+// out(NB x CW tile) = sum_l L[i][l] R[l][j], l < kb; thread (tx, ty) of 256 holds
+// rows ty + 16 a and columns tx + 16 b
+template <typename T, int NB, int CW = NB>
+__device__ __forceinline__ void tile_mma(const T (*L)[NB + 1], const T (*R)[CW + 1], int kb,
+                                         T acc[NB / 16][CW / 16]) {
+  constexpr int RA = NB / 16, RB = CW / 16;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
   for (int a = 0; a < RA; ++a)
 #pragma unroll
-    for (int b = 0; b < RA; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < RB; ++b) acc[a][b] = T(0);
   for (int l = 0; l < kb; ++l) {
-    T av[RA], bv[RA];
+    T av[RA], bv[RB];
 #pragma unroll
     for (int a = 0; a < RA; ++a) av[a] = L[ty + 16 * a][l];
 #pragma unroll
-    for (int b = 0; b < RA; ++b) bv[b] = R[l][tx + 16 * b];
+    for (int b = 0; b < RB; ++b) bv[b] = R[l][tx + 16 * b];
 #pragma unroll
     for (int a = 0; a < RA; ++a)
 #pragma unroll
-      for (int b = 0; b < RA; ++b) acc[a][b] += av[a] * bv[b];
+      for (int b = 0; b < RB; ++b) acc[a][b] += av[a] * bv[b];
   }
 }
 
@@ -290,12 +302,19 @@ __device__ __forceinline__ int gj_sign(int I, int J, int last_processed) {
 
 
 // old row panel R_Kt = A_Kt and Q_Kt = D^-1 A_Kt: each CTA loads D^-1 once and walks
-// `cols` columns in chunks of 16 (64 for large batches, 16 when few matrices need
-// the CTAs)
+// `cols` columns (a multiple of the chunk width CW) in chunks, each a register-blocked
+// tile product: CW = 64 in FP32 (16 outputs per thread); CW = 16 in FP64, whose few
+// FMA per clock per SM favour more, smaller CTAs on the look-ahead path
+template <typename T>
+struct PanelWidth {
+  static constexpr int value = sizeof(T) == 4 ? 64 : 16;
+};
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
 k_gj_panel(GJBatch bt, int step, int cols, const T* __restrict__ base, T* __restrict__ R, T* __restrict__ Q,
            const T* __restrict__ Dg) {
+  constexpr int CW = PanelWidth<T>::value;
+  constexpr int RA = NB / 16, RB = CW / 16;
   const int b = blockIdx.y;
   const InvDesc d = bt.d[b];
   const int k0 = step * NB;
@@ -303,18 +322,19 @@ k_gj_panel(GJBatch bt, int step, int cols, const T* __restrict__ base, T* __rest
   if (k0 >= d.n || cbase >= d.n) return;
   const int kb = min(NB, d.n - k0);
   __shared__ T Ds[NB][NB + 1];
-  __shared__ T W[NB][17];
+  __shared__ T W[NB][CW + 1];
   const T* A = base + d.off;
   const T* Db = Dg + (int64_t)b * NB * NB;
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) Ds[e / NB][e % NB] = Db[e];
   T* Rb = R + bt.qoff[b];
   T* Qb = Q + bt.qoff[b];
-  for (int c0 = cbase; c0 < min(cbase + cols, d.n); c0 += 16) {
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int c0 = cbase; c0 < min(cbase + cols, d.n); c0 += CW) {
     if (c0 >= k0 && c0 < k0 + NB) continue;   // the diagonal block (uniform across the CTA)
-    const int cb = min(16, d.n - c0);
+    const int cb = min(CW, d.n - c0);
     __syncthreads();
-    for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
-      const int r = e / 16, c = e % 16;
+    for (int e = threadIdx.x; e < NB * CW; e += blockDim.x) {
+      const int r = e / CW, c = e % CW;
       T v = T(0);
       if (r < kb && c < cb) {
         v = A[(int64_t)(k0 + r) * d.ld + c0 + c];
@@ -323,12 +343,16 @@ k_gj_panel(GJBatch bt, int step, int cols, const T* __restrict__ base, T* __rest
       W[r][c] = v;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < NB * 16; e += blockDim.x) {
-      const int r = e / 16, c = e % 16;
-      if (r >= kb || c >= cb) continue;
-      T acc = T(0);
-      for (int l = 0; l < kb; ++l) acc += Ds[r][l] * W[l][c];
-      Qb[(int64_t)r * d.ld + c0 + c] = acc;
+    T acc[RA][RB];
+    tile_mma<T, NB, CW>(Ds, W, kb, acc);
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int r = ty + 16 * a;
+#pragma unroll
+      for (int c4 = 0; c4 < RB; ++c4) {
+        const int c = tx + 16 * c4;
+        if (r < kb && c < cb) Qb[(int64_t)r * d.ld + c0 + c] = acc[a][c4];
+      }
     }
   }
 }
@@ -419,18 +443,21 @@ k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __res
                  nullptr);
 }
 
-// Look-ahead launch of step K: the tiles of block row / column K+1 (CTA t takes tile
-// (min(K+1, t), max(K+1, t))); CTA t = K+1 keeps the updated diagonal tile in shared
-// memory and inverts it into Dnext, the next step's D^-1.
+// Look-ahead launch of step K: the tiles of block row / column K+1 (tile index t takes
+// tile (min(K+1, t), max(K+1, t))); the CTA of t = K+1 keeps the updated diagonal tile
+// in shared memory and inverts it into Dnext, the next step's D^-1.  Grid (matrix,
+// tile) with the diagonal tiles in the first grid row, so that every matrix's serial
+// inversion starts in the first wave.
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
 k_gj_lookahead(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R,
                const T* __restrict__ Q, const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
-  const int b = blockIdx.y;
+  const int b = blockIdx.x;
   const InvDesc d = bt.d[b];
   const int nd = step + 1;
   if (nd >= nblk) return;
-  const int t = (int)blockIdx.x;
+  const int y = (int)blockIdx.y;
+  const int t = y == 0 ? nd : (y <= nd ? y - 1 : y);
   const int I = min(nd, t), J = max(nd, t);
   if (step * NB >= d.n || J * NB >= d.n) return;
   __shared__ T L[NB][NB + 1];
@@ -504,7 +531,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const int nblk = (nmax + NB - 1) / NB;
   const unsigned nb = (unsigned)descs.size();
   const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
-  const int pcols = descs.size() >= 16 ? 64 : 16;
+  const int pcols = PanelWidth<T>::value;   // one chunk per CTA
   {
     TimedLaunch tl;
     tl.begin(sizeof(T) == 8 ? "gj_diag_f64" : "gj_diag_f32", s);
@@ -530,7 +557,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
       T* Qn = Q.p + ((step + 1) & 1) * nq;
       TimedLaunch ta;
       ta.begin(sizeof(T) == 8 ? "gj_lookahead_f64" : "gj_lookahead_f32", s2);
-      k_gj_lookahead<T, NB><<<dim3(nblk, nb), kGJThreads, 0, s2>>>(bt, step, nblk, base, Rc, Qc, Dc, Dn, status,
+      k_gj_lookahead<T, NB><<<dim3(nb, nblk), kGJThreads, 0, s2>>>(bt, step, nblk, base, Rc, Qc, Dc, Dn, status,
                                                                    floor);
       UFE_CHECK_LAUNCH();
       ta.end(s2);
