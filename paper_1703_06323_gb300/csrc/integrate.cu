@@ -31,6 +31,9 @@ __constant__ double c_tet5_bary[kTet5Pts * 4];
 __constant__ double c_tet5_w[kTet5Pts];
 __constant__ double c_tri_bary[kTriPts * 3];
 __constant__ double c_tri_w[kTriPts];
+// moments int q_i(x) q_j(y) q_k(z) over each whole Kuhn tet (unit-cube coordinates),
+// q in {(1-t)^2, t(1-t), t^2}: added once for a Kuhn tet that lies inside the domain
+__constant__ double c_kuhn_mom[6][27];
 
 // Grundmann-Moeller rule of degree 2s+1 on the n-simplex; weights rescaled to sum to 1.
 static void gm_rule(int n, int s, std::vector<double>& bary, std::vector<double>& w) {
@@ -81,6 +84,35 @@ void ensure_constants() {
   UFE_REQUIRE((int)w.size() == kTet5Pts, UFE_ERR_CUDA, "tet degree-5 rule size");
   UFE_CUDA(cudaMemcpyToSymbol(c_tet5_bary, b.data(), b.size() * sizeof(double)));
   UFE_CUDA(cudaMemcpyToSymbol(c_tet5_w, w.data(), w.size() * sizeof(double)));
+  {
+    // Kuhn tet t: v000 -> v000 + e_a -> v000 + e_a + e_b -> v111 (the kernel's order),
+    // integrated with the same 35-point rule (degree 7: exact for these degree-6 moments)
+    std::vector<double> bt, wt;
+    gm_rule(3, 3, bt, wt);
+    const int ax0[6] = {0, 0, 1, 1, 2, 2}, ax1[6] = {1, 2, 0, 2, 0, 1};
+    double mom[6][27];
+    for (int t = 0; t < 6; ++t) {
+      const int vid[4] = {0, 1 << ax0[t], (1 << ax0[t]) | (1 << ax1[t]), 7};
+      for (int e = 0; e < 27; ++e) mom[t][e] = 0.0;
+      for (size_t qp = 0; qp < wt.size(); ++qp) {
+        double x[3] = {0.0, 0.0, 0.0};
+        for (int m = 0; m < 4; ++m)
+          for (int d = 0; d < 3; ++d) x[d] += bt[qp * 4 + m] * (double)((vid[m] >> d) & 1);
+        double qv[3][3];
+        for (int d = 0; d < 3; ++d) {
+          const double u = 1.0 - x[d];
+          qv[d][0] = u * u;
+          qv[d][1] = x[d] * u;
+          qv[d][2] = x[d] * x[d];
+        }
+        const double wq = wt[qp] / 6.0;   // every Kuhn tet has volume 1/6
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) mom[t][9 * i + 3 * j + k] += wq * qv[0][i] * qv[1][j] * qv[2][k];
+      }
+    }
+    UFE_CUDA(cudaMemcpyToSymbol(c_kuhn_mom, mom, sizeof(mom)));
+  }
   gm_rule(2, 3, b, w);
   UFE_REQUIRE((int)w.size() == kTriPts, UFE_ERR_CUDA, "triangle rule size");
   UFE_CUDA(cudaMemcpyToSymbol(c_tri_bary, b.data(), b.size() * sizeof(double)));
@@ -209,6 +241,7 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
   const bool valid = kc < n_cut;
   CellGeom& G = geo[warp];
   int ntet_l = 0, ntri_l = 0;
+  bool full = false;   // this lane's Kuhn tet lies inside: its moments come from the table
   double st[3][12], tr[2][12];
   if (valid) {
     const int64_t c = cut_cells[kc];
@@ -228,9 +261,11 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
         P[m] = {(double)(vid[m] & 1), (double)((vid[m] >> 1) & 1), (double)(vid[m] >> 2)};
         F[m] = phi[g.node(i + (vid[m] & 1), j + ((vid[m] >> 1) & 1), k + (vid[m] >> 2))];
       }
-      clip_tet(P, F, st, ntet_l, tr, ntri_l);
+      full = F[0] < 0.0 && F[1] < 0.0 && F[2] < 0.0 && F[3] < 0.0;
+      if (!full) clip_tet(P, F, st, ntet_l, tr, ntri_l);
     }
   }
+  const unsigned full_mask = __ballot_sync(0xffffffffu, full);
   // compact the per-tet pieces of lanes 0..5 into the warp's shared geometry
   int off_t = ntet_l, off_r = ntri_l;
 #pragma unroll
@@ -344,6 +379,9 @@ k_integrate_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells
       if (lane == a) fl = t;
     }
   }
+  if (lane < kMom)
+    for (int t = 0; t < 6; ++t)
+      if (full_mask & (1u << t)) v[0] += c_kuhn_mom[t][lane];
   __shared__ double s_val[kWarpsPerBlock][32];
   s_val[warp][lane] = v[0];
   __syncwarp();
