@@ -344,6 +344,10 @@ __device__ double local_entry(const SubMeta& sm, int w, int bi, int bj, int bk, 
   return val;
 }
 
+// CTAs per subdomain for the stencil-by-stencil set-up kernels (9^3 nodes x 27
+// neighbours of work per subdomain: one CTA alone is latency bound)
+constexpr int kLocalSplit = 8;
+
 // dense A_II and A_GG of every subdomain (Sect. 3.1: Neumann matrix over the cells of w);
 // local vector index NC p + c
 template <int NC>
@@ -356,7 +360,7 @@ __global__ void k_local_assemble(SubMeta sm, const int64_t* __restrict__ oII, co
   const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int ldI = pad4(nI), ldG = pad4(nG);
   const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
-  for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x * gridDim.y) {
     const int ln = e / 27, o = e % 27;
     const int32_t c1 = lm[ln];
     const int k1 = lmap_kind(c1);
@@ -396,7 +400,7 @@ __global__ void k_off_ell(SubMeta sm, int rows_kind, int32_t* __restrict__ ell_k
   const int nR = vptr[w + 1] - vptr[w];
   const int64_t base = 27 * NC * (int64_t)vptr[w];
   const int32_t* lm = sm.lmap + (int64_t)w * g.n_local_nodes;
-  for (int e = threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < g.n_local_nodes * 27; e += blockDim.x * gridDim.y) {
     const int ln = e / 27, o = e % 27;
     const int32_t c1 = lm[ln];
     if (lmap_kind(c1) != rows_kind) continue;
@@ -1151,18 +1155,18 @@ void bddc_build(Bddc& B) {
   dGraw.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
   const SubMeta sm = B.meta();
   if (NC == 3) {
-    k_local_assemble<3><<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
+    k_local_assemble<3><<<dim3(ns, kLocalSplit), 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
     UFE_CHECK_LAUNCH();
-    k_off_ell<3><<<ns, 256, 0, s>>>(sm, LKIND_G, ell_k.p, ell_v.p);
+    k_off_ell<3><<<dim3(ns, kLocalSplit), 256, 0, s>>>(sm, LKIND_G, ell_k.p, ell_v.p);
     UFE_CHECK_LAUNCH();
-    k_off_ell<3><<<ns, 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
+    k_off_ell<3><<<dim3(ns, kLocalSplit), 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
     UFE_CHECK_LAUNCH();
   } else {
-    k_local_assemble<1><<<ns, 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
+    k_local_assemble<1><<<dim3(ns, kLocalSplit), 256, 0, s>>>(sm, B.off_II.p, B.off_GG.p, AII.p, AGG.p);
     UFE_CHECK_LAUNCH();
-    k_off_ell<1><<<ns, 256, 0, s>>>(sm, LKIND_G, ell_k.p, ell_v.p);
+    k_off_ell<1><<<dim3(ns, kLocalSplit), 256, 0, s>>>(sm, LKIND_G, ell_k.p, ell_v.p);
     UFE_CHECK_LAUNCH();
-    k_off_ell<1><<<ns, 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
+    k_off_ell<1><<<dim3(ns, kLocalSplit), 256, 0, s>>>(sm, LKIND_I, B.ig_k.p, B.ig_v.p);
     UFE_CHECK_LAUNCH();
   }
   k_local_diag<<<ns, 256, 0, s>>>(sm, NC == 3 ? 1e-8 : 0.0, B.off_II.p, B.off_GG.p, AII.p, AGG.p, sI.p, sG.p,
