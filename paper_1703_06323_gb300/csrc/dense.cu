@@ -386,11 +386,12 @@ __device__ __forceinline__ void gj_tile(const InvDesc& d, int K, int I, int J, T
     }
     return;
   }
-  // P_IK = s R_KI^T with s = -1 when I is processed (I < K), else +1
+  // P_IK = s R_KI^T with s = -1 when I is processed (I < K), else +1; the loads run
+  // along rows of the panels (coalesced) and transpose through shared memory
   const T sP = I < K ? T(-1) : T(1);
   for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
-    L[r][c] = (r < ib && c < kb) ? sP * Rb[(int64_t)c * d.ld + i0 + r] : T(0);
+    L[c][r] = (c < ib && r < kb) ? sP * Rb[(int64_t)r * d.ld + i0 + c] : T(0);
     if (J == K)
       Rt[r][c] = (r < kb && c < kb) ? Db[r * NB + c] : T(0);
     else
@@ -411,13 +412,24 @@ __device__ __forceinline__ void gj_tile(const InvDesc& d, int K, int I, int J, T
       if (r >= ib || c >= jb) continue;
       T* ap = A + (int64_t)(i0 + r) * d.ld + j0 + c;
       const T v = (J == K) ? -acc[a][c4] : (*ap - acc[a][c4]);
-      if (keep) {
+      acc[a][c4] = v;
+      if (keep)
         keep[r][c] = v;
-      } else {
+      else
         *ap = v;
-        if (I != J) A[(int64_t)(j0 + c) * d.ld + i0 + r] = sM * v;
-      }
     }
+  }
+  if (keep || I == J) return;
+  // mirror tile (J, I) = sM * tile^T: staged transposed in shared memory, written by rows
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int c4 = 0; c4 < RA; ++c4) L[tx + 16 * c4][ty + 16 * a] = sM * acc[a][c4];
+  __syncthreads();
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int c = e / NB, r = e % NB;
+    if (c < jb && r < ib) A[(int64_t)(j0 + c) * d.ld + i0 + r] = L[c][r];
   }
 }
 
