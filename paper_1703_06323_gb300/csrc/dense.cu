@@ -82,6 +82,18 @@ k_batched_gemm(const GemmDesc* __restrict__ descs, const T* __restrict__ A, cons
   }
 }
 
+// streaming multiprocessors of the current device (looked up once per device)
+static int sm_count() {
+  static std::mutex mu;
+  static int n[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!n[dev]) UFE_CUDA(cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev));
+  return n[dev];
+}
+
 template <typename T>
 void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, const T* A, const T* B, T* C,
                   T alpha, T beta, cudaStream_t s) {
@@ -101,7 +113,7 @@ void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, 
   if (max64 == 0) return;
   // batches that give fewer 64 x 64 tiles than two per SM (the coarse layers) take
   // 16 x 16 tiles: FP64 runs a few FMA per clock per SM, so work must spread out
-  const bool small = total64 < 2 * 152;
+  const bool small = total64 < 2 * (int64_t)sm_count();
   const int max16 = tiles(16, &total16);
   DBuf<GemmDesc> dd;
   dd.alloc(descs.size(), s);
