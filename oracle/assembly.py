@@ -7,7 +7,7 @@ Box faces without a Dirichlet condition carry homogeneous Neumann data.
 
 Parity: the linear patch test (a linear u with matching flux data is reproduced
 exactly on plane-cut meshes) and symmetry / positive definiteness of A pin this
-module (tests/test_oracle_assembly.py).
+module (tests/test_oracle_integration.py).
 """
 from __future__ import annotations
 
