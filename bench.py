@@ -39,8 +39,9 @@ RTOL = 1e-8
 # FP64 1.25 TFLOP/s nominal for GB300; FP32 SIMT 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/ summary named
-# in the design doc); None once the kernel has changed since the counters were taken.
+# DRAM bytes per launch of the dominant kernel from one ncu capture (summarised in
+# profiles/launches_bumpy64_mixed_step.md); None once the kernel has changed since the
+# counters were taken.
 TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": 4.84e6, "gj_update_f32": None}
 
 
