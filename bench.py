@@ -363,9 +363,7 @@ def run_ours(args, rank, world):
     mean_mixed = statistics.mean(t_mixed)
     mean_fp64 = statistics.mean(t_fp64)
     if world > 1:
-        tt = torch.tensor([mean_mixed, mean_fp64, statistics.mean(e2e_times)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        mean_mixed, mean_fp64, e2e_mean = (float(v) for v in tt)
+        mean_mixed, mean_fp64, e2e_mean = max_over_ranks([mean_mixed, mean_fp64, statistics.mean(e2e_times)], dev)
     else:
         e2e_mean = statistics.mean(e2e_times) if e2e_times else float("nan")
     if rank != 0:
@@ -444,6 +442,15 @@ def run_ours(args, rank, world):
             line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
                                     "sample": f"oracle failed: {err.decode()[-200:]}"}
     print(json.dumps(line))
+
+
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks of the process group
+    (every rank receives it): the job's step time is that of its slowest rank."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t]
 
 
 def main():
