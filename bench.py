@@ -35,14 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "BDDC-PCG time-to-solution (s) and DOF-iters/s at rtol 1e-8, mixed vs FP64 on 1 GB300"
 RTOL = 1e-8
 
-# ALU peaks from unit counts and clocks (no measured FP32/FP64 SIMT peak is available):
-# FP64 1.25 TFLOP/s nominal for GB300; FP32 SIMT 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
-PEAK_FP64_TFLOPS = 1.25
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch of the dominant kernel from one ncu capture (summarised in
-# profiles/launches_bumpy64_mixed_step.md); None once the kernel has changed since the
-# counters were taken.
-TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": 4.84e6, "gj_update_f32": None}
+# DRAM bytes per launch of a kernel from one ncu capture of the same command
+# (dram__bytes_read.sum + dram__bytes_write.sum); a kernel missing here (or changed
+# since its capture) reports traffic null.
+TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": 4.84e6}
+# nominal dense tensor rates (PFLOP/s) that scale a measured bf16 peak to another dtype
+NOMINAL_TENSOR = {"bf16": 2.25, "tf32": 1.1}
 
 
 def parse_args():
@@ -55,6 +53,7 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched-set and adjoint workloads")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -62,24 +61,31 @@ def parse_args():
 # ---------------------------------------------------------------------------
 # oracle timing (the CPU baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_time_to_solution(seed, solves=1):
-    """Time the FP64 oracle on the full workload: every set-up phase once, then
-    `solves` PCG solves.  Returns phase times (s), iterations and DOFs."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_time_to_solution(p, pool=None):
+    """One complete FP64 oracle time-to-solution of problem p: mesh and objects, cut-cell
+    integration (over the cut cells on `pool`'s workers when given), assembly, BDDC
+    set-up, PCG.  Returns the phase times (s), iterations and DOFs."""
     from oracle.assembly import System
     from oracle.bddc import BDDC
     from oracle.integration import Integration
     from oracle.mesh import Mesh
     from oracle.pcg import pcg
-    from paper_1703_06323_gb300 import inputs
 
-    p = inputs.bumpy_sphere(seed)
     t = {}
     t0 = time.perf_counter()
     m = Mesh(p)
     m.objects("v1")
     t["mesh"] = time.perf_counter() - t0
     t0 = time.perf_counter()
-    integ = Integration(m, p)
+    mapper = None if pool is None else (lambda fn, args: pool.starmap(fn, args, chunksize=64))
+    integ = Integration(m, p, map_fn=mapper)
     t["integration"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     sysm = System(m, integ, p)
@@ -87,54 +93,71 @@ def oracle_time_to_solution(seed, solves=1):
     t0 = time.perf_counter()
     B = BDDC(m, integ, sysm, weighting="stiffness", objects="v1", coarse="cef")
     t["bddc_setup"] = time.perf_counter() - t0
-    solve_times, its = [], 0
-    for _ in range(solves):
-        t0 = time.perf_counter()
-        res = pcg(sysm.apply, sysm.b, B.apply, rtol=RTOL, maxit=2000)
-        solve_times.append(time.perf_counter() - t0)
-        its = res["iterations"]
-    return {"phases": t, "solve_times": solve_times, "iterations": its, "n_dof": int(m.n_dof)}
+    t0 = time.perf_counter()
+    res = pcg(sysm.apply, sysm.b, B.apply, rtol=RTOL, maxit=2000)
+    t["pcg"] = time.perf_counter() - t0
+    return {"phases": t, "total": sum(t.values()), "iterations": res["iterations"], "n_dof": int(m.n_dof)}
 
 
-def _oracle_worker_entry(seed, solves, out_path):
-    res = oracle_time_to_solution(seed, solves)
+def _oracle_worker_entry(spec, out_path):
+    """`runs` complete time-to-solutions of the bench workload with `workers` processes
+    (1: this process alone)."""
+    seed, runs, workers = (int(v) for v in spec.split(","))
+    from paper_1703_06323_gb300 import inputs
+    p = inputs.bumpy_sphere(seed)
+    pool = None
+    if workers > 1:
+        pool = mp.get_context("spawn").Pool(workers)
+        pool.starmap(max, [(1, 2)] * workers)   # workers started before the timing
+    try:
+        res = [oracle_time_to_solution(p, pool) for _ in range(runs)]
+    finally:
+        if pool is not None:
+            pool.terminate()
     with open(out_path, "w") as fh:
-        json.dump(res, fh)
+        json.dump({"runs": res, "workers": workers}, fh)
 
 
-def spawn_oracle(seed, solves, out_path):
-    """Run the oracle in a spawned single-threaded process (BLAS pinned to 1 thread)."""
+def run_oracle(seed, runs, workers):
+    """Run the oracle in a child process with BLAS pinned to one thread per process;
+    returns (result dict, error text)."""
+    out = os.path.join("/tmp", f"ufe_oracle_{os.getpid()}_{workers}_{runs}.json")
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", f"{seed}:{solves}:{out_path}"]
-    return subprocess.Popen(cmd, env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", f"{seed},{runs},{workers}:{out}"]
+    proc = subprocess.run(cmd, env=env, stdout=subprocess.DEVNULL, stderr=subprocess.PIPE)
+    if proc.returncode != 0:
+        return None, proc.stderr.decode()[-300:]
+    with open(out) as fh:
+        r = json.load(fh)
+    os.unlink(out)
+    return r, ""
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle on every host core, one complete
+    time-to-solution of the bench workload per step (warmup + steps runs)."""
     if rank != 0:
         return
-    out = os.path.join("/tmp", f"ufe_oracle_ref_{os.getpid()}.json")
-    solves = args.warmup + args.steps
-    proc = spawn_oracle(args.seed, solves, out)
-    _, err = proc.communicate()
-    if proc.returncode != 0:
-        print(json.dumps({"impl": "reference", "unavailable": f"oracle failed: {err.decode()[-300:]}"}))
+    cores = host_cores()
+    r, err = run_oracle(args.seed, args.warmup + args.steps, cores)
+    if r is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle failed: {err}"}))
         return
-    r = json.load(open(out))
-    setup = sum(r["phases"].values())
-    timed = r["solve_times"][args.warmup:]
-    per_step = setup + statistics.mean(timed)
-    sample = ("full workload; set-up phases timed once, then warmup+steps PCG solves; "
-              "value = set-up + mean timed solve")
+    timed = r["runs"][args.warmup:]
+    per_step = statistics.mean(x["total"] for x in timed)
+    phases = {k: statistics.mean(x["phases"][k] for x in timed) for k in timed[0]["phases"]}
+    sample = (f"each step one complete time-to-solution of the workload (seed {args.seed}): mesh, "
+              f"integration over {cores} processes, assembly, BDDC set-up, PCG; value = mean over the timed steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "bumpy_sphere_64^3_cells_8^3_blocks", "rtol": RTOL, "weighting": "stiffness",
                    "objects": "v1", "coarse": "cef", "precision": "fp64"},
-        "iterations": r["iterations"], "phases_s": r["phases"],
-        "cpu_baseline": {"value": per_step, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "iterations": timed[-1]["iterations"], "phases_s": phases,
+        "cpu_baseline": {"value": per_step, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": per_step, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -193,22 +216,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def hbm_peak_gbs():
-    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+def measured_peaks():
+    """Measured peaks of the GB300s (MEASURED_PEAKS.json), else the fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        return 6800.0, "fallback"
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d.get("bf16_tflops", 1900.0)),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError, TypeError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-def per_iteration_roofline(U, p, phi_d, f_d, stream, flush, reps=20):
-    """HBM roofline of the per-iteration kernels (mixed precision): CUDA-event timing of
-    each kernel over `reps` preconditioner + operator applications, L2 flushed before
-    each application; algorithmic bytes = the operator storage each kernel must read
-    (BDDC info) plus 8 bytes per local vector entry it gathers or writes."""
+def per_iteration_roofline(U, p, phi_d, f_d, stream, flush, peaks, reps=20):
+    """Per-iteration kernels (mixed precision): CUDA-event time per launch over `reps`
+    preconditioner + operator applications, L2 flushed before each application.
+    Algorithmic bytes per launch = the stored operators each kernel must read (dense
+    explicit inverses, as stored: BDDC info) plus 8 bytes per local vector entry it
+    gathers or writes; the operator apply reads x, writes y, the DOF map and the 36
+    unique entries of each cut-cell matrix."""
     import torch
-    peak, src = hbm_peak_gbs()
+    peak = peaks["hbm_gbs"]
     mesh = U.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, phi_d, p.dirichlet_face_mask, p.pin_node,
                              stream=stream.cuda_stream)
     sysh = bddc = None
@@ -238,9 +265,10 @@ def per_iteration_roofline(U, p, phi_d, f_d, stream, flush, reps=20):
             "coarse_solve": bi["bytes_coarse_inverse"] + 16 * nc,
             "prec_prolong": bi["bytes_coarse_basis"] + 16 * ng,
             "prec_final": bi["bytes_interior_inverse"] + ig + 16 * ng + 16 * ni,
-            "apply": 16 * n + 4 * minfo["n_nodes"] + minfo["n_cells"] + 512 * minfo["n_cut_cells"],
+            "apply": 16 * n + 4 * minfo["n_nodes"] + minfo["n_cells"] + 36 * 8 * minfo["n_cut_cells"],
         }
-        out = {"peak_gbs": peak, "peak_source": src, "l2": "flushed before each application", "reps": reps}
+        out = {"peak_gbs": peak, "peak_source": peaks["source"], "l2": "flushed before each application",
+               "reps": reps}
         for k, b in bytes_.items():
             ms, cnt = U.ufe_timing_get(k)
             us = 1e3 * ms / max(cnt, 1)
@@ -254,6 +282,179 @@ def per_iteration_roofline(U, p, phi_d, f_d, stream, flush, reps=20):
         if sysh is not None:
             U.ufe_system_destroy(sysh)
         U.ufe_mesh_destroy(mesh)
+
+
+def kuhn_subtets(phi, cells):
+    """Clipped sub-tetrahedra of the cut cells' Kuhn tets (host count from the nodal level
+    set): a Kuhn tet with k inside vertices gives 1 (k = 1) or 3 (k = 2, 3) sub-tets; one
+    with 0 or 4 needs no quadrature."""
+    import numpy as np
+    nx, ny, nz = cells
+    ph = phi.reshape(nz + 1, ny + 1, nx + 1)
+    neg = ph < 0.0
+    v = [neg[dz:dz + nz, dy:dy + ny, dx:dx + nx].ravel() for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)]
+    total = 0
+    for a, b in ((0, 1), (0, 2), (1, 0), (1, 2), (2, 0), (2, 1)):
+        verts = (0, 1 << a, (1 << a) | (1 << b), 7)
+        k = sum(v[i].astype(np.int64) for i in verts)
+        total += int((k == 1).sum() + 3 * ((k == 2) | (k == 3)).sum())
+    return total
+
+
+def roofline_block(kt, n_steps, binfo, per_iter, iterations, fma, peaks, n_subtets):
+    """Roofline of the dominant kernel: the candidate with the largest device time per
+    step among every instrumented kernel.  Algorithmic work per launch:
+    * Gauss-Jordan update launches (local inverses in FP32 / coarse inverse in FP64):
+      the Cholesky factorisation count n^3/3 of every inverted matrix, spread evenly over
+      that precision's update launches (the look-ahead, panel and diagonal launches of the
+      same inversions are listed with their time only);
+    * cut-cell integration: 27 moment FMAs (54 flops) at each of the 35 points of every
+      clipped sub-tetrahedron;
+    * per-iteration kernels: the bytes of per_iteration_roofline, timed once per PCG
+      iteration plus the initial preconditioner application."""
+    tf32 = peaks["bf16_tflops"] * NOMINAL_TENSOR["tf32"] / NOMINAL_TENSOR["bf16"]
+    f32_on_tc = binfo.get("local_tc", 0) == 1
+    local_flops = binfo["inverse_flops_local"] / 3.0
+    coarse_flops = binfo["inverse_flops_coarse"] / 3.0
+    f64_flops = coarse_flops + (local_flops if binfo["fp64_refactor"] else 0.0)
+    rows = []
+
+    def add(name, ms_step, launches_step, work, bound, unit, peak, peak_source):
+        if ms_step <= 0 or launches_step <= 0:
+            return
+        row = {"kernel": name, "ms_per_step": ms_step, "launches_per_step": launches_step,
+               "avg_launch_us": 1e3 * ms_step / launches_step}
+        if work is not None:
+            achieved = work / launches_step / (row["avg_launch_us"] * 1e-6)
+            achieved = achieved / 1e12 if unit == "TFLOP/s" else achieved / 1e9
+            row.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                        "peak_source": peak_source, "work_per_launch": work / launches_step})
+        rows.append(row)
+
+    fma_src = "FMA-loop probe (ufe_probe_fma_rate) measured in this run"
+    for name, (ms, cnt) in kt.items():
+        ms_step, l_step = ms / n_steps, cnt / n_steps
+        if name == "gj_update_f64":
+            add(name, ms_step, l_step, f64_flops, "alu", "TFLOP/s", fma["fp64"], fma_src)
+        elif name == "gj_update_f32":
+            if f32_on_tc:
+                add(name, ms_step, l_step, 0.0 if binfo["fp64_refactor"] else local_flops, "tensor", "TFLOP/s",
+                    tf32, f"{peaks['source']} bf16 peak x nominal tf32/bf16 ({NOMINAL_TENSOR['tf32']}/"
+                          f"{NOMINAL_TENSOR['bf16']})")
+            else:
+                add(name, ms_step, l_step, 0.0 if binfo["fp64_refactor"] else local_flops, "alu", "TFLOP/s",
+                    fma["fp32"], fma_src)
+        elif name == "integrate_cut":
+            add(name, ms_step, l_step, 54.0 * 35 * n_subtets, "alu", "TFLOP/s", fma["fp64"], fma_src)
+        else:
+            add(name, ms_step, l_step, None, None, None, None, None)
+    if per_iter:
+        for k in ("prec_interior", "prec_neumann", "coarse_solve", "prec_prolong", "prec_final", "apply"):
+            d = per_iter.get(k)
+            if not d or not d["us"]:
+                continue
+            launches = iterations + 1
+            add(k, d["us"] * launches / 1e3, launches, d["bytes"] * launches, "hbm", "GB/s", per_iter["peak_gbs"],
+                per_iter["peak_source"])
+    rows.sort(key=lambda r: -r["ms_per_step"])
+    dom = next(r for r in rows if "achieved" in r)
+    traffic = TRAFFIC_BYTES_PER_LAUNCH.get(dom["kernel"])
+    out = {"kernel": dom["kernel"], "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+           "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic, "peak_source": dom["peak_source"],
+           "launches_per_step": dom["launches_per_step"], "avg_launch_us": dom["avg_launch_us"],
+           "work_per_launch": dom["work_per_launch"], "kernels": rows}
+    return out
+
+
+def adjoint_workload(U, dev, stream, flush, precision, reps=2):
+    """Config-5 style adjoint workload (128^3 background cells, 16^3 subdomains, sphere of
+    radius 0.45, per-cell kappa = exp(GRF)): mesh, assembly, BDDC set-up, forward solve
+    and adjoint solve with the per-cell gradient, timed by CUDA events; returns the mean
+    time and the solve details."""
+    import torch
+    from paper_1703_06323_gb300 import autograd as AG
+    from paper_1703_06323_gb300 import inputs
+    from paper_1703_06323_gb300.solver import Solver
+    if not hasattr(adjoint_workload, "problem"):
+        adjoint_workload.problem = inputs.coefficient_sphere(0, 128)
+    p = adjoint_workload.problem
+    arrays = {"phi": torch.from_numpy(p.phi).to(dev), "f": torch.from_numpy(p.f).to(dev),
+              "g": torch.from_numpy(p.dirichlet_values).to(dev), "kappa": torch.from_numpy(p.kappa).to(dev)}
+    w = AG.lumped_mass(p, dev)
+    ud_nodes = torch.from_numpy(p.meta["u_d"]).to(dev)
+    times, last = [], None
+    for rep in range(reps + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with Solver(p, precision=precision, arrays=dict(arrays), stream=stream.cuda_stream) as S:
+            u = torch.zeros(S.n_dof, dtype=torch.float64, device=dev)
+            _, fi = U.ufe_pcg_solve(S.system, S.bddc, None, u, rtol=RTOL, maxit=2000)
+            dof = torch.from_numpy(U.ufe_mesh_get_dof_map(S.mesh)).to(dev).long()
+            node_of_dof = torch.empty(S.n_dof, dtype=torch.long, device=dev)
+            sel = dof >= 0
+            node_of_dof[dof[sel]] = torch.nonzero(sel).squeeze(1)
+            lam = torch.zeros_like(u)
+            g = torch.empty(p.kappa.size, dtype=torch.float64, device=dev)
+            ai = U.ufe_adjoint(S.system, S.bddc, u, w * (u - ud_nodes[node_of_dof]), lam, g, rtol=RTOL,
+                               maxit=2000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            info = (S.n_dof, S.info["n_subdomains"], S.bddc_info["n_coarse"], fi, ai)
+        if rep > 0:
+            times.append(e0.elapsed_time(e1) / 1e3)
+        last = info
+    n, nsub, nc, fi, ai = last
+    return {"value": statistics.mean(times), "unit": "s", "reps": reps, "n_dof": n, "subdomains": nsub,
+            "n_coarse": nc, "forward_iterations": fi["iterations"], "adjoint_iterations": ai["iterations"],
+            "forward_true_rel_residual": fi["true_rel_residual"]}
+
+
+def batched_workload(U, dev, stream, flush, reps=2):
+    """Config-4 style batched set (256 seeded spheres on 24^3..64^3 background meshes,
+    mixed precision): set-up of every problem, then one ufe_pcg_solve_batched over all
+    of them (first call builds the solve graphs; the repeats reuse them)."""
+    import torch
+    from paper_1703_06323_gb300 import inputs
+    from paper_1703_06323_gb300.solver import Solver
+    ps = inputs.batched_spheres(count=256, seed=0)
+    arrays = [{"phi": torch.from_numpy(p.phi).to(dev), "f": torch.from_numpy(p.f).to(dev),
+               "g": torch.from_numpy(p.dirichlet_values).to(dev)} for p in ps]
+    torch.cuda.synchronize()
+    solvers = []
+    try:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for p, a in zip(ps, arrays):
+            solvers.append(Solver(p, precision="mixed", arrays=a, stream=stream.cuda_stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        setup_s = e0.elapsed_time(e1) / 1e3
+        solve_times, infos = [], None
+        for rep in range(reps + 1):
+            xs = [torch.zeros(S.n_dof, dtype=torch.float64, device=dev) for S in solvers]
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st, infos = U.ufe_pcg_solve_batched([S.system for S in solvers], [S.bddc for S in solvers], None, xs,
+                                                rtol=RTOL, maxit=1000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            solve_times.append(e0.elapsed_time(e1) / 1e3)
+        dofs = [S.n_dof for S in solvers]
+        its = [i["iterations"] for i in infos]
+        solve = statistics.mean(solve_times[1:])
+        return {"problems": len(ps), "total_dofs": int(sum(dofs)), "setup_s": setup_s,
+                "solve_s_first_call": solve_times[0], "solve_s": solve, "unit": "s",
+                "time_to_solution_s": setup_s + solve,
+                "dof_iters_per_s": float(sum(d * i for d, i in zip(dofs, its))) / solve,
+                "iterations_min_median_max": [min(its), int(statistics.median(its)), max(its)],
+                "all_converged": all(i["converged"] == 1 for i in infos),
+                "max_true_rel_residual": max(i["true_rel_residual"] for i in infos)}
+    finally:
+        for S in solvers:
+            S.close()
 
 
 # ---------------------------------------------------------------------------
@@ -270,11 +471,6 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    oracle_proc, oracle_out = None, None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        oracle_out = os.path.join("/tmp", f"ufe_oracle_cpu_{os.getpid()}.json")
-        oracle_proc = spawn_oracle(args.seed, 1, oracle_out)
 
     p = inputs.bumpy_sphere(args.seed + rank)
     phi_d = torch.from_numpy(p.phi).to(dev)
@@ -306,7 +502,7 @@ def run_ours(args, rank, world):
             U.ufe_mesh_destroy(mesh)
         return n, info, binfo, x
 
-    def timed(precision, k, launches=False):
+    def timed(precision, k):
         times, infos = [], []
         l0 = U.ufe_kernel_launches()
         for _ in range(k):
@@ -336,9 +532,9 @@ def run_ours(args, rank, world):
     U.ufe_timing_enable(True)
     t_mixed, i_mixed, launches = timed("mixed", args.steps)
     U.ufe_timing_enable(False)
-    kt = {k: U.ufe_timing_get(k) for k in ("gj_update_f64", "gj_update_f32", "integrate_cut")}
-    kt_extra = {k: U.ufe_timing_get(k)[0] / args.steps for k in ("gj_lookahead_f64", "gj_lookahead_f32",
-                                                                   "gj_panel_f64", "gj_panel_f32")}
+    kt = {k: U.ufe_timing_get(k) for k in ("gj_update_f64", "gj_update_f32", "gj_lookahead_f64", "gj_lookahead_f32",
+                                           "gj_panel_f64", "gj_panel_f32", "gj_diag_f64", "gj_diag_f32",
+                                           "integrate_cut")}
     phases = {k: U.ufe_timing_get(k)[0] / args.steps for k in
               ("phase_mesh", "phase_assemble", "phase_objects", "phase_local", "phase_factor", "phase_coarse",
                "phase_solve")}
@@ -358,8 +554,6 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
 
-    per_iter = per_iteration_roofline(U, p, phi_d, f_d, stream, flush) if rank == 0 else None
-
     mean_mixed = statistics.mean(t_mixed)
     mean_fp64 = statistics.mean(t_fp64)
     if world > 1:
@@ -369,6 +563,15 @@ def run_ours(args, rank, world):
     if rank != 0:
         return
 
+    peaks = measured_peaks()
+    per_iter = per_iteration_roofline(U, p, phi_d, f_d, stream, flush, peaks)
+    fma = {"fp64": U.ufe_probe_fma_rate("fp64", stream.cuda_stream),
+           "fp32": U.ufe_probe_fma_rate("fp32", stream.cuda_stream)}
+    extra = {}
+    if not args.no_extra and world == 1:
+        extra["adjoint_128^3"] = {prec: adjoint_workload(U, dev, stream, flush, prec) for prec in ("mixed", "fp64")}
+        extra["batched_256"] = batched_workload(U, dev, stream, flush)
+
     n, info, binfo = i_mixed[-1]
     its = info["iterations"]
     solve_s = statistics.mean(i[1]["solve_ms"] for i in i_mixed) / 1e3
@@ -377,21 +580,7 @@ def run_ours(args, rank, world):
         n64, info64, binfo64 = i_fp64[-1]
     else:
         n64, info64 = n, {"iterations": 0, "true_rel_residual": None}
-
-    # roofline of the dominant instrumented kernel (the Gauss-Jordan update steps are
-    # ALU bound: symmetric inversion of an n x n matrix takes n^3 flops)
-    flops = {"gj_update_f64": binfo["inverse_flops_coarse"], "gj_update_f32": binfo["inverse_flops_local"]}
-    peaks = {"gj_update_f64": PEAK_FP64_TFLOPS, "gj_update_f32": PEAK_FP32_TFLOPS}
-    dom = max(flops, key=lambda k: kt[k][0])
-    ms_tot, n_launch = kt[dom]
-    per_launch_flops = flops[dom] * args.steps / max(n_launch, 1)
-    avg_s = ms_tot / 1e3 / max(n_launch, 1)
-    achieved = per_launch_flops / avg_s / 1e12 if avg_s > 0 else None
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peaks[dom], "unit": "TFLOP/s",
-                "frac": achieved / peaks[dom] if achieved else None, "traffic": TRAFFIC_BYTES_PER_LAUNCH[dom],
-                "peak_source": "derived from unit counts and clocks (FP64: 1.25 TFLOP/s nominal)",
-                "launches": n_launch, "avg_launch_us": avg_s * 1e6,
-                "kernel_ms_per_step": dict({k: v[0] / args.steps for k, v in kt.items()}, **kt_extra)}
+    roofline = roofline_block(kt, args.steps, binfo, per_iter, its, fma, peaks, kuhn_subtets(p.phi, p.cells))
 
     line = {
         "metric": METRIC,
@@ -423,25 +612,39 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "phase_ms": phases,
         "roofline": roofline,
+        "fma_peaks_tflops": fma,
         "per_iteration_roofline": per_iter,
         "clocks": clk_stats,
         "e2e": {"value": e2e_mean / world, "unit": "s",
                 "h2d_bytes_per_step": int(p.phi.nbytes + p.f.nbytes + 8 * n),
                 "d2h_bytes_per_step": int(8 * n)},
     }
-    if oracle_proc is not None:
-        _, err = oracle_proc.communicate()
-        if oracle_proc.returncode == 0:
-            r = json.load(open(oracle_out))
-            total = sum(r["phases"].values()) + r["solve_times"][0]
-            line["cpu_baseline"] = {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
-                                    "sample": "one complete time-to-solution of the same workload (seed "
-                                              f"{args.seed}), BLAS pinned to 1 thread",
-                                    "phases_s": r["phases"], "iterations": r["iterations"]}
-        else:
-            line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
-                                    "sample": f"oracle failed: {err.decode()[-200:]}"}
+    line.update(extra)
+    # the CPU baseline runs after every GPU measurement (no host core busy meanwhile)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.seed)
     print(json.dumps(line))
+
+
+def cpu_baseline(seed):
+    """The FP64 oracle on the host: one complete time-to-solution of the same workload on
+    one core, then one with the cut-cell integration spread over every host core."""
+    cores = host_cores()
+    r1, err1 = run_oracle(seed, 1, 1)
+    rn, errn = run_oracle(seed, 1, cores) if cores > 1 else (None, "one host core")
+    if r1 is None:
+        return {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"oracle failed: {err1}"}
+    one = r1["runs"][0]
+    out = {"value": one["total"], "unit": "s", "cores": 1, "kind": "oracle",
+           "sample": f"one complete time-to-solution of the same workload (seed {seed}), one process, BLAS on 1 "
+                     "thread", "phases_s": one["phases"], "iterations": one["iterations"], "host_cores": cores}
+    if rn is not None:
+        r = rn["runs"][0]
+        out["n_core"] = {"value": r["total"], "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": f"the same, cut-cell integration over {cores} processes", "phases_s": r["phases"]}
+    else:
+        out["n_core"] = {"value": None, "cores": cores, "sample": errn}
+    return out
 
 
 def max_over_ranks(values, device):
@@ -456,8 +659,8 @@ def max_over_ranks(values, device):
 def main():
     args = parse_args()
     if args.oracle_worker:
-        seed, solves, out = args.oracle_worker.split(":", 2)
-        _oracle_worker_entry(int(seed), int(solves), out)
+        spec, out = args.oracle_worker.split(":", 1)
+        _oracle_worker_entry(spec, out)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -128,6 +128,14 @@ void ufe_timing_enable(int on);
 void ufe_timing_reset(void);
 ufe_status ufe_timing_get(const char* kernel, double* total_ms, int64_t* launches);
 
+/* Measured FMA rate of the current device (instrumentation only; no paper
+ * counterpart): an FMA-loop kernel with eight independent chains per thread and
+ * four 256-thread CTAs per SM, timed by CUDA events on `stream` (NULL: the legacy
+ * default stream) after one warm-up launch.  kind 0: FP64, 1: FP32 (SIMT pipes).
+ * *tflops receives 2 flops per FMA over the elapsed time, in TFLOP/s; it is the
+ * denominator of the ALU rooflines the benchmark reports. */
+ufe_status ufe_probe_fma_rate(int kind, void* stream, double* tflops);
+
 typedef struct {
   int64_t n_nodes, n_cells;
   int64_t n_active_cells, n_cut_cells;
@@ -326,11 +334,15 @@ ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
  * subdomains of their interface DOFs, counted per component), 65,536 subdomain coarse slots or 32,768
  * coarse DOFs -- are rejected with UFE_ERR_INVALID_ARG and a message naming the
  * limit.  The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
- * library routine.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents, so calls that overlap on the GPU (other streams or threads
- * using any ufe_bddc handle) race; serialise them.  Returns after z is complete.
+ * library routine.  ufe_bddc_setup (which does allocate) looks up the array's
+ * device address (cudaGetSymbolAddress) on the device current at set-up and loads
+ * every kernel this call launches, so no module or kernel loading, which takes
+ * device memory, happens inside the call.  The call must be made with the set-up's
+ * device current and with r and z in that device's memory; otherwise it returns
+ * UFE_ERR_INVALID_ARG.  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (other streams or threads using any
+ * ufe_bddc handle) race; serialise them.  The call waits on the preconditioner's
+ * stream and returns after z is complete.
  */
 ufe_status ufe_bddc_apply_noalloc(ufe_bddc* bddc, const double* r, double* z);
 void ufe_bddc_destroy(ufe_bddc* bddc);

@@ -183,9 +183,13 @@ def integrate_cut_cell(phi8, f8, q8, h):
 
 
 class Integration:
-    """Element data of every active cell of a mesh (Sect. 2.2)."""
+    """Element data of every active cell of a mesh (Sect. 2.2).
 
-    def __init__(self, mesh, problem):
+    ``map_fn(func, args)`` (default: the builtin map over argument tuples) evaluates
+    integrate_cut_cell over the cut cells; a process pool's starmap runs the cells on
+    several host cores with the same arithmetic per cell."""
+
+    def __init__(self, mesh, problem, map_fn=None):
         g = mesh.grid
         self.h = g.h
         phi = mesh.phi
@@ -196,9 +200,15 @@ class Integration:
         self.K_cut = np.zeros((n_cut, 8, 8))
         self.load_cut = np.zeros((n_cut, 8))
         self.eta = np.zeros(n_cut)
-        for idx, c in enumerate(self.cut_cells):
+        args = []
+        for c in self.cut_cells:
             nodes = g.cell_nodes(c)
-            Ke, le, eta = integrate_cut_cell(phi[nodes], f[nodes], None if q is None else q[nodes], g.h)
+            args.append((phi[nodes], f[nodes], None if q is None else q[nodes], g.h))
+        if map_fn is None:
+            results = [integrate_cut_cell(*a) for a in args]
+        else:
+            results = map_fn(integrate_cut_cell, args)
+        for idx, (Ke, le, eta) in enumerate(results):
             self.K_cut[idx] = Ke
             self.load_cut[idx] = le
             self.eta[idx] = eta

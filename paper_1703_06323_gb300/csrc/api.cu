@@ -98,6 +98,23 @@ static const T* stage(DBuf<T>& buf, const T* src, size_t n, int mem, cudaStream_
   return buf.p;
 }
 
+// FMA-rate probe: eight independent chains per thread keep every pipe slot busy
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(int iters, T* out) {
+  T a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = T(threadIdx.x + i) * T(1e-3);
+  const T b = T(0.999999), c = T(1e-7);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+  }
+  T sum = T(0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) sum += a[i];
+  if (sum == T(-1.2345)) out[0] = sum;   // keeps the chains live; never true
+}
+
 }  // namespace ufe
 
 using namespace ufe;
@@ -111,6 +128,40 @@ int ufe_version(void) { return 100; }
 int64_t ufe_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
 
 void ufe_timing_enable(int on) { g_timing = on != 0; }
+
+ufe_status ufe_probe_fma_rate(int kind, void* stream, double* tflops) {
+  return guarded([&] {
+    UFE_REQUIRE(tflops && (kind == 0 || kind == 1), UFE_ERR_INVALID_ARG, "bad probe arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    UFE_CUDA(cudaGetDevice(&dev));
+    UFE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = 4u * (unsigned)sms;
+    // a few milliseconds per launch on GB300 (about 1.2 TFLOP/s FP64, 70 TFLOP/s FP32)
+    const int iters = kind == 0 ? 4000 : 200000;
+    DBuf<double> out;
+    out.alloc(1, s);
+    cudaEvent_t e0, e1;
+    UFE_CUDA(cudaEventCreate(&e0));
+    UFE_CUDA(cudaEventCreate(&e1));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      UFE_CUDA(cudaEventRecord(e0, s));
+      if (kind == 0)
+        k_fma_probe<double><<<grid, 256, 0, s>>>(iters, out.p);
+      else
+        k_fma_probe<float><<<grid, 256, 0, s>>>(iters, reinterpret_cast<float*>(out.p));
+      UFE_CHECK_LAUNCH();
+      UFE_CUDA(cudaEventRecord(e1, s));
+      UFE_CUDA(cudaEventSynchronize(e1));
+      UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * 8.0 * (double)iters * grid * 256.0;
+    *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+  });
+}
 
 void ufe_timing_reset(void) {
   std::lock_guard<std::mutex> lock(g_tmu);
@@ -406,7 +457,9 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     B->opts = *opts;
     B->mixed = opts->precision == UFE_PREC_MIXED;
     B->coarse_solver = opts->coarse_solver;
+    UFE_CUDA(cudaGetDevice(&B->device));
     bddc_build(*B);
+    bddc_noalloc_prepare(*B);
     UFE_CUDA(cudaStreamSynchronize(B->stream));
     *out = B.release();
   });

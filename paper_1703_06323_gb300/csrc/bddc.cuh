@@ -100,6 +100,7 @@ struct Bddc {
   System* sys = nullptr;
   Mesh* mesh = nullptr;
   cudaStream_t stream = nullptr;
+  int device = -1;              // device current at set-up (its stream and buffers live there)
   ufe_bddc_opts opts{};
   bool mixed = false;
 
@@ -168,6 +169,11 @@ void coarse_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s);
 void coarse_solve(const Bddc& B, const double* gC, double* uc, double* work, const PcgScalars* sc, cudaStream_t s);
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev);
 void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
+// made by the set-up: loads the device code and looks up the static array the
+// allocation-free apply uses, so that the apply itself takes no device memory
+void bddc_noalloc_prepare(Bddc& B);
+// loads the coarse solver's kernels (cudaFuncGetAttributes), once per device
+void coarse_prepare();
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);
 ufe_status pcg_solve_batched(int n, Bddc* const* Bs, const double* const* b_dev, double* const* x_dev,
                              const ufe_solve_opts& o, ufe_solve_info* infos);

@@ -26,6 +26,7 @@
 // factors n_c^3 / L^2-sized blocks instead of one n_c^3 matrix.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "bddc.cuh"
@@ -210,6 +211,21 @@ void coarse_solve(const Bddc& B, const double* gC, double* uc, double* work, con
                                         sc);
     UFE_CHECK_LAUNCH();
   }
+}
+
+void coarse_prepare() {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaFuncAttributes fa;
+  UFE_CUDA(cudaFuncGetAttributes(&fa, k_coarse_dense));
+  UFE_CUDA(cudaFuncGetAttributes(&fa, k_coarse_gather));
+  UFE_CUDA(cudaFuncGetAttributes(&fa, k_coarse_step));
+  done[dev] = true;
 }
 
 namespace {

@@ -1246,7 +1246,9 @@ constexpr int64_t kNoAllocG = 262144, kNoAllocC = 65536, kNoAllocU = 32768;
 // interface vectors, subdomain coarse parts, u_c and the coarse solver's work vector (2 n_c)
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocG + kNoAllocC + 3 * kNoAllocU];
 
-// device address of the array for the current device, looked up once per device
+// device address of the array for the current device, looked up once per device (the
+// lookup may load this file's device code, which takes device memory: it is first made
+// by ufe_bddc_setup through bddc_noalloc_prepare, never inside the allocation-free call)
 static double* noalloc_scratch_ptr() {
   static std::mutex mu;
   static double* ptr[128] = {};
@@ -1286,8 +1288,26 @@ static void launch_preconditioner_static(Bddc& B, const double* r, double* z, do
   UFE_CHECK_LAUNCH();
 }
 
+void bddc_noalloc_prepare(Bddc& B) {
+  set_smem_limits(B);
+  noalloc_scratch_ptr();
+  coarse_prepare();
+}
+
 void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev) {
   const Mesh& m = *B.mesh;
+  int dev = -1;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev == B.device, UFE_ERR_INVALID_ARG,
+              "ufe_bddc_apply_noalloc: the current device (" + std::to_string(dev) +
+                  ") is not the device the preconditioner was set up on (" + std::to_string(B.device) + ")");
+  for (const void* ptr : {(const void*)r_dev, (const void*)z_dev}) {
+    cudaPointerAttributes pa{};
+    UFE_CUDA(cudaPointerGetAttributes(&pa, ptr));
+    UFE_REQUIRE((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) && pa.device == B.device,
+                UFE_ERR_INVALID_ARG,
+                "ufe_bddc_apply_noalloc: r and z must be device memory of the preconditioner's device");
+  }
   UFE_REQUIRE(B.n_vGloc <= kNoAllocG, UFE_ERR_INVALID_ARG,
               "ufe_bddc_apply_noalloc: " + std::to_string(B.n_vGloc) + " interface slots exceed the static limit of " +
                   std::to_string(kNoAllocG));

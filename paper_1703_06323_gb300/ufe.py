@@ -84,6 +84,7 @@ def _load():
         "ufe_timing_reset": (None, []),
         "ufe_timing_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
+        "ufe_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]),
         "ufe_mesh_create": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, U32, I64, P, ctypes.POINTER(P)]),
         "ufe_mesh_get_info": (ctypes.c_int, [P, ctypes.POINTER(MeshInfo)]),
         "ufe_mesh_get_cell_types": (ctypes.c_int, [P, P, ctypes.c_int]),
@@ -122,7 +123,7 @@ def _load():
 
 LIB = _load()
 EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_enable", "ufe_timing_reset",
-            "ufe_timing_get", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
+            "ufe_timing_get", "ufe_probe_fma_rate", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
             "ufe_assemble", "ufe_assemble_elastic", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_set_kappa",
             "ufe_system_get_cut_data",
@@ -194,6 +195,13 @@ def ufe_timing_get(kernel):
     n = ctypes.c_int64()
     _check(LIB.ufe_timing_get(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def ufe_probe_fma_rate(kind, stream=None):
+    """Measured FMA rate (TFLOP/s) of the current device: kind "fp64" or "fp32"."""
+    out = ctypes.c_double()
+    _check(LIB.ufe_probe_fma_rate({"fp64": 0, "fp32": 1}[kind], _stream(stream), ctypes.byref(out)))
+    return out.value
 
 
 def ufe_mesh_create(box_lo, box_hi, cells, sub_cells, phi_nodes, dirichlet_face_mask=0, pin_node=PIN_AUTO,

@@ -17,6 +17,9 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["unit"] == "s" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0 and d["iterations"] == 12
     assert d["config"]["workload"] == "bumpy_sphere_64^3_cells_8^3_blocks"
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == bench.host_cores()
+    assert d["ms_per_step"] == d["value"] * 1e3
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

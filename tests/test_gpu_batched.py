@@ -69,14 +69,13 @@ def test_batched_parity_with_the_oracle(env):
     solvers = [Solver(r.p) for r in runs]
     try:
         xs = [np.zeros(S.n_dof) for S in solvers]
+        # both sides at rtol 1e-12: solution parity with no allowance for the stopping point
         st, infos = ufe.ufe_pcg_solve_batched([S.system for S in solvers], [S.bddc for S in solvers],
-                                              [None] * len(solvers), xs, rtol=1e-8, maxit=500)
+                                              [None] * len(solvers), xs, rtol=1e-12, maxit=5000)
         assert st == ufe.OK
         for r, x, info in zip(runs, xs, infos):
             ref = r.solve(rtol=1e-12)
-            ref8 = r.solve(rtol=1e-8)
-            floor = energy_error(r.sys.A, ref8["x"], ref["x"])
-            assert energy_error(r.sys.A, x, ref["x"]) <= max(1e-8, 4 * floor)
+            assert energy_error(r.sys.A, x, ref["x"]) <= 1e-8
     finally:
         for S in solvers:
             S.close()

@@ -206,20 +206,26 @@ def test_coarse_cyclic_reduction(ufe, name, precision):
 @pytest.mark.parametrize("name", SOLVABLE)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_pcg_solution(ufe, name, precision):
-    """Solution of PCG at rtol 1e-8 against the oracle's: energy norm 1e-8 (FP64) / 1e-6 (mixed)."""
+    """PCG at the method's rtol 1e-8: converged, true residual within the tolerance,
+    FP64 iteration counts within 1 of the oracle's.  Solution parity: both sides
+    solve to rtol 1e-12, where each is the discrete solution to well below the
+    stated tolerance, and the GPU solution must match the oracle's in the energy
+    norm to 1e-8 (FP64) / 1e-6 (mixed), with no allowance for either solver's
+    stopping point."""
     orc = oracle_run(name)
     ref = orc.solve(rtol=1e-12)
     ref8 = orc.solve(rtol=1e-8)
+    tol = 1e-8 if precision == "fp64" else 1e-6
     with _solver(ufe, orc.p, precision=precision) as S:
         x, info = S.solve(rtol=1e-8)
-    assert info["converged"] == 1
-    assert info["true_rel_residual"] <= 1e-8 * 1.5
-    tol = 1e-8 if precision == "fp64" else 1e-6
-    # the FP64 oracle at the same rtol sets the floor for "identical": both stop at |r| < 1e-8 |b|
-    floor = energy_error(orc.sys.A, ref8["x"], ref["x"])
-    assert energy_error(orc.sys.A, x, ref["x"]) <= max(tol, 4 * floor)
-    if precision == "fp64":
-        assert abs(info["iterations"] - ref8["iterations"]) <= 1
+        assert info["converged"] == 1
+        assert info["true_rel_residual"] <= 1e-8 * 1.5
+        # FP64: within 1 of the oracle; mixed (flexible PCG on FP32 local operators): within
+        # 2, which a mis-scaled local operator in any subdomain would break
+        assert abs(info["iterations"] - ref8["iterations"]) <= (1 if precision == "fp64" else 2)
+        x12, info12 = S.solve(rtol=1e-12, maxit=3000)
+    assert info12["converged"] == 1
+    assert energy_error(orc.sys.A, x12, ref["x"]) <= tol
 
 
 def test_pcg_initial_guess_and_zero_rhs(ufe):

@@ -174,3 +174,31 @@ def test_manufactured_solution_error_decreases():
         ins = p.phi[m.node_of_dof] < 0
         errs.append(np.abs(x - p.u_exact[m.node_of_dof])[ins].max())
     assert errs[1] < errs[0] / 3.0
+
+
+def test_flexible_pcg_absorbs_a_varying_preconditioner():
+    """Flexible CG (Notay 2000) against classical CG when the preconditioner changes from
+    one application to the next: z = A^-1 r plus 30 % random noise drawn afresh at every
+    application (2-D Laplacian, 576 unknowns).  The flexible beta keeps the search
+    directions useful and converges to 1e-10 in a few tens of iterations; the classical
+    beta assumes one fixed symmetric M and does not converge in 300.  Together with the
+    fixed-preconditioner test above (where both betas agree, which rules out a sign or
+    denominator mistake) this pins the flexible branch."""
+    n = 24
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    A = np.kron(T, np.eye(n)) + np.kron(np.eye(n), T)
+    b = np.random.default_rng(0).normal(size=n * n)
+    Ainv = np.linalg.inv(A)
+
+    def varying(seed):
+        g = np.random.default_rng(seed)
+
+        def M(r):
+            z = Ainv @ r
+            return z + 0.3 * np.linalg.norm(z) * g.normal(size=z.size) / np.sqrt(z.size)
+        return M
+
+    flex = pcg(lambda x: A @ x, b, varying(1), rtol=1e-10, maxit=300, flexible=True)
+    classic = pcg(lambda x: A @ x, b, varying(1), rtol=1e-10, maxit=300)
+    assert flex["converged"] and flex["iterations"] <= 40 and flex["true_residual"] < 1e-9
+    assert not classic["converged"]
