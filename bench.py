@@ -313,7 +313,7 @@ def roofline_block(kt, n_steps, binfo, per_iter, iterations, fma, peaks, n_subte
     * per-iteration kernels: the bytes of per_iteration_roofline, timed once per PCG
       iteration plus the initial preconditioner application."""
     tf32 = peaks["bf16_tflops"] * NOMINAL_TENSOR["tf32"] / NOMINAL_TENSOR["bf16"]
-    f32_on_tc = binfo.get("local_tc", 0) == 1
+    f32_on_tc = binfo.get("local_tensor_cores", 0) == 1
     local_flops = binfo["inverse_flops_local"] / 3.0
     coarse_flops = binfo["inverse_flops_coarse"] / 3.0
     f64_flops = coarse_flops + (local_flops if binfo["fp64_refactor"] else 0.0)

@@ -284,6 +284,8 @@ typedef struct {
                               FP32 coarse basis (Sect. 3.2 defines Phi by C Phi = I); above 1e-2
                               the problem keeps FP64 local operators (fp64_refactor = 1) */
   int32_t coarse_layers, coarse_levels;   /* cyclic reduction: non-empty z layers, reduction levels */
+  int32_t local_tensor_cores;   /* 1 when the FP32 local inversions ran their Gauss-Jordan updates on the
+                                   tensor cores (3xTF32 split products, tcgen05), 0 otherwise */
 } ufe_bddc_info;
 
 /*

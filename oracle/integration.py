@@ -151,13 +151,27 @@ def integrate_cut_cell(phi8, f8, q8, h):
     Returns (K (8,8), load (8,), eta) with K = int grad N_a . grad N_b over e cap Omega_h,
     load = int f_h N_a + int_{Gamma_h cap e} (q_h . n) N_a, eta = |e cap Omega_h| / |e|.
     """
+    K, load, vol, _ = _cut_cell(phi8, f8, q8, h, None)
+    return K, load, vol
+
+
+def integrate_cut_cell_nitsche(phi8, f8, g8, h):
+    """Element data of one cut cell whose unfitted boundary carries weak Dirichlet data
+    (Sect. 2.2, Nitsche): K and load gain the Nitsche terms of oracle.nitsche with the Q1
+    interpolant of g8.  Returns (K, load, eta, beta_e)."""
+    return _cut_cell(phi8, f8, None, h, g8)
+
+
+def _cut_cell(phi8, f8, q8, h, g8):
     K = np.zeros((8, 8))
     load = np.zeros(8)
     vol = 0.0
+    facets = []
     for tet in KUHN_TETS:
         P = UNIT_VERTS[list(tet)]
         F = phi8[list(tet)]
         subtets, tris, normal = clip_tet(P, F)
+        facets.extend((T, normal) for T in tris)
         for T in subtets:
             v = abs(np.linalg.det(np.stack([T[1] - T[0], T[2] - T[0], T[3] - T[0]]))) / 6.0
             if v == 0.0:
@@ -179,7 +193,12 @@ def integrate_cut_cell(phi8, f8, q8, h):
                 N = q1_shape(xq)
                 gq = (N @ q8) @ normal            # (m,) q_h . n
                 load += (wq * gq) @ N * h ** 2
-    return K * h, load, vol
+    beta = 0.0
+    if g8 is not None:
+        from .nitsche import nitsche_cell
+        Nmat, nload, beta = nitsche_cell(K, facets, np.asarray(g8, dtype=np.float64), h)
+        return K * h + Nmat, load + nload, vol, beta
+    return K * h, load, vol, beta
 
 
 class Integration:
@@ -200,18 +219,27 @@ class Integration:
         self.K_cut = np.zeros((n_cut, 8, 8))
         self.load_cut = np.zeros((n_cut, 8))
         self.eta = np.zeros(n_cut)
+        weak = bool(getattr(problem, "weak_dirichlet", False))
+        gd = None if not weak else np.asarray(problem.dirichlet_values, dtype=np.float64)
         args = []
         for c in self.cut_cells:
             nodes = g.cell_nodes(c)
-            args.append((phi[nodes], f[nodes], None if q is None else q[nodes], g.h))
+            if weak:
+                args.append((phi[nodes], f[nodes], gd[nodes], g.h))
+            else:
+                args.append((phi[nodes], f[nodes], None if q is None else q[nodes], g.h))
+        fn = integrate_cut_cell_nitsche if weak else integrate_cut_cell
         if map_fn is None:
-            results = [integrate_cut_cell(*a) for a in args]
+            results = [fn(*a) for a in args]
         else:
-            results = map_fn(integrate_cut_cell, args)
-        for idx, (Ke, le, eta) in enumerate(results):
-            self.K_cut[idx] = Ke
-            self.load_cut[idx] = le
-            self.eta[idx] = eta
+            results = map_fn(fn, args)
+        self.beta = np.zeros(n_cut)
+        for idx, res in enumerate(results):
+            self.K_cut[idx] = res[0]
+            self.load_cut[idx] = res[1]
+            self.eta[idx] = res[2]
+            if weak:
+                self.beta[idx] = res[3]
         self.cut_index = {int(c): i for i, c in enumerate(self.cut_cells)}
         self.f = f
         self.kappa = (np.ones(g.n_cells) if problem.kappa is None

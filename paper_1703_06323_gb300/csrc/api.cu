@@ -98,6 +98,25 @@ static const T* stage(DBuf<T>& buf, const T* src, size_t n, int mem, cudaStream_
   return buf.p;
 }
 
+// The library's buffers are stream-ordered allocations from the device's default memory
+// pool.  With the pool's default release threshold (0) every synchronisation returns the
+// freed memory to the driver and the next set-up maps it again; a threshold of the whole
+// device keeps it cached in the pool for reuse (once per device, process-local).
+void keep_pool_memory() {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  UFE_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t keep = UINT64_MAX;
+  UFE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  done[dev] = true;
+}
+
 // FMA-rate probe: eight independent chains per thread keep every pipe slot busy
 template <typename T>
 __global__ void __launch_bounds__(256) k_fma_probe(int iters, T* out) {
@@ -209,6 +228,7 @@ ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const
     UFE_REQUIRE(box_lo && box_hi && cells && sub_cells && phi_nodes && out, UFE_ERR_INVALID_ARG, "null argument");
     check_mem(mem);
     *out = nullptr;
+    keep_pool_memory();
     std::unique_ptr<ufe_mesh> m(new ufe_mesh());
     m->stream = (cudaStream_t)stream;
     GridGeom& g = m->g;
@@ -488,6 +508,7 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->coarse_solver = B->coarse_dense ? UFE_COARSE_SOLVER_DENSE : UFE_COARSE_SOLVER_CR;
     info->coarse_layers = B->cr.nlayers;
     info->cphi_error = B->cphi_error;
+    info->local_tensor_cores = B->local_tc;
     info->coarse_levels = B->cr.nlevels;
   });
 }

@@ -837,6 +837,10 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   auto check = [&](const char* what) {
     std::vector<int> st = to_host(status.p, ns, s);
     for (int w = 0; w < ns; ++w)
+      UFE_REQUIRE(!(st[w] & DEV_TIMEOUT), UFE_ERR_TIMEOUT,
+                  std::string(what) + " of subdomain " + std::to_string(w) + ": a tensor-core copy or product did not "
+                  "complete in time");
+    for (int w = 0; w < ns; ++w)
       UFE_REQUIRE(st[w] == 0, UFE_ERR_SINGULAR_LOCAL,
                   std::string(what) + " of subdomain " + std::to_string(w) +
                       ((st[w] & DEV_SINGULAR) ? " is not positive definite" : " is too ill-conditioned"));
@@ -1184,9 +1188,11 @@ void bddc_build(Bddc& B) {
   DBuf<double> Acw, rho;
   if (B.mixed) {
     try {
+      B.local_tc = fp32_tensor_cores() ? 1 : 0;
       factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
                              ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho);
     } catch (const Error& e) {
+      B.local_tc = 0;
       if (e.code != UFE_ERR_SINGULAR_LOCAL) throw;
       // a scaled local matrix is too ill-conditioned for FP32 (tiny cut fractions):
       // this problem keeps FP64 local operators (factored and applied in FP64)

@@ -156,6 +156,7 @@ struct Bddc {
   double bytes_II = 0.0, bytes_GG = 0.0, bytes_GC = 0.0, bytes_off = 0.0, bytes_Ac = 0.0;
   int fp64_refactor = 0;                // mixed precision requested, FP64 local operators kept (FP32 too ill-conditioned)
   double cphi_error = 0.0;              // mixed: max |C Phi - I| of the FP32 operators
+  int local_tc = 0;                     // FP32 local inversions ran the tensor-core update
 
   SubMeta meta() const;
   ~Bddc();

@@ -29,6 +29,10 @@ void batched_gemm(bool transA, bool transB, const std::vector<GemmDesc>& descs, 
 template <typename T>
 void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T pivot_floor = T(0));
 
+// FP32 inversions use the tensor-core (3xTF32) update unless the environment variable
+// UFE_FP32_GJ is "simt" (the SIMT update, kept for comparison)
+bool fp32_tensor_cores();
+
 // in-place inverse of one large SPD matrix using the whole GPU
 template <typename T>
 void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s);

@@ -58,6 +58,8 @@ class Problem:
     meta: dict = dataclasses.field(default_factory=dict)
     ncomp: int = 1                          # 1 Poisson; 3 linear elasticity
     lame: Optional[tuple] = None            # elasticity: (E, nu); kappa then scales E per cell
+    weak_dirichlet: bool = False            # Poisson: Dirichlet data (dirichlet_values, Q1 interpolated)
+                                            # imposed weakly (Nitsche) on the unfitted boundary
 
     @property
     def n_nodes(self) -> int:
