@@ -66,6 +66,26 @@ def object_rows(obj, grid, mesh, ncomp):
     return rows
 
 
+def stiffness_weights(mesh, integ):
+    """Eq. alge-weighting per interface DOF d: {w: A^w_dd / sum_w' A^w'_dd} over neigh(d),
+    A^w_dd the diagonal of the local Neumann matrix (sum over the active cells of w that
+    contain the node)."""
+    g = mesh.grid
+    diag = {}
+    for w in range(mesh.n_sub):
+        for c in mesh.sub_cells[w]:
+            Ke = integ.stiffness(c)
+            for a, v in enumerate(g.cell_nodes(c)):
+                d = int(mesh.dof_of_node[v])
+                if d >= 0 and mesh.is_gamma[d]:
+                    diag[(d, w)] = diag.get((d, w), 0.0) + Ke[a, a]
+    out = {}
+    for d in np.flatnonzero(mesh.is_gamma):
+        tot = sum(diag[(int(d), w)] for w in mesh.neigh[d])
+        out[int(d)] = {w: diag[(int(d), w)] / tot for w in mesh.neigh[d]}
+    return out
+
+
 class BDDC:
     def __init__(self, mesh, integ, system, weighting="stiffness", objects="v1", coarse="cef",
                  all_interface_corners=False):
@@ -78,6 +98,9 @@ class BDDC:
             # enlarged coarse space of Sect. 4.2: every interface DOF is a corner
             objs = [{"dofs": [d], "neigh": mesh.neigh[d], "kind": 0}
                     for d in np.flatnonzero(mesh.is_gamma)]
+        elif objects == "v2":
+            # Sect. 4.5: the edges are split by the stiffness weights of Eq. alge-weighting
+            objs = coarse_objects(mesh.objects("v2", weights=stiffness_weights(mesh, integ)), coarse)
         else:
             objs = coarse_objects(mesh.objects(objects), coarse)
         self.objs = objs

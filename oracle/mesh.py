@@ -359,6 +359,40 @@ def variant1_objects(grid: Grid, cell_type, dof_of_node, phi, std_objs):
     return out
 
 
+V2_WEIGHT_TOL = 1e-8
+
+
+def variant2_objects(grid: Grid, cell_type, dof_of_node, std_objs, weights):
+    """Sect. 4.5: split each edge object into runs of FE-edge-adjacent DOFs with the same
+    stiffness weights; DOFs left alone become corners (reading R22: weights "the same" when
+    every subdomain's weight differs by at most V2_WEIGHT_TOL; weights[d] maps each
+    subdomain of neigh(d) to A^w_dd / sum_w' A^w'_dd)."""
+    node_of_dof = np.flatnonzero(dof_of_node >= 0)
+    out = []
+    for o in std_objs:
+        if o["kind"] != EDGE:
+            out.append(o)
+            continue
+        members = set(o["dofs"])
+
+        def same(a, b):
+            return max(abs(weights[a][w] - weights[b][w]) for w in o["neigh"]) <= V2_WEIGHT_TOL
+
+        def adjacent(d):
+            v = node_of_dof[d]
+            res = []
+            for w in _axis_neighbours(grid, v):
+                e = int(dof_of_node[w])
+                if e in members and fe_edge_exists(grid, cell_type, v, w) and same(d, e):
+                    res.append(e)
+            return res
+
+        for comp in _components(sorted(members), adjacent):
+            out.append({"dofs": comp, "neigh": o["neigh"], "kind": CORNER if len(comp) == 1 else EDGE})
+    out.sort(key=lambda o: o["dofs"][0])
+    return out
+
+
 def coarse_objects(objs, coarse: str):
     """Lambda_O: 'c' corners, 'ce' corners+edges, 'cef' all (Sect. 3.2)."""
     keep = {"c": (CORNER,), "ce": (CORNER, EDGE), "cef": (CORNER, EDGE, FACE)}[coarse]
@@ -384,10 +418,13 @@ class Mesh:
         self.is_gamma = np.array([len(ns) >= 2 for ns in self.neigh], dtype=bool)
         self._objects = {}
 
-    def objects(self, variant: str = "v1"):
+    def objects(self, variant: str = "v1", weights=None):
+        """Objects of variant 'std', 'v1' or 'v2' (v2 needs the stiffness weights per DOF)."""
         if "std" not in self._objects:
             self._objects["std"] = standard_objects(self.grid, self.cell_type, self.dof_of_node, self.neigh)
         if variant == "v1" and "v1" not in self._objects:
             self._objects["v1"] = variant1_objects(self.grid, self.cell_type, self.dof_of_node,
                                                    self.phi, self._objects["std"])
+        if variant == "v2":
+            return variant2_objects(self.grid, self.cell_type, self.dof_of_node, self._objects["std"], weights)
         return self._objects[variant]

@@ -116,3 +116,37 @@ def test_weak_dirichlet_sphere_second_order():
         inside = p.phi[m.node_of_dof] < 0
         errs.append(np.abs(x - p.u_exact[m.node_of_dof])[inside].max())
     assert errs[1] < errs[0] / 3.0, errs
+
+
+def test_variant2_objects():
+    """Sect. 4.5 objects: on an uncut box the stiffness weights are constant along every
+    edge, so variant 2 leaves the standard objects unchanged; on a sphere with weak
+    Dirichlet data the split edges make BDDC no worse than the standard and variant-1
+    objects (the paper's robust choice for Nitsche, Sect. 5.2), and every variant-2
+    edge carries constant weights."""
+    from oracle.bddc import BDDC, stiffness_weights
+    from oracle.mesh import EDGE
+    from oracle.pcg import pcg
+    box = inputs.box_problem(cells=(8, 8, 8), sub_cells=(4, 4, 4))
+    m = Mesh(box)
+    integ = Integration(m, box)
+    w = stiffness_weights(m, integ)
+    assert m.objects("v2", weights=w) == m.objects("std")
+
+    p = inputs.sphere_problem(cells=(16, 16, 16), sub_cells=(4, 4, 4), centre=(0.51, 0.49, 0.5), radius=0.4,
+                              dirichlet_face_mask=inputs.ALL_FACES, pin_node=inputs.PIN_NONE)
+    p.q = None
+    p.weak_dirichlet = True
+    m = Mesh(p)
+    integ = Integration(m, p)
+    S = System(m, integ, p)
+    w = stiffness_weights(m, integ)
+    v2 = m.objects("v2", weights=w)
+    assert len(v2) > len(m.objects("std"))
+    for o in v2:
+        if o["kind"] == EDGE:
+            for d in o["dofs"][1:]:
+                assert max(abs(w[d][s] - w[o["dofs"][0]][s]) for s in o["neigh"]) <= 2e-8
+    its = {ob: pcg(S.apply, S.b, BDDC(m, integ, S, objects=ob, coarse="cef").apply, rtol=1e-8)["iterations"]
+           for ob in ("std", "v1", "v2")}
+    assert its["v2"] <= its["v1"] <= its["std"], its
