@@ -68,6 +68,8 @@ typedef int ufe_status;
 /* ufe_bddc_opts.objects */
 #define UFE_OBJECTS_STANDARD 0     /* Sect. 3.2 */
 #define UFE_OBJECTS_VARIANT1 1     /* Sect. 4.4: cut coarse edges split */
+#define UFE_OBJECTS_VARIANT2 2     /* Sect. 4.5: coarse edges split into runs of equal stiffness weights
+                                      (two weights equal when they differ by at most 1e-8); Poisson */
 /* ufe_bddc_opts.coarse: which objects carry a coarse DOF (Sect. 3.2) */
 #define UFE_COARSE_C   0
 #define UFE_COARSE_CE  1
@@ -204,6 +206,31 @@ void ufe_mesh_destroy(ufe_mesh* mesh);
 ufe_status ufe_assemble(ufe_mesh* mesh, const double* kappa_cells, const double* f_nodes,
                         const double* flux_nodes, const double* dirichlet_values, int mem,
                         ufe_system** out);
+/*
+ * ufe_assemble_nitsche -- Poisson with weak Dirichlet data on the unfitted boundary
+ * (Sect. 2.2, Nitsche's method; the boundary condition of the paper's Dirichlet
+ * experiments, Sect. 5.1).  Each cut cell's form gains
+ *   int_{Gamma cap e} ( beta_e u v - v (n . grad u) - u (n . grad v) ) dS
+ * and its load int_{Gamma cap e} ( beta_e v g - (n . grad v) g ) dS, with g the Q1
+ * interpolant of dirichlet_values, n the outward normal of the marching-tetrahedra
+ * boundary and beta_e = 2 C_e, C_e the largest eigenvalue of the cell's generalised
+ * eigenproblem B_e x = C D_e x (Eq. local-eigenvals; D_e the cut-cell stiffness, B_e
+ * the boundary form of the normal derivatives; both vanish on the constants).  Box
+ * faces of the mesh's dirichlet_face_mask keep strong Dirichlet values; use
+ * ufe_mesh_create with pin_node = -1 (the weak condition fixes the constant).
+ *
+ *  f_nodes           n_nodes doubles: nodal source (Q1 interpolated), or NULL for 0.
+ *  dirichlet_values  n_nodes doubles: the Dirichlet data, weak on the unfitted
+ *                    boundary and strong at the constrained box nodes (required).
+ * Errors: INVALID_ARG, SINGULAR_LOCAL (a cell's eigenproblem has no positive
+ * largest eigenvalue), CUDA, OUT_OF_MEMORY.
+ */
+ufe_status ufe_assemble_nitsche(ufe_mesh* mesh, const double* f_nodes, const double* dirichlet_values, int mem,
+                                ufe_system** out);
+/* beta: n_cut doubles, the Nitsche coefficient beta_e of each cut cell in cut-cell order
+ * (physical units, 0 for a cell without boundary area); INVALID_ARG for a system
+ * assembled without weak Dirichlet data. */
+ufe_status ufe_system_get_nitsche_beta(const ufe_system* sys, double* beta, int mem);
 /*
  * ufe_assemble_elastic -- the vector-valued (Q1^3) variant: isotropic linear
  * elasticity on the same unfitted mesh (no counterpart in the paper, which treats

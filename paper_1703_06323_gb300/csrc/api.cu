@@ -351,6 +351,38 @@ ufe_status ufe_assemble(ufe_mesh* m, const double* kappa, const double* f, const
   });
 }
 
+ufe_status ufe_assemble_nitsche(ufe_mesh* m, const double* f, const double* gval, int mem, ufe_system** out) {
+  return guarded([&] {
+    UFE_REQUIRE(m && gval && out, UFE_ERR_INVALID_ARG, "null argument");
+    check_mem(mem);
+    *out = nullptr;
+    std::unique_ptr<ufe_system> sys(new ufe_system());
+    sys->mesh = m;
+    sys->stream = m->stream;
+    cudaStream_t s = m->stream;
+    const int64_t nn = m->g.n_nodes();
+    DBuf<double> fb, gb;
+    const double* fd = stage(fb, f, nn, mem, s);
+    const double* gd = stage(gb, gval, nn, mem, s);
+    TimedLaunch tl;
+    tl.begin("phase_assemble", s);
+    system_build(*sys, nullptr, fd, nullptr, gd, true);
+    tl.end(s);
+    UFE_CUDA(cudaStreamSynchronize(s));
+    *out = sys.release();
+  });
+}
+
+ufe_status ufe_system_get_nitsche_beta(const ufe_system* sys, double* beta, int mem) {
+  return guarded([&] {
+    UFE_REQUIRE(sys && beta, UFE_ERR_INVALID_ARG, "null argument");
+    UFE_REQUIRE(sys->nitsche, UFE_ERR_INVALID_ARG, "the system has no weak Dirichlet data");
+    check_mem(mem);
+    if (sys->mesh->n_cut > 0) copy_out(beta, sys->beta.p, sys->mesh->n_cut * 8, mem, sys->stream);
+    UFE_CUDA(cudaStreamSynchronize(sys->stream));
+  });
+}
+
 ufe_status ufe_system_set_kappa(ufe_system* sys, const double* kappa, int mem) {
   return guarded([&] {
     UFE_REQUIRE(sys && kappa, UFE_ERR_INVALID_ARG, "null argument");
@@ -462,8 +494,11 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     UFE_REQUIRE(sys && opts && out, UFE_ERR_INVALID_ARG, "null argument");
     UFE_REQUIRE(opts->weighting == UFE_WEIGHT_STIFFNESS || opts->weighting == UFE_WEIGHT_TOPOLOGICAL,
                 UFE_ERR_INVALID_ARG, "bad weighting");
-    UFE_REQUIRE(opts->objects == UFE_OBJECTS_STANDARD || opts->objects == UFE_OBJECTS_VARIANT1, UFE_ERR_INVALID_ARG,
-                "bad objects");
+    UFE_REQUIRE(opts->objects == UFE_OBJECTS_STANDARD || opts->objects == UFE_OBJECTS_VARIANT1 ||
+                    opts->objects == UFE_OBJECTS_VARIANT2,
+                UFE_ERR_INVALID_ARG, "bad objects");
+    UFE_REQUIRE(opts->objects != UFE_OBJECTS_VARIANT2 || sys->ncomp == 1, UFE_ERR_UNSUPPORTED,
+                "variant-2 objects: Poisson systems only");
     UFE_REQUIRE(opts->coarse >= UFE_COARSE_C && opts->coarse <= UFE_COARSE_CEF, UFE_ERR_INVALID_ARG, "bad coarse");
     UFE_REQUIRE(opts->coarse_solver >= UFE_COARSE_SOLVER_AUTO && opts->coarse_solver <= UFE_COARSE_SOLVER_CR,
                 UFE_ERR_INVALID_ARG, "bad coarse solver");

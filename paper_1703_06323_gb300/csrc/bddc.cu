@@ -126,11 +126,14 @@ __device__ __forceinline__ void for_fe_neighbours(const GridGeom& g, const int32
 
 // min-label propagation; mode 0: interface DOFs with equal neigh sets (standard
 // objects); mode 1: non-corner DOFs of one edge object joined by uncut FE edges
+constexpr double kV2WeightTol = 1e-8;
+
 __global__ void k_obj_propagate(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
                                 const int32_t* __restrict__ dof_of_node, const uint8_t* __restrict__ cell_type,
                                 const int32_t* __restrict__ neigh, const uint8_t* __restrict__ nn,
                                 const double* __restrict__ phi, const int32_t* __restrict__ std_obj,
-                                const uint8_t* __restrict__ active, int mode, int32_t* label, int* changed) {
+                                const uint8_t* __restrict__ active, int mode, const double* __restrict__ wv2,
+                                int32_t* label, int* changed) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n_dof || !active[d]) return;
   int32_t m = label[d];
@@ -139,9 +142,13 @@ __global__ void k_obj_propagate(GridGeom g, int64_t n_dof, const int32_t* __rest
     if (!active[e]) return;
     if (mode == 0) {
       if (!same_neigh(neigh, nn, d, e)) return;
-    } else {
+    } else if (mode == 1) {
       if (std_obj[e] != std_obj[d]) return;
       if ((phi[wv] < 0.0) != in_d) return;
+    } else {
+      if (std_obj[e] != std_obj[d]) return;
+      for (int t = 0; t < nn[d]; ++t)   // d and e share one neigh list (same object)
+        if (fabs(wv2[d * 8 + t] - wv2[e * 8 + t]) > kV2WeightTol) return;
     }
     const int32_t l = label[e];
     if (l < m) m = l;
@@ -152,6 +159,50 @@ __global__ void k_obj_propagate(GridGeom g, int64_t n_dof, const int32_t* __rest
     label[d] = m;
     *changed = 1;
   }
+}
+
+// variant 2 (Sect. 4.5): stiffness weight of every (interface DOF, neigh slot), the slot's
+// subdomain's diagonal A^w_dd (sum over its active cells containing the node, kappa
+// included) over the sum of all neigh slots' diagonals
+__global__ void k_v2_weights(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                             const uint8_t* __restrict__ cell_type, const int32_t* __restrict__ sub_of_cell,
+                             const int32_t* __restrict__ cut_index, const double* __restrict__ K_cut,
+                             const double* __restrict__ kappa, const int32_t* __restrict__ neigh,
+                             const uint8_t* __restrict__ nn, double* __restrict__ w) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof || nn[d] < 2) return;
+  const int64_t v = node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  double diag[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < 8; ++a) {   // the cell whose vertex a is this node
+    const int ci = i - (a & 1), cj = j - ((a >> 1) & 1), ck = k - (a >> 2);
+    if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
+    const int64_t c = ci + (int64_t)g.nx * (cj + (int64_t)g.ny * ck);
+    if (cell_type[c] == UFE_CELL_EXTERNAL) continue;
+    const int32_t idx = cut_index[c];
+    double kaa = idx >= 0 ? K_cut[(int64_t)idx * 64 + a * 9] : g.h * q1_khat(a, a);
+    if (kappa) kaa *= kappa[c];
+    const int32_t sub = sub_of_cell[c];
+    for (int t = 0; t < nn[d]; ++t)
+      if (neigh[d * 8 + t] == sub) diag[t] += kaa;
+  }
+  double sum = 0.0;
+  for (int t = 0; t < nn[d]; ++t) sum += diag[t];
+  for (int t = 0; t < nn[d]; ++t) w[d * 8 + t] = diag[t] / sum;
+}
+
+// variant 2: every DOF of an edge object takes part in the relabelling, from its own id
+__global__ void k_v2_prepare(int64_t n_dof, const int32_t* __restrict__ obj_of_dof, const int32_t* __restrict__ obj_kind,
+                             uint8_t* __restrict__ corner, uint8_t* __restrict__ active, int32_t* __restrict__ label2,
+                             const int32_t* __restrict__ label) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof) return;
+  const int32_t o = obj_of_dof[d];
+  const bool is_edge = o >= 0 && obj_kind[o] == UFE_OBJ_EDGE;
+  corner[d] = 0;
+  active[d] = is_edge ? 1 : 0;
+  label2[d] = is_edge ? (int32_t)d : label[d];
 }
 
 // variant 1: DOFs of edge objects incident to a cut FE edge of the same object
@@ -763,7 +814,7 @@ __global__ void k_scale_ptr(int64_t n, int nc, const int32_t* __restrict__ in, i
 // host driver
 // ---------------------------------------------------------------------------
 static void propagate(const Mesh& m, const Bddc& B, const uint8_t* active, int mode, const int32_t* std_obj,
-                      int32_t* label) {
+                      int32_t* label, const double* wv2 = nullptr) {
   cudaStream_t s = B.stream;
   DBuf<int> changed;
   changed.alloc(1, s);
@@ -772,7 +823,7 @@ static void propagate(const Mesh& m, const Bddc& B, const uint8_t* active, int m
     for (int rep = 0; rep < 4; ++rep) {
       k_obj_propagate<<<grid_for(m.n_dof, 256), 256, 0, s>>>(m.g, m.n_dof, m.node_of_dof.p, m.dof_of_node.p,
                                                              m.cell_type.p, m.neigh.p, m.n_neigh.p, m.phi.p, std_obj,
-                                                             active, mode, label, changed.p);
+                                                             active, mode, wv2, label, changed.p);
       UFE_CHECK_LAUNCH();
     }
     if (scalar_to_host(changed.p, s) == 0) return;
@@ -990,16 +1041,31 @@ void bddc_build(Bddc& B) {
     UFE_CHECK_LAUNCH();
   }
 
-  // ---- variant 1 (Sect. 4.4): split the edge objects at their cut FE edges
-  if (B.opts.objects == UFE_OBJECTS_VARIANT1 && n_obj) {
+  // ---- variant 1 (Sect. 4.4): split the edge objects at their cut FE edges;
+  //      variant 2 (Sect. 4.5): split them into runs of equal stiffness weights
+  if ((B.opts.objects == UFE_OBJECTS_VARIANT1 || B.opts.objects == UFE_OBJECTS_VARIANT2) && n_obj) {
     DBuf<uint8_t> corner;
     DBuf<int32_t> label2;
+    DBuf<double> wv2;
     corner.alloc(nd, s);
     label2.alloc(nd, s);
-    k_v1_corners<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p, m.phi.p,
-                                               B.obj_of_dof.p, B.obj_kind.p, corner.p, active.p, label2.p, label.p);
-    UFE_CHECK_LAUNCH();
-    propagate(m, B, active.p, 1, B.obj_of_dof.p, label2.p);
+    if (B.opts.objects == UFE_OBJECTS_VARIANT1) {
+      k_v1_corners<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p, m.phi.p,
+                                                 B.obj_of_dof.p, B.obj_kind.p, corner.p, active.p, label2.p, label.p);
+      UFE_CHECK_LAUNCH();
+      propagate(m, B, active.p, 1, B.obj_of_dof.p, label2.p);
+    } else {
+      wv2.alloc(std::max<int64_t>(nd, 1) * 8, s);
+      k_v2_weights<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, m.cell_type.p, m.sub_of_cell.p,
+                                                 m.cut_index.p, B.sys->K_cut.p,
+                                                 B.sys->has_kappa ? B.sys->kappa.p : nullptr, m.neigh.p, m.n_neigh.p,
+                                                 wv2.p);
+      UFE_CHECK_LAUNCH();
+      k_v2_prepare<<<grid_for(nd, T), T, 0, s>>>(nd, B.obj_of_dof.p, B.obj_kind.p, corner.p, active.p, label2.p,
+                                                 label.p);
+      UFE_CHECK_LAUNCH();
+      propagate(m, B, active.p, 2, B.obj_of_dof.p, label2.p, wv2.p);
+    }
     k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label2.p, flags.p);
     UFE_CHECK_LAUNCH();
     const int64_t n_obj2 = scan_flags(flags.p, nd, rep_index.p, s);

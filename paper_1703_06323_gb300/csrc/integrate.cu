@@ -477,7 +477,306 @@ void launch_cut_list(const Mesh& m, cudaStream_t s) {
   UFE_CHECK_LAUNCH();
 }
 
-void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* gval) {
+// ---------------------------------------------------------------------------
+// Weak Dirichlet data on the unfitted boundary (Nitsche, Sect. 2.2).  Every cut cell
+// gains h (beta M - C - C^T) in its matrix and h (beta M g - C^T g) in its load, with
+// the unit-cube facet forms
+//   M_ab = int N_a N_b dS,  C_ab = int N_a (n . grad N_b) dS,  B_ab = int (n . grad N_a)(n . grad N_b) dS
+// over the cell's boundary triangles (the same marching-tetrahedra surface as the
+// Neumann data), g the Q1 interpolant of the nodal Dirichlet values, and beta = 2 C_e
+// (unit-cube; C_e the largest eigenvalue of B x = lambda D x on the complement of the
+// constants, D the cut-cell stiffness, Eq. local-eigenvals).  C_e is computed after a
+// symmetric Jacobi scaling by diag(D)^-1/2, in an orthonormal (Householder) basis of the
+// complement of the scaled kernel vector, by a Cholesky reduction to a 7 x 7 symmetric
+// matrix and cyclic Jacobi rotations.
+//
+// One warp per cut cell.  Six lanes clip the Kuhn tets (the triangles are kept); the
+// facet points are taken 32 at a time: each lane evaluates N and n . grad N of one
+// point into shared memory, then each lane accumulates its entries of M, B (36 unique
+// each) and C (64) over the 32 points in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kNiWarps = 4;
+constexpr int kNiEntries = 36 + 36 + 64;
+constexpr int kNiPerLane = (kNiEntries + 31) / 32;
+
+// largest eigenvalue of B x = lambda D x on the complement of the constants (8 x 8,
+// row-major, both symmetric with the constants in their kernel); w: kNiScratch doubles
+constexpr int kNiScratch = 56 + 4 * 49 + 8;
+__device__ double nitsche_constant(const double* __restrict__ D, const double* __restrict__ B, double* w) {
+  double* V = w;            // 8 x 7 orthonormal basis of the complement of the scaled kernel vector
+  double* L = w + 56;       // 7 x 7: S D S in the basis, then its Cholesky factor (lower)
+  double* B7 = w + 105;     // 7 x 7: S B S in the basis
+  double* Y = w + 154;      // 7 x 7: L^-1 B7
+  double* G = w + 203;      // 7 x 7: L^-1 B7 L^-T
+  double* T = w + 252;      // 8
+  double s[8], v[8];
+  double kn = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    s[a] = 1.0 / sqrt(D[a * 8 + a]);
+    v[a] = sqrt(D[a * 8 + a]);   // kernel of S D S: S^-1 (1, ..., 1)
+    kn += D[a * 8 + a];
+  }
+  kn = sqrt(kn);
+  for (int a = 0; a < 8; ++a) v[a] /= kn;
+  v[0] += v[0] >= 0.0 ? 1.0 : -1.0;   // Householder vector: H maps the kernel vector to -+e_0
+  double vv = 0.0;
+  for (int a = 0; a < 8; ++a) vv += v[a] * v[a];
+  for (int a = 0; a < 8; ++a)
+    for (int c = 1; c < 8; ++c) V[a * 7 + (c - 1)] = (a == c ? 1.0 : 0.0) - 2.0 * v[a] * v[c] / vv;
+  // L = V^T S D S V, B7 = V^T S B S V (each entry once, mirrored)
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* X = pass == 0 ? D : B;
+    double* Z = pass == 0 ? L : B7;
+    for (int j = 0; j < 7; ++j) {
+      for (int a = 0; a < 8; ++a) {
+        double t = 0.0;
+        for (int b = 0; b < 8; ++b) t += X[a * 8 + b] * (s[b] * V[b * 7 + j]);
+        T[a] = s[a] * t;
+      }
+      for (int i = j; i < 7; ++i) {
+        double t = 0.0;
+        for (int a = 0; a < 8; ++a) t += V[a * 7 + i] * T[a];
+        Z[i * 7 + j] = t;
+        Z[j * 7 + i] = t;
+      }
+    }
+  }
+  // Cholesky: L (lower triangle) with L L^T = the scaled D in the basis
+  for (int j = 0; j < 7; ++j) {
+    double d = L[j * 7 + j];
+    for (int m = 0; m < j; ++m) d -= L[j * 7 + m] * L[j * 7 + m];
+    if (!(d > 0.0)) return nan("");
+    d = sqrt(d);
+    L[j * 7 + j] = d;
+    for (int i = j + 1; i < 7; ++i) {
+      double t = L[i * 7 + j];
+      for (int m = 0; m < j; ++m) t -= L[i * 7 + m] * L[j * 7 + m];
+      L[i * 7 + j] = t / d;
+    }
+  }
+  // Y = L^-1 B7, G = L^-1 Y^T (= L^-1 B7 L^-T, B7 symmetric), column by column
+  for (int c = 0; c < 7; ++c)
+    for (int i = 0; i < 7; ++i) {
+      double t = B7[i * 7 + c];
+      for (int m = 0; m < i; ++m) t -= L[i * 7 + m] * Y[m * 7 + c];
+      Y[i * 7 + c] = t / L[i * 7 + i];
+    }
+  for (int c = 0; c < 7; ++c)
+    for (int i = 0; i < 7; ++i) {
+      double t = Y[c * 7 + i];
+      for (int m = 0; m < i; ++m) t -= L[i * 7 + m] * G[m * 7 + c];
+      G[i * 7 + c] = t / L[i * 7 + i];
+    }
+  for (int i = 0; i < 7; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double t = 0.5 * (G[i * 7 + j] + G[j * 7 + i]);
+      G[i * 7 + j] = t;
+      G[j * 7 + i] = t;
+    }
+  // cyclic Jacobi rotations (bounded number of sweeps)
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < 7; ++i)
+      for (int j = 0; j < 7; ++j) {
+        tot += G[i * 7 + j] * G[i * 7 + j];
+        if (i != j) off += G[i * 7 + j] * G[i * 7 + j];
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < 6; ++p)
+      for (int q = p + 1; q < 7; ++q) {
+        const double apq = G[p * 7 + q];
+        if (apq == 0.0) continue;
+        const double theta = (G[q * 7 + q] - G[p * 7 + p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < 7; ++r) {   // G <- G J (columns p, q)
+          const double gp = G[r * 7 + p], gq = G[r * 7 + q];
+          G[r * 7 + p] = c * gp - sn * gq;
+          G[r * 7 + q] = sn * gp + c * gq;
+        }
+        for (int r = 0; r < 7; ++r) {   // G <- J^T G (rows p, q)
+          const double gp = G[p * 7 + r], gq = G[q * 7 + r];
+          G[p * 7 + r] = c * gp - sn * gq;
+          G[q * 7 + r] = sn * gp + c * gq;
+        }
+      }
+  }
+  double lmax = G[0];
+  for (int i = 1; i < 7; ++i) lmax = fmax(lmax, G[i * 7 + i]);
+  return lmax;
+}
+
+__global__ void __launch_bounds__(kNiWarps * 32)
+k_nitsche_cut(GridGeom g, int64_t n_cut, const int32_t* __restrict__ cut_cells, const double* __restrict__ phi,
+              const double* __restrict__ gD, double* __restrict__ K_cut, double* __restrict__ load_cut,
+              double* __restrict__ beta_out, int* __restrict__ status) {
+  __shared__ double s_tri[kTriPts * 4];
+  __shared__ double tris[kNiWarps][kMaxTris][12];
+  __shared__ double s_pt[kNiWarps][32][17];
+  __shared__ double s_mat[kNiWarps][kNiEntries];
+  __shared__ double s_work[kNiWarps][64 + kNiScratch];
+  __shared__ double s_beta[kNiWarps];
+  for (int e = threadIdx.x; e < kTriPts; e += blockDim.x) {
+    for (int c = 0; c < 3; ++c) s_tri[e * 4 + c] = c_tri_bary[e * 3 + c];
+    s_tri[e * 4 + 3] = c_tri_w[e];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t kc = (int64_t)blockIdx.x * kNiWarps + warp;
+  const bool valid = kc < n_cut;
+  int ntri_l = 0;
+  double st[3][12], tr[2][12];
+  int cell_i = 0, cell_j = 0, cell_k = 0;
+  if (valid) {
+    const int64_t c = cut_cells[kc];
+    cell_i = (int)(c % g.nx);
+    cell_j = (int)((c / g.nx) % g.ny);
+    cell_k = (int)(c / ((int64_t)g.nx * g.ny));
+    if (lane < 6) {
+      const int ax0[6] = {0, 0, 1, 1, 2, 2};
+      const int ax1[6] = {1, 2, 0, 2, 0, 1};
+      const int vid[4] = {0, 1 << ax0[lane], (1 << ax0[lane]) | (1 << ax1[lane]), 7};
+      Vec3 P[4];
+      double F[4];
+      for (int m = 0; m < 4; ++m) {
+        P[m] = {(double)(vid[m] & 1), (double)((vid[m] >> 1) & 1), (double)(vid[m] >> 2)};
+        F[m] = phi[g.node(cell_i + (vid[m] & 1), cell_j + ((vid[m] >> 1) & 1), cell_k + (vid[m] >> 2))];
+      }
+      int nst = 0;
+      const bool full = F[0] < 0.0 && F[1] < 0.0 && F[2] < 0.0 && F[3] < 0.0;
+      if (!full) clip_tet(P, F, st, nst, tr, ntri_l);
+    }
+  }
+  int off = ntri_l;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const int a = __shfl_up_sync(0xffffffffu, off, o);
+    if (lane >= o) off += a;
+  }
+  const int ntri = __shfl_sync(0xffffffffu, off, 7);
+  off -= ntri_l;
+  for (int a = 0; a < ntri_l; ++a)
+    for (int e = 0; e < 12; ++e) tris[warp][off + a][e] = tr[a][e];
+  __syncthreads();
+  // entry e of this lane: M (0..35), B (36..71) as packed upper triangles, C (72..135) row-major
+  int ea[kNiPerLane], eb[kNiPerLane], ek[kNiPerLane];
+  double acc[kNiPerLane];
+#pragma unroll
+  for (int t = 0; t < kNiPerLane; ++t) {
+    const int e = lane + 32 * t;
+    acc[t] = 0.0;
+    ek[t] = e < 36 ? 0 : (e < 72 ? 1 : (e < kNiEntries ? 2 : 3));
+    int r = e < 36 ? e : (e < 72 ? e - 36 : e - 72);
+    if (ek[t] <= 1) {
+      int a = 0;
+      while (r >= 8 - a) {
+        r -= 8 - a;
+        ++a;
+      }
+      ea[t] = a;
+      eb[t] = a + r;
+    } else {
+      ea[t] = (r / 8) & 7;
+      eb[t] = r % 8;
+    }
+  }
+  const int npts = valid ? ntri * kTriPts : 0;
+  for (int base = 0; base < npts; base += 32) {
+    const int it = base + lane;
+    double* P = s_pt[warp][lane];
+    if (it < npts) {
+      const double* T = tris[warp][it / kTriPts];
+      const double* R = s_tri + (it % kTriPts) * 4;
+      const double ux = T[3] - T[0], uy = T[4] - T[1], uz = T[5] - T[2];
+      const double vx = T[6] - T[0], vy = T[7] - T[1], vz = T[8] - T[2];
+      const double cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
+      const double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+      const double px = R[0] * T[0] + R[1] * T[3] + R[2] * T[6];
+      const double py = R[0] * T[1] + R[1] * T[4] + R[2] * T[7];
+      const double pz = R[0] * T[2] + R[1] * T[5] + R[2] * T[8];
+      double N[8], G[8][3];
+      q1_shape_grad(px, py, pz, N, G);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        P[a] = N[a];
+        P[8 + a] = G[a][0] * T[9] + G[a][1] * T[10] + G[a][2] * T[11];
+      }
+      P[16] = R[3] * area;
+    } else {
+      P[16] = 0.0;
+    }
+    __syncwarp();
+    const int cnt = min(32, npts - base);
+    for (int q = 0; q < cnt; ++q) {
+      const double* Q = s_pt[warp][q];
+      const double wq = Q[16];
+#pragma unroll
+      for (int t = 0; t < kNiPerLane; ++t) {
+        const double x = ek[t] == 1 ? Q[8 + ea[t]] : Q[ea[t]];
+        const double y = ek[t] == 0 ? Q[eb[t]] : Q[8 + eb[t]];
+        if (ek[t] < 3) acc[t] = fma(wq * x, y, acc[t]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int t = 0; t < kNiPerLane; ++t)
+    if (ek[t] < 3) s_mat[warp][lane + 32 * t] = acc[t];
+  __syncwarp();
+  const double h = g.h;
+  if (valid && lane == 0) {
+    double beta = 0.0;
+    if (ntri > 0) {
+      double* D = s_work[warp];
+      double Bf[64];
+      const double* M = s_mat[warp];
+      for (int a = 0; a < 8; ++a)
+        for (int b = a; b < 8; ++b) {
+          const int pk = a * 8 - (a * (a - 1)) / 2 + (b - a);
+          Bf[a * 8 + b] = Bf[b * 8 + a] = M[36 + pk];
+        }
+      bool any = false;
+      for (int e = 0; e < 64; ++e) any = any || Bf[e] != 0.0;
+      if (any) {
+        for (int e = 0; e < 64; ++e) D[e] = K_cut[kc * 64 + e] / h;
+        const double lam = nitsche_constant(D, Bf, s_work[warp] + 64);
+        if (!(lam >= 0.0) || !isfinite(lam)) atomicOr(status, DEV_SINGULAR);
+        beta = 2.0 * lam;
+      }
+    }
+    s_beta[warp] = beta;
+  }
+  __syncwarp();
+  if (!valid) return;
+  const double beta = s_beta[warp];
+  const double* M = s_mat[warp];
+  const double* C = s_mat[warp] + 72;
+  auto msym = [&](int a, int b) {
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    return M[a * 8 - (a * (a - 1)) / 2 + (b - a)];
+  };
+  for (int e = lane; e < 64; e += 32) {
+    const int a = e >> 3, b = e & 7;
+    K_cut[kc * 64 + e] += h * (beta * msym(a, b) - C[a * 8 + b] - C[b * 8 + a]);
+  }
+  if (lane < 8) {
+    const int a = lane;
+    double mg = 0.0, cg = 0.0;
+    for (int b = 0; b < 8; ++b) {
+      const double gb = gD[g.node(cell_i + (b & 1), cell_j + ((b >> 1) & 1), cell_k + (b >> 2))];
+      mg += msym(a, b) * gb;
+      cg += C[b * 8 + a] * gb;
+    }
+    load_cut[kc * 8 + a] += h * (beta * mg - cg);
+  }
+  if (lane == 0) beta_out[kc] = beta / h;
+}
+
+void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* gval,
+                  bool weak_dirichlet) {
   ensure_constants();
   Mesh& m = *sys.mesh;
   cudaStream_t s = sys.stream;
@@ -494,6 +793,24 @@ void system_build(System& sys, const double* kappa, const double* f, const doubl
         m.g, n_cut, m.cut_cells.p, m.phi.p, f, q, sys.K_cut.p, sys.load_cut.p, sys.eta.p);
     UFE_CHECK_LAUNCH();
     tl.end(s);
+  }
+  sys.nitsche = weak_dirichlet;
+  if (weak_dirichlet) {
+    UFE_REQUIRE(gval != nullptr && q == nullptr, UFE_ERR_INVALID_ARG,
+                "weak Dirichlet data need nodal values and no Neumann flux");
+    sys.beta.alloc(n_cut > 0 ? n_cut : 1, s);
+    sys.beta.zero();
+    if (n_cut > 0) {
+      DBuf<int> st;
+      st.alloc(1, s);
+      st.zero();
+      k_nitsche_cut<<<grid_for(n_cut, kNiWarps), kNiWarps * 32, 0, s>>>(m.g, n_cut, m.cut_cells.p, m.phi.p, gval,
+                                                                        sys.K_cut.p, sys.load_cut.p, sys.beta.p,
+                                                                        st.p);
+      UFE_CHECK_LAUNCH();
+      UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_LOCAL,
+                  "a cut cell's Nitsche eigenproblem has no positive largest eigenvalue");
+    }
   }
   sys.gnode.alloc(m.g.n_nodes(), s);
   if (gval)

@@ -185,6 +185,8 @@ struct System {
   DBuf<double> b;           // ncomp * n_dof
   DBuf<double> gnode;       // ncomp * n_nodes: Dirichlet values read at constrained nodes (zeros if none given)
   DBuf<double> fnode;       // Poisson: nodal source (zeros if none given), kept to rebuild b after a kappa update
+  bool nitsche = false;     // weak Dirichlet data on the unfitted boundary (Nitsche terms in K_cut, load_cut)
+  DBuf<double> beta;        // n_cut Nitsche coefficients beta_e (physical units; 0 without boundary)
   int64_t n_vec() const { return (int64_t)ncomp * mesh->n_dof; }
 };
 
@@ -199,7 +201,8 @@ int64_t scan_flags(const uint8_t* flags, int64_t n, int32_t* index_out, cudaStre
 int64_t scan_counts(const int32_t* counts, int64_t n, int32_t* offsets_out, cudaStream_t s);
 
 void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node);
-void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* g);
+void system_build(System& sys, const double* kappa, const double* f, const double* q, const double* g,
+                  bool weak_dirichlet = false);
 // Poisson: b rebuilt from the kept source, cut loads and Dirichlet values after sys.kappa changed
 void system_rebuild_rhs(System& sys);
 // elasticity: f 3 values per node, sigma 9 per node (may be null), g 3 per node (may be null)

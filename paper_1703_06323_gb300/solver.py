@@ -10,7 +10,7 @@ import numpy as np
 from . import ufe
 
 WEIGHTING = {"stiffness": ufe.WEIGHT_STIFFNESS, "topological": ufe.WEIGHT_TOPOLOGICAL}
-OBJECTS = {"std": ufe.OBJECTS_STANDARD, "v1": ufe.OBJECTS_VARIANT1}
+OBJECTS = {"std": ufe.OBJECTS_STANDARD, "v1": ufe.OBJECTS_VARIANT1, "v2": ufe.OBJECTS_VARIANT2}
 COARSE = {"c": ufe.COARSE_C, "ce": ufe.COARSE_CE, "cef": ufe.COARSE_CEF}
 PRECISION = {"fp64": ufe.PREC_FP64, "mixed": ufe.PREC_MIXED}
 COARSE_SOLVER = {"auto": ufe.COARSE_SOLVER_AUTO, "dense": ufe.COARSE_SOLVER_DENSE, "cr": ufe.COARSE_SOLVER_CR}
@@ -33,6 +33,8 @@ class Solver:
                 E, nu = p.lame
                 self.system = ufe.ufe_assemble_elastic(self.mesh, E, nu, a.get("kappa", p.kappa), a.get("f", p.f),
                                                        a.get("q", p.q), a.get("g", p.dirichlet_values))
+            elif getattr(p, "weak_dirichlet", False):
+                self.system = ufe.ufe_assemble_nitsche(self.mesh, a.get("f", p.f), a.get("g", p.dirichlet_values))
             else:
                 self.system = ufe.ufe_assemble(self.mesh, a.get("kappa", p.kappa), a.get("f", p.f),
                                                a.get("q", p.q), a.get("g", p.dirichlet_values))

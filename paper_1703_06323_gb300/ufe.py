@@ -22,7 +22,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 CELL_EXTERNAL, CELL_CUT, CELL_INTERNAL = 0, 1, 2
 OBJ_CORNER, OBJ_EDGE, OBJ_FACE = 0, 1, 2
 WEIGHT_STIFFNESS, WEIGHT_TOPOLOGICAL = 0, 1
-OBJECTS_STANDARD, OBJECTS_VARIANT1 = 0, 1
+OBJECTS_STANDARD, OBJECTS_VARIANT1, OBJECTS_VARIANT2 = 0, 1, 2
 COARSE_C, COARSE_CE, COARSE_CEF = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 COARSE_SOLVER_AUTO, COARSE_SOLVER_DENSE, COARSE_SOLVER_CR = 0, 1, 2
@@ -96,6 +96,8 @@ def _load():
         "ufe_assemble": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.POINTER(P)]),
         "ufe_assemble_elastic": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, P, P, P, P, ctypes.c_int,
                                                 ctypes.POINTER(P)]),
+        "ufe_assemble_nitsche": (ctypes.c_int, [P, P, P, ctypes.c_int, ctypes.POINTER(P)]),
+        "ufe_system_get_nitsche_beta": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ufe_system_get_info": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
         "ufe_system_get_rhs": (ctypes.c_int, [P, P, ctypes.c_int]),
         "ufe_system_apply": (ctypes.c_int, [P, P, P, ctypes.c_int]),
@@ -126,7 +128,7 @@ LIB = _load()
 EXPORTED = ("ufe_last_error", "ufe_version", "ufe_kernel_launches", "ufe_timing_enable", "ufe_timing_reset",
             "ufe_timing_get", "ufe_probe_fma_rate", "ufe_mesh_create", "ufe_mesh_get_info", "ufe_mesh_get_cell_types",
             "ufe_mesh_get_dof_map", "ufe_mesh_get_subdomains", "ufe_mesh_get_neighbours", "ufe_mesh_destroy",
-            "ufe_assemble", "ufe_assemble_elastic", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_set_kappa",
+            "ufe_assemble", "ufe_assemble_elastic", "ufe_assemble_nitsche", "ufe_system_get_nitsche_beta", "ufe_system_get_info", "ufe_system_get_rhs", "ufe_system_apply", "ufe_system_set_kappa",
             "ufe_system_get_cut_data",
             "ufe_system_destroy", "ufe_bddc_setup", "ufe_bddc_get_info", "ufe_bddc_get_objects", "ufe_bddc_apply",
             "ufe_bddc_apply_noalloc",
@@ -258,6 +260,20 @@ def ufe_assemble(mesh, kappa_cells=None, f_nodes=None, flux_nodes=None, dirichle
     out = ctypes.c_void_p()
     _check(LIB.ufe_assemble(mesh, args[0][0], args[1][0], args[2][0], args[3][0], mem, ctypes.byref(out)))
     return out
+
+
+def ufe_assemble_nitsche(mesh, f_nodes, dirichlet_values):
+    """Poisson with weak (Nitsche) Dirichlet data on the unfitted boundary; dirichlet_values
+    are also the strong values at the constrained box nodes."""
+    args = [_ptr(f_nodes, np.float64), _ptr(dirichlet_values, np.float64)]
+    mem = _mem_of(*args)
+    out = ctypes.c_void_p()
+    _check(LIB.ufe_assemble_nitsche(mesh, args[0][0], args[1][0], mem, ctypes.byref(out)))
+    return out
+
+
+def ufe_system_get_nitsche_beta(system, n_cut):
+    return _get(LIB.ufe_system_get_nitsche_beta, system, n_cut, np.float64)
 
 
 def ufe_assemble_elastic(mesh, E, nu, E_scale_cells=None, f_nodes=None, stress_nodes=None, dirichlet_values=None):

@@ -76,6 +76,25 @@ def _slab(eps):
     return p
 
 
+def nitsche_problems():
+    """Weak Dirichlet data (Nitsche, Sect. 2.2) on the unfitted boundary: a sphere whose
+    whole boundary carries them, a linear solution below a plane cut (strong data on the
+    box faces it reaches), and the bumpy sphere at 32^3 with its forced small cuts."""
+    sphere = inputs.sphere_problem(cells=(16, 16, 16), sub_cells=(4, 4, 4), centre=(0.51, 0.49, 0.5), radius=0.4,
+                                   dirichlet_face_mask=inputs.ALL_FACES, pin_node=inputs.PIN_NONE, name="ni_sphere")
+    plane = inputs.plane_problem(cells=(8, 8, 8), sub_cells=(4, 4, 4), normal=(0.6, 0.8, 0.1), offset=0.61,
+                                 dirichlet_face_mask=inputs.ALL_FACES, pin_node=inputs.PIN_NONE, name="ni_plane")
+    bumpy = inputs.bumpy_sphere(0, n=32)
+    bumpy.name = "ni_bumpy"
+    bumpy.pin_node = inputs.PIN_NONE
+    bumpy.dirichlet_values = np.random.default_rng(3).uniform(-1, 1, bumpy.n_nodes)
+    out = {"ni_sphere": sphere, "ni_plane": plane, "ni_bumpy": bumpy}
+    for p in out.values():
+        p.q = None
+        p.weak_dirichlet = True
+    return out
+
+
 class OracleRun:
     def __init__(self, p):
         self.p = p
@@ -150,6 +169,8 @@ def oracle_run(name):
         return OracleRun(inputs.bumpy_sphere(0))
     if name.startswith("el_"):
         return ElasticOracleRun(elastic_problems()[name])
+    if name.startswith("ni_"):
+        return OracleRun(nitsche_problems()[name])
     return OracleRun(small_problems()[name])
 
 
