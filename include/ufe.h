@@ -313,6 +313,11 @@ typedef struct {
   int32_t coarse_layers, coarse_levels;   /* cyclic reduction: non-empty z layers, reduction levels */
   int32_t local_tensor_cores;   /* 1 when the FP32 local inversions ran their Gauss-Jordan updates on the
                                    tensor cores (3xTF32 split products, tcgen05), 0 otherwise */
+  int32_t prec_cluster, prec_stages;   /* launch shape of the per-iteration preconditioner kernels: CTAs per
+                                          subdomain cluster and row-stream stages per CTA (0: from the
+                                          shared-memory budget), chosen by timing the candidates once per
+                                          size class and process (Poisson; UFE_AUTOTUNE=0 keeps 4 and 0;
+                                          UFE_PREC_SHAPE="cl,stages" fixes them) */
 } ufe_bddc_info;
 
 /*

@@ -157,6 +157,8 @@ struct Bddc {
   int fp64_refactor = 0;                // mixed precision requested, FP64 local operators kept (FP32 too ill-conditioned)
   double cphi_error = 0.0;              // mixed: max |C Phi - I| of the FP32 operators
   int local_tc = 0;                     // FP32 local inversions ran the tensor-core update
+  int prec_cl = 4;                      // CTAs per subdomain cluster in the preconditioner kernels (tuned)
+  int prec_stages = 0;                  // row-stream stages per CTA (tuned; 0: from the shared-memory budget)
 
   SubMeta meta() const;
   ~Bddc();
@@ -173,6 +175,8 @@ void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
 // made by the set-up: loads the device code and looks up the static array the
 // allocation-free apply uses, so that the apply itself takes no device memory
 void bddc_noalloc_prepare(Bddc& B);
+// launch shape of the per-iteration preconditioner kernels, timed per size class (pcg.cu)
+void tune_preconditioner(Bddc& B);
 // loads the coarse solver's kernels (cudaFuncGetAttributes), once per device
 void coarse_prepare();
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);

@@ -19,7 +19,12 @@
 // Scalars live on the device.  Reductions are done by the last CTA to finish
 // (fixed summation order, deterministic).
 #include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include <cooperative_groups.h>
 
@@ -191,6 +196,50 @@ __device__ __forceinline__ void apply_node_el(const OpArgs& a, int64_t d, Val va
       }
 }
 
+// Poisson, one cell's part of row d: kappa_e sum_b K_e[a][b] x_b for the cell of which
+// node (i, j, k) is vertex a (the cell at (i, j, k) minus the bits of a); the eight
+// lanes of a group take the eight cells around the node and add their parts with a
+// fixed butterfly (deterministic)
+template <typename Val>
+__device__ __forceinline__ double apply_cell(const OpArgs& a, int i, int j, int k, int av, Val val) {
+  const GridGeom& g = a.g;
+  const int ci = i - (av & 1), cj = j - ((av >> 1) & 1), ck = k - (av >> 2);
+  if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) return 0.0;
+  const int64_t c = g.cell(ci, cj, ck);
+  const uint8_t t = a.cell_type[c];
+  if (t == UFE_CELL_EXTERNAL) return 0.0;
+  double xb[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int32_t e = a.dof_of_node[g.node(ci + (b & 1), cj + ((b >> 1) & 1), ck + (b >> 2))];
+    xb[b] = e >= 0 ? val(e) : 0.0;
+  }
+  double s = 0.0;
+  if (t == UFE_CELL_INTERNAL) {
+#pragma unroll
+    for (int b = 0; b < 8; ++b) s += q1_khat(av, b) * xb[b];
+    s *= g.h;
+  } else {
+    const double* Kc = a.K_cut + (int64_t)a.cut_index[c] * 64 + av * 8;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) s += Kc[b] * xb[b];
+  }
+  return a.kappa ? a.kappa[c] * s : s;
+}
+
+__device__ __forceinline__ double group8_sum(double s) {
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  return s;
+}
+
+__device__ __forceinline__ void node_ijk(const GridGeom& g, int64_t v, int& i, int& j, int& k) {
+  i = (int)(v % (g.nx + 1));
+  j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+}
+
 // the NC rows of free node d
 template <int NC, typename Val>
 __device__ __forceinline__ void apply_node(const OpArgs& a, int64_t d, Val val, double y[NC]) {
@@ -198,6 +247,21 @@ __device__ __forceinline__ void apply_node(const OpArgs& a, int64_t d, Val val, 
     y[0] = apply_row(a, d, val);
   else
     apply_node_el(a, d, val, y);
+}
+
+// Poisson y = A x, eight lanes per row (one per cell around the node)
+__global__ void __launch_bounds__(kApplyThreads) k_apply8(OpArgs a, const double* __restrict__ x,
+                                                          double* __restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t d = t >> 3;
+  double s = 0.0;
+  if (d < a.n_dof) {
+    int i, j, k;
+    node_ijk(a.g, a.node_of_dof[d], i, j, k);
+    s = apply_cell(a, i, j, k, (int)(t & 7), [&](int64_t e) { return x[e]; });
+  }
+  s = group8_sum(s);
+  if (d < a.n_dof && (t & 7) == 0) y[d] = s;
 }
 
 template <int NC>
@@ -277,6 +341,40 @@ k_dir_apply(OpArgs a, const double* __restrict__ z, double* p0, double* p1, doub
       q[e] = qd[c];
       pq += pd * qd[c];
     }
+  }
+  pq = block_sum(pq);
+  if (threadIdx.x == 0) part[blockIdx.x] = pq;
+  if (arrive_last(&sc->counter[1])) {
+    const double P = sum_partials(part, gridDim.x, 1);
+    if (threadIdx.x == 0) sc->pq = P;
+  }
+}
+
+// K1 for Poisson with eight lanes per row (one per cell around the node)
+__global__ void __launch_bounds__(kApplyThreads)
+k_dir_apply8(OpArgs a, const double* __restrict__ z, double* p0, double* p1, double* __restrict__ q,
+             double* __restrict__ part, PcgScalars* sc) {
+  if (sc->done) return;
+  const int it = sc->iter;
+  const double* pold = (it & 1) ? p1 : p0;
+  double* pnew = (it & 1) ? p0 : p1;
+  double beta = 0.0;
+  if (!sc->first) beta = sc->flexible ? (sc->rz_next - sc->rzold_next) / sc->rz : sc->rz_next / sc->rz;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t d = t >> 3;
+  double s = 0.0;
+  if (d < a.n_dof) {
+    int i, j, k;
+    node_ijk(a.g, a.node_of_dof[d], i, j, k);
+    s = apply_cell(a, i, j, k, (int)(t & 7), [&](int64_t e) { return z[e] + beta * pold[e]; });
+  }
+  s = group8_sum(s);
+  double pq = 0.0;
+  if (d < a.n_dof && (t & 7) == 0) {
+    const double pd = z[d] + beta * pold[d];
+    pnew[d] = pd;
+    q[d] = s;
+    pq = pd * s;
   }
   pq = block_sum(pq);
   if (threadIdx.x == 0) part[blockIdx.x] = pq;
@@ -583,41 +681,43 @@ __device__ void cta_gemv_short(const TM* __restrict__ M, int r0, int r1, int ld,
   }
 }
 
-// The per-subdomain stages run as thread-block clusters of kCL CTAs per subdomain:
-// each CTA computes a contiguous slice of the rows of a local GEMV and the slices
-// are exchanged through distributed shared memory.
+// The per-subdomain stages run as thread-block clusters of CL CTAs per subdomain (2, 4
+// or 8, chosen per problem by the launch-shape tuner): each CTA computes a contiguous
+// slice of the rows of a local GEMV and the slices are exchanged through distributed
+// shared memory.
+template <int CL>
 __device__ __forceinline__ void row_slice(int n, int rank, int& b, int& e) {
-  b = (n * rank) / kCL;
-  e = (n * (rank + 1)) / kCL;
+  b = (n * rank) / CL;
+  e = (n * (rank + 1)) / CL;
 }
 
 // copy the slices of `local` that the other CTAs of the cluster computed
-template <typename V>
+template <int CL, typename V>
 __device__ void cluster_gather(cg::cluster_group& cl, V* local, int n) {
   const int me = (int)cl.block_rank();
-  for (int r = 0; r < kCL; ++r) {
+  for (int r = 0; r < CL; ++r) {
     if (r == me) continue;
     int b, e;
-    row_slice(n, r, b, e);
+    row_slice<CL>(n, r, b, e);
     const V* remote = cl.map_shared_rank(local, r);
     for (int i = b + threadIdx.x; i < e; i += blockDim.x) local[i] = remote[i];
   }
 }
 
 // K3: y_I = A_II^-1 r_I; t_G = A_GI y_I
-template <typename TM, int NC>
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
+template <typename TM, int NC, int CL = kCL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, double* __restrict__ tG,
                  const PcgScalars* sc, SubLaunch L) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
+  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
   int r0, r1;
-  row_slice(z.nI, rank, r0, r1);
+  row_slice<CL>(z.nI, rank, r0, r1);
   RowStream<TM> rs;
   rs.begin(AIIinv + sm.off_II[w], r0, r1, z.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
@@ -627,13 +727,13 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   __syncthreads();
   rs.gemv(xI, S.dI + r0, sm.status);
   cl.sync();
-  cluster_gather(cl, S.dI, z.nI);
+  cluster_gather<CL>(cl, S.dI, z.nI);
   cl.sync();
   // y_I = S_I (Ahat_II^-1 (S_I r_I)), on every CTA's full copy
   for (int p = threadIdx.x; p < z.nI; p += blockDim.x) S.dI[p] *= sm.sI[i0 + p];
   __syncthreads();
   int j0, j1;
-  row_slice(z.nG, rank, j0, j1);
+  row_slice<CL>(z.nG, rank, j0, j1);
   constexpr int KS = 27 * NC;
   const int64_t e0 = KS * (int64_t)sm.vG_ptr[w];
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
@@ -648,8 +748,8 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
 }
 
 // K4: r~ = w (r_G - sum t_G); v = K r~ (stored weighted: vw = w v); g = Phi^T r~
-template <typename TM, int NC>
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
+template <typename TM, int NC, int CL = kCL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Phi, const double* __restrict__ r,
                const double* __restrict__ tG, double* __restrict__ vw, double* __restrict__ gC, const PcgScalars* sc,
                SubLaunch L) {
@@ -658,13 +758,13 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   extern __shared__ __align__(16) char smem[];
   __shared__ double gpart[kSubThreads / 32][64];
   __shared__ double gsum[1024];
-  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
+  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0) return;
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
   int r0, r1;
-  row_slice(z.nG, rank, r0, r1);
+  row_slice<CL>(z.nG, rank, r0, r1);
   RowStream<TM> rs;
   rs.begin(Kop + sm.off_GG[w], r0, r1, z.ldG, S.stage, full, L.n_stages);
   TM* xG = reinterpret_cast<TM*>(S.xT);
@@ -709,7 +809,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   if (rank == 0) {
     for (int c = threadIdx.x; c < z.nC; c += blockDim.x) {
       double sacc = 0.0;
-      for (int q = 0; q < kCL; ++q) sacc += cl.map_shared_rank(gsum, q)[c];
+      for (int q = 0; q < CL; ++q) sacc += cl.map_shared_rank(gsum, q)[c];
       gC[sm.C_ptr[w] + c] = sacc;
     }
   }
@@ -717,14 +817,14 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
 }
 
 // K6: coarse prolongation, vw += w Phi u_c^w on the interface rows of w
-template <typename TM, int NC>
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
+template <typename TM, int NC, int CL = kCL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict__ uc, double* __restrict__ vw,
                const PcgScalars* sc, SubLaunch L) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
+  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0 || z.nC == 0) return;
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
@@ -732,7 +832,7 @@ k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict_
   for (int c = threadIdx.x; c < z.ldC; c += blockDim.x) xc[c] = c < z.nC ? (TM)uc[sm.C_list[sm.C_ptr[w] + c]] : TM(0);
   __syncthreads();
   int j0, j1;
-  row_slice(z.nG, rank, j0, j1);
+  row_slice<CL>(z.nG, rank, j0, j1);
   if (z.ldC <= 32 * VecT<TM>::n)
     cta_gemv_short<TM>(Phi + sm.off_GC[w], j0, j1, z.ldC, xc, S.dG);
   else
@@ -744,19 +844,19 @@ k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict_
 
 // K7: u_G = sum_w' w' (v + Phi u_c) (the weighted local values, W); z_G = u_G (the
 // owner writes); z_I = A_II^-1 (r_I - A_IG u_G) (harmonic extension)
-template <typename TM, int NC>
-__global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kSubThreads)
+template <typename TM, int NC, int CL = kCL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSubThreads)
 k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict__ r, const double* __restrict__ vw,
              double* __restrict__ z, double* __restrict__ part, PcgScalars* sc, SubLaunch L, int with_dots) {
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x / kCL, rank = (int)cl.block_rank();
+  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
   const SubSizes zz = sub_sizes(sm, w);
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
   int p0, p1;
-  row_slice(zz.nI, rank, p0, p1);
+  row_slice<CL>(zz.nI, rank, p0, p1);
   RowStream<TM> rs;
   rs.begin(AIIinv + sm.off_II[w], p0, p1, zz.ldI, S.stage, full, L.n_stages);
   TM* xI = reinterpret_cast<TM*>(S.xT);
@@ -773,7 +873,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   }
   __syncthreads();
   int j0, j1;
-  row_slice(zz.nG, rank, j0, j1);
+  row_slice<CL>(zz.nG, rank, j0, j1);
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const int32_t xi = sm.G_list[gn0 + j / NC];
     if (sm.neigh[(int64_t)xi * 8] != w) continue;
@@ -799,7 +899,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   }
   for (int p = zz.nI + threadIdx.x; p < zz.ldI; p += blockDim.x) xI[p] = TM(0);
   cl.sync();
-  cluster_gather(cl, xI, zz.nI);
+  cluster_gather<CL>(cl, xI, zz.nI);
   cl.sync();
   rs.gemv(xI, S.dI + p0, sm.status);
   for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -893,7 +993,7 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
   if (sys.ncomp == 3)
     k_apply<3><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
   else
-    k_apply<1><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+    k_apply8<<<grid_for(8 * a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
   UFE_CHECK_LAUNCH();
   t.end(s);
 }
@@ -909,14 +1009,16 @@ static SubLaunch sub_launch(const Bddc& B, size_t tm_size, size_t* smem) {
   const size_t ldmax = (size_t)std::max(L.ldImax, L.ldGmax);
   const size_t stage = (size_t)kStreamRows * ldmax * tm_size;
   L.n_stages = (int)std::max<size_t>(1, std::min<size_t>(kMaxStages, kStageBudget / stage));
+  if (B.prec_stages > 0) L.n_stages = std::min(B.prec_stages, kMaxStages);   // tuned
   size_t off = (size_t)L.ldImax * 8 + (size_t)L.ldGmax * 8 + ldmax * tm_size;
   off = (off + 127) & ~(size_t)127;
   *smem = off + (size_t)L.n_stages * stage;
   return L;
 }
 
-template <typename TM, int NC>
-static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
+template <typename TM, int NC, int CL>
+static void launch_preconditioner_cl(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots,
+                                     cudaStream_t s) {
   const Mesh& m = *B.mesh;
   const SubMeta sm = B.meta();
   const int ns = (int)m.n_sub;
@@ -927,11 +1029,11 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
   TimedLaunch t3, t4, t5, t6, t7;   // per-stage event timing (outside graph capture, when enabled)
   t3.begin("prec_interior", s);
-  k_prec_interior1<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, L);
+  k_prec_interior1<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, L);
   UFE_CHECK_LAUNCH();
   t3.end(s);
   t4.begin("prec_neumann", s);
-  k_prec_neumann<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, L);
+  k_prec_neumann<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, L);
   UFE_CHECK_LAUNCH();
   t4.end(s);
   if (B.n_coarse > 0) {
@@ -939,14 +1041,25 @@ static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalar
     coarse_solve(B, B.gC.p, B.uc.p, B.cr.work.p, sc, s);
     t5.end(s);
     t6.begin("prec_prolong", s);
-    k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
+    k_prec_prolong<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
     UFE_CHECK_LAUNCH();
     t6.end(s);
   }
   t7.begin("prec_final", s);
-  k_prec_final<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, L, with_dots);
+  k_prec_final<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, L, with_dots);
   UFE_CHECK_LAUNCH();
   t7.end(s);
+}
+
+// the cluster size the launch-shape tuner chose (Poisson; elasticity keeps four CTAs)
+template <typename TM, int NC>
+static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
+  if (NC == 1 && B.prec_cl == 2)
+    launch_preconditioner_cl<TM, NC, 2>(B, r, z, sc, with_dots, s);
+  else if (NC == 1 && B.prec_cl == 8)
+    launch_preconditioner_cl<TM, NC, 8>(B, r, z, sc, with_dots, s);
+  else
+    launch_preconditioner_cl<TM, NC, kCL>(B, r, z, sc, with_dots, s);
 }
 
 // raise a kernel's dynamic shared-memory limit to what the device allows next to its
@@ -965,6 +1078,16 @@ static void set_smem_limits_for(int optin) {
   raise_smem_limit(k_prec_neumann<TM, NC>, optin);
   raise_smem_limit(k_prec_final<TM, NC>, optin);
   raise_smem_limit(k_prec_prolong<TM, NC>, optin);
+  if (NC == 1) {
+    raise_smem_limit(k_prec_interior1<TM, NC, 2>, optin);
+    raise_smem_limit(k_prec_neumann<TM, NC, 2>, optin);
+    raise_smem_limit(k_prec_final<TM, NC, 2>, optin);
+    raise_smem_limit(k_prec_prolong<TM, NC, 2>, optin);
+    raise_smem_limit(k_prec_interior1<TM, NC, 8>, optin);
+    raise_smem_limit(k_prec_neumann<TM, NC, 8>, optin);
+    raise_smem_limit(k_prec_final<TM, NC, 8>, optin);
+    raise_smem_limit(k_prec_prolong<TM, NC, 8>, optin);
+  }
 }
 
 // The per-subdomain kernels take their dynamic shared memory from the problem; the
@@ -1018,6 +1141,93 @@ static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Launch-shape tuner of the per-iteration preconditioner kernels (Poisson): CTAs per
+// subdomain cluster (2, 4, 8) and row-stream stages per CTA (1, 2, 4).  The first
+// set-up of a size class (device, precision, interior and interface sizes in steps of
+// 32, subdomain count in powers of two) times each candidate with CUDA events (one
+// warm-up and three applications of z = M r on the preconditioner's own work vectors)
+// and caches the fastest for the process; later set-ups of the class reuse it.
+// UFE_AUTOTUNE=0 keeps the default shape (4 CTAs, stages from the shared-memory budget).
+// ---------------------------------------------------------------------------
+static bool autotune_enabled() {
+  const char* e = getenv("UFE_AUTOTUNE");
+  return !(e && std::string(e) == "0");
+}
+
+void tune_preconditioner(Bddc& B) {
+  B.prec_cl = kCL;
+  B.prec_stages = 0;
+  if (B.ncomp != 1 || B.mesh->n_sub == 0) return;
+  if (const char* f = getenv("UFE_PREC_SHAPE")) {   // "cl,stages": a fixed shape (tests of every variant)
+    int cl = kCL, st = 0;
+    if (sscanf(f, "%d,%d", &cl, &st) == 2 && (cl == 2 || cl == 4 || cl == 8) && st >= 0 && st <= kMaxStages) {
+      B.prec_cl = cl;
+      B.prec_stages = st;
+    }
+    return;
+  }
+  if (!autotune_enabled()) return;
+  static std::mutex mu;
+  static std::map<std::array<int, 6>, std::pair<int, int>> cache;
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  int nsb = 0;
+  while ((1ll << nsb) < B.mesh->n_sub) ++nsb;
+  const std::array<int, 6> key = {dev, B.mixed ? 1 : 0, (B.max_nIv + 31) / 32, (B.max_nGv + 31) / 32, nsb,
+                                  B.n_coarse > 0 ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      B.prec_cl = it->second.first;
+      B.prec_stages = it->second.second;
+      return;
+    }
+  }
+  set_smem_limits(B);
+  cudaStream_t s = B.stream;
+  UFE_CUDA(cudaMemsetAsync(B.r.p, 0, (size_t)B.mesh->n_dof * 8, s));
+  cudaEvent_t e0, e1;
+  UFE_CUDA(cudaEventCreate(&e0));
+  UFE_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  std::pair<int, int> pick = {kCL, 0};
+  const bool was_timing = timing_enabled();
+  set_timing_enabled(false);   // the tuner's launches stay out of the instrumentation records
+  try {
+    for (int cl : {2, 4, 8})
+      for (int st : {1, 2, 4}) {
+        B.prec_cl = cl;
+        B.prec_stages = st;
+        precondition(B, B.r.p, B.z.p, nullptr, 0, s);
+        UFE_CUDA(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) precondition(B, B.r.p, B.z.p, nullptr, 0, s);
+        UFE_CUDA(cudaEventRecord(e1, s));
+        UFE_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          pick = {cl, st};
+        }
+      }
+  } catch (...) {
+    set_timing_enabled(was_timing);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  set_timing_enabled(was_timing);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_device_status(B);
+  B.prec_cl = pick.first;
+  B.prec_stages = pick.second;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = pick;
+}
+
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
   set_smem_limits(B);
   precondition(B, r_dev, z_dev, nullptr, 0, B.stream);
@@ -1030,7 +1240,8 @@ static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
   if (B.ncomp == 3)
     k_dir_apply<3><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   else
-    k_dir_apply<1><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+    k_dir_apply8<<<grid_for(8 * a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p,
+                                                                             B.part.p, B.sc.p);
   UFE_CHECK_LAUNCH();
   k_update<<<grid_for(nv, kApplyThreads), kApplyThreads, 0, s>>>(nv, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p,
                                                                  B.sc.p);

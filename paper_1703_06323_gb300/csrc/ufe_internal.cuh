@@ -214,6 +214,10 @@ void kappa_gradient(const System& sys, const double* u_dev, const double* lambda
 // constant tables (Q1 reference matrices, quadrature) uploaded once
 void ensure_constants();
 
+// whether ufe_timing_enable is on (the launch-shape tuner switches it off around its runs)
+bool timing_enabled();
+void set_timing_enabled(bool on);
+
 // optional event timing of named kernels (see ufe_timing_enable)
 struct TimedLaunch {
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -58,7 +58,8 @@ class BddcInfo(ctypes.Structure):
                 ("interior_slots", ctypes.c_int64), ("interface_slots", ctypes.c_int64),
                 ("fp64_refactor", ctypes.c_int32), ("coarse_solver", ctypes.c_int32), ("cphi_error", ctypes.c_double),
                 ("coarse_layers", ctypes.c_int32), ("coarse_levels", ctypes.c_int32),
-                ("local_tensor_cores", ctypes.c_int32)]
+                ("local_tensor_cores", ctypes.c_int32), ("prec_cluster", ctypes.c_int32),
+                ("prec_stages", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
