@@ -1315,9 +1315,8 @@ void bddc_build(Bddc& B) {
     v->alloc(NC * nd, s);
     v->zero();
   }
-  // per-CTA partial sums: the operator apply runs eight lanes per row, the preconditioner
-  // up to eight CTAs per subdomain
-  B.part_blocks = std::max<int64_t>(grid_for(8 * NC * nd, 256), 16 * (int64_t)ns) + 8;
+  // per-CTA partial sums (the preconditioner runs up to eight CTAs per subdomain)
+  B.part_blocks = std::max<int64_t>(grid_for(NC * nd, 256), 16 * (int64_t)ns) + 8;
   B.part.alloc(B.part_blocks * 2, s);
   B.sc.alloc(1, s);
   B.sc.zero();

@@ -196,50 +196,6 @@ __device__ __forceinline__ void apply_node_el(const OpArgs& a, int64_t d, Val va
       }
 }
 
-// Poisson, one cell's part of row d: kappa_e sum_b K_e[a][b] x_b for the cell of which
-// node (i, j, k) is vertex a (the cell at (i, j, k) minus the bits of a); the eight
-// lanes of a group take the eight cells around the node and add their parts with a
-// fixed butterfly (deterministic)
-template <typename Val>
-__device__ __forceinline__ double apply_cell(const OpArgs& a, int i, int j, int k, int av, Val val) {
-  const GridGeom& g = a.g;
-  const int ci = i - (av & 1), cj = j - ((av >> 1) & 1), ck = k - (av >> 2);
-  if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) return 0.0;
-  const int64_t c = g.cell(ci, cj, ck);
-  const uint8_t t = a.cell_type[c];
-  if (t == UFE_CELL_EXTERNAL) return 0.0;
-  double xb[8];
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int32_t e = a.dof_of_node[g.node(ci + (b & 1), cj + ((b >> 1) & 1), ck + (b >> 2))];
-    xb[b] = e >= 0 ? val(e) : 0.0;
-  }
-  double s = 0.0;
-  if (t == UFE_CELL_INTERNAL) {
-#pragma unroll
-    for (int b = 0; b < 8; ++b) s += q1_khat(av, b) * xb[b];
-    s *= g.h;
-  } else {
-    const double* Kc = a.K_cut + (int64_t)a.cut_index[c] * 64 + av * 8;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) s += Kc[b] * xb[b];
-  }
-  return a.kappa ? a.kappa[c] * s : s;
-}
-
-__device__ __forceinline__ double group8_sum(double s) {
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  return s;
-}
-
-__device__ __forceinline__ void node_ijk(const GridGeom& g, int64_t v, int& i, int& j, int& k) {
-  i = (int)(v % (g.nx + 1));
-  j = (int)((v / (g.nx + 1)) % (g.ny + 1));
-  k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
-}
-
 // the NC rows of free node d
 template <int NC, typename Val>
 __device__ __forceinline__ void apply_node(const OpArgs& a, int64_t d, Val val, double y[NC]) {
@@ -247,21 +203,6 @@ __device__ __forceinline__ void apply_node(const OpArgs& a, int64_t d, Val val, 
     y[0] = apply_row(a, d, val);
   else
     apply_node_el(a, d, val, y);
-}
-
-// Poisson y = A x, eight lanes per row (one per cell around the node)
-__global__ void __launch_bounds__(kApplyThreads) k_apply8(OpArgs a, const double* __restrict__ x,
-                                                          double* __restrict__ y) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t d = t >> 3;
-  double s = 0.0;
-  if (d < a.n_dof) {
-    int i, j, k;
-    node_ijk(a.g, a.node_of_dof[d], i, j, k);
-    s = apply_cell(a, i, j, k, (int)(t & 7), [&](int64_t e) { return x[e]; });
-  }
-  s = group8_sum(s);
-  if (d < a.n_dof && (t & 7) == 0) y[d] = s;
 }
 
 template <int NC>
@@ -341,40 +282,6 @@ k_dir_apply(OpArgs a, const double* __restrict__ z, double* p0, double* p1, doub
       q[e] = qd[c];
       pq += pd * qd[c];
     }
-  }
-  pq = block_sum(pq);
-  if (threadIdx.x == 0) part[blockIdx.x] = pq;
-  if (arrive_last(&sc->counter[1])) {
-    const double P = sum_partials(part, gridDim.x, 1);
-    if (threadIdx.x == 0) sc->pq = P;
-  }
-}
-
-// K1 for Poisson with eight lanes per row (one per cell around the node)
-__global__ void __launch_bounds__(kApplyThreads)
-k_dir_apply8(OpArgs a, const double* __restrict__ z, double* p0, double* p1, double* __restrict__ q,
-             double* __restrict__ part, PcgScalars* sc) {
-  if (sc->done) return;
-  const int it = sc->iter;
-  const double* pold = (it & 1) ? p1 : p0;
-  double* pnew = (it & 1) ? p0 : p1;
-  double beta = 0.0;
-  if (!sc->first) beta = sc->flexible ? (sc->rz_next - sc->rzold_next) / sc->rz : sc->rz_next / sc->rz;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t d = t >> 3;
-  double s = 0.0;
-  if (d < a.n_dof) {
-    int i, j, k;
-    node_ijk(a.g, a.node_of_dof[d], i, j, k);
-    s = apply_cell(a, i, j, k, (int)(t & 7), [&](int64_t e) { return z[e] + beta * pold[e]; });
-  }
-  s = group8_sum(s);
-  double pq = 0.0;
-  if (d < a.n_dof && (t & 7) == 0) {
-    const double pd = z[d] + beta * pold[d];
-    pnew[d] = pd;
-    q[d] = s;
-    pq = pd * s;
   }
   pq = block_sum(pq);
   if (threadIdx.x == 0) part[blockIdx.x] = pq;
@@ -993,7 +900,7 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
   if (sys.ncomp == 3)
     k_apply<3><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
   else
-    k_apply8<<<grid_for(8 * a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+    k_apply<1><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
   UFE_CHECK_LAUNCH();
   t.end(s);
 }
@@ -1240,8 +1147,7 @@ static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
   if (B.ncomp == 3)
     k_dir_apply<3><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   else
-    k_dir_apply8<<<grid_for(8 * a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p,
-                                                                             B.part.p, B.sc.p);
+    k_dir_apply<1><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   UFE_CHECK_LAUNCH();
   k_update<<<grid_for(nv, kApplyThreads), kApplyThreads, 0, s>>>(nv, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p,
                                                                  B.sc.p);

@@ -104,3 +104,36 @@ def test_config3_solve(env, precision):
         # recompute the residual with the (row-pinned) operator
         r = b - torch.from_numpy(S.apply(x.cpu().numpy())).cuda()
         assert float(r.norm() / b.norm()) <= 1.5e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config3_downscale_solution_against_the_oracle(precision):
+    """The config-3 geometry at 32^3 (the same seeded union of 8 spheres, 29 subdomains,
+    16,959 DOFs): the GPU solution at rtol 1e-12 against the FP64 elasticity oracle's in
+    the energy norm, 1e-8 in FP64 and 1e-6 in mixed precision (both sides at rtol 1e-12,
+    no allowance for the stopping point)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06323_gb300 import build_ext
+    build_ext.build()
+    from paper_1703_06323_gb300 import inputs
+    from paper_1703_06323_gb300.solver import Solver
+    from tests.oracle_cache import ElasticOracleRun, energy_error
+    p = inputs.elastic_spheres(seed=0, n=32, sub=8)
+    orc = _downscale_oracle(p)
+    ref = orc.solve(rtol=1e-12)
+    with Solver(p, precision=precision) as S:
+        x, info = S.solve(rtol=1e-12, maxit=5000)
+    assert info["converged"] == 1
+    assert energy_error(orc.sys.A, x, ref["x"]) <= (1e-8 if precision == "fp64" else 1e-6)
+
+
+_DOWNSCALE = {}
+
+
+def _downscale_oracle(p):
+    from tests.oracle_cache import ElasticOracleRun
+    if "orc" not in _DOWNSCALE:
+        _DOWNSCALE["orc"] = ElasticOracleRun(p)
+    return _DOWNSCALE["orc"]
