@@ -38,7 +38,7 @@ RTOL = 1e-8
 # DRAM bytes per launch of a kernel from one ncu capture of the same command
 # (dram__bytes_read.sum + dram__bytes_write.sum); a kernel missing here (or changed
 # since its capture) reports traffic null.
-TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": 4.84e6}
+TRAFFIC_BYTES_PER_LAUNCH = {"gj_update_f64": 4.86e6}
 # nominal dense tensor rates (PFLOP/s) that scale a measured bf16 peak to another dtype
 NOMINAL_TENSOR = {"bf16": 2.25, "tf32": 1.1}
 

@@ -163,11 +163,33 @@ __global__ void k_coarse_dense(int64_t nco, int ldc, const double* __restrict__ 
   if (sc && sc->done) return;
   extern __shared__ __align__(16) char smem[];
   double* rc = reinterpret_cast<double*>(smem);
-  for (int64_t l = threadIdx.x; l < ldc; l += blockDim.x) {
-    double s = 0.0;
-    if (l < nco)
-      for (int k = 0; k < cnn[l]; ++k) s += gC[cpos[l * 8 + k]];
-    rc[l] = s;
+  // the (at most eight) subdomain parts of each coarse DOF are loaded together, two
+  // coarse DOFs per thread and pass, and summed in subdomain order
+  for (int64_t l0 = threadIdx.x; l0 < ldc; l0 += 2 * (int64_t)blockDim.x) {
+    double v[2][8];
+    int n[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t l = l0 + h * (int64_t)blockDim.x;
+      n[h] = l < nco ? cnn[l] : 0;
+      int4 pa = make_int4(0, 0, 0, 0), pb = pa;
+      if (l < nco) {
+        pa = *reinterpret_cast<const int4*>(cpos + l * 8);
+        pb = *reinterpret_cast<const int4*>(cpos + l * 8 + 4);
+      }
+      const int p[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[h][k] = k < n[h] ? gC[p[k]] : 0.0;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t l = l0 + h * (int64_t)blockDim.x;
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < n[h]) s += v[h][k];
+      if (l < ldc) rc[l] = s;
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -242,6 +264,25 @@ struct Layer {
 
 constexpr int64_t kDenseCoarseMax = 2048;
 
+// first column with a nonzero in each row of the assembled coarse matrix (one warp per
+// row; the diagonal is positive, so every row has one at or before its own column)
+__global__ void k_first_nonzero(const double* __restrict__ A, int n, int ld, int32_t* __restrict__ first) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = A + (int64_t)row * ld;
+  int f = row;
+  for (int c0 = 0; c0 < row; c0 += 32) {
+    const int c = c0 + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, c < row && a[c] != 0.0);
+    if (m) {
+      f = c0 + __ffs(m) - 1;
+      break;
+    }
+  }
+  if (lane == 0) first[row] = f;
+}
+
 static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
   const int64_t n = B.n_coarse;
   int dev = 0, optin = 0;
@@ -258,7 +299,16 @@ static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
   DBuf<int> st;
   st.alloc(1, s);
   st.zero();
-  large_inverse<double>(Ac.p, (int)n, ldc, st.p, s);
+  // the coarse numbering follows the grid (objects in DOF order), so A_c is banded
+  // and the inversion skips the blocks outside its envelope
+  DBuf<int32_t> first;
+  first.alloc(std::max<int64_t>(n, 1), s);
+  k_first_nonzero<<<grid_for(n * 32, 256), 256, 0, s>>>(Ac.p, (int)n, ldc, first.p);
+  UFE_CHECK_LAUNCH();
+  std::vector<int32_t> first_h((size_t)n);
+  UFE_CUDA(cudaMemcpyAsync(first_h.data(), first.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  UFE_CUDA(cudaStreamSynchronize(s));
+  large_inverse<double>(Ac.p, (int)n, ldc, st.p, s, &first_h);
   UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
   B.Ac_inv.p = Ac.p;   // take the buffer over
   B.Ac_inv.n = Ac.n;

@@ -450,7 +450,8 @@ __device__ __forceinline__ void gj_tile(const InvDesc& d, int K, int I, int J, T
   }
 }
 
-// Tiles of step K other than block row / column K+1 (one CTA per tile I <= J).
+// Tiles of step K other than block row / column K+1 (one CTA per tile I <= J < nblk;
+// the caller may pass fewer blocks than the matrix has, see gj_run).
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
 k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R, const T* __restrict__ Q,
@@ -473,13 +474,13 @@ k_gj_update(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __res
 }
 
 // Look-ahead launch of step K: the tiles of block row / column K+1 (tile index t takes
-// tile (min(K+1, t), max(K+1, t))); the CTA of t = K+1 keeps the updated diagonal tile
-// in shared memory and inverts it into Dnext, the next step's D^-1.  Grid (matrix,
-// tile) with the diagonal tiles in the first grid row, so that every matrix's serial
-// inversion starts in the first wave.
+// tile (min(K+1, t), max(K+1, t))) up to block column jmax; the CTA of t = K+1 keeps the
+// updated diagonal tile in shared memory and inverts it into Dnext, the next step's
+// D^-1.  Grid (matrix, tile) with the diagonal tiles in the first grid row, so that
+// every matrix's serial inversion starts in the first wave.
 template <typename T, int NB>
 __global__ void __launch_bounds__(kGJThreads)
-k_gj_lookahead(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __restrict__ R,
+k_gj_lookahead(GJBatch bt, int step, int nblk, int jmax, T* __restrict__ base, const T* __restrict__ R,
                const T* __restrict__ Q, const T* __restrict__ Dg, T* __restrict__ Dnext, int* status, T floor) {
   const int b = blockIdx.x;
   const InvDesc d = bt.d[b];
@@ -488,7 +489,7 @@ k_gj_lookahead(GJBatch bt, int step, int nblk, T* __restrict__ base, const T* __
   const int y = (int)blockIdx.y;
   const int t = y == 0 ? nd : (y <= nd ? y - 1 : y);
   const int I = min(nd, t), J = max(nd, t);
-  if (step * NB >= d.n || J * NB >= d.n) return;
+  if (step * NB >= d.n || J * NB >= d.n || J > jmax) return;
   __shared__ T L[NB][NB + 1];
   __shared__ T Rt[NB][NB + 1];
   __shared__ T prow[2][NB], srow[2][NB];
@@ -1098,8 +1099,34 @@ struct GJEvents {
   cudaEvent_t operator[](int i) const { return e[i]; }
 };
 
+// Envelope of a symmetric matrix under block Gauss-Jordan.  With f_j the first column
+// holding a nonzero in row j, the unprocessed part keeps its envelope (as in a Cholesky
+// factorisation: no fill left of f_j), and a processed row reaches an unprocessed
+// column j only through rows whose envelope starts in the processed columns.  So at
+// step K block column K (and, by symmetry, block row K) is zero below (right of) block
+// lim_K = max{ j : f_j <= last column of block K } / NB, every update of step K stays
+// inside blocks [0, lim_K]^2, and lim_K is nondecreasing with lim_K >= K.
+static std::vector<int> gj_envelope(const std::vector<int32_t>& first_col, int n, int NB) {
+  const int nblk = (n + NB - 1) / NB;
+  std::vector<int> reach(nblk, 0);   // reach[b] = the largest row j whose envelope starts in block b
+  for (int j = 0; j < n; ++j) {
+    const int b = std::min(std::max(first_col[j], 0), j) / NB;
+    reach[b] = std::max(reach[b], j);
+  }
+  std::vector<int> lim(nblk);
+  int r = 0;
+  for (int K = 0; K < nblk; ++K) {
+    r = std::max(r, reach[K]);
+    lim[K] = std::max(K, r / NB);
+  }
+  return lim;
+}
+
+// lim (optional): per step K the last block that step K touches (gj_envelope); without
+// it every step covers the whole matrix
 template <typename T>
-static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T floor) {
+static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cudaStream_t s, T floor,
+                   const std::vector<int>* lim = nullptr) {
   constexpr int NB = GJWidth<T>::value;
   if (descs.empty()) return;
   int nmax = 0;
@@ -1128,7 +1155,15 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
   const GJBatch bt{dd.p, dq.p};
   const int nblk = (nmax + NB - 1) / NB;
   const unsigned nb = (unsigned)descs.size();
-  const unsigned ntri = (unsigned)(nblk * (nblk + 1) / 2);
+  UFE_REQUIRE(!lim || (descs.size() == 1 && (int)lim->size() == nblk), UFE_ERR_INVALID_ARG,
+              "an envelope applies to one matrix, one entry per block");
+  auto last = [&](int step) { return lim ? (*lim)[step] : nblk - 1; };
+  // columns of the row panel of a step: its envelope and, for the look-ahead, block K+2
+  auto panel_blocks = [&](int step) {
+    return (unsigned)((std::min(nmax, (std::min(std::max(last(step), step + 1), nblk - 1) + 1) * NB) +
+                       PanelWidth<T>::value - 1) /
+                      PanelWidth<T>::value);
+  };
   const int pcols = PanelWidth<T>::value;   // one chunk per CTA
   {
     TimedLaunch tl;
@@ -1143,7 +1178,7 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
     T* Rc = R.p + (step & 1) * nq;
     T* Qc = Q.p + (step & 1) * nq;
     if (step == 0) {
-      k_gj_panel<T, NB><<<dim3((nmax + pcols - 1) / pcols, nb), kGJThreads, 0, s>>>(bt, 0, pcols, base, Rc, Qc, Dc);
+      k_gj_panel<T, NB><<<dim3(panel_blocks(0), nb), kGJThreads, 0, s>>>(bt, 0, pcols, base, Rc, Qc, Dc);
       UFE_CHECK_LAUNCH();
     }
     // look-ahead: block row / column K+1 with the next diagonal inverse, then the next
@@ -1155,19 +1190,22 @@ static void gj_run(const std::vector<InvDesc>& descs, T* base, int* status, cuda
       T* Qn = Q.p + ((step + 1) & 1) * nq;
       TimedLaunch ta;
       ta.begin(sizeof(T) == 8 ? "gj_lookahead_f64" : "gj_lookahead_f32", s2);
-      k_gj_lookahead<T, NB><<<dim3(nb, nblk), kGJThreads, 0, s2>>>(bt, step, nblk, base, Rc, Qc, Dc, Dn, status,
-                                                                   floor);
+      const int jmax = std::max(last(step), step + 1);
+      k_gj_lookahead<T, NB><<<dim3(nb, jmax + 1), kGJThreads, 0, s2>>>(bt, step, nblk, jmax, base, Rc, Qc, Dc, Dn,
+                                                                       status, floor);
       UFE_CHECK_LAUNCH();
       ta.end(s2);
       TimedLaunch tp;
       tp.begin(sizeof(T) == 8 ? "gj_panel_f64" : "gj_panel_f32", s2);
-      k_gj_panel<T, NB><<<dim3((nmax + pcols - 1) / pcols, nb), kGJThreads, 0, s2>>>(bt, step + 1, pcols, base, Rn, Qn, Dn);
+      k_gj_panel<T, NB><<<dim3(panel_blocks(step + 1), nb), kGJThreads, 0, s2>>>(bt, step + 1, pcols, base, Rn, Qn,
+                                                                                 Dn);
       UFE_CHECK_LAUNCH();
       tp.end(s2);
     }
     TimedLaunch tl;
     tl.begin(sizeof(T) == 8 ? "gj_update_f64" : "gj_update_f32", s);
-    k_gj_update<T, NB><<<dim3(ntri, nb), kGJThreads, 0, s>>>(bt, step, nblk, base, Rc, Qc, Dc);
+    const int nl = last(step) + 1;
+    k_gj_update<T, NB><<<dim3((unsigned)(nl * (nl + 1) / 2), nb), kGJThreads, 0, s>>>(bt, step, nl, base, Rc, Qc, Dc);
     UFE_CHECK_LAUNCH();
     tl.end(s);
     UFE_CUDA(cudaEventRecord(ev[1], s2));
@@ -1292,7 +1330,12 @@ void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cu
 }
 
 template <typename T>
-void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s) {
+void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s, const std::vector<int32_t>* first_col) {
+  if (first_col) {
+    const std::vector<int> lim = gj_envelope(*first_col, n, GJWidth<T>::value);
+    gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s, T(0), &lim);
+    return;
+  }
   gj_run<T>(std::vector<InvDesc>{{n, ld, 0}}, A, status, s, T(0));
 }
 
@@ -1302,6 +1345,6 @@ template void batched_gemm<float>(bool, bool, const std::vector<GemmDesc>&, cons
                                   float, cudaStream_t);
 template void batched_inverse<double>(const std::vector<InvDesc>&, double*, int*, cudaStream_t, double);
 template void batched_inverse<float>(const std::vector<InvDesc>&, float*, int*, cudaStream_t, float);
-template void large_inverse<double>(double*, int, int, int*, cudaStream_t);
+template void large_inverse<double>(double*, int, int, int*, cudaStream_t, const std::vector<int32_t>*);
 
 }  // namespace ufe

@@ -33,8 +33,10 @@ void batched_inverse(const std::vector<InvDesc>& descs, T* base, int* status, cu
 // UFE_FP32_GJ is "simt" (the SIMT update, kept for comparison)
 bool fp32_tensor_cores();
 
-// in-place inverse of one large SPD matrix using the whole GPU
+// in-place inverse of one large SPD matrix using the whole GPU; first_col (optional,
+// host) holds for every row the first column with a nonzero, and the steps then skip
+// the blocks outside the matrix's envelope
 template <typename T>
-void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s);
+void large_inverse(T* A, int n, int ld, int* status, cudaStream_t s, const std::vector<int32_t>* first_col = nullptr);
 
 }  // namespace ufe
