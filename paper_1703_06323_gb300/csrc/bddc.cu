@@ -1316,7 +1316,8 @@ void bddc_build(Bddc& B) {
     v->zero();
   }
   // per-CTA partial sums (the preconditioner runs up to eight CTAs per subdomain)
-  B.part_blocks = std::max<int64_t>(grid_for(NC * nd, 256), 16 * (int64_t)ns) + 8;
+  B.part_blocks = std::max<int64_t>(std::max<int64_t>(grid_for(NC * nd, 256), B.sys->mesh->n_apply_tiles),
+                                    16 * (int64_t)ns) + 8;
   B.part.alloc(B.part_blocks * 2, s);
   B.sc.alloc(1, s);
   B.sc.zero();

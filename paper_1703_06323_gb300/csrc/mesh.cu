@@ -230,6 +230,21 @@ __global__ void k_node_of_dof(int64_t n, const int32_t* __restrict__ dof_of_node
   if (d >= 0) node_of_dof[d] = (int32_t)v;
 }
 
+// node tiles of the operator apply that hold a free DOF (flags, then the list in tile order)
+__global__ void k_apply_tile_flags(GridGeom g, int64_t n_dof, const int32_t* __restrict__ node_of_dof,
+                                   uint8_t* __restrict__ flags) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n_dof) return;
+  const int64_t v = node_of_dof[d];
+  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
+  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
+  flags[apply_tile_of_node(g, i, j, k)] = 1;
+}
+__global__ void k_apply_tile_list(int64_t n, const int32_t* __restrict__ index, int32_t* __restrict__ list) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && index[t] >= 0) list[index[t]] = (int32_t)t;
+}
+
 // ---------------------------------------------------------------------------
 // Sect. 2.1: subdomains = connected components (cells sharing a DOF) of the
 // active cells of each block.  One CTA per block, one thread per cell; labels
@@ -538,6 +553,20 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
   m.node_of_dof.alloc(m.n_dof, s);
   k_node_of_dof<<<grid_for(nn, T), T, 0, s>>>(nn, m.dof_of_node.p, m.node_of_dof.p);
   UFE_CHECK_LAUNCH();
+  {
+    const int64_t nt = (int64_t)apply_tiles_x(g) * apply_tiles_y(g) * apply_tiles_z(g);
+    DBuf<uint8_t> tf;
+    DBuf<int32_t> tidx;
+    tf.alloc(nt, s);
+    tf.zero();
+    tidx.alloc(nt, s);
+    k_apply_tile_flags<<<grid_for(m.n_dof, T), T, 0, s>>>(g, m.n_dof, m.node_of_dof.p, tf.p);
+    UFE_CHECK_LAUNCH();
+    m.n_apply_tiles = scan_flags(tf.p, nt, tidx.p, s);
+    m.apply_tiles.alloc(std::max<int64_t>(m.n_apply_tiles, 1), s);
+    k_apply_tile_list<<<grid_for(nt, T), T, 0, s>>>(nt, tidx.p, m.apply_tiles.p);
+    UFE_CHECK_LAUNCH();
+  }
 
   // cut cells, in cell order
   {

@@ -6,8 +6,8 @@
 // true residual.  The host launches it once and reads the result once; nothing
 // returns to the host between iterations.  One iteration is six kernels (seven
 // with the coarse prolongation):
-//   K1  p = z + beta p (double-buffered, computed on the fly for the 27-node
-//       neighbourhood) and q = A p, element by element; partial p.q
+//   K1  p = z + beta p (double-buffered, computed once per node of a tile with its
+//       halo) and q = A p, element by element; partial p.q
 //   K2  alpha = r.z / p.q;  x += alpha p;  r -= alpha q;  |r|^2, convergence
 //   K3  per subdomain: y_I = A_II^-1 r_I, t_G = A_GI y_I          (Eq. bddc, first term
 //       and E^T = I - A I0 A0^-1 I0^T)
@@ -92,7 +92,6 @@ __device__ double sum_partials(const double* part, int n, int stride) {
 // ---------------------------------------------------------------------------
 // element-by-element operator apply (Sect. 2.2): internal cells use kappa h Khat,
 // cut cells their own 8x8 matrix
-// ---------------------------------------------------------------------------
 struct OpArgs {
   GridGeom g;
   int64_t n_dof;            // free nodes
@@ -103,134 +102,181 @@ struct OpArgs {
   const double* K_cut;      // n_cut x (8 ncomp)^2
   const double* kappa;
   const double* Kref;       // elasticity: h Khat_el
+  const int32_t* tiles;     // node tiles holding a free DOF (one CTA each)
+  int64_t n_tiles;
 };
 
-template <typename Val>
-__device__ __forceinline__ double apply_row(const OpArgs& a, int64_t d, Val val) {  // Poisson
-  const GridGeom& g = a.g;
-  const int64_t v = a.node_of_dof[d];
-  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
-  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
-  double xn[27];
-#pragma unroll
-  for (int oz = -1; oz <= 1; ++oz)
-#pragma unroll
-    for (int oy = -1; oy <= 1; ++oy)
-#pragma unroll
-      for (int ox = -1; ox <= 1; ++ox) {
-        const int ii = i + ox, jj = j + oy, kk = k + oz;
-        double x = 0.0;
-        if (ii >= 0 && jj >= 0 && kk >= 0 && ii <= g.nx && jj <= g.ny && kk <= g.nz) {
-          const int32_t e = a.dof_of_node[g.node(ii, jj, kk)];
-          if (e >= 0) x = val(e);
-        }
-        xn[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] = x;
-      }
-  double acc = 0.0;
-#pragma unroll
-  for (int dk = -1; dk <= 0; ++dk)
-#pragma unroll
-    for (int dj = -1; dj <= 0; ++dj)
-#pragma unroll
-      for (int di = -1; di <= 0; ++di) {
-        const int ci = i + di, cj = j + dj, ck = k + dk;
-        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
-        const int64_t c = g.cell(ci, cj, ck);
-        const uint8_t t = a.cell_type[c];
-        if (t == UFE_CELL_EXTERNAL) continue;
-        const int av = (-di) + 2 * (-dj) + 4 * (-dk);
-        const double kap = a.kappa ? a.kappa[c] : 1.0;
-        double s = 0.0;
-        if (t == UFE_CELL_INTERNAL) {
-#pragma unroll
-          for (int b = 0; b < 8; ++b)
-            s += q1_khat(av, b) * xn[(di + (b & 1) + 1) + 3 * (dj + ((b >> 1) & 1) + 1) + 9 * (dk + (b >> 2) + 1)];
-          s *= g.h;
-        } else {
-          const double* Kc = a.K_cut + (int64_t)a.cut_index[c] * 64 + av * 8;
-#pragma unroll
-          for (int b = 0; b < 8; ++b)
-            s += Kc[b] * xn[(di + (b & 1) + 1) + 3 * (dj + ((b >> 1) & 1) + 1) + 9 * (dk + (b >> 2) + 1)];
-        }
-        acc += kap * s;
-      }
-  return acc;
-}
+// The operator is applied on node tiles: one CTA per kTX x kTY x kTZ box of grid nodes
+// (one thread per node), with the box's input values and a one-node halo
+// (kHX x kHY x kHZ), the DOF numbers of those nodes and the kCX x kCY x kCZ cells
+// around the box staged in shared memory.  Every input value and cell record is then
+// read from global memory once per tile instead of once per neighbouring row.
+constexpr int kTX = kApplyTX, kTY = kApplyTY, kTZ = kApplyTZ;
+constexpr int kTileThreads = kTX * kTY * kTZ;
+constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = kTZ + 2, kHalo = kHX * kHY * kHZ;
+constexpr int kCX = kTX + 1, kCY = kTY + 1, kCZ = kTZ + 1, kTileCells = kCX * kCY * kCZ;
+constexpr int kHaloPer = (kHalo + kTileThreads - 1) / kTileThreads;
+constexpr int kCellsPer = (kTileCells + kTileThreads - 1) / kTileThreads;
+constexpr int32_t kCellInternal = -1, kCellNone = -2;
 
-// elasticity: the three rows of free node d, y_c = sum over the cells around d of
-// kappa_e K_e[3 a + c][3 b + j] x_{3 e_b + j}  (val(3 e + j) returns the input entry)
-template <typename Val>
-__device__ __forceinline__ void apply_node_el(const OpArgs& a, int64_t d, Val val, double y[3]) {
+template <int NC>
+struct ApplyTile {
+  double x[NC][kHalo];
+  double kap[kTileCells];
+  int32_t code[kTileCells];   // cut index, kCellInternal, or kCellNone (external / off the grid)
+  int32_t dof[kHalo];
+};
+
+// Stages the tile and returns the free DOF of the calling thread's node (-1 if the
+// node is not free), with its NC rows of A x in y (x entry e = NC dof + component is
+// load(e)).  The cells around a node are visited in the same order, and each cell's
+// row summed in the same order, for every node, so results do not depend on the tiling.
+// Every thread of the CTA must call it.  The staging loads are issued in rounds
+// (all DOF numbers and cell records, then all input values) so that each thread has
+// all of its loads of a round in flight at once.
+template <int NC, typename Load>
+__device__ __forceinline__ int32_t tile_apply(const OpArgs& a, ApplyTile<NC>& T, Load load, double y[NC],
+                                              int* hc_out) {
   const GridGeom& g = a.g;
-  const int64_t v = a.node_of_dof[d];
-  const int i = (int)(v % (g.nx + 1)), j = (int)((v / (g.nx + 1)) % (g.ny + 1));
-  const int k = (int)(v / ((int64_t)(g.nx + 1) * (g.ny + 1)));
-  y[0] = y[1] = y[2] = 0.0;
+  const int ntx = apply_tiles_x(g), nty = apply_tiles_y(g);
+  const int t = a.tiles[blockIdx.x];
+  const int x0 = (t % ntx) * kTX, y0 = ((t / ntx) % nty) * kTY, z0 = (t / (ntx * nty)) * kTZ;
+  int32_t e[kHaloPer];
+#pragma unroll
+  for (int u = 0; u < kHaloPer; ++u) {
+    const int h = (int)threadIdx.x + u * kTileThreads;
+    const int i = x0 - 1 + h % kHX, j = y0 - 1 + (h / kHX) % kHY, k = z0 - 1 + h / (kHX * kHY);
+    e[u] = -1;
+    if (h < kHalo && i >= 0 && j >= 0 && k >= 0 && i <= g.nx && j <= g.ny && k <= g.nz)
+      e[u] = a.dof_of_node[g.node(i, j, k)];
+  }
+  uint8_t ty[kCellsPer];
+  int32_t ci[kCellsPer];
+  double kp[kCellsPer];
+#pragma unroll
+  for (int u = 0; u < kCellsPer; ++u) {
+    const int q = (int)threadIdx.x + u * kTileThreads;
+    const int i = x0 - 1 + q % kCX, j = y0 - 1 + (q / kCX) % kCY, k = z0 - 1 + q / (kCX * kCY);
+    ty[u] = UFE_CELL_EXTERNAL;
+    ci[u] = 0;
+    kp[u] = 0.0;
+    if (q < kTileCells && i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz) {
+      const int64_t c = g.cell(i, j, k);
+      ty[u] = a.cell_type[c];
+      ci[u] = a.cut_index[c];
+      kp[u] = a.kappa ? a.kappa[c] : 1.0;
+    }
+  }
+  double xv[kHaloPer][NC];
+#pragma unroll
+  for (int u = 0; u < kHaloPer; ++u)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) xv[u][c] = e[u] >= 0 ? load((int64_t)NC * e[u] + c) : 0.0;
+#pragma unroll
+  for (int u = 0; u < kHaloPer; ++u) {
+    const int h = (int)threadIdx.x + u * kTileThreads;
+    if (h < kHalo) {
+      T.dof[h] = e[u];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) T.x[c][h] = xv[u][c];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kCellsPer; ++u) {
+    const int q = (int)threadIdx.x + u * kTileThreads;
+    if (q < kTileCells) {
+      T.code[q] = ty[u] == UFE_CELL_EXTERNAL ? kCellNone : (ty[u] == UFE_CELL_INTERNAL ? kCellInternal : ci[u]);
+      T.kap[q] = kp[u];
+    }
+  }
+  __syncthreads();
+  const int lx = threadIdx.x % kTX, ly = (threadIdx.x / kTX) % kTY, lz = threadIdx.x / (kTX * kTY);
+  const int hc = (lx + 1) + kHX * ((ly + 1) + kHY * (lz + 1));
+  *hc_out = hc;
+  const int32_t d = T.dof[hc];
+  if (d < 0) return -1;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) y[c] = 0.0;
+#pragma unroll
   for (int dk = -1; dk <= 0; ++dk)
+#pragma unroll
     for (int dj = -1; dj <= 0; ++dj)
+#pragma unroll
       for (int di = -1; di <= 0; ++di) {
-        const int ci = i + di, cj = j + dj, ck = k + dk;
-        if (ci < 0 || cj < 0 || ck < 0 || ci >= g.nx || cj >= g.ny || ck >= g.nz) continue;
-        const int64_t c = g.cell(ci, cj, ck);
-        const uint8_t t = a.cell_type[c];
-        if (t == UFE_CELL_EXTERNAL) continue;
+        // cell (lx + di, ly + dj, lz + dk) relative to the box; its vertex b sits at halo
+        // offset (lx + di + 1 + (b & 1), ...)
+        const int cq = (lx + di + 1) + kCX * ((ly + dj + 1) + kCY * (lz + dk + 1));
+        const int32_t code = T.code[cq];
+        if (code == kCellNone) continue;
         const int av = (-di) + 2 * (-dj) + 4 * (-dk);
-        const double kap = a.kappa ? a.kappa[c] : 1.0;
-        const double* Ke = (t == UFE_CELL_INTERNAL ? a.Kref : a.K_cut + (int64_t)a.cut_index[c] * 576) + 3 * av * 24;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        const double kap = T.kap[cq];
+        const int h0 = (lx + di + 1) + kHX * ((ly + dj + 1) + kHY * (lz + dk + 1));
+        if constexpr (NC == 1) {
+          double s = 0.0;
+          if (code == kCellInternal) {
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int32_t e = a.dof_of_node[g.node(ci + (b & 1), cj + ((b >> 1) & 1), ck + (b >> 2))];
-          if (e < 0) continue;
+            for (int b = 0; b < 8; ++b)
+              s += q1_khat(av, b) * T.x[0][h0 + (b & 1) + kHX * (((b >> 1) & 1) + kHY * (b >> 2))];
+            s *= g.h;
+          } else {
+            const double* Kc = a.K_cut + (int64_t)code * 64 + av * 8;
 #pragma unroll
-          for (int jc = 0; jc < 3; ++jc) {
-            const double x = val(3 * (int64_t)e + jc);
-            s0 += Ke[3 * b + jc] * x;
-            s1 += Ke[24 + 3 * b + jc] * x;
-            s2 += Ke[48 + 3 * b + jc] * x;
+            for (int b = 0; b < 8; ++b) s += Kc[b] * T.x[0][h0 + (b & 1) + kHX * (((b >> 1) & 1) + kHY * (b >> 2))];
           }
+          y[0] += kap * s;
+        } else {
+          // elasticity: y_c += kappa_e sum_b sum_j K_e[3 av + c][3 b + j] x_{3 e_b + j}
+          const double* Ke = (code == kCellInternal ? a.Kref : a.K_cut + (int64_t)code * 576) + 3 * av * 24;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const int hb = h0 + (b & 1) + kHX * (((b >> 1) & 1) + kHY * (b >> 2));
+            if (T.dof[hb] < 0) continue;
+#pragma unroll
+            for (int jc = 0; jc < 3; ++jc) {
+              const double x = T.x[jc][hb];
+              s0 += Ke[3 * b + jc] * x;
+              s1 += Ke[24 + 3 * b + jc] * x;
+              s2 += Ke[48 + 3 * b + jc] * x;
+            }
+          }
+          y[0] += kap * s0;
+          y[1] += kap * s1;
+          y[2] += kap * s2;
         }
-        y[0] += kap * s0;
-        y[1] += kap * s1;
-        y[2] += kap * s2;
       }
-}
-
-// the NC rows of free node d
-template <int NC, typename Val>
-__device__ __forceinline__ void apply_node(const OpArgs& a, int64_t d, Val val, double y[NC]) {
-  if constexpr (NC == 1)
-    y[0] = apply_row(a, d, val);
-  else
-    apply_node_el(a, d, val, y);
+  return d;
 }
 
 template <int NC>
-__global__ void __launch_bounds__(kApplyThreads) k_apply(OpArgs a, const double* __restrict__ x, double* __restrict__ y) {
-  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= a.n_dof) return;
+__global__ void __launch_bounds__(kTileThreads) k_apply(OpArgs a, const double* __restrict__ x, double* __restrict__ y) {
+  __shared__ ApplyTile<NC> T;
   double yy[NC];
-  apply_node<NC>(a, d, [&](int64_t e) { return x[e]; }, yy);
+  int hc;
+  const int32_t d = tile_apply<NC>(a, T, [&](int64_t e) { return x[e]; }, yy, &hc);
+  if (d < 0) return;
 #pragma unroll
-  for (int c = 0; c < NC; ++c) y[NC * d + c] = yy[c];
+  for (int c = 0; c < NC; ++c) y[NC * (int64_t)d + c] = yy[c];
 }
 
 // r = b - A x, |r|^2 and |b|^2; mode 0 initialises the scalars, mode 1 only reports |b - A x|^2
 template <int NC>
-__global__ void __launch_bounds__(kApplyThreads)
+__global__ void __launch_bounds__(kTileThreads)
 k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x, double* __restrict__ r,
            double* __restrict__ part, PcgScalars* sc, int mode, double* out) {
-  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ ApplyTile<NC> T;
+  double ax[NC];
+  int hc;
+  const int32_t d = tile_apply<NC>(a, T, [&](int64_t e) { return x[e]; }, ax, &hc);
   double rr = 0.0, bb = 0.0;
-  if (d < a.n_dof) {
-    double ax[NC];
-    apply_node<NC>(a, d, [&](int64_t e) { return x[e]; }, ax);
+  if (d >= 0) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      const double res = b[NC * d + c] - ax[c];
-      if (r) r[NC * d + c] = res;
+      const int64_t e = NC * (int64_t)d + c;
+      const double res = b[e] - ax[c];
+      if (r) r[e] = res;
       rr += res * res;
-      bb += b[NC * d + c] * b[NC * d + c];
+      bb += b[e] * b[e];
     }
   }
   rr = block_sum(rr);
@@ -260,24 +306,25 @@ k_residual(OpArgs a, const double* __restrict__ b, const double* __restrict__ x,
 
 // K1: p_new = z + beta p_old (beta = 0 for the first direction); q = A p_new; p.q
 template <int NC>
-__global__ void __launch_bounds__(kApplyThreads)
+__global__ void __launch_bounds__(kTileThreads)
 k_dir_apply(OpArgs a, const double* __restrict__ z, double* p0, double* p1, double* __restrict__ q,
             double* __restrict__ part, PcgScalars* sc) {
   if (sc->done) return;
+  __shared__ ApplyTile<NC> T;
   const int it = sc->iter;
   const double* pold = (it & 1) ? p1 : p0;
   double* pnew = (it & 1) ? p0 : p1;
   double beta = 0.0;
   if (!sc->first) beta = sc->flexible ? (sc->rz_next - sc->rzold_next) / sc->rz : sc->rz_next / sc->rz;
-  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double qd[NC];
+  int hc;
+  const int32_t d = tile_apply<NC>(a, T, [&](int64_t e) { return z[e] + beta * pold[e]; }, qd, &hc);
   double pq = 0.0;
-  if (d < a.n_dof) {
-    double qd[NC];
-    apply_node<NC>(a, d, [&](int64_t e) { return z[e] + beta * pold[e]; }, qd);
+  if (d >= 0) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      const int64_t e = NC * d + c;
-      const double pd = z[e] + beta * pold[e];
+      const int64_t e = NC * (int64_t)d + c;
+      const double pd = T.x[c][hc];
       pnew[e] = pd;
       q[e] = qd[c];
       pq += pd * qd[c];
@@ -611,6 +658,23 @@ __device__ void cluster_gather(cg::cluster_group& cl, V* local, int n) {
   }
 }
 
+// acc + sign v[NC s_k + c] for the first cnt slots s_k = gpos[8 xi + k] of node xi, added
+// in slot order; the eight slots and then the values are loaded together
+template <int NC>
+__device__ __forceinline__ double gather_slots(const int32_t* __restrict__ gpos, int64_t xi, int cnt, int c,
+                                              const double* __restrict__ v, double acc, double sign) {
+  const int4 pa = *reinterpret_cast<const int4*>(gpos + xi * 8);
+  const int4 pb = *reinterpret_cast<const int4*>(gpos + xi * 8 + 4);
+  const int sl[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = k < cnt ? v[(int64_t)NC * sl[k] + c] : 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (k < cnt) acc += sign * x[k];
+  return acc;
+}
+
 // K3: y_I = A_II^-1 r_I; t_G = A_GI y_I
 template <typename TM, int NC, int CL = kCL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSubThreads)
@@ -681,9 +745,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
     if (j < z.nG) {
       const int32_t xi = sm.G_list[sm.G_ptr[w] + j / NC];
       const int c = j % NC;
-      double s = r[(int64_t)NC * xi + c];
-      const int cnt = sm.n_neigh[xi];
-      for (int k = 0; k < cnt; ++k) s -= tG[(int64_t)NC * sm.gpos[(int64_t)xi * 8 + k] + c];
+      const double s = gather_slots<NC>(sm.gpos, xi, sm.n_neigh[xi], c, tG, r[(int64_t)NC * xi + c], -1.0);
       v = (TM)(sm.sG[g0 + j] * sm.w[g0 + j] * s);
     }
     xG[j] = v;
@@ -695,6 +757,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   const TM* P = Phi + sm.off_GC[w];
   for (int c0 = 0; c0 < z.nC; c0 += 64) {
     double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
     for (int j = r0 + wid; j < r1; j += nw) {
       const double xj = (double)xG[j];
       if (c0 + lane < z.nC) a0 += (double)P[(int64_t)j * z.ldC + c0 + lane] * xj;
@@ -773,10 +836,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   for (int j = threadIdx.x; j < zz.nG; j += blockDim.x) {
     const int32_t xi = sm.G_list[gn0 + j / NC];
     const int c = j % NC;
-    const int cnt = sm.n_neigh[xi];
-    double u = 0.0;
-    for (int k = 0; k < cnt; ++k) u += vw[(int64_t)NC * sm.gpos[(int64_t)xi * 8 + k] + c];
-    S.dG[j] = u;
+    S.dG[j] = gather_slots<NC>(sm.gpos, xi, sm.n_neigh[xi], c, vw, 0.0, 1.0);
   }
   __syncthreads();
   int j0, j1;
@@ -850,6 +910,8 @@ static OpArgs op_args(const System& sys) {
   a.K_cut = sys.K_cut.p;
   a.kappa = sys.has_kappa ? sys.kappa.p : nullptr;
   a.Kref = sys.Kref.p;
+  a.tiles = m.apply_tiles.p;
+  a.n_tiles = m.n_apply_tiles;
   return a;
 }
 
@@ -898,9 +960,9 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
   TimedLaunch t;
   t.begin("apply", s);
   if (sys.ncomp == 3)
-    k_apply<3><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+    k_apply<3><<<(unsigned)a.n_tiles, kTileThreads, 0, s>>>(a, x_dev, y_dev);
   else
-    k_apply<1><<<grid_for(a.n_dof, kApplyThreads), kApplyThreads, 0, s>>>(a, x_dev, y_dev);
+    k_apply<1><<<(unsigned)a.n_tiles, kTileThreads, 0, s>>>(a, x_dev, y_dev);
   UFE_CHECK_LAUNCH();
   t.end(s);
 }
@@ -1142,12 +1204,12 @@ void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
 }
 
 static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
-  const unsigned nb = grid_for(a.n_dof, kApplyThreads);
+  const unsigned nb = (unsigned)a.n_tiles;
   const int64_t nv = (int64_t)B.ncomp * a.n_dof;
   if (B.ncomp == 3)
-    k_dir_apply<3><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+    k_dir_apply<3><<<nb, kTileThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   else
-    k_dir_apply<1><<<nb, kApplyThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
+    k_dir_apply<1><<<nb, kTileThreads, 0, s>>>(a, B.z.p, B.p0.p, B.p1.p, B.q.p, B.part.p, B.sc.p);
   UFE_CHECK_LAUNCH();
   k_update<<<grid_for(nv, kApplyThreads), kApplyThreads, 0, s>>>(nv, B.x.p, B.r.p, B.p0.p, B.p1.p, B.q.p, B.part.p,
                                                                  B.sc.p);
@@ -1156,11 +1218,11 @@ static void launch_iteration(Bddc& B, const OpArgs& a, cudaStream_t s) {
 }
 
 static void launch_residual(Bddc& B, const OpArgs& a, int mode, double* r, double* out, cudaStream_t s) {
-  const unsigned nb = grid_for(a.n_dof, kApplyThreads);
+  const unsigned nb = (unsigned)a.n_tiles;
   if (B.ncomp == 3)
-    k_residual<3><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, r, B.part.p, B.sc.p, mode, out);
+    k_residual<3><<<nb, kTileThreads, 0, s>>>(a, B.b.p, B.x.p, r, B.part.p, B.sc.p, mode, out);
   else
-    k_residual<1><<<nb, kApplyThreads, 0, s>>>(a, B.b.p, B.x.p, r, B.part.p, B.sc.p, mode, out);
+    k_residual<1><<<nb, kTileThreads, 0, s>>>(a, B.b.p, B.x.p, r, B.part.p, B.sc.p, mode, out);
   UFE_CHECK_LAUNCH();
 }
 

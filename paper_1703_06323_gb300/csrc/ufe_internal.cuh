@@ -134,6 +134,17 @@ struct GridGeom {
   __host__ __device__ int n_blocks() const { return bx * by * bz; }
 };
 
+// The operator apply works on boxes of kApplyTX x kApplyTY x kApplyTZ grid nodes
+// ("node tiles", numbered x fastest); only tiles that hold a free DOF are launched.
+constexpr int kApplyTX = 8, kApplyTY = 8, kApplyTZ = 4;
+__host__ __device__ inline int apply_tiles_x(const GridGeom& g) { return (g.nx + kApplyTX) / kApplyTX; }
+__host__ __device__ inline int apply_tiles_y(const GridGeom& g) { return (g.ny + kApplyTY) / kApplyTY; }
+__host__ __device__ inline int apply_tiles_z(const GridGeom& g) { return (g.nz + kApplyTZ) / kApplyTZ; }
+__host__ __device__ inline int64_t apply_tile_of_node(const GridGeom& g, int i, int j, int k) {
+  return (int64_t)(i / kApplyTX) +
+         (int64_t)apply_tiles_x(g) * ((int64_t)(j / kApplyTY) + (int64_t)apply_tiles_y(g) * (k / kApplyTZ));
+}
+
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
@@ -142,7 +153,7 @@ struct Mesh {
   GridGeom g{};
   uint32_t face_mask = 0;
   int64_t pin = -1;
-  int64_t n_dof = 0, n_sub = 0, n_active = 0, n_cut = 0, n_gamma = 0, n_constrained = 0;
+  int64_t n_dof = 0, n_sub = 0, n_active = 0, n_cut = 0, n_gamma = 0, n_constrained = 0, n_apply_tiles = 0;
   int64_t n_Iloc = 0, n_Gloc = 0;   // sum over subdomains of interior / interface sizes
   int max_nI = 0, max_nG = 0;
 
@@ -151,6 +162,7 @@ struct Mesh {
   DBuf<uint8_t> node_flags;    // n_nodes: bit0 active, bit1 constrained, bit2 pin candidate
   DBuf<int32_t> dof_of_node;   // n_nodes
   DBuf<int32_t> node_of_dof;   // n_dof
+  DBuf<int32_t> apply_tiles;   // n_apply_tiles: node tiles of the operator apply holding a free DOF
   DBuf<int32_t> cut_index;     // n_cells: index into cut arrays or -1
   DBuf<int32_t> cut_cells;     // n_cut
   DBuf<int32_t> sub_of_cell;   // n_cells
