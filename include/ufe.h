@@ -356,7 +356,8 @@ ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
  * must not allocate device memory while they run: a serving loop that reserved
  * its memory budget up front, or host code called back from another framework
  * that owns the device allocator.  The paper has no counterpart; this is a
- * deployment variant.
+ * deployment variant.  It launches the same kernels, in the launch shape the set-up
+ * chose, as ufe_bddc_apply.
  *
  *  r, z   n doubles each (n = ncomp n_dof), DEVICE pointers on the current device (host
  *         pointers are not accepted: staging them would need an allocation).

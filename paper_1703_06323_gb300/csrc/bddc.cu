@@ -19,6 +19,7 @@
 #include <chrono>
 #include <cmath>
 #include <memory>
+#include <mutex>
 
 #include "bddc.cuh"
 #include "dense.cuh"
@@ -612,10 +613,14 @@ __global__ void k_scale_block(const double* __restrict__ src, T* __restrict__ ds
   const int nr = rptr[w + 1] - rptr[w], nc = cptr[w + 1] - cptr[w];
   const int ld = pad4(nc);
   const int64_t o = off[w];
+  // the local matrices are sparse (at most 27 nonzeros per row of a few hundred): only
+  // nonzeros are scaled, which keeps this pass at memory speed on the scarce FP64 pipe
   for (int i = blockIdx.x; i < nr; i += gridDim.x) {
     const double ri = sr[rptr[w] + i];
-    for (int j = threadIdx.x; j < ld; j += blockDim.x)
-      dst[o + (int64_t)i * ld + j] = (T)(j < nc ? src[o + (int64_t)i * ld + j] * ri * scl[cptr[w] + j] : 0.0);
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+      const double a = j < nc ? src[o + (int64_t)i * ld + j] : 0.0;
+      dst[o + (int64_t)i * ld + j] = (T)(a != 0.0 ? a * ri * scl[cptr[w] + j] : 0.0);
+    }
   }
 }
 
@@ -813,9 +818,8 @@ __global__ void k_scale_ptr(int64_t n, int nc, const int32_t* __restrict__ in, i
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-static void propagate(const Mesh& m, const Bddc& B, const uint8_t* active, int mode, const int32_t* std_obj,
+static void propagate(const Mesh& m, cudaStream_t s, const uint8_t* active, int mode, const int32_t* std_obj,
                       int32_t* label, const double* wv2 = nullptr) {
-  cudaStream_t s = B.stream;
   DBuf<int> changed;
   changed.alloc(1, s);
   for (int round = 0; round < 512; ++round) {
@@ -840,6 +844,26 @@ __global__ void k_init_labels(int64_t n, const uint8_t* __restrict__ nn, int32_t
   active[d] = g ? 1 : 0;
 }
 
+// scaled A_II in precision T and its inverse (step 1 of the local factorisations; it
+// needs only the mesh, so it runs while the objects are found); the pivot flags land
+// in status and are checked with the later steps
+template <typename T>
+static void factor_interior(Bddc& B, const std::vector<int64_t>& oII, int64_t nII, DBuf<double>& AII,
+                            DBuf<double>& sI, DBuf<T>& II, DBuf<int>& status) {
+  cudaStream_t s = B.stream;
+  const int ns = (int)B.mesh->n_sub;
+  status.zero();
+  DBuf<int64_t> dII;
+  dII.alloc(std::max<size_t>(oII.size(), 1), s);
+  UFE_CUDA(cudaMemcpyAsync(dII.p, oII.data(), oII.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  II.alloc(std::max<int64_t>(nII, 1), s);
+  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AII.p, II.p, dII.p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p);
+  UFE_CHECK_LAUNCH();
+  std::vector<InvDesc> inv;
+  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
+  batched_inverse<T>(inv, II.p, status.p, s, sizeof(T) == 4 ? T(1e-3) : T(0));
+}
+
 template <typename T>
 static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std::vector<int64_t>& oIG,
                             const std::vector<int64_t>& oGG, const std::vector<int64_t>& oCG,
@@ -847,7 +871,9 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
                             int64_t nGG, int64_t nCG, int64_t nGC, int64_t nCC, DBuf<double>& AII, DBuf<double>& AIG,
                             DBuf<double>& AGG, DBuf<double>& sI, DBuf<double>& sG, DBuf<int32_t>& ell_k,
                             DBuf<double>& ell_v, DBuf<T>& II, DBuf<T>& GG,
-                            DBuf<T>& GC, DBuf<double>& Acw, DBuf<double>& rho) {
+                            DBuf<T>& GC, DBuf<double>& Acw, DBuf<double>& rho, DBuf<int>& status,
+                            bool interior_ready) {
+  if (!interior_ready) factor_interior<T>(B, oII, nII, AII, sI, II, status);
   Mesh& m = *B.mesh;
   cudaStream_t s = B.stream;
   const int ns = (int)m.n_sub;
@@ -859,12 +885,9 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
     return std::unique_ptr<DBuf<int64_t>>(d);
   };
   auto dII = up(oII), dIG = up(oIG), dGG = up(oGG), dCG = up(oCG), dCC = up(oCC);
-  // scaled blocks in precision T
-  II.alloc(std::max<int64_t>(nII, 1), s);
+  // scaled blocks in precision T (A_II: factor_interior)
   DBuf<T> Cs, Crho, X, Y, Sc;
   GG.alloc(std::max<int64_t>(nGG, 1), s);
-  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AII.p, II.p, dII->p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p);
-  UFE_CHECK_LAUNCH();
   k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AGG.p, GG.p, dGG->p, B.vG_ptr.p, B.vG_ptr.p, sG.p, sG.p);
   UFE_CHECK_LAUNCH();
   Cs.alloc(std::max<int64_t>(nCG, 1), s);
@@ -879,9 +902,6 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
                                            B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p);
   UFE_CHECK_LAUNCH();
 
-  DBuf<int> status;
-  status.alloc(ns, s);
-  status.zero();
   // a non-positive pivot in one of the local inversions (in FP32 also a pivot of a
   // Jacobi-scaled matrix below 1e-3: the operators of such a subdomain are too
   // ill-conditioned to be stored and applied in FP32): name the matrix and subdomain
@@ -899,9 +919,7 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   const T floor = sizeof(T) == 4 ? T(1e-3) : T(0);
   std::vector<InvDesc> inv;
   std::vector<GemmDesc> g;
-  // 1. A_II^-1
-  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
-  batched_inverse<T>(inv, II.p, status.p, s, floor);
+  // 1. A_II^-1 (factor_interior)
   check("A_II");
   // 2. X^T = (A_II^-1 A_IG)^T and 3. S = A_GG - A_GI X, both from the sparse A_GI
   X.alloc(std::max<int64_t>(nIG, 1), s);
@@ -987,31 +1005,16 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   //     unscaled entries of a DOF with a 1e-40 diagonal would overflow FP32)
 }
 
-void bddc_build(Bddc& B) {
+// Objects (Sect. 3.2, 4.4, 4.5), coarse DOFs and the per-subdomain coarse lists, on
+// stream s.  They depend on the mesh (and, for variant 2, on the assembled cut cells)
+// only, so bddc_build runs them on a stream of their own next to the local matrices
+// and the interior inversions; the host waits here at every count it needs.
+static void build_objects(Bddc& B, cudaStream_t s) {
   Mesh& m = *B.mesh;
-  cudaStream_t s = B.stream;
   const int T = 256;
   const int64_t nd = m.n_dof;
   const int ns = (int)m.n_sub;
-  cudaEvent_t e0, e1;
-  UFE_CUDA(cudaEventCreate(&e0));
-  UFE_CUDA(cudaEventCreate(&e1));
-  UFE_CUDA(cudaEventRecord(e0, s));
-  B.status.alloc(1, s);
-  B.status.zero();
-  B.ncomp = B.sys->ncomp;
   const int NC = B.ncomp;
-  B.vI_ptr.alloc(ns + 1, s);
-  B.vG_ptr.alloc(ns + 1, s);
-  k_scale_ptr<<<grid_for(ns + 1, T), T, 0, s>>>(ns + 1, NC, m.I_ptr.p, B.vI_ptr.p);
-  UFE_CHECK_LAUNCH();
-  k_scale_ptr<<<grid_for(ns + 1, T), T, 0, s>>>(ns + 1, NC, m.G_ptr.p, B.vG_ptr.p);
-  UFE_CHECK_LAUNCH();
-  B.n_vIloc = NC * m.n_Iloc;
-  B.n_vGloc = NC * m.n_Gloc;
-  B.max_nIv = NC * m.max_nI;
-  B.max_nGv = NC * m.max_nG;
-
   TimedLaunch ph_obj;
   ph_obj.begin("phase_objects", s);
   // ---- standard objects
@@ -1022,7 +1025,7 @@ void bddc_build(Bddc& B) {
   flags.alloc(nd, s);
   k_init_labels<<<grid_for(nd, T), T, 0, s>>>(nd, m.n_neigh.p, label.p, active.p);
   UFE_CHECK_LAUNCH();
-  propagate(m, B, active.p, 0, nullptr, label.p);
+  propagate(m, s, active.p, 0, nullptr, label.p);
   DBuf<int32_t> rep_index;
   rep_index.alloc(nd, s);
   k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label.p, flags.p);
@@ -1053,7 +1056,7 @@ void bddc_build(Bddc& B) {
       k_v1_corners<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, m.dof_of_node.p, m.cell_type.p, m.phi.p,
                                                  B.obj_of_dof.p, B.obj_kind.p, corner.p, active.p, label2.p, label.p);
       UFE_CHECK_LAUNCH();
-      propagate(m, B, active.p, 1, B.obj_of_dof.p, label2.p);
+      propagate(m, s, active.p, 1, B.obj_of_dof.p, label2.p);
     } else {
       wv2.alloc(std::max<int64_t>(nd, 1) * 8, s);
       k_v2_weights<<<grid_for(nd, T), T, 0, s>>>(m.g, nd, m.node_of_dof.p, m.cell_type.p, m.sub_of_cell.p,
@@ -1064,7 +1067,7 @@ void bddc_build(Bddc& B) {
       k_v2_prepare<<<grid_for(nd, T), T, 0, s>>>(nd, B.obj_of_dof.p, B.obj_kind.p, corner.p, active.p, label2.p,
                                                  label.p);
       UFE_CHECK_LAUNCH();
-      propagate(m, B, active.p, 2, B.obj_of_dof.p, label2.p, wv2.p);
+      propagate(m, s, active.p, 2, B.obj_of_dof.p, label2.p, wv2.p);
     }
     k_rep_flags<<<grid_for(nd, T), T, 0, s>>>(nd, label2.p, flags.p);
     UFE_CHECK_LAUNCH();
@@ -1147,13 +1150,9 @@ void bddc_build(Bddc& B) {
     UFE_CHECK_LAUNCH();
   }
   std::vector<int32_t> hC = to_host(B.C_ptr.p, ns + 1, s);
-  B.h_nI.resize(ns);
-  B.h_nG.resize(ns);
   B.h_nC.resize(ns);
   B.max_nC = 0;
   for (int w = 0; w < ns; ++w) {
-    B.h_nI[w] = NC * (m.h_I_ptr[w + 1] - m.h_I_ptr[w]);
-    B.h_nG[w] = NC * (m.h_G_ptr[w + 1] - m.h_G_ptr[w]);
     B.h_nC[w] = hC[w + 1] - hC[w];
     B.max_nC = std::max(B.max_nC, B.h_nC[w]);
   }
@@ -1176,19 +1175,76 @@ void bddc_build(Bddc& B) {
   }
 
   ph_obj.end(s);
+}
+
+// the objects' stream (one per device, like the Gauss-Jordan look-ahead stream)
+static cudaStream_t objects_stream() {
+  static std::mutex mu;
+  static cudaStream_t st[128] = {};
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!st[dev]) UFE_CUDA(cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking));
+  return st[dev];
+}
+
+void bddc_build(Bddc& B) {
+  Mesh& m = *B.mesh;
+  cudaStream_t s = B.stream;
+  const int T = 256;
+  const int64_t nd = m.n_dof;
+  const int ns = (int)m.n_sub;
+  cudaEvent_t e0, e1;
+  UFE_CUDA(cudaEventCreate(&e0));
+  UFE_CUDA(cudaEventCreate(&e1));
+  UFE_CUDA(cudaEventRecord(e0, s));
+  B.status.alloc(1, s);
+  B.status.zero();
+  B.ncomp = B.sys->ncomp;
+  const int NC = B.ncomp;
+  B.vI_ptr.alloc(ns + 1, s);
+  B.vG_ptr.alloc(ns + 1, s);
+  k_scale_ptr<<<grid_for(ns + 1, T), T, 0, s>>>(ns + 1, NC, m.I_ptr.p, B.vI_ptr.p);
+  UFE_CHECK_LAUNCH();
+  k_scale_ptr<<<grid_for(ns + 1, T), T, 0, s>>>(ns + 1, NC, m.G_ptr.p, B.vG_ptr.p);
+  UFE_CHECK_LAUNCH();
+  B.n_vIloc = NC * m.n_Iloc;
+  B.n_vGloc = NC * m.n_Gloc;
+  B.max_nIv = NC * m.max_nI;
+  B.max_nGv = NC * m.max_nG;
+
+  B.h_nI.resize(ns);
+  B.h_nG.resize(ns);
+  for (int w = 0; w < ns; ++w) {
+    B.h_nI[w] = NC * (m.h_I_ptr[w + 1] - m.h_I_ptr[w]);
+    B.h_nG[w] = NC * (m.h_G_ptr[w + 1] - m.h_G_ptr[w]);
+  }
+  // the objects (build_objects) need only the mesh: they start on their own stream once
+  // the local matrices and the interior inversions are queued on this one
+  cudaStream_t so = objects_stream();
+  cudaEvent_t fork_ev, join_ev;
+  UFE_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  UFE_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+  UFE_CUDA(cudaEventRecord(fork_ev, s));
+  struct EventsGuard {
+    cudaEvent_t a, b;
+    ~EventsGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } events_guard{fork_ev, join_ev};
+
   TimedLaunch ph_loc;
   ph_loc.begin("phase_local", s);
-  // ---- storage offsets
+  // ---- storage offsets (the coarse ones once the objects are known)
   std::vector<int64_t> oII(ns), oIG(ns), oGG(ns), oCG(ns), oGC(ns), oCC(ns);
   int64_t nII = 0, nIG = 0, nGG = 0, nCG = 0, nGC = 0, nCC = 0;
   for (int w = 0; w < ns; ++w) {
-    const int nI = B.h_nI[w], nG = B.h_nG[w], nc = B.h_nC[w];
+    const int nI = B.h_nI[w], nG = B.h_nG[w];
     oII[w] = nII; nII += (int64_t)nI * pad4(nI);
     oIG[w] = nIG; nIG += (int64_t)nG * pad4(nI);   // X^T (interface rows x interior columns)
     oGG[w] = nGG; nGG += (int64_t)nG * pad4(nG);
-    oCG[w] = nCG; nCG += (int64_t)nc * pad4(nG);
-    oGC[w] = nGC; nGC += (int64_t)nG * pad4(nc);
-    oCC[w] = nCC; nCC += (int64_t)nc * pad4(nc);
   }
   auto upload = [&](DBuf<int64_t>& d, const std::vector<int64_t>& v) {
     d.alloc(v.size(), s);
@@ -1196,12 +1252,10 @@ void bddc_build(Bddc& B) {
   };
   upload(B.off_II, oII);
   upload(B.off_GG, oGG);
-  upload(B.off_GC, oGC);
   {
     const double tm = B.mixed ? 4.0 : 8.0;
     B.bytes_II = tm * nII;
     B.bytes_GG = tm * nGG;
-    B.bytes_GC = tm * nGC;
     B.bytes_off = 12.0 * 27 * NC * (double)(B.n_vGloc + B.n_vIloc);
   }
 
@@ -1250,13 +1304,39 @@ void bddc_build(Bddc& B) {
   ph_loc.end(s);
   TimedLaunch ph_fac;
   ph_fac.begin("phase_factor", s);
-  // ---- factorisations and explicit local operators
+  // ---- factorisations and explicit local operators; step 1 (A_II^-1) is queued
+  // before the objects are found
+  DBuf<int> status;
+  status.alloc(ns, s);
+  if (B.mixed) {
+    B.local_tc = fp32_tensor_cores() ? 1 : 0;
+    factor_interior<float>(B, oII, nII, AII, sI, B.fII, status);
+  } else {
+    factor_interior<double>(B, oII, nII, AII, sI, B.dII, status);
+  }
+  UFE_CUDA(cudaStreamWaitEvent(so, fork_ev, 0));
+  build_objects(B, so);
+  UFE_CUDA(cudaEventRecord(join_ev, so));
+  UFE_CUDA(cudaStreamWaitEvent(s, join_ev, 0));
+  // the object buffers are used (and released) on this stream from here on
+  B.obj_of_dof.s = B.obj_size.s = B.obj_rep.s = B.obj_kind.s = B.coarse_of_obj.s = B.obj_nrows.s = B.obj_rot.s = s;
+  B.obj_lo.s = B.obj_hi.s = B.coarse_obj.s = B.coarse_rep.s = B.C_ptr.s = B.C_list.s = B.cpos.s = s;
+  B.obj_sum.s = s;
+  B.coarse_nn.s = s;
+  for (int w = 0; w < ns; ++w) {
+    const int nG = B.h_nG[w], nc = B.h_nC[w];
+    oCG[w] = nCG; nCG += (int64_t)nc * pad4(nG);
+    oGC[w] = nGC; nGC += (int64_t)nG * pad4(nc);
+    oCC[w] = nCC; nCC += (int64_t)nc * pad4(nc);
+  }
+  upload(B.off_GC, oGC);
+  B.bytes_GC = (B.mixed ? 4.0 : 8.0) * nGC;
+  const int64_t nco = B.n_coarse;
   DBuf<double> Acw, rho;
   if (B.mixed) {
     try {
-      B.local_tc = fp32_tensor_cores() ? 1 : 0;
       factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
-                             ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho);
+                             ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho, status, true);
     } catch (const Error& e) {
       B.local_tc = 0;
       if (e.code != UFE_ERR_SINGULAR_LOCAL) throw;
@@ -1271,11 +1351,11 @@ void bddc_build(Bddc& B) {
       B.bytes_GG *= 2.0;
       B.bytes_GC *= 2.0;
       factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
-                              ell_k, ell_v, B.dII, B.dGG, B.dGC, Acw, rho);
+                              ell_k, ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, false);
     }
   } else
     factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,
-                            ell_v, B.dII, B.dGG, B.dGC, Acw, rho);
+                            ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, true);
   AII.release();
   AIG.release();
   AGG.release();

@@ -52,6 +52,11 @@ __device__ __forceinline__ float warp_sumf(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// a warp sum in the operator's precision: FP32 partials of the FP32 operators are
+// summed in FP32 (five FP64 adds per row cost more FP64-pipe time on this part than
+// the whole FP32 row product), FP64 ones in FP64
+__device__ __forceinline__ float warp_sum_tm(float v) { return warp_sumf(v); }
+__device__ __forceinline__ double warp_sum_tm(double v) { return warp_sum(v); }
 
 // deterministic block sum (fixed tree); all threads get the result
 __device__ double block_sum(double v) {
@@ -125,13 +130,15 @@ struct ApplyTile {
   double kap[kTileCells];
   int32_t code[kTileCells];   // cut index, kCellInternal, or kCellNone (external / off the grid)
   int32_t dof[kHalo];
+  int16_t node[kTileThreads];  // the box's free nodes, in box order (thread t takes node[t])
+  int32_t warp_free[kTileThreads / 32];
 };
 
-// Stages the tile and returns the free DOF of the calling thread's node (-1 if the
-// node is not free), with its NC rows of A x in y (x entry e = NC dof + component is
-// load(e)).  The cells around a node are visited in the same order, and each cell's
-// row summed in the same order, for every node, so results do not depend on the tiling.
-// Every thread of the CTA must call it.  The staging loads are issued in rounds
+// Stages the tile and returns the free DOF of the node the calling thread computes
+// (-1 if it has none), with its NC rows of A x in y (x entry e = NC dof + component is
+// load(e)) and its halo index in *hc_out.  The cells around a node are visited in the
+// same order, and each cell's row summed in the same order, for every node, so results
+// do not depend on the tiling.  Every thread of the CTA must call it.  The staging loads are issued in rounds
 // (all DOF numbers and cell records, then all input values) so that each thread has
 // all of its loads of a round in flight at once.
 template <int NC, typename Load>
@@ -190,13 +197,61 @@ __device__ __forceinline__ int32_t tile_apply(const OpArgs& a, ApplyTile<NC>& T,
     }
   }
   __syncthreads();
-  const int lx = threadIdx.x % kTX, ly = (threadIdx.x / kTX) % kTY, lz = threadIdx.x / (kTX * kTY);
+  // the free nodes of the box are packed onto the first threads (most boxes are
+  // partly outside the domain; the FP64 rows then run on full warps)
+  {
+    const int tlx = threadIdx.x % kTX, tly = (threadIdx.x / kTX) % kTY, tlz = threadIdx.x / (kTX * kTY);
+    const bool free_node = T.dof[(tlx + 1) + kHX * ((tly + 1) + kHY * (tlz + 1))] >= 0;
+    const unsigned m = __ballot_sync(0xffffffffu, free_node);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) T.warp_free[wid] = __popc(m);
+    __syncthreads();
+    int rank = __popc(m & ((1u << lane) - 1u));
+    for (int q = 0; q < wid; ++q) rank += T.warp_free[q];
+    if (free_node) T.node[rank] = (int16_t)threadIdx.x;
+    __syncthreads();
+    int total = 0;
+    for (int q = 0; q < kTileThreads / 32; ++q) total += T.warp_free[q];
+    if ((int)threadIdx.x >= total) {
+      *hc_out = 0;
+      return -1;
+    }
+  }
+  const int tn = T.node[threadIdx.x];
+  const int lx = tn % kTX, ly = (tn / kTX) % kTY, lz = tn / (kTX * kTY);
   const int hc = (lx + 1) + kHX * ((ly + 1) + kHY * (lz + 1));
   *hc_out = hc;
   const int32_t d = T.dof[hc];
-  if (d < 0) return -1;
 #pragma unroll
   for (int c = 0; c < NC; ++c) y[c] = 0.0;
+  if constexpr (NC == 1) {
+    // a node whose eight cells are all internal with one coefficient: the assembled
+    // Q1 stencil, kappa h (8/3 x_0 - 1/6 sum of the 12 edge neighbours - 1/12 sum of the
+    // 8 corner neighbours) (the face neighbours' entries cancel to zero)
+    bool plain = true;
+    const double k0 = T.kap[lx + kCX * (ly + kCY * lz)];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int cq = (lx + (q & 1)) + kCX * ((ly + ((q >> 1) & 1)) + kCY * (lz + (q >> 2)));
+      plain = plain && T.code[cq] == kCellInternal && T.kap[cq] == k0;
+    }
+    if (plain) {
+      double se = 0.0, sc = 0.0;
+#pragma unroll
+      for (int oz = -1; oz <= 1; ++oz)
+#pragma unroll
+        for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int nz = (ox != 0) + (oy != 0) + (oz != 0);
+            const double v = T.x[0][hc + ox + kHX * (oy + kHY * oz)];
+            if (nz == 2) se += v;
+            if (nz == 3) sc += v;
+          }
+      y[0] = k0 * g.h * ((8.0 / 3.0) * T.x[0][hc] - (1.0 / 6.0) * se - (1.0 / 12.0) * sc);
+      return d;
+    }
+  }
 #pragma unroll
   for (int dk = -1; dk <= 0; ++dk)
 #pragma unroll
@@ -427,9 +482,7 @@ __device__ void cta_gemv_rows(const TM* __restrict__ M, int r0, int r1, int ld, 
       sa += dot_vec(va, xs + c);
       sb += dot_vec(vb, xs + c);
     }
-    double da = (double)sa, db = (double)sb;
-    da = warp_sum(da);
-    db = warp_sum(db);
+    const double da = (double)warp_sum_tm(sa), db = (double)warp_sum_tm(sb);
     if (lane == 0) {
       ys[r] = da;
       ys[r + nw] = db;
@@ -439,7 +492,7 @@ __device__ void cta_gemv_rows(const TM* __restrict__ M, int r0, int r1, int ld, 
     const TM* ra = M + (int64_t)r * ld;
     TM sa = TM(0);
     for (int c = lane * VN; c < ld; c += 32 * VN) sa += dot_vec(*reinterpret_cast<const V*>(ra + c), xs + c);
-    double da = warp_sum((double)sa);
+    const double da = (double)warp_sum_tm(sa);
     if (lane == 0) ys[r] = da;
   }
 }
@@ -602,7 +655,7 @@ struct RowStream {
         const TM* row = buf + ((size_t)slot * kStreamRows + wid) * ld;
         TM acc = TM(0);
         for (int c = lane * VN; c < ld; c += 32 * VN) acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
-        const double d = warp_sum((double)acc);
+        const double d = (double)warp_sum_tm(acc);
         if (lane == 0) ys[i] = d;
       }
       __syncthreads();
@@ -629,9 +682,9 @@ __device__ void cta_gemv_short(const TM* __restrict__ M, int r0, int r1, int ld,
       const TM* row = M + (int64_t)r * ld;
       for (int c = sub * VN; c < ld; c += G * VN) acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
     }
-    double d = (double)acc;
+    TM d = acc;
     for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (r < r1 && sub == 0) ys[r] = d;
+    if (r < r1 && sub == 0) ys[r] = (double)d;
   }
 }
 
@@ -756,15 +809,15 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const TM* P = Phi + sm.off_GC[w];
   for (int c0 = 0; c0 < z.nC; c0 += 64) {
-    double a0 = 0.0, a1 = 0.0;
+    TM a0 = TM(0), a1 = TM(0);   // in the operator's precision (FP64 adds are scarce)
 #pragma unroll 4
     for (int j = r0 + wid; j < r1; j += nw) {
-      const double xj = (double)xG[j];
-      if (c0 + lane < z.nC) a0 += (double)P[(int64_t)j * z.ldC + c0 + lane] * xj;
-      if (c0 + lane + 32 < z.nC) a1 += (double)P[(int64_t)j * z.ldC + c0 + lane + 32] * xj;
+      const TM xj = xG[j];
+      if (c0 + lane < z.nC) a0 += P[(int64_t)j * z.ldC + c0 + lane] * xj;
+      if (c0 + lane + 32 < z.nC) a1 += P[(int64_t)j * z.ldC + c0 + lane + 32] * xj;
     }
-    gpart[wid][lane] = a0;
-    gpart[wid][lane + 32] = a1;
+    gpart[wid][lane] = (double)a0;
+    gpart[wid][lane + 32] = (double)a1;
     __syncthreads();
     if (threadIdx.x < 64 && c0 + (int)threadIdx.x < z.nC) {
       double sacc = 0.0;
@@ -1443,9 +1496,9 @@ static double* noalloc_scratch_ptr() {
   return ptr[dev];
 }
 
-template <typename TM, int NC>
-static void launch_preconditioner_static(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
-                                         double* uc, cudaStream_t s) {
+template <typename TM, int NC, int CL>
+static void launch_preconditioner_static_cl(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
+                                            double* uc, cudaStream_t s) {
   const Mesh& m = *B.mesh;
   const SubMeta sm = B.meta();
   const int ns = (int)m.n_sub;
@@ -1454,17 +1507,29 @@ static void launch_preconditioner_static(Bddc& B, const double* r, double* z, do
   const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
   const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
   const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
-  k_prec_interior1<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, L);
+  k_prec_interior1<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, L);
   UFE_CHECK_LAUNCH();
-  k_prec_neumann<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
+  k_prec_neumann<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
   UFE_CHECK_LAUNCH();
   if (B.n_coarse > 0) {
     coarse_solve(B, gC, uc, uc + kNoAllocU, nullptr, s);
-    k_prec_prolong<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
+    k_prec_prolong<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
     UFE_CHECK_LAUNCH();
   }
-  k_prec_final<TM, NC><<<ns * kCL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, L, 0);
+  k_prec_final<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, L, 0);
   UFE_CHECK_LAUNCH();
+}
+
+// the launch shape the tuner chose, as in the allocating apply (same kernels, same order)
+template <typename TM, int NC>
+static void launch_preconditioner_static(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
+                                         double* uc, cudaStream_t s) {
+  if (NC == 1 && B.prec_cl == 2)
+    launch_preconditioner_static_cl<TM, NC, 2>(B, r, z, tG, vw, gC, uc, s);
+  else if (NC == 1 && B.prec_cl == 8)
+    launch_preconditioner_static_cl<TM, NC, 8>(B, r, z, tG, vw, gC, uc, s);
+  else
+    launch_preconditioner_static_cl<TM, NC, kCL>(B, r, z, tG, vw, gC, uc, s);
 }
 
 void bddc_noalloc_prepare(Bddc& B) {

@@ -1,7 +1,9 @@
 """Launch shapes of the per-iteration preconditioner kernels: every cluster size (2, 4,
 8 CTAs per subdomain) and stage count gives the same z = M r (the slices of the dense
 GEMVs change, the arithmetic of each row does not; the coarse restriction sums its
-slices in a different order) and the same PCG iterations; the tuner reports a shape
+slices in a different order, in FP64 for FP64 operators and from FP32 partial sums
+over each CTA's rows for FP32 ones, so mixed precision agrees to FP32 rounding) and
+the same PCG iterations (within one in mixed precision); the tuner reports a shape
 from its candidate set and reuses it for a second problem of the same size class."""
 import os
 
@@ -48,9 +50,10 @@ def test_every_launch_shape_gives_the_same_preconditioner(env, name, precision):
         else:
             os.environ["UFE_PREC_SHAPE"] = saved
     z0, it0 = out["4,0"]
+    tol, dit = (1e-12, 0) if precision == "fp64" else (1e-5, 1)
     for shape, (z, it) in out.items():
-        assert np.linalg.norm(z - z0) <= 1e-12 * np.linalg.norm(z0), shape
-        assert it == it0, shape
+        assert np.linalg.norm(z - z0) <= tol * np.linalg.norm(z0), shape
+        assert abs(it - it0) <= dit, shape
 
 
 def test_tuner_picks_a_candidate_and_caches_it(env):
