@@ -1168,8 +1168,9 @@ static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, in
 // subdomain cluster (2, 4, 8) and row-stream stages per CTA (1, 2, 4).  The first
 // set-up of a size class (device, precision, interior and interface sizes in steps of
 // 32, subdomain count in powers of two) times each candidate with CUDA events (one
-// warm-up and three applications of z = M r on the preconditioner's own work vectors)
-// and caches the fastest for the process; later set-ups of the class reuse it.
+// warm-up and three applications of z = M r on the preconditioner's own work vectors,
+// in three interleaved rounds, keeping each candidate's fastest) and caches the
+// fastest for the process; later set-ups of the class reuse it.
 // UFE_AUTOTUNE=0 keeps the default shape (4 CTAs, stages from the shared-memory budget).
 // ---------------------------------------------------------------------------
 static bool autotune_enabled() {
@@ -1213,15 +1214,20 @@ void tune_preconditioner(Bddc& B) {
   cudaEvent_t e0, e1;
   UFE_CUDA(cudaEventCreate(&e0));
   UFE_CUDA(cudaEventCreate(&e1));
-  float best = 1e30f;
+  // every shape is timed in each of kRounds interleaved rounds (so that a slow moment of
+  // the device does not single one out) and scored by its fastest round
+  constexpr int kRounds = 3;
+  const int shapes[9][2] = {{2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4}};
+  float score[9];
+  for (float& v : score) v = 1e30f;
   std::pair<int, int> pick = {kCL, 0};
   const bool was_timing = timing_enabled();
   set_timing_enabled(false);   // the tuner's launches stay out of the instrumentation records
   try {
-    for (int cl : {2, 4, 8})
-      for (int st : {1, 2, 4}) {
-        B.prec_cl = cl;
-        B.prec_stages = st;
+    for (int round = 0; round < kRounds; ++round)
+      for (int k = 0; k < 9; ++k) {
+        B.prec_cl = shapes[k][0];
+        B.prec_stages = shapes[k][1];
         precondition(B, B.r.p, B.z.p, nullptr, 0, s);
         UFE_CUDA(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 3; ++rep) precondition(B, B.r.p, B.z.p, nullptr, 0, s);
@@ -1229,10 +1235,13 @@ void tune_preconditioner(Bddc& B) {
         UFE_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         UFE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          pick = {cl, st};
-        }
+        score[k] = std::min(score[k], ms);
+      }
+    float best = 1e30f;
+    for (int k = 0; k < 9; ++k)
+      if (score[k] < best) {
+        best = score[k];
+        pick = {shapes[k][0], shapes[k][1]};
       }
   } catch (...) {
     set_timing_enabled(was_timing);
