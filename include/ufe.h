@@ -302,14 +302,13 @@ typedef struct {
    * A_IG stencils (index + value per slot), the FP64 coarse solver's matrices */
   double bytes_interior_inverse, bytes_neumann, bytes_coarse_basis, bytes_offdiag, bytes_coarse_inverse;
   int64_t interior_slots, interface_slots;   /* sum over subdomains of local interior / interface DOFs */
-  int32_t fp64_refactor;   /* mixed precision requested: 1 when a Jacobi-scaled local matrix had an FP32
-                              pivot below 1e-3 (or not positive), or the FP32 coarse basis missed
-                              C Phi = I by more than 1e-2, so this problem keeps FP64 local
-                              operators (factored and applied in FP64, classical PCG) */
+  int32_t fp64_refactor;   /* mixed precision requested: 1 when no subdomain could keep FP32 local
+                              operators (see fp64_subdomains), so the whole problem is factored and
+                              applied in FP64 (classical PCG) */
   int32_t coarse_solver;   /* the coarse solver used: UFE_COARSE_SOLVER_DENSE or _CR */
-  double cphi_error;       /* mixed precision requested: max over subdomains of max |C Phi - I| of the
-                              FP32 coarse basis (Sect. 3.2 defines Phi by C Phi = I); above 1e-2
-                              the problem keeps FP64 local operators (fp64_refactor = 1) */
+  double cphi_error;       /* mixed precision requested: max |C Phi - I| of the FP32 coarse basis (Sect.
+                              3.2 defines Phi by C Phi = I) over the subdomains that keep FP32
+                              operators; a subdomain above 1e-2 gets FP64 operators */
   int32_t coarse_layers, coarse_levels;   /* cyclic reduction: non-empty z layers, reduction levels */
   int32_t local_tensor_cores;   /* 1 when the FP32 local inversions ran their Gauss-Jordan updates on the
                                    tensor cores (3xTF32 split products, tcgen05), 0 otherwise */
@@ -318,6 +317,11 @@ typedef struct {
                                           shared-memory budget), chosen by timing the candidates once per
                                           size class and process (Poisson; UFE_AUTOTUNE=0 keeps 4 and 0;
                                           UFE_PREC_SHAPE="cl,stages" fixes them) */
+  int32_t fp64_subdomains;   /* mixed precision requested: subdomains whose local operators are FP64 --
+                                those whose Jacobi-scaled A_II or S' had an FP32 pivot below 1e-3 (or
+                                not positive), or whose FP32 coarse basis missed C Phi = I by more
+                                than 1e-2 (tiny cut fractions); they are factored and applied in
+                                FP64, the others in FP32 */
 } ufe_bddc_info;
 
 /*

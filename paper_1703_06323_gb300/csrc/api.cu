@@ -550,6 +550,7 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->local_tensor_cores = B->local_tc;
     info->prec_cluster = B->prec_cl;
     info->prec_stages = B->prec_stages;
+    info->fp64_subdomains = B->fp64_refactor ? (int32_t)B->mesh->n_sub : (B->mixed ? B->n_sub64 : 0);
     info->coarse_levels = B->cr.nlevels;
   });
 }

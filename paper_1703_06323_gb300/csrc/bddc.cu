@@ -475,8 +475,9 @@ __global__ void k_off_ell(SubMeta sm, int rows_kind, int32_t* __restrict__ ell_k
 // scaled A^_GI entries: s_G[j] A_GI[j][k] s_I[k]  (KS = 27 NC slots per row)
 template <typename T>
 __global__ void k_ell_scale(SubMeta sm, int KS, const int32_t* __restrict__ ell_k, const double* __restrict__ ell_v,
-                            const double* __restrict__ sI, const double* __restrict__ sG, T* __restrict__ ell_s) {
-  const int w = blockIdx.y;
+                            const double* __restrict__ sI, const double* __restrict__ sG, T* __restrict__ ell_s,
+                            const int32_t* __restrict__ wl) {
+  const int w = wl ? wl[blockIdx.y] : (int)blockIdx.y;
   const int nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nG * KS; e += gridDim.x * blockDim.x) {
     const int64_t slot = (int64_t)sm.vG_ptr[w] * KS + e;
@@ -490,10 +491,11 @@ constexpr int kMaxKS = 81;
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_xt(SubMeta sm, int KS, const int64_t* __restrict__ oII, const int64_t* __restrict__ oGI,
-     const int32_t* __restrict__ ell_k, const T* __restrict__ ell_s, const T* __restrict__ IIinv, T* __restrict__ Xt) {
+     const int32_t* __restrict__ ell_k, const T* __restrict__ ell_s, const T* __restrict__ IIinv, T* __restrict__ Xt,
+     const int32_t* __restrict__ wl) {
   __shared__ int32_t sk[8][kMaxKS];
   __shared__ T sv[8][kMaxKS];
-  const int w = blockIdx.y;
+  const int w = wl ? wl[blockIdx.y] : (int)blockIdx.y;
   const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int ldI = pad4(nI);
   const int j0 = blockIdx.x * 8;
@@ -524,10 +526,11 @@ k_xt(SubMeta sm, int KS, const int64_t* __restrict__ oII, const int64_t* __restr
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_schur(SubMeta sm, int KS, const int64_t* __restrict__ oGG, const int64_t* __restrict__ oGI,
-        const int32_t* __restrict__ ell_k, const T* __restrict__ ell_s, const T* __restrict__ Xt, T* __restrict__ GG) {
+        const int32_t* __restrict__ ell_k, const T* __restrict__ ell_s, const T* __restrict__ Xt, T* __restrict__ GG,
+        const int32_t* __restrict__ wl) {
   extern __shared__ __align__(16) char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);
-  const int w = blockIdx.y, j = blockIdx.x;
+  const int w = wl ? wl[blockIdx.y] : (int)blockIdx.y, j = blockIdx.x;
   const int nI = sm.vI_ptr[w + 1] - sm.vI_ptr[w], nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   if (j >= nG) return;
   const int ldI = pad4(nI), ldG = pad4(nG);
@@ -608,8 +611,9 @@ __global__ void k_weights(int64_t n_dof, int nc, const uint8_t* __restrict__ nn,
 template <typename T>
 __global__ void k_scale_block(const double* __restrict__ src, T* __restrict__ dst, const int64_t* __restrict__ off,
                               const int32_t* __restrict__ rptr, const int32_t* __restrict__ cptr,
-                              const double* __restrict__ sr, const double* __restrict__ scl) {
-  const int w = blockIdx.y;
+                              const double* __restrict__ sr, const double* __restrict__ scl,
+                              const int32_t* __restrict__ wl) {
+  const int w = wl ? wl[blockIdx.y] : (int)blockIdx.y;
   const int nr = rptr[w + 1] - rptr[w], nc = cptr[w + 1] - cptr[w];
   const int ld = pad4(nc);
   const int64_t o = off[w];
@@ -635,8 +639,8 @@ __global__ void k_constraints(SubMeta sm, const int32_t* __restrict__ node_of_do
                               const int32_t* __restrict__ obj_size, const int32_t* __restrict__ obj_rot,
                               const long long* __restrict__ obj_sum, const double* __restrict__ sG,
                               const int64_t* __restrict__ oCG, T* __restrict__ Cs, T* __restrict__ Crho,
-                              double* __restrict__ rho) {
-  const int w = blockIdx.x;
+                              double* __restrict__ rho, const int32_t* __restrict__ wl) {
+  const int w = wl ? wl[blockIdx.x] : (int)blockIdx.x;
   const int nGn = sm.G_ptr[w + 1] - sm.G_ptr[w];
   const int nG = sm.vG_ptr[w + 1] - sm.vG_ptr[w];
   const int c0 = sm.C_ptr[w], nC = sm.C_ptr[w + 1] - c0;
@@ -745,8 +749,9 @@ __global__ void k_coarse_first(int64_t n_obj, const int32_t* __restrict__ counts
 // A_c^w = (C S'^-1 C^T)^-1 - rho  (FP64)
 template <typename T>
 __global__ void k_coarse_local(const int32_t* __restrict__ C_ptr, const int64_t* __restrict__ oCC,
-                               const T* __restrict__ invSc, const double* __restrict__ rho, double* __restrict__ Acw) {
-  const int w = blockIdx.x;
+                               const T* __restrict__ invSc, const double* __restrict__ rho, double* __restrict__ Acw,
+                               const int32_t* __restrict__ wl) {
+  const int w = wl ? wl[blockIdx.x] : (int)blockIdx.x;
   const int c0 = C_ptr[w], nC = C_ptr[w + 1] - c0, ldC = pad4(nC);
   for (int e = threadIdx.x; e < nC * nC; e += blockDim.x) {
     const int i = e / nC, j = e % nC;
@@ -761,8 +766,9 @@ __global__ void k_coarse_local(const int32_t* __restrict__ C_ptr, const int64_t*
 // max |E - I|, and a subdomain above tol is flagged DEV_ILLCOND
 template <typename T>
 __global__ void k_cphi_error(const int32_t* __restrict__ C_ptr, const int64_t* __restrict__ oCC,
-                             const T* __restrict__ E, double tol, double* __restrict__ err, int* status) {
-  const int w = blockIdx.x;
+                             const T* __restrict__ E, double tol, double* __restrict__ err, int* status,
+                             const int32_t* __restrict__ wl) {
+  const int w = wl ? wl[blockIdx.x] : (int)blockIdx.x;
   const int nC = C_ptr[w + 1] - C_ptr[w], ldC = pad4(nC);
   double m = 0.0;
   for (int e = threadIdx.x; e < nC * nC; e += blockDim.x) {
@@ -846,21 +852,24 @@ __global__ void k_init_labels(int64_t n, const uint8_t* __restrict__ nn, int32_t
 
 // scaled A_II in precision T and its inverse (step 1 of the local factorisations; it
 // needs only the mesh, so it runs while the objects are found); the pivot flags land
-// in status and are checked with the later steps
+// in status and are checked with the later steps.  ws lists the subdomains to factor
+// (wl: the same list on the device, or null when ws holds every subdomain).
 template <typename T>
 static void factor_interior(Bddc& B, const std::vector<int64_t>& oII, int64_t nII, DBuf<double>& AII,
-                            DBuf<double>& sI, DBuf<T>& II, DBuf<int>& status) {
+                            DBuf<double>& sI, DBuf<T>& II, DBuf<int>& status, const std::vector<int>& ws,
+                            const int32_t* wl) {
   cudaStream_t s = B.stream;
-  const int ns = (int)B.mesh->n_sub;
+  const int nw = (int)ws.size();
   status.zero();
   DBuf<int64_t> dII;
   dII.alloc(std::max<size_t>(oII.size(), 1), s);
   UFE_CUDA(cudaMemcpyAsync(dII.p, oII.data(), oII.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   II.alloc(std::max<int64_t>(nII, 1), s);
-  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AII.p, II.p, dII.p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p);
+  if (nw > 0)
+    k_scale_block<T><<<dim3(64, nw), 128, 0, s>>>(AII.p, II.p, dII.p, B.vI_ptr.p, B.vI_ptr.p, sI.p, sI.p, wl);
   UFE_CHECK_LAUNCH();
   std::vector<InvDesc> inv;
-  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
+  for (int w : ws) inv.push_back({B.h_nI[w], pad4(B.h_nI[w]), oII[w]});
   batched_inverse<T>(inv, II.p, status.p, s, sizeof(T) == 4 ? T(1e-3) : T(0));
 }
 
@@ -872,11 +881,13 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
                             DBuf<double>& AGG, DBuf<double>& sI, DBuf<double>& sG, DBuf<int32_t>& ell_k,
                             DBuf<double>& ell_v, DBuf<T>& II, DBuf<T>& GG,
                             DBuf<T>& GC, DBuf<double>& Acw, DBuf<double>& rho, DBuf<int>& status,
-                            bool interior_ready) {
-  if (!interior_ready) factor_interior<T>(B, oII, nII, AII, sI, II, status);
+                            bool interior_ready, const std::vector<int>& ws, const int32_t* wl,
+                            std::vector<char>* bad) {
+  if (!interior_ready) factor_interior<T>(B, oII, nII, AII, sI, II, status, ws, wl);
   Mesh& m = *B.mesh;
   cudaStream_t s = B.stream;
   const int ns = (int)m.n_sub;
+  const int nw = (int)ws.size();
   const SubMeta sm = B.meta();
   auto up = [&](const std::vector<int64_t>& v) {
     DBuf<int64_t>* d = new DBuf<int64_t>();
@@ -888,33 +899,40 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   // scaled blocks in precision T (A_II: factor_interior)
   DBuf<T> Cs, Crho, X, Y, Sc;
   GG.alloc(std::max<int64_t>(nGG, 1), s);
-  k_scale_block<T><<<dim3(64, ns), 128, 0, s>>>(AGG.p, GG.p, dGG->p, B.vG_ptr.p, B.vG_ptr.p, sG.p, sG.p);
+  k_scale_block<T><<<dim3(64, nw), 128, 0, s>>>(AGG.p, GG.p, dGG->p, B.vG_ptr.p, B.vG_ptr.p, sG.p, sG.p, wl);
   UFE_CHECK_LAUNCH();
   Cs.alloc(std::max<int64_t>(nCG, 1), s);
   Crho.alloc(std::max<int64_t>(nCG, 1), s);
   Cs.zero();
-  rho.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
+  if (!wl) rho.alloc(std::max<int64_t>(B.n_Cloc, 1), s);   // a subset pass keeps the others' rho
   if (B.ncomp == 3)
-    k_constraints<T, 3><<<ns, 256, 0, s>>>(sm, m.node_of_dof.p, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p,
-                                           B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p);
+    k_constraints<T, 3><<<nw, 256, 0, s>>>(sm, m.node_of_dof.p, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p,
+                                           B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p, wl);
   else
-    k_constraints<T, 1><<<ns, 256, 0, s>>>(sm, m.node_of_dof.p, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p,
-                                           B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p);
+    k_constraints<T, 1><<<nw, 256, 0, s>>>(sm, m.node_of_dof.p, B.obj_of_dof.p, B.coarse_of_obj.p, B.obj_size.p,
+                                           B.obj_rot.p, B.obj_sum.p, sG.p, dCG->p, Cs.p, Crho.p, rho.p, wl);
   UFE_CHECK_LAUNCH();
 
   // a non-positive pivot in one of the local inversions (in FP32 also a pivot of a
   // Jacobi-scaled matrix below 1e-3: the operators of such a subdomain are too
-  // ill-conditioned to be stored and applied in FP32): name the matrix and subdomain
+  // ill-conditioned to be stored and applied in FP32).  With `bad` (the FP32 pass) the
+  // subdomain is marked for FP64 operators and the pass goes on (its later products
+  // are not used); otherwise the matrix and subdomain are named in the error.
   auto check = [&](const char* what) {
     std::vector<int> st = to_host(status.p, ns, s);
-    for (int w = 0; w < ns; ++w)
+    for (int w : ws)
       UFE_REQUIRE(!(st[w] & DEV_TIMEOUT), UFE_ERR_TIMEOUT,
                   std::string(what) + " of subdomain " + std::to_string(w) + ": a tensor-core copy or product did not "
                   "complete in time");
-    for (int w = 0; w < ns; ++w)
+    for (int w : ws) {
+      if (bad) {
+        if (st[w] != 0) (*bad)[w] = 1;
+        continue;
+      }
       UFE_REQUIRE(st[w] == 0, UFE_ERR_SINGULAR_LOCAL,
                   std::string(what) + " of subdomain " + std::to_string(w) +
                       ((st[w] & DEV_SINGULAR) ? " is not positive definite" : " is too ill-conditioned"));
+    }
   };
   const T floor = sizeof(T) == 4 ? T(1e-3) : T(0);
   std::vector<InvDesc> inv;
@@ -931,73 +949,78 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
     const int KS = 27 * B.ncomp;
     DBuf<T> ell_s;
     ell_s.alloc(std::max<int64_t>(B.n_vGloc, 1) * KS, s);
-    k_ell_scale<T><<<dim3(8, ns), 256, 0, s>>>(sm, KS, ell_k.p, ell_v.p, sI.p, sG.p, ell_s.p);
+    k_ell_scale<T><<<dim3(8, std::max(nw, 1)), 256, 0, s>>>(sm, KS, ell_k.p, ell_v.p, sI.p, sG.p, ell_s.p, wl);
     UFE_CHECK_LAUNCH();
-    k_xt<T><<<dim3((nGmax + 7) / 8, ns), 256, 0, s>>>(sm, KS, dII->p, dIG->p, ell_k.p, ell_s.p, II.p, X.p);
+    k_xt<T><<<dim3((nGmax + 7) / 8, std::max(nw, 1)), 256, 0, s>>>(sm, KS, dII->p, dIG->p, ell_k.p, ell_s.p, II.p, X.p,
+                                                                   wl);
     UFE_CHECK_LAUNCH();
-    k_schur<T><<<dim3(nGmax, ns), 256, nImax * sizeof(T), s>>>(sm, KS, dGG->p, dIG->p, ell_k.p, ell_s.p, X.p, GG.p);
+    k_schur<T><<<dim3(nGmax, std::max(nw, 1)), 256, nImax * sizeof(T), s>>>(sm, KS, dGG->p, dIG->p, ell_k.p, ell_s.p,
+                                                                          X.p, GG.p, wl);
     UFE_CHECK_LAUNCH();
   }
   X.release();
   // 4. S' = S + C^T rho C
   g.clear();
-  for (int w = 0; w < ns; ++w)
+  for (int w : ws)
     g.push_back({B.h_nG[w], B.h_nG[w], B.h_nC[w], pad4(B.h_nG[w]), pad4(B.h_nG[w]), pad4(B.h_nG[w]), oCG[w], oCG[w], oGG[w]});
   batched_gemm<T>(true, false, g, Cs.p, Crho.p, GG.p, T(1), T(1), s);
   Crho.release();
   // 5. S'^-1
   inv.clear();
-  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nG[w], pad4(B.h_nG[w]), oGG[w]});
+  for (int w : ws) inv.push_back({B.h_nG[w], pad4(B.h_nG[w]), oGG[w]});
   batched_inverse<T>(inv, GG.p, status.p, s, floor);
   check("S' = S + C^T rho C");
   // 6. Y = S'^-1 C^T
   Y.alloc(std::max<int64_t>(nGC, 1), s);
   g.clear();
-  for (int w = 0; w < ns; ++w)
+  for (int w : ws)
     g.push_back({B.h_nG[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nG[w]), pad4(B.h_nC[w]), oGG[w], oCG[w], oGC[w]});
   batched_gemm<T>(false, true, g, GG.p, Cs.p, Y.p, T(1), T(0), s);
   // 7. S_c = C Y, then S_c^-1
   Sc.alloc(std::max<int64_t>(nCC, 1), s);
   g.clear();
-  for (int w = 0; w < ns; ++w)
+  for (int w : ws)
     g.push_back({B.h_nC[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oCG[w], oGC[w], oCC[w]});
   batched_gemm<T>(false, false, g, Cs.p, Y.p, Sc.p, T(1), T(0), s);
   inv.clear();
-  for (int w = 0; w < ns; ++w) inv.push_back({B.h_nC[w], pad4(B.h_nC[w]), oCC[w]});
+  for (int w : ws) inv.push_back({B.h_nC[w], pad4(B.h_nC[w]), oCC[w]});
   batched_inverse<T>(inv, Sc.p, status.p, s);
   check("S_c = C S'^-1 C^T");
   // 8. Phi^ = Y S_c^-1
   GC.alloc(std::max<int64_t>(nGC, 1), s);
   GC.zero();
   g.clear();
-  for (int w = 0; w < ns; ++w)
+  for (int w : ws)
     g.push_back({B.h_nG[w], B.h_nC[w], B.h_nC[w], pad4(B.h_nC[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oGC[w], oCC[w], oGC[w]});
   batched_gemm<T>(false, false, g, Y.p, Sc.p, GC.p, T(1), T(0), s);
   // 9. K^ = S'^-1 - Phi^ Y^T
   g.clear();
-  for (int w = 0; w < ns; ++w)
+  for (int w : ws)
     g.push_back({B.h_nG[w], B.h_nG[w], B.h_nC[w], pad4(B.h_nC[w]), pad4(B.h_nC[w]), pad4(B.h_nG[w]), oGC[w], oGC[w], oGG[w]});
   batched_gemm<T>(false, true, g, GC.p, Y.p, GG.p, T(-1), T(1), s);
   // 10. A_c^w = S_c^-1 - rho (FP64)
-  Acw.alloc(std::max<int64_t>(nCC, 1), s);
-  k_coarse_local<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p);
+  if (!wl) Acw.alloc(std::max<int64_t>(nCC, 1), s);   // a subset pass overwrites only its subdomains
+  if (nw > 0) k_coarse_local<T><<<nw, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p, wl);
   UFE_CHECK_LAUNCH();
   if (sizeof(T) == 4) {
     // FP32 operators: the coarse basis must still satisfy C Phi = I to 1e-2, else this
     // problem keeps FP64 local operators (S_c = C S'^-1 C^T can be too ill-conditioned
     // for FP32, e.g. the rotation rows of small elasticity objects)
     g.clear();
-    for (int w = 0; w < ns; ++w)
+    for (int w : ws)
       g.push_back({B.h_nC[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oCG[w], oGC[w], oCC[w]});
     batched_gemm<T>(false, false, g, Cs.p, GC.p, Sc.p, T(1), T(0), s);
     DBuf<double> err;
     err.alloc(ns, s);
-    k_cphi_error<T><<<ns, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, 1e-2, err.p, status.p);
+    err.zero();
+    if (nw > 0) k_cphi_error<T><<<nw, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, 1e-2, err.p, status.p, wl);
     UFE_CHECK_LAUNCH();
     const std::vector<double> he = to_host(err.p, ns, s);
-    B.cphi_error = 0.0;
-    for (double v : he) B.cphi_error = std::max(B.cphi_error, v);
     check("the coarse basis (C Phi = I)");
+    // the largest error over the subdomains that keep FP32 operators
+    B.cphi_error = 0.0;
+    for (int w : ws)
+      if (!bad || !(*bad)[w]) B.cphi_error = std::max(B.cphi_error, he[w]);
   }
   // 11. the operators stay in the scaled variables: the iterations apply
   //     A_II^-1 = S_I Ahat_II^-1 S_I, K = S_G Khat S_G and Phi = S_G Phihat with the FP64
@@ -1308,11 +1331,13 @@ void bddc_build(Bddc& B) {
   // before the objects are found
   DBuf<int> status;
   status.alloc(ns, s);
+  std::vector<int> all_subs(ns);
+  for (int w = 0; w < ns; ++w) all_subs[w] = w;
   if (B.mixed) {
     B.local_tc = fp32_tensor_cores() ? 1 : 0;
-    factor_interior<float>(B, oII, nII, AII, sI, B.fII, status);
+    factor_interior<float>(B, oII, nII, AII, sI, B.fII, status, all_subs, nullptr);
   } else {
-    factor_interior<double>(B, oII, nII, AII, sI, B.dII, status);
+    factor_interior<double>(B, oII, nII, AII, sI, B.dII, status, all_subs, nullptr);
   }
   UFE_CUDA(cudaStreamWaitEvent(so, fork_ev, 0));
   build_objects(B, so);
@@ -1334,14 +1359,18 @@ void bddc_build(Bddc& B) {
   const int64_t nco = B.n_coarse;
   DBuf<double> Acw, rho;
   if (B.mixed) {
-    try {
-      factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
-                             ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho, status, true);
-    } catch (const Error& e) {
+    // FP32 local operators where they are accurate enough; a subdomain whose FP32 pivots
+    // or coarse basis fail the tests (tiny cut fractions) gets FP64 operators, factored
+    // in a second pass over those subdomains only, and the iterations apply each
+    // subdomain in its own precision
+    std::vector<char> bad(ns, 0);
+    factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
+                           ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho, status, true, all_subs, nullptr, &bad);
+    std::vector<int> sub64, sub32;
+    for (int w = 0; w < ns; ++w) (bad[w] ? sub64 : sub32).push_back(w);
+    if (sub32.empty()) {
+      // no subdomain keeps FP32: the problem is factored and applied in FP64 throughout
       B.local_tc = 0;
-      if (e.code != UFE_ERR_SINGULAR_LOCAL) throw;
-      // a scaled local matrix is too ill-conditioned for FP32 (tiny cut fractions):
-      // this problem keeps FP64 local operators (factored and applied in FP64)
       B.fII.release();
       B.fGG.release();
       B.fGC.release();
@@ -1351,11 +1380,21 @@ void bddc_build(Bddc& B) {
       B.bytes_GG *= 2.0;
       B.bytes_GC *= 2.0;
       factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
-                              ell_k, ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, false);
+                              ell_k, ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, false, all_subs, nullptr, nullptr);
+    } else if (!sub64.empty()) {
+      B.n_sub64 = (int)sub64.size();
+      B.wl64.alloc(sub64.size(), s);
+      B.wl32.alloc(sub32.size(), s);
+      UFE_CUDA(cudaMemcpyAsync(B.wl64.p, sub64.data(), sub64.size() * 4, cudaMemcpyHostToDevice, s));
+      UFE_CUDA(cudaMemcpyAsync(B.wl32.p, sub32.data(), sub32.size() * 4, cudaMemcpyHostToDevice, s));
+      factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
+                              ell_k, ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, false, sub64, B.wl64.p, nullptr);
+      // the host lists go out of scope: the copies above must have read them
+      UFE_CUDA(cudaStreamSynchronize(s));
     }
   } else
     factor_pipeline<double>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG, ell_k,
-                            ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, true);
+                            ell_v, B.dII, B.dGG, B.dGC, Acw, rho, status, true, all_subs, nullptr, nullptr);
   AII.release();
   AIG.release();
   AGG.release();

@@ -155,6 +155,10 @@ struct Bddc {
   double inv_flops_local = 0.0, inv_flops_coarse = 0.0;
   double bytes_II = 0.0, bytes_GG = 0.0, bytes_GC = 0.0, bytes_off = 0.0, bytes_Ac = 0.0;
   int fp64_refactor = 0;                // mixed precision requested, FP64 local operators kept (FP32 too ill-conditioned)
+  // mixed precision with some subdomains in FP64: their ids (wl64, n_sub64 of them; the
+  // FP64 operators dII, dGG, dGC hold those subdomains) and the FP32 ones (wl32)
+  int n_sub64 = 0;
+  DBuf<int32_t> wl32, wl64;
   double cphi_error = 0.0;              // mixed: max |C Phi - I| of the FP32 operators
   int local_tc = 0;                     // FP32 local inversions ran the tensor-core update
   int prec_cl = 4;                      // CTAs per subdomain cluster in the preconditioner kernels (tuned)

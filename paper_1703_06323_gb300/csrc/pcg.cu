@@ -501,7 +501,20 @@ __device__ void cta_gemv_rows(const TM* __restrict__ M, int r0, int r1, int ld, 
 struct SubLaunch {
   int ldImax, ldGmax;   // largest padded interior / interface sizes
   int n_stages;         // row-stream stages per CTA (1..kMaxStages)
+  // the subdomains of this launch: wl[cluster] (null: cluster c is subdomain c); with
+  // subdomains in two precisions each stage is two launches, and the final stage's
+  // dot products are partials part_off + CTA, summed (n_final of them) only by the
+  // last CTA of the launch with n_final > 0
+  const int32_t* wl;
+  int part_off, n_final;
 };
+
+// the subdomain of this CTA's cluster
+template <int CL>
+__device__ __forceinline__ int sub_of_cluster(const SubLaunch& L) {
+  const int c = (int)blockIdx.x / CL;
+  return L.wl ? L.wl[c] : c;
+}
 
 struct SubSizes {
   int nI, nG, nC, ldI, ldG, ldC, bi, bj, bk;
@@ -736,7 +749,7 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
+  const int w = sub_of_cluster<CL>(L), rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
@@ -782,7 +795,7 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   extern __shared__ __align__(16) char smem[];
   __shared__ double gpart[kSubThreads / 32][64];
   __shared__ double gsum[1024];
-  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
+  const int w = sub_of_cluster<CL>(L), rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0) return;
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
@@ -847,7 +860,7 @@ k_prec_prolong(SubMeta sm, const TM* __restrict__ Phi, const double* __restrict_
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
+  const int w = sub_of_cluster<CL>(L), rank = (int)cl.block_rank();
   const SubSizes z = sub_sizes(sm, w);
   if (z.nG == 0 || z.nC == 0) return;
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
@@ -874,7 +887,7 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   if (sc && sc->done) return;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) char smem[];
-  const int w = blockIdx.x / CL, rank = (int)cl.block_rank();
+  const int w = sub_of_cluster<CL>(L), rank = (int)cl.block_rank();
   const SubSizes zz = sub_sizes(sm, w);
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
@@ -935,12 +948,13 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   rz = block_sum(rz);
   rzo = block_sum(rzo);
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = rz;
-    part[2 * blockIdx.x + 1] = rzo;
+    part[2 * (L.part_off + blockIdx.x)] = rz;
+    part[2 * (L.part_off + blockIdx.x) + 1] = rzo;
   }
+  if (L.n_final == 0) return;
   if (arrive_last(&sc->counter[3])) {
-    const double a = sum_partials(part, gridDim.x, 2);
-    const double b = sum_partials(part + 1, gridDim.x, 2);
+    const double a = sum_partials(part, L.n_final, 2);
+    const double b = sum_partials(part + 1, L.n_final, 2);
     if (threadIdx.x == 0) {
       sc->rz_next = a;
       sc->rzold_next = b;
@@ -1038,50 +1052,116 @@ static SubLaunch sub_launch(const Bddc& B, size_t tm_size, size_t* smem) {
   return L;
 }
 
-template <typename TM, int NC, int CL>
+// the stored local operators of precision TM
+template <typename TM>
+struct LocalOps;
+template <>
+struct LocalOps<float> {
+  static const float* II(const Bddc& B) { return B.fII.p; }
+  static const float* GG(const Bddc& B) { return B.fGG.p; }
+  static const float* GC(const Bddc& B) { return B.fGC.p; }
+};
+template <>
+struct LocalOps<double> {
+  static const double* II(const Bddc& B) { return B.dII.p; }
+  static const double* GG(const Bddc& B) { return B.dGG.p; }
+  static const double* GC(const Bddc& B) { return B.dGC.p; }
+};
+
+// work vectors of one application z = M r (the preconditioner's own, or the
+// allocation-free apply's static ones)
+struct PrecBufs {
+  double *tG, *vw, *gC, *uc, *work;
+};
+
+// One application z = M r: every per-subdomain stage is launched once per precision
+// group -- all subdomains in one precision, or (mixed precision with some subdomains
+// kept in FP64) the FP32 subdomains and then the FP64 ones; the coarse solve runs once
+// between the Neumann and the prolongation stages.
+template <int NC, int CL>
 static void launch_preconditioner_cl(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots,
-                                     cudaStream_t s) {
-  const Mesh& m = *B.mesh;
+                                     cudaStream_t s, const PrecBufs& bf) {
   const SubMeta sm = B.meta();
-  const int ns = (int)m.n_sub;
-  size_t smem = 0;
-  const SubLaunch L = sub_launch(B, sizeof(TM), &smem);
-  const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
-  const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
-  const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
+  const int ns = (int)B.mesh->n_sub;
+  struct Group {
+    bool f64;
+    const int32_t* wl;
+    int n;
+  } gr[2];
+  int ng = 0;
+  if (!B.mixed)
+    gr[ng++] = {true, nullptr, ns};
+  else if (B.n_sub64 == 0)
+    gr[ng++] = {false, nullptr, ns};
+  else {
+    gr[ng++] = {false, B.wl32.p, ns - B.n_sub64};
+    gr[ng++] = {true, B.wl64.p, B.n_sub64};
+  }
+  size_t smem32 = 0, smem64 = 0;
+  const SubLaunch L32 = sub_launch(B, 4, &smem32), L64 = sub_launch(B, 8, &smem64);
+  // fn(TM tag, launch parameters, dynamic shared memory, subdomains) for each group
+  auto each = [&](auto fn) {
+    int off = 0;
+    for (int k = 0; k < ng; ++k) {
+      SubLaunch L = gr[k].f64 ? L64 : L32;
+      L.wl = gr[k].wl;
+      L.part_off = off;
+      L.n_final = k == ng - 1 ? off + gr[k].n * CL : 0;
+      if (gr[k].f64)
+        fn(double(0), L, smem64, gr[k].n);
+      else
+        fn(float(0), L, smem32, gr[k].n);
+      off += gr[k].n * CL;
+    }
+  };
   TimedLaunch t3, t4, t5, t6, t7;   // per-stage event timing (outside graph capture, when enabled)
   t3.begin("prec_interior", s);
-  k_prec_interior1<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, B.tG.p, sc, L);
-  UFE_CHECK_LAUNCH();
+  each([&](auto tag, const SubLaunch& L, size_t smem, int n) {
+    using TM = decltype(tag);
+    k_prec_interior1<TM, NC, CL><<<n * CL, kSubThreads, smem, s>>>(sm, LocalOps<TM>::II(B), r, bf.tG, sc, L);
+    UFE_CHECK_LAUNCH();
+  });
   t3.end(s);
   t4.begin("prec_neumann", s);
-  k_prec_neumann<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GG, GC, r, B.tG.p, B.vw.p, B.gC.p, sc, L);
-  UFE_CHECK_LAUNCH();
+  each([&](auto tag, const SubLaunch& L, size_t smem, int n) {
+    using TM = decltype(tag);
+    k_prec_neumann<TM, NC, CL><<<n * CL, kSubThreads, smem, s>>>(sm, LocalOps<TM>::GG(B), LocalOps<TM>::GC(B), r,
+                                                                 bf.tG, bf.vw, bf.gC, sc, L);
+    UFE_CHECK_LAUNCH();
+  });
   t4.end(s);
   if (B.n_coarse > 0) {
     t5.begin("coarse_solve", s);
-    coarse_solve(B, B.gC.p, B.uc.p, B.cr.work.p, sc, s);
+    coarse_solve(B, bf.gC, bf.uc, bf.work, sc, s);
     t5.end(s);
     t6.begin("prec_prolong", s);
-    k_prec_prolong<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GC, B.uc.p, B.vw.p, sc, L);
-    UFE_CHECK_LAUNCH();
+    each([&](auto tag, const SubLaunch& L, size_t smem, int n) {
+      using TM = decltype(tag);
+      k_prec_prolong<TM, NC, CL><<<n * CL, kSubThreads, smem, s>>>(sm, LocalOps<TM>::GC(B), bf.uc, bf.vw, sc, L);
+      UFE_CHECK_LAUNCH();
+    });
     t6.end(s);
   }
   t7.begin("prec_final", s);
-  k_prec_final<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, B.vw.p, z, B.part.p, sc, L, with_dots);
-  UFE_CHECK_LAUNCH();
+  each([&](auto tag, const SubLaunch& L, size_t smem, int n) {
+    using TM = decltype(tag);
+    k_prec_final<TM, NC, CL><<<n * CL, kSubThreads, smem, s>>>(sm, LocalOps<TM>::II(B), r, bf.vw, z, B.part.p, sc,
+                                                               L, with_dots);
+    UFE_CHECK_LAUNCH();
+  });
   t7.end(s);
 }
 
 // the cluster size the launch-shape tuner chose (Poisson; elasticity keeps four CTAs)
-template <typename TM, int NC>
-static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
+template <int NC>
+static void launch_preconditioner(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s,
+                                  const PrecBufs& bf) {
   if (NC == 1 && B.prec_cl == 2)
-    launch_preconditioner_cl<TM, NC, 2>(B, r, z, sc, with_dots, s);
+    launch_preconditioner_cl<NC, 2>(B, r, z, sc, with_dots, s, bf);
   else if (NC == 1 && B.prec_cl == 8)
-    launch_preconditioner_cl<TM, NC, 8>(B, r, z, sc, with_dots, s);
+    launch_preconditioner_cl<NC, 8>(B, r, z, sc, with_dots, s, bf);
   else
-    launch_preconditioner_cl<TM, NC, kCL>(B, r, z, sc, with_dots, s);
+    launch_preconditioner_cl<NC, kCL>(B, r, z, sc, with_dots, s, bf);
 }
 
 // raise a kernel's dynamic shared-memory limit to what the device allows next to its
@@ -1150,17 +1230,11 @@ static void check_device_status(Bddc& B) {
 }
 
 static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, int with_dots, cudaStream_t s) {
-  if (B.ncomp == 3) {
-    if (B.mixed)
-      launch_preconditioner<float, 3>(B, r, z, sc, with_dots, s);
-    else
-      launch_preconditioner<double, 3>(B, r, z, sc, with_dots, s);
-  } else {
-    if (B.mixed)
-      launch_preconditioner<float, 1>(B, r, z, sc, with_dots, s);
-    else
-      launch_preconditioner<double, 1>(B, r, z, sc, with_dots, s);
-  }
+  const PrecBufs bf{B.tG.p, B.vw.p, B.gC.p, B.uc.p, B.cr.work.p};
+  if (B.ncomp == 3)
+    launch_preconditioner<3>(B, r, z, sc, with_dots, s, bf);
+  else
+    launch_preconditioner<1>(B, r, z, sc, with_dots, s, bf);
 }
 
 // ---------------------------------------------------------------------------
@@ -1505,42 +1579,6 @@ static double* noalloc_scratch_ptr() {
   return ptr[dev];
 }
 
-template <typename TM, int NC, int CL>
-static void launch_preconditioner_static_cl(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
-                                            double* uc, cudaStream_t s) {
-  const Mesh& m = *B.mesh;
-  const SubMeta sm = B.meta();
-  const int ns = (int)m.n_sub;
-  size_t smem = 0;
-  const SubLaunch L = sub_launch(B, sizeof(TM), &smem);
-  const TM* II = B.mixed ? (const TM*)B.fII.p : (const TM*)B.dII.p;
-  const TM* GG = B.mixed ? (const TM*)B.fGG.p : (const TM*)B.dGG.p;
-  const TM* GC = B.mixed ? (const TM*)B.fGC.p : (const TM*)B.dGC.p;
-  k_prec_interior1<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, tG, nullptr, L);
-  UFE_CHECK_LAUNCH();
-  k_prec_neumann<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GG, GC, r, tG, vw, gC, nullptr, L);
-  UFE_CHECK_LAUNCH();
-  if (B.n_coarse > 0) {
-    coarse_solve(B, gC, uc, uc + kNoAllocU, nullptr, s);
-    k_prec_prolong<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, GC, uc, vw, nullptr, L);
-    UFE_CHECK_LAUNCH();
-  }
-  k_prec_final<TM, NC, CL><<<ns * CL, kSubThreads, smem, s>>>(sm, II, r, vw, z, nullptr, nullptr, L, 0);
-  UFE_CHECK_LAUNCH();
-}
-
-// the launch shape the tuner chose, as in the allocating apply (same kernels, same order)
-template <typename TM, int NC>
-static void launch_preconditioner_static(Bddc& B, const double* r, double* z, double* tG, double* vw, double* gC,
-                                         double* uc, cudaStream_t s) {
-  if (NC == 1 && B.prec_cl == 2)
-    launch_preconditioner_static_cl<TM, NC, 2>(B, r, z, tG, vw, gC, uc, s);
-  else if (NC == 1 && B.prec_cl == 8)
-    launch_preconditioner_static_cl<TM, NC, 8>(B, r, z, tG, vw, gC, uc, s);
-  else
-    launch_preconditioner_static_cl<TM, NC, kCL>(B, r, z, tG, vw, gC, uc, s);
-}
-
 void bddc_noalloc_prepare(Bddc& B) {
   set_smem_limits(B);
   noalloc_scratch_ptr();
@@ -1579,17 +1617,13 @@ void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev) {
   // every entry of z is written by the kernels; clearing it first keeps the
   // behaviour identical to ufe_bddc_apply
   UFE_CUDA(cudaMemsetAsync(z_dev, 0, (size_t)B.ncomp * m.n_dof * sizeof(double), B.stream));
-  if (B.ncomp == 3) {
-    if (B.mixed)
-      launch_preconditioner_static<float, 3>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
-    else
-      launch_preconditioner_static<double, 3>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
-  } else {
-    if (B.mixed)
-      launch_preconditioner_static<float, 1>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
-    else
-      launch_preconditioner_static<double, 1>(B, r_dev, z_dev, tG, vw, gC, uc, B.stream);
-  }
+  // the same kernels in the same launch shape as ufe_bddc_apply, on the static vectors
+  // (the cyclic-reduction coarse solver's work vector follows uc)
+  const PrecBufs bf{tG, vw, gC, uc, uc + kNoAllocU};
+  if (B.ncomp == 3)
+    launch_preconditioner<3>(B, r_dev, z_dev, nullptr, 0, B.stream, bf);
+  else
+    launch_preconditioner<1>(B, r_dev, z_dev, nullptr, 0, B.stream, bf);
   check_device_status(B);
 }
 

@@ -59,7 +59,7 @@ class BddcInfo(ctypes.Structure):
                 ("fp64_refactor", ctypes.c_int32), ("coarse_solver", ctypes.c_int32), ("cphi_error", ctypes.c_double),
                 ("coarse_layers", ctypes.c_int32), ("coarse_levels", ctypes.c_int32),
                 ("local_tensor_cores", ctypes.c_int32), ("prec_cluster", ctypes.c_int32),
-                ("prec_stages", ctypes.c_int32)]
+                ("prec_stages", ctypes.c_int32), ("fp64_subdomains", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):

@@ -98,9 +98,9 @@ def test_elastic_preconditioner_mixed(ufe, name):
     """Mixed precision M r: FP32 local operators; the FP32 rounding of S'^-1 is
     amplified by cond(S_c) (1e5 .. 1e9 here), so M r is an approximation of a few
     1e-3 in the energy norm (1e-2 bound); flexible PCG absorbs it and the mixed
-    solutions still meet 1e-6 (test_elastic_pcg_solution).  Problems whose FP32
-    coarse basis misses C Phi = I by more than 1e-2 keep FP64 operators (el_sphere8,
-    el_wall: checked below)."""
+    solutions still meet 1e-6 (test_elastic_pcg_solution).  Subdomains whose FP32
+    coarse basis misses C Phi = I by more than 1e-2 keep FP64 operators while the
+    others stay FP32 (el_sphere8 and el_wall have such subdomains: checked below)."""
     orc = oracle_run(name)
     B = orc.bddc()
     r = np.random.default_rng(3).normal(size=orc.sys.n)
@@ -108,9 +108,10 @@ def test_elastic_preconditioner_mixed(ufe, name):
     with _solver(orc.p, precision="mixed") as S:
         z = S.precondition(r)
         bi = S.bddc_info
-    assert bi["cphi_error"] <= 1e-2 or bi["fp64_refactor"] == 1
+    # the FP32 subdomains meet C Phi = I to 1e-2; the others are kept in FP64
+    assert bi["cphi_error"] <= 1e-2
     if name in ("el_sphere8", "el_wall"):
-        assert bi["fp64_refactor"] == 1
+        assert bi["fp64_subdomains"] >= 1
     assert energy_error(orc.sys.A, z, ref) <= 1e-2
 
 
