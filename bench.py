@@ -644,6 +644,8 @@ def run_ours(args, rank, world):
         "setup_s_device": setup_s,
         "solve_s_device": solve_s,
         "n_coarse": binfo["n_coarse"],
+        "launch_shape": {"cluster_ctas": binfo["prec_cluster"], "row_stages": binfo["prec_stages"],
+                         "chosen_by": "UFE_PREC_SHAPE" if os.environ.get("UFE_PREC_SHAPE") else "tuner"},
         "fp64": {"value": mean_fp64 / world, "unit": "s", "iterations": info64["iterations"],
                  "dof_iters_per_s": n64 * info64["iterations"] / mean_fp64 if mean_fp64 == mean_fp64 else None,
                  "true_rel_residual": info64["true_rel_residual"]},

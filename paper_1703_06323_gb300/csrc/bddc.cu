@@ -850,6 +850,20 @@ __global__ void k_init_labels(int64_t n, const uint8_t* __restrict__ nn, int32_t
   active[d] = g ? 1 : 0;
 }
 
+// Steps 8, 9 and the C Phi = I test of an FP32 pass, run on a second stream beside the
+// coarse set-up (which needs only A_c^w, step 10): `pending` once they are queued,
+// `done` recorded after them, `err` the per-subdomain |C Phi - I| (finish_deferred).
+struct DeferredCheck {
+  bool pending = false;
+  cudaEvent_t done = nullptr;
+  DBuf<double> err;
+  ~DeferredCheck() {
+    if (done) cudaEventDestroy(done);
+  }
+};
+
+static cudaStream_t objects_stream();
+
 // scaled A_II in precision T and its inverse (step 1 of the local factorisations; it
 // needs only the mesh, so it runs while the objects are found); the pivot flags land
 // in status and are checked with the later steps.  ws lists the subdomains to factor
@@ -882,7 +896,7 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
                             DBuf<double>& ell_v, DBuf<T>& II, DBuf<T>& GG,
                             DBuf<T>& GC, DBuf<double>& Acw, DBuf<double>& rho, DBuf<int>& status,
                             bool interior_ready, const std::vector<int>& ws, const int32_t* wl,
-                            std::vector<char>* bad) {
+                            std::vector<char>* bad, DeferredCheck* later = nullptr) {
   if (!interior_ready) factor_interior<T>(B, oII, nII, AII, sI, II, status, ws, wl);
   Mesh& m = *B.mesh;
   cudaStream_t s = B.stream;
@@ -986,41 +1000,66 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
   for (int w : ws) inv.push_back({B.h_nC[w], pad4(B.h_nC[w]), oCC[w]});
   batched_inverse<T>(inv, Sc.p, status.p, s);
   check("S_c = C S'^-1 C^T");
-  // 8. Phi^ = Y S_c^-1
+  // 10. A_c^w = S_c^-1 - rho (FP64), first: the coarse set-up needs nothing else
+  if (!wl) Acw.alloc(std::max<int64_t>(nCC, 1), s);   // a subset pass overwrites only its subdomains
+  if (nw > 0) k_coarse_local<T><<<nw, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p, wl);
+  UFE_CHECK_LAUNCH();
   GC.alloc(std::max<int64_t>(nGC, 1), s);
   GC.zero();
+  DBuf<double> err;
+  if (sizeof(T) == 4) {
+    err.alloc(ns, s);
+    err.zero();
+  }
+  // an FP32 pass with no failed pivot so far runs the rest on a second stream beside
+  // the coarse set-up, and its C Phi = I test is read after both (finish_deferred)
+  bool defer = later && bad && sizeof(T) == 4;
+  if (defer)
+    for (int w : ws) defer = defer && !(*bad)[w];
+  cudaStream_t sx = s;
+  if (defer) {
+    UFE_CUDA(cudaEventCreateWithFlags(&later->done, cudaEventDisableTiming));
+    UFE_CUDA(cudaEventRecord(later->done, s));
+    sx = objects_stream();
+    UFE_CUDA(cudaStreamWaitEvent(sx, later->done, 0));
+  }
+  // 8. Phi^ = Y S_c^-1
   g.clear();
   for (int w : ws)
     g.push_back({B.h_nG[w], B.h_nC[w], B.h_nC[w], pad4(B.h_nC[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oGC[w], oCC[w], oGC[w]});
-  batched_gemm<T>(false, false, g, Y.p, Sc.p, GC.p, T(1), T(0), s);
+  batched_gemm<T>(false, false, g, Y.p, Sc.p, GC.p, T(1), T(0), sx);
   // 9. K^ = S'^-1 - Phi^ Y^T
   g.clear();
   for (int w : ws)
     g.push_back({B.h_nG[w], B.h_nG[w], B.h_nC[w], pad4(B.h_nC[w]), pad4(B.h_nC[w]), pad4(B.h_nG[w]), oGC[w], oGC[w], oGG[w]});
-  batched_gemm<T>(false, true, g, GC.p, Y.p, GG.p, T(-1), T(1), s);
-  // 10. A_c^w = S_c^-1 - rho (FP64)
-  if (!wl) Acw.alloc(std::max<int64_t>(nCC, 1), s);   // a subset pass overwrites only its subdomains
-  if (nw > 0) k_coarse_local<T><<<nw, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, rho.p, Acw.p, wl);
-  UFE_CHECK_LAUNCH();
+  batched_gemm<T>(false, true, g, GC.p, Y.p, GG.p, T(-1), T(1), sx);
   if (sizeof(T) == 4) {
-    // FP32 operators: the coarse basis must still satisfy C Phi = I to 1e-2, else this
-    // problem keeps FP64 local operators (S_c = C S'^-1 C^T can be too ill-conditioned
+    // FP32 operators: the coarse basis must still satisfy C Phi = I to 1e-2, else the
+    // subdomain gets FP64 local operators (S_c = C S'^-1 C^T can be too ill-conditioned
     // for FP32, e.g. the rotation rows of small elasticity objects)
     g.clear();
     for (int w : ws)
       g.push_back({B.h_nC[w], B.h_nC[w], B.h_nG[w], pad4(B.h_nG[w]), pad4(B.h_nC[w]), pad4(B.h_nC[w]), oCG[w], oGC[w], oCC[w]});
-    batched_gemm<T>(false, false, g, Cs.p, GC.p, Sc.p, T(1), T(0), s);
-    DBuf<double> err;
-    err.alloc(ns, s);
-    err.zero();
-    if (nw > 0) k_cphi_error<T><<<nw, 256, 0, s>>>(B.C_ptr.p, dCC->p, Sc.p, 1e-2, err.p, status.p, wl);
+    batched_gemm<T>(false, false, g, Cs.p, GC.p, Sc.p, T(1), T(0), sx);
+    if (nw > 0) k_cphi_error<T><<<nw, 256, 0, sx>>>(B.C_ptr.p, dCC->p, Sc.p, 1e-2, err.p, status.p, wl);
     UFE_CHECK_LAUNCH();
-    const std::vector<double> he = to_host(err.p, ns, s);
-    check("the coarse basis (C Phi = I)");
-    // the largest error over the subdomains that keep FP32 operators
-    B.cphi_error = 0.0;
-    for (int w : ws)
-      if (!bad || !(*bad)[w]) B.cphi_error = std::max(B.cphi_error, he[w]);
+    if (defer) {
+      UFE_CUDA(cudaEventRecord(later->done, sx));
+      later->pending = true;
+      std::swap(later->err.p, err.p);
+      std::swap(later->err.n, err.n);
+      std::swap(later->err.s, err.s);
+      // the buffers the second stream reads are released on it, after its work
+      Y.s = Sc.s = Cs.s = sx;
+      dCC->s = sx;
+    } else {
+      const std::vector<double> he = to_host(err.p, ns, s);
+      check("the coarse basis (C Phi = I)");
+      // the largest error over the subdomains that keep FP32 operators
+      B.cphi_error = 0.0;
+      for (int w : ws)
+        if (!bad || !(*bad)[w]) B.cphi_error = std::max(B.cphi_error, he[w]);
+    }
   }
   // 11. the operators stay in the scaled variables: the iterations apply
   //     A_II^-1 = S_I Ahat_II^-1 S_I, K = S_G Khat S_G and Phi = S_G Phihat with the FP64
@@ -1358,16 +1397,64 @@ void bddc_build(Bddc& B) {
   B.bytes_GC = (B.mixed ? 4.0 : 8.0) * nGC;
   const int64_t nco = B.n_coarse;
   DBuf<double> Acw, rho;
+  TimedLaunch ph_co;
+  // ---- coarse matrix (FP64), assembled densely, then inverted (small problems) or
+  // factored by block cyclic reduction over the z layers of subdomain blocks (coarse.cu)
+  auto do_coarse = [&]() {
+    ph_co.begin("phase_coarse", s);
+    if (nco) {
+      const int ldc = pad4((int)nco);
+      DBuf<double> Ac;
+      Ac.alloc((size_t)nco * ldc, s);
+      Ac.zero();
+      DBuf<int64_t> dCC;
+      upload(dCC, oCC);
+      k_coarse_assemble<<<(unsigned)nco, 128, 0, s>>>(nco, ldc, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p,
+                                                      B.C_ptr.p, B.C_list.p, dCC.p, Acw.p, Ac.p);
+      UFE_CHECK_LAUNCH();
+      k_symmetrize<<<grid_for(nco * nco, T), T, 0, s>>>(Ac.p, (int)nco, ldc);
+      UFE_CHECK_LAUNCH();
+      B.Ac_inv.release();   // a second set-up (after the FP64 pass of some subdomains) replaces the first
+      coarse_setup(B, Ac, ldc, s);
+    } else {
+      DBuf<double> none;
+      coarse_setup(B, none, 4, s);
+    }
+    B.bytes_Ac = B.cr.bytes;
+    B.inv_flops_coarse = B.cr.inv_flops;
+    ph_co.end(s);
+  };
+  bool coarse_done = false;
   if (B.mixed) {
     // FP32 local operators where they are accurate enough; a subdomain whose FP32 pivots
     // or coarse basis fail the tests (tiny cut fractions) gets FP64 operators, factored
     // in a second pass over those subdomains only, and the iterations apply each
     // subdomain in its own precision
     std::vector<char> bad(ns, 0);
+    DeferredCheck later;
     factor_pipeline<float>(B, oII, oIG, oGG, oCG, oGC, oCC, nII, nIG, nGG, nCG, nGC, nCC, AII, AIG, AGG, sI, sG,
-                           ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho, status, true, all_subs, nullptr, &bad);
+                           ell_k, ell_v, B.fII, B.fGG, B.fGC, Acw, rho, status, true, all_subs, nullptr, &bad, &later);
+    if (later.pending) {
+      // every pivot passed: the coarse set-up runs while the last FP32 products and the
+      // C Phi = I test finish on the second stream, then the test is read
+      ph_fac.end(s);
+      do_coarse();
+      coarse_done = true;
+      UFE_CUDA(cudaStreamWaitEvent(s, later.done, 0));
+      const std::vector<double> he = to_host(later.err.p, ns, s);
+      const std::vector<int> st = to_host(status.p, ns, s);
+      for (int w = 0; w < ns; ++w)
+        UFE_REQUIRE(!(st[w] & DEV_TIMEOUT), UFE_ERR_TIMEOUT,
+                    "the coarse basis of subdomain " + std::to_string(w) + ": a device wait did not complete in time");
+      B.cphi_error = 0.0;
+      for (int w = 0; w < ns; ++w) {
+        if (st[w]) bad[w] = 1;
+        if (!bad[w]) B.cphi_error = std::max(B.cphi_error, he[w]);
+      }
+    }
     std::vector<int> sub64, sub32;
     for (int w = 0; w < ns; ++w) (bad[w] ? sub64 : sub32).push_back(w);
+    if (!sub64.empty()) coarse_done = false;   // A_c^w of those subdomains changes
     if (sub32.empty()) {
       // no subdomain keeps FP32: the problem is factored and applied in FP64 throughout
       B.local_tc = 0;
@@ -1399,32 +1486,11 @@ void bddc_build(Bddc& B) {
   AIG.release();
   AGG.release();
 
-  ph_fac.end(s);
-  TimedLaunch ph_co;
-  ph_co.begin("phase_coarse", s);
-  // ---- coarse matrix (FP64), assembled densely, then inverted (small problems) or
-  // factored by block cyclic reduction over the z layers of subdomain blocks (coarse.cu)
-  if (nco) {
-    const int ldc = pad4((int)nco);
-    DBuf<double> Ac;
-    Ac.alloc((size_t)nco * ldc, s);
-    Ac.zero();
-    DBuf<int64_t> dCC;
-    upload(dCC, oCC);
-    k_coarse_assemble<<<(unsigned)nco, 128, 0, s>>>(nco, ldc, B.coarse_rep.p, B.coarse_nn.p, m.neigh.p, B.cpos.p,
-                                                    B.C_ptr.p, B.C_list.p, dCC.p, Acw.p, Ac.p);
-    UFE_CHECK_LAUNCH();
-    k_symmetrize<<<grid_for(nco * nco, T), T, 0, s>>>(Ac.p, (int)nco, ldc);
-    UFE_CHECK_LAUNCH();
-    coarse_setup(B, Ac, ldc, s);
-  } else {
-    DBuf<double> none;
-    coarse_setup(B, none, 4, s);
+  if (!coarse_done) {
+    ph_fac.end(s);
+    do_coarse();
   }
-  B.bytes_Ac = B.cr.bytes;
-  B.inv_flops_coarse = B.cr.inv_flops;
 
-  ph_co.end(s);
   // ---- solver work space
   B.tG.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
   B.vw.alloc(std::max<int64_t>(B.n_vGloc, 1), s);

@@ -1242,9 +1242,10 @@ static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, in
 // subdomain cluster (2, 4, 8) and row-stream stages per CTA (1, 2, 4).  The first
 // set-up of a size class (device, precision, interior and interface sizes in steps of
 // 32, subdomain count in powers of two) times each candidate with CUDA events (one
-// warm-up and three applications of z = M r on the preconditioner's own work vectors,
-// in three interleaved rounds, keeping each candidate's fastest) and caches the
-// fastest for the process; later set-ups of the class reuse it.
+// warm-up, then three operator applies each followed by z = M r, as in an iteration,
+// on the preconditioner's own work vectors, in five interleaved rounds, keeping each
+// candidate's fastest) and caches the fastest for the process; later set-ups of the
+// class reuse it.
 // UFE_AUTOTUNE=0 keeps the default shape (4 CTAs, stages from the shared-memory budget).
 // ---------------------------------------------------------------------------
 static bool autotune_enabled() {
@@ -1290,7 +1291,7 @@ void tune_preconditioner(Bddc& B) {
   UFE_CUDA(cudaEventCreate(&e1));
   // every shape is timed in each of kRounds interleaved rounds (so that a slow moment of
   // the device does not single one out) and scored by its fastest round
-  constexpr int kRounds = 3;
+  constexpr int kRounds = 5;
   const int shapes[9][2] = {{2, 1}, {2, 2}, {2, 4}, {4, 1}, {4, 2}, {4, 4}, {8, 1}, {8, 2}, {8, 4}};
   float score[9];
   for (float& v : score) v = 1e30f;
@@ -1304,7 +1305,11 @@ void tune_preconditioner(Bddc& B) {
         B.prec_stages = shapes[k][1];
         precondition(B, B.r.p, B.z.p, nullptr, 0, s);
         UFE_CUDA(cudaEventRecord(e0, s));
-        for (int rep = 0; rep < 3; ++rep) precondition(B, B.r.p, B.z.p, nullptr, 0, s);
+        // as in an iteration: the operator apply, then the preconditioner
+        for (int rep = 0; rep < 3; ++rep) {
+          system_apply(*B.sys, B.z.p, B.q.p, s);
+          precondition(B, B.r.p, B.z.p, nullptr, 0, s);
+        }
         UFE_CUDA(cudaEventRecord(e1, s));
         UFE_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
