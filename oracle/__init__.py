@@ -32,7 +32,11 @@ Modules and what they follow:
                        variant of the same unfitted discretisation: 24x24 element
                        matrices, loads, assembly (no counterpart in the paper; the
                        BDDC of ``bddc`` takes 3 DOFs per node and rigid-mode
-                       coarse rows for it).
+                       coarse rows for it);
+  * ``multilevel``  -- three-level BDDC: the coarse problem of ``bddc`` itself
+                       preconditioned by BDDC over groups of subdomains (Sect. 6
+                       names multilevel BDDC as the way past one coarse
+                       factorisation; the construction is reading R26).
 
 Parity status per function is stated in each module header.
 """

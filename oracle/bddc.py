@@ -204,8 +204,9 @@ class BDDC:
             v[L["dofs"]] += L["w"] * u
         return v
 
-    def bddc_solve(self, r_loc):
-        """A~^-1 on the BDDC space: local constrained Neumann + coarse correction."""
+    def bddc_solve(self, r_loc, coarse_solve=None):
+        """A~^-1 on the BDDC space: local constrained Neumann + coarse correction.
+        coarse_solve (optional) replaces the exact A_c^-1 (a multilevel method)."""
         out = []
         rc = np.zeros(self.n_coarse)
         for L, r in zip(self.local, r_loc):
@@ -215,7 +216,10 @@ class BDDC:
             out.append(sla.lu_solve(L["kkt_lu"], rhs)[:n])
             if nc:
                 rc[L["cids"]] += L["Phi"].T @ r
-        uc = sla.cho_solve(self.ac_chol, rc) if self.n_coarse else rc
+        if coarse_solve is not None:
+            uc = coarse_solve(rc)
+        else:
+            uc = sla.cho_solve(self.ac_chol, rc) if self.n_coarse else rc
         for k, L in enumerate(self.local):
             if L["cids"].size:
                 out[k] = out[k] + L["Phi"] @ uc[L["cids"]]
@@ -225,11 +229,11 @@ class BDDC:
         """E v = v - I0 A0^-1 I0^T A v."""
         return v - self.interior_solve(self.system.apply(v))
 
-    def apply(self, r):
+    def apply(self, r, coarse_solve=None):
         """z = M r with M = I0 A0^-1 I0^T + E W A~^-1 W^T E^T (Eq. bddc)."""
         z0 = self.interior_solve(r)
         s = r - self.system.apply(z0)                 # E^T r
-        u_loc = self.bddc_solve(self.weight_T(s))
+        u_loc = self.bddc_solve(self.weight_T(s), coarse_solve)
         return z0 + self.harmonic_extension(self.weight(u_loc))
 
     # -- diagnostics ------------------------------------------------------------
