@@ -158,7 +158,7 @@ typedef struct {
  *
  *  box_lo, box_hi   3 doubles each (host); cells must be cubes (equal spacing).
  *  cells            3 ints (host): nx, ny, nz >= 1.
- *  sub_cells        3 ints (host): cells per subdomain block edge, 1..8, dividing cells.
+ *  sub_cells        3 ints (host): cells per subdomain block edge, 1..16, dividing cells.
  *  phi_nodes        (nx+1)(ny+1)(nz+1) doubles, nodal level set; memory per `mem`.
  *  dirichlet_face_mask  bit f set = strong Dirichlet on box face f (x-,x+,y-,y+,z-,z+).
  *  pin_node         UFE_PIN_NONE, UFE_PIN_AUTO (pin the node whose 8 cells are

@@ -238,8 +238,8 @@ ufe_status ufe_mesh_create(const double box_lo[3], const double box_hi[3], const
     g.nx = cells[0]; g.ny = cells[1]; g.nz = cells[2];
     g.sx = sub_cells[0]; g.sy = sub_cells[1]; g.sz = sub_cells[2];
     UFE_REQUIRE(g.nx > 0 && g.ny > 0 && g.nz > 0, UFE_ERR_INVALID_ARG, "cells must be positive");
-    UFE_REQUIRE(g.sx >= 1 && g.sy >= 1 && g.sz >= 1 && g.sx <= 8 && g.sy <= 8 && g.sz <= 8, UFE_ERR_INVALID_ARG,
-                "sub_cells must lie in 1..8");
+    UFE_REQUIRE(g.sx >= 1 && g.sy >= 1 && g.sz >= 1 && g.sx <= 16 && g.sy <= 16 && g.sz <= 16, UFE_ERR_INVALID_ARG,
+                "sub_cells must lie in 1..16");
     UFE_REQUIRE(g.nx % g.sx == 0 && g.ny % g.sy == 0 && g.nz % g.sz == 0, UFE_ERR_INVALID_ARG,
                 "sub_cells must divide cells");
     UFE_REQUIRE((int64_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) < (int64_t)1 << 31, UFE_ERR_INVALID_ARG, "grid too large");

@@ -968,6 +968,8 @@ static void factor_pipeline(Bddc& B, const std::vector<int64_t>& oII, const std:
     k_xt<T><<<dim3((nGmax + 7) / 8, std::max(nw, 1)), 256, 0, s>>>(sm, KS, dII->p, dIG->p, ell_k.p, ell_s.p, II.p, X.p,
                                                                    wl);
     UFE_CHECK_LAUNCH();
+    if (nImax * sizeof(T) > 48 * 1024)   // interiors of large blocks
+      UFE_CUDA(cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nImax * sizeof(T))));
     k_schur<T><<<dim3(nGmax, std::max(nw, 1)), 256, nImax * sizeof(T), s>>>(sm, KS, dGG->p, dIG->p, ell_k.p, ell_s.p,
                                                                           X.p, GG.p, wl);
     UFE_CHECK_LAUNCH();
@@ -1275,6 +1277,9 @@ void bddc_build(Bddc& B) {
   B.n_vGloc = NC * m.n_Gloc;
   B.max_nIv = NC * m.max_nI;
   B.max_nGv = NC * m.max_nG;
+  // the per-iteration kernels hold a subdomain's vectors in one CTA's shared memory:
+  // refuse local sizes beyond that before any local operator is allocated
+  check_local_sizes(B);
 
   B.h_nI.resize(ns);
   B.h_nG.resize(ns);

@@ -181,6 +181,8 @@ void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
 void bddc_noalloc_prepare(Bddc& B);
 // launch shape of the per-iteration preconditioner kernels, timed per size class (pcg.cu)
 void tune_preconditioner(Bddc& B);
+// UFE_ERR_UNSUPPORTED if a subdomain's vectors and one operator row do not fit one CTA's shared memory
+void check_local_sizes(const Bddc& B);
 // loads the coarse solver's kernels (cudaFuncGetAttributes), once per device
 void coarse_prepare();
 void pcg_solve(Bddc& B, const double* b_dev, double* x_dev, const ufe_solve_opts& o, ufe_solve_info* info);

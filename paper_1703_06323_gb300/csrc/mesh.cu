@@ -247,43 +247,43 @@ __global__ void k_apply_tile_list(int64_t n, const int32_t* __restrict__ index, 
 
 // ---------------------------------------------------------------------------
 // Sect. 2.1: subdomains = connected components (cells sharing a DOF) of the
-// active cells of each block.  One CTA per block, one thread per cell; labels
-// converge to the smallest cell index of the component (min propagation with
-// pointer jumping; bounded).
+// active cells of each block.  One CTA per block (up to 16^3 cells), each thread
+// walking the block's cells with a stride; labels converge to the smallest cell
+// index of the component (min propagation with pointer jumping; bounded).
 // ---------------------------------------------------------------------------
-constexpr int kMaxBlockCells = 512;
+constexpr int kMaxBlockCells = 16 * 16 * 16;
+constexpr int kBlockThreads = 1024;
+constexpr unsigned kCellActive = 0x100;   // vm bit: the cell is active (low 8 bits: vertices holding a DOF)
 
-__global__ void __launch_bounds__(kMaxBlockCells)
+__global__ void __launch_bounds__(kBlockThreads)
 k_block_components(GridGeom g, const uint8_t* __restrict__ cell_type, const int32_t* __restrict__ dof_of_node,
                    int32_t* __restrict__ comp_rank, int32_t* __restrict__ n_comp, int* status) {
   __shared__ int lab[kMaxBlockCells];
   __shared__ int rank_of[kMaxBlockCells];
+  __shared__ uint16_t vm[kMaxBlockCells];
   const int b = blockIdx.x;
   const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
   const int ncb = g.sx * g.sy * g.sz;
-  const int lc = threadIdx.x;
-  const bool valid = lc < ncb;
-  int li = 0, lj = 0, lk = 0;
-  int64_t c = -1;
-  bool act = false;
-  unsigned vmask = 0;
-  if (valid) {
-    li = lc % g.sx;
-    lj = (lc / g.sx) % g.sy;
-    lk = lc / (g.sx * g.sy);
+  for (int lc = threadIdx.x; lc < ncb; lc += blockDim.x) {
+    const int li = lc % g.sx, lj = (lc / g.sx) % g.sy, lk = lc / (g.sx * g.sy);
     const int gi = bi * g.sx + li, gj = bj * g.sy + lj, gk = bk * g.sz + lk;
-    c = g.cell(gi, gj, gk);
-    act = cell_type[c] != UFE_CELL_EXTERNAL;
-    if (act)
+    unsigned m = 0;
+    if (cell_type[g.cell(gi, gj, gk)] != UFE_CELL_EXTERNAL) {
+      m = kCellActive;
       for (int a = 0; a < 8; ++a)
-        if (dof_of_node[g.node(gi + (a & 1), gj + ((a >> 1) & 1), gk + (a >> 2))] >= 0) vmask |= 1u << a;
+        if (dof_of_node[g.node(gi + (a & 1), gj + ((a >> 1) & 1), gk + (a >> 2))] >= 0) m |= 1u << a;
+    }
+    vm[lc] = (uint16_t)m;
+    lab[lc] = m ? lc : INT_MAX;
   }
-  lab[lc] = (valid && act) ? lc : INT_MAX;
   __syncthreads();
   int it = 0;
   for (; it < 4 * kMaxBlockCells; ++it) {
     int changed = 0;
-    if (valid && act) {
+    for (int lc = threadIdx.x; lc < ncb; lc += blockDim.x) {
+      const unsigned vmask = vm[lc];
+      if (!vmask) continue;
+      const int li = lc % g.sx, lj = (lc / g.sx) % g.sy, lk = lc / (g.sx * g.sy);
       int m = lab[lc];
       for (int a = 0; a < 8; ++a) {
         if (!(vmask & (1u << a))) continue;
@@ -320,7 +320,10 @@ k_block_components(GridGeom g, const uint8_t* __restrict__ cell_type, const int3
     n_comp[b] = r;
   }
   __syncthreads();
-  if (valid) comp_rank[c] = act ? rank_of[lab[lc]] : -1;
+  for (int lc = threadIdx.x; lc < ncb; lc += blockDim.x) {
+    const int li = lc % g.sx, lj = (lc / g.sx) % g.sy, lk = lc / (g.sx * g.sy);
+    comp_rank[g.cell(bi * g.sx + li, bj * g.sy + lj, bk * g.sz + lk)] = vm[lc] ? rank_of[lab[lc]] : -1;
+  }
 }
 
 __global__ void k_sub_of_cell(GridGeom g, const int32_t* __restrict__ comp_rank, const int32_t* __restrict__ sub_base,
@@ -378,9 +381,10 @@ __global__ void k_neigh(GridGeom g, int64_t n_dof, const int32_t* __restrict__ n
 // ---------------------------------------------------------------------------
 // subdomain-local numbering: the DOFs of subdomain w are the DOF nodes of its
 // cells, in node order, split into interior (|neigh| = 1) and interface.
-// One CTA per subdomain, one thread per local node of its block.
+// One CTA per subdomain, walking the local nodes of its block in chunks of one node
+// per thread (the running counts carry the order from chunk to chunk).
 // ---------------------------------------------------------------------------
-constexpr int kMaxLocalNodes = 1024;
+constexpr int kLocalThreads = 1024;
 
 __device__ __forceinline__ bool node_in_sub(const GridGeom& g, int bi, int bj, int bk, int lx, int ly, int lz, int w,
                                             const int32_t* __restrict__ sub_of_cell) {
@@ -397,32 +401,37 @@ __device__ __forceinline__ bool node_in_sub(const GridGeom& g, int bi, int bj, i
   return false;
 }
 
-__global__ void __launch_bounds__(kMaxLocalNodes)
+__global__ void __launch_bounds__(kLocalThreads)
 k_local_count(GridGeom g, const int32_t* __restrict__ sub_block, const int32_t* __restrict__ sub_of_cell,
               const int32_t* __restrict__ dof_of_node, const uint8_t* __restrict__ n_neigh,
               int32_t* __restrict__ lmap, int32_t* __restrict__ nI, int32_t* __restrict__ nG) {
   const int w = blockIdx.x;
   const int b = sub_block[w];
   const int bi = b % g.bx, bj = (b / g.bx) % g.by, bk = b / (g.bx * g.by);
-  const int ln = threadIdx.x;
-  int kind = LKIND_NONE;
-  if (ln < g.n_local_nodes) {
-    const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
-    const int64_t v = g.node(bi * g.sx + lx, bj * g.sy + ly, bk * g.sz + lz);
-    const int32_t d = dof_of_node[v];
-    if (d >= 0 && node_in_sub(g, bi, bj, bk, lx, ly, lz, w, sub_of_cell))
-      kind = n_neigh[d] >= 2 ? LKIND_G : LKIND_I;
-  }
-  int totI, totG;
-  int pI = block_excl_scan(kind == LKIND_I, &totI);
-  int pG = block_excl_scan(kind == LKIND_G, &totG);
-  if (ln < g.n_local_nodes) {
-    int idx = kind == LKIND_I ? pI : (kind == LKIND_G ? pG : 0);
-    lmap[(int64_t)w * g.n_local_nodes + ln] = (kind << 24) | idx;
+  int baseI = 0, baseG = 0;
+  for (int l0 = 0; l0 < g.n_local_nodes; l0 += blockDim.x) {
+    const int ln = l0 + (int)threadIdx.x;
+    int kind = LKIND_NONE;
+    if (ln < g.n_local_nodes) {
+      const int lx = ln % g.lnx, ly = (ln / g.lnx) % g.lny, lz = ln / (g.lnx * g.lny);
+      const int64_t v = g.node(bi * g.sx + lx, bj * g.sy + ly, bk * g.sz + lz);
+      const int32_t d = dof_of_node[v];
+      if (d >= 0 && node_in_sub(g, bi, bj, bk, lx, ly, lz, w, sub_of_cell))
+        kind = n_neigh[d] >= 2 ? LKIND_G : LKIND_I;
+    }
+    int totI, totG;
+    const int pI = block_excl_scan(kind == LKIND_I, &totI);
+    const int pG = block_excl_scan(kind == LKIND_G, &totG);
+    if (ln < g.n_local_nodes) {
+      const int idx = kind == LKIND_I ? baseI + pI : (kind == LKIND_G ? baseG + pG : 0);
+      lmap[(int64_t)w * g.n_local_nodes + ln] = (kind << 24) | idx;
+    }
+    baseI += totI;
+    baseG += totG;
   }
   if (threadIdx.x == 0) {
-    nI[w] = totI;
-    nG[w] = totG;
+    nI[w] = baseI;
+    nG[w] = baseG;
   }
 }
 
@@ -585,8 +594,10 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
   sub_base.alloc(nblocks + 1, s);
   status.alloc(1, s);
   status.zero();
-  k_block_components<<<nblocks, kMaxBlockCells, 0, s>>>(g, m.cell_type.p, m.dof_of_node.p, comp_rank.p, n_comp.p,
-                                                          status.p);
+  const int ncb = g.sx * g.sy * g.sz;
+  UFE_REQUIRE(ncb <= kMaxBlockCells, UFE_ERR_INVALID_ARG, "more than 16^3 cells in one subdomain block");
+  k_block_components<<<nblocks, ncb <= 512 ? 512 : kBlockThreads, 0, s>>>(g, m.cell_type.p, m.dof_of_node.p,
+                                                                          comp_rank.p, n_comp.p, status.p);
   UFE_CHECK_LAUNCH();
   m.n_sub = scan_counts(n_comp.p, nblocks, sub_base.p, s);
   UFE_REQUIRE(scalar_to_host(status.p, s) == 0, UFE_ERR_TIMEOUT, "subdomain labelling did not converge");
@@ -609,8 +620,8 @@ void mesh_build(Mesh& m, const double* phi_dev, int64_t pin_node) {
   DBuf<int32_t> nI, nG;
   nI.alloc(m.n_sub, s);
   nG.alloc(m.n_sub, s);
-  k_local_count<<<(unsigned)m.n_sub, kMaxLocalNodes, 0, s>>>(g, m.sub_block.p, m.sub_of_cell.p, m.dof_of_node.p,
-                                                              m.n_neigh.p, m.lmap.p, nI.p, nG.p);
+  k_local_count<<<(unsigned)m.n_sub, kLocalThreads, 0, s>>>(g, m.sub_block.p, m.sub_of_cell.p, m.dof_of_node.p,
+                                                             m.n_neigh.p, m.lmap.p, nI.p, nG.p);
   UFE_CHECK_LAUNCH();
   m.I_ptr.alloc(m.n_sub + 1, s);
   m.G_ptr.alloc(m.n_sub + 1, s);

@@ -501,6 +501,7 @@ __device__ void cta_gemv_rows(const TM* __restrict__ M, int r0, int r1, int ld, 
 struct SubLaunch {
   int ldImax, ldGmax;   // largest padded interior / interface sizes
   int n_stages;         // row-stream stages per CTA (1..kMaxStages)
+  int stream_rows;      // rows per stage (kStreamRows, or fewer when one stage of long rows would not fit)
   // the subdomains of this launch: wl[cluster] (null: cluster c is subdomain c); with
   // subdomains in two precisions each stage is two launches, and the final stage's
   // dot products are partials part_off + CTA, summed (n_final of them) only by the
@@ -565,10 +566,12 @@ __device__ __forceinline__ SubSmem carve(char* smem, int ldImax, int ldGmax, siz
 // ---------------------------------------------------------------------------
 // row streaming: the rows of a CTA's slice of a dense local operator are moved
 // from HBM into a ring of shared-memory stages by bulk asynchronous copies
-// (cp.async.bulk, completion counted on an mbarrier), kStreamRows rows per stage,
+// (cp.async.bulk, completion counted on an mbarrier), kStreamRows rows per stage
+// (fewer for rows too long to fit eight in shared memory: 16-cell blocks in FP64),
 // so that a whole stage per CTA is in flight while the previous one is consumed.
-// One warp per row of a stage; each lane reads 16 bytes at a time from shared
-// memory.  Every wait is bounded by a wall-clock limit; on expiry the CTA records
+// One warp per row of a stage (with R < kStreamRows rows, kStreamRows / R warps split
+// each row's columns and their sums are added in warp order); each lane reads 16
+// bytes at a time from shared memory.  Every wait is bounded by a wall-clock limit; on expiry the CTA records
 // DEV_TIMEOUT, drains its copies (again bounded) and leaves its results undefined.
 // ---------------------------------------------------------------------------
 constexpr int kStreamRows = kSubThreads / 32;
@@ -618,28 +621,32 @@ __device__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 template <typename TM>
 struct RowStream {
   const TM* M;      // first row of the slice
-  TM* buf;          // n_stages * kStreamRows * ld values
+  TM* buf;          // n_stages * R * ld values
   uint64_t* full;   // one barrier per stage
-  int rows, ld, n_stages, n_steps;
+  double* part;     // kStreamRows partial row sums (R < kStreamRows)
+  int rows, ld, n_stages, n_steps, R;
 
   __device__ void issue(int step) const {
-    const int row0 = step * kStreamRows;
-    const int nr = min(kStreamRows, rows - row0);
+    const int row0 = step * R;
+    const int nr = min(R, rows - row0);
     const int slot = step % n_stages;
     const unsigned bytes = (unsigned)(nr * ld * (int)sizeof(TM));
     mbar_arrive_tx(&full[slot], bytes);
-    bulk_load(buf + (size_t)slot * kStreamRows * ld, M + (size_t)row0 * ld, bytes, &full[slot]);
+    bulk_load(buf + (size_t)slot * R * ld, M + (size_t)row0 * ld, bytes, &full[slot]);
   }
   // thread 0: initialise the barriers and put the first stages in flight; the
   // other threads may wait on them only after a later __syncthreads
-  __device__ void begin(const TM* M_, int r0, int r1, int ld_, void* stage, uint64_t* bars, int n_stages_) {
+  __device__ void begin(const TM* M_, int r0, int r1, int ld_, void* stage, uint64_t* bars, double* part_,
+                        const SubLaunch& L) {
     M = M_ + (size_t)r0 * ld_;
     buf = reinterpret_cast<TM*>(stage);
     full = bars;
+    part = part_;
     rows = r1 - r0;
     ld = ld_;
-    n_stages = n_stages_;
-    n_steps = (rows + kStreamRows - 1) / kStreamRows;
+    n_stages = L.n_stages;
+    R = L.stream_rows;
+    n_steps = (rows + R - 1) / R;
     if (threadIdx.x == 0) {
       for (int i = 0; i < n_stages; ++i) mbar_init(&full[i], 1);
       mbar_fence_init();
@@ -663,17 +670,38 @@ struct RowStream {
         __syncthreads();
         return;
       }
-      const int i = step * kStreamRows + wid;
-      if (i < rows) {
-        const TM* row = buf + ((size_t)slot * kStreamRows + wid) * ld;
-        TM acc = TM(0);
-        for (int c = lane * VN; c < ld; c += 32 * VN) acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
-        const double d = (double)warp_sum_tm(acc);
-        if (lane == 0) ys[i] = d;
+      if (R == kStreamRows) {
+        const int i = step * kStreamRows + wid;
+        if (i < rows) {
+          const TM* row = buf + ((size_t)slot * kStreamRows + wid) * ld;
+          TM acc = TM(0);
+          for (int c = lane * VN; c < ld; c += 32 * VN) acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
+          const double d = (double)warp_sum_tm(acc);
+          if (lane == 0) ys[i] = d;
+        }
+        __syncthreads();
+      } else {
+        // P = kStreamRows / R warps per row, each over every P-th chunk of 32 VN columns
+        const int P = kStreamRows / R, rl = wid / P, q = wid % P;
+        const int i = step * R + rl;
+        if (i < rows) {
+          const TM* row = buf + ((size_t)slot * R + rl) * ld;
+          TM acc = TM(0);
+          for (int c = (q * 32 + lane) * VN; c < ld; c += 32 * VN * P)
+            acc += dot_vec(*reinterpret_cast<const V*>(row + c), xs + c);
+          const double d = (double)warp_sum_tm(acc);
+          if (lane == 0) part[wid] = d;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < R && step * R + (int)threadIdx.x < rows) {
+          double d = 0.0;
+          for (int x = 0; x < P; ++x) d += part[threadIdx.x * P + x];
+          ys[step * R + threadIdx.x] = d;
+        }
       }
-      __syncthreads();
       if (threadIdx.x == 0 && step + n_stages < n_steps) issue(step + n_stages);
     }
+    if (R != kStreamRows) __syncthreads();   // the last step's sums are written after its barrier
   }
 };
 
@@ -753,10 +781,11 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   const SubSizes z = sub_sizes(sm, w);
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
+  __shared__ double rpart[kStreamRows];
   int r0, r1;
   row_slice<CL>(z.nI, rank, r0, r1);
   RowStream<TM> rs;
-  rs.begin(AIIinv + sm.off_II[w], r0, r1, z.ldI, S.stage, full, L.n_stages);
+  rs.begin(AIIinv + sm.off_II[w], r0, r1, z.ldI, S.stage, full, rpart, L);
   TM* xI = reinterpret_cast<TM*>(S.xT);
   const int i0 = sm.vI_ptr[w];
   for (int p = threadIdx.x; p < z.ldI; p += blockDim.x)
@@ -800,10 +829,11 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   if (z.nG == 0) return;
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
+  __shared__ double rpart[kStreamRows];
   int r0, r1;
   row_slice<CL>(z.nG, rank, r0, r1);
   RowStream<TM> rs;
-  rs.begin(Kop + sm.off_GG[w], r0, r1, z.ldG, S.stage, full, L.n_stages);
+  rs.begin(Kop + sm.off_GG[w], r0, r1, z.ldG, S.stage, full, rpart, L);
   TM* xG = reinterpret_cast<TM*>(S.xT);
   const int g0 = sm.vG_ptr[w];
   for (int j = threadIdx.x; j < z.ldG; j += blockDim.x) {
@@ -891,10 +921,11 @@ k_prec_final(SubMeta sm, const TM* __restrict__ AIIinv, const double* __restrict
   const SubSizes zz = sub_sizes(sm, w);
   SubSmem S = carve(smem, L.ldImax, L.ldGmax, sizeof(TM));
   __shared__ uint64_t full[kMaxStages];
+  __shared__ double rpart[kStreamRows];
   int p0, p1;
   row_slice<CL>(zz.nI, rank, p0, p1);
   RowStream<TM> rs;
-  rs.begin(AIIinv + sm.off_II[w], p0, p1, zz.ldI, S.stage, full, L.n_stages);
+  rs.begin(AIIinv + sm.off_II[w], p0, p1, zz.ldI, S.stage, full, rpart, L);
   TM* xI = reinterpret_cast<TM*>(S.xT);
   double rz = 0.0, rzo = 0.0;
   const int gn0 = sm.G_ptr[w];
@@ -1035,19 +1066,26 @@ void system_apply(const System& sys, const double* x_dev, double* y_dev, cudaStr
 }
 
 // shared-memory size and stage count of the per-subdomain kernels: the row-stream
-// ring gets about 26 KB, so that five CTAs fit on an SM next to each other
+// ring gets about 26 KB, so that five CTAs fit on an SM next to each other.  Rows so
+// long that one stage of kStreamRows of them does not fit next to the vectors (FP64
+// operators of 16-cell blocks) are streamed fewer to a stage.
 constexpr size_t kStageBudget = 26 * 1024;
+constexpr int kMaxDynSmem = 211 * 1024;
 
 static SubLaunch sub_launch(const Bddc& B, size_t tm_size, size_t* smem) {
   SubLaunch L;
   L.ldImax = pad4(std::max(B.max_nIv, 1));
   L.ldGmax = pad4(std::max(B.max_nGv, 1));
   const size_t ldmax = (size_t)std::max(L.ldImax, L.ldGmax);
-  const size_t stage = (size_t)kStreamRows * ldmax * tm_size;
-  L.n_stages = (int)std::max<size_t>(1, std::min<size_t>(kMaxStages, kStageBudget / stage));
-  if (B.prec_stages > 0) L.n_stages = std::min(B.prec_stages, kMaxStages);   // tuned
   size_t off = (size_t)L.ldImax * 8 + (size_t)L.ldGmax * 8 + ldmax * tm_size;
   off = (off + 127) & ~(size_t)127;
+  L.stream_rows = kStreamRows;
+  while (L.stream_rows > 1 && off + (size_t)L.stream_rows * ldmax * tm_size > (size_t)kMaxDynSmem) L.stream_rows >>= 1;
+  const size_t stage = (size_t)L.stream_rows * ldmax * tm_size;
+  L.n_stages = (int)std::max<size_t>(1, std::min<size_t>(kMaxStages, kStageBudget / stage));
+  if (B.prec_stages > 0) L.n_stages = std::min(B.prec_stages, kMaxStages);   // tuned
+  // never more stages than fit
+  while (L.n_stages > 1 && off + (size_t)L.n_stages * stage > (size_t)kMaxDynSmem) --L.n_stages;
   *smem = off + (size_t)L.n_stages * stage;
   return L;
 }
@@ -1197,18 +1235,21 @@ static void set_smem_limits_for(int optin) {
 // does not change what a launch requests, so problems of different sizes can share
 // it); each problem checks that its own request fits (with 16 KB left for the
 // kernels' static shared memory).
-constexpr int kMaxDynSmem = 211 * 1024;
+void check_local_sizes(const Bddc& B) {
+  size_t sd = 0, sf = 0;
+  sub_launch(B, 8, &sd);
+  sub_launch(B, 4, &sf);
+  UFE_REQUIRE(std::max(sd, sf) <= (size_t)kMaxDynSmem, UFE_ERR_UNSUPPORTED,
+              "local interface / interior sizes exceed one CTA's shared memory");
+}
+
 static void set_smem_limits(Bddc& B) {
   static std::mutex mu;
   static bool done[128] = {};
   int dev = 0;
   UFE_CUDA(cudaGetDevice(&dev));
   UFE_REQUIRE(dev >= 0 && dev < 128, UFE_ERR_UNSUPPORTED, "device ordinal beyond 127");
-  size_t sd = 0, sf = 0;
-  sub_launch(B, 8, &sd);
-  sub_launch(B, 4, &sf);
-  UFE_REQUIRE(std::max(sd, sf) <= (size_t)kMaxDynSmem, UFE_ERR_UNSUPPORTED,
-              "local interface / interior sizes exceed one CTA's shared memory");
+  check_local_sizes(B);
   std::lock_guard<std::mutex> lock(mu);
   if (done[dev]) return;
   int optin = 0;

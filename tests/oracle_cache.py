@@ -39,6 +39,23 @@ def small_problems():
     }
 
 
+def large_block_problems():
+    """Blocks of more than 8 cells per edge (Sect. 5.2 studies H/h up to 16): a sphere
+    in 16^3-cell blocks, a plane cut that leaves whole blocks nearly full (17^3 local
+    nodes, interiors near 15^3), and a ragged 16 x 12 x 16 block shape."""
+    return {
+        "lb_sphere": inputs.sphere_problem(cells=(32, 32, 32), sub_cells=(16, 16, 16), centre=(0.02, -0.01, 0.03),
+                                           radius=0.7, box_lo=(-1, -1, -1), box_hi=(1, 1, 1),
+                                           dirichlet_face_mask=0, pin_node=inputs.PIN_AUTO, name="lb_sphere"),
+        "lb_plane": inputs.plane_problem(cells=(32, 32, 32), sub_cells=(16, 16, 16), normal=(0.3, 0.2, 0.93),
+                                         offset=0.97, dirichlet_face_mask=inputs.ALL_FACES, name="lb_plane"),
+        "lb_ragged": inputs.sphere_problem(cells=(32, 24, 16), sub_cells=(16, 12, 16), centre=(0.55, 0.4, 0.26),
+                                           radius=0.4, box_lo=(0, 0, 0), box_hi=(1.0, 0.75, 0.5),
+                                           dirichlet_face_mask=inputs.FACE_XLO, pin_node=inputs.PIN_AUTO,
+                                           name="lb_ragged"),
+    }
+
+
 def _tower():
     """A wavy cylinder along z through 8 layers of 4^3-cell blocks (pure Neumann, pinned)."""
     cells = (8, 8, 32)
@@ -171,6 +188,8 @@ def oracle_run(name):
         return ElasticOracleRun(elastic_problems()[name])
     if name.startswith("ni_"):
         return OracleRun(nitsche_problems()[name])
+    if name.startswith("lb_"):
+        return OracleRun(large_block_problems()[name])
     return OracleRun(small_problems()[name])
 
 
