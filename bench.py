@@ -369,7 +369,7 @@ def roofline_block(kt, n_steps, binfo, per_iter, iterations, fma, peaks, n_subte
     return out
 
 
-def adjoint_workload(U, dev, stream, flush, precision, reps=2):
+def adjoint_workload(U, dev, stream, flush, precision, reps=2, coarse_solver="auto"):
     """Config-5 style adjoint workload (128^3 background cells, 16^3 subdomains, sphere of
     radius 0.45, per-cell kappa = exp(GRF)): mesh, assembly, BDDC set-up, forward solve
     and adjoint solve with the per-cell gradient, timed by CUDA events; returns the mean
@@ -391,7 +391,8 @@ def adjoint_workload(U, dev, stream, flush, precision, reps=2):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        with Solver(p, precision=precision, arrays=dict(arrays), stream=stream.cuda_stream) as S:
+        with Solver(p, precision=precision, arrays=dict(arrays), stream=stream.cuda_stream,
+                    coarse_solver=coarse_solver) as S:
             u = torch.zeros(S.n_dof, dtype=torch.float64, device=dev)
             _, fi = U.ufe_pcg_solve(S.system, S.bddc, None, u, rtol=RTOL, maxit=2000)
             dof = torch.from_numpy(U.ufe_mesh_get_dof_map(S.mesh)).to(dev).long()
@@ -404,14 +405,16 @@ def adjoint_workload(U, dev, stream, flush, precision, reps=2):
                                maxit=2000)
             e1.record(stream)
             torch.cuda.synchronize()
-            info = (S.n_dof, S.info["n_subdomains"], S.bddc_info["n_coarse"], fi, ai)
+            info = (S.n_dof, S.info["n_subdomains"], S.bddc_info["n_coarse"], fi, ai, S.bddc_info)
         if rep > 0:
             times.append(e0.elapsed_time(e1) / 1e3)
         last = info
-    n, nsub, nc, fi, ai = last
+    n, nsub, nc, fi, ai, bi = last
     return {"value": statistics.mean(times), "unit": "s", "reps": reps, "n_dof": n, "subdomains": nsub,
             "n_coarse": nc, "forward_iterations": fi["iterations"], "adjoint_iterations": ai["iterations"],
-            "forward_true_rel_residual": fi["true_rel_residual"]}
+            "forward_true_rel_residual": fi["true_rel_residual"], "setup_ms": bi["setup_ms"],
+            "forward_solve_ms": fi["solve_ms"], "coarse_solver": bi["coarse_solver"],
+            "level2_subdomains": bi["level2_subdomains"], "level3_coarse": bi["level3_coarse"]}
 
 
 def elastic_workload(U, dev, stream, flush, precision, reps=2):
@@ -516,7 +519,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def step(precision, host=False):
+    def step(precision, host=False, coarse_solver=0):
         if host:
             phi, f = p.phi, p.f
         else:
@@ -528,7 +531,7 @@ def run_ours(args, rank, world):
             n = U.ufe_mesh_get_info(mesh)["n_dof"]
             sysh = U.ufe_assemble(mesh, None, f, None, None)
             bddc = U.ufe_bddc_setup(sysh, U.WEIGHT_STIFFNESS, U.OBJECTS_VARIANT1, U.COARSE_CEF,
-                                    U.PREC_MIXED if precision == "mixed" else U.PREC_FP64)
+                                    U.PREC_MIXED if precision == "mixed" else U.PREC_FP64, coarse_solver)
             x = np.zeros(n) if host else torch.zeros(n, dtype=torch.float64, device=dev)
             _, info = U.ufe_pcg_solve(sysh, bddc, None, x, rtol=RTOL, maxit=1000)
             binfo = U.ufe_bddc_get_info(bddc)
@@ -607,7 +610,30 @@ def run_ours(args, rank, world):
            "fp32": U.ufe_probe_fma_rate("fp32", stream.cuda_stream)}
     extra = {}
     if not args.no_extra and world == 1:
+        # the same workload with the three-level method (the coarse problem preconditioned
+        # by BDDC over groups of 2^3 blocks instead of inverted)
+        tl = {}
+        for prec in ("mixed", "fp64"):
+            step(prec, coarse_solver=U.COARSE_SOLVER_BDDC)
+            ts = []
+            for _ in range(5):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, tinfo, tb, _ = step(prec, coarse_solver=U.COARSE_SOLVER_BDDC)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            tl[prec] = {"ms_per_step": statistics.mean(ts), "iterations": tinfo["iterations"],
+                        "setup_ms": tb["setup_ms"], "solve_ms": tinfo["solve_ms"],
+                        "true_rel_residual": tinfo["true_rel_residual"],
+                        "level2_subdomains": tb["level2_subdomains"], "level3_coarse": tb["level3_coarse"]}
+        extra["three_level"] = tl
         extra["adjoint_128^3"] = {prec: adjoint_workload(U, dev, stream, flush, prec) for prec in ("mixed", "fp64")}
+        extra["adjoint_128^3"]["mixed_three_level"] = adjoint_workload(U, dev, stream, flush, "mixed",
+                                                                       coarse_solver="bddc")
         extra["batched_256"] = batched_workload(U, dev, stream, flush)
         extra["elastic_96^3"] = {prec: elastic_workload(U, dev, stream, flush, prec) for prec in ("mixed", "fp64")}
 

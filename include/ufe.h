@@ -83,6 +83,9 @@ typedef int ufe_status;
 #define UFE_COARSE_SOLVER_AUTO  0  /* dense inverse up to 2048 coarse DOFs, else cyclic reduction */
 #define UFE_COARSE_SOLVER_DENSE 1  /* explicit FP64 inverse of A_c (n_coarse up to ~28,000: r_c in one CTA's shared memory) */
 #define UFE_COARSE_SOLVER_CR    2  /* FP64 block cyclic reduction over the z layers of subdomain blocks */
+#define UFE_COARSE_SOLVER_BDDC  3  /* three-level method (Poisson): the coarse problem is not solved but
+                                      preconditioned by BDDC over groups of coarse_group^3 blocks of
+                                      subdomains, whose own coarse problem is inverted in FP64 */
 
 #define UFE_PIN_NONE -1
 #define UFE_PIN_AUTO -2
@@ -286,7 +289,10 @@ typedef struct {
   int32_t objects;     /* UFE_OBJECTS_* */
   int32_t coarse;      /* UFE_COARSE_* */
   int32_t precision;   /* UFE_PREC_* */
-  int32_t coarse_solver;   /* UFE_COARSE_SOLVER_* (both solve the coarse problem exactly in FP64) */
+  int32_t coarse_solver;   /* UFE_COARSE_SOLVER_* (DENSE and CR solve the coarse problem exactly in FP64,
+                              BDDC preconditions it one level up) */
+  int32_t coarse_group;    /* UFE_COARSE_SOLVER_BDDC: blocks per level-2 subdomain edge (0: 2); read
+                              only with that solver */
 } ufe_bddc_opts;
 
 typedef struct {
@@ -305,7 +311,7 @@ typedef struct {
   int32_t fp64_refactor;   /* mixed precision requested: 1 when no subdomain could keep FP32 local
                               operators (see fp64_subdomains), so the whole problem is factored and
                               applied in FP64 (classical PCG) */
-  int32_t coarse_solver;   /* the coarse solver used: UFE_COARSE_SOLVER_DENSE or _CR */
+  int32_t coarse_solver;   /* the coarse solver used: UFE_COARSE_SOLVER_DENSE, _CR or _BDDC */
   double cphi_error;       /* mixed precision requested: max |C Phi - I| of the FP32 coarse basis (Sect.
                               3.2 defines Phi by C Phi = I) over the subdomains that keep FP32
                               operators; a subdomain above 1e-2 gets FP64 operators */
@@ -322,6 +328,10 @@ typedef struct {
                                 not positive), or whose FP32 coarse basis missed C Phi = I by more
                                 than 1e-2 (tiny cut fractions); they are factored and applied in
                                 FP64, the others in FP32 */
+  int32_t level2_subdomains;   /* UFE_COARSE_SOLVER_BDDC: level-2 subdomains (groups of blocks split
+                                  into components linked by shared coarse DOFs); 0 otherwise */
+  int32_t level3_coarse;       /* UFE_COARSE_SOLVER_BDDC: level-2 objects, the DOFs of the inverted
+                                  level-3 problem; 0 otherwise */
 } ufe_bddc_info;
 
 /*
@@ -336,8 +346,15 @@ typedef struct {
  * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled in FP64 and solved
  * exactly in FP64: explicit inverse, or block cyclic reduction over the z layers of
  * subdomain blocks, in which order A_c is block tridiagonal (opts.coarse_solver).
+ * With UFE_COARSE_SOLVER_BDDC (Poisson; Sect. 6 points to multilevel BDDC beyond one
+ * coarse factorisation) A_c is instead preconditioned by BDDC one level up: level-2
+ * subdomains group coarse_group^3 blocks (split into components linked by shared
+ * coarse DOFs), level-2 objects are the coarse DOFs shared by equal sets of level-2
+ * subdomains (split into components; corners / edges / faces by opts.coarse), their
+ * means are the level-3 DOFs, weights are stiffness weights of the level-2 matrices,
+ * and the level-3 matrix is inverted in FP64.
  * Errors: SINGULAR_LOCAL (e.g. a floating subdomain with no coarse DOF),
- * SINGULAR_COARSE, INVALID_ARG, CUDA, OUT_OF_MEMORY, TIMEOUT.
+ * SINGULAR_COARSE, INVALID_ARG, UNSUPPORTED, CUDA, OUT_OF_MEMORY, TIMEOUT.
  */
 ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc** out);
 ufe_status ufe_bddc_get_info(const ufe_bddc* bddc, ufe_bddc_info* info);
@@ -368,7 +385,9 @@ ufe_status ufe_bddc_apply(ufe_bddc* bddc, const double* r, double* z, int mem);
  *
  * The preconditioner's intermediate vectors live in one file-scope device array
  * of fixed size (688,128 doubles, about 5.5 MB, held by every device that loads the
- * library until the process exits) instead of the buffers ufe_bddc_setup made.
+ * library until the process exits) instead of the buffers ufe_bddc_setup made; with
+ * UFE_COARSE_SOLVER_BDDC the level-2 vectors stay in the handle's own buffers, which
+ * set-up allocated and the call reuses.
  * Problems beyond its limits -- more than 262,144 interface slots (the sum over
  * subdomains of their interface DOFs, counted per component), 65,536 subdomain coarse slots or 32,768
  * coarse DOFs -- are rejected with UFE_ERR_INVALID_ARG and a message naming the

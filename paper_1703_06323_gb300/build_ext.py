@@ -12,7 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(OUT_DIR, "libufe.so")
 
-SOURCES = ["mesh.cu", "integrate.cu", "dense.cu", "bddc.cu", "coarse.cu", "pcg.cu", "api.cu"]
+SOURCES = ["mesh.cu", "integrate.cu", "dense.cu", "bddc.cu", "coarse.cu", "multilevel.cu", "pcg.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "--extended-lambda", "-I", INCLUDE]
 

@@ -503,8 +503,12 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     UFE_REQUIRE(opts->objects != UFE_OBJECTS_VARIANT2 || sys->ncomp == 1, UFE_ERR_UNSUPPORTED,
                 "variant-2 objects: Poisson systems only");
     UFE_REQUIRE(opts->coarse >= UFE_COARSE_C && opts->coarse <= UFE_COARSE_CEF, UFE_ERR_INVALID_ARG, "bad coarse");
-    UFE_REQUIRE(opts->coarse_solver >= UFE_COARSE_SOLVER_AUTO && opts->coarse_solver <= UFE_COARSE_SOLVER_CR,
+    UFE_REQUIRE(opts->coarse_solver >= UFE_COARSE_SOLVER_AUTO && opts->coarse_solver <= UFE_COARSE_SOLVER_BDDC,
                 UFE_ERR_INVALID_ARG, "bad coarse solver");
+    UFE_REQUIRE(opts->coarse_solver != UFE_COARSE_SOLVER_BDDC || sys->ncomp == 1, UFE_ERR_UNSUPPORTED,
+                "the three-level coarse solver: Poisson systems only");
+    UFE_REQUIRE(opts->coarse_solver != UFE_COARSE_SOLVER_BDDC || (opts->coarse_group >= 0 && opts->coarse_group <= 1024),
+                UFE_ERR_INVALID_ARG, "coarse_group must lie in 0..1024");
     UFE_REQUIRE(opts->precision == UFE_PREC_FP64 || opts->precision == UFE_PREC_MIXED, UFE_ERR_INVALID_ARG,
                 "bad precision");
     *out = nullptr;
@@ -515,6 +519,7 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     B->opts = *opts;
     B->mixed = opts->precision == UFE_PREC_MIXED;
     B->coarse_solver = opts->coarse_solver;
+    if (opts->coarse_solver == UFE_COARSE_SOLVER_BDDC && opts->coarse_group > 0) B->coarse_group = opts->coarse_group;
     UFE_CUDA(cudaGetDevice(&B->device));
     bddc_build(*B);
     tune_preconditioner(*B);
@@ -544,7 +549,11 @@ ufe_status ufe_bddc_get_info(const ufe_bddc* B, ufe_bddc_info* info) {
     info->interior_slots = B->n_vIloc;
     info->interface_slots = B->n_vGloc;
     info->fp64_refactor = B->fp64_refactor;
-    info->coarse_solver = B->coarse_dense ? UFE_COARSE_SOLVER_DENSE : UFE_COARSE_SOLVER_CR;
+    info->coarse_solver = B->ml.n2 > 0     ? UFE_COARSE_SOLVER_BDDC
+                          : B->coarse_dense ? UFE_COARSE_SOLVER_DENSE
+                                            : UFE_COARSE_SOLVER_CR;
+    info->level2_subdomains = B->ml.n2;
+    info->level3_coarse = B->ml.n3;
     info->coarse_layers = B->cr.nlayers;
     info->cphi_error = B->cphi_error;
     info->local_tensor_cores = B->local_tc;

@@ -1407,7 +1407,14 @@ void bddc_build(Bddc& B) {
   // factored by block cyclic reduction over the z layers of subdomain blocks (coarse.cu)
   auto do_coarse = [&]() {
     ph_co.begin("phase_coarse", s);
-    if (nco) {
+    if (nco && B.coarse_solver == UFE_COARSE_SOLVER_BDDC) {
+      // three-level method: the coarse problem is never assembled; BDDC over groups of
+      // subdomains is built from the A_c^w (multilevel.cu)
+      B.coarse_dense = false;
+      ml_setup(B, Acw, oCC, B.coarse_group, s);
+      B.cr.bytes = B.ml.bytes;
+      B.cr.inv_flops = B.ml.inv_flops;
+    } else if (nco) {
       const int ldc = pad4((int)nco);
       DBuf<double> Ac;
       Ac.alloc((size_t)nco * ldc, s);

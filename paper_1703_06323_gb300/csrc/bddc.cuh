@@ -96,6 +96,23 @@ struct CoarseCR {
   double inv_flops = 0.0;      // sum of n_j^3 over the inverted layer blocks
 };
 
+// three-level method (multilevel.cu): the coarse problem preconditioned by BDDC over
+// groups of subdomains ("level 2"), whose own coarse problem ("level 3") is inverted
+struct MultiLevel {
+  int n2 = 0;                   // level-2 subdomains (0: the three-level method is not in use)
+  int n3 = 0, ld3 = 4;          // level-3 coarse DOFs (level-2 objects)
+  int n_obj2 = 0;
+  int64_t n_slots = 0;          // sum over level-2 subdomains of their coarse DOFs
+  int max_n = 0, max_nI = 0, max_nG = 0, max_nC = 0;
+  DBuf<int32_t> dof_ptr, nI, dofs, slot_J, gpos2, c_ptr, c_list, cpos3;
+  DBuf<uint8_t> owner, nn2, nn3;
+  DBuf<int64_t> offA, offK, offP;
+  DBuf<double> store;           // every level-2 operator (FP64)
+  DBuf<double> A3inv;           // level-3 inverse (n3 x ld3)
+  DBuf<double> w2, y2, rc2, t2, vw2, g3, u3;
+  double bytes = 0.0, inv_flops = 0.0;
+};
+
 struct Bddc {
   System* sys = nullptr;
   Mesh* mesh = nullptr;
@@ -131,10 +148,12 @@ struct Bddc {
   DBuf<int32_t> gi_k, ig_k;     // A_GI / A_IG in ELL form (local indices)
   DBuf<double> gi_v, ig_v;
   int coarse_solver = 0;        // requested UFE_COARSE_SOLVER_*
+  int coarse_group = 2;         // three-level method: blocks per level-2 subdomain edge
   bool coarse_dense = true;     // resolved: explicit inverse (else cyclic reduction)
   DBuf<double> Ac_inv;          // dense: n_coarse x ldc, FP64
   int ldc = 0;
   CoarseCR cr;                  // cyclic reduction over the z layers of subdomain blocks
+  MultiLevel ml;                // three-level method (coarse_solver UFE_COARSE_SOLVER_BDDC)
 
   // solver work space
   DBuf<double> tG, vw, gC, uc;
@@ -174,6 +193,15 @@ void bddc_build(Bddc& B);
 // from the subdomain parts gC (work: 2 n_coarse doubles)
 void coarse_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s);
 void coarse_solve(const Bddc& B, const double* gC, double* uc, double* work, const PcgScalars* sc, cudaStream_t s);
+// u = A^-1 r with r gathered from up to eight parts per row (parts[cpos[8 l + k]], k < cnn[l])
+// checks that r of n values fits one CTA's shared memory and raises the kernel's limit
+void dense_coarse_prepare(int64_t n, int ld);
+void dense_coarse_gemv(int64_t n, int ld, const double* Ainv, const int32_t* cpos, const uint8_t* cnn,
+                       const double* parts, double* u, const PcgScalars* sc, cudaStream_t s);
+// three-level method: level-2 set-up from the subdomains' coarse matrices A_c^w (offsets
+// oCC, host) with groups of `group`^3 blocks, and one application u_c = M_2 r_c
+void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& oCC, int group, cudaStream_t s);
+void ml_coarse_solve(const Bddc& B, const double* gC, double* uc, const PcgScalars* sc, cudaStream_t s);
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev);
 void bddc_apply_noalloc(Bddc& B, const double* r_dev, double* z_dev);
 // made by the set-up: loads the device code and looks up the static array the

@@ -215,13 +215,22 @@ __global__ void k_coarse_dense(int64_t nco, int ldc, const double* __restrict__ 
   }
 }
 
+void dense_coarse_gemv(int64_t n, int ld, const double* Ainv, const int32_t* cpos, const uint8_t* cnn,
+                       const double* parts, double* u, const PcgScalars* sc, cudaStream_t s) {
+  const size_t csm = (size_t)ld * 8;
+  const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 1216));
+  k_coarse_dense<<<cg, 256, csm, s>>>(n, ld, Ainv, cpos, cnn, parts, u, sc);
+  UFE_CHECK_LAUNCH();
+}
+
 void coarse_solve(const Bddc& B, const double* gC, double* uc, double* work, const PcgScalars* sc, cudaStream_t s) {
   if (B.n_coarse == 0) return;
+  if (B.ml.n2 > 0) {
+    ml_coarse_solve(B, gC, uc, sc, s);
+    return;
+  }
   if (B.coarse_dense) {
-    const size_t csm = (size_t)B.ldc * 8;
-    const unsigned cg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((B.n_coarse + 7) / 8, 1216));
-    k_coarse_dense<<<cg, 256, csm, s>>>(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, sc);
-    UFE_CHECK_LAUNCH();
+    dense_coarse_gemv(B.n_coarse, B.ldc, B.Ac_inv.p, B.cpos.p, B.coarse_nn.p, gC, uc, sc, s);
     return;
   }
   const CoarseCR& C = B.cr;
@@ -283,19 +292,23 @@ __global__ void k_first_nonzero(const double* __restrict__ A, int n, int ld, int
   if (lane == 0) first[row] = f;
 }
 
-static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
-  const int64_t n = B.n_coarse;
+void dense_coarse_prepare(int64_t n, int ld) {
   int dev = 0, optin = 0;
   UFE_CUDA(cudaGetDevice(&dev));
   UFE_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   cudaFuncAttributes fa;
   UFE_CUDA(cudaFuncGetAttributes(&fa, k_coarse_dense));
-  const int64_t smem = 8 * (int64_t)ldc;
+  const int64_t smem = 8 * (int64_t)ld;
   UFE_REQUIRE(smem <= optin - (int64_t)fa.sharedSizeBytes, UFE_ERR_UNSUPPORTED,
               "dense coarse solver: " + std::to_string(n) + " coarse DOFs exceed one CTA's shared memory");
   if (smem > 48 * 1024)   // the largest allowed, so that no later set-up lowers it under an earlier one
     UFE_CUDA(cudaFuncSetAttribute(k_coarse_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   optin - (int)fa.sharedSizeBytes));
+}
+
+static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
+  const int64_t n = B.n_coarse;
+  dense_coarse_prepare(n, ldc);
   DBuf<int> st;
   st.alloc(1, s);
   st.zero();

@@ -13,14 +13,15 @@ WEIGHTING = {"stiffness": ufe.WEIGHT_STIFFNESS, "topological": ufe.WEIGHT_TOPOLO
 OBJECTS = {"std": ufe.OBJECTS_STANDARD, "v1": ufe.OBJECTS_VARIANT1, "v2": ufe.OBJECTS_VARIANT2}
 COARSE = {"c": ufe.COARSE_C, "ce": ufe.COARSE_CE, "cef": ufe.COARSE_CEF}
 PRECISION = {"fp64": ufe.PREC_FP64, "mixed": ufe.PREC_MIXED}
-COARSE_SOLVER = {"auto": ufe.COARSE_SOLVER_AUTO, "dense": ufe.COARSE_SOLVER_DENSE, "cr": ufe.COARSE_SOLVER_CR}
+COARSE_SOLVER = {"auto": ufe.COARSE_SOLVER_AUTO, "dense": ufe.COARSE_SOLVER_DENSE, "cr": ufe.COARSE_SOLVER_CR,
+                 "bddc": ufe.COARSE_SOLVER_BDDC}
 
 
 class Solver:
     """Owns the ufe handles of one problem (host numpy inputs or torch CUDA tensors)."""
 
     def __init__(self, problem, weighting="stiffness", objects="v1", coarse="cef", precision="fp64", stream=None,
-                 arrays=None, coarse_solver="auto"):
+                 arrays=None, coarse_solver="auto", coarse_group=0):
         p = problem
         a = arrays or {}
         self.mesh = ufe.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, a.get("phi", p.phi),
@@ -39,7 +40,7 @@ class Solver:
                 self.system = ufe.ufe_assemble(self.mesh, a.get("kappa", p.kappa), a.get("f", p.f),
                                                a.get("q", p.q), a.get("g", p.dirichlet_values))
             self.bddc = ufe.ufe_bddc_setup(self.system, WEIGHTING[weighting], OBJECTS[objects], COARSE[coarse],
-                                           PRECISION[precision], COARSE_SOLVER[coarse_solver])
+                                           PRECISION[precision], COARSE_SOLVER[coarse_solver], coarse_group)
             self.bddc_info = ufe.ufe_bddc_get_info(self.bddc)
         except Exception:
             self.close()

@@ -25,7 +25,7 @@ WEIGHT_STIFFNESS, WEIGHT_TOPOLOGICAL = 0, 1
 OBJECTS_STANDARD, OBJECTS_VARIANT1, OBJECTS_VARIANT2 = 0, 1, 2
 COARSE_C, COARSE_CE, COARSE_CEF = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
-COARSE_SOLVER_AUTO, COARSE_SOLVER_DENSE, COARSE_SOLVER_CR = 0, 1, 2
+COARSE_SOLVER_AUTO, COARSE_SOLVER_DENSE, COARSE_SOLVER_CR, COARSE_SOLVER_BDDC = 0, 1, 2, 3
 PIN_NONE, PIN_AUTO = -1, -2
 
 
@@ -45,7 +45,7 @@ class MeshInfo(ctypes.Structure):
 
 class BddcOpts(ctypes.Structure):
     _fields_ = [("weighting", ctypes.c_int32), ("objects", ctypes.c_int32), ("coarse", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("coarse_solver", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("coarse_solver", ctypes.c_int32), ("coarse_group", ctypes.c_int32)]
 
 
 class BddcInfo(ctypes.Structure):
@@ -59,7 +59,8 @@ class BddcInfo(ctypes.Structure):
                 ("fp64_refactor", ctypes.c_int32), ("coarse_solver", ctypes.c_int32), ("cphi_error", ctypes.c_double),
                 ("coarse_layers", ctypes.c_int32), ("coarse_levels", ctypes.c_int32),
                 ("local_tensor_cores", ctypes.c_int32), ("prec_cluster", ctypes.c_int32),
-                ("prec_stages", ctypes.c_int32), ("fp64_subdomains", ctypes.c_int32)]
+                ("prec_stages", ctypes.c_int32), ("fp64_subdomains", ctypes.c_int32),
+                ("level2_subdomains", ctypes.c_int32), ("level3_coarse", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -332,8 +333,8 @@ def ufe_system_destroy(system):
 
 
 def ufe_bddc_setup(system, weighting=WEIGHT_STIFFNESS, objects=OBJECTS_VARIANT1, coarse=COARSE_CEF,
-                   precision=PREC_FP64, coarse_solver=0):
-    opts = BddcOpts(weighting, objects, coarse, precision, coarse_solver)
+                   precision=PREC_FP64, coarse_solver=0, coarse_group=0):
+    opts = BddcOpts(weighting, objects, coarse, precision, coarse_solver, coarse_group)
     out = ctypes.c_void_p()
     _check(LIB.ufe_bddc_setup(system, ctypes.byref(opts), ctypes.byref(out)))
     return out

@@ -190,6 +190,11 @@ def oracle_run(name):
         return OracleRun(nitsche_problems()[name])
     if name.startswith("lb_"):
         return OracleRun(large_block_problems()[name])
+    if name == "ml_box":
+        # whole box, 8^3 cells in 2^3-cell blocks (64 subdomains): with groups of 2^3
+        # blocks the level-2 objects of the three-level method hold several coarse DOFs
+        return OracleRun(inputs.box_problem(cells=(8, 8, 8), sub_cells=(2, 2, 2), dirichlet_face_mask=inputs.ALL_FACES,
+                                            name="ml_box"))
     return OracleRun(small_problems()[name])
 
 

@@ -1,0 +1,139 @@
+"""GPU parity of the three-level method (UFE_COARSE_SOLVER_BDDC) against the oracle's
+ThreeLevelBDDC (reading R26): the level-2 partition (level-2 subdomain and level-3
+DOF counts) bit for bit; z = M_3 r in the energy norm (FP64 1e-9, mixed 1e-3);
+PCG iteration counts at rtol 1e-8 (FP64 within 1; mixed at most 35 % + 1 above the
+oracle's FP64 count, see test_solution) and the solution
+at rtol 1e-12 against the oracle's discrete solution (FP64 1e-8, mixed 1e-6); the
+exact limit of one level-2 subdomain against the two-level method; and the 64^3
+bumpy sphere solved by both methods to the same solution.
+"""
+import numpy as np
+import pytest
+
+from tests.oracle_cache import energy_error, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ufe():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06323_gb300 import build_ext
+    build_ext.build()
+    from paper_1703_06323_gb300 import ufe as U
+    return U
+
+
+def _solver(p, **kw):
+    from paper_1703_06323_gb300.solver import Solver
+    return Solver(p, **kw)
+
+
+def _run(name):
+    return oracle_run(name)
+
+
+CASES = [("ml_box", 2), ("tower", 1), ("tower", 2), ("sphere_ragged", 2), ("ni_sphere", 2), ("sphere16", 1)]
+
+
+def _three(orc, group):
+    from oracle.multilevel import ThreeLevelBDDC
+    return ThreeLevelBDDC(orc.bddc(), group=group)
+
+
+@pytest.mark.parametrize("name,group", CASES)
+def test_partition_and_preconditioner_fp64(ufe, name, group):
+    orc = _run(name)
+    T = _three(orc, group)
+    r = np.random.default_rng(21).normal(size=orc.mesh.n_dof)
+    ref = T.apply(r)
+    with _solver(orc.p, coarse_solver="bddc", coarse_group=group) as S:
+        bi = S.bddc_info
+        assert bi["coarse_solver"] == ufe.COARSE_SOLVER_BDDC
+        assert bi["level2_subdomains"] == T.level2.n_sub2
+        assert bi["level3_coarse"] == T.level2.n_coarse
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("name,group", [("tower", 2), ("ni_sphere", 2)])
+def test_preconditioner_mixed(ufe, name, group):
+    orc = _run(name)
+    r = np.random.default_rng(22).normal(size=orc.mesh.n_dof)
+    ref = _three(orc, group).apply(r)
+    with _solver(orc.p, precision="mixed", coarse_solver="bddc", coarse_group=group) as S:
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("name,group", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solution(ufe, name, group, precision):
+    from oracle.pcg import pcg
+    orc = _run(name)
+    T = _three(orc, group)
+    ref8 = pcg(orc.sys.apply, orc.sys.b, T.apply, rtol=1e-8, maxit=2000)
+    ref = orc.solve(rtol=1e-12)
+    with _solver(orc.p, precision=precision, coarse_solver="bddc", coarse_group=group) as S:
+        x, info = S.solve(rtol=1e-8)
+        assert info["converged"] == 1 and info["true_rel_residual"] <= 1.5e-8
+        if precision == "fp64":
+            assert abs(info["iterations"] - ref8["iterations"]) <= 1
+        else:
+            # the inexact coarse solve makes the count sensitive to the FP32 rounding of
+            # the first level's A_c^w: perturbing them by 1e-6 relative moves the
+            # oracle's own count on the tower from 17 to 19
+            assert ref8["iterations"] - 2 <= info["iterations"] <= 1.35 * ref8["iterations"] + 1
+        x12, info12 = S.solve(rtol=1e-12, maxit=3000)
+    assert info12["converged"] == 1
+    assert energy_error(orc.sys.A, x12, ref["x"]) <= (1e-8 if precision == "fp64" else 1e-6)
+
+
+def test_one_level2_subdomain_is_the_two_level_method(ufe):
+    """Groups larger than the block grid: one level-2 subdomain with no interface, so
+    M_2 = A_c^-1 and M_3 r equals the two-level M r (dense coarse inverse) to rounding."""
+    orc = _run("tower")
+    r = np.random.default_rng(23).normal(size=orc.mesh.n_dof)
+    with _solver(orc.p, coarse_solver="dense") as S:
+        z2 = S.precondition(r)
+    with _solver(orc.p, coarse_solver="bddc", coarse_group=64) as S:
+        assert S.bddc_info["level2_subdomains"] == 1 and S.bddc_info["level3_coarse"] == 0
+        z3 = S.precondition(r)
+    assert energy_error(orc.sys.A, z3, z2) <= 1e-11
+
+
+def test_bench_workload_three_level(ufe):
+    """The 64^3 bumpy sphere (51,081 DOFs, 172 subdomains, 1,075 coarse DOFs) with the
+    three-level method, groups of 2^3 blocks: converged at rtol 1e-8 with the true
+    residual within it, and the rtol 1e-12 solution equal to the two-level one in the
+    energy norm to 1e-8 (both are the discrete solution)."""
+    from paper_1703_06323_gb300 import inputs
+    p = inputs.bumpy_sphere(0)
+    out = {}
+    for cs in ("dense", "bddc"):
+        for precision in ("fp64", "mixed"):
+            with _solver(p, precision=precision, coarse_solver=cs) as S:
+                x, info = S.solve(rtol=1e-8)
+                assert info["converged"] == 1 and info["true_rel_residual"] <= 1.5e-8
+                x12, _ = S.solve(rtol=1e-12, maxit=3000)
+                out[cs, precision] = (info["iterations"], x12, S.bddc_info)
+    print("bumpy 64^3 iterations (dense / three-level):",
+          {k: v[0] for k, v in out.items()}, "level-2 subdomains", out["bddc", "fp64"][2]["level2_subdomains"],
+          "level-3 DOFs", out["bddc", "fp64"][2]["level3_coarse"])
+    ref = out["dense", "fp64"][1]
+    with _solver(p) as S:   # the energy norm through the library's operator
+        def energy(x):
+            e = x - ref
+            return float(np.sqrt(max(e @ S.apply(e), 0.0) / (ref @ S.apply(ref))))
+        assert energy(out["bddc", "fp64"][1]) <= 1e-8
+        assert energy(out["bddc", "mixed"][1]) <= 1e-6
+    assert out["bddc", "fp64"][0] >= out["dense", "fp64"][0]
+
+
+def test_elasticity_is_refused(ufe):
+    from tests.oracle_cache import elastic_problems
+    with pytest.raises(ufe.UfeError) as e:
+        _solver(elastic_problems()["el_sphere8"], coarse_solver="bddc")
+    assert e.value.status == ufe.ERR_UNSUPPORTED

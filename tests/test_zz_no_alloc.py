@@ -5,7 +5,8 @@ host code called back from a framework that owns the device allocator).
 
 Checked against ufe_bddc_apply, which uses the buffers allocated by
 ufe_bddc_setup, on two calls in a row (the second call reuses the array the first
-one left behind), with both coarse solvers; the free device memory is unchanged
+one left behind), with the three coarse solvers (dense, cyclic reduction, and the
+three-level method, whose level-2 work space set-up allocates); the free device memory is unchanged
 across calls made right after set-up; problems beyond the array's limits are
 refused.  This file is named to be collected last, so a run that stops at the
 first failure has run every other test first.
@@ -34,13 +35,13 @@ def _problem(inputs, name):
     return inputs.manufactured_sphere(0)
 
 
-@pytest.mark.parametrize("name,coarse_solver", [("sphere16", "dense"), ("tower", "cr")])
+@pytest.mark.parametrize("name,coarse_solver", [("sphere16", "dense"), ("tower", "cr"), ("tower", "bddc")])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_noalloc_matches_allocating_apply(precision, name, coarse_solver):
     torch, inputs, ufe, Solver = _env()
     dev = torch.device("cuda", 0)
     with Solver(_problem(inputs, name), precision=precision, coarse_solver=coarse_solver) as S:
-        want = ufe.COARSE_SOLVER_CR if coarse_solver == "cr" else ufe.COARSE_SOLVER_DENSE
+        want = {"dense": ufe.COARSE_SOLVER_DENSE, "cr": ufe.COARSE_SOLVER_CR, "bddc": ufe.COARSE_SOLVER_BDDC}[coarse_solver]
         assert S.bddc_info["coarse_solver"] == want
         rng = np.random.default_rng(17)
         for call in range(2):
@@ -55,7 +56,7 @@ def test_noalloc_matches_allocating_apply(precision, name, coarse_solver):
             assert err <= 1e-12, (call, err)
 
 
-@pytest.mark.parametrize("coarse_solver", ["dense", "cr"])
+@pytest.mark.parametrize("coarse_solver", ["dense", "cr", "bddc"])
 def test_noalloc_takes_no_device_memory(coarse_solver):
     """Right after set-up (no other apply or solve before it), two calls leave the
     free device memory exactly as it was: set-up already loaded the device code and
