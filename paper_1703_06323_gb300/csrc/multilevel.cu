@@ -20,11 +20,13 @@
 // the constrained Neumann operator K_2 = S'^-1 - Phi_2 X^T on the level-2 interface
 // (S' = S + C^T diag(rho) C, X = S'^-1 C^T, Phi_2 = X (C X)^-1) and Phi_2 itself.
 //
-// One application u_c = M_2 r_c (replacing u_c = A_c^-1 r_c) is five launches:
+// One application u_c = M_2 r_c (replacing u_c = A_c^-1 r_c) is four launches:
 //   L1  per J: r_c gathered from the subdomain parts; y = A_II^-1 r_I; t = A_GI y
 //   L2  per J: r~ = w (r_G - sum_J' t^J'); v = K_2 r~ (stored weighted); g = Phi_2^T r~
-//   L3  level 3: u_3 = A_3^-1 sum g (the first level's dense coarse kernel)
-//   L4  per J: vw += w Phi_2 u_3
+//   L34 per J: r_3 = sum g gathered whole; u_3 on J's level-3 DOFs (rows of A_3^-1);
+//       vw += w Phi_2 u_3  (a level-3 problem too large for one CTA's shared memory
+//       takes two launches instead: the first level's dense coarse kernel, then the
+//       prolongation)
 //   L5  per J: u_G = sum_J' vw^J'; z_I = y - A_II^-1 A_IG u_G; u_c = z
 #include <algorithm>
 #include <cmath>
@@ -161,6 +163,37 @@ __global__ void __launch_bounds__(256) k_ml_prolong(MlMeta M, const PcgScalars* 
   double* u = reinterpret_cast<double*>(smem);
   double* pu = u + ldC;
   for (int c = threadIdx.x; c < nC; c += blockDim.x) u[c] = M.u3[M.c_list[c0 + c]];
+  __syncthreads();
+  ml_rows(M.store + M.offP[J], ldC, 0, nG, 0, nC, u, pu);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nG; i += blockDim.x) M.vw2[base + nI + i] += M.w2[base + nI + i] * pu[i];
+}
+
+// L3 and L4 in one launch (level-3 problems whose r_3 fits shared memory): each J
+// gathers the whole r_3 (the parts of every level-3 DOF from the level-2 subdomains
+// holding it, in their order), forms u_3 on its own level-3 DOFs from those rows of
+// A_3^-1, and adds w Phi_2 u_3 to its interface rows
+__global__ void __launch_bounds__(256)
+k_ml_coarse3(MlMeta M, int n3, int ld3, const double* __restrict__ A3inv, const int32_t* __restrict__ cpos3,
+             const uint8_t* __restrict__ nn3, const PcgScalars* sc) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) char smem[];
+  const int J = blockIdx.x, base = M.dof_ptr[J], n = M.dof_ptr[J + 1] - base, nI = M.nI[J], nG = n - nI;
+  const int c0 = M.c_ptr[J], nC = M.c_ptr[J + 1] - c0, ldC = pad4(nC);
+  if (nG == 0 || nC == 0) return;
+  double* r3 = reinterpret_cast<double*>(smem);
+  double* u = r3 + ld3;
+  double* pu = u + ldC;
+  for (int q = threadIdx.x; q < n3; q += blockDim.x) r3[q] = ml_gather8(cpos3 + (int64_t)q * 8, nn3[q], M.g3);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = wid; c < nC; c += nw) {
+    const double* row = A3inv + (int64_t)M.c_list[c0 + c] * ld3;
+    double acc = 0.0;
+    for (int j = lane; j < n3; j += 32) acc += row[j] * r3[j];
+    acc = ml_warp_sum(acc);
+    if (lane == 0) u[c] = acc;
+  }
   __syncthreads();
   ml_rows(M.store + M.offP[J], ldC, 0, nG, 0, nC, u, pu);
   __syncthreads();
@@ -489,7 +522,10 @@ void scaled_inverse(const std::vector<InvDesc>& descs, double* store, StatusList
 
 }  // namespace
 
-void ml_prepare(int max_n, int max_nI, int max_nG, int max_nC);
+// level-3 problems up to this many bytes of r_3 (plus J's vectors) take the fused launch
+constexpr size_t kFusedCoarse3Smem = 160 * 1024;
+
+void ml_prepare(int max_n, int max_nI, int max_nG, int max_nC, int ld3);
 
 void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC, int group, cudaStream_t s) {
   MultiLevel& L = B.ml;
@@ -815,13 +851,20 @@ void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC,
   }
   L.bytes = bytes + 8.0 * n3 * (double)L.ld3;
   L.inv_flops = flops;
-  ml_prepare(L.max_n, L.max_nI, L.max_nG, L.max_nC);
+  ml_prepare(L.max_n, L.max_nI, L.max_nG, L.max_nC, L.ld3);
   if (n3 > 0) dense_coarse_prepare(n3, L.ld3);
   // the host tables the uploads above read go out of scope here
   UFE_CUDA(cudaStreamSynchronize(s));
 }
 
-void ml_prepare(int max_n, int max_nI, int max_nG, int max_nC) {
+void ml_prepare(int max_n, int max_nI, int max_nG, int max_nC, int ld3) {
+  const size_t s34 = (size_t)(ld3 + pad4(max_nC) + pad4(max_nG)) * 8;
+  if (s34 <= kFusedCoarse3Smem) {
+    if (s34 > 48 * 1024)
+      UFE_CUDA(cudaFuncSetAttribute(k_ml_coarse3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s34));
+    cudaFuncAttributes fa3;
+    UFE_CUDA(cudaFuncGetAttributes(&fa3, k_ml_coarse3));
+  }
   const size_t a = (size_t)(pad4(max_n) + pad4(max_nI)) * 8, b = (size_t)2 * pad4(max_nG) * 8,
                c = (size_t)(pad4(max_nG) + 2 * pad4(max_nI)) * 8, d = (size_t)(pad4(max_nC) + pad4(max_nG)) * 8;
   const size_t need = std::max(std::max(a, d), std::max(b, c));
@@ -849,7 +892,11 @@ void ml_coarse_solve(const Bddc& B, const double* gC, double* uc, const PcgScala
   UFE_CHECK_LAUNCH();
   k_ml_neumann<<<L.n2, 256, s2, s>>>(M, sc);
   UFE_CHECK_LAUNCH();
-  if (L.n3 > 0) {
+  const size_t s34 = (size_t)(L.ld3 + pad4(L.max_nC) + pad4(L.max_nG)) * 8;
+  if (L.n3 > 0 && s34 <= kFusedCoarse3Smem) {
+    k_ml_coarse3<<<L.n2, 256, s34, s>>>(M, L.n3, L.ld3, L.A3inv.p, L.cpos3.p, L.nn3.p, sc);
+    UFE_CHECK_LAUNCH();
+  } else if (L.n3 > 0) {
     dense_coarse_gemv(L.n3, L.ld3, L.A3inv.p, L.cpos3.p, L.nn3.p, L.g3.p, L.u3.p, sc, s);
     k_ml_prolong<<<L.n2, 256, (size_t)(pad4(L.max_nC) + pad4(L.max_nG)) * 8, s>>>(M, sc);
     UFE_CHECK_LAUNCH();
