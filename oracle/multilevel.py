@@ -61,7 +61,8 @@ def group_of_block(grid, b, G):
 class CoarseBDDC:
     """BDDC of the coarse problem of a two-level oracle BDDC (level 2 of the method)."""
 
-    def __init__(self, two, group=2, coarse="cef", weighting="stiffness", all_interface_corners=False):
+    def __init__(self, two, group=2, coarse="cef", weighting="stiffness", all_interface_corners=False,
+                 level1_corners=False):
         if two.ncomp != 1:
             raise ValueError("the three-level method is built for Poisson (one coarse DOF per object)")
         mesh = two.mesh
@@ -112,12 +113,19 @@ class CoarseBDDC:
             objs = [{"dofs": [int(k)], "neigh": self.neigh2[k], "kind": CORNER} for k in np.flatnonzero(gamma)]
         else:
             classes = {}
+            kind1 = [two.objs[o]["kind"] for o in two.coarse_obj]
             for k in np.flatnonzero(gamma):
-                classes.setdefault(self.neigh2[k], []).append(int(k))
+                if level1_corners and kind1[k] == CORNER:
+                    classes.setdefault(("corner", int(k)), []).append(int(k))
+                else:
+                    classes.setdefault(self.neigh2[k], []).append(int(k))
             objs = []
-            for ns, ks in classes.items():
+            for key, ks in classes.items():
+                ns = self.neigh2[ks[0]]
                 for comp in _components(sorted(ks), adjacent):
                     kind = FACE if len(ns) == 2 else (CORNER if len(comp) == 1 else EDGE)
+                    if key[0] == "corner":
+                        kind = CORNER
                     objs.append({"dofs": comp, "neigh": ns, "kind": kind})
             keep = {"c": (CORNER,), "ce": (CORNER, EDGE), "cef": (CORNER, EDGE, FACE)}[coarse]
             objs = [o for o in objs if o["kind"] in keep]

@@ -70,6 +70,16 @@ def test_full_box_objects_by_hand(box):
     assert all(len(o["neigh"]) == {CORNER: 8, EDGE: 4, FACE: 2}[o["kind"]] for o in L2.objs)
     assert CoarseBDDC(B, group=2, coarse="ce").n_coarse == 7
     assert CoarseBDDC(B, group=2, coarse="c").n_coarse == 1
+    # first-level corners kept as level-2 corners: the 3 x 3 block vertices of each mid
+    # plane, 3 x 9 - 3 x 3 + 1 = 19 distinct (the centre lines' 3 each lie on two planes,
+    # the centre on three): the centre, 6 on the half-lines, 12 quadrant centres.  The
+    # two first-level edges of a half-line were joined only through the corner between
+    # them, so each becomes a one-DOF corner (12 more); each quadrant keeps its 4 faces
+    # and 4 edges as one face of 8
+    L2c = CoarseBDDC(B, group=2, level1_corners=True)
+    got = sorted((o["kind"], len(o["dofs"]), len(o["neigh"])) for o in L2c.objs)
+    assert got == sorted([(CORNER, 1, 8)] + [(CORNER, 1, 4)] * 18 + [(CORNER, 1, 2)] * 12 + [(FACE, 8, 2)] * 12)
+    assert int(L2c.is_gamma.sum()) == 127
 
 
 def _rel(a, b):
@@ -90,9 +100,10 @@ def test_exact_level2_reproduces_two_level(case, request):
 
 
 @pytest.mark.parametrize("case,group", [("tiny", 1), ("tower", 1), ("tower", 2), ("box", 2)])
-def test_constraints_and_weights(case, group, request):
+@pytest.mark.parametrize("level1_corners", [False, True])
+def test_constraints_and_weights(case, group, level1_corners, request):
     m, S, B = request.getfixturevalue(case)
-    L2 = CoarseBDDC(B, group=group)
+    L2 = CoarseBDDC(B, group=group, level1_corners=level1_corners)
     assert L2.n_sub2 > 1 and L2.n_coarse > 0
     for L in L2.local:
         if L["cids"].size:
@@ -101,17 +112,21 @@ def test_constraints_and_weights(case, group, request):
 
 
 @pytest.mark.parametrize("case,group", [("sbox", 2), ("tower", 1), ("tower", 2)])
-def test_level2_spectrum(case, group, request):
+@pytest.mark.parametrize("level1_corners", [False, True])
+def test_level2_spectrum(case, group, level1_corners, request):
     """M_2 symmetric positive definite with lambda_min(M_2 A_c) >= 1 (and > 1 somewhere:
     these level-2 spaces are genuinely smaller than the assembled one)."""
     m, S, B = request.getfixturevalue(case)
-    L2 = CoarseBDDC(B, group=group)
+    L2 = CoarseBDDC(B, group=group, level1_corners=level1_corners)
     n = L2.n
     M2 = np.column_stack([L2.apply(e) for e in np.eye(n)])
     assert np.abs(M2 - M2.T).max() <= 1e-10 * np.abs(M2).max()
     ev = np.sort(np.linalg.eigvals(M2 @ B.Ac).real)
     assert ev[0] >= 1.0 - 1e-9
-    assert ev[-1] > 1.0 + 1e-3   # a genuinely inexact coarse solve
+    if any(len(o["dofs"]) > 1 for o in L2.objs):
+        assert ev[-1] > 1.0 + 1e-3   # means over several coarse DOFs: a genuinely inexact coarse solve
+    else:
+        assert ev[-1] <= 1.0 + 1e-9  # every level-2 object a single coarse DOF: M_2 = A_c^-1
 
 
 def test_three_level_dominates_two_level(sbox):
