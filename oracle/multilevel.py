@@ -18,7 +18,9 @@ one application of BDDC to that problem, built the way Sect. 3 builds the first 
   * level-2 objects: interface coarse DOFs with equal neigh_2, split into connected
     components under "held by a common subdomain"; FACE when |neigh_2| = 2, else
     CORNER for one coarse DOF and EDGE for more (the rule of Sect. 3.2); Lambda_O
-    by 'c' / 'ce' / 'cef';
+    by 'c' / 'ce' / 'cef'; with level1_corners, every coarse DOF of a first-level
+    corner is a level-2 corner of its own (the corner enrichment of Sect. 4.4 is
+    not averaged away one level up);
   * level-2 coarse DOFs: the uniform mean over each object (Eq. coarse-dofs);
   * weights: stiffness (Eq. alge-weighting on the diagonals of the level-2 Neumann
     matrices A_2^J = sum_{w in J} A_c^w) or topological (1 / |neigh_2|);
