@@ -369,7 +369,7 @@ def roofline_block(kt, n_steps, binfo, per_iter, iterations, fma, peaks, n_subte
     return out
 
 
-def adjoint_workload(U, dev, stream, flush, precision, reps=2, coarse_solver="auto"):
+def adjoint_workload(U, dev, stream, flush, precision, reps=2, coarse_solver="auto", keep_corners=False):
     """Config-5 style adjoint workload (128^3 background cells, 16^3 subdomains, sphere of
     radius 0.45, per-cell kappa = exp(GRF)): mesh, assembly, BDDC set-up, forward solve
     and adjoint solve with the per-cell gradient, timed by CUDA events; returns the mean
@@ -392,7 +392,7 @@ def adjoint_workload(U, dev, stream, flush, precision, reps=2, coarse_solver="au
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         with Solver(p, precision=precision, arrays=dict(arrays), stream=stream.cuda_stream,
-                    coarse_solver=coarse_solver) as S:
+                    coarse_solver=coarse_solver, coarse_keep_corners=keep_corners) as S:
             u = torch.zeros(S.n_dof, dtype=torch.float64, device=dev)
             _, fi = U.ufe_pcg_solve(S.system, S.bddc, None, u, rtol=RTOL, maxit=2000)
             dof = torch.from_numpy(U.ufe_mesh_get_dof_map(S.mesh)).to(dev).long()
@@ -519,7 +519,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def step(precision, host=False, coarse_solver=0):
+    def step(precision, host=False, coarse_solver=0, keep_corners=0):
         if host:
             phi, f = p.phi, p.f
         else:
@@ -531,7 +531,8 @@ def run_ours(args, rank, world):
             n = U.ufe_mesh_get_info(mesh)["n_dof"]
             sysh = U.ufe_assemble(mesh, None, f, None, None)
             bddc = U.ufe_bddc_setup(sysh, U.WEIGHT_STIFFNESS, U.OBJECTS_VARIANT1, U.COARSE_CEF,
-                                    U.PREC_MIXED if precision == "mixed" else U.PREC_FP64, coarse_solver)
+                                    U.PREC_MIXED if precision == "mixed" else U.PREC_FP64, coarse_solver, 0,
+                                    keep_corners)
             x = np.zeros(n) if host else torch.zeros(n, dtype=torch.float64, device=dev)
             _, info = U.ufe_pcg_solve(sysh, bddc, None, x, rtol=RTOL, maxit=1000)
             binfo = U.ufe_bddc_get_info(bddc)
@@ -613,8 +614,9 @@ def run_ours(args, rank, world):
         # the same workload with the three-level method (the coarse problem preconditioned
         # by BDDC over groups of 2^3 blocks instead of inverted)
         tl = {}
-        for prec in ("mixed", "fp64"):
-            step(prec, coarse_solver=U.COARSE_SOLVER_BDDC)
+        for prec, keep in (("mixed", 0), ("fp64", 0), ("mixed_keep_corners", 1)):
+            pr = prec.split("_")[0]
+            step(pr, coarse_solver=U.COARSE_SOLVER_BDDC, keep_corners=keep)
             ts = []
             for _ in range(5):
                 flush.fill_(1.0)
@@ -622,7 +624,7 @@ def run_ours(args, rank, world):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                _, tinfo, tb, _ = step(prec, coarse_solver=U.COARSE_SOLVER_BDDC)
+                _, tinfo, tb, _ = step(pr, coarse_solver=U.COARSE_SOLVER_BDDC, keep_corners=keep)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
@@ -634,6 +636,8 @@ def run_ours(args, rank, world):
         extra["adjoint_128^3"] = {prec: adjoint_workload(U, dev, stream, flush, prec) for prec in ("mixed", "fp64")}
         extra["adjoint_128^3"]["mixed_three_level"] = adjoint_workload(U, dev, stream, flush, "mixed",
                                                                        coarse_solver="bddc")
+        extra["adjoint_128^3"]["mixed_three_level_keep_corners"] = adjoint_workload(
+            U, dev, stream, flush, "mixed", coarse_solver="bddc", keep_corners=True)
         extra["batched_256"] = batched_workload(U, dev, stream, flush)
         extra["elastic_96^3"] = {prec: elastic_workload(U, dev, stream, flush, prec) for prec in ("mixed", "fp64")}
 

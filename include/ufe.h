@@ -293,6 +293,9 @@ typedef struct {
                               BDDC preconditions it one level up) */
   int32_t coarse_group;    /* UFE_COARSE_SOLVER_BDDC: blocks per level-2 subdomain edge (0: 2); read
                               only with that solver */
+  int32_t coarse_keep_corners;   /* UFE_COARSE_SOLVER_BDDC: 1 keeps every coarse DOF of a first-level
+                                    corner (Sect. 3.2, 4.4) as a level-2 corner instead of merging it
+                                    into the level-2 edge or face means; read only with that solver */
 } ufe_bddc_opts;
 
 typedef struct {

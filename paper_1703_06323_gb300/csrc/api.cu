@@ -520,6 +520,7 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     B->mixed = opts->precision == UFE_PREC_MIXED;
     B->coarse_solver = opts->coarse_solver;
     if (opts->coarse_solver == UFE_COARSE_SOLVER_BDDC && opts->coarse_group > 0) B->coarse_group = opts->coarse_group;
+    B->coarse_keep_corners = opts->coarse_solver == UFE_COARSE_SOLVER_BDDC && opts->coarse_keep_corners != 0;
     UFE_CUDA(cudaGetDevice(&B->device));
     bddc_build(*B);
     tune_preconditioner(*B);

@@ -149,6 +149,7 @@ struct Bddc {
   DBuf<double> gi_v, ig_v;
   int coarse_solver = 0;        // requested UFE_COARSE_SOLVER_*
   int coarse_group = 2;         // three-level method: blocks per level-2 subdomain edge
+  bool coarse_keep_corners = false;   // three-level method: first-level corners stay level-2 corners
   bool coarse_dense = true;     // resolved: explicit inverse (else cyclic reduction)
   DBuf<double> Ac_inv;          // dense: n_coarse x ldc, FP64
   int ldc = 0;

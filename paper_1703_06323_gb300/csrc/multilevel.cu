@@ -590,9 +590,22 @@ void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC,
   };
   std::vector<Obj> objs;
   {
+    // with coarse_keep_corners, a coarse DOF of a first-level corner is a level-2 corner
+    std::vector<int32_t> kind1;
+    if (B.coarse_keep_corners) {
+      const std::vector<int32_t> cobj = to_host(B.coarse_obj.p, nc, s);
+      const std::vector<int32_t> okind = to_host(B.obj_kind.p, B.n_obj, s);
+      kind1.resize(nc);
+      for (int64_t k = 0; k < nc; ++k) kind1[k] = okind[cobj[k]];
+    }
     std::map<std::vector<int>, std::vector<int>> classes;
     for (int64_t k = 0; k < nc; ++k)
-      if (neigh2[k].size() >= 2) classes[neigh2[k]].push_back((int)k);
+      if (neigh2[k].size() >= 2) {
+        if (!kind1.empty() && kind1[k] == UFE_OBJ_CORNER)
+          objs.push_back(Obj{{(int)k}, neigh2[k], UFE_OBJ_CORNER});
+        else
+          classes[neigh2[k]].push_back((int)k);
+      }
     std::vector<int> cls(nc, -1), seen(nc, 0);
     int ci = 0;
     for (auto& kv : classes) {

@@ -21,7 +21,7 @@ class Solver:
     """Owns the ufe handles of one problem (host numpy inputs or torch CUDA tensors)."""
 
     def __init__(self, problem, weighting="stiffness", objects="v1", coarse="cef", precision="fp64", stream=None,
-                 arrays=None, coarse_solver="auto", coarse_group=0):
+                 arrays=None, coarse_solver="auto", coarse_group=0, coarse_keep_corners=False):
         p = problem
         a = arrays or {}
         self.mesh = ufe.ufe_mesh_create(p.box_lo, p.box_hi, p.cells, p.sub_cells, a.get("phi", p.phi),
@@ -40,7 +40,8 @@ class Solver:
                 self.system = ufe.ufe_assemble(self.mesh, a.get("kappa", p.kappa), a.get("f", p.f),
                                                a.get("q", p.q), a.get("g", p.dirichlet_values))
             self.bddc = ufe.ufe_bddc_setup(self.system, WEIGHTING[weighting], OBJECTS[objects], COARSE[coarse],
-                                           PRECISION[precision], COARSE_SOLVER[coarse_solver], coarse_group)
+                                           PRECISION[precision], COARSE_SOLVER[coarse_solver], coarse_group,
+                                           int(bool(coarse_keep_corners)))
             self.bddc_info = ufe.ufe_bddc_get_info(self.bddc)
         except Exception:
             self.close()

@@ -45,7 +45,8 @@ class MeshInfo(ctypes.Structure):
 
 class BddcOpts(ctypes.Structure):
     _fields_ = [("weighting", ctypes.c_int32), ("objects", ctypes.c_int32), ("coarse", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("coarse_solver", ctypes.c_int32), ("coarse_group", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("coarse_solver", ctypes.c_int32), ("coarse_group", ctypes.c_int32),
+                ("coarse_keep_corners", ctypes.c_int32)]
 
 
 class BddcInfo(ctypes.Structure):
@@ -333,8 +334,8 @@ def ufe_system_destroy(system):
 
 
 def ufe_bddc_setup(system, weighting=WEIGHT_STIFFNESS, objects=OBJECTS_VARIANT1, coarse=COARSE_CEF,
-                   precision=PREC_FP64, coarse_solver=0, coarse_group=0):
-    opts = BddcOpts(weighting, objects, coarse, precision, coarse_solver, coarse_group)
+                   precision=PREC_FP64, coarse_solver=0, coarse_group=0, coarse_keep_corners=0):
+    opts = BddcOpts(weighting, objects, coarse, precision, coarse_solver, coarse_group, coarse_keep_corners)
     out = ctypes.c_void_p()
     _check(LIB.ufe_bddc_setup(system, ctypes.byref(opts), ctypes.byref(out)))
     return out

@@ -38,18 +38,19 @@ def _run(name):
 CASES = [("ml_box", 2), ("tower", 1), ("tower", 2), ("sphere_ragged", 2), ("ni_sphere", 2), ("sphere16", 1)]
 
 
-def _three(orc, group):
+def _three(orc, group, keep=False):
     from oracle.multilevel import ThreeLevelBDDC
-    return ThreeLevelBDDC(orc.bddc(), group=group)
+    return ThreeLevelBDDC(orc.bddc(), group=group, level1_corners=keep)
 
 
 @pytest.mark.parametrize("name,group", CASES)
-def test_partition_and_preconditioner_fp64(ufe, name, group):
+@pytest.mark.parametrize("keep", [False, True])
+def test_partition_and_preconditioner_fp64(ufe, name, group, keep):
     orc = _run(name)
-    T = _three(orc, group)
+    T = _three(orc, group, keep)
     r = np.random.default_rng(21).normal(size=orc.mesh.n_dof)
     ref = T.apply(r)
-    with _solver(orc.p, coarse_solver="bddc", coarse_group=group) as S:
+    with _solver(orc.p, coarse_solver="bddc", coarse_group=group, coarse_keep_corners=keep) as S:
         bi = S.bddc_info
         assert bi["coarse_solver"] == ufe.COARSE_SOLVER_BDDC
         assert bi["level2_subdomains"] == T.level2.n_sub2
@@ -68,15 +69,17 @@ def test_preconditioner_mixed(ufe, name, group):
     assert energy_error(orc.sys.A, z, ref) <= 1e-3
 
 
-@pytest.mark.parametrize("name,group", CASES)
+@pytest.mark.parametrize("name,group,keep", [c + (False,) for c in CASES] + [("tower", 2, True),
+                                                                              ("ni_sphere", 2, True)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_solution(ufe, name, group, precision):
+def test_solution(ufe, name, group, keep, precision):
     from oracle.pcg import pcg
     orc = _run(name)
-    T = _three(orc, group)
+    T = _three(orc, group, keep)
     ref8 = pcg(orc.sys.apply, orc.sys.b, T.apply, rtol=1e-8, maxit=2000)
     ref = orc.solve(rtol=1e-12)
-    with _solver(orc.p, precision=precision, coarse_solver="bddc", coarse_group=group) as S:
+    with _solver(orc.p, precision=precision, coarse_solver="bddc", coarse_group=group,
+                 coarse_keep_corners=keep) as S:
         x, info = S.solve(rtol=1e-8)
         assert info["converged"] == 1 and info["true_rel_residual"] <= 1.5e-8
         if precision == "fp64":
@@ -112,23 +115,23 @@ def test_bench_workload_three_level(ufe):
     from paper_1703_06323_gb300 import inputs
     p = inputs.bumpy_sphere(0)
     out = {}
-    for cs in ("dense", "bddc"):
+    for cs, keep in (("dense", False), ("bddc", False), ("bddc", True)):
         for precision in ("fp64", "mixed"):
-            with _solver(p, precision=precision, coarse_solver=cs) as S:
+            with _solver(p, precision=precision, coarse_solver=cs, coarse_keep_corners=keep) as S:
                 x, info = S.solve(rtol=1e-8)
                 assert info["converged"] == 1 and info["true_rel_residual"] <= 1.5e-8
                 x12, _ = S.solve(rtol=1e-12, maxit=3000)
-                out[cs, precision] = (info["iterations"], x12, S.bddc_info)
-    print("bumpy 64^3 iterations (dense / three-level):",
-          {k: v[0] for k, v in out.items()}, "level-2 subdomains", out["bddc", "fp64"][2]["level2_subdomains"],
-          "level-3 DOFs", out["bddc", "fp64"][2]["level3_coarse"])
+                out[cs + ("+corners" if keep else ""), precision] = (info["iterations"], x12, S.bddc_info)
+    print("bumpy 64^3 iterations:", {k: v[0] for k, v in out.items()},
+          "level-3 DOFs", out["bddc", "fp64"][2]["level3_coarse"], out["bddc+corners", "fp64"][2]["level3_coarse"])
     ref = out["dense", "fp64"][1]
     with _solver(p) as S:   # the energy norm through the library's operator
         def energy(x):
             e = x - ref
             return float(np.sqrt(max(e @ S.apply(e), 0.0) / (ref @ S.apply(ref))))
-        assert energy(out["bddc", "fp64"][1]) <= 1e-8
-        assert energy(out["bddc", "mixed"][1]) <= 1e-6
+        for m in ("bddc", "bddc+corners"):
+            assert energy(out[m, "fp64"][1]) <= 1e-8
+            assert energy(out[m, "mixed"][1]) <= 1e-6
     assert out["bddc", "fp64"][0] >= out["dense", "fp64"][0]
 
 
