@@ -324,8 +324,9 @@ typedef struct {
   int32_t prec_cluster, prec_stages;   /* launch shape of the per-iteration preconditioner kernels: CTAs per
                                           subdomain cluster and row-stream stages per CTA (0: from the
                                           shared-memory budget), chosen by timing the candidates once per
-                                          size class and process (Poisson; UFE_AUTOTUNE=0 keeps 4 and 0;
-                                          UFE_PREC_SHAPE="cl,stages" fixes them) */
+                                          size class and process (Poisson, 128 subdomains or more; otherwise
+                                          and with UFE_AUTOTUNE=0: 4 and 0; UFE_PREC_SHAPE="cl,stages" fixes
+                                          them) */
   int32_t fp64_subdomains;   /* mixed precision requested: subdomains whose local operators are FP64 --
                                 those whose Jacobi-scaled A_II or S' had an FP32 pivot below 1e-3 (or
                                 not positive), or whose FP32 coarse basis missed C Phi = I by more

@@ -1287,8 +1287,13 @@ static void precondition(Bddc& B, const double* r, double* z, PcgScalars* sc, in
 // on the preconditioner's own work vectors, in five interleaved rounds, keeping each
 // candidate's fastest) and caches the fastest for the process; later set-ups of the
 // class reuse it.
-// UFE_AUTOTUNE=0 keeps the default shape (4 CTAs, stages from the shared-memory budget).
+// UFE_AUTOTUNE=0 keeps the default shape (4 CTAs, stages from the shared-memory budget),
+// and so do problems of fewer than kTuneMinSubdomains subdomains: their stages are
+// short, and a set of many small problems of different sizes (one solve each) would
+// spend more time tuning its size classes than the shape can save.
 // ---------------------------------------------------------------------------
+constexpr int64_t kTuneMinSubdomains = 128;
+
 static bool autotune_enabled() {
   const char* e = getenv("UFE_AUTOTUNE");
   return !(e && std::string(e) == "0");
@@ -1306,7 +1311,7 @@ void tune_preconditioner(Bddc& B) {
     }
     return;
   }
-  if (!autotune_enabled()) return;
+  if (!autotune_enabled() || B.mesh->n_sub < kTuneMinSubdomains) return;
   static std::mutex mu;
   static std::map<std::array<int, 6>, std::pair<int, int>> cache;
   int dev = 0;
