@@ -813,6 +813,20 @@ k_prec_interior1(SubMeta sm, const TM* __restrict__ AIIinv, const double* __rest
   }
 }
 
+// one term of a compensated FP32 dot product (Ogita, Rump, Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26 (2005), Dot2): a + e accumulates p (x + l);
+// the rounded intrinsics keep the compiler from fusing the product into the sum
+__device__ __forceinline__ void dot2_step(float& a, float& e, float p, float x, float l) {
+  const float prod = __fmul_rn(p, x);
+  const float perr = fmaf(p, x, -prod);
+  const float s = __fadd_rn(a, prod);
+  const float bp = __fsub_rn(s, a);
+  const float serr = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(prod, bp));
+  a = s;
+  e = fmaf(p, l, e + serr + perr);
+}
+__device__ __forceinline__ void dot2_step(double&, double&, double, double, double) {}
+
 // K4: r~ = w (r_G - sum t_G); v = K r~ (stored weighted: vw = w v); g = Phi^T r~
 template <typename TM, int NC, int CL = kCL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kSubThreads)
@@ -835,32 +849,48 @@ k_prec_neumann(SubMeta sm, const TM* __restrict__ Kop, const TM* __restrict__ Ph
   RowStream<TM> rs;
   rs.begin(Kop + sm.off_GG[w], r0, r1, z.ldG, S.stage, full, rpart, L);
   TM* xG = reinterpret_cast<TM*>(S.xT);
+  // FP32 operators: the part of r~ below FP32 precision, kept in dG's storage until
+  // the rows of K overwrite it (after the coarse restriction below has read it)
+  float* xlo = reinterpret_cast<float*>(S.dG);
   const int g0 = sm.vG_ptr[w];
   for (int j = threadIdx.x; j < z.ldG; j += blockDim.x) {
     TM v = TM(0);
+    double t = 0.0;
     if (j < z.nG) {
       const int32_t xi = sm.G_list[sm.G_ptr[w] + j / NC];
       const int c = j % NC;
       const double s = gather_slots<NC>(sm.gpos, xi, sm.n_neigh[xi], c, tG, r[(int64_t)NC * xi + c], -1.0);
-      v = (TM)(sm.sG[g0 + j] * sm.w[g0 + j] * s);
+      t = sm.sG[g0 + j] * sm.w[g0 + j] * s;
+      v = (TM)t;
     }
     xG[j] = v;
+    if constexpr (sizeof(TM) == 4) xlo[j] = (float)(t - (double)v);
   }
   __syncthreads();
   // partial g = Phi^T r~ over this CTA's rows (while the first rows of K are in
-  // flight): warps split the rows, lanes the columns
+  // flight): warps split the rows, lanes the columns.  With FP32 operators the sums
+  // are compensated (Ogita, Rump and Oishi's Dot2: the exact error of every product
+  // by FMA, of every addition by Knuth's TwoSum, plus Phi times the low part of r~):
+  // coarse residual parts cancel heavily next to tiny cut cells, where a plain FP32
+  // sum depends on how the rows are split over CTAs
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const TM* P = Phi + sm.off_GC[w];
   for (int c0 = 0; c0 < z.nC; c0 += 64) {
-    TM a0 = TM(0), a1 = TM(0);   // in the operator's precision (FP64 adds are scarce)
+    TM a0 = TM(0), a1 = TM(0), e0 = TM(0), e1 = TM(0);
 #pragma unroll 4
     for (int j = r0 + wid; j < r1; j += nw) {
       const TM xj = xG[j];
-      if (c0 + lane < z.nC) a0 += P[(int64_t)j * z.ldC + c0 + lane] * xj;
-      if (c0 + lane + 32 < z.nC) a1 += P[(int64_t)j * z.ldC + c0 + lane + 32] * xj;
+      if constexpr (sizeof(TM) == 4) {
+        const float lj = xlo[j];
+        if (c0 + lane < z.nC) dot2_step(a0, e0, P[(int64_t)j * z.ldC + c0 + lane], xj, lj);
+        if (c0 + lane + 32 < z.nC) dot2_step(a1, e1, P[(int64_t)j * z.ldC + c0 + lane + 32], xj, lj);
+      } else {
+        if (c0 + lane < z.nC) a0 += P[(int64_t)j * z.ldC + c0 + lane] * xj;
+        if (c0 + lane + 32 < z.nC) a1 += P[(int64_t)j * z.ldC + c0 + lane + 32] * xj;
+      }
     }
-    gpart[wid][lane] = (double)a0;
-    gpart[wid][lane + 32] = (double)a1;
+    gpart[wid][lane] = (double)a0 + (double)e0;
+    gpart[wid][lane + 32] = (double)a1 + (double)e1;
     __syncthreads();
     if (threadIdx.x < 64 && c0 + (int)threadIdx.x < z.nC) {
       double sacc = 0.0;
