@@ -1436,6 +1436,26 @@ void bddc_build(Bddc& B) {
     B.inv_flops_coarse = B.cr.inv_flops;
     ph_co.end(s);
   };
+  // ---- solver work space (before the coarse set-up: the solve graph can then be
+  // recorded while the GPU inverts the coarse matrix)
+  B.tG.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
+  B.vw.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
+  B.gC.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
+  B.uc.alloc(std::max<int64_t>(nco, 1), s);
+  for (DBuf<double>* v : {&B.x, &B.r, &B.b, &B.z, &B.q, &B.p0, &B.p1}) {
+    v->alloc(NC * nd, s);
+    v->zero();
+  }
+  // per-CTA partial sums (the preconditioner runs up to eight CTAs per subdomain)
+  B.part_blocks = std::max<int64_t>(std::max<int64_t>(grid_for(NC * nd, 256), B.sys->mesh->n_apply_tiles),
+                                    16 * (int64_t)ns) + 8;
+  B.part.alloc(B.part_blocks * 2, s);
+  B.sc.alloc(1, s);
+  B.sc.zero();
+  B.tres.alloc(2, s);
+  B.tres.zero();
+  if (!B.h_sc) UFE_CUDA(cudaMallocHost((void**)&B.h_sc, sizeof(PcgScalars)));
+
   bool coarse_done = false;
   if (B.mixed) {
     // FP32 local operators where they are accurate enough; a subdomain whose FP32 pivots
@@ -1452,6 +1472,9 @@ void bddc_build(Bddc& B) {
       ph_fac.end(s);
       do_coarse();
       coarse_done = true;
+      // the solve graph for the all-FP32 outcome, recorded while the GPU works (the
+      // host is free); dropped below if a subdomain fails the tests
+      solve_graph_early(B);
       UFE_CUDA(cudaStreamWaitEvent(s, later.done, 0));
       const std::vector<double> he = to_host(later.err.p, ns, s);
       const std::vector<int> st = to_host(status.p, ns, s);
@@ -1466,7 +1489,10 @@ void bddc_build(Bddc& B) {
     }
     std::vector<int> sub64, sub32;
     for (int w = 0; w < ns; ++w) (bad[w] ? sub64 : sub32).push_back(w);
-    if (!sub64.empty()) coarse_done = false;   // A_c^w of those subdomains changes
+    if (!sub64.empty()) {
+      coarse_done = false;   // A_c^w of those subdomains changes
+      solve_graph_reset(B);  // and so do the operators and the launch groups
+    }
     if (sub32.empty()) {
       // no subdomain keeps FP32: the problem is factored and applied in FP64 throughout
       B.local_tc = 0;
@@ -1502,25 +1528,10 @@ void bddc_build(Bddc& B) {
     ph_fac.end(s);
     do_coarse();
   }
-
-  // ---- solver work space
-  B.tG.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
-  B.vw.alloc(std::max<int64_t>(B.n_vGloc, 1), s);
-  B.gC.alloc(std::max<int64_t>(B.n_Cloc, 1), s);
-  B.uc.alloc(std::max<int64_t>(nco, 1), s);
-  for (DBuf<double>* v : {&B.x, &B.r, &B.b, &B.z, &B.q, &B.p0, &B.p1}) {
-    v->alloc(NC * nd, s);
-    v->zero();
-  }
-  // per-CTA partial sums (the preconditioner runs up to eight CTAs per subdomain)
-  B.part_blocks = std::max<int64_t>(std::max<int64_t>(grid_for(NC * nd, 256), B.sys->mesh->n_apply_tiles),
-                                    16 * (int64_t)ns) + 8;
-  B.part.alloc(B.part_blocks * 2, s);
-  B.sc.alloc(1, s);
-  B.sc.zero();
-  B.tres.alloc(2, s);
-  B.tres.zero();
-  if (!B.h_sc) UFE_CUDA(cudaMallocHost((void**)&B.h_sc, sizeof(PcgScalars)));
+  // the solve graph is recorded while the GPU finishes the set-up (the host is free),
+  // then the coarse inversion's pivots are read
+  solve_graph_early(B);
+  coarse_check(B);
 
   UFE_CUDA(cudaEventRecord(e1, s));
   UFE_CUDA(cudaEventSynchronize(e1));

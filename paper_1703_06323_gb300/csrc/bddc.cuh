@@ -155,6 +155,7 @@ struct Bddc {
   int ldc = 0;
   CoarseCR cr;                  // cyclic reduction over the z layers of subdomain blocks
   MultiLevel ml;                // three-level method (coarse_solver UFE_COARSE_SOLVER_BDDC)
+  DBuf<int> coarse_status;      // dense coarse inversion in flight: its pivot flags (coarse_check reads them)
 
   // solver work space
   DBuf<double> tG, vw, gC, uc;
@@ -193,6 +194,13 @@ void bddc_build(Bddc& B);
 // dense solver takes ownership of the buffer), and u_c = A_c^-1 r_c with r_c gathered
 // from the subdomain parts gC (work: 2 n_coarse doubles)
 void coarse_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s);
+// SINGULAR_COARSE if the dense coarse inversion queued by coarse_setup met a bad pivot
+void coarse_check(Bddc& B);
+// records the solve graph during the set-up when the launch shape is already known
+// (fixed, cached for the size class, or not tuned); returns whether it did
+bool solve_graph_early(Bddc& B);
+// drops a solve graph recorded for operators that the set-up then replaced
+void solve_graph_reset(Bddc& B);
 void coarse_solve(const Bddc& B, const double* gC, double* uc, double* work, const PcgScalars* sc, cudaStream_t s);
 // u = A^-1 r with r gathered from up to eight parts per row (parts[cpos[8 l + k]], k < cnn[l])
 // checks that r of n values fits one CTA's shared memory and raises the kernel's limit

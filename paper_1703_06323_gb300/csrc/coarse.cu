@@ -309,9 +309,9 @@ void dense_coarse_prepare(int64_t n, int ld) {
 static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
   const int64_t n = B.n_coarse;
   dense_coarse_prepare(n, ldc);
-  DBuf<int> st;
-  st.alloc(1, s);
-  st.zero();
+  // the status is read by coarse_check, so that the host is free while the inversion runs
+  B.coarse_status.alloc(1, s);
+  B.coarse_status.zero();
   // the coarse numbering follows the grid (objects in DOF order), so A_c is banded
   // and the inversion skips the blocks outside its envelope
   DBuf<int32_t> first;
@@ -321,8 +321,7 @@ static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
   std::vector<int32_t> first_h((size_t)n);
   UFE_CUDA(cudaMemcpyAsync(first_h.data(), first.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   UFE_CUDA(cudaStreamSynchronize(s));
-  large_inverse<double>(Ac.p, (int)n, ldc, st.p, s, &first_h);
-  UFE_REQUIRE(scalar_to_host(st.p, s) == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
+  large_inverse<double>(Ac.p, (int)n, ldc, B.coarse_status.p, s, &first_h);
   B.Ac_inv.p = Ac.p;   // take the buffer over
   B.Ac_inv.n = Ac.n;
   B.Ac_inv.s = Ac.s;
@@ -331,6 +330,13 @@ static void dense_setup(Bddc& B, DBuf<double>& Ac, int ldc, cudaStream_t s) {
   B.ldc = ldc;
   B.cr.bytes = 8.0 * (double)n * ldc;
   B.cr.inv_flops = std::pow((double)n, 3);
+}
+
+void coarse_check(Bddc& B) {
+  if (!B.coarse_status.n) return;
+  const int st = scalar_to_host(B.coarse_status.p, B.stream);
+  B.coarse_status.release();
+  UFE_REQUIRE(st == 0, UFE_ERR_SINGULAR_COARSE, "coarse matrix is not positive definite");
 }
 
 void coarse_setup(Bddc& B, DBuf<double>& Acb, int ldc, cudaStream_t s) {

@@ -1329,36 +1329,44 @@ static bool autotune_enabled() {
   return !(e && std::string(e) == "0");
 }
 
-void tune_preconditioner(Bddc& B) {
+static std::mutex g_tune_mu;
+static std::map<std::array<int, 6>, std::pair<int, int>> g_tune_cache;   // size class -> (CTAs, stages)
+
+static std::array<int, 6> tune_key(const Bddc& B) {
+  int dev = 0;
+  UFE_CUDA(cudaGetDevice(&dev));
+  int nsb = 0;
+  while ((1ll << nsb) < B.mesh->n_sub) ++nsb;
+  return {dev, B.mixed ? 1 : 0, (B.max_nIv + 31) / 32, (B.max_nGv + 31) / 32, nsb, B.n_coarse > 0 ? 1 : 0};
+}
+
+// the launch shape where no timing is needed (fixed by the environment, untuned, or
+// cached for the size class): sets it and returns true; false when it must be tuned
+static bool known_shape(Bddc& B) {
   B.prec_cl = kCL;
   B.prec_stages = 0;
-  if (B.ncomp != 1 || B.mesh->n_sub == 0) return;
+  if (B.ncomp != 1 || B.mesh->n_sub == 0) return true;
   if (const char* f = getenv("UFE_PREC_SHAPE")) {   // "cl,stages": a fixed shape (tests of every variant)
     int cl = kCL, st = 0;
     if (sscanf(f, "%d,%d", &cl, &st) == 2 && (cl == 2 || cl == 4 || cl == 8) && st >= 0 && st <= kMaxStages) {
       B.prec_cl = cl;
       B.prec_stages = st;
     }
-    return;
+    return true;
   }
-  if (!autotune_enabled() || B.mesh->n_sub < kTuneMinSubdomains) return;
-  static std::mutex mu;
-  static std::map<std::array<int, 6>, std::pair<int, int>> cache;
-  int dev = 0;
-  UFE_CUDA(cudaGetDevice(&dev));
-  int nsb = 0;
-  while ((1ll << nsb) < B.mesh->n_sub) ++nsb;
-  const std::array<int, 6> key = {dev, B.mixed ? 1 : 0, (B.max_nIv + 31) / 32, (B.max_nGv + 31) / 32, nsb,
-                                  B.n_coarse > 0 ? 1 : 0};
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) {
-      B.prec_cl = it->second.first;
-      B.prec_stages = it->second.second;
-      return;
-    }
-  }
+  if (!autotune_enabled() || B.mesh->n_sub < kTuneMinSubdomains) return true;
+  const std::array<int, 6> key = tune_key(B);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune_cache.find(key);
+  if (it == g_tune_cache.end()) return false;
+  B.prec_cl = it->second.first;
+  B.prec_stages = it->second.second;
+  return true;
+}
+
+void tune_preconditioner(Bddc& B) {
+  if (known_shape(B)) return;
+  const std::array<int, 6> key = tune_key(B);
   set_smem_limits(B);
   cudaStream_t s = B.stream;
   UFE_CUDA(cudaMemsetAsync(B.r.p, 0, (size_t)B.mesh->n_dof * 8, s));
@@ -1410,8 +1418,8 @@ void tune_preconditioner(Bddc& B) {
   check_device_status(B);
   B.prec_cl = pick.first;
   B.prec_stages = pick.second;
-  std::lock_guard<std::mutex> lock(mu);
-  cache[key] = pick;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = pick;
 }
 
 void bddc_apply(Bddc& B, const double* r_dev, double* z_dev) {
@@ -1510,6 +1518,19 @@ static void build_solve_graph(Bddc& B) {
   const cudaError_t e = cudaGraphInstantiate(&B.solve_exec, gr, 0);
   cudaGraphDestroy(gr);
   UFE_CUDA(e);
+}
+
+bool solve_graph_early(Bddc& B) {
+  if (B.solve_exec) return true;
+  if (!known_shape(B)) return false;
+  set_smem_limits(B);
+  build_solve_graph(B);
+  return true;
+}
+
+void solve_graph_reset(Bddc& B) {
+  if (B.solve_exec) cudaGraphExecDestroy(B.solve_exec);
+  B.solve_exec = nullptr;
 }
 
 // stage the inputs and launch the solve graph on stream s
