@@ -540,8 +540,6 @@ void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC,
   const std::vector<int32_t> Cp = to_host(B.C_ptr.p, ns + 1, s);
   const std::vector<int32_t> Cl = to_host(B.C_list.p, Cp[ns], s);
   const std::vector<int32_t> blk = to_host(m.sub_block.p, ns, s);
-  const std::vector<int32_t> cpos = to_host(B.cpos.p, nc * 8, s);
-  const std::vector<uint8_t> cnn = to_host(B.coarse_nn.p, nc, s);
   std::vector<std::vector<int>> holders(nc);
   for (int w = 0; w < ns; ++w)
     for (int c = Cp[w]; c < Cp[w + 1]; ++c) holders[Cl[c]].push_back(w);
