@@ -514,7 +514,9 @@ void scaled_inverse(const std::vector<InvDesc>& descs, double* store, StatusList
   int* st = sl.next(d.size(), s);
   k_ml_jacobi<<<(unsigned)d.size(), 256, 0, s>>>(dd.p, ds.p, sv.p, store, 0, st);
   UFE_CHECK_LAUNCH();
-  batched_inverse<double>(d, store, st, s);
+  // unit diagonals after the scaling: a pivot at rounding level means a singular block
+  // (a level-2 subdomain that floats without a level-2 coarse DOF)
+  batched_inverse<double>(d, store, st, s, 1e-15);
   k_ml_jacobi<<<(unsigned)d.size(), 256, 0, s>>>(dd.p, ds.p, sv.p, store, 1, st);
   UFE_CHECK_LAUNCH();
   // the buffers above are released stream-ordered, after the kernels that read them

@@ -140,3 +140,34 @@ def test_elasticity_is_refused(ufe):
     with pytest.raises(ufe.UfeError) as e:
         _solver(elastic_problems()["el_sphere8"], coarse_solver="bddc")
     assert e.value.status == ufe.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("name,weighting,coarse", [("tower", "topological", "cef"), ("ml_box", "stiffness", "ce")])
+def test_weighting_and_coarse_variants(ufe, name, weighting, coarse):
+    """Both levels follow the weighting (Eq. weighting or Eq. alge-weighting) and the
+    corners / edges / faces choice of the options: M_3 r against the oracle's
+    three-level method built with the same choices (the tower's level-2 interfaces
+    are faces only, so 'ce' is taken on the box, whose level 2 has edges and a corner)."""
+    from oracle.multilevel import ThreeLevelBDDC
+    orc = _run(name)
+    T = ThreeLevelBDDC(orc.bddc(weighting=weighting, coarse=coarse), group=2, weighting=weighting, coarse=coarse)
+    r = np.random.default_rng(24).normal(size=orc.mesh.n_dof)
+    ref = T.apply(r)
+    with _solver(orc.p, weighting=weighting, coarse=coarse, coarse_solver="bddc", coarse_group=2) as S:
+        assert S.bddc_info["level3_coarse"] == T.level2.n_coarse
+        z = S.precondition(r)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-9
+
+
+def test_floating_level2_subdomain_without_coarse_dof_is_refused(ufe):
+    """The tower's level-2 interfaces are faces only; with 'ce' they carry no level-2
+    coarse DOF, its floating groups have singular level-2 Neumann problems (the oracle
+    refuses them as SingularLocal), and the set-up reports SINGULAR_COARSE."""
+    from oracle.bddc import SingularLocal
+    from oracle.multilevel import ThreeLevelBDDC
+    orc = _run("tower")
+    with pytest.raises(SingularLocal):
+        ThreeLevelBDDC(orc.bddc(coarse="ce"), group=2, coarse="ce")
+    with pytest.raises(ufe.UfeError) as e:
+        _solver(orc.p, coarse="ce", coarse_solver="bddc", coarse_group=2)
+    assert e.value.status == ufe.ERR_SINGULAR_COARSE
