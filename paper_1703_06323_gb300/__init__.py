@@ -8,6 +8,7 @@ background mesh whose cell blocks are the subdomains.
   * ``paper_1703_06323_gb300.ufe``       -- ctypes binding of the C ABI (include/ufe.h);
   * ``paper_1703_06323_gb300.solver``    -- a small Python convenience layer over it;
   * ``paper_1703_06323_gb300.inputs``    -- seeded synthetic problems;
+  * ``paper_1703_06323_gb300.autograd``  -- torch.autograd wrapper of the adjoint gradient;
   * ``paper_1703_06323_gb300.build_ext`` -- builds libufe.so in-tree for sm_103a.
 
 The binding is imported lazily so that the input generators work without the
@@ -16,7 +17,7 @@ missing.
 """
 import importlib
 
-__all__ = ["ufe", "solver", "inputs", "build_ext"]
+__all__ = ["ufe", "solver", "inputs", "build_ext", "autograd"]
 
 
 def __getattr__(name):
