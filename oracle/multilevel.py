@@ -26,9 +26,13 @@ one application of BDDC to that problem, built the way Sect. 3 builds the first 
     matrices A_2^J = sum_{w in J} A_c^w) or topological (1 / |neigh_2|);
   * level-3 problem: A_3 = sum_J R_3J^T Phi_2^JT A_2^J Phi_2^J R_3J, solved exactly.
 
-Poisson only (one coarse DOF per first-level object).  With M_2 the level-2 BDDC
-preconditioner of A_c (Eq. bddc one level up), the three-level preconditioner is
-Eq. bddc with u_c = M_2 r_c.
+For elasticity a first-level object carries several coarse DOFs (reading R20: the
+mean of each displacement component, then rotation moments about the kept axes);
+the classes are then also split by that type, so that a level-2 coarse DOF is the
+mean of one kind of first-level coarse DOF (a displacement component, or a rotation
+moment about one axis) over the object.  With M_2 the level-2 BDDC preconditioner of
+A_c (Eq. bddc one level up), the three-level preconditioner is Eq. bddc with
+u_c = M_2 r_c.
 
 Pinned in tests/test_oracle_multilevel.py: one level-2 subdomain and the all-corner
 level-2 space both give M_2 = A_c^-1 (hence the two-level M); the level-2 objects of
@@ -52,6 +56,17 @@ def subdomain_blocks(mesh):
     return np.array([mesh.grid.block_of_cell(int(cells[0])) for cells in mesh.sub_cells], dtype=np.int64)
 
 
+def coarse_dof_types(two):
+    """Type of every first-level coarse DOF: its displacement component c (0..2; 0 for
+    Poisson), or 3 + k for a rotation moment about axis k (its row involves the two
+    components other than k)."""
+    out = []
+    for row in two.coarse_rows:
+        comps = sorted({c for (_, c) in row})
+        out.append(comps[0] if len(comps) == 1 else 3 + ({0, 1, 2} - set(comps)).pop())
+    return out
+
+
 def group_of_block(grid, b, G):
     """Group (G x G x G blocks) of block b, groups numbered x fastest."""
     nb = grid.nb
@@ -65,8 +80,6 @@ class CoarseBDDC:
 
     def __init__(self, two, group=2, coarse="cef", weighting="stiffness", all_interface_corners=False,
                  level1_corners=False):
-        if two.ncomp != 1:
-            raise ValueError("the three-level method is built for Poisson (one coarse DOF per object)")
         mesh = two.mesh
         self.Ac = two.Ac
         nsub, nc = mesh.n_sub, two.n_coarse
@@ -116,11 +129,12 @@ class CoarseBDDC:
         else:
             classes = {}
             kind1 = [two.objs[o]["kind"] for o in two.coarse_obj]
+            types = coarse_dof_types(two)
             for k in np.flatnonzero(gamma):
                 if level1_corners and kind1[k] == CORNER:
                     classes.setdefault(("corner", int(k)), []).append(int(k))
                 else:
-                    classes.setdefault(self.neigh2[k], []).append(int(k))
+                    classes.setdefault((types[k],) + self.neigh2[k], []).append(int(k))
             objs = []
             for key, ks in classes.items():
                 ns = self.neigh2[ks[0]]

@@ -148,3 +148,32 @@ def test_three_level_dominates_two_level(sbox):
     r3 = pcg(S.apply, S.b, T.apply, rtol=1e-10)
     assert r3["converged"] and r3["iterations"] > r2["iterations"]
     assert np.linalg.norm(r3["x"] - r2["x"]) <= 1e-8 * np.linalg.norm(r2["x"])
+
+
+@pytest.mark.parametrize("name,group", [("el_sphere8", 1), ("el_wall", 1), ("el_wall", 2)])
+def test_elastic_level2(name, group):
+    """Elasticity (reading R20 rows: component means, rotation moments): every level-2
+    object holds first-level coarse DOFs of one type only, C_2 Phi_2 = I, the weights
+    sum to one, M_2 is symmetric with lambda_min(M_2 A_c) >= 1, and PCG with the
+    three-level preconditioner reaches the two-level solution."""
+    from oracle.multilevel import coarse_dof_types
+    from tests.oracle_cache import oracle_run
+    orc = oracle_run(name)
+    B = orc.bddc()
+    L2 = CoarseBDDC(B, group=group)
+    types = coarse_dof_types(B)
+    assert set(types) <= set(range(6)) and {0, 1, 2} <= set(types)
+    assert all(len({types[k] for k in o["dofs"]}) == 1 for o in L2.objs)
+    for L in L2.local:
+        if L["cids"].size:
+            assert np.abs(L["C"] @ L["Phi"] - np.eye(L["cids"].size)).max() <= 1e-10
+    assert np.abs(L2.weight_sums() - 1.0).max() <= 1e-14
+    M2 = np.column_stack([L2.apply(e) for e in np.eye(L2.n)])
+    assert np.abs(M2 - M2.T).max() <= 1e-8 * np.abs(M2).max()
+    ev = np.sort(np.linalg.eigvals(M2 @ B.Ac).real)
+    assert ev[0] >= 1.0 - 1e-8 and ev[-1] > 1.0 + 1e-3
+    T = ThreeLevelBDDC(B, group=group)
+    r2 = pcg(orc.sys.apply, orc.sys.b, B.apply, rtol=1e-10, maxit=2000)
+    r3 = pcg(orc.sys.apply, orc.sys.b, T.apply, rtol=1e-10, maxit=2000)
+    assert r3["converged"]
+    assert np.linalg.norm(r3["x"] - r2["x"]) <= 1e-7 * np.linalg.norm(r2["x"])
