@@ -417,7 +417,7 @@ def adjoint_workload(U, dev, stream, flush, precision, reps=2, coarse_solver="au
             "level2_subdomains": bi["level2_subdomains"], "level3_coarse": bi["level3_coarse"]}
 
 
-def elastic_workload(U, dev, stream, flush, precision, reps=2):
+def elastic_workload(U, dev, stream, flush, precision, reps=2, coarse_solver="auto"):
     """Config-3 elasticity workload (the 96^3 union of 8 seeded spheres, 8^3 subdomains,
     3 DOFs per node): mesh, assembly, BDDC set-up and solve at rtol 1e-8 from device
     inputs, timed by CUDA events; returns the mean time-to-solution and the details."""
@@ -436,20 +436,23 @@ def elastic_workload(U, dev, stream, flush, precision, reps=2):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        with Solver(p, precision=precision, arrays=dict(arrays), stream=stream.cuda_stream) as S:
+        with Solver(p, precision=precision, arrays=dict(arrays), stream=stream.cuda_stream,
+                    coarse_solver=coarse_solver) as S:
             x = torch.zeros(S.n_dof, dtype=torch.float64, device=dev)
             _, fi = U.ufe_pcg_solve(S.system, S.bddc, None, x, rtol=RTOL, maxit=2000)
             e1.record(stream)
             torch.cuda.synchronize()
             bi = S.bddc_info
-            info = (S.n_dof, S.info["n_subdomains"], bi["n_coarse"], bi["setup_ms"], bi["fp64_subdomains"], fi)
+            info = (S.n_dof, S.info["n_subdomains"], bi["n_coarse"], bi["setup_ms"], bi["fp64_subdomains"], fi,
+                    bi["level3_coarse"])
         if rep > 0:
             times.append(e0.elapsed_time(e1) / 1e3)
         last = info
-    n, nsub, nc, setup_ms, n64, fi = last
+    n, nsub, nc, setup_ms, n64, fi, n3 = last
     return {"value": statistics.mean(times), "unit": "s", "reps": reps, "n_dof": n, "subdomains": nsub,
             "n_coarse": nc, "setup_s_device": setup_ms / 1e3, "solve_s_device": fi["solve_ms"] / 1e3,
-            "fp64_subdomains": n64, "iterations": fi["iterations"], "true_rel_residual": fi["true_rel_residual"]}
+            "fp64_subdomains": n64, "iterations": fi["iterations"], "true_rel_residual": fi["true_rel_residual"],
+            "level3_coarse": n3}
 
 
 def batched_workload(U, dev, stream, flush, reps=2):
@@ -640,6 +643,8 @@ def run_ours(args, rank, world):
             U, dev, stream, flush, "mixed", coarse_solver="bddc", keep_corners=True)
         extra["batched_256"] = batched_workload(U, dev, stream, flush)
         extra["elastic_96^3"] = {prec: elastic_workload(U, dev, stream, flush, prec) for prec in ("mixed", "fp64")}
+        extra["elastic_96^3"]["mixed_three_level"] = elastic_workload(U, dev, stream, flush, "mixed",
+                                                                      coarse_solver="bddc")
 
     n, info, binfo = i_mixed[-1]
     its = info["iterations"]

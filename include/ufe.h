@@ -83,7 +83,7 @@ typedef int ufe_status;
 #define UFE_COARSE_SOLVER_AUTO  0  /* dense inverse up to 2048 coarse DOFs, else cyclic reduction */
 #define UFE_COARSE_SOLVER_DENSE 1  /* explicit FP64 inverse of A_c (n_coarse up to ~28,000: r_c in one CTA's shared memory) */
 #define UFE_COARSE_SOLVER_CR    2  /* FP64 block cyclic reduction over the z layers of subdomain blocks */
-#define UFE_COARSE_SOLVER_BDDC  3  /* three-level method (Poisson): the coarse problem is not solved but
+#define UFE_COARSE_SOLVER_BDDC  3  /* three-level method: the coarse problem is not solved but
                                       preconditioned by BDDC over groups of coarse_group^3 blocks of
                                       subdomains, whose own coarse problem is inverted in FP64 */
 
@@ -350,10 +350,11 @@ typedef struct {
  * basis; the coarse matrix sum_w Phi^T A^w Phi is assembled in FP64 and solved
  * exactly in FP64: explicit inverse, or block cyclic reduction over the z layers of
  * subdomain blocks, in which order A_c is block tridiagonal (opts.coarse_solver).
- * With UFE_COARSE_SOLVER_BDDC (Poisson; Sect. 6 points to multilevel BDDC beyond one
- * coarse factorisation) A_c is instead preconditioned by BDDC one level up: level-2
+ * With UFE_COARSE_SOLVER_BDDC (Sect. 6 points to multilevel BDDC beyond one coarse
+ * factorisation) A_c is instead preconditioned by BDDC one level up: level-2
  * subdomains group coarse_group^3 blocks (split into components linked by shared
- * coarse DOFs), level-2 objects are the coarse DOFs shared by equal sets of level-2
+ * coarse DOFs), level-2 objects are the coarse DOFs of one type (Poisson: one; elasticity:
+ * a component mean or a rotation moment about one axis) shared by equal sets of level-2
  * subdomains (split into components; corners / edges / faces by opts.coarse), their
  * means are the level-3 DOFs, weights are stiffness weights of the level-2 matrices,
  * and the level-3 matrix is inverted in FP64.

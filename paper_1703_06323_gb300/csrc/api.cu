@@ -505,8 +505,6 @@ ufe_status ufe_bddc_setup(ufe_system* sys, const ufe_bddc_opts* opts, ufe_bddc**
     UFE_REQUIRE(opts->coarse >= UFE_COARSE_C && opts->coarse <= UFE_COARSE_CEF, UFE_ERR_INVALID_ARG, "bad coarse");
     UFE_REQUIRE(opts->coarse_solver >= UFE_COARSE_SOLVER_AUTO && opts->coarse_solver <= UFE_COARSE_SOLVER_BDDC,
                 UFE_ERR_INVALID_ARG, "bad coarse solver");
-    UFE_REQUIRE(opts->coarse_solver != UFE_COARSE_SOLVER_BDDC || sys->ncomp == 1, UFE_ERR_UNSUPPORTED,
-                "the three-level coarse solver: Poisson systems only");
     UFE_REQUIRE(opts->coarse_solver != UFE_COARSE_SOLVER_BDDC || (opts->coarse_group >= 0 && opts->coarse_group <= 1024),
                 UFE_ERR_INVALID_ARG, "coarse_group must lie in 0..1024");
     UFE_REQUIRE(opts->precision == UFE_PREC_FP64 || opts->precision == UFE_PREC_MIXED, UFE_ERR_INVALID_ARG,

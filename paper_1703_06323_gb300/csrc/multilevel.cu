@@ -13,6 +13,8 @@
 //     components under "held by a common subdomain"; face when |neigh_2| = 2, else
 //     corner for one coarse DOF and edge for more; the first level's choice of
 //     corners / edges / faces (opts.coarse) applies;
+//   * for elasticity the classes are also split by the type of first-level coarse
+//     DOF (a component mean, or a rotation moment about one axis);
 //   * level-2 coarse DOFs ("level 3"): the uniform mean over each object;
 //   * stiffness weights from the diagonals of A_2^J = sum_{w in J} A_c^w;
 //   * the level-3 matrix, assembled from Phi_2^JT A_2^J Phi_2^J, inverted exactly.
@@ -534,7 +536,6 @@ void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC,
   const Mesh& m = *B.mesh;
   const int ns = (int)m.n_sub;
   const int64_t nc = B.n_coarse;
-  UFE_REQUIRE(B.ncomp == 1, UFE_ERR_UNSUPPORTED, "the three-level coarse solver is built for Poisson");
   UFE_REQUIRE(group >= 1, UFE_ERR_INVALID_ARG, "coarse_group must be positive");
   L.n2 = 0;
   if (nc == 0) return;
@@ -590,21 +591,44 @@ void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC,
   };
   std::vector<Obj> objs;
   {
+    // the type of each first-level coarse DOF: its row within the object's rows, the
+    // component means first (0 .. ncomp-1), then the rotation moments about the kept
+    // axes k in increasing order (3 + k); classes are split by type, so that a level-2
+    // coarse DOF averages one kind of first-level coarse DOF
+    const std::vector<int32_t> cobj = to_host(B.coarse_obj.p, nc, s);
+    const std::vector<int32_t> cfirst = to_host(B.coarse_of_obj.p, B.n_obj, s);
+    const std::vector<int32_t> orot = to_host(B.obj_rot.p, B.n_obj, s);
+    std::vector<int32_t> type1(nc);
+    for (int64_t k = 0; k < nc; ++k) {
+      const int o = cobj[k], r = (int)(k - cfirst[o]);
+      int t = r;
+      if (r >= B.ncomp) {
+        for (int axis = 0, seen = 0; axis < 3; ++axis)
+          if ((orot[o] >> axis) & 1) {
+            if (seen == r - B.ncomp) t = 3 + axis;
+            ++seen;
+          }
+      }
+      type1[k] = t;
+    }
     // with coarse_keep_corners, a coarse DOF of a first-level corner is a level-2 corner
     std::vector<int32_t> kind1;
     if (B.coarse_keep_corners) {
-      const std::vector<int32_t> cobj = to_host(B.coarse_obj.p, nc, s);
       const std::vector<int32_t> okind = to_host(B.obj_kind.p, B.n_obj, s);
       kind1.resize(nc);
       for (int64_t k = 0; k < nc; ++k) kind1[k] = okind[cobj[k]];
     }
+    // key: the type, then neigh_2
     std::map<std::vector<int>, std::vector<int>> classes;
     for (int64_t k = 0; k < nc; ++k)
       if (neigh2[k].size() >= 2) {
-        if (!kind1.empty() && kind1[k] == UFE_OBJ_CORNER)
+        if (!kind1.empty() && kind1[k] == UFE_OBJ_CORNER) {
           objs.push_back(Obj{{(int)k}, neigh2[k], UFE_OBJ_CORNER});
-        else
-          classes[neigh2[k]].push_back((int)k);
+        } else {
+          std::vector<int> key{type1[k]};
+          key.insert(key.end(), neigh2[k].begin(), neigh2[k].end());
+          classes[key].push_back((int)k);
+        }
       }
     std::vector<int> cls(nc, -1), seen(nc, 0);
     int ci = 0;
@@ -629,10 +653,11 @@ void ml_setup(Bddc& B, const DBuf<double>& Acw, const std::vector<int64_t>& hCC,
             }
         }
         std::sort(comp.begin(), comp.end());
-        const int kind = kv.first.size() == 2 ? UFE_OBJ_FACE : (comp.size() == 1 ? UFE_OBJ_CORNER : UFE_OBJ_EDGE);
+        const std::vector<int> ns2(kv.first.begin() + 1, kv.first.end());
+        const int kind = ns2.size() == 2 ? UFE_OBJ_FACE : (comp.size() == 1 ? UFE_OBJ_CORNER : UFE_OBJ_EDGE);
         const bool keep = kind == UFE_OBJ_CORNER || (kind == UFE_OBJ_EDGE && B.opts.coarse != UFE_COARSE_C) ||
                           (kind == UFE_OBJ_FACE && B.opts.coarse == UFE_COARSE_CEF);
-        if (keep) objs.push_back(Obj{comp, kv.first, kind});
+        if (keep) objs.push_back(Obj{comp, ns2, kind});
       }
       ++ci;
     }

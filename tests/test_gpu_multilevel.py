@@ -4,8 +4,9 @@ DOF counts) bit for bit; z = M_3 r in the energy norm (FP64 1e-9, mixed 1e-3);
 PCG iteration counts at rtol 1e-8 (FP64 within 1; mixed at most 35 % + 1 above the
 oracle's FP64 count, see test_solution) and the solution
 at rtol 1e-12 against the oracle's discrete solution (FP64 1e-8, mixed 1e-6); the
-exact limit of one level-2 subdomain against the two-level method; and the 64^3
-bumpy sphere solved by both methods to the same solution.
+exact limit of one level-2 subdomain against the two-level method; the 64^3
+bumpy sphere solved by both methods to the same solution; and elasticity, whose
+level-2 classes are split by the type of first-level coarse DOF.
 """
 import numpy as np
 import pytest
@@ -135,11 +136,35 @@ def test_bench_workload_three_level(ufe):
     assert out["bddc", "fp64"][0] >= out["dense", "fp64"][0]
 
 
-def test_elasticity_is_refused(ufe):
-    from tests.oracle_cache import elastic_problems
-    with pytest.raises(ufe.UfeError) as e:
-        _solver(elastic_problems()["el_sphere8"], coarse_solver="bddc")
-    assert e.value.status == ufe.ERR_UNSUPPORTED
+@pytest.mark.parametrize("name,group", [("el_sphere8", 1), ("el_wall", 1), ("el_wall", 2)])
+def test_elastic_three_level(ufe, name, group):
+    """Elasticity: level-2 classes split by the type of first-level coarse DOF.  Counts
+    bit for bit, M_3 r against the oracle in the energy norm to 1e-6 (the FP64
+    elasticity tolerance: S_c reaches condition 1e9 with rotation rows), FP64
+    iterations within one of the oracle's three-level PCG, the rtol 1e-12 solution
+    against the oracle's discrete one to 1e-8, and mixed precision converging to it
+    within 1e-6."""
+    from oracle.multilevel import ThreeLevelBDDC
+    from oracle.pcg import pcg
+    orc = _run(name)
+    T = ThreeLevelBDDC(orc.bddc(), group=group)
+    r = np.random.default_rng(25).normal(size=orc.sys.n)
+    ref = T.apply(r)
+    ref8 = pcg(orc.sys.apply, orc.sys.b, T.apply, rtol=1e-8, maxit=2000)
+    exact = orc.solve(rtol=1e-12)["x"]
+    with _solver(orc.p, coarse_solver="bddc", coarse_group=group) as S:
+        bi = S.bddc_info
+        assert bi["level2_subdomains"] == T.level2.n_sub2 and bi["level3_coarse"] == T.level2.n_coarse
+        z = S.precondition(r)
+        x, info = S.solve(rtol=1e-8)
+        assert info["converged"] == 1 and info["true_rel_residual"] <= 1.5e-8
+        assert abs(info["iterations"] - ref8["iterations"]) <= 1
+        x12, info12 = S.solve(rtol=1e-12, maxit=3000)
+    assert energy_error(orc.sys.A, z, ref) <= 1e-6
+    assert info12["converged"] == 1 and energy_error(orc.sys.A, x12, exact) <= 1e-8
+    with _solver(orc.p, precision="mixed", coarse_solver="bddc", coarse_group=group) as S:
+        xm, infom = S.solve(rtol=1e-12, maxit=3000)
+    assert infom["converged"] == 1 and energy_error(orc.sys.A, xm, exact) <= 1e-6
 
 
 @pytest.mark.parametrize("name,weighting,coarse", [("tower", "topological", "cef"), ("ml_box", "stiffness", "ce")])
