@@ -61,3 +61,31 @@ def test_fp32_tensor_update_uses_the_sustained_tf32_peak():
     assert out["kernel"] == "gj_update_f32" and out["bound"] == "tensor"
     assert math.isclose(out["peak"], tf32, rel_tol=1e-12)
     assert math.isclose(out["work_per_launch"], 1.0e11 / 14, rel_tol=1e-12)
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_reads_median_clock_and_throttle_reasons():
+    """The clocks record of the bench line: median SM clock over the samples taken
+    during the timed steps, the maximum clock, and every throttle reason seen Active
+    (hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown reject a run; sw_power_cap
+    is kept and noted)."""
+    c = bench.ClockSampler(0)
+    c.proc = _FakeProc()
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    out = c.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    c2 = bench.ClockSampler(0)
+    c2.proc = _FakeProc()
+    c2.lines = ["0, 1500, 2070, 1000, 0x40, Not Active, Active, Not Active, Not Active"]
+    assert c2.stop()["reasons"] == ["hw_thermal_slowdown"]
