@@ -8,7 +8,7 @@ import pytest
 from oracle import integration as IN
 from oracle import quadrature as Q
 from oracle.assembly import System
-from oracle.mesh import Mesh, CUT, INTERNAL
+from oracle.mesh import Mesh, INTERNAL
 from paper_1703_06323_gb300 import inputs
 
 
