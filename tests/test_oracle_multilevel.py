@@ -10,7 +10,11 @@
   make M_2 = A_c^-1, so the three-level M is the two-level M;
 * C_2 Phi_2 = I on every level-2 subdomain and the level-2 weights sum to one;
 * M_2 is symmetric with lambda_min(M_2 A_c) >= 1 (the Sect. 3.4 argument one level
-  up), so M_3 >= M and the eigenvalues of M_3 A bound those of M A from above in order.
+  up), so M_3 >= M and the eigenvalues of M_3 A bound those of M A from above in order;
+* the option keeping first-level corners as level-2 corners, counted by hand on the
+  same box;
+* elasticity: one type of first-level coarse DOF per level-2 object, and the same
+  properties on three elastic cases.
 """
 import numpy as np
 import pytest
